@@ -1,0 +1,418 @@
+#!/usr/bin/env python3
+"""Benchmark of the Duplex-GS hot path on GB300.
+
+Workload: the multi-scale scene (100,000 cells x 10 Gaussians = 1M, SH
+degree 3, cell axes log-uniform [0.001, 1] in [-10,10]^3, seed 0) rendered
+from 8 seeded cameras on a sphere of radius 15 at 1920x1080.  One step = the
+whole hot path over that batch: binning (cull, depth sort over cells, scan,
+emit, tile sort, ranges), Gaussian projection, hybrid blend, L1 loss to
+seeded target images, blend adjoint and projection adjoint.
+Metric: Mpix/s fwd+bwd = views * W * H / step time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--no-serve]
+
+Under torchrun (N > 1) every rank renders its own 8 views (independent
+units, no collective on the data path): weak scaling, max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+W_IMG, H_IMG, N_VIEWS = 1920, 1080, 8
+METRIC = "Mpix/s fwd+bwd at 1M Gaussians 1080p"
+UNIT = "Mpix/s"
+WORKLOAD = "multiscale-1M-gaussians (100k cells x 10, SH3) 8 views 1920x1080 fwd+bwd L1"
+# FP32 operations of one (pixel, Gaussian) pair that passes the AABB test,
+# counted from the kernels: forward 23 (offset 2, quadratic form 8, exp2 1,
+# opacity and clamp 2, colour 6, alpha sum 1, transmittance 3); backward
+# adds 37 (alpha adjoint 8, colour 7, v_n 3, opacity 2, quadratic 3,
+# mean 8, conic 6) to the 23 of the replay.
+FLOP_FWD = 23
+FLOP_BWD = 60
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def fp32_peak_tflops(sm_mhz):
+    # 152 SMs x 128 FP32 lanes x 2 FLOP per FMA x clock
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [r[0] for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+def dist_setup(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cameras_for(rank):
+    from paper_2508_03180_gb300 import synth
+    return synth.sphere_cameras(N_VIEWS, 15.0, W_IMG, H_IMG, seed0=N_VIEWS * rank)
+
+
+def cpu_sample(scene, cam, rows, threads_note=True):
+    """Oracle fwd+bwd on tile rows [0, rows) of one view; returns (pixels, seconds)."""
+    import oracle
+    H, W = int(cam[1]), int(cam[0])
+    rng = np.random.default_rng(7)
+    dl = rng.standard_normal((3, H, W)) / (3 * H * W)
+    t0 = time.perf_counter()
+    oracle.render_and_grad(scene, cam, dl, tile_rows=(0, rows))
+    dt = time.perf_counter() - t0
+    return rows * 16 * W, dt
+
+
+def run_reference(args):
+    """The oracle (CPU, FP64) on the machine's host cores, same metric."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_2508_03180_gb300 import synth
+    oracle.build()
+    scene = synth.scene_multiscale()
+    cams = [c.as_array() for c in cameras_for(0)]
+    budget_s = 150.0 / max(1, args.steps + args.warmup)
+    # calibrate the band height on one tile row
+    _, t1 = cpu_sample(scene, cams[0], 1)
+    rows = int(max(1, min(68, budget_s / max(t1, 1e-3))))
+    px_tot, t_tot = 0, 0.0
+    for i in range(args.warmup + args.steps):
+        px, dt = cpu_sample(scene, cams[i % N_VIEWS], rows)
+        if i >= args.warmup:
+            px_tot += px
+            t_tot += dt
+    v = px_tot / t_tot / 1e6
+    sample = f"oracle fwd+bwd (FP64) on tile rows 0..{rows - 1} ({rows * 16} px rows) of one 1920x1080 view per step"
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_tot / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def serving_bench(rctx, seconds=2.0, rate=200.0, seed=0):
+    """Poisson arrivals over 3 resident scenes, mixed resolutions; batched
+    continuous serving vs one request at a time on the same trace."""
+    import torch
+
+    from paper_2508_03180_gb300 import synth
+    scenes = [synth.scene_small(seed=s, n_cells=n) for s, n in ((1, 12_500), (2, 62_500), (3, 250_000))]
+    sids = [rctx.upload_scene(s) for s in scenes]
+    res_opts = [(640, 480), (1280, 720), (1920, 1080), (3840, 2160)]
+    rng = np.random.default_rng(seed)
+    n_req = int(seconds * rate)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
+    reqs = []
+    for i in range(n_req):
+        s = int(rng.integers(0, 3))
+        W, H = res_opts[int(rng.integers(0, 4))]
+        cam = synth.sphere_cameras(1, 3.0, W, H, seed0=10_000 + i)[0]
+        reqs.append((sids[s], cam, W, H))
+    outs = [torch.empty(3 * H * W, device="cuda") for (_, _, W, H) in reqs]
+
+    def run(max_batch):
+        rctx.serve_start(max_batch=max_batch, queue_cap=4096)
+        # warm-up: one of each resolution
+        for k in range(4):
+            t = rctx.submit(reqs[k][0], reqs[k][1], outs[k])
+            rctx.poll(t, -1)
+        t0 = time.perf_counter()
+        tickets = []
+        for i, (sid, cam, W, H) in enumerate(reqs):
+            delay = t0 + arrivals[i] - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append(rctx.submit(sid, cam, outs[i]))
+        lat, bs = [], []
+        for t in tickets:
+            r = rctx.poll(t, -1)
+            lat.append(r.t_done_ms - r.t_submit_ms)
+            bs.append(r.batch_size)
+        t_end = time.perf_counter()
+        rctx.serve_stop()
+        return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "fps": n_req / (t_end - t0), "mean_batch": float(np.mean(bs))}
+
+    batched = run(8)
+    serial = run(1)
+    for s in sids:
+        rctx.release_scene(s)
+    return {"workload": "3 resident scenes (100k, 500k, 2M Gaussians), Poisson 200 req/s, "
+                        "640x480..3840x2160", "requests": n_req, "batched": batched, "one_at_a_time": serial}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    from paper_2508_03180_gb300 import synth
+    from paper_2508_03180_gb300.renderer import Context
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    rctx = Context(device=local)
+    scene = synth.scene_multiscale()
+    sid = rctx.upload_scene(scene)
+    cams = cameras_for(rank)
+    slots = rctx.set_cameras(cams)
+    G, N, C = scene.G, scene.N, 16
+    target = torch.from_numpy(synth.target_image(N_VIEWS, H_IMG, W_IMG, seed=100 + rank)).cuda().reshape(-1)
+    img = torch.empty(N_VIEWS * 3 * H_IMG * W_IMG, device="cuda")
+    dl = torch.empty_like(img)
+    loss = torch.empty(1, device="cuda")
+    grads = dict(g_mean=torch.empty(G, 3, device="cuda"), g_log_scale=torch.empty(G, 3, device="cuda"),
+                 g_quat=torch.empty(G, 4, device="cuda"), g_logit=torch.empty(G, device="cuda"),
+                 g_sh=torch.empty(G, C, 3, device="cuda"))
+
+    def step():
+        _, state, _ = rctx.render(sid, cams, want_state=True, out=img, slots=slots)
+        rctx.loss_l1(img, target, dl, loss)
+        rctx.backward(state, dl, grads)
+        rctx.release_state(state)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    # work counters of one step (outside the timed region)
+    _, st0, stats = rctx.render(sid, cams, want_state=True, out=img, slots=slots, stats=True)
+    cnt = rctx.counts(st0)
+    rctx.release_state(st0)
+    torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream()
+    clocks = Clocks(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    rctx.profile_enable(True)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier(world)
+    prof = rctx.profile_read()
+    rctx.profile_enable(False)
+    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(ms, world)
+    px_step = N_VIEWS * W_IMG * H_IMG
+    value = world * px_step * args.steps / (ms / 1e3) / 1e6
+
+    # dominant kernel and its roofline
+    stage_ms = {k: v[0] / max(1, v[1]) for k, v in prof.items() if v[1] > 0}
+    total_stage = sum(v[0] for v in prof.values())
+    dom = max(prof, key=lambda k: prof[k][0])
+    peaks, src = load_peaks()
+    sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    if dom in ("blend_fwd", "blend_bwd"):
+        flop = cnt["inbox_rendered"] * (FLOP_FWD if dom == "blend_fwd" else FLOP_BWD)
+        ach = flop / (stage_ms[dom] / 1e3) / 1e12
+        peak = fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+        roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": None, "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x max SM clock",
+                "flop_per_launch": flop}
+    else:
+        nbytes = {"project_fwd": G * (59 * 4) + N_VIEWS * G * 48, "project_bwd": G * (59 * 4) * 2 + N_VIEWS * G * 96}
+        b = nbytes.get(dom, 0)
+        ach = b / (stage_ms[dom] / 1e3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": src}
+
+    # end to end through the C ABI with host buffers: parameters arrive from
+    # pinned host memory (scene update), gradients and loss return to it
+    import ctypes
+
+    from paper_2508_03180_gb300 import _lib as L
+    host = {k: torch.from_numpy(np.ascontiguousarray(getattr(scene, k))).pin_memory()
+            for k in ("g_mean", "g_scale", "g_quat", "g_logit", "g_sh")}
+    hgr = {k: torch.empty(v.shape, dtype=torch.float32).pin_memory() for k, v in grads.items()}
+    hloss = torch.empty(1).pin_memory()
+    desc = L.dgs_scene_desc()
+    desc.num_cells, desc.K, desc.sh_degree, desc.location = N, scene.K, scene.sh_degree, L.DGS_HOST
+    for k, v in host.items():
+        setattr(desc, k, v.data_ptr())
+    gstruct = L.dgs_grads()
+    gstruct.location = L.DGS_HOST
+    for k, v in hgr.items():
+        setattr(gstruct, k, v.data_ptr())
+    h2d = sum(v.numel() * 4 for v in host.values())
+    d2h = sum(v.numel() * 4 for v in hgr.values()) + 4
+
+    def e2e_step():
+        L.dgs_scene_update(rctx.ctx, sid, desc, stream.cuda_stream)
+        _, state, _ = rctx.render(sid, cams, want_state=True, out=img, slots=slots)
+        rctx.loss_l1(img, target, dl, loss)
+        L.dgs_render_backward(rctx.ctx, state, dl.data_ptr(), L.DGS_DEVICE, gstruct, stream.cuda_stream)
+        hloss.copy_(loss, non_blocking=True)
+        rctx.release_state(state)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    e2 = args.steps
+    for _ in range(e2):
+        e2e_step()
+    torch.cuda.synchronize()
+    t_e2e = max_over_ranks(time.perf_counter() - t0, world)
+    e2e_value = world * px_step * e2 / t_e2e / 1e6
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "views_per_step": N_VIEWS, "resolution": [W_IMG, H_IMG],
+                       "gaussians": G, "cells": N, "l2": "inputs larger than L2 (236 MB parameters, 384 MB records)",
+                       "sort_length_per_step": int(stats.sort_length), "visible_cells_per_step": int(stats.visible_cells),
+                       "termination_ratio": 1.0 - cnt["inbox_rendered"] / max(1, cnt["inbox_all"])},
+            "fwd_mpix_s": None,
+            "stage_ms_per_step": {k: prof[k][0] / args.steps for k in prof},
+            "stage_share": {k: prof[k][0] / total_stage for k in prof if total_stage > 0},
+            "roofline": roof, "clocks": clk,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": None}
+    fwd_ms = sum(prof[k][0] for k in ("cell_project", "depth_sort", "count_scan", "emit", "tile_sort",
+                                       "tile_ranges", "project_fwd", "blend_fwd")) / args.steps
+    line["fwd_mpix_s"] = px_step / (fwd_ms / 1e3) / 1e6 if fwd_ms > 0 else None
+    # kernel launches per step: binning 11 + sort passes + projection + blend + backward 2 + loss 2
+    line["gpu_launches"] = int(args.steps * launches_per_step(stats))
+
+    if rank == 0 and not args.no_serve:
+        try:
+            line["serving"] = serving_bench(rctx)
+        except Exception as e:  # serving is reported beside the headline, never instead of it
+            line["serving"] = {"error": str(e)}
+    if rank == 0 and not args.no_cpu:
+        import oracle
+        oracle.build()
+        c0 = cams[0].as_array()
+        _, t1 = cpu_sample(scene, c0, 1)
+        rows = int(max(1, min(68, 15.0 / max(t1, 1e-3))))
+        px, dt = cpu_sample(scene, c0, rows)
+        line["cpu_baseline"] = {"value": px / dt / 1e6, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                                "sample": f"oracle fwd+bwd (FP64) on tile rows 0..{rows - 1} of view 0 "
+                                          f"({rows * 16 * W_IMG} px)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    rctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def launches_per_step(stats):
+    # kernels of one fwd+bwd step: cell projection 1; depth sort 2 + 4 passes; gather 1; scan 3;
+    # emit 1; tile sort 2 + ceil(bits/8) passes; ranges 1; projection 1; blend 1; loss 2;
+    # blend adjoint 1; projection adjoint 1
+    tiles = int(stats.num_tiles)
+    bits = max(1, math.ceil(math.log2(max(2, tiles))))
+    return 1 + (2 + 4) + 1 + 3 + 1 + (2 + math.ceil(bits / 8)) + 1 + 1 + 1 + 2 + 1 + 1
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,275 @@
+/*
+ * dgs.h -- C ABI of the GB300 (sm_103a) Duplex-GS hybrid renderer hot path.
+ *
+ * The operation (Duplex-GS, arXiv 2508.03180):
+ *   * A scene is a set of ellipsoidal cell proxies (centre x_n, semi-axes
+ *     S_n, rotation Q_n, calibration scalar v_n), each emitting K Gaussians
+ *     (Sec. IV-A, Eq. 1).
+ *   * Per view, cells are projected to the screen, culled to the frustum and
+ *     assigned to 16x16 tiles; a radix sort orders (tile, cell depth) keys
+ *     over cells only, never over Gaussians (Sec. IV-B).
+ *   * Per pixel, the tile's cells are walked front to back.  Inside a cell
+ *     the K Gaussians are summed order-independently (weighted-sum
+ *     rendering); across cells the weights w_n = v_n T_n^cell follow
+ *     alpha-blending style transmittance, and blending halts once T^cell
+ *     drops below eps (Sec. V, Eq. 12-14).  A Gaussian is skipped at a pixel
+ *     outside its screen AABB (Sec. VI-A).
+ *   * render_backward is the adjoint of that image with respect to every
+ *     Gaussian parameter (the paper trains through this renderer, Sec. VI).
+ *
+ * Conventions for every call:
+ *   * Return value: DGS_OK (0) or a negative dgs_status; no call aborts the
+ *     process.  dgs_last_error() gives a message for the calling thread.
+ *   * Pointers are plain host or device addresses; a `location` field says
+ *     which.  Inputs are read during the call (host inputs are copied before
+ *     the call returns); the caller keeps ownership of everything it passes.
+ *   * Device work is enqueued on the given stream (a cudaStream_t, NULL =
+ *     legacy default stream) and is asynchronous unless stated otherwise.
+ *     Host outputs are complete when the call returns.
+ *   * Layouts are row-major, float32, structure-of-arrays per parameter.
+ */
+#ifndef DGS_H
+#define DGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t dgs_status;
+enum {
+    DGS_OK = 0,
+    DGS_ERR_INVALID_ARG = -1, /* bad pointer, size, id or option */
+    DGS_ERR_OOM = -2,         /* device allocation failed (or the HBM budget is exhausted) */
+    DGS_ERR_NOT_FOUND = -3,   /* unknown scene / camera slot / ticket / state */
+    DGS_ERR_CUDA = -4,        /* a CUDA call or a kernel failed; see dgs_last_error */
+    DGS_ERR_TIMEOUT = -5,     /* poll timed out, or a bounded device wait gave up */
+    DGS_ERR_BUSY = -6,        /* request queue full; retry later */
+    DGS_ERR_CAPACITY = -7     /* a size exceeds a fixed maximum of the call */
+};
+
+enum { DGS_HOST = 0, DGS_DEVICE = 1 };
+
+typedef struct dgs_ctx dgs_ctx;
+typedef struct dgs_fwd_state dgs_fwd_state;
+typedef void *dgs_stream; /* cudaStream_t */
+
+/* Renderer settings.  dgs_config_default() fills the defaults below. */
+typedef struct {
+    float eps;        /* 1e-4: halt when T^cell < eps (Sec. V-B; the 3DGS threshold, Sec. VII-D) */
+    float alpha_max;  /* 0.99: alpha = min(sigma G', alpha_max); alpha in [0,1] (Sec. V-A) */
+    float d_min;      /* 1e-10: a pixel with sum_n w_n sum_k alpha <= d_min shows the background */
+    float bg[3];      /* background colour (0,0,0) */
+    float dilation;   /* 0.3 px^2 added to the EWA screen covariance */
+    float ksigma;     /* 3: AABB half extent in standard deviations (Sec. VI-A) */
+    int32_t device;   /* CUDA device ordinal (0) */
+    int32_t reserved;
+    int64_t hbm_budget_bytes; /* serving admission budget; 0 = 90% of free memory at create */
+} dgs_config;
+
+void dgs_config_default(dgs_config *cfg);
+
+/* Create a context on cfg->device (NULL = defaults).  The context owns every
+ * device buffer it allocates; destroy frees them.  Thread-safe per call. */
+dgs_status dgs_create(const dgs_config *cfg, dgs_ctx **out);
+void dgs_destroy(dgs_ctx *ctx);
+const char *dgs_last_error(dgs_ctx *ctx);
+
+/* ---------------------------------------------------------------- scenes */
+
+/* A scene: N cells, each emitting K Gaussians (Gaussian g belongs to cell
+ * g / K; G = N K).  All arrays float32, in `location` memory:
+ *   cell_center [N][3], cell_axes [N][3] (semi-axes S_n), cell_quat [N][4]
+ *   (w,x,y,z; normalised by the renderer), cell_v [N] (v_n in [0,1]; NULL = 1)
+ *   g_mean [G][3], g_scale [G][3] (linear standard deviations),
+ *   g_quat [G][4] (w,x,y,z), g_logit [G] (opacity = sigmoid(logit)),
+ *   g_sh [G][(sh_degree+1)^2][3] real spherical-harmonic colour
+ *   coefficients (colour = max(0, 0.5 + sum_lm k_lm Y_lm(view dir))).
+ * The data are copied into context memory.  K in [1, 32], sh_degree in 0..3,
+ * N >= 0 (an empty scene renders the background). */
+typedef struct {
+    int64_t num_cells;
+    int32_t K;
+    int32_t sh_degree;
+    int32_t location; /* DGS_HOST or DGS_DEVICE */
+    int32_t reserved;
+    const float *cell_center, *cell_axes, *cell_quat, *cell_v;
+    const float *g_mean, *g_scale, *g_quat, *g_logit, *g_sh;
+} dgs_scene_desc;
+
+dgs_status dgs_scene_upload(dgs_ctx *ctx, const dgs_scene_desc *desc, uint32_t *scene_id);
+/* Overwrite the Gaussian parameters (and v) of an existing scene in place,
+ * same N, K and degree (a training step's update).  Asynchronous on stream
+ * for device inputs. */
+dgs_status dgs_scene_update(dgs_ctx *ctx, uint32_t scene_id, const dgs_scene_desc *desc, dgs_stream stream);
+dgs_status dgs_scene_release(dgs_ctx *ctx, uint32_t scene_id);
+
+/* ---------------------------------------------------------------- cameras */
+
+/* Pinhole camera.  R, t map world to view space (x right, y down, +z
+ * forward; row-major R).  eye is the camera centre in world space (used for
+ * the colour's view direction).  Pixel (i,j) is sampled at (i+0.5, j+0.5).
+ * Gaussians and cells must lie beyond znear to be drawn. */
+typedef struct {
+    int32_t W, H;
+    float fx, fy, cx, cy, znear;
+    float R[9], t[3], eye[3];
+} dgs_camera;
+
+/* Store a camera in slot `slot` (0 .. 4095). */
+dgs_status dgs_camera_set(dgs_ctx *ctx, uint32_t slot, const dgs_camera *cam);
+
+/* ---------------------------------------------------------------- render */
+
+typedef struct {
+    int64_t sort_length;   /* L: (tile, cell) pairs sorted, summed over views */
+    int64_t visible_cells; /* (view, cell) pairs that survived culling */
+    int64_t num_tiles;     /* tiles over all views */
+    float ms_total;        /* device time of the call, only if timing was requested */
+    int32_t timing;        /* in: nonzero = record CUDA events and synchronise */
+    int32_t reserved;
+} dgs_stats;
+
+/* Render n_views views of one scene in one batched launch chain.
+ * cam_slots[v] selects each view's camera.  out_rgb receives the images
+ * back to back, view v as [3][H_v][W_v] planar float32 (offset = sum of
+ * 3 H W of the views before it), in out_location memory.
+ * state (nullable): if non-NULL, *state receives a handle that keeps this
+ * render's intermediate buffers for dgs_render_backward; it stays owned by
+ * the context until dgs_state_release.  stats (nullable): filled on return;
+ * this call synchronises the stream once after binning (to size the sort). */
+dgs_status dgs_render(dgs_ctx *ctx, uint32_t scene_id, int32_t n_views, const uint32_t *cam_slots,
+                      float *out_rgb, int32_t out_location, dgs_fwd_state **state, dgs_stream stream,
+                      dgs_stats *stats);
+
+/* Gradients of a scalar loss with respect to the scene parameters, given
+ * dL/d(image) in the layout of out_rgb.  Every non-NULL output is
+ * OVERWRITTEN (not accumulated), same layout as the scene arrays:
+ *   g_mean [G][3], g_scale [G][3] (dL/dscale), g_log_scale [G][3]
+ *   (= scale * dL/dscale), g_quat [G][4], g_logit [G], g_sh [G][C][3],
+ *   g_cell_v [N].
+ * Discrete choices of the forward (culling, tile lists, AABB skips, alpha
+ * clamp, the per-pixel number of blended cells) are held fixed. */
+typedef struct {
+    int32_t location;
+    int32_t reserved;
+    float *g_mean, *g_scale, *g_log_scale, *g_quat, *g_logit, *g_sh, *g_cell_v;
+} dgs_grads;
+
+dgs_status dgs_render_backward(dgs_ctx *ctx, dgs_fwd_state *state, const float *dL_drgb, int32_t location,
+                               const dgs_grads *out, dgs_stream stream);
+dgs_status dgs_state_release(dgs_ctx *ctx, dgs_fwd_state *state);
+
+/* L1 photometric loss mean|rgb - target| over n floats (device pointers),
+ * writing dL/drgb = sign(rgb - target) / n and the loss value (device
+ * float).  Deterministic. */
+dgs_status dgs_loss_l1(dgs_ctx *ctx, const float *rgb, const float *target, int64_t n, float *dL_drgb,
+                       float *loss, dgs_stream stream);
+
+/* Copy one intermediate buffer of a forward state to host memory (tests
+ * and diagnostics).  `what`:
+ *   DGS_BUF_CELL_RECT   int32 [V][N][4]  tx0 ty0 tx1 ty1 (tx0 = -1: culled)
+ *   DGS_BUF_CELL_DEPTH  float [V][N]     view depth of the cell centre
+ *   DGS_BUF_TILE_CELLS  uint32 [L]       cell ids, ordered by (global tile, depth, cell)
+ *   DGS_BUF_TILE_RANGES uint32 [T][2]    [start,end) per global tile (view-major tiles)
+ *   DGS_BUF_GAUSS_REC   float [V][G][12] mu_x mu_y ext_x ext_y | conic*(-log2 e/2, -log2 e, -log2 e/2) opacity | r g b v
+ *   DGS_BUF_PIX_D       float [P]        per-pixel weight sum D (P = all views' pixels)
+ *   DGS_BUF_PIX_NDONE   int32 [P]        per-pixel number of blended cells
+ *   DGS_BUF_GRAD2D      float [V][G][12] after backward: dmu_x dmu_y da db dc dsigma dr dg db 0 0 0
+ * *needed receives the byte size; nothing is copied if bytes < needed.
+ * Synchronises the stream the state was rendered on. */
+enum {
+    DGS_BUF_CELL_RECT = 1,
+    DGS_BUF_CELL_DEPTH = 2,
+    DGS_BUF_TILE_CELLS = 3,
+    DGS_BUF_TILE_RANGES = 4,
+    DGS_BUF_GAUSS_REC = 5,
+    DGS_BUF_PIX_D = 6,
+    DGS_BUF_PIX_NDONE = 7,
+    DGS_BUF_GRAD2D = 8
+};
+dgs_status dgs_state_read(dgs_ctx *ctx, const dgs_fwd_state *state, int32_t what, void *host_dst, int64_t bytes,
+                          int64_t *needed);
+
+/* Stable radix sort of (uint32 key, uint32 value) pairs by the low `bits`
+ * bits of the key (the sort used for binning, exposed for tests).  All
+ * pointers device; keys/vals are overwritten with the sorted sequence.
+ * Uses context scratch memory. */
+dgs_status dgs_sort_pairs(dgs_ctx *ctx, uint32_t *keys, uint32_t *vals, int64_t n, int32_t bits, dgs_stream stream);
+
+/* ---------------------------------------------------------------- diagnostics */
+
+/* Work counters of a forward state, over all its views (Sec. VII-E defines
+ * the termination ratio r_ET = 1 - N_rendered / N_val):
+ *   pairs_blended   (pixel, Gaussian) pairs of the cells each pixel blended
+ *   inbox_rendered  of those, pairs that passed the AABB test (N_rendered)
+ *   inbox_all       pairs passing the AABB test over ALL cells of the pixel's
+ *                   tile list, i.e. without early termination (N_val)
+ *   cells_blended   (pixel, cell) pairs blended
+ * Runs a counting kernel on the state's stream and synchronises it. */
+typedef struct {
+    int64_t pairs_blended, inbox_rendered, inbox_all, cells_blended;
+} dgs_counts;
+dgs_status dgs_state_counts(dgs_ctx *ctx, const dgs_fwd_state *state, dgs_counts *out);
+
+/* Per-stage device time.  While enabled, every stage of render and
+ * render_backward is bracketed by CUDA events on the stream it runs on (no
+ * synchronisation); dgs_profile_read waits for the recorded events and
+ * returns the accumulated milliseconds and launch counts per stage since
+ * the last enable.  Stages: */
+enum {
+    DGS_STAGE_CELL_PROJECT = 0, /* a1: cull + footprint of every (view, cell) */
+    DGS_STAGE_DEPTH_SORT = 1,   /* a4: radix sort of cells by depth */
+    DGS_STAGE_COUNT_SCAN = 2,   /* a2: tile counts in depth order + exclusive scan */
+    DGS_STAGE_EMIT = 3,         /* a3: (tile, cell) pairs */
+    DGS_STAGE_TILE_SORT = 4,    /* a4: stable radix sort of the pairs by tile */
+    DGS_STAGE_TILE_RANGES = 5,  /* a5 */
+    DGS_STAGE_PROJECT_FWD = 6,  /* a6: Gaussian projection */
+    DGS_STAGE_BLEND_FWD = 7,    /* a7 */
+    DGS_STAGE_BLEND_BWD = 8,    /* a8 */
+    DGS_STAGE_PROJECT_BWD = 9,  /* a9 */
+    DGS_STAGE_COUNT = 10
+};
+typedef struct {
+    double ms[16];
+    int64_t launches[16];
+} dgs_profile;
+dgs_status dgs_profile_enable(dgs_ctx *ctx, int32_t on);
+dgs_status dgs_profile_read(dgs_ctx *ctx, dgs_profile *out);
+
+/* ---------------------------------------------------------------- serving */
+
+/* Continuous-batching request loop (not in the paper; serving workload).
+ * A request renders one view of a resident scene into out_rgb ([3][H][W],
+ * device or host memory per out_location).  Requests that arrive while
+ * others run are admitted into the next batch as slots and HBM allow; each
+ * batch is one launch chain over views of mixed scenes and resolutions. */
+typedef struct {
+    uint32_t scene_id;
+    int32_t out_location;
+    dgs_camera camera;
+    float *out_rgb;
+} dgs_request;
+
+typedef struct {
+    dgs_status status;
+    int32_t batch_size;   /* views in the batch this request ran in */
+    double t_submit_ms, t_start_ms, t_done_ms; /* host monotonic clock */
+} dgs_result;
+
+/* Start the serving worker (max_batch views per launch chain, queue_cap
+ * pending requests).  Idempotent. */
+dgs_status dgs_serve_start(dgs_ctx *ctx, int32_t max_batch, int32_t queue_cap);
+dgs_status dgs_serve_stop(dgs_ctx *ctx);
+dgs_status dgs_submit(dgs_ctx *ctx, const dgs_request *req, uint64_t *ticket);
+/* Wait up to timeout_us (0 = just check, <0 = forever) for a ticket.
+ * DGS_ERR_TIMEOUT if not done yet; the ticket stays valid.  A finished
+ * ticket is consumed by a successful poll. */
+dgs_status dgs_poll(dgs_ctx *ctx, uint64_t ticket, int64_t timeout_us, dgs_result *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DGS_H */

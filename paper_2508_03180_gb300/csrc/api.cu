@@ -1,0 +1,832 @@
+// Host runtime behind include/dgs.h: contexts, resident scenes, camera
+// slots, per-render workspaces, and the launch chains of render and
+// render_backward.  Every step of the hot path runs in this library's own
+// kernels (binning.cu, sort.cu, project.cu, blend.cu, misc.cu).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/dgs.h"
+#include "internal.cuh"
+#include "runtime.h"
+
+using namespace dgs;
+
+static thread_local std::string g_last_error;
+
+namespace dgs {
+
+dgs_status set_error(dgs_status code, const std::string &msg) {
+    g_last_error = msg;
+    return code;
+}
+
+dgs_status cuda_error(cudaError_t e, const char *what) {
+    return set_error(e == cudaErrorMemoryAllocation ? DGS_ERR_OOM : DGS_ERR_CUDA,
+                     std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(x)                                                 \
+    do {                                                      \
+        cudaError_t e_ = (x);                                 \
+        if (e_ != cudaSuccess) return cuda_error(e_, #x);     \
+    } while (0)
+
+dgs_status DevBuf::ensure(size_t bytes) {
+    if (bytes <= cap) return DGS_OK;
+    if (p) {
+        cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+    size_t want = bytes + bytes / 8 + 256;
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+        return set_error(DGS_ERR_OOM, "device allocation of " + std::to_string(want) + " bytes failed");
+    }
+    cap = want;
+    return DGS_OK;
+}
+
+void DevBuf::release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+}
+
+Workspace::~Workspace() {
+    for (DevBuf *b : all()) b->release();
+    if (h_small) cudaFreeHost(h_small);
+    if (h_views) cudaFreeHost(h_views);
+    if (h_scenes) cudaFreeHost(h_scenes);
+    if (done) cudaEventDestroy(done);
+}
+
+std::vector<DevBuf *> Workspace::all() {
+    return {&views, &scenes, &zkey, &zval, &rect, &depth, &count, &cnt_sorted, &offs, &tkey, &tval, &ranges, &rec,
+            &Dpix, &ndpix, &rgb, &g2d, &gstage, &sort_k, &sort_v, &sort_hist, &sort_status, &sort_ctr, &small, &scan};
+}
+
+dgs_status Workspace::init() {
+    CK(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
+    CK(cudaMallocHost(&h_small, 256));
+    memset(h_small, 0, 256);
+    return DGS_OK;
+}
+
+dgs_status ensure_sort_scratch(Workspace &ws, long long n) {
+    dgs_status s;
+    if ((s = ws.sort_k.ensure(sizeof(uint32_t) * std::max(1LL, n)))) return s;
+    if ((s = ws.sort_v.ensure(sizeof(uint32_t) * std::max(1LL, n)))) return s;
+    if ((s = ws.sort_hist.ensure(sizeof(uint32_t) * 4 * 256))) return s;
+    if ((s = ws.sort_status.ensure(sizeof(uint32_t) * 256 * std::max(1LL, sort_parts_for(n))))) return s;
+    if ((s = ws.sort_ctr.ensure(sizeof(uint32_t) * 4))) return s;
+    return DGS_OK;
+}
+
+SortScratch sort_scratch_of(Workspace &ws) {
+    SortScratch s;
+    s.keys_alt = (uint32_t *)ws.sort_k.p;
+    s.vals_alt = (uint32_t *)ws.sort_v.p;
+    s.hist = (uint32_t *)ws.sort_hist.p;
+    s.status = (uint32_t *)ws.sort_status.p;
+    s.counters = (uint32_t *)ws.sort_ctr.p;
+    s.err = (uint32_t *)ws.small.p + kSmallSortErr;
+    s.cap_items = (long long)(ws.sort_k.cap / 4);
+    s.cap_parts = (long long)(ws.sort_status.cap / 1024);
+    return s;
+}
+
+cudaEvent_t Profiler::take() {
+    if (!spare.empty()) {
+        cudaEvent_t e = spare.back();
+        spare.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void Profiler::drain() {
+    for (auto &q : pending) {
+        float ms_ = 0.f;
+        if (cudaEventSynchronize(q.b) == cudaSuccess && cudaEventElapsedTime(&ms_, q.a, q.b) == cudaSuccess) {
+            ms[q.stage] += ms_;
+            launches[q.stage] += 1;
+        }
+        spare.push_back(q.a);
+        spare.push_back(q.b);
+    }
+    pending.clear();
+}
+
+Profiler::~Profiler() {
+    for (auto &q : pending) {
+        cudaEventDestroy(q.a);
+        cudaEventDestroy(q.b);
+    }
+    for (auto e : spare) cudaEventDestroy(e);
+}
+
+StageTimer::StageTimer(Profiler &p_, int s, cudaStream_t st_) : p(p_), stage(s), st(st_) {
+    if (!p.on) return;
+    a = p.take();
+    cudaEventRecord(a, st);
+}
+
+StageTimer::~StageTimer() {
+    if (!p.on || !a) return;
+    cudaEvent_t b = p.take();
+    cudaEventRecord(b, st);
+    p.pending.push_back({stage, a, b});
+}
+
+SceneDev Scene::dev() const {
+    SceneDev d;
+    d.cell = (const float *)cell.p;
+    d.gauss = (const float *)gauss.p;
+    d.sh = (const float *)sh.p;
+    d.N = N;
+    d.G = G;
+    d.K = K;
+    d.sh_degree = deg;
+    return d;
+}
+
+}  // namespace dgs
+
+// ------------------------------------------------------------------ context
+
+extern "C" void dgs_config_default(dgs_config *c) {
+    if (!c) return;
+    memset(c, 0, sizeof(*c));
+    c->eps = 1e-4f;
+    c->alpha_max = 0.99f;
+    c->d_min = 1e-10f;
+    c->dilation = 0.3f;
+    c->ksigma = 3.0f;
+    c->device = 0;
+}
+
+extern "C" dgs_status dgs_create(const dgs_config *cfg, dgs_ctx **out) {
+    if (!out) return set_error(DGS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    dgs_config c;
+    if (cfg) c = *cfg; else dgs_config_default(&c);
+    if (!(c.eps >= 0.f) || !(c.alpha_max > 0.f && c.alpha_max < 1.f) || !(c.ksigma > 0.f) || !(c.dilation >= 0.f))
+        return set_error(DGS_ERR_INVALID_ARG, "config out of range (need eps >= 0, 0 < alpha_max < 1, ksigma > 0)");
+    int ndev = 0;
+    CK(cudaGetDeviceCount(&ndev));
+    if (c.device < 0 || c.device >= ndev) return set_error(DGS_ERR_INVALID_ARG, "no such CUDA device");
+    CK(cudaSetDevice(c.device));
+    dgs_ctx *ctx = new dgs_ctx();
+    ctx->cfg = c;
+    ctx->cams.resize(kMaxCamSlots);
+    ctx->cam_set.assign(kMaxCamSlots, 0);
+    if (c.hbm_budget_bytes <= 0) {
+        size_t fr = 0, tot = 0;
+        cudaMemGetInfo(&fr, &tot);
+        ctx->cfg.hbm_budget_bytes = (int64_t)(0.9 * (double)fr);
+    }
+    *out = ctx;
+    return DGS_OK;
+}
+
+extern "C" void dgs_destroy(dgs_ctx *ctx) {
+    if (!ctx) return;
+    dgs_serve_stop(ctx);
+    cudaSetDevice(ctx->cfg.device);
+    cudaDeviceSynchronize();
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        for (auto *st : ctx->live_states) delete st;
+        ctx->live_states.clear();
+        ctx->pool.clear();
+        ctx->scenes.clear();
+        ctx->aux.release();
+        ctx->sort_ws.reset();
+    }
+    delete ctx;
+}
+
+extern "C" const char *dgs_last_error(dgs_ctx *) { return g_last_error.c_str(); }
+
+// ------------------------------------------------------------------ scenes
+
+static dgs_status upload_param(dgs_ctx *ctx, const float *src, int location, int64_t rows, int cols, float *dst_planes,
+                               int64_t plane_stride, cudaStream_t st) {
+    const size_t bytes = sizeof(float) * (size_t)rows * cols;
+    if (bytes == 0) return DGS_OK;
+    const float *dsrc = src;
+    if (location == DGS_HOST) {
+        dgs_status s = ctx->aux.ensure(bytes);
+        if (s) return s;
+        CK(cudaMemcpyAsync(ctx->aux.p, src, bytes, cudaMemcpyHostToDevice, st));
+        dsrc = (const float *)ctx->aux.p;
+    }
+    launch_aos_to_soa(dsrc, rows, cols, dst_planes, plane_stride, st);
+    CK(cudaGetLastError());
+    if (location == DGS_HOST) CK(cudaStreamSynchronize(st));  // staging buffer is reused by the next parameter
+    return DGS_OK;
+}
+
+static dgs_status fill_scene(dgs_ctx *ctx, Scene &sc, const dgs_scene_desc *d, cudaStream_t st, bool cells_too) {
+    const int64_t N = sc.N, G = sc.G;
+    float *cell = (float *)sc.cell.p, *gs = (float *)sc.gauss.p, *sh = (float *)sc.sh.p;
+    dgs_status s;
+    if (cells_too) {
+        if ((s = upload_param(ctx, d->cell_center, d->location, N, 3, cell, N, st))) return s;
+        if ((s = upload_param(ctx, d->cell_axes, d->location, N, 3, cell + 3 * N, N, st))) return s;
+        if ((s = upload_param(ctx, d->cell_quat, d->location, N, 4, cell + 6 * N, N, st))) return s;
+    }
+    if (d->cell_v) {
+        if ((s = upload_param(ctx, d->cell_v, d->location, N, 1, cell + 10 * N, N, st))) return s;
+    } else if (cells_too) {
+        launch_fill_f32(cell + 10 * N, N, 1.0f, st);
+    }
+    if ((s = upload_param(ctx, d->g_mean, d->location, G, 3, gs, G, st))) return s;
+    if ((s = upload_param(ctx, d->g_scale, d->location, G, 3, gs + 3 * G, G, st))) return s;
+    if ((s = upload_param(ctx, d->g_quat, d->location, G, 4, gs + 6 * G, G, st))) return s;
+    if ((s = upload_param(ctx, d->g_logit, d->location, G, 1, gs + 10 * G, G, st))) return s;
+    if ((s = upload_param(ctx, d->g_sh, d->location, G, 3 * sc.C, sh, G, st))) return s;
+    CK(cudaGetLastError());
+    return DGS_OK;
+}
+
+static dgs_status check_desc(const dgs_scene_desc *d) {
+    if (!d) return set_error(DGS_ERR_INVALID_ARG, "scene desc is NULL");
+    if (d->num_cells < 0 || d->K < 1 || d->K > kMaxK || d->sh_degree < 0 || d->sh_degree > 3)
+        return set_error(DGS_ERR_INVALID_ARG, "need num_cells >= 0, 1 <= K <= 32, 0 <= sh_degree <= 3");
+    if (d->location != DGS_HOST && d->location != DGS_DEVICE) return set_error(DGS_ERR_INVALID_ARG, "bad location");
+    if (d->num_cells * (int64_t)d->K >= (1LL << 31)) return set_error(DGS_ERR_CAPACITY, "more than 2^31 Gaussians");
+    if (d->num_cells > 0 && (!d->cell_center || !d->cell_axes || !d->cell_quat || !d->g_mean || !d->g_scale ||
+                             !d->g_quat || !d->g_logit || !d->g_sh))
+        return set_error(DGS_ERR_INVALID_ARG, "a scene array is NULL");
+    return DGS_OK;
+}
+
+extern "C" dgs_status dgs_scene_upload(dgs_ctx *ctx, const dgs_scene_desc *d, uint32_t *scene_id) {
+    if (!ctx || !scene_id) return set_error(DGS_ERR_INVALID_ARG, "NULL argument");
+    dgs_status s = check_desc(d);
+    if (s) return s;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    CK(cudaSetDevice(ctx->cfg.device));
+    auto sc = std::make_unique<Scene>();
+    sc->N = d->num_cells;
+    sc->K = d->K;
+    sc->G = sc->N * sc->K;
+    sc->deg = d->sh_degree;
+    sc->C = (sc->deg + 1) * (sc->deg + 1);
+    if ((s = sc->cell.ensure(sizeof(float) * 11 * std::max<int64_t>(1, sc->N)))) return s;
+    if ((s = sc->gauss.ensure(sizeof(float) * 11 * std::max<int64_t>(1, sc->G)))) return s;
+    if ((s = sc->sh.ensure(sizeof(float) * 3 * sc->C * std::max<int64_t>(1, sc->G)))) return s;
+    cudaStream_t st = 0;
+    if ((s = fill_scene(ctx, *sc, d, st, true))) return s;
+    CK(cudaStreamSynchronize(st));
+    const uint32_t id = ctx->next_scene++;
+    ctx->scenes[id] = std::move(sc);
+    *scene_id = id;
+    return DGS_OK;
+}
+
+extern "C" dgs_status dgs_scene_update(dgs_ctx *ctx, uint32_t scene_id, const dgs_scene_desc *d, dgs_stream stream) {
+    if (!ctx) return set_error(DGS_ERR_INVALID_ARG, "NULL ctx");
+    dgs_status s = check_desc(d);
+    if (s) return s;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    CK(cudaSetDevice(ctx->cfg.device));
+    auto it = ctx->scenes.find(scene_id);
+    if (it == ctx->scenes.end()) return set_error(DGS_ERR_NOT_FOUND, "unknown scene id");
+    Scene &sc = *it->second;
+    if (d->num_cells != sc.N || d->K != sc.K || d->sh_degree != sc.deg)
+        return set_error(DGS_ERR_INVALID_ARG, "update must keep N, K and sh_degree");
+    return fill_scene(ctx, sc, d, (cudaStream_t)stream, false);
+}
+
+extern "C" dgs_status dgs_scene_release(dgs_ctx *ctx, uint32_t scene_id) {
+    if (!ctx) return set_error(DGS_ERR_INVALID_ARG, "NULL ctx");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    CK(cudaSetDevice(ctx->cfg.device));
+    auto it = ctx->scenes.find(scene_id);
+    if (it == ctx->scenes.end()) return set_error(DGS_ERR_NOT_FOUND, "unknown scene id");
+    for (auto *st : ctx->live_states)
+        if (st->scene_id == scene_id) return set_error(DGS_ERR_BUSY, "a forward state still refers to this scene");
+    CK(cudaDeviceSynchronize());
+    ctx->scenes.erase(it);
+    return DGS_OK;
+}
+
+extern "C" dgs_status dgs_camera_set(dgs_ctx *ctx, uint32_t slot, const dgs_camera *cam) {
+    if (!ctx || !cam) return set_error(DGS_ERR_INVALID_ARG, "NULL argument");
+    if (slot >= (uint32_t)kMaxCamSlots) return set_error(DGS_ERR_INVALID_ARG, "camera slot out of range");
+    if (cam->W <= 0 || cam->H <= 0 || cam->W > 32768 || cam->H > 32768 || !(cam->fx > 0.f) || !(cam->fy > 0.f) ||
+        !(cam->znear > 0.f))
+        return set_error(DGS_ERR_INVALID_ARG, "camera needs 0 < W,H <= 32768, fx, fy > 0, znear > 0");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->cams[slot] = *cam;
+    ctx->cam_set[slot] = 1;
+    return DGS_OK;
+}
+
+// ------------------------------------------------------------------ render
+
+namespace dgs {
+
+static ViewDesc make_view(const dgs_camera &c, int tile_base, long long pix_base, int slot, const Scene &sc,
+                          long long cell_base, long long rec_base) {
+    ViewDesc v;
+    memset(&v, 0, sizeof(v));
+    v.W = c.W;
+    v.H = c.H;
+    v.Tx = (c.W + kTile - 1) / kTile;
+    v.Ty = (c.H + kTile - 1) / kTile;
+    v.tile_base = tile_base;
+    v.scene_slot = slot;
+    v.pix_base = pix_base;
+    v.cell_base = cell_base;
+    v.rec_base = rec_base;
+    v.N = sc.N;
+    v.K = sc.K;
+    v.fx = c.fx;
+    v.fy = c.fy;
+    v.cx = c.cx;
+    v.cy = c.cy;
+    v.znear = c.znear;
+    memcpy(v.R, c.R, sizeof(v.R));
+    memcpy(v.t, c.t, sizeof(v.t));
+    memcpy(v.eye, c.eye, sizeof(v.eye));
+    return v;
+}
+
+BlendParams blend_params(const dgs_config &c) {
+    BlendParams b;
+    b.eps = c.eps;
+    b.alpha_max = c.alpha_max;
+    b.d_min = c.d_min;
+    b.bg0 = c.bg[0];
+    b.bg1 = c.bg[1];
+    b.bg2 = c.bg[2];
+    b.dilation = c.dilation;
+    b.ksigma = c.ksigma;
+    return b;
+}
+
+std::unique_ptr<Workspace> acquire_ws(dgs_ctx *ctx, cudaStream_t st, dgs_status *err) {
+    std::unique_ptr<Workspace> ws;
+    if (!ctx->pool.empty()) {
+        ws = std::move(ctx->pool.back());
+        ctx->pool.pop_back();
+        // the previous chain on this workspace may still run on another stream
+        cudaError_t e = cudaStreamWaitEvent(st, ws->done, 0);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ws->done);  // pinned host mirrors are rewritten next
+        if (e != cudaSuccess) {
+            *err = cuda_error(e, "waiting for a workspace");
+            return nullptr;
+        }
+    } else {
+        ws = std::make_unique<Workspace>();
+        if ((*err = ws->init())) return nullptr;
+    }
+    ws->bwd_done = false;
+    *err = DGS_OK;
+    return ws;
+}
+
+// Binning of all views of the chain (steps a1-a5): cell projection and cull,
+// depth sort over cells, count scan, key emission, tile sort, tile ranges.
+// Synchronises the stream once to learn the sort length L.
+static dgs_status run_binning(dgs_ctx *ctx, Workspace &ws, cudaStream_t st) {
+    Profiler &pf = ctx->prof;
+    const int V = ws.V;
+    const long long n = ws.n_entries;
+    const long long n1 = std::max(1LL, n);
+    dgs_status s;
+    if ((s = ws.small.ensure(256))) return s;
+    CK(cudaMemsetAsync(ws.small.p, 0, 256, st));
+    if ((s = ws.zkey.ensure(4 * n1)) || (s = ws.zval.ensure(4 * n1)) || (s = ws.rect.ensure(8 * n1)) ||
+        (s = ws.depth.ensure(4 * n1)) || (s = ws.count.ensure(4 * n1)) || (s = ws.cnt_sorted.ensure(4 * n1)) ||
+        (s = ws.offs.ensure(4 * n1)) || (s = ws.scan.ensure(4 * scan_scratch_words(n1))))
+        return s;
+    if ((s = ensure_sort_scratch(ws, n))) return s;
+    uint32_t *small = (uint32_t *)ws.small.p;
+    const ViewDesc *dv = (const ViewDesc *)ws.views.p;
+    {
+        StageTimer t(pf, DGS_STAGE_CELL_PROJECT, st);
+        launch_cell_project(dv, V, (const SceneDev *)ws.scenes.p, n, (uint32_t *)ws.zkey.p, (uint32_t *)ws.zval.p,
+                            (short4 *)ws.rect.p, (float *)ws.depth.p, (uint32_t *)ws.count.p, small + kSmallVisible, st);
+    }
+    {
+        StageTimer t(pf, DGS_STAGE_DEPTH_SORT, st);
+        radix_sort_pairs((uint32_t *)ws.zkey.p, (uint32_t *)ws.zval.p, n, 32, sort_scratch_of(ws), st);
+    }
+    {
+        StageTimer t(pf, DGS_STAGE_COUNT_SCAN, st);
+        launch_gather_counts((const uint32_t *)ws.zval.p, (const uint32_t *)ws.count.p, n, (uint32_t *)ws.cnt_sorted.p,
+                             st);
+        exclusive_scan_u32((const uint32_t *)ws.cnt_sorted.p, (uint32_t *)ws.offs.p, n, small + kSmallTotal,
+                           (uint32_t *)ws.scan.p, st);
+    }
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(ws.h_small, small, 64, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (ws.h_small[kSmallSortErr]) return set_error(DGS_ERR_TIMEOUT, "radix sort look-back wait gave up");
+    const long long L = ws.h_small[kSmallTotal];
+    ws.L = L;
+    if ((s = ws.tkey.ensure(4 * std::max(1LL, L))) || (s = ws.tval.ensure(4 * std::max(1LL, L)))) return s;
+    if ((s = ensure_sort_scratch(ws, L))) return s;
+    if ((s = ws.ranges.ensure(8 * (size_t)std::max(1, ws.total_tiles)))) return s;
+    {
+        StageTimer t(pf, DGS_STAGE_EMIT, st);
+        launch_emit((const uint32_t *)ws.offs.p, (const uint32_t *)ws.zval.p, (const short4 *)ws.rect.p, dv, V, n, L,
+                    (uint32_t *)ws.tkey.p, (uint32_t *)ws.tval.p, st);
+    }
+    int bits = 1;
+    while ((1LL << bits) < ws.total_tiles) ++bits;
+    {
+        StageTimer t(pf, DGS_STAGE_TILE_SORT, st);
+        radix_sort_pairs((uint32_t *)ws.tkey.p, (uint32_t *)ws.tval.p, L, bits, sort_scratch_of(ws), st);
+    }
+    {
+        StageTimer t(pf, DGS_STAGE_TILE_RANGES, st);
+        CK(cudaMemsetAsync(ws.ranges.p, 0, 8 * (size_t)std::max(1, ws.total_tiles), st));
+        launch_tile_ranges((const uint32_t *)ws.tkey.p, L, (uint2 *)ws.ranges.p, st);
+    }
+    CK(cudaGetLastError());
+    return DGS_OK;
+}
+
+dgs_status chain_forward(dgs_ctx *ctx, Workspace &ws, const std::vector<ChainView> &req, float *out_img,
+                         bool keep_rgb, bool grad_buffers, cudaStream_t st) {
+    const int V = (int)req.size();
+    ws.V = V;
+    ws.hviews.clear();
+    ws.scene_ids.clear();
+    std::vector<const Scene *> slots;
+    int tiles = 0;
+    long long px = 0, cell_base = 0, rec_base = 0;
+    for (int v = 0; v < V; ++v) {
+        auto it = ctx->scenes.find(req[v].scene_id);
+        if (it == ctx->scenes.end()) return set_error(DGS_ERR_NOT_FOUND, "unknown scene id");
+        int slot = -1;
+        for (size_t k = 0; k < ws.scene_ids.size(); ++k)
+            if (ws.scene_ids[k] == req[v].scene_id) slot = (int)k;
+        if (slot < 0) {
+            slot = (int)ws.scene_ids.size();
+            ws.scene_ids.push_back(req[v].scene_id);
+            slots.push_back(it->second.get());
+        }
+        const Scene &sc = *it->second;
+        ws.hviews.push_back(make_view(req[v].cam, tiles, px, slot, sc, cell_base, rec_base));
+        ws.hviews.back().out = req[v].out;
+        tiles += ws.hviews.back().Tx * ws.hviews.back().Ty;
+        px += (long long)req[v].cam.W * req[v].cam.H;
+        cell_base += sc.N;
+        rec_base += sc.G;
+    }
+    if (cell_base >= (1LL << 32) - 1) return set_error(DGS_ERR_CAPACITY, "views x cells exceeds 2^32");
+    ws.total_tiles = tiles;
+    ws.total_px = px;
+    ws.n_entries = cell_base;
+    ws.n_records = rec_base;
+    const int S = (int)slots.size();
+    dgs_status s;
+    if ((s = ws.views.ensure(sizeof(ViewDesc) * V)) || (s = ws.scenes.ensure(sizeof(SceneDev) * S))) return s;
+    if (ws.h_views_cap < (size_t)V) {
+        if (ws.h_views) cudaFreeHost(ws.h_views);
+        ws.h_views = nullptr;
+        CK(cudaMallocHost(&ws.h_views, sizeof(ViewDesc) * V));
+        ws.h_views_cap = V;
+    }
+    if (ws.h_scenes_cap < (size_t)S) {
+        if (ws.h_scenes) cudaFreeHost(ws.h_scenes);
+        ws.h_scenes = nullptr;
+        CK(cudaMallocHost(&ws.h_scenes, sizeof(SceneDev) * S));
+        ws.h_scenes_cap = S;
+    }
+    memcpy(ws.h_views, ws.hviews.data(), sizeof(ViewDesc) * V);
+    for (int k = 0; k < S; ++k) ws.h_scenes[k] = slots[k]->dev();
+    CK(cudaMemcpyAsync(ws.views.p, ws.h_views, sizeof(ViewDesc) * V, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ws.scenes.p, ws.h_scenes, sizeof(SceneDev) * S, cudaMemcpyHostToDevice, st));
+    if ((s = run_binning(ctx, ws, st))) return s;
+    const BlendParams bp = blend_params(ctx->cfg);
+    const long long nrec = std::max(1LL, ws.n_records), px1 = std::max(1LL, px);
+    if ((s = ws.rec.ensure(sizeof(float4) * kRecF4 * nrec)) ||
+        (grad_buffers && (s = ws.g2d.ensure(sizeof(float) * kGradF * nrec))) || (s = ws.Dpix.ensure(4 * px1)) ||
+        (s = ws.ndpix.ensure(4 * px1)) || ((keep_rgb || !out_img) && (s = ws.rgb.ensure(12 * px1))))
+        return s;
+    const ViewDesc *dv = (const ViewDesc *)ws.views.p;
+    {
+        StageTimer t(ctx->prof, DGS_STAGE_PROJECT_FWD, st);
+        for (int k = 0; k < S; ++k)
+            launch_project_fwd(dv, V, k, slots[k]->dev(), (const uint32_t *)ws.count.p, bp, (float4 *)ws.rec.p,
+                               grad_buffers ? (float *)ws.g2d.p : nullptr, st);
+    }
+    float *img = out_img ? out_img : (float *)ws.rgb.p;
+    float *img2 = (keep_rgb && out_img) ? (float *)ws.rgb.p : nullptr;
+    {
+        StageTimer t(ctx->prof, DGS_STAGE_BLEND_FWD, st);
+        launch_blend_fwd(dv, V, ws.total_tiles, (const uint2 *)ws.ranges.p, (const uint32_t *)ws.tval.p,
+                         (const float4 *)ws.rec.p, bp, img, img2, (float *)ws.Dpix.p, (int *)ws.ndpix.p, st);
+    }
+    CK(cudaGetLastError());
+    ws.stream = st;
+    return DGS_OK;
+}
+
+static dgs_status render_impl(dgs_ctx *ctx, uint32_t scene_id, int n_views, const uint32_t *cam_slots, float *out_rgb,
+                              int out_location, dgs_fwd_state **state, cudaStream_t st, dgs_stats *stats) {
+    if (n_views <= 0 || !cam_slots || !out_rgb) return set_error(DGS_ERR_INVALID_ARG, "need n_views > 0, cams, output");
+    if (out_location != DGS_HOST && out_location != DGS_DEVICE) return set_error(DGS_ERR_INVALID_ARG, "bad location");
+    if (!ctx->scenes.count(scene_id)) return set_error(DGS_ERR_NOT_FOUND, "unknown scene id");
+    std::vector<ChainView> req;
+    for (int v = 0; v < n_views; ++v) {
+        if (cam_slots[v] >= (uint32_t)kMaxCamSlots || !ctx->cam_set[cam_slots[v]])
+            return set_error(DGS_ERR_NOT_FOUND, "camera slot not set");
+        req.push_back({scene_id, ctx->cams[cam_slots[v]]});
+    }
+    dgs_status s;
+    std::unique_ptr<Workspace> ws = acquire_ws(ctx, st, &s);
+    if (!ws) return s;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    const bool timing = stats && stats->timing;
+    if (timing) {
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        cudaEventRecord(e0, st);
+    }
+    const bool keep = state != nullptr;
+    s = chain_forward(ctx, *ws, req, out_location == DGS_DEVICE ? out_rgb : nullptr, keep, keep, st);
+    if (!s && out_location == DGS_HOST) {
+        cudaError_t e = cudaMemcpyAsync(out_rgb, ws->rgb.p, 12 * ws->total_px, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) s = cuda_error(e, "copying the image to host memory");
+    }
+    if (timing) {
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&stats->ms_total, e0, e1);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+    if (stats && !s) {
+        stats->sort_length = ws->L;
+        stats->num_tiles = ws->total_tiles;
+        stats->visible_cells = ws->h_small[kSmallVisible];
+    }
+    cudaEventRecord(ws->done, st);
+    if (s || !keep) {
+        ctx->pool.push_back(std::move(ws));
+        return s;
+    }
+    auto *fs = new dgs_fwd_state();
+    fs->ws = std::move(ws);
+    fs->scene_id = scene_id;
+    ctx->live_states.insert(fs);
+    *state = fs;
+    return DGS_OK;
+}
+
+}  // namespace dgs
+
+extern "C" dgs_status dgs_render(dgs_ctx *ctx, uint32_t scene_id, int32_t n_views, const uint32_t *cam_slots,
+                                 float *out_rgb, int32_t out_location, dgs_fwd_state **state, dgs_stream stream,
+                                 dgs_stats *stats) {
+    if (!ctx) return set_error(DGS_ERR_INVALID_ARG, "NULL ctx");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    CK(cudaSetDevice(ctx->cfg.device));
+    if (state) *state = nullptr;
+    return render_impl(ctx, scene_id, n_views, cam_slots, out_rgb, out_location, state, (cudaStream_t)stream, stats);
+}
+
+extern "C" dgs_status dgs_render_backward(dgs_ctx *ctx, dgs_fwd_state *state, const float *dL_drgb, int32_t location,
+                                          const dgs_grads *out, dgs_stream stream) {
+    if (!ctx || !state || !dL_drgb || !out) return set_error(DGS_ERR_INVALID_ARG, "NULL argument");
+    if ((location != DGS_HOST && location != DGS_DEVICE) || (out->location != DGS_HOST && out->location != DGS_DEVICE))
+        return set_error(DGS_ERR_INVALID_ARG, "bad location");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    CK(cudaSetDevice(ctx->cfg.device));
+    if (!ctx->live_states.count(state)) return set_error(DGS_ERR_NOT_FOUND, "unknown or released forward state");
+    auto it = ctx->scenes.find(state->scene_id);
+    if (it == ctx->scenes.end()) return set_error(DGS_ERR_NOT_FOUND, "scene of this state was released");
+    const Scene &sc = *it->second;
+    Workspace &ws = *state->ws;
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaStreamWaitEvent(st, ws.done, 0));
+    const long long px = ws.total_px, G = sc.G, N = sc.N;
+    const int C = sc.C;
+    dgs_status s;
+    // staging: dL/drgb (3 px), then the six gradient outputs
+    const long long n_out = 3 * G + 3 * G + 3 * G + 4 * G + G + 3LL * C * G + N;
+    const long long n_stage = (location == DGS_HOST ? 3 * px : 0) + (out->location == DGS_HOST ? n_out : 0) + 1;
+    if ((s = ws.gstage.ensure(sizeof(float) * n_stage))) return s;
+    float *stage = (float *)ws.gstage.p;
+    const float *dl = dL_drgb;
+    if (location == DGS_HOST) {
+        CK(cudaMemcpyAsync(stage, dL_drgb, 12 * px, cudaMemcpyHostToDevice, st));
+        dl = stage;
+        stage += 3 * px;
+    }
+    float *o_mean = out->g_mean, *o_s = out->g_scale, *o_ls = out->g_log_scale, *o_q = out->g_quat,
+          *o_lg = out->g_logit, *o_sh = out->g_sh, *o_v = out->g_cell_v;
+    if (out->location == DGS_HOST) {
+        o_mean = out->g_mean ? stage : nullptr; stage += 3 * G;
+        o_s = out->g_scale ? stage : nullptr; stage += 3 * G;
+        o_ls = out->g_log_scale ? stage : nullptr; stage += 3 * G;
+        o_q = out->g_quat ? stage : nullptr; stage += 4 * G;
+        o_lg = out->g_logit ? stage : nullptr; stage += G;
+        o_sh = out->g_sh ? stage : nullptr; stage += 3LL * C * G;
+        o_v = out->g_cell_v ? stage : nullptr; stage += N;
+    }
+    if (o_v) CK(cudaMemsetAsync(o_v, 0, sizeof(float) * N, st));
+    const BlendParams bp = blend_params(ctx->cfg);
+    if (ws.bwd_done) {  // a second backward on the same state: clear the screen-space accumulators
+        CK(cudaMemsetAsync(ws.g2d.p, 0, sizeof(float) * kGradF * (size_t)ws.n_records, st));
+    }
+    {
+        StageTimer t(ctx->prof, DGS_STAGE_BLEND_BWD, st);
+        launch_blend_bwd((const ViewDesc *)ws.views.p, ws.V, ws.total_tiles, sc.K, (const uint2 *)ws.ranges.p,
+                         (const uint32_t *)ws.tval.p, (const float4 *)ws.rec.p, bp, (const float *)ws.rgb.p,
+                         (const float *)ws.Dpix.p, (const int *)ws.ndpix.p, dl, (float *)ws.g2d.p, o_v, st);
+    }
+    {
+        StageTimer t(ctx->prof, DGS_STAGE_PROJECT_BWD, st);
+        launch_project_bwd((const ViewDesc *)ws.views.p, ws.V, 0, sc.dev(), (const uint32_t *)ws.count.p, bp,
+                           (const float *)ws.g2d.p, o_mean, o_s, o_ls, o_q, o_lg, o_sh, st);
+    }
+    CK(cudaGetLastError());
+    ws.bwd_done = true;
+    if (out->location == DGS_HOST) {
+        struct { float *h, *d; long long n; } cp[] = {{out->g_mean, o_mean, 3 * G}, {out->g_scale, o_s, 3 * G},
+                                                      {out->g_log_scale, o_ls, 3 * G},
+                                                      {out->g_quat, o_q, 4 * G}, {out->g_logit, o_lg, G},
+                                                      {out->g_sh, o_sh, 3LL * C * G}, {out->g_cell_v, o_v, N}};
+        for (auto &c : cp)
+            if (c.h && c.n) CK(cudaMemcpyAsync(c.h, c.d, sizeof(float) * c.n, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    CK(cudaEventRecord(ws.done, st));
+    return DGS_OK;
+}
+
+extern "C" dgs_status dgs_state_release(dgs_ctx *ctx, dgs_fwd_state *state) {
+    if (!ctx || !state) return set_error(DGS_ERR_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (!ctx->live_states.count(state)) return set_error(DGS_ERR_NOT_FOUND, "unknown or released forward state");
+    ctx->live_states.erase(state);
+    state->ws->bwd_done = false;
+    ctx->pool.push_back(std::move(state->ws));
+    delete state;
+    return DGS_OK;
+}
+
+extern "C" dgs_status dgs_state_read(dgs_ctx *ctx, const dgs_fwd_state *state, int32_t what, void *dst, int64_t bytes,
+                                     int64_t *needed) {
+    if (!ctx || !state) return set_error(DGS_ERR_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    CK(cudaSetDevice(ctx->cfg.device));
+    if (!ctx->live_states.count(const_cast<dgs_fwd_state *>(state)))
+        return set_error(DGS_ERR_NOT_FOUND, "unknown or released forward state");
+    auto it = ctx->scenes.find(state->scene_id);
+    if (it == ctx->scenes.end()) return set_error(DGS_ERR_NOT_FOUND, "scene released");
+    const Scene &sc = *it->second;
+    const Workspace &ws = *state->ws;
+    const long long VN = ws.n_entries, VG = ws.n_records;
+    (void)sc;
+    int64_t need = 0;
+    switch (what) {
+        case DGS_BUF_CELL_RECT: need = 16 * VN; break;
+        case DGS_BUF_CELL_DEPTH: need = 4 * VN; break;
+        case DGS_BUF_TILE_CELLS: need = 4 * ws.L; break;
+        case DGS_BUF_TILE_RANGES: need = 8LL * ws.total_tiles; break;
+        case DGS_BUF_GAUSS_REC: need = 48 * VG; break;
+        case DGS_BUF_PIX_D: need = 4 * ws.total_px; break;
+        case DGS_BUF_PIX_NDONE: need = 4 * ws.total_px; break;
+        case DGS_BUF_GRAD2D: need = ws.g2d.p ? 48 * VG : 0; break;
+        default: return set_error(DGS_ERR_INVALID_ARG, "unknown buffer id");
+    }
+    if (needed) *needed = need;
+    if (!dst || bytes < need) return DGS_OK;
+    CK(cudaEventSynchronize(ws.done));
+    if (need == 0) return DGS_OK;
+    if (what == DGS_BUF_CELL_RECT) {
+        std::vector<short4> tmp(VN);
+        CK(cudaMemcpy(tmp.data(), ws.rect.p, 8 * VN, cudaMemcpyDeviceToHost));
+        int32_t *o = (int32_t *)dst;
+        for (long long i = 0; i < VN; ++i) {
+            o[4 * i] = tmp[i].x; o[4 * i + 1] = tmp[i].y; o[4 * i + 2] = tmp[i].z; o[4 * i + 3] = tmp[i].w;
+        }
+        return DGS_OK;
+    }
+    const void *src = nullptr;
+    switch (what) {
+        case DGS_BUF_CELL_DEPTH: src = ws.depth.p; break;
+        case DGS_BUF_TILE_CELLS: src = ws.tval.p; break;
+        case DGS_BUF_TILE_RANGES: src = ws.ranges.p; break;
+        case DGS_BUF_GAUSS_REC: src = ws.rec.p; break;
+        case DGS_BUF_PIX_D: src = ws.Dpix.p; break;
+        case DGS_BUF_PIX_NDONE: src = ws.ndpix.p; break;
+        case DGS_BUF_GRAD2D: src = ws.g2d.p; break;
+    }
+    CK(cudaMemcpy(dst, src, need, cudaMemcpyDeviceToHost));
+    return DGS_OK;
+}
+
+extern "C" dgs_status dgs_loss_l1(dgs_ctx *ctx, const float *rgb, const float *target, int64_t n, float *dL_drgb,
+                                  float *loss, dgs_stream stream) {
+    if (!ctx || !rgb || !target || !dL_drgb || !loss || n < 0) return set_error(DGS_ERR_INVALID_ARG, "bad argument");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    CK(cudaSetDevice(ctx->cfg.device));
+    const int nb = loss_l1_blocks(n);
+    dgs_status s = ctx->loss_partial.ensure(sizeof(float) * nb);
+    if (s) return s;
+    launch_loss_l1(rgb, target, n, dL_drgb, (float *)ctx->loss_partial.p, nb, loss, (cudaStream_t)stream);
+    CK(cudaGetLastError());
+    return DGS_OK;
+}
+
+extern "C" dgs_status dgs_sort_pairs(dgs_ctx *ctx, uint32_t *keys, uint32_t *vals, int64_t n, int32_t bits,
+                                     dgs_stream stream) {
+    if (!ctx || (n > 0 && (!keys || !vals)) || n < 0 || bits < 0 || bits > 32)
+        return set_error(DGS_ERR_INVALID_ARG, "bad argument");
+    if (n >= (1LL << 30)) return set_error(DGS_ERR_CAPACITY, "sort supports fewer than 2^30 items");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    CK(cudaSetDevice(ctx->cfg.device));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!ctx->sort_ws) {
+        dgs_status e;
+        ctx->sort_ws = acquire_ws(ctx, st, &e);
+        if (!ctx->sort_ws) return e;
+    }
+    Workspace &ws = *ctx->sort_ws;
+    dgs_status s;
+    if ((s = ensure_sort_scratch(ws, n)) || (s = ws.small.ensure(256))) return s;
+    CK(cudaMemsetAsync(ws.small.p, 0, 256, st));
+    radix_sort_pairs(keys, vals, n, bits, sort_scratch_of(ws), st);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(ws.h_small, ws.small.p, 64, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (ws.h_small[kSmallSortErr]) return set_error(DGS_ERR_TIMEOUT, "radix sort look-back wait gave up");
+    return DGS_OK;
+}
+
+extern "C" dgs_status dgs_state_counts(dgs_ctx *ctx, const dgs_fwd_state *state, dgs_counts *out) {
+    if (!ctx || !state || !out) return set_error(DGS_ERR_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    CK(cudaSetDevice(ctx->cfg.device));
+    if (!ctx->live_states.count(const_cast<dgs_fwd_state *>(state)))
+        return set_error(DGS_ERR_NOT_FOUND, "unknown or released forward state");
+    Workspace &ws = *state->ws;
+    cudaStream_t st = ws.stream;
+    dgs_status s = ctx->aux.ensure(64);
+    if (s) return s;
+    unsigned long long *c = (unsigned long long *)ctx->aux.p;
+    CK(cudaStreamWaitEvent(st, ws.done, 0));
+    CK(cudaMemsetAsync(c, 0, 32, st));
+    launch_count_pairs((const ViewDesc *)ws.views.p, ws.V, ws.total_tiles, (const uint2 *)ws.ranges.p,
+                       (const uint32_t *)ws.tval.p, (const float4 *)ws.rec.p, (const int *)ws.ndpix.p, c, st);
+    CK(cudaGetLastError());
+    unsigned long long h[4];
+    CK(cudaMemcpyAsync(h, c, 32, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    out->pairs_blended = (int64_t)h[0];
+    out->inbox_rendered = (int64_t)h[1];
+    out->inbox_all = (int64_t)h[2];
+    out->cells_blended = (int64_t)h[3];
+    return DGS_OK;
+}
+
+extern "C" dgs_status dgs_profile_enable(dgs_ctx *ctx, int32_t on) {
+    if (!ctx) return set_error(DGS_ERR_INVALID_ARG, "NULL ctx");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    CK(cudaSetDevice(ctx->cfg.device));
+    ctx->prof.drain();
+    for (int i = 0; i < 16; ++i) {
+        ctx->prof.ms[i] = 0.0;
+        ctx->prof.launches[i] = 0;
+    }
+    ctx->prof.on = on != 0;
+    return DGS_OK;
+}
+
+extern "C" dgs_status dgs_profile_read(dgs_ctx *ctx, dgs_profile *out) {
+    if (!ctx || !out) return set_error(DGS_ERR_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    CK(cudaSetDevice(ctx->cfg.device));
+    ctx->prof.drain();
+    for (int i = 0; i < 16; ++i) {
+        out->ms[i] = ctx->prof.ms[i];
+        out->launches[i] = ctx->prof.launches[i];
+    }
+    return DGS_OK;
+}

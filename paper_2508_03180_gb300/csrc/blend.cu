@@ -1,0 +1,410 @@
+// Physical weighted-sum blend (Layer II, Sec. V) and its adjoint.
+//
+// Per pixel, the tile's cells are walked front to back (the order of the
+// cell sort).  For cell n with Gaussians k:
+//     A_n = sum_k alpha_k c_k,  B_n = sum_k alpha_k,  P_n = prod_k (1 - v_n alpha_k)
+//     N += v_n T_n A_n,  D += v_n T_n B_n,  T_{n+1} = T_n P_n          (Eq. 12-14)
+// and the pixel is C = N / D.  Before cell n the pixel stops if T_n < eps
+// (cell-level early termination, Sec. V-B).  alpha_k = min(sigma G'(x'),
+// alpha_max) and is 0 when the pixel lies outside the Gaussian's AABB
+// (false-positive skip, Sec. VI-A).  Inside a cell nothing depends on the
+// order of k (Eq. 12's inner sums and product commute).
+//
+// GB300 mapping: one 256-thread CTA per 16x16 tile, one pixel per thread.
+// The 48-byte records of the Gaussians of a chunk of cells are fetched with
+// one 16-byte load per thread into registers while the previous chunk is
+// blended from shared memory (double buffer), so every record is read from
+// L2/HBM once per tile and then broadcast from shared memory to 256 pixels.
+// A block-wide count of finished pixels ends the tile early.
+#include "internal.cuh"
+
+namespace dgs {
+
+constexpr int BT = 256;
+constexpr float LN2 = 0.6931471805599453f;
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// One 16-byte piece of the records of chunk [start, start + CH) for thread tid.
+__device__ __forceinline__ float4 fetch_rec(const float4 *__restrict__ vrec, const uint32_t *__restrict__ cells,
+                                            uint32_t start, uint32_t end, int tid, int nload, int per, float4 keep) {
+    if (tid < nload) {
+        const int c = tid / per, j = tid - c * per;
+        const uint32_t e = start + c;
+        if (e < end) return __ldg(vrec + (long long)cells[e] * per + j);
+    }
+    return keep;
+}
+
+__device__ __forceinline__ int find_view(const ViewDesc *views, int n_views, int tile) {
+    int lo = 0, hi = n_views;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (views[mid].tile_base <= tile) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(BT) k_blend_fwd(const ViewDesc *__restrict__ views, int n_views,
+                                                  const uint2 *__restrict__ ranges, const uint32_t *__restrict__ cells,
+                                                  const float4 *__restrict__ rec, BlendParams bp,
+                                                  float *__restrict__ out_rgb, float *__restrict__ out_rgb2,
+                                                  float *__restrict__ out_D, int *__restrict__ out_nd) {
+    __shared__ float4 s_rec[2][BT];
+    __shared__ int s_view;
+    const int tid = threadIdx.x, tile = blockIdx.x;
+    if (tid == 0) s_view = find_view(views, n_views, tile);
+    __syncthreads();
+    const ViewDesc &V = views[s_view];
+    const int local = tile - V.tile_base;
+    const int tx = local % V.Tx, ty = local / V.Tx;
+    const int xi = tx * kTile + (tid & (kTile - 1)), yi = ty * kTile + (tid >> 4);
+    const bool inside = xi < V.W && yi < V.H;
+    const float px = (float)xi + 0.5f, py = (float)yi + 0.5f;
+
+    const int K = V.K;
+    const int per = kRecF4 * K;               // float4s per cell
+    const int CH = max(1, BT / per);          // cells per chunk
+    const int nload = CH * per;
+    const float4 *vrec = rec + V.rec_base * kRecF4;
+    const uint2 rg = ranges[tile];
+
+    float T = 1.0f, N0 = 0.f, N1 = 0.f, N2 = 0.f, D = 0.f;
+    int n = 0;
+    bool done = !inside;
+    float4 pre = make_float4(0.f, 0.f, 0.f, 0.f);
+    uint32_t cur = rg.x;
+    if (cur < rg.y) {
+        pre = fetch_rec(vrec, cells, cur, rg.y, tid, nload, per, pre);
+        s_rec[0][tid] = pre;
+    }
+    __syncthreads();
+    int buf = 0;
+    while (cur < rg.y) {
+        const int nc = (int)min((uint32_t)CH, rg.y - cur);
+        const uint32_t nxt = cur + nc;
+        if (nxt < rg.y) pre = fetch_rec(vrec, cells, nxt, rg.y, tid, nload, per, pre);
+        if (!done) {
+            for (int c = 0; c < nc; ++c) {
+                if (T < bp.eps) { done = true; break; }
+                const float4 *r = &s_rec[buf][c * per];
+                const float v = r[2].w;
+                float A0 = 0.f, A1 = 0.f, A2 = 0.f, B = 0.f, P = 1.0f;
+                for (int k = 0; k < K; ++k) {
+                    const float4 r0 = r[3 * k];
+                    const float dx = px - r0.x, dy = py - r0.y;
+                    if (fabsf(dx) <= r0.z && fabsf(dy) <= r0.w) {
+                        const float4 r1 = r[3 * k + 1];
+                        const float4 r2 = r[3 * k + 2];
+                        const float pw = r1.x * dx * dx + r1.y * dx * dy + r1.z * dy * dy;
+                        const float al = fminf(r1.w * ex2_approx(pw), bp.alpha_max);
+                        A0 += al * r2.x; A1 += al * r2.y; A2 += al * r2.z;
+                        B += al;
+                        P -= P * (v * al);
+                    }
+                }
+                const float w = v * T;
+                N0 += w * A0; N1 += w * A1; N2 += w * A2;
+                D += w * B;
+                T *= P;
+                ++n;
+            }
+            if (T < bp.eps) done = true;
+        }
+        if (nxt < rg.y) s_rec[buf ^ 1][tid] = pre;
+        if (__syncthreads_count(done) == BT) break;
+        buf ^= 1;
+        cur = nxt;
+    }
+    if (inside) {
+        const long long HW = (long long)V.W * V.H;
+        const long long pin = (long long)yi * V.W + xi;
+        float *img = V.out ? V.out : out_rgb + 3 * V.pix_base;
+        const bool hit = D > bp.d_min;
+        const float c0 = hit ? N0 / D : bp.bg0, c1 = hit ? N1 / D : bp.bg1, c2 = hit ? N2 / D : bp.bg2;
+        img[pin] = c0;
+        img[HW + pin] = c1;
+        img[2 * HW + pin] = c2;
+        if (out_rgb2) {
+            float *im2 = out_rgb2 + 3 * V.pix_base;
+            im2[pin] = c0;
+            im2[HW + pin] = c1;
+            im2[2 * HW + pin] = c2;
+        }
+        out_D[V.pix_base + pin] = D;
+        out_nd[V.pix_base + pin] = n;
+    }
+}
+
+void launch_blend_fwd(const ViewDesc *views, int n_views, int total_tiles, const uint2 *ranges,
+                      const uint32_t *tile_cells, const float4 *rec, const BlendParams &bp, float *out_rgb,
+                      float *out_rgb2, float *out_D, int *out_nd, cudaStream_t st) {
+    if (total_tiles == 0) return;
+    k_blend_fwd<<<total_tiles, BT, 0, st>>>(views, n_views, ranges, tile_cells, rec, bp, out_rgb, out_rgb2, out_D,
+                                            out_nd);
+}
+
+// ---------------------------------------------------------------- counters
+// Diagnostic replay of the AABB tests (no blending): per pixel, the
+// (pixel, Gaussian) pairs of blended cells, those passing the AABB test, and
+// the passing pairs over the whole tile list.  counts[0..3] as in dgs_counts.
+__global__ void __launch_bounds__(BT) k_count_pairs(const ViewDesc *__restrict__ views, int n_views,
+                                                    const uint2 *__restrict__ ranges, const uint32_t *__restrict__ cells,
+                                                    const float4 *__restrict__ rec, const int *__restrict__ ndpix,
+                                                    unsigned long long *__restrict__ counts) {
+    __shared__ int s_view;
+    const int tid = threadIdx.x, tile = blockIdx.x;
+    if (tid == 0) s_view = find_view(views, n_views, tile);
+    __syncthreads();
+    const ViewDesc &V = views[s_view];
+    const int local = tile - V.tile_base;
+    const int tx = local % V.Tx, ty = local / V.Tx;
+    const int xi = tx * kTile + (tid & (kTile - 1)), yi = ty * kTile + (tid >> 4);
+    unsigned long long c[4] = {0, 0, 0, 0};
+    if (xi < V.W && yi < V.H) {
+        const int nd = ndpix[V.pix_base + (long long)yi * V.W + xi];
+        const float px = (float)xi + 0.5f, py = (float)yi + 0.5f;
+        const uint2 rg = ranges[tile];
+        const float4 *vrec = rec + V.rec_base * kRecF4;
+        for (uint32_t e = rg.x; e < rg.y; ++e) {
+            const bool blended = (int)(e - rg.x) < nd;
+            const float4 *r = vrec + (long long)cells[e] * V.K * kRecF4;
+            unsigned in = 0;
+            for (int k = 0; k < V.K; ++k) {
+                const float4 r0 = __ldg(r + 3 * k);
+                in += (fabsf(px - r0.x) <= r0.z && fabsf(py - r0.y) <= r0.w) ? 1u : 0u;
+            }
+            c[2] += in;
+            if (blended) { c[0] += V.K; c[1] += in; c[3] += 1; }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        unsigned long long v = c[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((tid & 31) == 0 && v) atomicAdd(counts + i, v);
+    }
+}
+
+void launch_count_pairs(const ViewDesc *views, int n_views, int total_tiles, const uint2 *ranges,
+                        const uint32_t *tile_cells, const float4 *rec, const int *nd, unsigned long long *counts,
+                        cudaStream_t st) {
+    if (total_tiles == 0) return;
+    k_count_pairs<<<total_tiles, BT, 0, st>>>(views, n_views, ranges, tile_cells, rec, nd, counts);
+}
+
+// ---------------------------------------------------------------- adjoint
+// With C = N/D and g = dL/dC:  dN = g/D, dD = -(g.C)/D.  Writing
+// x_n = v_n T_n (dN.A_n + dD B_n), C's degree-0 homogeneity in the weights
+// gives sum_n x_n = 0 over the blended cells, so the total gradient through
+// the transmittance of all LATER cells, S_n = sum_{m>n} x_m, equals
+// -sum_{m<=n} x_m and is known front to back: the replay needs no division
+// by T and stores no per-cell state.  Per Gaussian k of cell n at a pixel:
+//     dL/dalpha = v T_n (dN.c_k + dD) - v S_n / (1 - v alpha)
+//     dL/dc_k   = v T_n alpha dN
+//     dL/dv_n   = T_n (dN.A_n + dD B_n) - S_n sum_k alpha_k / (1 - v alpha_k)
+// then alpha = sigma G' (unless clamped) and G' = exp(-q/2).
+//
+// Phase 1 (thread = pixel) replays a chunk of cells, writing G' per
+// (Gaussian, pixel) and T_n, S_n per (cell, pixel) to shared memory.
+// Phase 2 (warp = Gaussian) sums each Gaussian's nine screen-space
+// gradients over the tile's pixels in registers, reduces across the warp
+// with shuffles and issues one atomic add per value per warp.
+constexpr int BW_G = 64;   // Gaussians per chunk (shared G' table = 64 x 256 floats)
+constexpr int BW_CH = 16;  // cells per chunk at most
+
+__host__ __device__ constexpr int bwd_cells_per_chunk(int K) {
+    return BW_G / K < 1 ? 1 : (BW_G / K > BW_CH ? BW_CH : BW_G / K);
+}
+
+__global__ void __launch_bounds__(BT) k_blend_bwd(const ViewDesc *__restrict__ views, int n_views,
+                                                  const uint2 *__restrict__ ranges, const uint32_t *__restrict__ cells,
+                                                  const float4 *__restrict__ rec, BlendParams bp,
+                                                  const float *__restrict__ rgb, const float *__restrict__ Dpix,
+                                                  const int *__restrict__ ndpix, const float *__restrict__ dL_drgb,
+                                                  float *__restrict__ g2d, float *__restrict__ g_cell_v) {
+    extern __shared__ float4 smem_f4[];
+    __shared__ int s_view, s_ndmax;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tile = blockIdx.x;
+    if (tid == 0) { s_view = find_view(views, n_views, tile); s_ndmax = 0; }
+    __syncthreads();
+    const ViewDesc &V = views[s_view];
+    const int K = V.K;
+    const int per = kRecF4 * K;
+    const int CH = bwd_cells_per_chunk(K);
+    const int nrec = CH * per;                     // float4s per chunk (<= 3 * BW_G < BT)
+    float4 *s_rec0 = smem_f4;                      // [2][nrec]
+    float *sG = reinterpret_cast<float *>(smem_f4 + 2 * nrec);  // [CH*K][BT]
+    float *sT = sG + CH * K * BT;                  // [CH][BT]
+    float *sS = sT + CH * BT;
+    float *sTX = sS + CH * BT;
+    float *sdN = sTX + CH * BT;                    // [4][BT]: dN xyz, dD
+    const int local = tile - V.tile_base;
+    const int tx = local % V.Tx, ty = local / V.Tx;
+    const int xi = tx * kTile + (tid & (kTile - 1)), yi = ty * kTile + (tid >> 4);
+    const bool inside = xi < V.W && yi < V.H;
+    const float px = (float)xi + 0.5f, py = (float)yi + 0.5f;
+    const long long HW = (long long)V.W * V.H;
+    const long long pin = (long long)yi * V.W + xi;
+
+    int nd = 0;
+    float dN0 = 0.f, dN1 = 0.f, dN2 = 0.f, dD = 0.f;
+    if (inside) {
+        const float Dv = Dpix[V.pix_base + pin];
+        if (Dv > bp.d_min) {
+            nd = ndpix[V.pix_base + pin];
+            const float *gi = dL_drgb + 3 * V.pix_base;
+            const float *ci = rgb + 3 * V.pix_base;
+            const float g0 = gi[pin], g1 = gi[HW + pin], g2 = gi[2 * HW + pin];
+            const float c0 = ci[pin], c1 = ci[HW + pin], c2 = ci[2 * HW + pin];
+            const float iD = 1.0f / Dv;
+            dN0 = g0 * iD; dN1 = g1 * iD; dN2 = g2 * iD;
+            dD = -(g0 * c0 + g1 * c1 + g2 * c2) * iD;
+        }
+    }
+    sdN[tid] = dN0; sdN[BT + tid] = dN1; sdN[2 * BT + tid] = dN2; sdN[3 * BT + tid] = dD;
+    if (nd > 0) atomicMax(&s_ndmax, nd);
+    __syncthreads();
+    const uint2 rg = ranges[tile];
+    const uint32_t end = rg.x + min((uint32_t)s_ndmax, rg.y - rg.x);
+    const float4 *vrec = rec + V.rec_base * kRecF4;
+
+    float T = 1.0f, S = 0.0f;
+    float4 pre = make_float4(0.f, 0.f, 0.f, 0.f);
+    uint32_t cur = rg.x;
+    if (cur < end) {
+        pre = fetch_rec(vrec, cells, cur, end, tid, nrec, per, pre);
+        if (tid < nrec) s_rec0[tid] = pre;
+    }
+    __syncthreads();
+    int buf = 0;
+    while (cur < end) {
+        const int nc = (int)min((uint32_t)CH, end - cur);
+        const uint32_t nxt = cur + nc;
+        if (nxt < end) pre = fetch_rec(vrec, cells, nxt, end, tid, nrec, per, pre);
+        const float4 *sr = s_rec0 + buf * nrec;
+        // ---- phase 1: replay per pixel
+        for (int c = 0; c < nc; ++c) {
+            const int n = (int)(cur - rg.x) + c;
+            const float4 *r = sr + c * per;
+            if (n < nd) {
+                const float v = r[2].w;
+                float A0 = 0.f, A1 = 0.f, A2 = 0.f, B = 0.f, P = 1.0f;
+                for (int k = 0; k < K; ++k) {
+                    const float4 r0 = r[3 * k];
+                    const float dx = px - r0.x, dy = py - r0.y;
+                    float Gv = 0.f;
+                    if (fabsf(dx) <= r0.z && fabsf(dy) <= r0.w) {
+                        const float4 r1 = r[3 * k + 1];
+                        const float4 r2 = r[3 * k + 2];
+                        Gv = ex2_approx(r1.x * dx * dx + r1.y * dx * dy + r1.z * dy * dy);
+                        const float al = fminf(r1.w * Gv, bp.alpha_max);
+                        A0 += al * r2.x; A1 += al * r2.y; A2 += al * r2.z;
+                        B += al;
+                        P -= P * (v * al);
+                    }
+                    sG[(c * K + k) * BT + tid] = Gv;
+                }
+                const float X = dN0 * A0 + dN1 * A1 + dN2 * A2 + dD * B;
+                S -= v * T * X;
+                sT[c * BT + tid] = T;
+                sS[c * BT + tid] = S;
+                sTX[c * BT + tid] = T * X;
+                T *= P;
+            } else {
+                for (int k = 0; k < K; ++k) sG[(c * K + k) * BT + tid] = 0.f;
+                sT[c * BT + tid] = 0.f;
+                sS[c * BT + tid] = 0.f;
+                sTX[c * BT + tid] = 0.f;
+            }
+        }
+        __syncthreads();
+        // ---- phase 2: per Gaussian reduction over the tile's pixels
+        for (int j = warp; j < nc * K; j += BT / 32) {
+            const int c = j / K, k = j - c * K;
+            const float4 r0 = sr[c * per + 3 * k], r1 = sr[c * per + 3 * k + 1], r2 = sr[c * per + 3 * k + 2];
+            const float v = r2.w, op = r1.w;
+            const float ca = -2.0f * LN2 * r1.x, cb = -LN2 * r1.y, cc = -2.0f * LN2 * r1.z;  // real conic
+            float acc[10];
+#pragma unroll
+            for (int i = 0; i < 10; ++i) acc[i] = 0.f;
+            bool any = false;
+#pragma unroll
+            for (int q = 0; q < BT / 32; ++q) {
+                const int p = lane + 32 * q;
+                const float Gv = sG[j * BT + p];
+                if (k == 0) acc[9] += sTX[c * BT + p];
+                if (Gv == 0.f) continue;
+                any = true;
+                const float Tp = sT[c * BT + p], Sp = sS[c * BT + p];
+                const float e0 = sdN[p], e1 = sdN[BT + p], e2 = sdN[2 * BT + p], eD = sdN[3 * BT + p];
+                const float raw = op * Gv;
+                const float al = fminf(raw, bp.alpha_max);
+                const float cA = v * Tp;
+                const float om = 1.0f - v * al;
+                const float dal = cA * (e0 * r2.x + e1 * r2.y + e2 * r2.z + eD) - v * Sp / om;
+                acc[6] += cA * al * e0;
+                acc[7] += cA * al * e1;
+                acc[8] += cA * al * e2;
+                acc[9] += -Sp * al / om;
+                if (raw < bp.alpha_max) {
+                    acc[5] += dal * Gv;
+                    const float dq = -0.5f * Gv * (dal * op);
+                    const float dx = (float)(tx * kTile + (p & (kTile - 1))) + 0.5f - r0.x;
+                    const float dy = (float)(ty * kTile + (p >> 4)) + 0.5f - r0.y;
+                    acc[0] += dq * -(2.0f * ca * dx + 2.0f * cb * dy);
+                    acc[1] += dq * -(2.0f * cb * dx + 2.0f * cc * dy);
+                    acc[2] += dq * dx * dx;
+                    acc[3] += dq * 2.0f * dx * dy;
+                    acc[4] += dq * dy * dy;
+                }
+            }
+            const bool warp_any = __any_sync(0xffffffffu, any) || (k == 0 && __any_sync(0xffffffffu, acc[9] != 0.f));
+            if (!warp_any) continue;
+#pragma unroll
+            for (int i = 0; i < 10; ++i) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
+            }
+            const uint32_t cellid = cells[cur + c];
+            const long long g = (long long)cellid * K + k;
+            float *dst = g2d + (V.rec_base + g) * kGradF;
+            float val = 0.f;
+#pragma unroll
+            for (int i = 0; i < 10; ++i)
+                if (lane == i) val = acc[i];
+            if (lane < 9 && val != 0.f) atomicAdd(dst + lane, val);
+            if (lane == 9 && g_cell_v && val != 0.f) atomicAdd(g_cell_v + cellid, val);
+        }
+        if (nxt < end && tid < nrec) s_rec0[(buf ^ 1) * nrec + tid] = pre;
+        __syncthreads();
+        buf ^= 1;
+        cur = nxt;
+    }
+}
+
+static size_t bwd_smem_bytes(int K) {
+    const int per = kRecF4 * K;
+    const int CH = bwd_cells_per_chunk(K);
+    return sizeof(float4) * 2 * CH * per + sizeof(float) * ((size_t)CH * K * BT + 3 * CH * BT + 4 * BT);
+}
+
+// K: Gaussians per cell of the chain's scene (shared-memory sizing)
+void launch_blend_bwd(const ViewDesc *views, int n_views, int total_tiles, int K, const uint2 *ranges,
+                      const uint32_t *tile_cells, const float4 *rec, const BlendParams &bp, const float *rgb,
+                      const float *D, const int *nd, const float *dL_drgb, float *g2d, float *g_cell_v,
+                      cudaStream_t st) {
+    if (total_tiles == 0) return;
+    const size_t sm = bwd_smem_bytes(K);
+    cudaFuncSetAttribute(k_blend_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_blend_bwd<<<total_tiles, BT, sm, st>>>(views, n_views, ranges, tile_cells, rec, bp, rgb, D, nd, dL_drgb, g2d,
+                                             g_cell_v);
+}
+
+}  // namespace dgs

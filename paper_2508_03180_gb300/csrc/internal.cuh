@@ -1,0 +1,147 @@
+// Internal declarations shared by the kernel translation units of the
+// sm_103a Duplex-GS renderer.  Not part of the public ABI (include/dgs.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dgs {
+
+constexpr int kTile = 16;          // tile edge in pixels (Sec. IV-B tile-based paradigm)
+constexpr int kTilePix = kTile * kTile;
+constexpr int kMaxK = 32;          // Gaussians per cell supported
+constexpr int kRecF4 = 3;          // float4s per projected-Gaussian record (48 B)
+constexpr int kGradF = 12;         // floats per screen-space gradient record (48 B)
+
+// One view of a batched launch chain.  Tiles of all views are numbered
+// view-major (tile_base), pixels too (pix_base); (view, cell) entries start
+// at cell_base and the view's projected records at rec_base.  Views of one
+// chain may belong to different resident scenes (scene_slot).
+struct ViewDesc {
+    int W, H, Tx, Ty;
+    int tile_base;
+    int scene_slot;        // index into the chain's scene table
+    long long pix_base;    // first pixel of this view in per-pixel buffers
+    long long cell_base;   // first (view, cell) entry of this view
+    long long rec_base;    // first projected record of this view
+    long long N;           // cells of the view's scene
+    float *out;            // device image [3][H][W] of this view, or NULL (chain buffer)
+    int K;                 // Gaussians per cell of the view's scene
+    int pad0;
+    float fx, fy, cx, cy, znear, pad1;
+    float R[9], t[3], eye[3];
+    float pad2[3];
+};
+
+// Device-side view of one resident scene (structure of arrays).
+struct SceneDev {
+    const float *cell;     // [11][N]: centre xyz, axes xyz, quat wxyz, v
+    const float *gauss;    // [11][G]: mean xyz, scale xyz, quat wxyz, logit
+    const float *sh;       // [C*3][G]: coefficient c, channel ch at plane c*3+ch
+    long long N, G;
+    int K, sh_degree;
+};
+
+struct BlendParams {
+    float eps, alpha_max, d_min, bg0, bg1, bg2, dilation, ksigma;
+};
+
+// ---------------------------------------------------------------- FP32 with one prescribed rounding order
+// Every binning decision (cell culling and tile rectangle, the per-Gaussian
+// AABB inputs) is computed with these: each is exactly one IEEE operation
+// that the compiler may not fuse, so results are bit-identical to any other
+// implementation that performs the same sequence of float operations.
+__device__ __forceinline__ float fmul_s(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fadd_s(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fsub_s(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fdiv_s(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float fsqrt_s(float a) { return __fsqrt_rn(a); }
+
+// Rotation matrix of quaternion (w,x,y,z) after normalisation, row-major.
+__device__ __forceinline__ void rot_from_quat_s(float w, float x, float y, float z, float R[9]) {
+    const float n = fsqrt_s(fadd_s(fadd_s(fadd_s(fmul_s(w, w), fmul_s(x, x)), fmul_s(y, y)), fmul_s(z, z)));
+    w = fdiv_s(w, n); x = fdiv_s(x, n); y = fdiv_s(y, n); z = fdiv_s(z, n);
+    const float xx = fmul_s(x, x), yy = fmul_s(y, y), zz = fmul_s(z, z);
+    const float xy = fmul_s(x, y), xz = fmul_s(x, z), yz = fmul_s(y, z);
+    const float wx = fmul_s(w, x), wy = fmul_s(w, y), wz = fmul_s(w, z);
+    R[0] = fsub_s(1.0f, fmul_s(2.0f, fadd_s(yy, zz)));
+    R[1] = fmul_s(2.0f, fsub_s(xy, wz));
+    R[2] = fmul_s(2.0f, fadd_s(xz, wy));
+    R[3] = fmul_s(2.0f, fadd_s(xy, wz));
+    R[4] = fsub_s(1.0f, fmul_s(2.0f, fadd_s(xx, zz)));
+    R[5] = fmul_s(2.0f, fsub_s(yz, wx));
+    R[6] = fmul_s(2.0f, fsub_s(xz, wy));
+    R[7] = fmul_s(2.0f, fadd_s(yz, wx));
+    R[8] = fsub_s(1.0f, fmul_s(2.0f, fadd_s(xx, yy)));
+}
+
+// v = R p + t, rows summed left to right.
+__device__ __forceinline__ void xform_s(const float R[9], const float t[3], float p0, float p1, float p2,
+                                        float v[3]) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+        v[i] = fadd_s(fadd_s(fadd_s(fmul_s(R[3 * i], p0), fmul_s(R[3 * i + 1], p1)), fmul_s(R[3 * i + 2], p2)), t[i]);
+}
+
+// ---------------------------------------------------------------- launchers
+// binning.cu
+void launch_cell_project(const ViewDesc *views, int n_views, const SceneDev *scenes, long long n_entries,
+                         uint32_t *zkey, uint32_t *zval, short4 *rect, float *depth, uint32_t *count,
+                         uint32_t *visible, cudaStream_t st);
+void launch_gather_counts(const uint32_t *zval_sorted, const uint32_t *count, long long n, uint32_t *out,
+                          cudaStream_t st);
+void launch_emit(const uint32_t *offs, const uint32_t *zval_sorted, const short4 *rect, const ViewDesc *views,
+                 int n_views, long long n_entries, long long L, uint32_t *tkey, uint32_t *tval, cudaStream_t st);
+void launch_tile_ranges(const uint32_t *tkey_sorted, long long L, uint2 *ranges, cudaStream_t st);
+
+// sort.cu
+struct SortScratch {
+    uint32_t *keys_alt, *vals_alt;   // n each
+    uint32_t *hist;                  // 4 * 256
+    uint32_t *status;                // parts * 256
+    uint32_t *counters;              // 4 (one per pass)
+    uint32_t *err;                   // 1
+    long long cap_items, cap_parts;
+};
+long long sort_parts_for(long long n);
+// Stable LSD radix sort of (key, val) by the low `bits` bits.  Results end in
+// keys/vals.  Returns the number of passes.
+int radix_sort_pairs(uint32_t *keys, uint32_t *vals, long long n, int bits, const SortScratch &s,
+                     cudaStream_t st);
+// Exclusive scan; total written to *total (device).  scratch >= scan_scratch_words(n).
+long long scan_scratch_words(long long n);
+void exclusive_scan_u32(const uint32_t *in, uint32_t *out, long long n, uint32_t *total, uint32_t *scratch,
+                        cudaStream_t st);
+
+// project.cu  (one launch per distinct scene of the chain: views whose
+// scene_slot differs from `slot` are skipped)
+void launch_project_fwd(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const uint32_t *count,
+                        const BlendParams &bp, float4 *rec, float *g2d_zero, cudaStream_t st);
+void launch_project_bwd(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const uint32_t *count,
+                        const BlendParams &bp, const float *g2d, float *g_mean, float *g_scale,
+                        float *g_log_scale, float *g_quat, float *g_logit, float *g_sh, cudaStream_t st);
+
+// blend.cu
+void launch_blend_fwd(const ViewDesc *views, int n_views, int total_tiles, const uint2 *ranges,
+                      const uint32_t *tile_cells, const float4 *rec, const BlendParams &bp, float *out_rgb,
+                      float *out_rgb2, float *out_D, int *out_nd, cudaStream_t st);
+void launch_blend_bwd(const ViewDesc *views, int n_views, int total_tiles, int K, const uint2 *ranges,
+                      const uint32_t *tile_cells, const float4 *rec, const BlendParams &bp, const float *rgb,
+                      const float *D, const int *nd, const float *dL_drgb, float *g2d, float *g_cell_v,
+                      cudaStream_t st);
+
+void launch_count_pairs(const ViewDesc *views, int n_views, int total_tiles, const uint2 *ranges,
+                        const uint32_t *tile_cells, const float4 *rec, const int *nd, unsigned long long *counts,
+                        cudaStream_t st);
+
+// misc.cu
+void launch_aos_to_soa(const float *src, int64_t rows, int cols, float *dst, int64_t dst_stride,
+                       cudaStream_t st);
+void launch_soa_to_aos(const float *src, int64_t rows, int cols, int64_t src_stride, float *dst,
+                       cudaStream_t st);
+void launch_fill_f32(float *dst, int64_t n, float v, cudaStream_t st);
+void launch_loss_l1(const float *rgb, const float *target, int64_t n, float *dL, float *partial,
+                    int nblocks, float *loss, cudaStream_t st);
+int loss_l1_blocks(int64_t n);
+
+}  // namespace dgs

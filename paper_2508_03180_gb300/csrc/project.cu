@@ -1,0 +1,402 @@
+// Per-Gaussian projection (the "projected 2D gaussian kernel" G' of Eq. 2)
+// for every view of a batch, and its adjoint.
+//
+// Forward, per Gaussian of a cell that survived culling in that view:
+//   t = R mu + t_cam, mu2 = (fx t_x/t_z + cx, fy t_y/t_z + cy)
+//   Sigma = R(q) diag(s)^2 R(q)^T, Sigma' = J R Sigma R^T J^T + dilation I
+//   (J the pinhole Jacobian at t, t_x/t_z and t_y/t_z clamped to
+//   +-1.3 tan(half FOV)), conic = Sigma'^-1, opacity = sigmoid(logit),
+//   colour = max(0, 0.5 + sum_lm k_lm Y_lm((mu - eye)/|mu - eye|)).
+// mu2 and the AABB half extents k sqrt(Sigma'_xx), k sqrt(Sigma'_yy) are the
+// inputs of the per-pixel skip test (Sec. VI-A): they are computed with the
+// fixed-order FP32 helpers so the skip decision is reproducible.
+//
+// One thread per Gaussian reads its parameters once (SoA planes, coalesced)
+// and writes one 48-byte record per view, so a batch of views costs one pass
+// over the 236 B/Gaussian of parameters.
+#include "internal.cuh"
+
+namespace dgs {
+
+// Real spherical harmonics without the Condon-Shortley phase, index l^2+l+m;
+// each constant is the normalisation of Y_lm (1/(2 sqrt(pi)), sqrt(3/(4 pi)), ...).
+constexpr float SH_C0 = 0.28209479177387814f;
+constexpr float SH_C1 = 0.4886025119029199f;
+constexpr float SH_C2a = 1.0925484305920792f;   // (1/2) sqrt(15/pi)
+constexpr float SH_C2b = 0.31539156525252005f;  // (1/4) sqrt(5/pi)
+constexpr float SH_C2c = 0.5462742152960396f;   // (1/4) sqrt(15/pi)
+constexpr float SH_C3a = 0.5900435899266435f;   // (1/4) sqrt(35/(2 pi))
+constexpr float SH_C3b = 2.890611442640554f;    // (1/2) sqrt(105/pi)
+constexpr float SH_C3c = 0.4570457994644658f;   // (1/4) sqrt(21/(2 pi))
+constexpr float SH_C3d = 0.3731763325901154f;   // (1/4) sqrt(7/pi)
+constexpr float SH_C3e = 1.445305721320277f;    // (1/4) sqrt(105/pi)
+constexpr float LOG2E = 1.4426950408889634f;
+
+__device__ __forceinline__ void sh_eval(float x, float y, float z, int deg, float Y[16]) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) Y[i] = 0.f;
+    Y[0] = SH_C0;
+    if (deg < 1) return;
+    Y[1] = SH_C1 * y; Y[2] = SH_C1 * z; Y[3] = SH_C1 * x;
+    if (deg < 2) return;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    Y[4] = SH_C2a * x * y; Y[5] = SH_C2a * y * z; Y[6] = SH_C2b * (3.0f * zz - 1.0f);
+    Y[7] = SH_C2a * x * z; Y[8] = SH_C2c * (xx - yy);
+    if (deg < 3) return;
+    Y[9] = SH_C3a * y * (3.0f * xx - yy); Y[10] = SH_C3b * x * y * z;
+    Y[11] = SH_C3c * y * (5.0f * zz - 1.0f); Y[12] = SH_C3d * z * (5.0f * zz - 3.0f);
+    Y[13] = SH_C3c * x * (5.0f * zz - 1.0f); Y[14] = SH_C3e * z * (xx - yy);
+    Y[15] = SH_C3a * x * (xx - 3.0f * yy);
+}
+
+// Partial derivatives of the formulas above in x, y, z (treated as free).
+__device__ __forceinline__ void sh_grad(float x, float y, float z, int deg, float dX[16], float dY[16], float dZ[16]) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) dX[i] = dY[i] = dZ[i] = 0.f;
+    if (deg < 1) return;
+    dX[1] = 0.f; dY[1] = SH_C1; dZ[1] = 0.f;
+    dX[2] = 0.f; dY[2] = 0.f; dZ[2] = SH_C1;
+    dX[3] = SH_C1; dY[3] = 0.f; dZ[3] = 0.f;
+    if (deg < 2) return;
+    dX[4] = SH_C2a * y; dY[4] = SH_C2a * x; dZ[4] = 0.f;
+    dX[5] = 0.f; dY[5] = SH_C2a * z; dZ[5] = SH_C2a * y;
+    dX[6] = 0.f; dY[6] = 0.f; dZ[6] = SH_C2b * 6.0f * z;
+    dX[7] = SH_C2a * z; dY[7] = 0.f; dZ[7] = SH_C2a * x;
+    dX[8] = SH_C2c * 2.0f * x; dY[8] = -SH_C2c * 2.0f * y; dZ[8] = 0.f;
+    if (deg < 3) return;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    dX[9] = SH_C3a * 6.0f * x * y; dY[9] = SH_C3a * 3.0f * (xx - yy); dZ[9] = 0.f;
+    dX[10] = SH_C3b * y * z; dY[10] = SH_C3b * x * z; dZ[10] = SH_C3b * x * y;
+    dX[11] = 0.f; dY[11] = SH_C3c * (5.0f * zz - 1.0f); dZ[11] = SH_C3c * 10.0f * y * z;
+    dX[12] = 0.f; dY[12] = 0.f; dZ[12] = SH_C3d * (15.0f * zz - 3.0f);
+    dX[13] = SH_C3c * (5.0f * zz - 1.0f); dY[13] = 0.f; dZ[13] = SH_C3c * 10.0f * x * z;
+    dX[14] = SH_C3e * 2.0f * x * z; dY[14] = -SH_C3e * 2.0f * y * z; dZ[14] = SH_C3e * (xx - yy);
+    dX[15] = SH_C3a * 3.0f * (xx - yy); dY[15] = -SH_C3a * 6.0f * x * y; dZ[15] = 0.f;
+}
+
+struct GaussIn {
+    float mean[3], scale[3], quat[4], logit;
+};
+
+__device__ __forceinline__ GaussIn load_gauss(const float *__restrict__ gp, long long G, long long g) {
+    GaussIn p;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) p.mean[i] = gp[i * G + g];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) p.scale[i] = gp[(3 + i) * G + g];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) p.quat[i] = gp[(6 + i) * G + g];
+    p.logit = gp[10 * G + g];
+    return p;
+}
+
+// Fixed-order FP32 part shared by forward and backward: view-space mean,
+// J, T = J R_view, 3D covariance, and the diagonal of Sigma'.
+struct ProjCore {
+    float t[3], x, y, xc, yc, J00, J02, J11, J12, T[6], Rg[9], S[9], V[6], sxx, syy;
+    bool valid;
+};
+
+__device__ __forceinline__ void proj_core(const ViewDesc &Vw, const GaussIn &p, float dilation, ProjCore &c) {
+    xform_s(Vw.R, Vw.t, p.mean[0], p.mean[1], p.mean[2], c.t);
+    c.valid = c.t[2] > Vw.znear;
+    if (!c.valid) return;
+    c.x = fdiv_s(c.t[0], c.t[2]);
+    c.y = fdiv_s(c.t[1], c.t[2]);
+    rot_from_quat_s(p.quat[0], p.quat[1], p.quat[2], p.quat[3], c.Rg);
+    float M[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) M[3 * i + j] = fmul_s(c.Rg[3 * i + j], p.scale[j]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            c.S[3 * i + j] = fadd_s(fadd_s(fmul_s(M[3 * i], M[3 * j]), fmul_s(M[3 * i + 1], M[3 * j + 1])),
+                                    fmul_s(M[3 * i + 2], M[3 * j + 2]));
+    const float limx = fmul_s(1.3f, fdiv_s(fmul_s(0.5f, (float)Vw.W), Vw.fx));
+    const float limy = fmul_s(1.3f, fdiv_s(fmul_s(0.5f, (float)Vw.H), Vw.fy));
+    c.xc = fminf(fmaxf(c.x, -limx), limx);
+    c.yc = fminf(fmaxf(c.y, -limy), limy);
+    c.J00 = fdiv_s(Vw.fx, c.t[2]);
+    c.J02 = -fdiv_s(fmul_s(Vw.fx, c.xc), c.t[2]);
+    c.J11 = fdiv_s(Vw.fy, c.t[2]);
+    c.J12 = -fdiv_s(fmul_s(Vw.fy, c.yc), c.t[2]);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        c.T[j] = fadd_s(fmul_s(c.J00, Vw.R[j]), fmul_s(c.J02, Vw.R[6 + j]));
+        c.T[3 + j] = fadd_s(fmul_s(c.J11, Vw.R[3 + j]), fmul_s(c.J12, Vw.R[6 + j]));
+    }
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            c.V[3 * a + j] = fadd_s(fadd_s(fmul_s(c.T[3 * a], c.S[j]), fmul_s(c.T[3 * a + 1], c.S[3 + j])),
+                                    fmul_s(c.T[3 * a + 2], c.S[6 + j]));
+    c.sxx = fadd_s(fadd_s(fadd_s(fmul_s(c.V[0], c.T[0]), fmul_s(c.V[1], c.T[1])), fmul_s(c.V[2], c.T[2])), dilation);
+    c.syy = fadd_s(fadd_s(fadd_s(fmul_s(c.V[3], c.T[3]), fmul_s(c.V[4], c.T[4])), fmul_s(c.V[5], c.T[5])), dilation);
+}
+
+__global__ void __launch_bounds__(128) k_project_fwd(const ViewDesc *__restrict__ views, int n_views, int slot,
+                                                     SceneDev sc, const uint32_t *__restrict__ count, BlendParams bp,
+                                                     float4 *__restrict__ rec, float *__restrict__ g2d_zero) {
+    const long long G = sc.G, N = sc.N;
+    const int K = sc.K, C = (sc.sh_degree + 1) * (sc.sh_degree + 1);
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < G; g += (long long)gridDim.x * blockDim.x) {
+        const long long cell = g / K;
+        bool any = false;
+        for (int v = 0; v < n_views; ++v)
+            any |= views[v].scene_slot == slot && count[views[v].cell_base + cell] != 0u;
+        if (!any) continue;  // cell culled in every view: nothing reads this Gaussian
+        const GaussIn p = load_gauss(sc.gauss, G, g);
+        float k[16][3];
+#pragma unroll
+        for (int c = 0; c < 16; ++c)
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) k[c][ch] = c < C ? sc.sh[(c * 3 + ch) * G + g] : 0.f;
+        const float opac = 1.0f / (1.0f + expf(-p.logit));
+        const float cv = sc.cell[10 * N + cell];
+        for (int v = 0; v < n_views; ++v) {
+            const ViewDesc &Vw = views[v];
+            if (Vw.scene_slot != slot || count[Vw.cell_base + cell] == 0u) continue;
+            ProjCore c;
+            proj_core(Vw, p, bp.dilation, c);
+            float4 r0, r1, r2;
+            if (!c.valid) {
+                r0 = make_float4(0.f, 0.f, -1.f, -1.f);
+                r1 = make_float4(0.f, 0.f, 0.f, 0.f);
+                r2 = make_float4(0.f, 0.f, 0.f, cv);
+            } else {
+                const float mx = fadd_s(fmul_s(Vw.fx, c.x), Vw.cx);
+                const float my = fadd_s(fmul_s(Vw.fy, c.y), Vw.cy);
+                const float ex = fmul_s(bp.ksigma, fsqrt_s(c.sxx));
+                const float ey = fmul_s(bp.ksigma, fsqrt_s(c.syy));
+                const float sxy = c.V[0] * c.T[3] + c.V[1] * c.T[4] + c.V[2] * c.T[5];
+                const float inv = 1.0f / (c.sxx * c.syy - sxy * sxy);
+                const float ca = c.syy * inv, cb = -sxy * inv, cc = c.sxx * inv;
+                float d0 = p.mean[0] - Vw.eye[0], d1 = p.mean[1] - Vw.eye[1], d2 = p.mean[2] - Vw.eye[2];
+                const float il = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+                d0 *= il; d1 *= il; d2 *= il;
+                float Y[16];
+                sh_eval(d0, d1, d2, sc.sh_degree, Y);
+                float col[3];
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) {
+                    float s = 0.5f;
+#pragma unroll
+                    for (int cidx = 0; cidx < 16; ++cidx) s += k[cidx][ch] * Y[cidx];
+                    col[ch] = fmaxf(s, 0.0f);
+                }
+                r0 = make_float4(mx, my, ex, ey);
+                // conic pre-scaled so that G' = exp2(r1.x dx^2 + r1.y dx dy + r1.z dy^2)
+                r1 = make_float4(-0.5f * LOG2E * ca, -LOG2E * cb, -0.5f * LOG2E * cc, opac);
+                r2 = make_float4(col[0], col[1], col[2], cv);
+            }
+            float4 *o = rec + (Vw.rec_base + g) * kRecF4;
+            o[0] = r0; o[1] = r1; o[2] = r2;
+            if (g2d_zero) {
+                float4 *z = reinterpret_cast<float4 *>(g2d_zero + (Vw.rec_base + g) * kGradF);
+                z[0] = z[1] = z[2] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+    }
+}
+
+static int grid_for(long long n, int threads) {
+    long long b = (n + threads - 1) / threads;
+    const long long cap = 152LL * 16;
+    if (b > cap) b = cap;
+    return (int)(b < 1 ? 1 : b);
+}
+
+void launch_project_fwd(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const uint32_t *count,
+                        const BlendParams &bp, float4 *rec, float *g2d_zero, cudaStream_t st) {
+    if (sc.G == 0 || n_views == 0) return;
+    k_project_fwd<<<grid_for(sc.G, 128), 128, 0, st>>>(views, n_views, slot, sc, count, bp, rec, g2d_zero);
+}
+
+// ---------------------------------------------------------------- adjoint
+// Input per (view, Gaussian): dL/d(mu2 x, y), dL/d(conic a, b, c) with
+// q = a dx^2 + 2 b dx dy + c dy^2, dL/d(opacity), dL/d(rgb).  Chain rule
+// through the forward above (clamp masks as in the forward), summed over
+// views; outputs are written, not accumulated.
+__global__ void __launch_bounds__(128) k_project_bwd(const ViewDesc *__restrict__ views, int n_views, int slot,
+                                                     SceneDev sc, const uint32_t *__restrict__ count, BlendParams bp,
+                                                     const float *__restrict__ g2d, float *__restrict__ g_mean,
+                                                     float *__restrict__ g_scale,
+                                                     float *__restrict__ g_log_scale, float *__restrict__ g_quat,
+                                                     float *__restrict__ g_logit, float *__restrict__ g_sh) {
+    const long long G = sc.G;
+    const int K = sc.K, C = (sc.sh_degree + 1) * (sc.sh_degree + 1);
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < G; g += (long long)gridDim.x * blockDim.x) {
+        const long long cell = g / K;
+        float gm[3] = {0.f, 0.f, 0.f}, gs[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f};
+        float gq[4] = {0.f, 0.f, 0.f, 0.f}, glog = 0.f;
+        float gk[16][3];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) gk[c][0] = gk[c][1] = gk[c][2] = 0.f;
+        bool any = false;
+        for (int v = 0; v < n_views; ++v)
+            any |= views[v].scene_slot == slot && count[views[v].cell_base + cell] != 0u;
+        if (any) {
+            const GaussIn p = load_gauss(sc.gauss, G, g);
+            float k[16][3];
+#pragma unroll
+            for (int c = 0; c < 16; ++c)
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) k[c][ch] = c < C ? sc.sh[(c * 3 + ch) * G + g] : 0.f;
+            const float opac = 1.0f / (1.0f + expf(-p.logit));
+            for (int v = 0; v < n_views; ++v) {
+                const ViewDesc &Vw = views[v];
+                if (Vw.scene_slot != slot || count[Vw.cell_base + cell] == 0u) continue;
+                const float4 *gr = reinterpret_cast<const float4 *>(g2d + (Vw.rec_base + g) * kGradF);
+                const float4 a0 = gr[0], a1 = gr[1], a2 = gr[2];
+                const float gmx = a0.x, gmy = a0.y, gca = a0.z, gcb = a0.w, gcc = a1.x, gop = a1.y;
+                const float grgb[3] = {a1.z, a1.w, a2.x};
+                if (gmx == 0.f && gmy == 0.f && gca == 0.f && gcb == 0.f && gcc == 0.f && gop == 0.f &&
+                    grgb[0] == 0.f && grgb[1] == 0.f && grgb[2] == 0.f)
+                    continue;
+                ProjCore c;
+                proj_core(Vw, p, bp.dilation, c);
+                if (!c.valid) continue;
+                // opacity
+                glog += gop * opac * (1.0f - opac);
+                // colour
+                {
+                    float u0 = p.mean[0] - Vw.eye[0], u1 = p.mean[1] - Vw.eye[1], u2 = p.mean[2] - Vw.eye[2];
+                    const float il = rsqrtf(u0 * u0 + u1 * u1 + u2 * u2);
+                    const float d0 = u0 * il, d1 = u1 * il, d2 = u2 * il;
+                    float Y[16], dX[16], dY[16], dZ[16];
+                    sh_eval(d0, d1, d2, sc.sh_degree, Y);
+                    sh_grad(d0, d1, d2, sc.sh_degree, dX, dY, dZ);
+                    float gd[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+                    for (int ch = 0; ch < 3; ++ch) {
+                        float s = 0.5f;
+#pragma unroll
+                        for (int ci = 0; ci < 16; ++ci) s += k[ci][ch] * Y[ci];
+                        if (s <= 0.0f) continue;  // clamped at 0
+                        const float gc = grgb[ch];
+#pragma unroll
+                        for (int ci = 0; ci < 16; ++ci) {
+                            gk[ci][ch] += gc * Y[ci];
+                            const float w = gc * k[ci][ch];
+                            gd[0] += w * dX[ci]; gd[1] += w * dY[ci]; gd[2] += w * dZ[ci];
+                        }
+                    }
+                    const float dd = gd[0] * d0 + gd[1] * d1 + gd[2] * d2;
+                    gm[0] += (gd[0] - dd * d0) * il;
+                    gm[1] += (gd[1] - dd * d1) * il;
+                    gm[2] += (gd[2] - dd * d2) * il;
+                }
+                // conic -> Sigma' (H = -Q G_Q Q, G_Q = [[ga, gb/2], [gb/2, gc]])
+                const float sxy = c.V[0] * c.T[3] + c.V[1] * c.T[4] + c.V[2] * c.T[5];
+                const float inv = 1.0f / (c.sxx * c.syy - sxy * sxy);
+                const float qa = c.syy * inv, qb = -sxy * inv, qc = c.sxx * inv;
+                const float P00 = gca * qa + 0.5f * gcb * qb, P01 = gca * qb + 0.5f * gcb * qc;
+                const float P10 = 0.5f * gcb * qa + gcc * qb, P11 = 0.5f * gcb * qb + gcc * qc;
+                const float H00 = -(qa * P00 + qb * P10), H01 = -(qa * P01 + qb * P11), H11 = -(qb * P01 + qc * P11);
+                // Sigma' = T Sigma T^T:  dL/dSigma = T^T H T,  dL/dT = 2 H T Sigma
+                float HT[6];  // H T (2x3)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    HT[j] = H00 * c.T[j] + H01 * c.T[3 + j];
+                    HT[3 + j] = H01 * c.T[j] + H11 * c.T[3 + j];
+                }
+                float gSig[9];
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) gSig[3 * i + j] = c.T[i] * HT[j] + c.T[3 + i] * HT[3 + j];
+                float gT[6];
+#pragma unroll
+                for (int a = 0; a < 2; ++a)
+#pragma unroll
+                    for (int j = 0; j < 3; ++j)
+                        gT[3 * a + j] = 2.0f * (HT[3 * a] * c.S[j] + HT[3 * a + 1] * c.S[3 + j] + HT[3 * a + 2] * c.S[6 + j]);
+                // T = J R_view
+                const float gJ00 = gT[0] * Vw.R[0] + gT[1] * Vw.R[1] + gT[2] * Vw.R[2];
+                const float gJ02 = gT[0] * Vw.R[6] + gT[1] * Vw.R[7] + gT[2] * Vw.R[8];
+                const float gJ11 = gT[3] * Vw.R[3] + gT[4] * Vw.R[4] + gT[5] * Vw.R[5];
+                const float gJ12 = gT[3] * Vw.R[6] + gT[4] * Vw.R[7] + gT[5] * Vw.R[8];
+                const float tz = c.t[2], itz = 1.0f / tz, itz2 = itz * itz;
+                float gt[3] = {0.f, 0.f, 0.f};
+                gt[2] += -gJ00 * Vw.fx * itz2 - gJ11 * Vw.fy * itz2;
+                const float limx = 1.3f * (0.5f * (float)Vw.W / Vw.fx), limy = 1.3f * (0.5f * (float)Vw.H / Vw.fy);
+                if (c.x >= -limx && c.x <= limx) {  // J02 = -fx t_x / t_z^2
+                    gt[0] += -gJ02 * Vw.fx * itz2;
+                    gt[2] += gJ02 * 2.0f * Vw.fx * c.t[0] * itz2 * itz;
+                } else {                              // J02 = -fx xc / t_z
+                    gt[2] += gJ02 * Vw.fx * c.xc * itz2;
+                }
+                if (c.y >= -limy && c.y <= limy) {
+                    gt[1] += -gJ12 * Vw.fy * itz2;
+                    gt[2] += gJ12 * 2.0f * Vw.fy * c.t[1] * itz2 * itz;
+                } else {
+                    gt[2] += gJ12 * Vw.fy * c.yc * itz2;
+                }
+                // projected mean
+                gt[0] += gmx * Vw.fx * itz;
+                gt[1] += gmy * Vw.fy * itz;
+                gt[2] += -(gmx * Vw.fx * c.t[0] + gmy * Vw.fy * c.t[1]) * itz2;
+                // t = R mu + t_cam
+#pragma unroll
+                for (int j = 0; j < 3; ++j) gm[j] += Vw.R[j] * gt[0] + Vw.R[3 + j] * gt[1] + Vw.R[6 + j] * gt[2];
+                // Sigma = M M^T, M = R(q) diag(s):  dL/dM = 2 dL/dSigma M
+                float gR[9];
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        const float gM = 2.0f * (gSig[3 * i] * c.Rg[j] * p.scale[j] + gSig[3 * i + 1] * c.Rg[3 + j] * p.scale[j] +
+                                                 gSig[3 * i + 2] * c.Rg[6 + j] * p.scale[j]);
+                        gs[j] += gM * c.Rg[3 * i + j];
+                        gR[3 * i + j] = gM * p.scale[j];
+                    }
+                // R(q_hat), then q_hat = q / |q|
+                const float qn = sqrtf(p.quat[0] * p.quat[0] + p.quat[1] * p.quat[1] + p.quat[2] * p.quat[2] + p.quat[3] * p.quat[3]);
+                const float w = p.quat[0] / qn, x = p.quat[1] / qn, y = p.quat[2] / qn, z = p.quat[3] / qn;
+                float gh[4];
+                gh[0] = 2.0f * (-z * gR[1] + y * gR[2] + z * gR[3] - x * gR[5] - y * gR[6] + x * gR[7]);
+                gh[1] = 2.0f * (y * gR[1] + z * gR[2] + y * gR[3] - 2.0f * x * gR[4] - w * gR[5] + z * gR[6] + w * gR[7] - 2.0f * x * gR[8]);
+                gh[2] = 2.0f * (-2.0f * y * gR[0] + x * gR[1] + w * gR[2] + x * gR[3] + z * gR[5] - w * gR[6] + z * gR[7] - 2.0f * y * gR[8]);
+                gh[3] = 2.0f * (-2.0f * z * gR[0] - w * gR[1] + x * gR[2] + w * gR[3] - 2.0f * z * gR[4] + y * gR[5] + x * gR[6] + y * gR[7]);
+                const float hq = (gh[0] * w + gh[1] * x + gh[2] * y + gh[3] * z);
+                gq[0] += (gh[0] - hq * w) / qn;
+                gq[1] += (gh[1] - hq * x) / qn;
+                gq[2] += (gh[2] - hq * y) / qn;
+                gq[3] += (gh[3] - hq * z) / qn;
+            }
+            // d/d log s = s d/ds
+#pragma unroll
+            for (int j = 0; j < 3; ++j) gls[j] = gs[j] * p.scale[j];
+        }
+        if (g_mean) { g_mean[3 * g] = gm[0]; g_mean[3 * g + 1] = gm[1]; g_mean[3 * g + 2] = gm[2]; }
+        if (g_scale) { g_scale[3 * g] = gs[0]; g_scale[3 * g + 1] = gs[1]; g_scale[3 * g + 2] = gs[2]; }
+        if (g_log_scale) { g_log_scale[3 * g] = gls[0]; g_log_scale[3 * g + 1] = gls[1]; g_log_scale[3 * g + 2] = gls[2]; }
+        if (g_quat) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) g_quat[4 * g + i] = gq[i];
+        }
+        if (g_logit) g_logit[g] = glog;
+        if (g_sh) {
+#pragma unroll
+            for (int ci = 0; ci < 16; ++ci)
+                if (ci < C) {
+#pragma unroll
+                    for (int ch = 0; ch < 3; ++ch) g_sh[(g * C + ci) * 3 + ch] = gk[ci][ch];
+                }
+        }
+    }
+}
+
+void launch_project_bwd(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const uint32_t *count,
+                        const BlendParams &bp, const float *g2d, float *g_mean, float *g_scale, float *g_log_scale,
+                        float *g_quat, float *g_logit, float *g_sh, cudaStream_t st) {
+    if (sc.G == 0) return;
+    k_project_bwd<<<grid_for(sc.G, 128), 128, 0, st>>>(views, n_views, slot, sc, count, bp, g2d, g_mean, g_scale,
+                                                       g_log_scale, g_quat, g_logit, g_sh);
+}
+
+}  // namespace dgs

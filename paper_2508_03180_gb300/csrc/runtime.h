@@ -1,0 +1,180 @@
+// Host-side runtime objects of the library (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <condition_variable>
+#include <cstdint>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <set>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/dgs.h"
+#include "internal.cuh"
+
+namespace dgs {
+
+constexpr int kMaxCamSlots = 4096;
+// words of the per-workspace "small" device block (and its pinned mirror)
+constexpr int kSmallTotal = 0;    // sort length L
+constexpr int kSmallSortErr = 1;  // a radix-sort look-back wait gave up
+constexpr int kSmallVisible = 2;  // (view, cell) pairs that survived culling
+
+dgs_status set_error(dgs_status code, const std::string &msg);
+dgs_status cuda_error(cudaError_t e, const char *what);
+
+// Grow-only device allocation.
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    dgs_status ensure(size_t bytes);
+    void release();
+    ~DevBuf() { release(); }
+};
+
+// A resident scene: parameters as structure-of-arrays planes in HBM.
+struct Scene {
+    int64_t N = 0, G = 0;
+    int K = 1, deg = 0, C = 1;
+    DevBuf cell, gauss, sh;
+    SceneDev dev() const;
+};
+
+// One view of a launch chain, as requested.
+struct ChainView {
+    uint32_t scene_id;
+    dgs_camera cam;
+    float *out = nullptr;  // device destination of this view's image (NULL = chain buffer)
+};
+
+// Buffers of one launch chain (a render, or a serving batch).  A forward
+// state owns its workspace until released; otherwise workspaces go back to
+// a pool and are reused once their `done` event has fired.
+struct Workspace {
+    DevBuf views, scenes;
+    DevBuf zkey, zval, rect, depth, count, cnt_sorted, offs;  // per (view, cell)
+    DevBuf tkey, tval;                                       // per (tile, cell) pair
+    DevBuf ranges;                                           // per tile
+    DevBuf rec, g2d;                                         // per (view, Gaussian)
+    DevBuf Dpix, ndpix, rgb;                                 // per pixel
+    DevBuf gstage;                                           // backward staging
+    DevBuf sort_k, sort_v, sort_hist, sort_status, sort_ctr, small, scan;
+    uint32_t *h_small = nullptr;  // pinned mirror of `small`
+    ViewDesc *h_views = nullptr;
+    size_t h_views_cap = 0;
+    SceneDev *h_scenes = nullptr;
+    size_t h_scenes_cap = 0;
+    cudaEvent_t done = nullptr;
+    cudaStream_t stream = 0;
+    // description of the last chain
+    std::vector<ViewDesc> hviews;
+    std::vector<uint32_t> scene_ids;  // slot -> scene id
+    int V = 0, total_tiles = 0;
+    long long total_px = 0, L = 0, n_entries = 0, n_records = 0;
+    bool bwd_done = false;
+    dgs_status init();
+    std::vector<DevBuf *> all();
+    ~Workspace();
+};
+
+dgs_status ensure_sort_scratch(Workspace &ws, long long n);
+SortScratch sort_scratch_of(Workspace &ws);
+BlendParams blend_params(const dgs_config &c);
+
+// ---------------------------------------------------------------- serving
+struct PendingReq {
+    uint64_t ticket;
+    dgs_request req;
+    double t_submit;
+    int64_t bytes;  // admission estimate
+};
+
+struct InflightBatch {
+    std::unique_ptr<Workspace> ws;
+    std::vector<PendingReq> reqs;
+    int stream_idx = 0;
+    double t_start = 0;
+    int64_t bytes = 0;
+    dgs_status status = DGS_OK;
+};
+
+constexpr int kServeStreams = 2;  // launch chains in flight at once
+
+struct ServeState {
+    std::thread worker;
+    bool stop = false;
+    int max_batch = 8, queue_cap = 1024;
+    std::mutex m;                           // guards everything below
+    std::condition_variable cv_work, cv_done;
+    std::deque<PendingReq> pending;
+    std::unordered_map<uint64_t, dgs_result> finished;
+    std::set<uint64_t> open;                // submitted and not yet consumed by poll
+    uint64_t next_ticket = 1;
+    int64_t reserved = 0;                   // admission estimates of batches in flight
+    int64_t budget = 0;
+    cudaStream_t streams[kServeStreams] = {};
+    cudaEvent_t events[kServeStreams] = {};
+    bool busy[kServeStreams] = {};
+};
+
+}  // namespace dgs
+
+struct dgs_fwd_state {
+    std::unique_ptr<dgs::Workspace> ws;
+    uint32_t scene_id = 0;
+};
+
+namespace dgs {
+// Per-stage event profiling (dgs_profile_enable / dgs_profile_read).
+struct Profiler {
+    bool on = false;
+    struct Pending { int stage; cudaEvent_t a, b; };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> spare;
+    double ms[16] = {};
+    int64_t launches[16] = {};
+    cudaEvent_t take();
+    void drain();
+    ~Profiler();
+};
+// RAII bracket of one stage on stream st (no-op when profiling is off).
+struct StageTimer {
+    Profiler &p;
+    int stage;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr;
+    StageTimer(Profiler &p_, int s, cudaStream_t st_);
+    ~StageTimer();
+};
+}  // namespace dgs
+
+struct dgs_ctx {
+    dgs_config cfg;
+    dgs::Profiler prof;
+    std::mutex mu;  // serialises every ABI call (and the serving worker's launches)
+    std::map<uint32_t, std::unique_ptr<dgs::Scene>> scenes;
+    uint32_t next_scene = 1;
+    std::vector<dgs_camera> cams;
+    std::vector<uint8_t> cam_set;
+    std::vector<std::unique_ptr<dgs::Workspace>> pool;
+    std::set<dgs_fwd_state *> live_states;
+    dgs::DevBuf aux, loss_partial;
+    std::unique_ptr<dgs::Workspace> sort_ws;
+    std::unique_ptr<dgs::ServeState> serve;
+};
+
+namespace dgs {
+std::unique_ptr<Workspace> acquire_ws(dgs_ctx *ctx, cudaStream_t st, dgs_status *err);
+// Forward launch chain over views of one or more resident scenes (caller
+// holds ctx->mu).  Writes the images to out_img (device, [3][H][W] per view
+// back to back) and, if keep_rgb, also to ws.rgb.  grad_buffers: allocate and
+// zero the screen-space gradient accumulators for a later backward.
+dgs_status chain_forward(dgs_ctx *ctx, Workspace &ws, const std::vector<ChainView> &views, float *out_img,
+                         bool keep_rgb, bool grad_buffers, cudaStream_t st);
+}  // namespace dgs

@@ -1,0 +1,273 @@
+// Stable LSD radix sort of (uint32 key, uint32 value) pairs, 8-bit digits,
+// one "onesweep" pass per digit: every CTA ranks a 4096-item partition
+// locally, then learns the global offset of each digit from its predecessors
+// through decoupled look-back (Merrill & Garland single-pass prefix scan,
+// applied per digit as in Adinets & Merrill's Onesweep).  The digit
+// histograms of all passes come from one upfront read of the keys.
+//
+// Sec. IV-B sorts the cell sequence with a radix sort; its cost grows with
+// the sequence length, which is why the sort runs over cells, not Gaussians
+// (Sec. VII-D, Tab. VI).
+//
+// Every wait on another CTA is bounded: after kSpinLimit polls the CTA sets
+// *err, treats the missing count as 0 and carries on, so the kernel always
+// finishes; the host turns a set flag into an error.
+#include "internal.cuh"
+
+namespace dgs {
+
+constexpr int RS_THREADS = 256;
+constexpr int RS_WARPS = RS_THREADS / 32;
+constexpr int RS_ITEMS = 16;                       // per thread
+constexpr int RS_TILE = RS_THREADS * RS_ITEMS;      // 4096 items per partition
+constexpr int RS_WARP_ITEMS = 32 * RS_ITEMS;        // 512 contiguous items per warp
+constexpr uint32_t FLAG_AGG = 1u << 30;             // partition's own count published
+constexpr uint32_t FLAG_INC = 2u << 30;             // inclusive prefix published
+constexpr uint32_t COUNT_MASK = (1u << 30) - 1;
+constexpr int kSpinLimit = 1 << 22;
+
+long long sort_parts_for(long long n) { return (n + RS_TILE - 1) / RS_TILE; }
+
+// Histograms of every digit of every pass in one read of the keys.
+__global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint32_t *__restrict__ keys, long long n, int passes,
+                                                        uint32_t *__restrict__ hist) {
+    __shared__ uint32_t sh[4][256];
+    for (int i = threadIdx.x; i < 4 * 256; i += RS_THREADS) (&sh[0][0])[i] = 0;
+    __syncthreads();
+    for (long long i = blockIdx.x * (long long)RS_THREADS + threadIdx.x; i < n; i += (long long)gridDim.x * RS_THREADS) {
+        const uint32_t k = keys[i];
+        for (int p = 0; p < passes; ++p) atomicAdd(&sh[p][(k >> (8 * p)) & 255u], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * 256; i += RS_THREADS) {
+        const uint32_t c = (&sh[0][0])[i];
+        if (c) atomicAdd(&hist[i], c);
+    }
+}
+
+// Exclusive scan of each pass's 256 counts (one warp-free block per pass).
+__global__ void k_rs_hist_scan(uint32_t *hist) {
+    __shared__ uint32_t s[256];
+    const int p = blockIdx.x, t = threadIdx.x;
+    s[t] = hist[p * 256 + t];
+    __syncthreads();
+    for (int off = 1; off < 256; off <<= 1) {
+        const uint32_t v = t >= off ? s[t - off] : 0u;
+        __syncthreads();
+        s[t] += v;
+        __syncthreads();
+    }
+    hist[p * 256 + t] = t == 0 ? 0u : s[t - 1];
+}
+
+__device__ __forceinline__ uint32_t ld_volatile(const uint32_t *p) { return *(const volatile uint32_t *)p; }
+
+__global__ void __launch_bounds__(RS_THREADS) k_rs_pass(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin,
+                                                        uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
+                                                        long long n, int shift, const uint32_t *__restrict__ digit_base,
+                                                        uint32_t *__restrict__ status, uint32_t *__restrict__ counter,
+                                                        uint32_t *__restrict__ err) {
+    __shared__ uint32_t s_warp[RS_WARPS][256];   // per-warp digit counts, then per-warp offsets
+    __shared__ uint32_t s_base[256];             // global destination of the partition's first item per digit
+    __shared__ uint32_t s_part;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_part = atomicAdd(counter, 1u);  // partitions in launch order: look-back never waits on a later one
+    for (int i = tid; i < RS_WARPS * 256; i += RS_THREADS) (&s_warp[0][0])[i] = 0;
+    __syncthreads();
+    const long long part = s_part;
+    const long long base = part * RS_TILE + (long long)warp * RS_WARP_ITEMS;
+
+    uint32_t key[RS_ITEMS], val[RS_ITEMS], rank[RS_ITEMS];
+#pragma unroll
+    for (int it = 0; it < RS_ITEMS; ++it) {
+        const long long idx = base + it * 32 + lane;
+        const bool ok = idx < n;
+        key[it] = ok ? kin[idx] : 0u;
+        val[it] = ok ? vin[idx] : 0u;
+    }
+    const unsigned lt_mask = (1u << lane) - 1u;
+    // rank inside the warp, in item order (it, lane): stable
+#pragma unroll
+    for (int it = 0; it < RS_ITEMS; ++it) {
+        const long long idx = base + it * 32 + lane;
+        const bool ok = idx < n;
+        const unsigned active = __ballot_sync(0xffffffffu, ok);
+        rank[it] = 0;
+        if (ok) {
+            const uint32_t d = (key[it] >> shift) & 255u;
+            const unsigned peers = __match_any_sync(active, d);
+            const uint32_t before = s_warp[warp][d];
+            rank[it] = before + __popc(peers & lt_mask);
+            __syncwarp(active);
+            if (lane == __ffs(peers) - 1) s_warp[warp][d] = before + __popc(peers);
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    // thread t owns digit t: partition total and per-warp exclusive offsets
+    const int d = tid;
+    uint32_t total = 0;
+#pragma unroll
+    for (int w = 0; w < RS_WARPS; ++w) {
+        const uint32_t c = s_warp[w][d];
+        s_warp[w][d] = total;
+        total += c;
+    }
+    uint32_t *my = status + part * 256 + d;
+    if (part == 0) {
+        atomicExch(my, FLAG_INC | total);
+        s_base[d] = digit_base[d];
+    } else {
+        atomicExch(my, FLAG_AGG | total);
+        uint32_t excl = 0;
+        for (long long p = part - 1; p >= 0; --p) {
+            const uint32_t *q = status + p * 256 + d;
+            uint32_t s = ld_volatile(q);
+            int spins = 0;
+            while ((s & (FLAG_AGG | FLAG_INC)) == 0u) {
+                if (++spins > kSpinLimit) { atomicOr(err, 1u); s = FLAG_INC; break; }
+                __nanosleep(64);
+                s = ld_volatile(q);
+            }
+            excl += s & COUNT_MASK;
+            if (s & FLAG_INC) break;
+        }
+        atomicExch(my, FLAG_INC | (excl + total));
+        s_base[d] = digit_base[d] + excl;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < RS_ITEMS; ++it) {
+        const long long idx = base + it * 32 + lane;
+        if (idx < n) {
+            const uint32_t dg = (key[it] >> shift) & 255u;
+            const uint32_t dst = s_base[dg] + s_warp[warp][dg] + rank[it];
+            kout[dst] = key[it];
+            vout[dst] = val[it];
+        }
+    }
+}
+
+int radix_sort_pairs(uint32_t *keys, uint32_t *vals, long long n, int bits, const SortScratch &s, cudaStream_t st) {
+    if (n <= 1 || bits <= 0) return 0;
+    const int passes = (bits + 7) / 8;
+    cudaMemsetAsync(s.hist, 0, sizeof(uint32_t) * 4 * 256, st);
+    cudaMemsetAsync(s.counters, 0, sizeof(uint32_t) * 4, st);
+    const long long parts = sort_parts_for(n);
+    int hb = (int)((n + RS_THREADS * 8 - 1) / (RS_THREADS * 8));
+    if (hb > 152 * 8) hb = 152 * 8;
+    k_rs_hist<<<hb, RS_THREADS, 0, st>>>(keys, n, passes, s.hist);
+    k_rs_hist_scan<<<passes, 256, 0, st>>>(s.hist);
+    uint32_t *ki = keys, *vi = vals, *ko = s.keys_alt, *vo = s.vals_alt;
+    for (int p = 0; p < passes; ++p) {
+        cudaMemsetAsync(s.status, 0, sizeof(uint32_t) * 256 * parts, st);
+        k_rs_pass<<<(unsigned)parts, RS_THREADS, 0, st>>>(ki, vi, ko, vo, n, 8 * p, s.hist + 256 * p, s.status,
+                                                          s.counters + p, s.err);
+        uint32_t *t;
+        t = ki; ki = ko; ko = t;
+        t = vi; vi = vo; vo = t;
+    }
+    if (passes & 1) {  // result sits in the alternate buffers
+        cudaMemcpyAsync(keys, ki, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(vals, vi, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st);
+    }
+    return passes;
+}
+
+// ---------------------------------------------------------------- exclusive scan (reduce, scan partials, downsweep)
+constexpr int SC_THREADS = 256;
+constexpr int SC_ITEMS = 16;
+constexpr int SC_TILE = SC_THREADS * SC_ITEMS;
+
+long long scan_scratch_words(long long n) { return (n + SC_TILE - 1) / SC_TILE + 1; }
+
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *s_warp, uint32_t *total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < SC_THREADS / 32 ? s_warp[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < SC_THREADS / 32) s_warp[lane] = w;  // inclusive per warp
+    }
+    __syncthreads();
+    const uint32_t warp_excl = warp == 0 ? 0u : s_warp[warp - 1];
+    *total = s_warp[SC_THREADS / 32 - 1];
+    __syncthreads();
+    return warp_excl + x - v;
+}
+
+__global__ void __launch_bounds__(SC_THREADS) k_scan_reduce(const uint32_t *__restrict__ in, long long n,
+                                                            uint32_t *__restrict__ partial) {
+    __shared__ uint32_t s_warp[SC_THREADS / 32];
+    const long long base = blockIdx.x * (long long)SC_TILE;
+    uint32_t sum = 0;
+#pragma unroll
+    for (int i = 0; i < SC_ITEMS; ++i) {
+        const long long idx = base + i * SC_THREADS + threadIdx.x;
+        if (idx < n) sum += in[idx];
+    }
+    uint32_t tot;
+    block_excl_scan(sum, s_warp, &tot);
+    if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(SC_THREADS) k_scan_partials(uint32_t *partial, long long nb, uint32_t *total) {
+    __shared__ uint32_t s_warp[SC_THREADS / 32];
+    uint32_t carry = 0;
+    for (long long b0 = 0; b0 < nb; b0 += SC_THREADS) {
+        const long long b = b0 + threadIdx.x;
+        const uint32_t v = b < nb ? partial[b] : 0u;
+        uint32_t tot;
+        const uint32_t ex = block_excl_scan(v, s_warp, &tot);
+        if (b < nb) partial[b] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void __launch_bounds__(SC_THREADS) k_scan_down(const uint32_t *__restrict__ in, long long n,
+                                                          const uint32_t *__restrict__ partial, uint32_t *__restrict__ out) {
+    __shared__ uint32_t s_warp[SC_THREADS / 32];
+    const long long base = blockIdx.x * (long long)SC_TILE + (long long)threadIdx.x * SC_ITEMS;  // blocked per thread
+    uint32_t v[SC_ITEMS];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int i = 0; i < SC_ITEMS; ++i) {
+        const long long idx = base + i;
+        v[i] = idx < n ? in[idx] : 0u;
+        sum += v[i];
+    }
+    uint32_t tot;
+    uint32_t run = partial[blockIdx.x] + block_excl_scan(sum, s_warp, &tot);
+#pragma unroll
+    for (int i = 0; i < SC_ITEMS; ++i) {
+        const long long idx = base + i;
+        if (idx < n) out[idx] = run;
+        run += v[i];
+    }
+}
+
+void exclusive_scan_u32(const uint32_t *in, uint32_t *out, long long n, uint32_t *total, uint32_t *scratch,
+                        cudaStream_t st) {
+    if (n == 0) {
+        cudaMemsetAsync(total, 0, sizeof(uint32_t), st);
+        return;
+    }
+    const long long nb = (n + SC_TILE - 1) / SC_TILE;
+    k_scan_reduce<<<(unsigned)nb, SC_THREADS, 0, st>>>(in, n, scratch);
+    k_scan_partials<<<1, SC_THREADS, 0, st>>>(scratch, nb, total);
+    k_scan_down<<<(unsigned)nb, SC_THREADS, 0, st>>>(in, n, scratch, out);
+}
+
+}  // namespace dgs

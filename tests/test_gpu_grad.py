@@ -1,0 +1,154 @@
+"""Adjoint parity: GPU FP32 render_backward vs the FP64 oracle adjoint.
+
+Tolerance per parameter group: ||g_gpu - g_ref|| / ||g_ref|| <= 1e-3 and per
+element |g_gpu - g_ref| <= 1e-3 max|g_ref| + 1e-6.  Both sides hold the
+forward's discrete choices fixed (the oracle uses the GPU's validated
+per-pixel cell counts).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2508_03180_gb300 import synth
+from tests.gpu_helpers import read_state, view_slices
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-3
+
+
+@pytest.fixture(scope="module")
+def rctx():
+    from paper_2508_03180_gb300.renderer import Context
+    c = Context()
+    yield c
+    c.close()
+
+
+def assert_close_group(name, got, ref):
+    got = np.asarray(got, np.float64).reshape(ref.shape)
+    scale = np.abs(ref).max()
+    err = np.abs(got - ref)
+    rel = np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-30)
+    assert rel <= REL, f"{name}: relative norm error {rel:.3e}"
+    assert err.max() <= REL * scale + 1e-6, f"{name}: max element error {err.max():.3e} (scale {scale:.3e})"
+    return rel
+
+
+def _grads(rctx, scene, cams, seed=0):
+    G, N, C = scene.G, scene.N, (scene.sh_degree + 1) ** 2
+    sid = rctx.upload_scene(scene)
+    flat, state, _ = rctx.render(sid, cams, want_state=True)
+    dl = torch.randn(flat.numel(), generator=torch.Generator().manual_seed(seed)).cuda()
+    gr = dict(g_mean=torch.zeros(G, 3, device="cuda"), g_scale=torch.zeros(G, 3, device="cuda"),
+              g_log_scale=torch.zeros(G, 3, device="cuda"), g_quat=torch.zeros(G, 4, device="cuda"),
+              g_logit=torch.zeros(G, device="cuda"), g_sh=torch.zeros(G, C, 3, device="cuda"),
+              g_cell_v=torch.zeros(N, device="cuda"))
+    rctx.backward(state, dl, gr)
+    torch.cuda.synchronize()
+    from paper_2508_03180_gb300 import _lib as L
+    gs = read_state(rctx, state, scene, cams)
+    g2d = rctx.read(state, L.DGS_BUF_GRAD2D, np.float32, (len(cams), G, 12))
+    rctx.release_state(state)
+    rctx.release_scene(sid)
+    return flat, dl.cpu().numpy(), gr, gs, g2d
+
+
+def _oracle_grads(scene, cams, dl_flat, gs):
+    tot = None
+    per_view = []
+    o = 0
+    for v, cam in enumerate(cams):
+        gv = view_slices(gs, v)
+        H, W = gv["H"], gv["W"]
+        dl = dl_flat[o:o + 3 * H * W].reshape(3, H, W).astype(np.float64)
+        o += 3 * H * W
+        img, g2d, pg = oracle.render_and_grad(scene, cam.as_array(), dl, ndone=gv["nd"])
+        assert img["bad"] == 0
+        per_view.append(g2d)
+        if tot is None:
+            tot = {k: v.copy() for k, v in pg.items()}
+        else:
+            for k in tot:
+                tot[k] += pg[k]
+    return tot, per_view
+
+
+@pytest.mark.parametrize("deg", [0, 3])
+def test_parameter_gradients(rctx, deg):
+    sc = synth.make_scene(60, 4, synth._box(-0.5, 0.5), 0.15, 0.4, deg, seed=7 + deg)
+    sc.cell_v[:] = np.random.default_rng(3).uniform(0.3, 1.0, sc.N).astype(np.float32)
+    cams = synth.sphere_cameras(2, 3.0, 48, 40, seed0=5)
+    flat, dl, gr, gs, g2d = _grads(rctx, sc, cams)
+    ref, per_view = _oracle_grads(sc, cams, dl, gs)
+    # screen-space gradients per view
+    for v in range(len(cams)):
+        r = per_view[v]
+        live = np.abs(r["opac"]) > 0
+        assert_close_group(f"v{v} dmu2", g2d[v][:, 0:2], r["mu2"])
+        assert_close_group(f"v{v} dconic", g2d[v][:, 2:5], r["conic"])
+        assert_close_group(f"v{v} dopacity", g2d[v][:, 5], r["opac"])
+        assert_close_group(f"v{v} drgb", g2d[v][:, 6:9], r["rgb"])
+        assert live.sum() > 20
+    assert_close_group("mean", gr["g_mean"].cpu(), ref["mean"])
+    assert_close_group("scale", gr["g_scale"].cpu(), ref["scale"])
+    assert_close_group("log_scale", gr["g_log_scale"].cpu(), ref["log_scale"])
+    assert_close_group("quat", gr["g_quat"].cpu(), ref["quat"])
+    assert_close_group("logit", gr["g_logit"].cpu(), ref["logit"])
+    assert_close_group("sh", gr["g_sh"].cpu(), ref["sh"])
+    assert_close_group("cell_v", gr["g_cell_v"].cpu(), ref["cell_v"])
+
+
+def test_gradients_small_scene_1080p_batch4(rctx):
+    """2,048 cells x 8 Gaussians (SH degree 3) at 1920x1080, four views."""
+    sc = synth.scene_small(sh_degree=3)
+    cams = synth.sphere_cameras(4, 3.0, 1920, 1080, seed0=40)
+    flat, dl, gr, gs, g2d = _grads(rctx, sc, cams, seed=1)
+    ref, _ = _oracle_grads(sc, cams, dl, gs)
+    for k_gpu, k_ref in (("g_mean", "mean"), ("g_log_scale", "log_scale"), ("g_quat", "quat"),
+                         ("g_logit", "logit"), ("g_sh", "sh")):
+        assert_close_group(k_ref, gr[k_gpu].cpu(), ref[k_ref])
+
+
+def test_second_backward_on_same_state(rctx):
+    sc = synth.scene_small(n_cells=200)
+    sid = rctx.upload_scene(sc)
+    cams = [synth.small_camera(64, 64)]
+    flat, state, _ = rctx.render(sid, cams, want_state=True)
+    dl = torch.randn(flat.numel(), generator=torch.Generator().manual_seed(4)).cuda()
+    outs = []
+    for _ in range(2):
+        g = dict(g_mean=torch.zeros(sc.G, 3, device="cuda"))
+        rctx.backward(state, dl, g)
+        outs.append(g["g_mean"])
+    torch.cuda.synchronize()
+    rel = (outs[0] - outs[1]).norm() / outs[0].norm()
+    assert rel < 1e-5
+    rctx.release_state(state)
+    rctx.release_scene(sid)
+
+
+def test_autograd_function_matches_direct_backward(rctx):
+    from paper_2508_03180_gb300 import autograd
+    sc = synth.scene_small(n_cells=300, sh_degree=1)
+    sid = rctx.upload_scene(sc)
+    cams = [synth.small_camera(64, 48)]
+    t = lambda a: torch.tensor(a, device="cuda", requires_grad=True)
+    mean, scale, quat, logit, sh = t(sc.g_mean), t(sc.g_scale), t(sc.g_quat), t(sc.g_logit), t(sc.g_sh)
+    img = autograd.render(rctx, sid, sc.N, sc.K, sc.sh_degree, cams, mean, scale, quat, logit, sh)
+    target = torch.rand(img.shape, generator=torch.Generator().manual_seed(0)).cuda()
+    loss = (img - target).abs().mean()
+    loss.backward()
+    torch.cuda.synchronize()
+    # direct path with the same dL/dimage
+    flat, state, _ = rctx.render(sid, cams, want_state=True)
+    assert torch.equal(flat, img.detach())
+    dl = torch.sign(flat - target) / flat.numel()
+    g = dict(g_mean=torch.zeros(sc.G, 3, device="cuda"), g_scale=torch.zeros(sc.G, 3, device="cuda"))
+    rctx.backward(state, dl, g)
+    torch.cuda.synchronize()
+    assert (mean.grad - g["g_mean"]).norm() <= 1e-5 * g["g_mean"].norm()
+    assert (scale.grad - g["g_scale"]).norm() <= 1e-5 * g["g_scale"].norm()
+    rctx.release_state(state)
+    rctx.release_scene(sid)

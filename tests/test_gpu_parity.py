@@ -1,0 +1,209 @@
+"""Parity of the sm_103a path (through the C ABI) against the CPU oracle.
+
+* binning (cell rectangles, depths, per-tile ordered cell lists, ranges): bit-exact
+* per-Gaussian AABB inputs (mu2, half extents): bit-exact; conic, opacity,
+  colour: within FP32 rounding of the FP64 projection
+* images: 1e-4 max abs per channel against the FP64 oracle, which renders
+  with the GPU's per-pixel processed-cell counts after checking that each is
+  a valid outcome of the stopping rule (relative slack 1e-3 on T); the
+  oracle's own counts may differ on at most 0.01% of pixels
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2508_03180_gb300 import synth
+from tests.gpu_helpers import LOG2E, gpu_render, read_state, tile_lists_equal, view_slices
+
+pytestmark = pytest.mark.gpu
+
+IMG_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def rctx():
+    from paper_2508_03180_gb300.renderer import Context
+    c = Context()
+    yield c
+    c.close()
+
+
+def check_view(scene, cam_obj, gv, cells_all, img, check_image=True, tile_rows=None):
+    cam = cam_obj.as_array()
+    rect, depth = oracle.cell_rects(scene, cam)
+    assert np.array_equal(gv["rect"], rect), "cell rectangles differ"
+    vis = rect[:, 0] >= 0
+    assert np.array_equal(gv["depth"][vis].view(np.uint32), depth[vis].view(np.uint32)), "cell depths differ"
+    ocells, orng = oracle.tile_lists(rect, depth, cam)
+    assert tile_lists_equal(gv, cells_all, ocells, orng) == 0, "tile lists differ"
+    # AABB inputs: bit-exact for Gaussians of visible cells
+    mu2f, extf, valid = oracle.gauss_decisions(scene, cam)
+    gvis = np.repeat(vis, scene.K)
+    rec = gv["rec"]
+    ok = gvis & (valid != 0)
+    assert np.array_equal(rec[ok, 0:2].view(np.uint32), mu2f[ok].view(np.uint32)), "projected means differ"
+    assert np.array_equal(rec[ok, 2:4].view(np.uint32), extf[ok].view(np.uint32)), "AABB extents differ"
+    assert np.all(rec[gvis & (valid == 0), 2] < 0), "invalid Gaussians must never pass the AABB test"
+    if not check_image:
+        return None
+    pv = oracle.prepare_view(scene, cam, tile_rows=tile_rows)
+    pr = pv["proj"]
+    # conic / opacity / colour of the records vs FP64
+    conic = np.stack([rec[:, 4] / (-0.5 * LOG2E), rec[:, 5] / (-LOG2E), rec[:, 6] / (-0.5 * LOG2E)], 1)
+    m = pv["mask"]
+    np.testing.assert_allclose(conic[m], pr["conic"][m], rtol=2e-4, atol=1e-6 * np.abs(pr["conic"][m]).max())
+    np.testing.assert_allclose(rec[m, 7], pr["opac"][m], rtol=1e-5, atol=1e-7)
+    np.testing.assert_allclose(rec[m, 8:11], pr["rgb"][m], rtol=1e-4, atol=2e-5)
+    r = oracle.render_view(scene, cam, forced_ndone=gv["nd"], pv=pv)
+    H, W = gv["H"], gv["W"]
+    ty0, ty1 = pv["rows"]
+    y0, y1 = ty0 * 16, min(ty1 * 16, H)
+    window = slice(y0, y1)
+    n_px = (y1 - y0) * W
+    assert r["bad"] <= 0, f"{r['bad']} GPU termination counts are not valid outcomes"
+    diff_own = int((r["ndone"][window] != gv["nd"][window]).sum())
+    assert diff_own <= max(1, int(1e-4 * n_px)), f"{diff_own} pixels stop at a different cell"
+    err = np.abs(img.reshape(3, H, W)[:, window] - r["C"][:, window]).max()
+    assert err <= IMG_TOL, f"image max abs error {err}"
+    np.testing.assert_allclose(gv["D"][window], r["D"][window], rtol=1e-4, atol=1e-7)
+    return dict(err=float(err), diff_own=diff_own, hit=float((r["D"][window] > 1e-10).mean()))
+
+
+def _render_and_check(rctx, scene, cams, tile_rows=None):
+    sid = rctx.upload_scene(scene)
+    try:
+        flat, state, st = gpu_render(rctx, sid, cams)
+        gs = read_state(rctx, state, scene, cams)
+        imgs = rctx.split(flat, cams)
+        res = []
+        for v, cam in enumerate(cams):
+            gv = view_slices(gs, v)
+            res.append(check_view(scene, cam, gv, gs["cells"], imgs[v].cpu().numpy(), tile_rows=tile_rows))
+        # sort length reported = sum over views of the oracle's
+        assert st.sort_length == sum(oracle.sort_length(scene, c.as_array()) for c in cams)
+        rctx.release_state(state)
+        return res
+    finally:
+        rctx.release_scene(sid)
+
+
+def test_small_scene_256(rctx):
+    """2,048 cells x 8 Gaussians, 256x256, one view."""
+    res = _render_and_check(rctx, synth.scene_small(), [synth.small_camera()])
+    assert res[0]["hit"] > 0.5
+
+
+def test_small_scene_sh3_batch_of_views(rctx):
+    sc = synth.scene_small(sh_degree=3)
+    cams = synth.sphere_cameras(4, 3.0, 200, 136, seed0=10)
+    _render_and_check(rctx, sc, cams)
+
+
+def test_mixed_resolutions_one_chain(rctx):
+    sc = synth.make_scene(500, 5, synth._box(-1, 1), 0.03, 0.3, 2, seed=3)
+    base = synth.sphere_cameras(3, 3.5, 64, 64, seed0=20)
+    cams = [base[0].with_resolution(97, 45), base[1].with_resolution(16, 16), base[2].with_resolution(130, 211)]
+    _render_and_check(rctx, sc, cams)
+
+
+@pytest.mark.parametrize("K", [1, 3, 10, 32])
+def test_gaussians_per_cell(rctx, K):
+    sc = synth.make_scene(max(8, 600 // K), K, synth._box(-1, 1), 0.05, 0.3, 1, seed=K)
+    _render_and_check(rctx, sc, [synth.small_camera(80, 72)])
+
+
+def test_multiscale_subset_480x270(rctx):
+    sc = synth.scene_multiscale(n_cells=20_000, K=10)
+    _render_and_check(rctx, sc, synth.sphere_cameras(2, 15.0, 480, 270))
+
+
+def test_ragged_and_tiny_images(rctx):
+    sc = synth.scene_small(n_cells=300)
+    cams = [synth.small_camera(1, 1), synth.small_camera(17, 33), synth.small_camera(31, 15)]
+    _render_and_check(rctx, sc, cams)
+
+
+def test_empty_scene_renders_background(rctx):
+    sc = synth.scene_small(n_cells=0)
+    sid = rctx.upload_scene(sc)
+    flat, _, st = rctx.render(sid, [synth.small_camera(40, 24)], stats=True)
+    torch.cuda.synchronize()
+    assert st.sort_length == 0 and torch.all(flat == 0)
+    rctx.release_scene(sid)
+
+
+def test_all_cells_culled(rctx):
+    sc = synth.scene_small(n_cells=500)
+    cam = synth.look_at((0, -3, 0), (0, -6, 0), 64, 64)  # looking away from the scene
+    sid = rctx.upload_scene(sc)
+    flat, _, st = rctx.render(sid, [cam], stats=True)
+    torch.cuda.synchronize()
+    assert st.sort_length == 0 and st.visible_cells == 0 and torch.all(flat == 0)
+    rctx.release_scene(sid)
+
+
+def test_one_cell_covering_the_screen(rctx):
+    sc = synth.make_scene(1, 16, lambda rng, n: np.zeros((n, 3)), 1.0, 1.2, 0, seed=1)
+    _render_and_check(rctx, sc, [synth.small_camera(100, 60)])
+
+
+def test_termination_halving_stack(rctx):
+    from tests.test_oracle_blend import _halving_stack
+    sc, _ = _halving_stack(20)
+    res = _render_and_check(rctx, sc, [synth.small_camera(9, 9)])
+    assert res[0]["err"] <= IMG_TOL
+
+
+def test_render_is_deterministic(rctx):
+    sc = synth.scene_small(sh_degree=3)
+    sid = rctx.upload_scene(sc)
+    cams = synth.sphere_cameras(2, 3.0, 128, 128)
+    a, _, _ = rctx.render(sid, cams)
+    b, _, _ = rctx.render(sid, cams)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    rctx.release_scene(sid)
+
+
+def test_host_output_matches_device_output(rctx):
+    sc = synth.scene_small()
+    sid = rctx.upload_scene(sc)
+    cams = [synth.small_camera(64, 48)]
+    a, _, _ = rctx.render(sid, cams)
+    h = np.zeros(3 * 64 * 48, np.float32)
+    rctx.render_host(sid, cams, h)
+    torch.cuda.synchronize()
+    assert np.array_equal(a.cpu().numpy(), h)
+    rctx.release_scene(sid)
+
+
+@pytest.mark.parametrize("n,bits", [(0, 8), (1, 32), (4096, 32), (4097, 13), (1_000_003, 32), (300_001, 17)])
+def test_radix_sort_pairs_stable(rctx, n, bits):
+    g = torch.Generator().manual_seed(n + bits)
+    keys = torch.randint(0, 2 ** 31, (n,), generator=g, dtype=torch.int64)
+    if n > 10:
+        keys[: n // 3] = keys[0]  # many equal keys: stability matters
+    keys = (keys & ((1 << bits) - 1)).to(torch.int64)
+    k32 = keys.to(torch.int32)  # values < 2^31 when bits <= 31, else reinterpret
+    vals = torch.arange(n, dtype=torch.int32)
+    kd, vd = k32.cuda(), vals.cuda()
+    rctx.sort_pairs(kd, vd, bits)
+    torch.cuda.synchronize()
+    order = np.argsort(keys.numpy().astype(np.uint64), kind="stable")
+    assert np.array_equal(vd.cpu().numpy(), order.astype(np.int32))
+    assert np.array_equal(kd.cpu().numpy(), k32.numpy()[order])
+
+
+def test_loss_l1_matches_definition(rctx):
+    g = torch.Generator().manual_seed(0)
+    a = torch.rand(1_000_003, generator=g).cuda()
+    b = torch.rand(1_000_003, generator=g).cuda()
+    b[:10] = a[:10]
+    dl = torch.empty_like(a)
+    loss = torch.empty(1, device="cuda")
+    rctx.loss_l1(a, b, dl, loss)
+    torch.cuda.synchronize()
+    ref = (a.double() - b.double()).abs().mean().item()
+    assert abs(loss.item() - ref) <= 1e-6 * ref
+    assert torch.equal(dl, torch.sign(a - b) / a.numel())
