@@ -264,14 +264,14 @@ static dgs_status fill_scene(dgs_ctx *ctx, Scene &sc, const dgs_scene_desc *d, c
     return DGS_OK;
 }
 
-static dgs_status check_desc(const dgs_scene_desc *d) {
+static dgs_status check_desc(const dgs_scene_desc *d, bool need_cells = true) {
     if (!d) return set_error(DGS_ERR_INVALID_ARG, "scene desc is NULL");
     if (d->num_cells < 0 || d->K < 1 || d->K > kMaxK || d->sh_degree < 0 || d->sh_degree > 3)
         return set_error(DGS_ERR_INVALID_ARG, "need num_cells >= 0, 1 <= K <= 32, 0 <= sh_degree <= 3");
     if (d->location != DGS_HOST && d->location != DGS_DEVICE) return set_error(DGS_ERR_INVALID_ARG, "bad location");
     if (d->num_cells * (int64_t)d->K >= (1LL << 31)) return set_error(DGS_ERR_CAPACITY, "more than 2^31 Gaussians");
-    if (d->num_cells > 0 && (!d->cell_center || !d->cell_axes || !d->cell_quat || !d->g_mean || !d->g_scale ||
-                             !d->g_quat || !d->g_logit || !d->g_sh))
+    if (d->num_cells > 0 && ((need_cells && (!d->cell_center || !d->cell_axes || !d->cell_quat)) || !d->g_mean ||
+                             !d->g_scale || !d->g_quat || !d->g_logit || !d->g_sh))
         return set_error(DGS_ERR_INVALID_ARG, "a scene array is NULL");
     return DGS_OK;
 }
@@ -302,7 +302,7 @@ extern "C" dgs_status dgs_scene_upload(dgs_ctx *ctx, const dgs_scene_desc *d, ui
 
 extern "C" dgs_status dgs_scene_update(dgs_ctx *ctx, uint32_t scene_id, const dgs_scene_desc *d, dgs_stream stream) {
     if (!ctx) return set_error(DGS_ERR_INVALID_ARG, "NULL ctx");
-    dgs_status s = check_desc(d);
+    dgs_status s = check_desc(d, false);
     if (s) return s;
     std::lock_guard<std::mutex> lk(ctx->mu);
     CK(cudaSetDevice(ctx->cfg.device));

@@ -52,7 +52,10 @@ def check_view(scene, cam_obj, gv, cells_all, img, check_image=True, tile_rows=N
     # conic / opacity / colour of the records vs FP64
     conic = np.stack([rec[:, 4] / (-0.5 * LOG2E), rec[:, 5] / (-LOG2E), rec[:, 6] / (-0.5 * LOG2E)], 1)
     m = pv["mask"]
-    np.testing.assert_allclose(conic[m], pr["conic"][m], rtol=2e-4, atol=1e-6 * np.abs(pr["conic"][m]).max())
+    # each entry within 2e-4 of the conic's own scale (FP32 cancellation in the
+    # off-diagonal of strongly correlated Gaussians is relative to the matrix)
+    scale = np.maximum(np.abs(pr["conic"][m][:, 0]), np.abs(pr["conic"][m][:, 2]))[:, None]
+    assert np.all(np.abs(conic[m] - pr["conic"][m]) <= 2e-4 * scale), "conic differs"
     np.testing.assert_allclose(rec[m, 7], pr["opac"][m], rtol=1e-5, atol=1e-7)
     np.testing.assert_allclose(rec[m, 8:11], pr["rgb"][m], rtol=1e-4, atol=2e-5)
     r = oracle.render_view(scene, cam, forced_ndone=gv["nd"], pv=pv)
@@ -72,6 +75,7 @@ def check_view(scene, cam_obj, gv, cells_all, img, check_image=True, tile_rows=N
 
 def _render_and_check(rctx, scene, cams, tile_rows=None):
     sid = rctx.upload_scene(scene)
+    state = None
     try:
         flat, state, st = gpu_render(rctx, sid, cams)
         gs = read_state(rctx, state, scene, cams)
@@ -82,9 +86,10 @@ def _render_and_check(rctx, scene, cams, tile_rows=None):
             res.append(check_view(scene, cam, gv, gs["cells"], imgs[v].cpu().numpy(), tile_rows=tile_rows))
         # sort length reported = sum over views of the oracle's
         assert st.sort_length == sum(oracle.sort_length(scene, c.as_array()) for c in cams)
-        rctx.release_state(state)
         return res
     finally:
+        if state is not None:
+            rctx.release_state(state)
         rctx.release_scene(sid)
 
 

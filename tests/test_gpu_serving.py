@@ -72,8 +72,10 @@ def test_admission_respects_budget(scenes):
 
 def test_poll_timeout_and_errors(scenes):
     from paper_2508_03180_gb300 import _lib as L
-    c = _ctx()
-    sid = c.upload_scene(scenes[0])
+    # a budget below one request: one chain in flight, one view per chain, so
+    # a burst of 4K renders of a 2M-Gaussian scene must back up the queue
+    c = _ctx(hbm_budget_bytes=1)
+    sid = c.upload_scene(synth.scene_small(seed=3, n_cells=250_000))
     with pytest.raises(L.DgsError):
         c.submit(sid, synth.small_camera(), torch.zeros(3 * 256 * 256, device="cuda"))  # serving not started
     c.serve_start(max_batch=2, queue_cap=2)
