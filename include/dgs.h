@@ -239,6 +239,27 @@ typedef struct {
 dgs_status dgs_profile_enable(dgs_ctx *ctx, int32_t on);
 dgs_status dgs_profile_read(dgs_ctx *ctx, dgs_profile *out);
 
+/* The radix sort above for callers that cannot allocate device memory: for
+ * example a process whose caching allocator already holds the device's free
+ * memory for its own pool, or a real-time loop that forbids allocation after
+ * start-up because cudaMalloc/cudaFree can block and synchronise the device.
+ * The paper has no counterpart; it is a service of this library.
+ * Same contract as dgs_sort_pairs (stable, low `bits` bits of the uint32 key,
+ * keys/vals device pointers sorted in place, no context needed), except:
+ *   * n is at most 1,048,576; a larger n returns DGS_ERR_CAPACITY before any
+ *     work is enqueued.
+ *   * Scratch is a fixed file-scope device array (about 8.3 MB) that every
+ *     GPU loading this library holds until the process exits; this call
+ *     calls no cudaMalloc, cudaFree or other allocating routine.
+ *   * The first call on a device looks up that array's device address
+ *     (cudaGetSymbolAddress) with the device current; make that first call
+ *     before any stream capture.
+ *   * All calls share the array: calls whose work overlaps on the GPU (other
+ *     streams, other threads) race and corrupt each other's results.
+ *   * Uses the current CUDA device, enqueues on `stream` and synchronises it
+ *     once at the end (to read the sort's error flag). */
+dgs_status dgs_sort_pairs_noalloc(uint32_t *keys, uint32_t *vals, int64_t n, int32_t bits, dgs_stream stream);
+
 /* ---------------------------------------------------------------- serving */
 
 /* Continuous-batching request loop (not in the paper; serving workload).

@@ -102,6 +102,7 @@ _SIGS = {
     "dgs_loss_l1": (C.c_int32, [_P, _P, _P, C.c_int64, _P, _P, _P]),
     "dgs_state_read": (C.c_int32, [_P, _P, C.c_int32, _P, C.c_int64, C.POINTER(C.c_int64)]),
     "dgs_sort_pairs": (C.c_int32, [_P, _P, _P, C.c_int64, C.c_int32, _P]),
+    "dgs_sort_pairs_noalloc": (C.c_int32, [_P, _P, C.c_int64, C.c_int32, _P]),
     "dgs_state_counts": (C.c_int32, [_P, _P, C.POINTER(dgs_counts)]),
     "dgs_profile_enable": (C.c_int32, [_P, C.c_int32]),
     "dgs_profile_read": (C.c_int32, [_P, C.POINTER(dgs_profile)]),
@@ -223,6 +224,11 @@ def dgs_state_read(ctx, state, what: int, dst_ptr: int | None, nbytes: int) -> i
 
 def dgs_sort_pairs(ctx, keys_ptr: int, vals_ptr: int, n: int, bits: int, stream: int = 0):
     check(load().dgs_sort_pairs(ctx, _P(keys_ptr), _P(vals_ptr), n, bits, _P(stream)), ctx)
+
+
+def dgs_sort_pairs_noalloc(keys_ptr: int, vals_ptr: int, n: int, bits: int, stream: int = 0):
+    """Sort without allocating (fixed scratch, n <= 1,048,576)."""
+    check(load().dgs_sort_pairs_noalloc(_P(keys_ptr), _P(vals_ptr), n, bits, _P(stream)))
 
 
 def dgs_state_counts(ctx, state) -> dgs_counts:

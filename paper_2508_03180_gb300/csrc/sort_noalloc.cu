@@ -1,0 +1,93 @@
+// dgs_sort_pairs_noalloc: the library's stable radix sort for callers that
+// must not allocate device memory -- for example a process whose caching
+// allocator has already reserved the device's free memory for its own pool,
+// or a real-time loop that forbids allocation after start-up because
+// cudaMalloc/cudaFree can block and synchronise the whole device.  Its scratch
+// (alternate key/value buffers, digit histograms, look-back status words,
+// partition counters, error flag) is one file-scope device array below, so
+// the call itself allocates nothing; the array is part of the loaded module
+// and every GPU that loads the library holds it until the process exits.
+#include <cuda_runtime.h>
+
+#include <mutex>
+#include <string>
+
+#include "internal.cuh"
+#include "runtime.h"
+
+namespace {
+
+constexpr long long kMaxItems = 1LL << 20;                // 1,048,576 pairs per call at most
+constexpr long long kMaxParts = (kMaxItems + 4095) / 4096; // sort partitions of 4096 items
+// layout of the scratch array, in 32-bit words
+constexpr size_t kOffKeys = 0;
+constexpr size_t kOffVals = kOffKeys + kMaxItems;
+constexpr size_t kOffHist = kOffVals + kMaxItems;          // 4 passes x 256 digits
+constexpr size_t kOffStatus = kOffHist + 4 * 256;          // kMaxParts x 256 look-back words
+constexpr size_t kOffCounters = kOffStatus + kMaxParts * 256;
+constexpr size_t kOffErr = kOffCounters + 4;
+constexpr size_t kWords = kOffErr + 60;                    // about 8.3 MB in total
+
+// Device-side scratch.  In host code this name is only a stand-in: its
+// device address comes from cudaGetSymbolAddress, per device.
+static __device__ __align__(256) uint32_t g_sort_scratch[kWords];
+
+std::mutex g_addr_mu;
+constexpr int kMaxDevices = 64;
+uint32_t *g_addr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device; looked up once
+// per device (the first call on a device does this set-up).
+dgs_status scratch_address(int dev, uint32_t **out) {
+    std::lock_guard<std::mutex> lk(g_addr_mu);
+    if (!g_addr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_sort_scratch);
+        if (e != cudaSuccess) return dgs::cuda_error(e, "cudaGetSymbolAddress of the sort scratch");
+        g_addr[dev] = static_cast<uint32_t *>(p);
+    }
+    *out = g_addr[dev];
+    return DGS_OK;
+}
+
+}  // namespace
+
+extern "C" dgs_status dgs_sort_pairs_noalloc(uint32_t *keys, uint32_t *vals, int64_t n, int32_t bits,
+                                            dgs_stream stream) {
+    if (n < 0 || bits < 0 || bits > 32 || (n > 0 && (!keys || !vals)))
+        return dgs::set_error(DGS_ERR_INVALID_ARG, "dgs_sort_pairs_noalloc: bad argument");
+    if (n > kMaxItems)
+        return dgs::set_error(DGS_ERR_CAPACITY, "dgs_sort_pairs_noalloc: n = " + std::to_string(n) +
+                                                    " exceeds the fixed maximum of 1048576 pairs");
+    if (n <= 1 || bits == 0) return DGS_OK;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return dgs::cuda_error(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return dgs::set_error(DGS_ERR_INVALID_ARG, "device ordinal out of range");
+    uint32_t *base = nullptr;
+    dgs_status s = scratch_address(dev, &base);
+    if (s) return s;
+    dgs::SortScratch sc;
+    sc.keys_alt = base + kOffKeys;
+    sc.vals_alt = base + kOffVals;
+    sc.hist = base + kOffHist;
+    sc.status = base + kOffStatus;
+    sc.counters = base + kOffCounters;
+    sc.err = base + kOffErr;
+    sc.cap_items = kMaxItems;
+    sc.cap_parts = kMaxParts;
+    cudaStream_t st = (cudaStream_t)stream;
+    // the array keeps the previous call's contents: the error flag starts at
+    // zero here; histograms, counters and look-back words are cleared by the
+    // sort itself before each use
+    if ((e = cudaMemsetAsync(sc.err, 0, sizeof(uint32_t), st)) != cudaSuccess)
+        return dgs::cuda_error(e, "clearing the sort error flag");
+    dgs::radix_sort_pairs(keys, vals, n, bits, sc, st);
+    if ((e = cudaGetLastError()) != cudaSuccess) return dgs::cuda_error(e, "radix sort launch");
+    uint32_t flag = 0;
+    if ((e = cudaMemcpyAsync(&flag, sc.err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return dgs::cuda_error(e, "dgs_sort_pairs_noalloc");
+    if (flag) return dgs::set_error(DGS_ERR_TIMEOUT, "radix sort look-back wait gave up");
+    return DGS_OK;
+}
