@@ -133,9 +133,9 @@ def max_over_ranks(x, world):
     return float(t.item())
 
 
-def cameras_for(rank):
+def cameras_for(rank, n_views=N_VIEWS):
     from paper_2508_03180_gb300 import synth
-    return synth.sphere_cameras(N_VIEWS, 15.0, W_IMG, H_IMG, seed0=N_VIEWS * rank)
+    return synth.sphere_cameras(n_views, 15.0, W_IMG, H_IMG, seed0=N_VIEWS * rank)
 
 
 def cpu_sample(scene, cam, rows, threads_note=True):
@@ -242,6 +242,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--views", type=int, default=N_VIEWS, help="views per step (profiling of smaller cases)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -255,11 +257,12 @@ def main():
     rctx = Context(device=local)
     scene = synth.scene_multiscale()
     sid = rctx.upload_scene(scene)
-    cams = cameras_for(rank)
+    nv = args.views
+    cams = cameras_for(rank, nv)
     slots = rctx.set_cameras(cams)
     G, N, C = scene.G, scene.N, 16
-    target = torch.from_numpy(synth.target_image(N_VIEWS, H_IMG, W_IMG, seed=100 + rank)).cuda().reshape(-1)
-    img = torch.empty(N_VIEWS * 3 * H_IMG * W_IMG, device="cuda")
+    target = torch.from_numpy(synth.target_image(nv, H_IMG, W_IMG, seed=100 + rank)).cuda().reshape(-1)
+    img = torch.empty(nv * 3 * H_IMG * W_IMG, device="cuda")
     dl = torch.empty_like(img)
     loss = torch.empty(1, device="cuda")
     grads = dict(g_mean=torch.empty(G, 3, device="cuda"), g_log_scale=torch.empty(G, 3, device="cuda"),
@@ -300,7 +303,7 @@ def main():
     rctx.profile_enable(False)
     ms = e0.elapsed_time(e1)
     ms = max_over_ranks(ms, world)
-    px_step = N_VIEWS * W_IMG * H_IMG
+    px_step = nv * W_IMG * H_IMG
     value = world * px_step * args.steps / (ms / 1e3) / 1e6
 
     # dominant kernel and its roofline
@@ -317,7 +320,7 @@ def main():
                 "traffic": None, "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x max SM clock",
                 "flop_per_launch": flop}
     else:
-        nbytes = {"project_fwd": G * (59 * 4) + N_VIEWS * G * 48, "project_bwd": G * (59 * 4) * 2 + N_VIEWS * G * 96}
+        nbytes = {"project_fwd": G * (59 * 4) + nv * G * 48, "project_bwd": G * (59 * 4) * 2 + nv * G * 96}
         b = nbytes.get(dom, 0)
         ach = b / (stage_ms[dom] / 1e3) / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -351,25 +354,29 @@ def main():
         hloss.copy_(loss, non_blocking=True)
         rctx.release_state(state)
 
-    for _ in range(2):
-        e2e_step()
-    torch.cuda.synchronize()
-    barrier(world)
-    t0 = time.perf_counter()
-    e2 = args.steps
-    for _ in range(e2):
-        e2e_step()
-    torch.cuda.synchronize()
-    t_e2e = max_over_ranks(time.perf_counter() - t0, world)
-    e2e_value = world * px_step * e2 / t_e2e / 1e6
+    e2e_value = None
+    if not args.no_e2e:
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        e2 = args.steps
+        for _ in range(e2):
+            e2e_step()
+        torch.cuda.synchronize()
+        t_e2e = max_over_ranks(time.perf_counter() - t0, world)
+        e2e_value = world * px_step * e2 / t_e2e / 1e6
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "views_per_step": N_VIEWS, "resolution": [W_IMG, H_IMG],
+            "config": {"workload": WORKLOAD if nv == N_VIEWS else WORKLOAD.replace("8 views", f"{nv} views"),
+                       "views_per_step": nv, "resolution": [W_IMG, H_IMG],
                        "gaussians": G, "cells": N, "l2": "inputs larger than L2 (236 MB parameters, 384 MB records)",
                        "sort_length_per_step": int(stats.sort_length), "visible_cells_per_step": int(stats.visible_cells),
-                       "termination_ratio": 1.0 - cnt["inbox_rendered"] / max(1, cnt["inbox_all"])},
+                       "termination_ratio": 1.0 - cnt["inbox_rendered"] / max(1, cnt["inbox_all"]),
+                       "counts_per_step": cnt},
             "fwd_mpix_s": None,
             "stage_ms_per_step": {k: prof[k][0] / args.steps for k in prof},
             "stage_share": {k: prof[k][0] / total_stage for k in prof if total_stage > 0},
