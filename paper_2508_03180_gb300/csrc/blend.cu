@@ -40,6 +40,32 @@ __device__ __forceinline__ float4 fetch_rec(const float4 *__restrict__ vrec, con
     return keep;
 }
 
+// Can Gaussian record piece r0 = (mu_x, mu_y, ext_x, ext_y) pass the per-pixel
+// AABB test at any pixel centre of the tile whose first pixel is (x0, y0)?
+// Exactly conservative: FP32 subtraction is monotone, so if the nearest pixel
+// centre of the tile already fails |p - mu| <= ext, every pixel does.
+__device__ __forceinline__ bool touches_tile(float4 r0, float x0, float y0) {
+    const float lx = x0 + 0.5f, hx = x0 + (float)kTile - 0.5f;
+    const float ly = y0 + 0.5f, hy = y0 + (float)kTile - 0.5f;
+    return !(lx - r0.x > r0.z || r0.x - hx > r0.z || ly - r0.y > r0.w || r0.y - hy > r0.w);
+}
+
+// Rows of the tile (0..15) that can hold a pixel passing the AABB test of
+// record piece r0, packed as yl | yh << 8 (a superset with a one-row margin
+// over FP32 rounding; 0x00FF = no row, when the record misses the tile).
+// Warp w blends tile rows 2w and 2w+1 and skips the record if both lie
+// outside [yl, yh]: a warp-uniform branch that changes no pixel's result.
+__device__ __forceinline__ int row_span(float4 r0, float x0, float y0) {
+    if (!touches_tile(r0, x0, y0)) return 0x00FF;
+    const int yl = (int)fmaxf(floorf(r0.y - r0.w - 0.5f - y0) - 1.0f, 0.0f);
+    const int yh = (int)fminf(ceilf(r0.y + r0.w - 0.5f - y0) + 1.0f, (float)(kTile - 1));
+    return yl | (yh << 8);
+}
+
+__device__ __forceinline__ bool rows_hit(int span, int warp) {
+    return !(2 * warp + 1 < (span & 0xFF) || 2 * warp > (span >> 8));
+}
+
 __device__ __forceinline__ int find_view(const ViewDesc *views, int n_views, int tile) {
     int lo = 0, hi = n_views;
     while (hi - lo > 1) {
@@ -55,6 +81,7 @@ __global__ void __launch_bounds__(BT) k_blend_fwd(const ViewDesc *__restrict__ v
                                                   float *__restrict__ out_rgb, float *__restrict__ out_rgb2,
                                                   float *__restrict__ out_D, int *__restrict__ out_nd) {
     __shared__ float4 s_rec[2][BT];
+    __shared__ int s_flag[2][BT / kRecF4 + 1];  // row span of each record in this tile
     __shared__ int s_view;
     const int tid = threadIdx.x, tile = blockIdx.x;
     if (tid == 0) s_view = find_view(views, n_views, tile);
@@ -65,6 +92,7 @@ __global__ void __launch_bounds__(BT) k_blend_fwd(const ViewDesc *__restrict__ v
     const int xi = tx * kTile + (tid & (kTile - 1)), yi = ty * kTile + (tid >> 4);
     const bool inside = xi < V.W && yi < V.H;
     const float px = (float)xi + 0.5f, py = (float)yi + 0.5f;
+    const float tx0 = (float)(tx * kTile), ty0 = (float)(ty * kTile);
 
     const int K = V.K;
     const int per = kRecF4 * K;               // float4s per cell
@@ -81,8 +109,10 @@ __global__ void __launch_bounds__(BT) k_blend_fwd(const ViewDesc *__restrict__ v
     if (cur < rg.y) {
         pre = fetch_rec(vrec, cells, cur, rg.y, tid, nload, per, pre);
         s_rec[0][tid] = pre;
+        if (tid < nload && tid % kRecF4 == 0) s_flag[0][tid / kRecF4] = row_span(pre, tx0, ty0);
     }
     __syncthreads();
+    const int warp = tid >> 5;
     int buf = 0;
     while (cur < rg.y) {
         const int nc = (int)min((uint32_t)CH, rg.y - cur);
@@ -92,9 +122,11 @@ __global__ void __launch_bounds__(BT) k_blend_fwd(const ViewDesc *__restrict__ v
             for (int c = 0; c < nc; ++c) {
                 if (T < bp.eps) { done = true; break; }
                 const float4 *r = &s_rec[buf][c * per];
+                const int *fl = &s_flag[buf][c * K];
                 const float v = r[2].w;
                 float A0 = 0.f, A1 = 0.f, A2 = 0.f, B = 0.f, P = 1.0f;
                 for (int k = 0; k < K; ++k) {
+                    if (!rows_hit(fl[k], warp)) continue;
                     const float4 r0 = r[3 * k];
                     const float dx = px - r0.x, dy = py - r0.y;
                     if (fabsf(dx) <= r0.z && fabsf(dy) <= r0.w) {
@@ -115,7 +147,10 @@ __global__ void __launch_bounds__(BT) k_blend_fwd(const ViewDesc *__restrict__ v
             }
             if (T < bp.eps) done = true;
         }
-        if (nxt < rg.y) s_rec[buf ^ 1][tid] = pre;
+        if (nxt < rg.y) {
+            s_rec[buf ^ 1][tid] = pre;
+            if (tid < nload && tid % kRecF4 == 0) s_flag[buf ^ 1][tid / kRecF4] = row_span(pre, tx0, ty0);
+        }
         if (__syncthreads_count(done) == BT) break;
         buf ^= 1;
         cur = nxt;
@@ -211,18 +246,42 @@ void launch_count_pairs(const ViewDesc *views, int n_views, int total_tiles, con
 // then alpha = sigma G' (unless clamped) and G' = exp(-q/2).
 //
 // Phase 1 (thread = pixel) replays a chunk of cells, writing G' per
-// (Gaussian, pixel) and T_n, S_n per (cell, pixel) to shared memory.
-// Phase 2 (warp = Gaussian) sums each Gaussian's nine screen-space
-// gradients over the tile's pixels in registers, reduces across the warp
-// with shuffles and issues one atomic add per value per warp.
-constexpr int BW_G = 64;   // Gaussians per chunk (shared G' table = 64 x 256 floats)
-constexpr int BW_CH = 16;  // cells per chunk at most
+// (Gaussian touching the tile, pixel) and T_n, S_n per (cell, pixel) to
+// shared memory.  Phase 2 (warp = Gaussian) walks only the pixels of the
+// Gaussian's AABB inside the tile, sums its nine screen-space gradients in
+// registers, reduces them across the warp with a transposed shuffle tree
+// (each step halves the values each lane carries) and issues one atomic add
+// per value.  Gaussians whose AABB misses the tile cost one flag test.
+constexpr int BW_G = 32;  // Gaussians per chunk (shared G' table = 32 x 256 floats)
+constexpr int BW_CH = 8;  // cells per chunk at most
 
 __host__ __device__ constexpr int bwd_cells_per_chunk(int K) {
     return BW_G / K < 1 ? 1 : (BW_G / K > BW_CH ? BW_CH : BW_G / K);
 }
 
-__global__ void __launch_bounds__(BT) k_blend_bwd(const ViewDesc *__restrict__ views, int n_views,
+// Sum v[0..15] over the warp.  On return lane L holds the total of value
+// 8 b1 + 4 b2 + 2 b3 + b4 (b_i = bit i of L); lanes with b0 = 1 duplicate it.
+__device__ __forceinline__ float transposed_warp_sum16(float v[16], int lane) {
+#pragma unroll
+    for (int step = 0; step < 4; ++step) {
+        const int bit = 16 >> step;
+        const bool hi = lane & bit;
+        const int n = 8 >> step;  // pairs at this step
+#pragma unroll
+        for (int i = 0; i < n; ++i) {
+            const float keep = hi ? v[2 * i + 1] : v[2 * i];
+            const float send = hi ? v[2 * i] : v[2 * i + 1];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, bit);
+        }
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+__device__ __forceinline__ int transposed_owner(int lane) {
+    return ((lane >> 1) & 1) * 8 + ((lane >> 2) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 4) & 1);
+}
+
+__global__ void __launch_bounds__(BT, 4) k_blend_bwd(const ViewDesc *__restrict__ views, int n_views,
                                                   const uint2 *__restrict__ ranges, const uint32_t *__restrict__ cells,
                                                   const float4 *__restrict__ rec, BlendParams bp,
                                                   const float *__restrict__ rgb, const float *__restrict__ Dpix,
@@ -230,6 +289,7 @@ __global__ void __launch_bounds__(BT) k_blend_bwd(const ViewDesc *__restrict__ v
                                                   float *__restrict__ g2d, float *__restrict__ g_cell_v) {
     extern __shared__ float4 smem_f4[];
     __shared__ int s_view, s_ndmax;
+    __shared__ int s_flag[2][BW_G];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tile = blockIdx.x;
     if (tid == 0) { s_view = find_view(views, n_views, tile); s_ndmax = 0; }
@@ -247,6 +307,7 @@ __global__ void __launch_bounds__(BT) k_blend_bwd(const ViewDesc *__restrict__ v
     float *sdN = sTX + CH * BT;                    // [4][BT]: dN xyz, dD
     const int local = tile - V.tile_base;
     const int tx = local % V.Tx, ty = local / V.Tx;
+    const float tx0 = (float)(tx * kTile), ty0 = (float)(ty * kTile);
     const int xi = tx * kTile + (tid & (kTile - 1)), yi = ty * kTile + (tid >> 4);
     const bool inside = xi < V.W && yi < V.H;
     const float px = (float)xi + 0.5f, py = (float)yi + 0.5f;
@@ -274,13 +335,17 @@ __global__ void __launch_bounds__(BT) k_blend_bwd(const ViewDesc *__restrict__ v
     const uint2 rg = ranges[tile];
     const uint32_t end = rg.x + min((uint32_t)s_ndmax, rg.y - rg.x);
     const float4 *vrec = rec + V.rec_base * kRecF4;
+    const bool want_v = g_cell_v != nullptr;
 
     float T = 1.0f, S = 0.0f;
     float4 pre = make_float4(0.f, 0.f, 0.f, 0.f);
     uint32_t cur = rg.x;
     if (cur < end) {
         pre = fetch_rec(vrec, cells, cur, end, tid, nrec, per, pre);
-        if (tid < nrec) s_rec0[tid] = pre;
+        if (tid < nrec) {
+            s_rec0[tid] = pre;
+            if (tid % kRecF4 == 0) s_flag[0][tid / kRecF4] = row_span(pre, tx0, ty0);
+        }
     }
     __syncthreads();
     int buf = 0;
@@ -289,6 +354,7 @@ __global__ void __launch_bounds__(BT) k_blend_bwd(const ViewDesc *__restrict__ v
         const uint32_t nxt = cur + nc;
         if (nxt < end) pre = fetch_rec(vrec, cells, nxt, end, tid, nrec, per, pre);
         const float4 *sr = s_rec0 + buf * nrec;
+        const int *fl = s_flag[buf];
         // ---- phase 1: replay per pixel
         for (int c = 0; c < nc; ++c) {
             const int n = (int)(cur - rg.x) + c;
@@ -297,6 +363,7 @@ __global__ void __launch_bounds__(BT) k_blend_bwd(const ViewDesc *__restrict__ v
                 const float v = r[2].w;
                 float A0 = 0.f, A1 = 0.f, A2 = 0.f, B = 0.f, P = 1.0f;
                 for (int k = 0; k < K; ++k) {
+                    if (!rows_hit(fl[c * K + k], warp)) continue;
                     const float4 r0 = r[3 * k];
                     const float dx = px - r0.x, dy = py - r0.y;
                     float Gv = 0.f;
@@ -318,28 +385,46 @@ __global__ void __launch_bounds__(BT) k_blend_bwd(const ViewDesc *__restrict__ v
                 sTX[c * BT + tid] = T * X;
                 T *= P;
             } else {
-                for (int k = 0; k < K; ++k) sG[(c * K + k) * BT + tid] = 0.f;
-                sT[c * BT + tid] = 0.f;
-                sS[c * BT + tid] = 0.f;
+                for (int k = 0; k < K; ++k)
+                    if (rows_hit(fl[c * K + k], warp)) sG[(c * K + k) * BT + tid] = 0.f;
                 sTX[c * BT + tid] = 0.f;
             }
         }
         __syncthreads();
-        // ---- phase 2: per Gaussian reduction over the tile's pixels
-        for (int j = warp; j < nc * K; j += BT / 32) {
+        // ---- phase 2: per Gaussian, over its AABB within the tile
+        const int n_tasks = nc * K + (want_v ? nc : 0);
+        for (int j = warp; j < n_tasks; j += BT / 32) {
+            if (j >= nc * K) {  // per-cell term of dL/dv: sum_p T_n X over the tile
+                const int c = j - nc * K;
+                float a = 0.f;
+#pragma unroll
+                for (int q = 0; q < BT / 32; ++q) a += sTX[c * BT + lane + 32 * q];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+                if (lane == 0 && a != 0.f) atomicAdd(g_cell_v + cells[cur + c], a);
+                continue;
+            }
+            const int span = fl[j];
+            if ((span & 0xFF) > (span >> 8)) continue;  // misses the tile
             const int c = j / K, k = j - c * K;
             const float4 r0 = sr[c * per + 3 * k], r1 = sr[c * per + 3 * k + 1], r2 = sr[c * per + 3 * k + 2];
             const float v = r2.w, op = r1.w;
             const float ca = -2.0f * LN2 * r1.x, cb = -LN2 * r1.y, cc = -2.0f * LN2 * r1.z;  // real conic
-            float acc[10];
+            // pixel columns/rows of the tile that can lie in the AABB (a superset; sG decides)
+            const int xl = (int)fmaxf(floorf(r0.x - r0.z - 0.5f - tx0) - 1.0f, 0.0f);
+            const int xh = (int)fminf(ceilf(r0.x + r0.z - 0.5f - tx0) + 1.0f, (float)(kTile - 1));
+            // rows [yl, yh] are exactly those whose warps wrote sG for this record
+            const int yl = span & 0xFF, yh = span >> 8;
+            const int w = xh - xl + 1;
+            float acc[16];
 #pragma unroll
-            for (int i = 0; i < 10; ++i) acc[i] = 0.f;
+            for (int i = 0; i < 16; ++i) acc[i] = 0.f;
             bool any = false;
-#pragma unroll
-            for (int q = 0; q < BT / 32; ++q) {
-                const int p = lane + 32 * q;
+            for (int yy = yl + (lane >> 4); yy <= yh; yy += 2) {
+                const int xx = xl + (lane & 15);
+                if ((lane & 15) >= w) continue;
+                const int p = yy * kTile + xx;
                 const float Gv = sG[j * BT + p];
-                if (k == 0) acc[9] += sTX[c * BT + p];
                 if (Gv == 0.f) continue;
                 any = true;
                 const float Tp = sT[c * BT + p], Sp = sS[c * BT + p];
@@ -347,42 +432,38 @@ __global__ void __launch_bounds__(BT) k_blend_bwd(const ViewDesc *__restrict__ v
                 const float raw = op * Gv;
                 const float al = fminf(raw, bp.alpha_max);
                 const float cA = v * Tp;
-                const float om = 1.0f - v * al;
-                const float dal = cA * (e0 * r2.x + e1 * r2.y + e2 * r2.z + eD) - v * Sp / om;
-                acc[6] += cA * al * e0;
-                acc[7] += cA * al * e1;
-                acc[8] += cA * al * e2;
-                acc[9] += -Sp * al / om;
+                const float rom = __frcp_rn(1.0f - v * al);
+                const float dal = cA * (e0 * r2.x + e1 * r2.y + e2 * r2.z + eD) - v * Sp * rom;
+                const float ca_al = cA * al;
+                acc[6] += ca_al * e0;
+                acc[7] += ca_al * e1;
+                acc[8] += ca_al * e2;
+                acc[9] -= Sp * al * rom;
                 if (raw < bp.alpha_max) {
                     acc[5] += dal * Gv;
                     const float dq = -0.5f * Gv * (dal * op);
-                    const float dx = (float)(tx * kTile + (p & (kTile - 1))) + 0.5f - r0.x;
-                    const float dy = (float)(ty * kTile + (p >> 4)) + 0.5f - r0.y;
-                    acc[0] += dq * -(2.0f * ca * dx + 2.0f * cb * dy);
-                    acc[1] += dq * -(2.0f * cb * dx + 2.0f * cc * dy);
+                    const float dx = (tx0 + (float)xx + 0.5f) - r0.x;
+                    const float dy = (ty0 + (float)yy + 0.5f) - r0.y;
+                    acc[0] -= dq * 2.0f * (ca * dx + cb * dy);
+                    acc[1] -= dq * 2.0f * (cb * dx + cc * dy);
                     acc[2] += dq * dx * dx;
                     acc[3] += dq * 2.0f * dx * dy;
                     acc[4] += dq * dy * dy;
                 }
             }
-            const bool warp_any = __any_sync(0xffffffffu, any) || (k == 0 && __any_sync(0xffffffffu, acc[9] != 0.f));
-            if (!warp_any) continue;
-#pragma unroll
-            for (int i = 0; i < 10; ++i) {
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
+            if (!__any_sync(0xffffffffu, any)) continue;
+            const float tot = transposed_warp_sum16(acc, lane);
+            const int idx = transposed_owner(lane);
+            if ((lane & 1) == 0 && tot != 0.f) {
+                const uint32_t cellid = cells[cur + c];
+                if (idx < 9) atomicAdd(g2d + (V.rec_base + (long long)cellid * K + k) * kGradF + idx, tot);
+                else if (idx == 9 && want_v) atomicAdd(g_cell_v + cellid, tot);
             }
-            const uint32_t cellid = cells[cur + c];
-            const long long g = (long long)cellid * K + k;
-            float *dst = g2d + (V.rec_base + g) * kGradF;
-            float val = 0.f;
-#pragma unroll
-            for (int i = 0; i < 10; ++i)
-                if (lane == i) val = acc[i];
-            if (lane < 9 && val != 0.f) atomicAdd(dst + lane, val);
-            if (lane == 9 && g_cell_v && val != 0.f) atomicAdd(g_cell_v + cellid, val);
         }
-        if (nxt < end && tid < nrec) s_rec0[(buf ^ 1) * nrec + tid] = pre;
+        if (nxt < end && tid < nrec) {
+            s_rec0[(buf ^ 1) * nrec + tid] = pre;
+            if (tid % kRecF4 == 0) s_flag[buf ^ 1][tid / kRecF4] = row_span(pre, tx0, ty0);
+        }
         __syncthreads();
         buf ^= 1;
         cur = nxt;
