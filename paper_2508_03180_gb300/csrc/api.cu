@@ -536,8 +536,11 @@ dgs_status chain_forward(dgs_ctx *ctx, Workspace &ws, const std::vector<ChainVie
     float *img2 = (keep_rgb && out_img) ? (float *)ws.rgb.p : nullptr;
     {
         StageTimer t(ctx->prof, DGS_STAGE_BLEND_FWD, st);
+        int K_all = slots[0]->K;
+        for (int k = 1; k < S; ++k)
+            if (slots[k]->K != K_all) K_all = 0;
         launch_blend_fwd(dv, V, ws.total_tiles, (const uint2 *)ws.ranges.p, (const uint32_t *)ws.tval.p,
-                         (const float4 *)ws.rec.p, bp, img, img2, (float *)ws.Dpix.p, (int *)ws.ndpix.p, st);
+                         (const float4 *)ws.rec.p, bp, img, img2, (float *)ws.Dpix.p, (int *)ws.ndpix.p, K_all, st);
     }
     CK(cudaGetLastError());
     ws.stream = st;

@@ -75,112 +75,162 @@ __device__ __forceinline__ int find_view(const ViewDesc *views, int n_views, int
     return lo;
 }
 
-__global__ void __launch_bounds__(BT) k_blend_fwd(const ViewDesc *__restrict__ views, int n_views,
+// Forward: 128 threads per 16x16 tile, each thread blends the two
+// vertically adjacent pixels (x, 2r) and (x, 2r+1), so a record fetched from
+// shared memory, its tile-row test and the x half of its AABB test serve two
+// pixels; warp w owns tile rows 4w..4w+3.  KT > 0 fixes K at compile time.
+constexpr int FT = 128;
+
+__device__ __forceinline__ bool rows_hit4(int span, int warp) {
+    return !(4 * warp + 3 < (span & 0xFF) || 4 * warp > (span >> 8));
+}
+
+template <int KT>
+__global__ void __launch_bounds__(FT) k_blend_fwd(const ViewDesc *__restrict__ views, int n_views,
                                                   const uint2 *__restrict__ ranges, const uint32_t *__restrict__ cells,
                                                   const float4 *__restrict__ rec, BlendParams bp,
                                                   float *__restrict__ out_rgb, float *__restrict__ out_rgb2,
                                                   float *__restrict__ out_D, int *__restrict__ out_nd) {
-    __shared__ float4 s_rec[2][BT];
-    __shared__ int s_flag[2][BT / kRecF4 + 1];  // row span of each record in this tile
+    __shared__ float4 s_rec[2][FT];
+    __shared__ int s_span[2][FT / kRecF4 + 1];  // row span of each record in this tile
     __shared__ int s_view;
-    const int tid = threadIdx.x, tile = blockIdx.x;
+    const int tid = threadIdx.x, tile = blockIdx.x, warp = tid >> 5;
     if (tid == 0) s_view = find_view(views, n_views, tile);
     __syncthreads();
     const ViewDesc &V = views[s_view];
     const int local = tile - V.tile_base;
     const int tx = local % V.Tx, ty = local / V.Tx;
-    const int xi = tx * kTile + (tid & (kTile - 1)), yi = ty * kTile + (tid >> 4);
-    const bool inside = xi < V.W && yi < V.H;
-    const float px = (float)xi + 0.5f, py = (float)yi + 0.5f;
     const float tx0 = (float)(tx * kTile), ty0 = (float)(ty * kTile);
+    const int xi = tx * kTile + (tid & (kTile - 1));
+    const int yi0 = ty * kTile + 2 * (tid >> 4), yi1 = yi0 + 1;
+    const bool in0 = xi < V.W && yi0 < V.H, in1 = xi < V.W && yi1 < V.H;
+    const float px = (float)xi + 0.5f, py0 = (float)yi0 + 0.5f, py1 = (float)yi1 + 0.5f;
 
-    const int K = V.K;
+    const int K = KT > 0 ? KT : V.K;
     const int per = kRecF4 * K;               // float4s per cell
-    const int CH = max(1, BT / per);          // cells per chunk
+    const int CH = max(1, FT / per);          // cells per chunk
     const int nload = CH * per;
     const float4 *vrec = rec + V.rec_base * kRecF4;
     const uint2 rg = ranges[tile];
 
-    float T = 1.0f, N0 = 0.f, N1 = 0.f, N2 = 0.f, D = 0.f;
-    int n = 0;
-    bool done = !inside;
+    float T0 = 1.0f, N00 = 0.f, N01 = 0.f, N02 = 0.f, D0 = 0.f;
+    float T1 = 1.0f, N10 = 0.f, N11 = 0.f, N12 = 0.f, D1 = 0.f;
+    int n0 = 0, n1 = 0;
+    bool done0 = !in0, done1 = !in1;
     float4 pre = make_float4(0.f, 0.f, 0.f, 0.f);
     uint32_t cur = rg.x;
     if (cur < rg.y) {
         pre = fetch_rec(vrec, cells, cur, rg.y, tid, nload, per, pre);
         s_rec[0][tid] = pre;
-        if (tid < nload && tid % kRecF4 == 0) s_flag[0][tid / kRecF4] = row_span(pre, tx0, ty0);
+        if (tid < nload && tid % kRecF4 == 0) s_span[0][tid / kRecF4] = row_span(pre, tx0, ty0);
     }
     __syncthreads();
-    const int warp = tid >> 5;
     int buf = 0;
     while (cur < rg.y) {
         const int nc = (int)min((uint32_t)CH, rg.y - cur);
         const uint32_t nxt = cur + nc;
         if (nxt < rg.y) pre = fetch_rec(vrec, cells, nxt, rg.y, tid, nload, per, pre);
-        if (!done) {
-            for (int c = 0; c < nc; ++c) {
-                if (T < bp.eps) { done = true; break; }
-                const float4 *r = &s_rec[buf][c * per];
-                const int *fl = &s_flag[buf][c * K];
-                const float v = r[2].w;
-                float A0 = 0.f, A1 = 0.f, A2 = 0.f, B = 0.f, P = 1.0f;
-                for (int k = 0; k < K; ++k) {
-                    if (!rows_hit(fl[k], warp)) continue;
-                    const float4 r0 = r[3 * k];
-                    const float dx = px - r0.x, dy = py - r0.y;
-                    if (fabsf(dx) <= r0.z && fabsf(dy) <= r0.w) {
-                        const float4 r1 = r[3 * k + 1];
-                        const float4 r2 = r[3 * k + 2];
-                        const float pw = r1.x * dx * dx + r1.y * dx * dy + r1.z * dy * dy;
-                        const float al = fminf(r1.w * ex2_approx(pw), bp.alpha_max);
-                        A0 += al * r2.x; A1 += al * r2.y; A2 += al * r2.z;
-                        B += al;
-                        P -= P * (v * al);
-                    }
+        for (int c = 0; c < nc; ++c) {
+            // before cell n a pixel stops if T_n < eps (Sec. V-B)
+            done0 = done0 || T0 < bp.eps;
+            done1 = done1 || T1 < bp.eps;
+            if (done0 && done1) break;
+            const float4 *r = &s_rec[buf][c * per];
+            const int *sp = &s_span[buf][c * K];
+            const float v = r[2].w;
+            float A00 = 0.f, A01 = 0.f, A02 = 0.f, B0 = 0.f, P0 = 1.0f;
+            float A10 = 0.f, A11 = 0.f, A12 = 0.f, B1 = 0.f, P1 = 1.0f;
+#pragma unroll (KT > 0 ? KT : 1)
+            for (int k = 0; k < K; ++k) {
+                if (!rows_hit4(sp[k], warp)) continue;
+                const float4 r0 = r[3 * k];
+                const float dx = px - r0.x;
+                if (!(fabsf(dx) <= r0.z)) continue;
+                const float dy0 = py0 - r0.y, dy1 = py1 - r0.y;
+                const bool h0 = !done0 && fabsf(dy0) <= r0.w;
+                const bool h1 = !done1 && fabsf(dy1) <= r0.w;
+                if (!(h0 || h1)) continue;
+                const float4 r1 = r[3 * k + 1];
+                const float4 r2 = r[3 * k + 2];
+                const float qx = r1.x * dx * dx;
+                const float bx = r1.y * dx;
+                if (h0) {
+                    const float al = fminf(r1.w * ex2_approx(qx + (bx + r1.z * dy0) * dy0), bp.alpha_max);
+                    A00 += al * r2.x; A01 += al * r2.y; A02 += al * r2.z;
+                    B0 += al;
+                    P0 -= P0 * (v * al);
                 }
-                const float w = v * T;
-                N0 += w * A0; N1 += w * A1; N2 += w * A2;
-                D += w * B;
-                T *= P;
-                ++n;
+                if (h1) {
+                    const float al = fminf(r1.w * ex2_approx(qx + (bx + r1.z * dy1) * dy1), bp.alpha_max);
+                    A10 += al * r2.x; A11 += al * r2.y; A12 += al * r2.z;
+                    B1 += al;
+                    P1 -= P1 * (v * al);
+                }
             }
-            if (T < bp.eps) done = true;
+            if (!done0) {
+                const float w = v * T0;
+                N00 += w * A00; N01 += w * A01; N02 += w * A02;
+                D0 += w * B0;
+                T0 *= P0;
+                ++n0;
+            }
+            if (!done1) {
+                const float w = v * T1;
+                N10 += w * A10; N11 += w * A11; N12 += w * A12;
+                D1 += w * B1;
+                T1 *= P1;
+                ++n1;
+            }
         }
+        done0 = done0 || T0 < bp.eps;
+        done1 = done1 || T1 < bp.eps;
         if (nxt < rg.y) {
             s_rec[buf ^ 1][tid] = pre;
-            if (tid < nload && tid % kRecF4 == 0) s_flag[buf ^ 1][tid / kRecF4] = row_span(pre, tx0, ty0);
+            if (tid < nload && tid % kRecF4 == 0) s_span[buf ^ 1][tid / kRecF4] = row_span(pre, tx0, ty0);
         }
-        if (__syncthreads_count(done) == BT) break;
+        if (__syncthreads_count(done0 && done1) == FT) break;
         buf ^= 1;
         cur = nxt;
     }
-    if (inside) {
-        const long long HW = (long long)V.W * V.H;
-        const long long pin = (long long)yi * V.W + xi;
-        float *img = V.out ? V.out : out_rgb + 3 * V.pix_base;
+    const long long HW = (long long)V.W * V.H;
+    float *img = V.out ? V.out : out_rgb + 3 * V.pix_base;
+    float *im2 = out_rgb2 ? out_rgb2 + 3 * V.pix_base : nullptr;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        if (!(q == 0 ? in0 : in1)) continue;
+        const float D = q == 0 ? D0 : D1;
+        const long long pin = (long long)(q == 0 ? yi0 : yi1) * V.W + xi;
         const bool hit = D > bp.d_min;
-        const float c0 = hit ? N0 / D : bp.bg0, c1 = hit ? N1 / D : bp.bg1, c2 = hit ? N2 / D : bp.bg2;
+        const float c0 = hit ? (q == 0 ? N00 : N10) / D : bp.bg0;
+        const float c1 = hit ? (q == 0 ? N01 : N11) / D : bp.bg1;
+        const float c2 = hit ? (q == 0 ? N02 : N12) / D : bp.bg2;
         img[pin] = c0;
         img[HW + pin] = c1;
         img[2 * HW + pin] = c2;
-        if (out_rgb2) {
-            float *im2 = out_rgb2 + 3 * V.pix_base;
+        if (im2) {
             im2[pin] = c0;
             im2[HW + pin] = c1;
             im2[2 * HW + pin] = c2;
         }
         out_D[V.pix_base + pin] = D;
-        out_nd[V.pix_base + pin] = n;
+        out_nd[V.pix_base + pin] = q == 0 ? n0 : n1;
     }
 }
 
+// K of the chain's views when they all share one (compile-time loop), else 0
 void launch_blend_fwd(const ViewDesc *views, int n_views, int total_tiles, const uint2 *ranges,
                       const uint32_t *tile_cells, const float4 *rec, const BlendParams &bp, float *out_rgb,
-                      float *out_rgb2, float *out_D, int *out_nd, cudaStream_t st) {
+                      float *out_rgb2, float *out_D, int *out_nd, int K_all, cudaStream_t st) {
     if (total_tiles == 0) return;
-    k_blend_fwd<<<total_tiles, BT, 0, st>>>(views, n_views, ranges, tile_cells, rec, bp, out_rgb, out_rgb2, out_D,
-                                            out_nd);
+#define DGS_FWD(KV)                                                                                              \
+    k_blend_fwd<KV><<<total_tiles, FT, 0, st>>>(views, n_views, ranges, tile_cells, rec, bp, out_rgb, out_rgb2, \
+                                                out_D, out_nd)
+    switch (K_all) {
+        case 8: DGS_FWD(8); break;
+        case 10: DGS_FWD(10); break;
+        default: DGS_FWD(0); break;
+    }
+#undef DGS_FWD
 }
 
 // ---------------------------------------------------------------- counters
@@ -288,7 +338,7 @@ __global__ void __launch_bounds__(BT, 4) k_blend_bwd(const ViewDesc *__restrict_
                                                   const int *__restrict__ ndpix, const float *__restrict__ dL_drgb,
                                                   float *__restrict__ g2d, float *__restrict__ g_cell_v) {
     extern __shared__ float4 smem_f4[];
-    __shared__ int s_view, s_ndmax;
+    __shared__ int s_view, s_ndmax, s_task;
     __shared__ int s_flag[2][BW_G];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tile = blockIdx.x;
@@ -300,11 +350,10 @@ __global__ void __launch_bounds__(BT, 4) k_blend_bwd(const ViewDesc *__restrict_
     const int CH = bwd_cells_per_chunk(K);
     const int nrec = CH * per;                     // float4s per chunk (<= 3 * BW_G < BT)
     float4 *s_rec0 = smem_f4;                      // [2][nrec]
-    float *sG = reinterpret_cast<float *>(smem_f4 + 2 * nrec);  // [CH*K][BT]
-    float *sT = sG + CH * K * BT;                  // [CH][BT]
-    float *sS = sT + CH * BT;
-    float *sTX = sS + CH * BT;
-    float *sdN = sTX + CH * BT;                    // [4][BT]: dN xyz, dD
+    float4 *sdN = smem_f4 + 2 * nrec;              // [BT]: dL/dN xyz, dL/dD per pixel
+    float2 *sTS = reinterpret_cast<float2 *>(sdN + BT);  // [CH][BT]: T_n, S_n per (cell, pixel)
+    float *sG = reinterpret_cast<float *>(sTS + CH * BT);  // [CH*K][BT]
+    float *sTX = sG + CH * K * BT;                 // [CH][BT]: T_n X_n for dL/dv
     const int local = tile - V.tile_base;
     const int tx = local % V.Tx, ty = local / V.Tx;
     const float tx0 = (float)(tx * kTile), ty0 = (float)(ty * kTile);
@@ -329,7 +378,7 @@ __global__ void __launch_bounds__(BT, 4) k_blend_bwd(const ViewDesc *__restrict_
             dD = -(g0 * c0 + g1 * c1 + g2 * c2) * iD;
         }
     }
-    sdN[tid] = dN0; sdN[BT + tid] = dN1; sdN[2 * BT + tid] = dN2; sdN[3 * BT + tid] = dD;
+    sdN[tid] = make_float4(dN0, dN1, dN2, dD);
     if (nd > 0) atomicMax(&s_ndmax, nd);
     __syncthreads();
     const uint2 rg = ranges[tile];
@@ -356,6 +405,7 @@ __global__ void __launch_bounds__(BT, 4) k_blend_bwd(const ViewDesc *__restrict_
         const float4 *sr = s_rec0 + buf * nrec;
         const int *fl = s_flag[buf];
         // ---- phase 1: replay per pixel
+        if (tid == 0) s_task = 0;
         for (int c = 0; c < nc; ++c) {
             const int n = (int)(cur - rg.x) + c;
             const float4 *r = sr + c * per;
@@ -380,8 +430,7 @@ __global__ void __launch_bounds__(BT, 4) k_blend_bwd(const ViewDesc *__restrict_
                 }
                 const float X = dN0 * A0 + dN1 * A1 + dN2 * A2 + dD * B;
                 S -= v * T * X;
-                sT[c * BT + tid] = T;
-                sS[c * BT + tid] = S;
+                sTS[c * BT + tid] = make_float2(T, S);
                 sTX[c * BT + tid] = T * X;
                 T *= P;
             } else {
@@ -391,9 +440,14 @@ __global__ void __launch_bounds__(BT, 4) k_blend_bwd(const ViewDesc *__restrict_
             }
         }
         __syncthreads();
-        // ---- phase 2: per Gaussian, over its AABB within the tile
+        // ---- phase 2: per Gaussian, over its AABB within the tile; warps take
+        // the next task from a shared counter so uneven windows balance out
         const int n_tasks = nc * K + (want_v ? nc : 0);
-        for (int j = warp; j < n_tasks; j += BT / 32) {
+        for (;;) {
+            int j = 0;
+            if (lane == 0) j = atomicAdd(&s_task, 1);
+            j = __shfl_sync(0xffffffffu, j, 0);
+            if (j >= n_tasks) break;
             if (j >= nc * K) {  // per-cell term of dL/dv: sum_p T_n X over the tile
                 const int c = j - nc * K;
                 float a = 0.f;
@@ -410,35 +464,37 @@ __global__ void __launch_bounds__(BT, 4) k_blend_bwd(const ViewDesc *__restrict_
             const float4 r0 = sr[c * per + 3 * k], r1 = sr[c * per + 3 * k + 1], r2 = sr[c * per + 3 * k + 2];
             const float v = r2.w, op = r1.w;
             const float ca = -2.0f * LN2 * r1.x, cb = -LN2 * r1.y, cc = -2.0f * LN2 * r1.z;  // real conic
-            // pixel columns/rows of the tile that can lie in the AABB (a superset; sG decides)
+            // columns of the tile that can lie in the AABB (a superset; sG decides);
+            // rows [yl, yh] are exactly those whose warps wrote sG for this record
             const int xl = (int)fmaxf(floorf(r0.x - r0.z - 0.5f - tx0) - 1.0f, 0.0f);
             const int xh = (int)fminf(ceilf(r0.x + r0.z - 0.5f - tx0) + 1.0f, (float)(kTile - 1));
-            // rows [yl, yh] are exactly those whose warps wrote sG for this record
             const int yl = span & 0xFF, yh = span >> 8;
             const int w = xh - xl + 1;
+            const int npx = w * (yh - yl + 1);
+            const float inv_w = 1.0f / (float)w;
             float acc[16];
 #pragma unroll
             for (int i = 0; i < 16; ++i) acc[i] = 0.f;
             bool any = false;
-            for (int yy = yl + (lane >> 4); yy <= yh; yy += 2) {
-                const int xx = xl + (lane & 15);
-                if ((lane & 15) >= w) continue;
+            for (int i = lane; i < npx; i += 32) {
+                const int row = (int)(((float)i + 0.5f) * inv_w);  // exact: i < 256, w <= 16
+                const int xx = xl + i - row * w, yy = yl + row;
                 const int p = yy * kTile + xx;
                 const float Gv = sG[j * BT + p];
                 if (Gv == 0.f) continue;
                 any = true;
-                const float Tp = sT[c * BT + p], Sp = sS[c * BT + p];
-                const float e0 = sdN[p], e1 = sdN[BT + p], e2 = sdN[2 * BT + p], eD = sdN[3 * BT + p];
+                const float2 ts = sTS[c * BT + p];
+                const float4 e = sdN[p];
                 const float raw = op * Gv;
                 const float al = fminf(raw, bp.alpha_max);
-                const float cA = v * Tp;
+                const float cA = v * ts.x;
                 const float rom = __frcp_rn(1.0f - v * al);
-                const float dal = cA * (e0 * r2.x + e1 * r2.y + e2 * r2.z + eD) - v * Sp * rom;
+                const float dal = cA * (e.x * r2.x + e.y * r2.y + e.z * r2.z + e.w) - v * ts.y * rom;
                 const float ca_al = cA * al;
-                acc[6] += ca_al * e0;
-                acc[7] += ca_al * e1;
-                acc[8] += ca_al * e2;
-                acc[9] -= Sp * al * rom;
+                acc[6] += ca_al * e.x;
+                acc[7] += ca_al * e.y;
+                acc[8] += ca_al * e.z;
+                acc[9] -= ts.y * al * rom;
                 if (raw < bp.alpha_max) {
                     acc[5] += dal * Gv;
                     const float dq = -0.5f * Gv * (dal * op);
@@ -473,7 +529,7 @@ __global__ void __launch_bounds__(BT, 4) k_blend_bwd(const ViewDesc *__restrict_
 static size_t bwd_smem_bytes(int K) {
     const int per = kRecF4 * K;
     const int CH = bwd_cells_per_chunk(K);
-    return sizeof(float4) * 2 * CH * per + sizeof(float) * ((size_t)CH * K * BT + 3 * CH * BT + 4 * BT);
+    return sizeof(float4) * (2 * CH * per + BT) + sizeof(float2) * CH * BT + sizeof(float) * ((size_t)CH * K * BT + CH * BT);
 }
 
 // K: Gaussians per cell of the chain's scene (shared-memory sizing)

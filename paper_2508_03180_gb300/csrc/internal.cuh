@@ -124,7 +124,7 @@ void launch_project_bwd(const ViewDesc *views, int n_views, int slot, const Scen
 // blend.cu
 void launch_blend_fwd(const ViewDesc *views, int n_views, int total_tiles, const uint2 *ranges,
                       const uint32_t *tile_cells, const float4 *rec, const BlendParams &bp, float *out_rgb,
-                      float *out_rgb2, float *out_D, int *out_nd, cudaStream_t st);
+                      float *out_rgb2, float *out_D, int *out_nd, int K_all, cudaStream_t st);
 void launch_blend_bwd(const ViewDesc *views, int n_views, int total_tiles, int K, const uint2 *ranges,
                       const uint32_t *tile_cells, const float4 *rec, const BlendParams &bp, const float *rgb,
                       const float *D, const int *nd, const float *dL_drgb, float *g2d, float *g_cell_v,
