@@ -75,41 +75,68 @@ __device__ __forceinline__ int find_view(const ViewDesc *views, int n_views, int
     return lo;
 }
 
-// Forward: 128 threads per 16x16 tile, each thread blends the two
-// vertically adjacent pixels (x, 2r) and (x, 2r+1), so a record fetched from
-// shared memory, its tile-row test and the x half of its AABB test serve two
-// pixels; warp w owns tile rows 4w..4w+3.  KT > 0 fixes K at compile time.
-constexpr int FT = 128;
+// Work unit: one warp per 16x4-pixel sub-tile (a quarter of a 16x16 tile,
+// a one-warp CTA), each lane blending the two vertically adjacent pixels
+// (x, 2r) and (x, 2r+1).  Warps never wait for one another: each stages the
+// 48-byte records of one cell at a time in its own shared memory (double
+// buffered through registers), takes a ballot of the cell's Gaussians whose
+// AABB reaches its sub-tile and loops over those only, and stops as soon as
+// its own 64 pixels are done.  KT > 0 fixes K at compile time.
+constexpr int WT = 32;       // threads per work unit
+constexpr int WSUB = 4;      // sub-tiles per tile (rows 4s .. 4s+3)
+constexpr int MAXPER = kRecF4 * kMaxK;  // float4s of one cell's records
 
-__device__ __forceinline__ bool rows_hit4(int span, int warp) {
-    return !(4 * warp + 3 < (span & 0xFF) || 4 * warp > (span >> 8));
+// Can record piece r0 pass the AABB test at some pixel centre of the 16-wide,
+// 4-high block whose first pixel is (x0, y0)?  Exactly conservative (FP32
+// subtraction is monotone, so testing the nearest centres suffices).
+__device__ __forceinline__ bool touches_block(float4 r0, float x0, float y0) {
+    const float lx = x0 + 0.5f, hx = x0 + (float)kTile - 0.5f;
+    const float ly = y0 + 0.5f, hy = y0 + (float)WSUB - 0.5f;
+    return !(lx - r0.x > r0.z || r0.x - hx > r0.z || ly - r0.y > r0.w || r0.y - hy > r0.w);
+}
+
+// Stage the records of tile-list entry e (per float4s) into dst; one to three
+// 16-byte loads per lane.
+__device__ __forceinline__ void stage_cell(float4 *dst, const float4 *__restrict__ vrec,
+                                           const uint32_t *__restrict__ cells, uint32_t e, int per, int lane,
+                                           float4 pre[3]) {
+    const float4 *src = vrec + (long long)__ldg(cells + e) * per;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const int i = lane + 32 * q;
+        if (i < per) pre[q] = __ldg(src + i);
+    }
+    (void)dst;
+}
+
+__device__ __forceinline__ void stash_cell(float4 *dst, int per, int lane, const float4 pre[3]) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const int i = lane + 32 * q;
+        if (i < per) dst[i] = pre[q];
+    }
 }
 
 template <int KT>
-__global__ void __launch_bounds__(FT) k_blend_fwd(const ViewDesc *__restrict__ views, int n_views,
+__global__ void __launch_bounds__(WT) k_blend_fwd(const ViewDesc *__restrict__ views, int n_views,
                                                   const uint2 *__restrict__ ranges, const uint32_t *__restrict__ cells,
                                                   const float4 *__restrict__ rec, BlendParams bp,
                                                   float *__restrict__ out_rgb, float *__restrict__ out_rgb2,
                                                   float *__restrict__ out_D, int *__restrict__ out_nd) {
-    __shared__ float4 s_rec[2][FT];
-    __shared__ int s_span[2][FT / kRecF4 + 1];  // row span of each record in this tile
-    __shared__ int s_view;
-    const int tid = threadIdx.x, tile = blockIdx.x, warp = tid >> 5;
-    if (tid == 0) s_view = find_view(views, n_views, tile);
-    __syncthreads();
-    const ViewDesc &V = views[s_view];
+    __shared__ float4 s_rec[2][MAXPER];
+    const int lane = threadIdx.x;
+    const int tile = blockIdx.x / WSUB, sub = blockIdx.x % WSUB;
+    const int vi = find_view(views, n_views, tile);
+    const ViewDesc &V = views[vi];
     const int local = tile - V.tile_base;
     const int tx = local % V.Tx, ty = local / V.Tx;
-    const float tx0 = (float)(tx * kTile), ty0 = (float)(ty * kTile);
-    const int xi = tx * kTile + (tid & (kTile - 1));
-    const int yi0 = ty * kTile + 2 * (tid >> 4), yi1 = yi0 + 1;
+    const float bx0 = (float)(tx * kTile), by0 = (float)(ty * kTile + WSUB * sub);
+    const int xi = tx * kTile + (lane & (kTile - 1));
+    const int yi0 = ty * kTile + WSUB * sub + 2 * (lane >> 4), yi1 = yi0 + 1;
     const bool in0 = xi < V.W && yi0 < V.H, in1 = xi < V.W && yi1 < V.H;
     const float px = (float)xi + 0.5f, py0 = (float)yi0 + 0.5f, py1 = (float)yi1 + 0.5f;
-
     const int K = KT > 0 ? KT : V.K;
-    const int per = kRecF4 * K;               // float4s per cell
-    const int CH = max(1, FT / per);          // cells per chunk
-    const int nload = CH * per;
+    const int per = kRecF4 * K;
     const float4 *vrec = rec + V.rec_base * kRecF4;
     const uint2 rg = ranges[tile];
 
@@ -117,80 +144,68 @@ __global__ void __launch_bounds__(FT) k_blend_fwd(const ViewDesc *__restrict__ v
     float T1 = 1.0f, N10 = 0.f, N11 = 0.f, N12 = 0.f, D1 = 0.f;
     int n0 = 0, n1 = 0;
     bool done0 = !in0, done1 = !in1;
-    float4 pre = make_float4(0.f, 0.f, 0.f, 0.f);
-    uint32_t cur = rg.x;
-    if (cur < rg.y) {
-        pre = fetch_rec(vrec, cells, cur, rg.y, tid, nload, per, pre);
-        s_rec[0][tid] = pre;
-        if (tid < nload && tid % kRecF4 == 0) s_span[0][tid / kRecF4] = row_span(pre, tx0, ty0);
+    float4 pre[3];
+    if (rg.x < rg.y) {
+        stage_cell(s_rec[0], vrec, cells, rg.x, per, lane, pre);
+        stash_cell(s_rec[0], per, lane, pre);
     }
-    __syncthreads();
+    __syncwarp();
     int buf = 0;
-    while (cur < rg.y) {
-        const int nc = (int)min((uint32_t)CH, rg.y - cur);
-        const uint32_t nxt = cur + nc;
-        if (nxt < rg.y) pre = fetch_rec(vrec, cells, nxt, rg.y, tid, nload, per, pre);
-        for (int c = 0; c < nc; ++c) {
-            // before cell n a pixel stops if T_n < eps (Sec. V-B)
-            done0 = done0 || T0 < bp.eps;
-            done1 = done1 || T1 < bp.eps;
-            if (done0 && done1) break;
-            const float4 *r = &s_rec[buf][c * per];
-            const int *sp = &s_span[buf][c * K];
-            const float v = r[2].w;
-            float A00 = 0.f, A01 = 0.f, A02 = 0.f, B0 = 0.f, P0 = 1.0f;
-            float A10 = 0.f, A11 = 0.f, A12 = 0.f, B1 = 0.f, P1 = 1.0f;
-#pragma unroll (KT > 0 ? KT : 1)
-            for (int k = 0; k < K; ++k) {
-                if (!rows_hit4(sp[k], warp)) continue;
-                const float4 r0 = r[3 * k];
-                const float dx = px - r0.x;
-                if (!(fabsf(dx) <= r0.z)) continue;
-                const float dy0 = py0 - r0.y, dy1 = py1 - r0.y;
-                const bool h0 = !done0 && fabsf(dy0) <= r0.w;
-                const bool h1 = !done1 && fabsf(dy1) <= r0.w;
-                if (!(h0 || h1)) continue;
-                const float4 r1 = r[3 * k + 1];
-                const float4 r2 = r[3 * k + 2];
-                const float qx = r1.x * dx * dx;
-                const float bx = r1.y * dx;
-                if (h0) {
-                    const float al = fminf(r1.w * ex2_approx(qx + (bx + r1.z * dy0) * dy0), bp.alpha_max);
-                    A00 += al * r2.x; A01 += al * r2.y; A02 += al * r2.z;
-                    B0 += al;
-                    P0 -= P0 * (v * al);
-                }
-                if (h1) {
-                    const float al = fminf(r1.w * ex2_approx(qx + (bx + r1.z * dy1) * dy1), bp.alpha_max);
-                    A10 += al * r2.x; A11 += al * r2.y; A12 += al * r2.z;
-                    B1 += al;
-                    P1 -= P1 * (v * al);
-                }
-            }
-            if (!done0) {
-                const float w = v * T0;
-                N00 += w * A00; N01 += w * A01; N02 += w * A02;
-                D0 += w * B0;
-                T0 *= P0;
-                ++n0;
-            }
-            if (!done1) {
-                const float w = v * T1;
-                N10 += w * A10; N11 += w * A11; N12 += w * A12;
-                D1 += w * B1;
-                T1 *= P1;
-                ++n1;
-            }
-        }
+    for (uint32_t e = rg.x; e < rg.y; ++e) {
+        // before cell n a pixel stops if T_n < eps (Sec. V-B)
         done0 = done0 || T0 < bp.eps;
         done1 = done1 || T1 < bp.eps;
-        if (nxt < rg.y) {
-            s_rec[buf ^ 1][tid] = pre;
-            if (tid < nload && tid % kRecF4 == 0) s_span[buf ^ 1][tid / kRecF4] = row_span(pre, tx0, ty0);
+        if (__all_sync(0xffffffffu, done0 && done1)) break;
+        if (e + 1 < rg.y) stage_cell(s_rec[buf ^ 1], vrec, cells, e + 1, per, lane, pre);
+        const float4 *r = s_rec[buf];
+        const float v = r[2].w;
+        unsigned mask = __ballot_sync(0xffffffffu, lane < K && touches_block(r[kRecF4 * lane], bx0, by0));
+        float A00 = 0.f, A01 = 0.f, A02 = 0.f, B0 = 0.f, P0 = 1.0f;
+        float A10 = 0.f, A11 = 0.f, A12 = 0.f, B1 = 0.f, P1 = 1.0f;
+        for (; mask; mask &= mask - 1) {
+            const int k = __ffs(mask) - 1;
+            const float4 r0 = r[3 * k];
+            const float dx = px - r0.x;
+            if (!(fabsf(dx) <= r0.z)) continue;
+            const float dy0 = py0 - r0.y, dy1 = py1 - r0.y;
+            const bool h0 = !done0 && fabsf(dy0) <= r0.w;
+            const bool h1 = !done1 && fabsf(dy1) <= r0.w;
+            if (!(h0 || h1)) continue;
+            const float4 r1 = r[3 * k + 1];
+            const float4 r2 = r[3 * k + 2];
+            const float qx = r1.x * dx * dx;
+            const float bxx = r1.y * dx;
+            if (h0) {
+                const float al = fminf(r1.w * ex2_approx(qx + (bxx + r1.z * dy0) * dy0), bp.alpha_max);
+                A00 += al * r2.x; A01 += al * r2.y; A02 += al * r2.z;
+                B0 += al;
+                P0 -= P0 * (v * al);
+            }
+            if (h1) {
+                const float al = fminf(r1.w * ex2_approx(qx + (bxx + r1.z * dy1) * dy1), bp.alpha_max);
+                A10 += al * r2.x; A11 += al * r2.y; A12 += al * r2.z;
+                B1 += al;
+                P1 -= P1 * (v * al);
+            }
         }
-        if (__syncthreads_count(done0 && done1) == FT) break;
+        if (!done0) {
+            const float w = v * T0;
+            N00 += w * A00; N01 += w * A01; N02 += w * A02;
+            D0 += w * B0;
+            T0 *= P0;
+            ++n0;
+        }
+        if (!done1) {
+            const float w = v * T1;
+            N10 += w * A10; N11 += w * A11; N12 += w * A12;
+            D1 += w * B1;
+            T1 *= P1;
+            ++n1;
+        }
+        __syncwarp();
+        if (e + 1 < rg.y) stash_cell(s_rec[buf ^ 1], per, lane, pre);
+        __syncwarp();
         buf ^= 1;
-        cur = nxt;
     }
     const long long HW = (long long)V.W * V.H;
     float *img = V.out ? V.out : out_rgb + 3 * V.pix_base;
@@ -222,9 +237,10 @@ void launch_blend_fwd(const ViewDesc *views, int n_views, int total_tiles, const
                       const uint32_t *tile_cells, const float4 *rec, const BlendParams &bp, float *out_rgb,
                       float *out_rgb2, float *out_D, int *out_nd, int K_all, cudaStream_t st) {
     if (total_tiles == 0) return;
-#define DGS_FWD(KV)                                                                                              \
-    k_blend_fwd<KV><<<total_tiles, FT, 0, st>>>(views, n_views, ranges, tile_cells, rec, bp, out_rgb, out_rgb2, \
-                                                out_D, out_nd)
+    const unsigned grid = (unsigned)total_tiles * WSUB;
+#define DGS_FWD(KV)                                                                                          \
+    k_blend_fwd<KV><<<grid, WT, 0, st>>>(views, n_views, ranges, tile_cells, rec, bp, out_rgb, out_rgb2, out_D, \
+                                         out_nd)
     switch (K_all) {
         case 8: DGS_FWD(8); break;
         case 10: DGS_FWD(10); break;
@@ -295,19 +311,13 @@ void launch_count_pairs(const ViewDesc *views, int n_views, int total_tiles, con
 //     dL/dv_n   = T_n (dN.A_n + dD B_n) - S_n sum_k alpha_k / (1 - v alpha_k)
 // then alpha = sigma G' (unless clamped) and G' = exp(-q/2).
 //
-// Phase 1 (thread = pixel) replays a chunk of cells, writing G' per
-// (Gaussian touching the tile, pixel) and T_n, S_n per (cell, pixel) to
-// shared memory.  Phase 2 (warp = Gaussian) walks only the pixels of the
-// Gaussian's AABB inside the tile, sums its nine screen-space gradients in
-// registers, reduces them across the warp with a transposed shuffle tree
-// (each step halves the values each lane carries) and issues one atomic add
-// per value.  Gaussians whose AABB misses the tile cost one flag test.
-constexpr int BW_G = 32;  // Gaussians per chunk (shared G' table = 32 x 256 floats)
-constexpr int BW_CH = 8;  // cells per chunk at most
-
-__host__ __device__ constexpr int bwd_cells_per_chunk(int K) {
-    return BW_G / K < 1 ? 1 : (BW_G / K > BW_CH ? BW_CH : BW_G / K);
-}
+// Same work unit as the forward (one warp per 16x4 sub-tile, two pixels per
+// lane, no inter-warp waits).  Per cell, the warp replays its pixels keeping
+// G' of the Gaussians that reach the sub-tile in registers, updates S and T,
+// then for each such Gaussian sums its pixels' nine screen-space gradient
+// terms across the warp with a transposed shuffle tree (each step halves the
+// values a lane carries) and adds the totals to global memory (one atomic
+// add per value per sub-tile).
 
 // Sum v[0..15] over the warp.  On return lane L holds the total of value
 // 8 b1 + 4 b2 + 2 b3 + b4 (b_i = bit i of L); lanes with b0 = 1 duplicate it.
@@ -331,217 +341,195 @@ __device__ __forceinline__ int transposed_owner(int lane) {
     return ((lane >> 1) & 1) * 8 + ((lane >> 2) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 4) & 1);
 }
 
-__global__ void __launch_bounds__(BT, 4) k_blend_bwd(const ViewDesc *__restrict__ views, int n_views,
+// Screen-space gradient terms of one (pixel, Gaussian) pair into acc[0..9]:
+// dmu_x dmu_y da db dc dsigma dr dg db, and the Gaussian's share of dL/dv.
+__device__ __forceinline__ void pair_grad(float acc[16], float Gv, float4 r0, float4 r1, float4 r2, float px, float py,
+                                          float Tn, float Sn, float e0, float e1, float e2, float eD, float alpha_max) {
+    const float v = r2.w, op = r1.w;
+    const float raw = op * Gv;
+    const float al = fminf(raw, alpha_max);
+    const float cA = v * Tn;
+    const float rom = __frcp_rn(1.0f - v * al);
+    const float dal = cA * (e0 * r2.x + e1 * r2.y + e2 * r2.z + eD) - v * Sn * rom;
+    const float ca_al = cA * al;
+    acc[6] += ca_al * e0;
+    acc[7] += ca_al * e1;
+    acc[8] += ca_al * e2;
+    acc[9] -= Sn * al * rom;
+    if (raw < alpha_max) {
+        const float ca = -2.0f * LN2 * r1.x, cb = -LN2 * r1.y, cc = -2.0f * LN2 * r1.z;  // real conic
+        acc[5] += dal * Gv;
+        const float dq = -0.5f * Gv * (dal * op);
+        const float dx = px - r0.x, dy = py - r0.y;
+        acc[0] -= dq * 2.0f * (ca * dx + cb * dy);
+        acc[1] -= dq * 2.0f * (cb * dx + cc * dy);
+        acc[2] += dq * dx * dx;
+        acc[3] += dq * 2.0f * dx * dy;
+        acc[4] += dq * dy * dy;
+    }
+}
+
+template <int KT>
+__global__ void __launch_bounds__(WT) k_blend_bwd(const ViewDesc *__restrict__ views, int n_views,
                                                   const uint2 *__restrict__ ranges, const uint32_t *__restrict__ cells,
                                                   const float4 *__restrict__ rec, BlendParams bp,
                                                   const float *__restrict__ rgb, const float *__restrict__ Dpix,
                                                   const int *__restrict__ ndpix, const float *__restrict__ dL_drgb,
                                                   float *__restrict__ g2d, float *__restrict__ g_cell_v) {
-    extern __shared__ float4 smem_f4[];
-    __shared__ int s_view, s_ndmax, s_task;
-    __shared__ int s_flag[2][BW_G];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int tile = blockIdx.x;
-    if (tid == 0) { s_view = find_view(views, n_views, tile); s_ndmax = 0; }
-    __syncthreads();
-    const ViewDesc &V = views[s_view];
-    const int K = V.K;
-    const int per = kRecF4 * K;
-    const int CH = bwd_cells_per_chunk(K);
-    const int nrec = CH * per;                     // float4s per chunk (<= 3 * BW_G < BT)
-    float4 *s_rec0 = smem_f4;                      // [2][nrec]
-    float4 *sdN = smem_f4 + 2 * nrec;              // [BT]: dL/dN xyz, dL/dD per pixel
-    float2 *sTS = reinterpret_cast<float2 *>(sdN + BT);  // [CH][BT]: T_n, S_n per (cell, pixel)
-    float *sG = reinterpret_cast<float *>(sTS + CH * BT);  // [CH*K][BT]
-    float *sTX = sG + CH * K * BT;                 // [CH][BT]: T_n X_n for dL/dv
+    __shared__ float4 s_rec[2][MAXPER];
+    const int lane = threadIdx.x;
+    const int tile = blockIdx.x / WSUB, sub = blockIdx.x % WSUB;
+    const int vi = find_view(views, n_views, tile);
+    const ViewDesc &V = views[vi];
     const int local = tile - V.tile_base;
     const int tx = local % V.Tx, ty = local / V.Tx;
-    const float tx0 = (float)(tx * kTile), ty0 = (float)(ty * kTile);
-    const int xi = tx * kTile + (tid & (kTile - 1)), yi = ty * kTile + (tid >> 4);
-    const bool inside = xi < V.W && yi < V.H;
-    const float px = (float)xi + 0.5f, py = (float)yi + 0.5f;
+    const float bx0 = (float)(tx * kTile), by0 = (float)(ty * kTile + WSUB * sub);
+    const int xi = tx * kTile + (lane & (kTile - 1));
+    const int yi[2] = {ty * kTile + WSUB * sub + 2 * (lane >> 4), ty * kTile + WSUB * sub + 2 * (lane >> 4) + 1};
+    const float px = (float)xi + 0.5f;
+    const float py[2] = {(float)yi[0] + 0.5f, (float)yi[1] + 0.5f};
     const long long HW = (long long)V.W * V.H;
-    const long long pin = (long long)yi * V.W + xi;
+    const int K = KT > 0 ? KT : V.K;
+    const int per = kRecF4 * K;
 
-    int nd = 0;
-    float dN0 = 0.f, dN1 = 0.f, dN2 = 0.f, dD = 0.f;
-    if (inside) {
-        const float Dv = Dpix[V.pix_base + pin];
-        if (Dv > bp.d_min) {
-            nd = ndpix[V.pix_base + pin];
-            const float *gi = dL_drgb + 3 * V.pix_base;
-            const float *ci = rgb + 3 * V.pix_base;
-            const float g0 = gi[pin], g1 = gi[HW + pin], g2 = gi[2 * HW + pin];
-            const float c0 = ci[pin], c1 = ci[HW + pin], c2 = ci[2 * HW + pin];
-            const float iD = 1.0f / Dv;
-            dN0 = g0 * iD; dN1 = g1 * iD; dN2 = g2 * iD;
-            dD = -(g0 * c0 + g1 * c1 + g2 * c2) * iD;
+    int nd[2] = {0, 0};
+    float e0[2] = {0.f, 0.f}, e1[2] = {0.f, 0.f}, e2[2] = {0.f, 0.f}, eD[2] = {0.f, 0.f};
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        if (xi < V.W && yi[q] < V.H) {
+            const long long pin = (long long)yi[q] * V.W + xi;
+            const float Dv = Dpix[V.pix_base + pin];
+            if (Dv > bp.d_min) {
+                nd[q] = ndpix[V.pix_base + pin];
+                const float *gi = dL_drgb + 3 * V.pix_base;
+                const float *ci = rgb + 3 * V.pix_base;
+                const float g0 = gi[pin], g1 = gi[HW + pin], g2 = gi[2 * HW + pin];
+                const float c0 = ci[pin], c1 = ci[HW + pin], c2 = ci[2 * HW + pin];
+                const float iD = 1.0f / Dv;
+                e0[q] = g0 * iD; e1[q] = g1 * iD; e2[q] = g2 * iD;
+                eD[q] = -(g0 * c0 + g1 * c1 + g2 * c2) * iD;
+            }
         }
     }
-    sdN[tid] = make_float4(dN0, dN1, dN2, dD);
-    if (nd > 0) atomicMax(&s_ndmax, nd);
-    __syncthreads();
+    const int ndmax = __reduce_max_sync(0xffffffffu, max(nd[0], nd[1]));
     const uint2 rg = ranges[tile];
-    const uint32_t end = rg.x + min((uint32_t)s_ndmax, rg.y - rg.x);
+    const uint32_t end = rg.x + min((uint32_t)ndmax, rg.y - rg.x);
     const float4 *vrec = rec + V.rec_base * kRecF4;
     const bool want_v = g_cell_v != nullptr;
+    constexpr int KR = KT > 0 ? KT : kMaxK;
 
-    float T = 1.0f, S = 0.0f;
-    float4 pre = make_float4(0.f, 0.f, 0.f, 0.f);
-    uint32_t cur = rg.x;
-    if (cur < end) {
-        pre = fetch_rec(vrec, cells, cur, end, tid, nrec, per, pre);
-        if (tid < nrec) {
-            s_rec0[tid] = pre;
-            if (tid % kRecF4 == 0) s_flag[0][tid / kRecF4] = row_span(pre, tx0, ty0);
-        }
+    float T[2] = {1.0f, 1.0f}, S[2] = {0.f, 0.f};
+    float4 pre[3];
+    if (rg.x < end) {
+        stage_cell(s_rec[0], vrec, cells, rg.x, per, lane, pre);
+        stash_cell(s_rec[0], per, lane, pre);
     }
-    __syncthreads();
+    __syncwarp();
     int buf = 0;
-    while (cur < end) {
-        const int nc = (int)min((uint32_t)CH, end - cur);
-        const uint32_t nxt = cur + nc;
-        if (nxt < end) pre = fetch_rec(vrec, cells, nxt, end, tid, nrec, per, pre);
-        const float4 *sr = s_rec0 + buf * nrec;
-        const int *fl = s_flag[buf];
-        // ---- phase 1: replay per pixel
-        if (tid == 0) s_task = 0;
-        for (int c = 0; c < nc; ++c) {
-            const int n = (int)(cur - rg.x) + c;
-            const float4 *r = sr + c * per;
-            if (n < nd) {
-                const float v = r[2].w;
-                float A0 = 0.f, A1 = 0.f, A2 = 0.f, B = 0.f, P = 1.0f;
-                for (int k = 0; k < K; ++k) {
-                    if (!rows_hit(fl[c * K + k], warp)) continue;
-                    const float4 r0 = r[3 * k];
-                    const float dx = px - r0.x, dy = py - r0.y;
-                    float Gv = 0.f;
-                    if (fabsf(dx) <= r0.z && fabsf(dy) <= r0.w) {
-                        const float4 r1 = r[3 * k + 1];
-                        const float4 r2 = r[3 * k + 2];
-                        Gv = ex2_approx(r1.x * dx * dx + r1.y * dx * dy + r1.z * dy * dy);
-                        const float al = fminf(r1.w * Gv, bp.alpha_max);
-                        A0 += al * r2.x; A1 += al * r2.y; A2 += al * r2.z;
-                        B += al;
-                        P -= P * (v * al);
-                    }
-                    sG[(c * K + k) * BT + tid] = Gv;
-                }
-                const float X = dN0 * A0 + dN1 * A1 + dN2 * A2 + dD * B;
-                S -= v * T * X;
-                sTS[c * BT + tid] = make_float2(T, S);
-                sTX[c * BT + tid] = T * X;
-                T *= P;
-            } else {
-                for (int k = 0; k < K; ++k)
-                    if (rows_hit(fl[c * K + k], warp)) sG[(c * K + k) * BT + tid] = 0.f;
-                sTX[c * BT + tid] = 0.f;
+    for (uint32_t e = rg.x; e < end; ++e) {
+        if (e + 1 < end) stage_cell(s_rec[buf ^ 1], vrec, cells, e + 1, per, lane, pre);
+        const int n = (int)(e - rg.x);
+        const bool a0 = n < nd[0], a1 = n < nd[1];
+        const float4 *r = s_rec[buf];
+        const float v = r[2].w;
+        unsigned mask = __ballot_sync(0xffffffffu, lane < K && touches_block(r[kRecF4 * lane], bx0, by0));
+        const int nhit = __popc(mask);
+        int kk[KR];
+        float G0[KR], G1[KR];
+        float A00 = 0.f, A01 = 0.f, A02 = 0.f, B0 = 0.f, P0 = 1.0f;
+        float A10 = 0.f, A11 = 0.f, A12 = 0.f, B1 = 0.f, P1 = 1.0f;
+#pragma unroll
+        for (int i = 0; i < KR; ++i) {
+            if (i >= nhit) break;
+            const int k = __ffs(mask) - 1;
+            mask &= mask - 1;
+            kk[i] = k;
+            G0[i] = 0.f;
+            G1[i] = 0.f;
+            const float4 r0 = r[3 * k];
+            const float dx = px - r0.x;
+            if (!(fabsf(dx) <= r0.z)) continue;
+            const float dy0 = py[0] - r0.y, dy1 = py[1] - r0.y;
+            const bool h0 = a0 && fabsf(dy0) <= r0.w;
+            const bool h1 = a1 && fabsf(dy1) <= r0.w;
+            if (!(h0 || h1)) continue;
+            const float4 r1 = r[3 * k + 1];
+            const float4 r2 = r[3 * k + 2];
+            const float qx = r1.x * dx * dx;
+            const float bxx = r1.y * dx;
+            if (h0) {
+                const float Gv = ex2_approx(qx + (bxx + r1.z * dy0) * dy0);
+                G0[i] = Gv;
+                const float al = fminf(r1.w * Gv, bp.alpha_max);
+                A00 += al * r2.x; A01 += al * r2.y; A02 += al * r2.z;
+                B0 += al;
+                P0 -= P0 * (v * al);
+            }
+            if (h1) {
+                const float Gv = ex2_approx(qx + (bxx + r1.z * dy1) * dy1);
+                G1[i] = Gv;
+                const float al = fminf(r1.w * Gv, bp.alpha_max);
+                A10 += al * r2.x; A11 += al * r2.y; A12 += al * r2.z;
+                B1 += al;
+                P1 -= P1 * (v * al);
             }
         }
-        __syncthreads();
-        // ---- phase 2: per Gaussian, over its AABB within the tile; warps take
-        // the next task from a shared counter so uneven windows balance out
-        const int n_tasks = nc * K + (want_v ? nc : 0);
-        for (;;) {
-            int j = 0;
-            if (lane == 0) j = atomicAdd(&s_task, 1);
-            j = __shfl_sync(0xffffffffu, j, 0);
-            if (j >= n_tasks) break;
-            if (j >= nc * K) {  // per-cell term of dL/dv: sum_p T_n X over the tile
-                const int c = j - nc * K;
-                float a = 0.f;
+        // per-pixel transmittance bookkeeping (S_n includes x_n)
+        const float X0 = e0[0] * A00 + e1[0] * A01 + e2[0] * A02 + eD[0] * B0;
+        const float X1 = e0[1] * A10 + e1[1] * A11 + e2[1] * A12 + eD[1] * B1;
+        const float Tn0 = T[0], Tn1 = T[1];
+        if (a0) { S[0] -= v * Tn0 * X0; T[0] *= P0; }
+        if (a1) { S[1] -= v * Tn1 * X1; T[1] *= P1; }
+        const uint32_t cellid = __ldg(cells + e);
+        if (want_v) {  // cell term of dL/dv: sum over pixels of T_n X_n
+            float a = (a0 ? Tn0 * X0 : 0.f) + (a1 ? Tn1 * X1 : 0.f);
 #pragma unroll
-                for (int q = 0; q < BT / 32; ++q) a += sTX[c * BT + lane + 32 * q];
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            if (lane == 0 && a != 0.f) atomicAdd(g_cell_v + cellid, a);
+        }
+        // gradient terms per Gaussian reaching the sub-tile
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-                if (lane == 0 && a != 0.f) atomicAdd(g_cell_v + cells[cur + c], a);
-                continue;
-            }
-            const int span = fl[j];
-            if ((span & 0xFF) > (span >> 8)) continue;  // misses the tile
-            const int c = j / K, k = j - c * K;
-            const float4 r0 = sr[c * per + 3 * k], r1 = sr[c * per + 3 * k + 1], r2 = sr[c * per + 3 * k + 2];
-            const float v = r2.w, op = r1.w;
-            const float ca = -2.0f * LN2 * r1.x, cb = -LN2 * r1.y, cc = -2.0f * LN2 * r1.z;  // real conic
-            // columns of the tile that can lie in the AABB (a superset; sG decides);
-            // rows [yl, yh] are exactly those whose warps wrote sG for this record
-            const int xl = (int)fmaxf(floorf(r0.x - r0.z - 0.5f - tx0) - 1.0f, 0.0f);
-            const int xh = (int)fminf(ceilf(r0.x + r0.z - 0.5f - tx0) + 1.0f, (float)(kTile - 1));
-            const int yl = span & 0xFF, yh = span >> 8;
-            const int w = xh - xl + 1;
-            const int npx = w * (yh - yl + 1);
-            const float inv_w = 1.0f / (float)w;
+        for (int i = 0; i < KR; ++i) {
+            if (i >= nhit) break;
+            const bool hit0 = G0[i] > 0.f, hit1 = G1[i] > 0.f;
+            if (!__any_sync(0xffffffffu, hit0 || hit1)) continue;
+            const int k = kk[i];
+            const float4 r0 = r[3 * k], r1 = r[3 * k + 1], r2 = r[3 * k + 2];
             float acc[16];
 #pragma unroll
-            for (int i = 0; i < 16; ++i) acc[i] = 0.f;
-            bool any = false;
-            for (int i = lane; i < npx; i += 32) {
-                const int row = (int)(((float)i + 0.5f) * inv_w);  // exact: i < 256, w <= 16
-                const int xx = xl + i - row * w, yy = yl + row;
-                const int p = yy * kTile + xx;
-                const float Gv = sG[j * BT + p];
-                if (Gv == 0.f) continue;
-                any = true;
-                const float2 ts = sTS[c * BT + p];
-                const float4 e = sdN[p];
-                const float raw = op * Gv;
-                const float al = fminf(raw, bp.alpha_max);
-                const float cA = v * ts.x;
-                const float rom = __frcp_rn(1.0f - v * al);
-                const float dal = cA * (e.x * r2.x + e.y * r2.y + e.z * r2.z + e.w) - v * ts.y * rom;
-                const float ca_al = cA * al;
-                acc[6] += ca_al * e.x;
-                acc[7] += ca_al * e.y;
-                acc[8] += ca_al * e.z;
-                acc[9] -= ts.y * al * rom;
-                if (raw < bp.alpha_max) {
-                    acc[5] += dal * Gv;
-                    const float dq = -0.5f * Gv * (dal * op);
-                    const float dx = (tx0 + (float)xx + 0.5f) - r0.x;
-                    const float dy = (ty0 + (float)yy + 0.5f) - r0.y;
-                    acc[0] -= dq * 2.0f * (ca * dx + cb * dy);
-                    acc[1] -= dq * 2.0f * (cb * dx + cc * dy);
-                    acc[2] += dq * dx * dx;
-                    acc[3] += dq * 2.0f * dx * dy;
-                    acc[4] += dq * dy * dy;
-                }
-            }
-            if (!__any_sync(0xffffffffu, any)) continue;
+            for (int j = 0; j < 16; ++j) acc[j] = 0.f;
+            if (hit0) pair_grad(acc, G0[i], r0, r1, r2, px, py[0], Tn0, S[0], e0[0], e1[0], e2[0], eD[0], bp.alpha_max);
+            if (hit1) pair_grad(acc, G1[i], r0, r1, r2, px, py[1], Tn1, S[1], e0[1], e1[1], e2[1], eD[1], bp.alpha_max);
             const float tot = transposed_warp_sum16(acc, lane);
             const int idx = transposed_owner(lane);
             if ((lane & 1) == 0 && tot != 0.f) {
-                const uint32_t cellid = cells[cur + c];
                 if (idx < 9) atomicAdd(g2d + (V.rec_base + (long long)cellid * K + k) * kGradF + idx, tot);
                 else if (idx == 9 && want_v) atomicAdd(g_cell_v + cellid, tot);
             }
         }
-        if (nxt < end && tid < nrec) {
-            s_rec0[(buf ^ 1) * nrec + tid] = pre;
-            if (tid % kRecF4 == 0) s_flag[buf ^ 1][tid / kRecF4] = row_span(pre, tx0, ty0);
-        }
-        __syncthreads();
+        __syncwarp();
+        if (e + 1 < end) stash_cell(s_rec[buf ^ 1], per, lane, pre);
+        __syncwarp();
         buf ^= 1;
-        cur = nxt;
     }
 }
 
-static size_t bwd_smem_bytes(int K) {
-    const int per = kRecF4 * K;
-    const int CH = bwd_cells_per_chunk(K);
-    return sizeof(float4) * (2 * CH * per + BT) + sizeof(float2) * CH * BT + sizeof(float) * ((size_t)CH * K * BT + CH * BT);
-}
-
-// K: Gaussians per cell of the chain's scene (shared-memory sizing)
-void launch_blend_bwd(const ViewDesc *views, int n_views, int total_tiles, int K, const uint2 *ranges,
+// K_all: K of the chain's scene (compile-time loop for common values)
+void launch_blend_bwd(const ViewDesc *views, int n_views, int total_tiles, int K_all, const uint2 *ranges,
                       const uint32_t *tile_cells, const float4 *rec, const BlendParams &bp, const float *rgb,
                       const float *D, const int *nd, const float *dL_drgb, float *g2d, float *g_cell_v,
                       cudaStream_t st) {
     if (total_tiles == 0) return;
-    const size_t sm = bwd_smem_bytes(K);
-    cudaFuncSetAttribute(k_blend_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_blend_bwd<<<total_tiles, BT, sm, st>>>(views, n_views, ranges, tile_cells, rec, bp, rgb, D, nd, dL_drgb, g2d,
-                                             g_cell_v);
+    const unsigned grid = (unsigned)total_tiles * WSUB;
+#define DGS_BWD(KV)                                                                                       \
+    k_blend_bwd<KV><<<grid, WT, 0, st>>>(views, n_views, ranges, tile_cells, rec, bp, rgb, D, nd, dL_drgb, g2d, \
+                                         g_cell_v)
+    switch (K_all) {
+        case 8: DGS_BWD(8); break;
+        case 10: DGS_BWD(10); break;
+        default: DGS_BWD(0); break;
+    }
+#undef DGS_BWD
 }
 
 }  // namespace dgs
