@@ -313,7 +313,8 @@ void launch_count_pairs(const ViewDesc *views, int n_views, int total_tiles, con
 //
 // Same work unit as the forward (one warp per 16x4 sub-tile, two pixels per
 // lane, no inter-warp waits).  Per cell, the warp replays its pixels keeping
-// G' of the Gaussians that reach the sub-tile in registers, updates S and T,
+// G' of the Gaussians that reach the sub-tile in warp-private shared memory
+// (registers stay below ~80 so 24 warps fit per SM), updates S and T,
 // then for each such Gaussian sums its pixels' nine screen-space gradient
 // terms across the warp with a transposed shuffle tree (each step halves the
 // values a lane carries) and adds the totals to global memory (one atomic
@@ -370,13 +371,15 @@ __device__ __forceinline__ void pair_grad(float acc[16], float Gv, float4 r0, fl
 }
 
 template <int KT>
-__global__ void __launch_bounds__(WT) k_blend_bwd(const ViewDesc *__restrict__ views, int n_views,
+__global__ void __launch_bounds__(WT, 24) k_blend_bwd(const ViewDesc *__restrict__ views, int n_views,
                                                   const uint2 *__restrict__ ranges, const uint32_t *__restrict__ cells,
                                                   const float4 *__restrict__ rec, BlendParams bp,
                                                   const float *__restrict__ rgb, const float *__restrict__ Dpix,
                                                   const int *__restrict__ ndpix, const float *__restrict__ dL_drgb,
                                                   float *__restrict__ g2d, float *__restrict__ g_cell_v) {
     __shared__ float4 s_rec[2][MAXPER];
+    constexpr int KRS = KT > 0 ? KT : kMaxK;
+    __shared__ float s_G[2][KRS][WT];
     const int lane = threadIdx.x;
     const int tile = blockIdx.x / WSUB, sub = blockIdx.x % WSUB;
     const int vi = find_view(views, n_views, tile);
@@ -435,7 +438,7 @@ __global__ void __launch_bounds__(WT) k_blend_bwd(const ViewDesc *__restrict__ v
         unsigned mask = __ballot_sync(0xffffffffu, lane < K && touches_block(r[kRecF4 * lane], bx0, by0));
         const int nhit = __popc(mask);
         int kk[KR];
-        float G0[KR], G1[KR];
+        float *G0 = &s_G[0][0][0], *G1 = &s_G[1][0][0];
         float A00 = 0.f, A01 = 0.f, A02 = 0.f, B0 = 0.f, P0 = 1.0f;
         float A10 = 0.f, A11 = 0.f, A12 = 0.f, B1 = 0.f, P1 = 1.0f;
 #pragma unroll
@@ -444,8 +447,8 @@ __global__ void __launch_bounds__(WT) k_blend_bwd(const ViewDesc *__restrict__ v
             const int k = __ffs(mask) - 1;
             mask &= mask - 1;
             kk[i] = k;
-            G0[i] = 0.f;
-            G1[i] = 0.f;
+            G0[i * WT + lane] = 0.f;
+            G1[i * WT + lane] = 0.f;
             const float4 r0 = r[3 * k];
             const float dx = px - r0.x;
             if (!(fabsf(dx) <= r0.z)) continue;
@@ -459,7 +462,7 @@ __global__ void __launch_bounds__(WT) k_blend_bwd(const ViewDesc *__restrict__ v
             const float bxx = r1.y * dx;
             if (h0) {
                 const float Gv = ex2_approx(qx + (bxx + r1.z * dy0) * dy0);
-                G0[i] = Gv;
+                G0[i * WT + lane] = Gv;
                 const float al = fminf(r1.w * Gv, bp.alpha_max);
                 A00 += al * r2.x; A01 += al * r2.y; A02 += al * r2.z;
                 B0 += al;
@@ -467,7 +470,7 @@ __global__ void __launch_bounds__(WT) k_blend_bwd(const ViewDesc *__restrict__ v
             }
             if (h1) {
                 const float Gv = ex2_approx(qx + (bxx + r1.z * dy1) * dy1);
-                G1[i] = Gv;
+                G1[i * WT + lane] = Gv;
                 const float al = fminf(r1.w * Gv, bp.alpha_max);
                 A10 += al * r2.x; A11 += al * r2.y; A12 += al * r2.z;
                 B1 += al;
@@ -491,15 +494,16 @@ __global__ void __launch_bounds__(WT) k_blend_bwd(const ViewDesc *__restrict__ v
 #pragma unroll
         for (int i = 0; i < KR; ++i) {
             if (i >= nhit) break;
-            const bool hit0 = G0[i] > 0.f, hit1 = G1[i] > 0.f;
+            const float g0v = G0[i * WT + lane], g1v = G1[i * WT + lane];
+            const bool hit0 = g0v > 0.f, hit1 = g1v > 0.f;
             if (!__any_sync(0xffffffffu, hit0 || hit1)) continue;
             const int k = kk[i];
             const float4 r0 = r[3 * k], r1 = r[3 * k + 1], r2 = r[3 * k + 2];
             float acc[16];
 #pragma unroll
             for (int j = 0; j < 16; ++j) acc[j] = 0.f;
-            if (hit0) pair_grad(acc, G0[i], r0, r1, r2, px, py[0], Tn0, S[0], e0[0], e1[0], e2[0], eD[0], bp.alpha_max);
-            if (hit1) pair_grad(acc, G1[i], r0, r1, r2, px, py[1], Tn1, S[1], e0[1], e1[1], e2[1], eD[1], bp.alpha_max);
+            if (hit0) pair_grad(acc, g0v, r0, r1, r2, px, py[0], Tn0, S[0], e0[0], e1[0], e2[0], eD[0], bp.alpha_max);
+            if (hit1) pair_grad(acc, g1v, r0, r1, r2, px, py[1], Tn1, S[1], e0[1], e1[1], e2[1], eD[1], bp.alpha_max);
             const float tot = transposed_warp_sum16(acc, lane);
             const int idx = transposed_owner(lane);
             if ((lane & 1) == 0 && tot != 0.f) {
