@@ -51,6 +51,20 @@ def load_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def measured_traffic(kernel, views):
+    """DRAM bytes per launch from the committed ncu record, if the kernel
+    source is unchanged since the capture (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic_blend_bwd.json")
+    if kernel != "blend_bwd" or not os.path.exists(path):
+        return None
+    rec = json.load(open(path))
+    src = os.path.join(ROOT, rec["source"])
+    if hashlib.sha256(open(src, "rb").read()).hexdigest() != rec["sha256"]:
+        return None
+    return rec["bytes_per_launch"] * views / rec["views_in_capture"]
+
+
 def fp32_peak_tflops(sm_mhz):
     # 152 SMs x 128 FP32 lanes x 2 FLOP per FMA x clock
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
@@ -323,8 +337,11 @@ def main():
         ach = flop / (stage_ms[dom] / 1e3) / 1e12
         peak = fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
         roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": None, "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x max SM clock",
-                "flop_per_launch": flop}
+                "traffic": measured_traffic(dom, nv),
+                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x max SM clock (2070 MHz)",
+                "flop_per_launch": flop, "flop_per_unit": FLOP_FWD if dom == "blend_fwd" else FLOP_BWD,
+                "units_per_launch": cnt["inbox_rendered"], "unit_def": "(pixel, Gaussian) pairs inside the AABB of "
+                                                                        "blended cells"}
     else:
         nbytes = {"project_fwd": G * (59 * 4) + nv * G * 48, "project_bwd": G * (59 * 4) * 2 + nv * G * 96}
         b = nbytes.get(dom, 0)
