@@ -174,7 +174,8 @@ dgs_status dgs_loss_l1(dgs_ctx *ctx, const float *rgb, const float *target, int6
  *   DGS_BUF_CELL_DEPTH  float [V][N]     view depth of the cell centre
  *   DGS_BUF_TILE_CELLS  uint32 [L]       cell ids, ordered by (global tile, depth, cell)
  *   DGS_BUF_TILE_RANGES uint32 [T][2]    [start,end) per global tile (view-major tiles)
- *   DGS_BUF_GAUSS_REC   float [V][G][12] mu_x mu_y ext_x ext_y | conic*(-log2 e/2, -log2 e, -log2 e/2) opacity | r g b v
+ *   DGS_BUF_GAUSS_REC   float [V][G][12] mu_x mu_y ext_x ext_y | k p, k r, k t, opacity | r g b v
+ *                       where the conic Sigma'^-1 = L L^T, L = [[p, 0], [r, t]], k = sqrt(log2(e)/2)
  *   DGS_BUF_PIX_D       float [P]        per-pixel weight sum D (P = all views' pixels)
  *   DGS_BUF_PIX_NDONE   int32 [P]        per-pixel number of blended cells
  *   DGS_BUF_GRAD2D      float [V][G][12] after backward: dmu_x dmu_y da db dc dsigma dr dg db 0 0 0

@@ -173,16 +173,17 @@ __global__ void __launch_bounds__(WT) k_blend_fwd(const ViewDesc *__restrict__ v
             if (!(h0 || h1)) continue;
             const float4 r1 = r[3 * k + 1];
             const float4 r2 = r[3 * k + 2];
-            const float qx = r1.x * dx * dx;
-            const float bxx = r1.y * dx;
+            const float pdx = r1.x * dx;
             if (h0) {
-                const float al = fminf(r1.w * ex2_approx(qx + (bxx + r1.z * dy0) * dy0), bp.alpha_max);
+                const float s1 = fmaf(r1.y, dy0, pdx), s2 = r1.z * dy0;
+                const float al = fminf(r1.w * ex2_approx(-fmaf(s1, s1, s2 * s2)), bp.alpha_max);
                 A00 += al * r2.x; A01 += al * r2.y; A02 += al * r2.z;
                 B0 += al;
                 P0 -= P0 * (v * al);
             }
             if (h1) {
-                const float al = fminf(r1.w * ex2_approx(qx + (bxx + r1.z * dy1) * dy1), bp.alpha_max);
+                const float s1 = fmaf(r1.y, dy1, pdx), s2 = r1.z * dy1;
+                const float al = fminf(r1.w * ex2_approx(-fmaf(s1, s1, s2 * s2)), bp.alpha_max);
                 A10 += al * r2.x; A11 += al * r2.y; A12 += al * r2.z;
                 B1 += al;
                 P1 -= P1 * (v * al);
@@ -358,12 +359,15 @@ __device__ __forceinline__ void pair_grad(float acc[16], float Gv, float4 r0, fl
     acc[8] += ca_al * e2;
     acc[9] -= Sn * al * rom;
     if (raw < alpha_max) {
-        const float ca = -2.0f * LN2 * r1.x, cb = -LN2 * r1.y, cc = -2.0f * LN2 * r1.z;  // real conic
         acc[5] += dal * Gv;
         const float dq = -0.5f * Gv * (dal * op);
         const float dx = px - r0.x, dy = py - r0.y;
-        acc[0] -= dq * 2.0f * (ca * dx + cb * dy);
-        acc[1] -= dq * 2.0f * (cb * dx + cc * dy);
+        // q = |L^T d|^2 with the record's L scaled by kappa (kappa^2 = log2(e)/2):
+        // dq/dmu = -2 Q d = -(2/kappa^2) L (s1, s2)
+        const float s1 = fmaf(r1.y, dy, r1.x * dx), s2 = r1.z * dy;
+        const float dqs = dq * (2.0f * 2.0f * LN2);  // 2 / kappa^2 = 4 ln 2
+        acc[0] -= dqs * (r1.x * s1);
+        acc[1] -= dqs * fmaf(r1.y, s1, r1.z * s2);
         acc[2] += dq * dx * dx;
         acc[3] += dq * 2.0f * dx * dy;
         acc[4] += dq * dy * dy;
@@ -458,10 +462,10 @@ __global__ void __launch_bounds__(WT, 24) k_blend_bwd(const ViewDesc *__restrict
             if (!(h0 || h1)) continue;
             const float4 r1 = r[3 * k + 1];
             const float4 r2 = r[3 * k + 2];
-            const float qx = r1.x * dx * dx;
-            const float bxx = r1.y * dx;
+            const float pdx = r1.x * dx;
             if (h0) {
-                const float Gv = ex2_approx(qx + (bxx + r1.z * dy0) * dy0);
+                const float s1 = fmaf(r1.y, dy0, pdx), s2 = r1.z * dy0;
+                const float Gv = ex2_approx(-fmaf(s1, s1, s2 * s2));
                 G0[i * WT + lane] = Gv;
                 const float al = fminf(r1.w * Gv, bp.alpha_max);
                 A00 += al * r2.x; A01 += al * r2.y; A02 += al * r2.z;
@@ -469,7 +473,8 @@ __global__ void __launch_bounds__(WT, 24) k_blend_bwd(const ViewDesc *__restrict
                 P0 -= P0 * (v * al);
             }
             if (h1) {
-                const float Gv = ex2_approx(qx + (bxx + r1.z * dy1) * dy1);
+                const float s1 = fmaf(r1.y, dy1, pdx), s2 = r1.z * dy1;
+                const float Gv = ex2_approx(-fmaf(s1, s1, s2 * s2));
                 G1[i * WT + lane] = Gv;
                 const float al = fminf(r1.w * Gv, bp.alpha_max);
                 A10 += al * r2.x; A11 += al * r2.y; A12 += al * r2.z;

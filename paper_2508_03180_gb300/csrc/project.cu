@@ -31,6 +31,7 @@ constexpr float SH_C3c = 0.4570457994644658f;   // (1/4) sqrt(21/(2 pi))
 constexpr float SH_C3d = 0.3731763325901154f;   // (1/4) sqrt(7/pi)
 constexpr float SH_C3e = 1.445305721320277f;    // (1/4) sqrt(105/pi)
 constexpr float LOG2E = 1.4426950408889634f;
+constexpr float KAPPA = 0.8493218002880191f;  // sqrt(log2(e) / 2)
 
 __device__ __forceinline__ void sh_eval(float x, float y, float z, int deg, float Y[16]) {
 #pragma unroll
@@ -93,9 +94,37 @@ __device__ __forceinline__ GaussIn load_gauss(const float *__restrict__ gp, long
 // Fixed-order FP32 part shared by forward and backward: view-space mean,
 // J, T = J R_view, 3D covariance, and the diagonal of Sigma'.
 struct ProjCore {
-    float t[3], x, y, xc, yc, J00, J02, J11, J12, T[6], Rg[9], S[9], V[6], sxx, syy;
+    float t[3], x, y, xc, yc, J00, J02, J11, J12, T[6], Rg[9], M[9], S[9], V[6], sxx, syy;
     bool valid;
 };
+
+// Screen covariance without cancellation: with U = T M (2x3, rows u and w),
+// Sigma' = U U^T + dilation I, so s_xx = |u|^2 + d, s_yy = |w|^2 + d, s_xy = u.w
+// and det = |u x w|^2 + d (|u|^2 + |w|^2) + d^2 (Lagrange's identity), a sum of
+// non-negative terms.  (The fixed-order s_xx, s_yy of ProjCore serve only the
+// AABB extents.)
+struct ScreenCov {
+    float u[3], w[3], sxx, syy, sxy, det;
+};
+
+__device__ __forceinline__ ScreenCov screen_cov(const ProjCore &c, float dilation) {
+    ScreenCov q;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        q.u[j] = c.T[0] * c.M[j] + c.T[1] * c.M[3 + j] + c.T[2] * c.M[6 + j];
+        q.w[j] = c.T[3] * c.M[j] + c.T[4] * c.M[3 + j] + c.T[5] * c.M[6 + j];
+    }
+    const float uu = q.u[0] * q.u[0] + q.u[1] * q.u[1] + q.u[2] * q.u[2];
+    const float ww = q.w[0] * q.w[0] + q.w[1] * q.w[1] + q.w[2] * q.w[2];
+    q.sxy = q.u[0] * q.w[0] + q.u[1] * q.w[1] + q.u[2] * q.w[2];
+    const float x0 = q.u[1] * q.w[2] - q.u[2] * q.w[1];
+    const float x1 = q.u[2] * q.w[0] - q.u[0] * q.w[2];
+    const float x2 = q.u[0] * q.w[1] - q.u[1] * q.w[0];
+    q.sxx = uu + dilation;
+    q.syy = ww + dilation;
+    q.det = (x0 * x0 + x1 * x1 + x2 * x2) + dilation * (uu + ww) + dilation * dilation;
+    return q;
+}
 
 __device__ __forceinline__ void proj_core(const ViewDesc &Vw, const GaussIn &p, float dilation, ProjCore &c) {
     xform_s(Vw.R, Vw.t, p.mean[0], p.mean[1], p.mean[2], c.t);
@@ -104,7 +133,7 @@ __device__ __forceinline__ void proj_core(const ViewDesc &Vw, const GaussIn &p, 
     c.x = fdiv_s(c.t[0], c.t[2]);
     c.y = fdiv_s(c.t[1], c.t[2]);
     rot_from_quat_s(p.quat[0], p.quat[1], p.quat[2], p.quat[3], c.Rg);
-    float M[9];
+    float *M = c.M;
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -172,9 +201,12 @@ __global__ void __launch_bounds__(128) k_project_fwd(const ViewDesc *__restrict_
                 const float my = fadd_s(fmul_s(Vw.fy, c.y), Vw.cy);
                 const float ex = fmul_s(bp.ksigma, fsqrt_s(c.sxx));
                 const float ey = fmul_s(bp.ksigma, fsqrt_s(c.syy));
-                const float sxy = c.V[0] * c.T[3] + c.V[1] * c.T[4] + c.V[2] * c.T[5];
-                const float inv = 1.0f / (c.sxx * c.syy - sxy * sxy);
-                const float ca = c.syy * inv, cb = -sxy * inv, cc = c.sxx * inv;
+                // conic Q = Sigma'^-1 = L L^T, L = [[p, 0], [r, t]]:
+                // p = sqrt(s_yy/det), r = -s_xy/sqrt(s_yy det), t = 1/sqrt(s_yy),
+                // so q(d) = (p dx + r dy)^2 + (t dy)^2 is a sum of squares
+                const ScreenCov sc2 = screen_cov(c, bp.dilation);
+                const float ip = rsqrtf(sc2.syy * sc2.det);
+                const float fp = sc2.syy * ip, fr = -sc2.sxy * ip, ft = rsqrtf(sc2.syy);
                 float d0 = p.mean[0] - Vw.eye[0], d1 = p.mean[1] - Vw.eye[1], d2 = p.mean[2] - Vw.eye[2];
                 const float il = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
                 d0 *= il; d1 *= il; d2 *= il;
@@ -189,8 +221,9 @@ __global__ void __launch_bounds__(128) k_project_fwd(const ViewDesc *__restrict_
                     col[ch] = fmaxf(s, 0.0f);
                 }
                 r0 = make_float4(mx, my, ex, ey);
-                // conic pre-scaled so that G' = exp2(r1.x dx^2 + r1.y dx dy + r1.z dy^2)
-                r1 = make_float4(-0.5f * LOG2E * ca, -LOG2E * cb, -0.5f * LOG2E * cc, opac);
+                // L scaled by kappa = sqrt(log2(e)/2): G' = exp2(-(s1^2 + s2^2)),
+                // s1 = r1.x dx + r1.y dy, s2 = r1.z dy
+                r1 = make_float4(KAPPA * fp, KAPPA * fr, KAPPA * ft, opac);
                 r2 = make_float4(col[0], col[1], col[2], cv);
             }
             float4 *o = rec + (Vw.rec_base + g) * kRecF4;
@@ -290,31 +323,45 @@ __global__ void __launch_bounds__(128) k_project_bwd(const ViewDesc *__restrict_
                     gm[1] += (gd[1] - dd * d1) * il;
                     gm[2] += (gd[2] - dd * d2) * il;
                 }
-                // conic -> Sigma' (H = -Q G_Q Q, G_Q = [[ga, gb/2], [gb/2, gc]])
-                const float sxy = c.V[0] * c.T[3] + c.V[1] * c.T[4] + c.V[2] * c.T[5];
-                const float inv = 1.0f / (c.sxx * c.syy - sxy * sxy);
-                const float qa = c.syy * inv, qb = -sxy * inv, qc = c.sxx * inv;
-                const float P00 = gca * qa + 0.5f * gcb * qb, P01 = gca * qb + 0.5f * gcb * qc;
-                const float P10 = 0.5f * gcb * qa + gcc * qb, P11 = 0.5f * gcb * qb + gcc * qc;
-                const float H00 = -(qa * P00 + qb * P10), H01 = -(qa * P01 + qb * P11), H11 = -(qb * P01 + qc * P11);
-                // Sigma' = T Sigma T^T:  dL/dSigma = T^T H T,  dL/dT = 2 H T Sigma
-                float HT[6];  // H T (2x3)
-#pragma unroll
-                for (int j = 0; j < 3; ++j) {
-                    HT[j] = H00 * c.T[j] + H01 * c.T[3 + j];
-                    HT[3 + j] = H01 * c.T[j] + H11 * c.T[3 + j];
+                // conic -> Sigma' (H = -Q G_Q Q, G_Q = [[ga, gb/2], [gb/2, gc]]), then
+                // dL/dU = 2 H U.  For needle-like Gaussians the rows of U are nearly
+                // parallel and H U cancels heavily, so this block runs in FP64.
+                const ScreenCov sc2 = screen_cov(c, bp.dilation);
+                float gU[6];
+                {
+                    const double u0 = sc2.u[0], u1 = sc2.u[1], u2 = sc2.u[2];
+                    const double w0 = sc2.w[0], w1 = sc2.w[1], w2 = sc2.w[2];
+                    const double uu = u0 * u0 + u1 * u1 + u2 * u2, ww = w0 * w0 + w1 * w1 + w2 * w2;
+                    const double uw = u0 * w0 + u1 * w1 + u2 * w2;
+                    const double x0 = u1 * w2 - u2 * w1, x1 = u2 * w0 - u0 * w2, x2 = u0 * w1 - u1 * w0;
+                    const double dd = bp.dilation;
+                    const double det = (x0 * x0 + x1 * x1 + x2 * x2) + dd * (uu + ww) + dd * dd;
+                    const double inv = 1.0 / det;
+                    const double qa = (ww + dd) * inv, qb = -uw * inv, qc = (uu + dd) * inv;
+                    const double ga = gca, gb = gcb, gc = gcc;
+                    const double P00 = ga * qa + 0.5 * gb * qb, P01 = ga * qb + 0.5 * gb * qc;
+                    const double P10 = 0.5 * gb * qa + gc * qb, P11 = 0.5 * gb * qb + gc * qc;
+                    const double H00 = -(qa * P00 + qb * P10), H01 = -(qa * P01 + qb * P11);
+                    const double H11 = -(qb * P01 + qc * P11);
+                    gU[0] = (float)(2.0 * (H00 * u0 + H01 * w0));
+                    gU[1] = (float)(2.0 * (H00 * u1 + H01 * w1));
+                    gU[2] = (float)(2.0 * (H00 * u2 + H01 * w2));
+                    gU[3] = (float)(2.0 * (H01 * u0 + H11 * w0));
+                    gU[4] = (float)(2.0 * (H01 * u1 + H11 * w1));
+                    gU[5] = (float)(2.0 * (H01 * u2 + H11 * w2));
                 }
-                float gSig[9];
-#pragma unroll
-                for (int i = 0; i < 3; ++i)
-#pragma unroll
-                    for (int j = 0; j < 3; ++j) gSig[3 * i + j] = c.T[i] * HT[j] + c.T[3 + i] * HT[3 + j];
+                // Sigma' = U U^T + d I, U = T M:  dL/dT = dL/dU M^T,  dL/dM = T^T dL/dU
                 float gT[6];
 #pragma unroll
                 for (int a = 0; a < 2; ++a)
 #pragma unroll
                     for (int j = 0; j < 3; ++j)
-                        gT[3 * a + j] = 2.0f * (HT[3 * a] * c.S[j] + HT[3 * a + 1] * c.S[3 + j] + HT[3 * a + 2] * c.S[6 + j]);
+                        gT[3 * a + j] = gU[3 * a] * c.M[3 * j] + gU[3 * a + 1] * c.M[3 * j + 1] + gU[3 * a + 2] * c.M[3 * j + 2];
+                float gMm[9];
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) gMm[3 * j + k] = c.T[j] * gU[k] + c.T[3 + j] * gU[3 + k];
                 // T = J R_view
                 const float gJ00 = gT[0] * Vw.R[0] + gT[1] * Vw.R[1] + gT[2] * Vw.R[2];
                 const float gJ02 = gT[0] * Vw.R[6] + gT[1] * Vw.R[7] + gT[2] * Vw.R[8];
@@ -343,16 +390,14 @@ __global__ void __launch_bounds__(128) k_project_bwd(const ViewDesc *__restrict_
                 // t = R mu + t_cam
 #pragma unroll
                 for (int j = 0; j < 3; ++j) gm[j] += Vw.R[j] * gt[0] + Vw.R[3 + j] * gt[1] + Vw.R[6 + j] * gt[2];
-                // Sigma = M M^T, M = R(q) diag(s):  dL/dM = 2 dL/dSigma M
+                // M = R(q) diag(s)
                 float gR[9];
 #pragma unroll
                 for (int i = 0; i < 3; ++i)
 #pragma unroll
                     for (int j = 0; j < 3; ++j) {
-                        const float gM = 2.0f * (gSig[3 * i] * c.Rg[j] * p.scale[j] + gSig[3 * i + 1] * c.Rg[3 + j] * p.scale[j] +
-                                                 gSig[3 * i + 2] * c.Rg[6 + j] * p.scale[j]);
-                        gs[j] += gM * c.Rg[3 * i + j];
-                        gR[3 * i + j] = gM * p.scale[j];
+                        gs[j] += gMm[3 * i + j] * c.Rg[3 * i + j];
+                        gR[3 * i + j] = gMm[3 * i + j] * p.scale[j];
                     }
                 // R(q_hat), then q_hat = q / |q|
                 const float qn = sqrtf(p.quat[0] * p.quat[0] + p.quat[1] * p.quat[1] + p.quat[2] * p.quat[2] + p.quat[3] * p.quat[3]);

@@ -50,12 +50,15 @@ def check_view(scene, cam_obj, gv, cells_all, img, check_image=True, tile_rows=N
     pv = oracle.prepare_view(scene, cam, tile_rows=tile_rows)
     pr = pv["proj"]
     # conic / opacity / colour of the records vs FP64
-    conic = np.stack([rec[:, 4] / (-0.5 * LOG2E), rec[:, 5] / (-LOG2E), rec[:, 6] / (-0.5 * LOG2E)], 1)
+    # the record holds the conic's Cholesky factor L = [[p, 0], [r, t]] scaled by
+    # kappa = sqrt(log2(e)/2): a = p^2, b = p r, c = r^2 + t^2 (divided by kappa^2)
+    k2 = 0.5 * LOG2E
+    pp, rr, tt = (rec[:, 4].astype(np.float64), rec[:, 5].astype(np.float64), rec[:, 6].astype(np.float64))
+    conic = np.stack([pp * pp / k2, pp * rr / k2, (rr * rr + tt * tt) / k2], 1)
     m = pv["mask"]
-    # each entry within 2e-4 of the conic's own scale (FP32 cancellation in the
-    # off-diagonal of strongly correlated Gaussians is relative to the matrix)
+    # each entry within 1e-4 of the conic's own scale
     scale = np.maximum(np.abs(pr["conic"][m][:, 0]), np.abs(pr["conic"][m][:, 2]))[:, None]
-    assert np.all(np.abs(conic[m] - pr["conic"][m]) <= 2e-4 * scale), "conic differs"
+    assert np.all(np.abs(conic[m] - pr["conic"][m]) <= 1e-4 * scale), "conic differs"
     np.testing.assert_allclose(rec[m, 7], pr["opac"][m], rtol=1e-5, atol=1e-7)
     np.testing.assert_allclose(rec[m, 8:11], pr["rgb"][m], rtol=1e-4, atol=2e-5)
     r = oracle.render_view(scene, cam, forced_ndone=gv["nd"], pv=pv)
