@@ -315,7 +315,7 @@ void launch_count_pairs(const ViewDesc *views, int n_views, int total_tiles, con
 // Same work unit as the forward (one warp per 16x4 sub-tile, two pixels per
 // lane, no inter-warp waits).  Per cell, the warp replays its pixels keeping
 // G' of the Gaussians that reach the sub-tile in warp-private shared memory
-// (registers stay below ~80 so 24 warps fit per SM), updates S and T,
+// (registers capped at 64 so 32 warps fit per SM), updates S and T,
 // then for each such Gaussian sums its pixels' nine screen-space gradient
 // terms across the warp with a transposed shuffle tree (each step halves the
 // values a lane carries) and adds the totals to global memory (one atomic
@@ -375,7 +375,7 @@ __device__ __forceinline__ void pair_grad(float acc[16], float Gv, float4 r0, fl
 }
 
 template <int KT>
-__global__ void __launch_bounds__(WT, 24) k_blend_bwd(const ViewDesc *__restrict__ views, int n_views,
+__global__ void __launch_bounds__(WT, 32) k_blend_bwd(const ViewDesc *__restrict__ views, int n_views,
                                                   const uint2 *__restrict__ ranges, const uint32_t *__restrict__ cells,
                                                   const float4 *__restrict__ rec, BlendParams bp,
                                                   const float *__restrict__ rgb, const float *__restrict__ Dpix,
