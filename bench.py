@@ -220,12 +220,14 @@ def serving_bench(rctx, rates=(200.0, 1000.0, 2500.0, 5000.0), n_req=400, seed=0
     gaps = rng.exponential(1.0, n_req)
     outs = [torch.empty(3 * H * W, device="cuda") for (_, _, W, H) in reqs]
 
-    def run(max_batch, rate):
+    def run(max_batch, rate, graphs=True):
         arrivals = np.cumsum(gaps / rate)
-        rctx.serve_start(max_batch=max_batch, queue_cap=8192)
-        for k in range(4):  # warm-up: one request of each resolution class
-            t = rctx.submit(reqs[k][0], reqs[k][1], outs[k])
+        rctx.serve_start(max_batch=max_batch, queue_cap=8192, graphs=graphs)
+        # warm-up: the whole trace as one burst, so buffers reach their
+        # capacities and the graphs of the scene sets exist before timing
+        for t in [rctx.submit(sid, cam, outs[i]) for i, (sid, cam, W, H) in enumerate(reqs)]:
             rctx.poll(t, -1)
+        st0 = rctx.serve_stats()
         t0 = time.perf_counter()
         tickets = []
         for i, (sid, cam, W, H) in enumerate(reqs):
@@ -239,15 +241,23 @@ def serving_bench(rctx, rates=(200.0, 1000.0, 2500.0, 5000.0), n_req=400, seed=0
             lat.append(r.t_done_ms - r.t_submit_ms)
             bs.append(r.batch_size)
         t_end = time.perf_counter()
+        st1 = rctx.serve_stats()
         rctx.serve_stop()
         return {"offered_rps": rate, "p50_ms": float(np.percentile(lat, 50)),
                 "p99_ms": float(np.percentile(lat, 99)), "fps": n_req / (t_end - t0),
-                "mean_batch": float(np.mean(bs))}
+                "mean_batch": float(np.mean(bs)), "batches": st1["batches"] - st0["batches"],
+                "graph_captures": st1["graphs_captured"] - st0["graphs_captured"],
+                "overflow_reruns": st1["overflow_retries"] - st0["overflow_retries"]}
 
     out = {"workload": "3 resident scenes (100k, 500k, 2M Gaussians), Poisson arrivals, 640x480..3840x2160",
-           "requests_per_rate": n_req, "batched": [], "one_at_a_time": []}
+           "requests_per_rate": n_req,
+           "modes": {"batched": "up to 8 views per chain, each batch one CUDA-graph replay",
+                     "batched_no_graph": "up to 8 views per chain, plain launches, sort length read back midway",
+                     "one_at_a_time": "one view per chain, CUDA-graph replay"},
+           "batched": [], "batched_no_graph": [], "one_at_a_time": []}
     for rate in rates:
         out["batched"].append(run(8, rate))
+        out["batched_no_graph"].append(run(8, rate, graphs=False))
         out["one_at_a_time"].append(run(1, rate))
     for s in sids:
         rctx.release_scene(s)

@@ -249,7 +249,7 @@ dgs_status dgs_profile_read(dgs_ctx *ctx, dgs_profile *out);
  * keys/vals device pointers sorted in place, no context needed), except:
  *   * n is at most 1,048,576; a larger n returns DGS_ERR_CAPACITY before any
  *     work is enqueued.
- *   * Scratch is a fixed file-scope device array (about 8.3 MB) that every
+ *   * Scratch is a fixed file-scope device array (about 8.6 MB) that every
  *     GPU loading this library holds until the process exits; this call
  *     calls no cudaMalloc, cudaFree or other allocating routine.
  *   * The first call on a device looks up that array's device address
@@ -282,14 +282,39 @@ typedef struct {
 } dgs_result;
 
 /* Start the serving worker (max_batch views per launch chain, queue_cap
- * pending requests).  Idempotent. */
-dgs_status dgs_serve_start(dgs_ctx *ctx, int32_t max_batch, int32_t queue_cap);
+ * pending requests).  Idempotent.
+ *
+ * By default every batch is one replay of a captured CUDA graph of the whole
+ * forward chain: each of the worker's streams keeps buffers sized for the
+ * largest batch seen so far (plus headroom) and one graph per set of scenes
+ * in a batch; the batch's views and sizes are copied to the device by the
+ * graph's first nodes and every kernel reads its sizes there, so no host
+ * synchronisation separates binning from blending.  If the (tile, cell)
+ * pairs of a batch exceed the buffers, the kernels stop at the capacity, the
+ * worker sees the overflow flag when the batch finishes, grows the buffers,
+ * captures again and re-runs the batch before reporting it.
+ * flags: DGS_SERVE_NO_GRAPHS runs every batch as a plain launch chain that
+ * reads the sort length back to the host midway (for comparison). */
+#define DGS_SERVE_NO_GRAPHS 1
+dgs_status dgs_serve_start(dgs_ctx *ctx, int32_t max_batch, int32_t queue_cap, int32_t flags);
 dgs_status dgs_serve_stop(dgs_ctx *ctx);
 dgs_status dgs_submit(dgs_ctx *ctx, const dgs_request *req, uint64_t *ticket);
 /* Wait up to timeout_us (0 = just check, <0 = forever) for a ticket.
  * DGS_ERR_TIMEOUT if not done yet; the ticket stays valid.  A finished
  * ticket is consumed by a successful poll. */
 dgs_status dgs_poll(dgs_ctx *ctx, uint64_t ticket, int64_t timeout_us, dgs_result *out);
+
+/* Counters of the serving worker since dgs_serve_start: batches launched
+ * (re-runs included), graphs captured, re-runs after a pair-buffer overflow,
+ * and the current (tile, cell) pairs-per-tile estimate that sizes the
+ * buffers.  INVALID_ARG if serving is not started. */
+typedef struct {
+    int64_t batches;
+    int64_t graphs_captured;
+    int64_t overflow_retries;
+    double pairs_per_tile;
+} dgs_serve_stats;
+dgs_status dgs_serve_read_stats(dgs_ctx *ctx, dgs_serve_stats *out);
 
 #ifdef __cplusplus
 }

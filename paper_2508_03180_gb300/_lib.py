@@ -81,6 +81,14 @@ class dgs_request(C.Structure):
     _fields_ = [("scene_id", C.c_uint32), ("out_location", C.c_int32), ("camera", dgs_camera), ("out_rgb", _P)]
 
 
+class dgs_serve_stats(C.Structure):
+    _fields_ = [("batches", C.c_int64), ("graphs_captured", C.c_int64), ("overflow_retries", C.c_int64),
+                ("pairs_per_tile", C.c_double)]
+
+
+DGS_SERVE_NO_GRAPHS = 1
+
+
 class dgs_result(C.Structure):
     _fields_ = [("status", C.c_int32), ("batch_size", C.c_int32), ("t_submit_ms", C.c_double),
                 ("t_start_ms", C.c_double), ("t_done_ms", C.c_double)]
@@ -106,7 +114,8 @@ _SIGS = {
     "dgs_state_counts": (C.c_int32, [_P, _P, C.POINTER(dgs_counts)]),
     "dgs_profile_enable": (C.c_int32, [_P, C.c_int32]),
     "dgs_profile_read": (C.c_int32, [_P, C.POINTER(dgs_profile)]),
-    "dgs_serve_start": (C.c_int32, [_P, C.c_int32, C.c_int32]),
+    "dgs_serve_start": (C.c_int32, [_P, C.c_int32, C.c_int32, C.c_int32]),
+    "dgs_serve_read_stats": (C.c_int32, [_P, C.POINTER(dgs_serve_stats)]),
     "dgs_serve_stop": (C.c_int32, [_P]),
     "dgs_submit": (C.c_int32, [_P, C.POINTER(dgs_request), C.POINTER(C.c_uint64)]),
     "dgs_poll": (C.c_int32, [_P, C.c_uint64, C.c_int64, C.POINTER(dgs_result)]),
@@ -247,8 +256,14 @@ def dgs_profile_read(ctx) -> dgs_profile:
     return p
 
 
-def dgs_serve_start(ctx, max_batch: int, queue_cap: int):
-    check(load().dgs_serve_start(ctx, max_batch, queue_cap), ctx)
+def dgs_serve_start(ctx, max_batch: int, queue_cap: int, flags: int = 0):
+    check(load().dgs_serve_start(ctx, max_batch, queue_cap, flags), ctx)
+
+
+def dgs_serve_read_stats(ctx) -> dgs_serve_stats:
+    r = dgs_serve_stats()
+    check(load().dgs_serve_read_stats(ctx, C.byref(r)), ctx)
+    return r
 
 
 def dgs_serve_stop(ctx):

@@ -69,18 +69,21 @@ Workspace::~Workspace() {
     if (h_small) cudaFreeHost(h_small);
     if (h_views) cudaFreeHost(h_views);
     if (h_scenes) cudaFreeHost(h_scenes);
+    if (h_sizes) cudaFreeHost(h_sizes);
     if (done) cudaEventDestroy(done);
 }
 
 std::vector<DevBuf *> Workspace::all() {
     return {&views, &scenes, &zkey, &zval, &rect, &depth, &count, &cnt_sorted, &offs, &tkey, &tval, &ranges, &rec,
-            &Dpix, &ndpix, &rgb, &g2d, &gstage, &sort_k, &sort_v, &sort_hist, &sort_status, &sort_ctr, &small, &scan};
+            &Dpix, &ndpix, &rgb, &g2d, &gstage, &sort_k, &sort_v, &sort_hist, &sort_status, &sort_ctr, &small, &scan, &sizes};
 }
 
 dgs_status Workspace::init() {
     CK(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
     CK(cudaMallocHost(&h_small, 256));
     memset(h_small, 0, 256);
+    CK(cudaMallocHost(&h_sizes, sizeof(ChainSizes)));
+    memset(h_sizes, 0, sizeof(ChainSizes));
     return DGS_OK;
 }
 
@@ -89,7 +92,7 @@ dgs_status ensure_sort_scratch(Workspace &ws, long long n) {
     if ((s = ws.sort_k.ensure(sizeof(uint32_t) * std::max(1LL, n)))) return s;
     if ((s = ws.sort_v.ensure(sizeof(uint32_t) * std::max(1LL, n)))) return s;
     if ((s = ws.sort_hist.ensure(sizeof(uint32_t) * 4 * 256))) return s;
-    if ((s = ws.sort_status.ensure(sizeof(uint32_t) * 256 * std::max(1LL, sort_parts_for(n))))) return s;
+    if ((s = ws.sort_status.ensure(sizeof(uint32_t) * 2 * 256 * std::max(1LL, sort_parts_for(n))))) return s;
     if ((s = ws.sort_ctr.ensure(sizeof(uint32_t) * 4))) return s;
     return DGS_OK;
 }
@@ -103,7 +106,7 @@ SortScratch sort_scratch_of(Workspace &ws) {
     s.counters = (uint32_t *)ws.sort_ctr.p;
     s.err = (uint32_t *)ws.small.p + kSmallSortErr;
     s.cap_items = (long long)(ws.sort_k.cap / 4);
-    s.cap_parts = (long long)(ws.sort_status.cap / 1024);
+    s.cap_parts = (long long)(ws.sort_status.cap / 2048);
     return s;
 }
 
@@ -324,6 +327,7 @@ extern "C" dgs_status dgs_scene_release(dgs_ctx *ctx, uint32_t scene_id) {
         if (st->scene_id == scene_id) return set_error(DGS_ERR_BUSY, "a forward state still refers to this scene");
     CK(cudaDeviceSynchronize());
     ctx->scenes.erase(it);
+    ++ctx->scene_epoch;  // captured serving graphs may hold its pointers
     return DGS_OK;
 }
 
@@ -343,7 +347,7 @@ extern "C" dgs_status dgs_camera_set(dgs_ctx *ctx, uint32_t slot, const dgs_came
 
 namespace dgs {
 
-static ViewDesc make_view(const dgs_camera &c, int tile_base, long long pix_base, int slot, const Scene &sc,
+ViewDesc make_view(const dgs_camera &c, int tile_base, long long pix_base, int slot, const Scene &sc,
                           long long cell_base, long long rec_base) {
     ViewDesc v;
     memset(&v, 0, sizeof(v));

@@ -18,7 +18,9 @@ __global__ void __launch_bounds__(256) k_cell_project(const ViewDesc *__restrict
                                                       const SceneDev *__restrict__ scenes,
                                                       uint32_t *__restrict__ zkey, uint32_t *__restrict__ zval,
                                                       short4 *__restrict__ rect, float *__restrict__ depth,
-                                                      uint32_t *__restrict__ count, uint32_t *__restrict__ visible) {
+                                                      uint32_t *__restrict__ count, uint32_t *__restrict__ visible,
+                                                      const ChainSizes *__restrict__ dsz) {
+    if (dsz) n_views = dsz->n_views;
     uint32_t nvis = 0;
     for (int v = 0; v < n_views; ++v) {
     const ViewDesc &V = views[v];
@@ -102,22 +104,23 @@ static int grid_for(long long n, int threads) {
 
 void launch_cell_project(const ViewDesc *views, int n_views, const SceneDev *scenes, long long n_entries,
                          uint32_t *zkey, uint32_t *zval, short4 *rect, float *depth, uint32_t *count,
-                         uint32_t *visible, cudaStream_t st) {
+                         uint32_t *visible, cudaStream_t st, const ChainSizes *dsz) {
     if (n_entries == 0) return;
     k_cell_project<<<grid_for(n_entries / n_views + 1, 256), 256, 0, st>>>(views, n_views, scenes, zkey, zval, rect,
-                                                                          depth, count, visible);
+                                                                          depth, count, visible, dsz);
 }
 
 __global__ void k_gather_counts(const uint32_t *__restrict__ idx, const uint32_t *__restrict__ count, long long n,
-                                uint32_t *__restrict__ out) {
+                                const uint32_t *__restrict__ d_n, uint32_t *__restrict__ out) {
+    if (d_n) n = *d_n;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         out[i] = count[idx[i]];
 }
 
 void launch_gather_counts(const uint32_t *zval_sorted, const uint32_t *count, long long n, uint32_t *out,
-                          cudaStream_t st) {
+                          cudaStream_t st, const uint32_t *d_n) {
     if (n == 0) return;
-    k_gather_counts<<<grid_for(n, 256), 256, 0, st>>>(zval_sorted, count, n, out);
+    k_gather_counts<<<grid_for(n, 256), 256, 0, st>>>(zval_sorted, count, n, d_n, out);
 }
 
 // One thread per output slot j: the owning entry e is the last one with
@@ -128,7 +131,13 @@ void launch_gather_counts(const uint32_t *zval_sorted, const uint32_t *count, lo
 __global__ void __launch_bounds__(256) k_emit(const uint32_t *__restrict__ offs, const uint32_t *__restrict__ zval,
                                               const short4 *__restrict__ rect, const ViewDesc *__restrict__ views,
                                               int n_views, long long n_entries, long long L,
-                                              uint32_t *__restrict__ tkey, uint32_t *__restrict__ tval) {
+                                              uint32_t *__restrict__ tkey, uint32_t *__restrict__ tval,
+                                              const ChainSizes *__restrict__ dsz, const uint32_t *__restrict__ d_L) {
+    if (dsz) {
+        n_views = dsz->n_views;
+        n_entries = dsz->n_entries;
+    }
+    if (d_L) L = *d_L;
     for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < L; j += (long long)gridDim.x * blockDim.x) {
         long long lo = 0, hi = n_entries;  // find last e with offs[e] <= j
         while (hi - lo > 1) {
@@ -154,14 +163,18 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t *__restrict__ offs,
 }
 
 void launch_emit(const uint32_t *offs, const uint32_t *zval_sorted, const short4 *rect, const ViewDesc *views,
-                 int n_views, long long n_entries, long long L, uint32_t *tkey, uint32_t *tval, cudaStream_t st) {
+                 int n_views, long long n_entries, long long L, uint32_t *tkey, uint32_t *tval, cudaStream_t st,
+                 const ChainSizes *dsz, const uint32_t *d_L) {
     if (L == 0) return;
-    k_emit<<<grid_for(L, 256), 256, 0, st>>>(offs, zval_sorted, rect, views, n_views, n_entries, L, tkey, tval);
+    k_emit<<<grid_for(L, 256), 256, 0, st>>>(offs, zval_sorted, rect, views, n_views, n_entries, L, tkey, tval, dsz,
+                                             d_L);
 }
 
 // [start, end) of every non-empty tile from the tile-sorted keys; empty
 // tiles keep the (0,0) the caller cleared them to.
-__global__ void k_tile_ranges(const uint32_t *__restrict__ key, long long L, uint2 *__restrict__ ranges) {
+__global__ void k_tile_ranges(const uint32_t *__restrict__ key, long long L, const uint32_t *__restrict__ d_L,
+                              uint2 *__restrict__ ranges) {
+    if (d_L) L = *d_L;
     for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < L; j += (long long)gridDim.x * blockDim.x) {
         const uint32_t k = key[j];
         if (j == 0 || key[j - 1] != k) ranges[k].x = (uint32_t)j;
@@ -169,9 +182,21 @@ __global__ void k_tile_ranges(const uint32_t *__restrict__ key, long long L, uin
     }
 }
 
-void launch_tile_ranges(const uint32_t *tkey_sorted, long long L, uint2 *ranges, cudaStream_t st) {
+void launch_tile_ranges(const uint32_t *tkey_sorted, long long L, uint2 *ranges, cudaStream_t st,
+                        const uint32_t *d_L) {
     if (L == 0) return;
-    k_tile_ranges<<<grid_for(L, 256), 256, 0, st>>>(tkey_sorted, L, ranges);
+    k_tile_ranges<<<grid_for(L, 256), 256, 0, st>>>(tkey_sorted, L, d_L, ranges);
+}
+
+__global__ void k_clamp_pairs(uint32_t *small, int total, int clamped, int overflow, const ChainSizes *dsz) {
+    const uint32_t L = small[total], cap = dsz->L_cap;
+    small[clamped] = L < cap ? L : cap;
+    small[overflow] = L > cap ? 1u : 0u;
+}
+
+void launch_clamp_pairs(uint32_t *small, int total, int clamped, int overflow, const ChainSizes *dsz,
+                        cudaStream_t st) {
+    k_clamp_pairs<<<1, 1, 0, st>>>(small, total, clamped, overflow, dsz);
 }
 
 }  // namespace dgs

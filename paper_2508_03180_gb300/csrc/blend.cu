@@ -16,6 +16,8 @@
 // blended from shared memory (double buffer), so every record is read from
 // L2/HBM once per tile and then broadcast from shared memory to 256 pixels.
 // A block-wide count of finished pixels ends the tile early.
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace dgs {
@@ -117,15 +119,16 @@ __device__ __forceinline__ void stash_cell(float4 *dst, int per, int lane, const
     }
 }
 
+// One work unit (sub-tile `unit` of the chain) of the forward blend.
 template <int KT>
-__global__ void __launch_bounds__(WT) k_blend_fwd(const ViewDesc *__restrict__ views, int n_views,
-                                                  const uint2 *__restrict__ ranges, const uint32_t *__restrict__ cells,
-                                                  const float4 *__restrict__ rec, BlendParams bp,
-                                                  float *__restrict__ out_rgb, float *__restrict__ out_rgb2,
-                                                  float *__restrict__ out_D, int *__restrict__ out_nd) {
-    __shared__ float4 s_rec[2][MAXPER];
+__device__ __forceinline__ void blend_fwd_unit(int unit, const ViewDesc *__restrict__ views, int n_views,
+                                               const uint2 *__restrict__ ranges, const uint32_t *__restrict__ cells,
+                                               const float4 *__restrict__ rec, const BlendParams &bp,
+                                               float *__restrict__ out_rgb, float *__restrict__ out_rgb2,
+                                               float *__restrict__ out_D, int *__restrict__ out_nd,
+                                               float4 (*s_rec)[MAXPER]) {
     const int lane = threadIdx.x;
-    const int tile = blockIdx.x / WSUB, sub = blockIdx.x % WSUB;
+    const int tile = unit / WSUB, sub = unit % WSUB;
     const int vi = find_view(views, n_views, tile);
     const ViewDesc &V = views[vi];
     const int local = tile - V.tile_base;
@@ -233,11 +236,74 @@ __global__ void __launch_bounds__(WT) k_blend_fwd(const ViewDesc *__restrict__ v
     }
 }
 
-// K of the chain's views when they all share one (compile-time loop), else 0
+template <int KT>
+__global__ void __launch_bounds__(WT) k_blend_fwd(const ViewDesc *__restrict__ views, int n_views,
+                                                  const uint2 *__restrict__ ranges, const uint32_t *__restrict__ cells,
+                                                  const float4 *__restrict__ rec, BlendParams bp,
+                                                  float *__restrict__ out_rgb, float *__restrict__ out_rgb2,
+                                                  float *__restrict__ out_D, int *__restrict__ out_nd) {
+    __shared__ float4 s_rec[2][MAXPER];
+    blend_fwd_unit<KT>(blockIdx.x, views, n_views, ranges, cells, rec, bp, out_rgb, out_rgb2, out_D, out_nd, s_rec);
+}
+
+// Persistent form for chains whose sizes live on the device: a fixed grid of
+// exactly the resident warps pulls sub-tiles from an atomic counter (*work
+// starts at 0) until the chain's total_tiles * WSUB units are taken, so the
+// dense and the empty regions of the images balance dynamically.  One
+// atomic per sub-tile: their rate is bounded by the blend work between them.
+template <int KT>
+__global__ void __launch_bounds__(WT) k_blend_fwd_pull(const ViewDesc *__restrict__ views,
+                                                       const uint2 *__restrict__ ranges,
+                                                       const uint32_t *__restrict__ cells,
+                                                       const float4 *__restrict__ rec, BlendParams bp,
+                                                       float *__restrict__ out_rgb, float *__restrict__ out_D,
+                                                       int *__restrict__ out_nd, const ChainSizes *__restrict__ dsz,
+                                                       uint32_t *__restrict__ work) {
+    __shared__ float4 s_rec[2][MAXPER];
+    const int n_views = dsz->n_views;
+    const uint32_t units = (uint32_t)dsz->total_tiles * WSUB;
+    for (;;) {
+        uint32_t u = 0;
+        if (threadIdx.x == 0) u = atomicAdd(work, 1u);
+        u = __shfl_sync(0xffffffffu, u, 0);
+        if (u >= units) break;
+        blend_fwd_unit<KT>((int)u, views, n_views, ranges, cells, rec, bp, out_rgb, nullptr, out_D, out_nd, s_rec);
+        __syncwarp();
+    }
+}
+
+// min(units, SMs x resident CTAs of k_blend_fwd_pull<KT>), queried once.
+template <int KT>
+static unsigned pull_grid(int total_tiles) {
+    static int per_grid = 0;
+    if (!per_grid) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_blend_fwd_pull<KT>, WT, 0);
+        per_grid = std::max(1, sms * std::max(1, per_sm));
+    }
+    return (unsigned)std::min<long long>((long long)total_tiles * WSUB, per_grid);
+}
+
 void launch_blend_fwd(const ViewDesc *views, int n_views, int total_tiles, const uint2 *ranges,
                       const uint32_t *tile_cells, const float4 *rec, const BlendParams &bp, float *out_rgb,
-                      float *out_rgb2, float *out_D, int *out_nd, int K_all, cudaStream_t st) {
+                      float *out_rgb2, float *out_D, int *out_nd, int K_all, cudaStream_t st,
+                      const ChainSizes *dsz, uint32_t *work) {
     if (total_tiles == 0) return;
+    if (dsz) {
+        // exactly the resident warps
+#define DGS_PULL(KV)                                                                                            \
+        k_blend_fwd_pull<KV><<<pull_grid<KV>(total_tiles), WT, 0, st>>>(views, ranges, tile_cells, rec, bp, out_rgb, \
+                                                                       out_D, out_nd, dsz, work)
+        switch (K_all) {
+            case 8: DGS_PULL(8); break;
+            case 10: DGS_PULL(10); break;
+            default: DGS_PULL(0); break;
+        }
+#undef DGS_PULL
+        return;
+    }
     const unsigned grid = (unsigned)total_tiles * WSUB;
 #define DGS_FWD(KV)                                                                                          \
     k_blend_fwd<KV><<<grid, WT, 0, st>>>(views, n_views, ranges, tile_cells, rec, bp, out_rgb, out_rgb2, out_D, \

@@ -42,6 +42,19 @@ struct SceneDev {
     int K, sh_degree;
 };
 
+// Sizes of one launch chain kept in device memory.  A captured CUDA graph
+// replays over batches of other sizes: kernels handed a non-NULL pointer read
+// their sizes here when they run, and their host arguments are then only the
+// capacities that sized the grids and buffers.
+struct ChainSizes {
+    uint32_t n_entries;    // (view, cell) entries, <= capacity
+    int32_t n_views;
+    int32_t total_tiles;
+    uint32_t L_cap;        // capacity of the (tile, cell) pair buffers
+    int32_t n_scenes;      // entries of the chain's device scene table
+    int32_t pad[3];
+};
+
 struct BlendParams {
     float eps, alpha_max, d_min, bg0, bg1, bg2, dilation, ksigma;
 };
@@ -85,20 +98,29 @@ __device__ __forceinline__ void xform_s(const float R[9], const float t[3], floa
 
 // ---------------------------------------------------------------- launchers
 // binning.cu
+// Every launcher taking `dsz` (nullable) reads the sizes from it at run time;
+// `d_L` likewise points at the device-side pair count.
 void launch_cell_project(const ViewDesc *views, int n_views, const SceneDev *scenes, long long n_entries,
                          uint32_t *zkey, uint32_t *zval, short4 *rect, float *depth, uint32_t *count,
-                         uint32_t *visible, cudaStream_t st);
+                         uint32_t *visible, cudaStream_t st, const ChainSizes *dsz = nullptr);
 void launch_gather_counts(const uint32_t *zval_sorted, const uint32_t *count, long long n, uint32_t *out,
-                          cudaStream_t st);
+                          cudaStream_t st, const uint32_t *d_n = nullptr);
 void launch_emit(const uint32_t *offs, const uint32_t *zval_sorted, const short4 *rect, const ViewDesc *views,
-                 int n_views, long long n_entries, long long L, uint32_t *tkey, uint32_t *tval, cudaStream_t st);
-void launch_tile_ranges(const uint32_t *tkey_sorted, long long L, uint2 *ranges, cudaStream_t st);
+                 int n_views, long long n_entries, long long L, uint32_t *tkey, uint32_t *tval, cudaStream_t st,
+                 const ChainSizes *dsz = nullptr, const uint32_t *d_L = nullptr);
+void launch_tile_ranges(const uint32_t *tkey_sorted, long long L, uint2 *ranges, cudaStream_t st,
+                        const uint32_t *d_L = nullptr);
+// small[total] = pairs needed; writes small[clamped] = min(total, L_cap) and
+// small[overflow] = (total > L_cap), for chains whose pair buffers are
+// sized in advance.
+void launch_clamp_pairs(uint32_t *small, int total, int clamped, int overflow, const ChainSizes *dsz,
+                        cudaStream_t st);
 
 // sort.cu
 struct SortScratch {
     uint32_t *keys_alt, *vals_alt;   // n each
     uint32_t *hist;                  // 4 * 256
-    uint32_t *status;                // parts * 256
+    uint32_t *status;                // 2 * parts * 256 (alternate passes)
     uint32_t *counters;              // 4 (one per pass)
     uint32_t *err;                   // 1
     long long cap_items, cap_parts;
@@ -107,16 +129,20 @@ long long sort_parts_for(long long n);
 // Stable LSD radix sort of (key, val) by the low `bits` bits.  Results end in
 // keys/vals.  Returns the number of passes.
 int radix_sort_pairs(uint32_t *keys, uint32_t *vals, long long n, int bits, const SortScratch &s,
-                     cudaStream_t st);
+                     cudaStream_t st, const uint32_t *d_n = nullptr);
 // Exclusive scan; total written to *total (device).  scratch >= scan_scratch_words(n).
 long long scan_scratch_words(long long n);
 void exclusive_scan_u32(const uint32_t *in, uint32_t *out, long long n, uint32_t *total, uint32_t *scratch,
-                        cudaStream_t st);
+                        cudaStream_t st, const uint32_t *d_n = nullptr);
 
 // project.cu  (one launch per distinct scene of the chain: views whose
 // scene_slot differs from `slot` are skipped)
 void launch_project_fwd(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const uint32_t *count,
                         const BlendParams &bp, float4 *rec, float *g2d_zero, cudaStream_t st);
+// One launch for every scene of the device scene table (dsz->n_scenes
+// entries, Gaussian counts <= G_cap, which sizes the grid).
+void launch_project_fwd_table(const ViewDesc *views, const SceneDev *scenes, long long G_cap, const uint32_t *count,
+                              const BlendParams &bp, float4 *rec, cudaStream_t st, const ChainSizes *dsz);
 void launch_project_bwd(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const uint32_t *count,
                         const BlendParams &bp, const float *g2d, float *g_mean, float *g_scale,
                         float *g_log_scale, float *g_quat, float *g_logit, float *g_sh, cudaStream_t st);
@@ -124,7 +150,8 @@ void launch_project_bwd(const ViewDesc *views, int n_views, int slot, const Scen
 // blend.cu
 void launch_blend_fwd(const ViewDesc *views, int n_views, int total_tiles, const uint2 *ranges,
                       const uint32_t *tile_cells, const float4 *rec, const BlendParams &bp, float *out_rgb,
-                      float *out_rgb2, float *out_D, int *out_nd, int K_all, cudaStream_t st);
+                      float *out_rgb2, float *out_D, int *out_nd, int K_all, cudaStream_t st,
+                      const ChainSizes *dsz = nullptr, uint32_t *work = nullptr);
 void launch_blend_bwd(const ViewDesc *views, int n_views, int total_tiles, int K, const uint2 *ranges,
                       const uint32_t *tile_cells, const float4 *rec, const BlendParams &bp, const float *rgb,
                       const float *D, const int *nd, const float *dL_drgb, float *g2d, float *g_cell_v,

@@ -30,8 +30,7 @@ constexpr float SH_C3b = 2.890611442640554f;    // (1/2) sqrt(105/pi)
 constexpr float SH_C3c = 0.4570457994644658f;   // (1/4) sqrt(21/(2 pi))
 constexpr float SH_C3d = 0.3731763325901154f;   // (1/4) sqrt(7/pi)
 constexpr float SH_C3e = 1.445305721320277f;    // (1/4) sqrt(105/pi)
-constexpr float LOG2E = 1.4426950408889634f;
-constexpr float KAPPA = 0.8493218002880191f;  // sqrt(log2(e) / 2)
+constexpr float KAPPA = 0.8493218002880191f;  // sqrt(log2(e) / 2), log2(e) = 1/ln 2
 
 __device__ __forceinline__ void sh_eval(float x, float y, float z, int deg, float Y[16]) {
 #pragma unroll
@@ -167,9 +166,12 @@ __device__ __forceinline__ void proj_core(const ViewDesc &Vw, const GaussIn &p, 
     c.syy = fadd_s(fadd_s(fadd_s(fmul_s(c.V[3], c.T[3]), fmul_s(c.V[4], c.T[4])), fmul_s(c.V[5], c.T[5])), dilation);
 }
 
-__global__ void __launch_bounds__(128) k_project_fwd(const ViewDesc *__restrict__ views, int n_views, int slot,
-                                                     SceneDev sc, const uint32_t *__restrict__ count, BlendParams bp,
-                                                     float4 *__restrict__ rec, float *__restrict__ g2d_zero) {
+// Records of every Gaussian of scene `slot` (grid-stride over its G) for each
+// view of that scene in which its cell survived culling.
+__device__ __forceinline__ void project_scene(const ViewDesc *__restrict__ views, int n_views, int slot,
+                                              const SceneDev &sc, const uint32_t *__restrict__ count,
+                                              const BlendParams &bp, float4 *__restrict__ rec,
+                                              float *__restrict__ g2d_zero) {
     const long long G = sc.G, N = sc.N;
     const int K = sc.K, C = (sc.sh_degree + 1) * (sc.sh_degree + 1);
     for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < G; g += (long long)gridDim.x * blockDim.x) {
@@ -236,6 +238,25 @@ __global__ void __launch_bounds__(128) k_project_fwd(const ViewDesc *__restrict_
     }
 }
 
+__global__ void __launch_bounds__(128) k_project_fwd(const ViewDesc *__restrict__ views, int n_views, int slot,
+                                                     SceneDev sc, const uint32_t *__restrict__ count, BlendParams bp,
+                                                     float4 *__restrict__ rec, float *__restrict__ g2d_zero) {
+    project_scene(views, n_views, slot, sc, count, bp, rec, g2d_zero);
+}
+
+// Every scene of a device scene table in one launch (sizes read at run time).
+__global__ void __launch_bounds__(128) k_project_fwd_table(const ViewDesc *__restrict__ views,
+                                                           const SceneDev *__restrict__ scenes,
+                                                           const uint32_t *__restrict__ count, BlendParams bp,
+                                                           float4 *__restrict__ rec,
+                                                           const ChainSizes *__restrict__ dsz) {
+    const int n_views = dsz->n_views, n_scenes = dsz->n_scenes;
+    for (int s = 0; s < n_scenes; ++s) {
+        const SceneDev sc = scenes[s];
+        project_scene(views, n_views, s, sc, count, bp, rec, nullptr);
+    }
+}
+
 static int grid_for(long long n, int threads) {
     long long b = (n + threads - 1) / threads;
     const long long cap = 152LL * 16;
@@ -247,6 +268,12 @@ void launch_project_fwd(const ViewDesc *views, int n_views, int slot, const Scen
                         const BlendParams &bp, float4 *rec, float *g2d_zero, cudaStream_t st) {
     if (sc.G == 0 || n_views == 0) return;
     k_project_fwd<<<grid_for(sc.G, 128), 128, 0, st>>>(views, n_views, slot, sc, count, bp, rec, g2d_zero);
+}
+
+void launch_project_fwd_table(const ViewDesc *views, const SceneDev *scenes, long long G_cap, const uint32_t *count,
+                              const BlendParams &bp, float4 *rec, cudaStream_t st, const ChainSizes *dsz) {
+    if (G_cap == 0) return;
+    k_project_fwd_table<<<grid_for(G_cap, 128), 128, 0, st>>>(views, scenes, count, bp, rec, dsz);
 }
 
 // ---------------------------------------------------------------- adjoint

@@ -25,6 +25,9 @@ constexpr int kMaxCamSlots = 4096;
 constexpr int kSmallTotal = 0;    // sort length L
 constexpr int kSmallSortErr = 1;  // a radix-sort look-back wait gave up
 constexpr int kSmallVisible = 2;  // (view, cell) pairs that survived culling
+constexpr int kSmallPairs = 3;    // L clamped to the pair capacity (captured chains)
+constexpr int kSmallOverflow = 4; // L exceeded the pair capacity (captured chains)
+constexpr int kSmallWork = 5;     // work counter of the pulling blend (captured chains)
 
 dgs_status set_error(dgs_status code, const std::string &msg);
 dgs_status cuda_error(cudaError_t e, const char *what);
@@ -65,7 +68,9 @@ struct Workspace {
     DevBuf Dpix, ndpix, rgb;                                 // per pixel
     DevBuf gstage;                                           // backward staging
     DevBuf sort_k, sort_v, sort_hist, sort_status, sort_ctr, small, scan;
+    DevBuf sizes;                 // ChainSizes of a captured chain
     uint32_t *h_small = nullptr;  // pinned mirror of `small`
+    ChainSizes *h_sizes = nullptr;
     ViewDesc *h_views = nullptr;
     size_t h_views_cap = 0;
     SceneDev *h_scenes = nullptr;
@@ -95,13 +100,37 @@ struct PendingReq {
     int64_t bytes;  // admission estimate
 };
 
-struct InflightBatch {
+// Capacities of a serving chain slot.  Every buffer of the slot's workspace
+// is sized for them, so its captured graphs stay valid until one grows.
+struct ChainCaps {
+    int V = 0, S = 0;
+    long long E = 0, R = 0, T = 0, P = 0, L = 0;
+    long long G = 0;  // Gaussians of the largest scene (sizes the projection grid)
+};
+
+// One stream's serving chain: a workspace sized for `caps` and one
+// instantiated graph of the whole forward chain per Gaussians-per-cell class
+// of the batch (K = 8, 10 or mixed pick the blend's specialisation).  Scenes,
+// views and every size are read from device memory when the graph runs.
+struct GraphSlot {
     std::unique_ptr<Workspace> ws;
+    ChainCaps caps;
+    long long view_tiles = 0, view_px = 0;  // largest view seen
+    long long L_need = 0;                   // pairs of the last overflowing batch, with headroom
+    uint64_t scene_epoch = 0;
+    std::map<int, cudaGraphExec_t> graphs;
+    void drop();
+    ~GraphSlot() { drop(); }
+};
+
+struct InflightBatch {
+    std::unique_ptr<Workspace> ws;  // non-graph chains only
     std::vector<PendingReq> reqs;
     int stream_idx = 0;
     double t_start = 0;
     int64_t bytes = 0;
     dgs_status status = DGS_OK;
+    bool graph = false;             // ran as a replay of a captured chain
 };
 
 constexpr int kServeStreams = 2;  // launch chains in flight at once
@@ -121,6 +150,12 @@ struct ServeState {
     cudaStream_t streams[kServeStreams] = {};
     cudaEvent_t events[kServeStreams] = {};
     bool busy[kServeStreams] = {};
+    bool use_graphs = true;
+    bool gpu_signal = false;                // a chain completed since the worker last looked
+    uint64_t submits = 0;                   // requests accepted so far
+    GraphSlot gslot[kServeStreams];
+    double pairs_per_tile = 128.0;          // running estimate that sizes the pair buffers
+    int64_t graphs_captured = 0, batches = 0, overflow_retries = 0;
 };
 
 }  // namespace dgs
@@ -167,6 +202,7 @@ struct dgs_ctx {
     dgs::DevBuf aux, loss_partial;
     std::unique_ptr<dgs::Workspace> sort_ws;
     std::unique_ptr<dgs::ServeState> serve;
+    uint64_t scene_epoch = 0;  // bumped when a scene's buffers go away
 };
 
 namespace dgs {
@@ -177,4 +213,6 @@ std::unique_ptr<Workspace> acquire_ws(dgs_ctx *ctx, cudaStream_t st, dgs_status 
 // zero the screen-space gradient accumulators for a later backward.
 dgs_status chain_forward(dgs_ctx *ctx, Workspace &ws, const std::vector<ChainView> &views, float *out_img,
                          bool keep_rgb, bool grad_buffers, cudaStream_t st);
+ViewDesc make_view(const dgs_camera &c, int tile_base, long long pix_base, int slot, const Scene &sc,
+                   long long cell_base, long long rec_base);
 }  // namespace dgs

@@ -12,6 +12,8 @@
 // Every wait on another CTA is bounded: after kSpinLimit polls the CTA sets
 // *err, treats the missing count as 0 and carries on, so the kernel always
 // finishes; the host turns a set flag into an error.
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace dgs {
@@ -29,8 +31,14 @@ constexpr int kSpinLimit = 1 << 22;
 long long sort_parts_for(long long n) { return (n + RS_TILE - 1) / RS_TILE; }
 
 // Histograms of every digit of every pass in one read of the keys.
-__global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint32_t *__restrict__ keys, long long n, int passes,
-                                                        uint32_t *__restrict__ hist) {
+// Also clears the look-back words of the first pass (status0).
+__global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint32_t *__restrict__ keys, long long n,
+                                                        const uint32_t *__restrict__ d_n, int passes,
+                                                        uint32_t *__restrict__ hist, uint32_t *__restrict__ status0) {
+    if (d_n) n = *d_n;
+    const long long words = 256LL * ((n + RS_TILE - 1) / RS_TILE);
+    for (long long i = blockIdx.x * (long long)RS_THREADS + threadIdx.x; i < words; i += (long long)gridDim.x * RS_THREADS)
+        status0[i] = 0u;
     __shared__ uint32_t sh[4][256];
     for (int i = threadIdx.x; i < 4 * 256; i += RS_THREADS) (&sh[0][0])[i] = 0;
     __syncthreads();
@@ -62,114 +70,173 @@ __global__ void k_rs_hist_scan(uint32_t *hist) {
 
 __device__ __forceinline__ uint32_t ld_volatile(const uint32_t *p) { return *(const volatile uint32_t *)p; }
 
-__global__ void __launch_bounds__(RS_THREADS) k_rs_pass(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin,
-                                                        uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
-                                                        long long n, int shift, const uint32_t *__restrict__ digit_base,
-                                                        uint32_t *__restrict__ status, uint32_t *__restrict__ counter,
+// Pass `pass` of the sort.  The data ping-pongs between (k0, v0) and
+// (k1, v1).  With skip_trivial, a pass whose digit is 0 for every key (the
+// histogram says so) is the identity permutation and does nothing; every pass
+// then takes its input from the buffer the previous non-trivial pass wrote,
+// and the look-back arrays alternate over non-trivial passes.
+__device__ __forceinline__ bool rs_trivial(const uint32_t *hist, int q, long long n) {
+    return (long long)hist[256 * q + 1] == n;  // scanned base of digit 1 = count of digit 0
+}
+
+__global__ void __launch_bounds__(RS_THREADS) k_rs_pass(uint32_t *__restrict__ k0, uint32_t *__restrict__ v0,
+                                                        uint32_t *__restrict__ k1, uint32_t *__restrict__ v1,
+                                                        long long n, const uint32_t *__restrict__ d_n, int pass,
+                                                        const uint32_t *__restrict__ hist, bool skip_trivial,
+                                                        uint32_t *__restrict__ status0, uint32_t *__restrict__ status1,
+                                                        uint32_t *__restrict__ counter,
                                                         uint32_t *__restrict__ err) {
     __shared__ uint32_t s_warp[RS_WARPS][256];   // per-warp digit counts, then per-warp offsets
     __shared__ uint32_t s_base[256];             // global destination of the partition's first item per digit
     __shared__ uint32_t s_part;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) s_part = atomicAdd(counter, 1u);  // partitions in launch order: look-back never waits on a later one
-    for (int i = tid; i < RS_WARPS * 256; i += RS_THREADS) (&s_warp[0][0])[i] = 0;
-    __syncthreads();
-    const long long part = s_part;
-    const long long base = part * RS_TILE + (long long)warp * RS_WARP_ITEMS;
+    if (d_n) n = *d_n;
+    int ord = pass;  // non-trivial passes before this one
+    if (skip_trivial) {
+        if (rs_trivial(hist, pass, n)) return;
+        ord = 0;
+        for (int q = 0; q < pass; ++q) ord += rs_trivial(hist, q, n) ? 0 : 1;
+    }
+    const int shift = 8 * pass;
+    const uint32_t *__restrict__ digit_base = hist + 256 * pass;
+    const uint32_t *__restrict__ kin = (ord & 1) ? k1 : k0;
+    const uint32_t *__restrict__ vin = (ord & 1) ? v1 : v0;
+    uint32_t *__restrict__ kout = (ord & 1) ? k0 : k1;
+    uint32_t *__restrict__ vout = (ord & 1) ? v0 : v1;
+    uint32_t *__restrict__ status = (ord & 1) ? status1 : status0;
+    uint32_t *__restrict__ status_next = (ord & 1) ? status0 : status1;
+    const long long n_parts = (n + RS_TILE - 1) / RS_TILE;
+    if (blockIdx.x >= n_parts) return;  // the first min(grid, n_parts) CTAs take every partition
+    // Persistent CTAs claim partitions in increasing order: a partition only
+    // waits for earlier ones, which CTAs that are already running own.
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_part = atomicAdd(counter, 1u);
+        __syncthreads();
+        const long long part = s_part;
+        if (part >= n_parts) break;
+        for (int i = tid; i < RS_WARPS * 256; i += RS_THREADS) (&s_warp[0][0])[i] = 0;
+        // the next pass's look-back words of this partition: that array was
+        // last used by the previous pass, which has finished
+        status_next[part * 256 + tid] = 0u;
+        __syncthreads();
+        const long long base = part * RS_TILE + (long long)warp * RS_WARP_ITEMS;
 
-    uint32_t key[RS_ITEMS], val[RS_ITEMS], rank[RS_ITEMS];
+        uint32_t key[RS_ITEMS], val[RS_ITEMS], rank[RS_ITEMS];
 #pragma unroll
-    for (int it = 0; it < RS_ITEMS; ++it) {
-        const long long idx = base + it * 32 + lane;
-        const bool ok = idx < n;
-        key[it] = ok ? kin[idx] : 0u;
-        val[it] = ok ? vin[idx] : 0u;
-    }
-    const unsigned lt_mask = (1u << lane) - 1u;
-    // rank inside the warp, in item order (it, lane): stable
-#pragma unroll
-    for (int it = 0; it < RS_ITEMS; ++it) {
-        const long long idx = base + it * 32 + lane;
-        const bool ok = idx < n;
-        const unsigned active = __ballot_sync(0xffffffffu, ok);
-        rank[it] = 0;
-        if (ok) {
-            const uint32_t d = (key[it] >> shift) & 255u;
-            const unsigned peers = __match_any_sync(active, d);
-            const uint32_t before = s_warp[warp][d];
-            rank[it] = before + __popc(peers & lt_mask);
-            __syncwarp(active);
-            if (lane == __ffs(peers) - 1) s_warp[warp][d] = before + __popc(peers);
+        for (int it = 0; it < RS_ITEMS; ++it) {
+            const long long idx = base + it * 32 + lane;
+            const bool ok = idx < n;
+            key[it] = ok ? kin[idx] : 0u;
+            val[it] = ok ? vin[idx] : 0u;
         }
-        __syncwarp();
-    }
-    __syncthreads();
-    // thread t owns digit t: partition total and per-warp exclusive offsets
-    const int d = tid;
-    uint32_t total = 0;
+        const unsigned lt_mask = (1u << lane) - 1u;
+        // rank inside the warp, in item order (it, lane): stable
 #pragma unroll
-    for (int w = 0; w < RS_WARPS; ++w) {
-        const uint32_t c = s_warp[w][d];
-        s_warp[w][d] = total;
-        total += c;
-    }
-    uint32_t *my = status + part * 256 + d;
-    if (part == 0) {
-        atomicExch(my, FLAG_INC | total);
-        s_base[d] = digit_base[d];
-    } else {
-        atomicExch(my, FLAG_AGG | total);
-        uint32_t excl = 0;
-        for (long long p = part - 1; p >= 0; --p) {
-            const uint32_t *q = status + p * 256 + d;
-            uint32_t s = ld_volatile(q);
-            int spins = 0;
-            while ((s & (FLAG_AGG | FLAG_INC)) == 0u) {
-                if (++spins > kSpinLimit) { atomicOr(err, 1u); s = FLAG_INC; break; }
-                __nanosleep(64);
-                s = ld_volatile(q);
+        for (int it = 0; it < RS_ITEMS; ++it) {
+            const long long idx = base + it * 32 + lane;
+            const bool ok = idx < n;
+            const unsigned active = __ballot_sync(0xffffffffu, ok);
+            rank[it] = 0;
+            if (ok) {
+                const uint32_t d = (key[it] >> shift) & 255u;
+                const unsigned peers = __match_any_sync(active, d);
+                const uint32_t before = s_warp[warp][d];
+                rank[it] = before + __popc(peers & lt_mask);
+                __syncwarp(active);
+                if (lane == __ffs(peers) - 1) s_warp[warp][d] = before + __popc(peers);
             }
-            excl += s & COUNT_MASK;
-            if (s & FLAG_INC) break;
+            __syncwarp();
         }
-        atomicExch(my, FLAG_INC | (excl + total));
-        s_base[d] = digit_base[d] + excl;
-    }
-    __syncthreads();
+        __syncthreads();
+        // thread t owns digit t: partition total and per-warp exclusive offsets
+        const int d = tid;
+        uint32_t total = 0;
 #pragma unroll
-    for (int it = 0; it < RS_ITEMS; ++it) {
-        const long long idx = base + it * 32 + lane;
-        if (idx < n) {
-            const uint32_t dg = (key[it] >> shift) & 255u;
-            const uint32_t dst = s_base[dg] + s_warp[warp][dg] + rank[it];
-            kout[dst] = key[it];
-            vout[dst] = val[it];
+        for (int w = 0; w < RS_WARPS; ++w) {
+            const uint32_t c = s_warp[w][d];
+            s_warp[w][d] = total;
+            total += c;
+        }
+        uint32_t *my = status + part * 256 + d;
+        if (part == 0) {
+            atomicExch(my, FLAG_INC | total);
+            s_base[d] = digit_base[d];
+        } else {
+            atomicExch(my, FLAG_AGG | total);
+            uint32_t excl = 0;
+            for (long long p = part - 1; p >= 0; --p) {
+                const uint32_t *q = status + p * 256 + d;
+                uint32_t s = ld_volatile(q);
+                int spins = 0;
+                while ((s & (FLAG_AGG | FLAG_INC)) == 0u) {
+                    if (++spins > kSpinLimit) { atomicOr(err, 1u); s = FLAG_INC; break; }
+                    __nanosleep(64);
+                    s = ld_volatile(q);
+                }
+                excl += s & COUNT_MASK;
+                if (s & FLAG_INC) break;
+            }
+            atomicExch(my, FLAG_INC | (excl + total));
+            s_base[d] = digit_base[d] + excl;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int it = 0; it < RS_ITEMS; ++it) {
+            const long long idx = base + it * 32 + lane;
+            if (idx < n) {
+                const uint32_t dg = (key[it] >> shift) & 255u;
+                const uint32_t dst = s_base[dg] + s_warp[warp][dg] + rank[it];
+                kout[dst] = key[it];
+                vout[dst] = val[it];
+            }
         }
     }
 }
 
-int radix_sort_pairs(uint32_t *keys, uint32_t *vals, long long n, int bits, const SortScratch &s, cudaStream_t st) {
-    if (n <= 1 || bits <= 0) return 0;
+// Copy the result back to (kd, vd) if an odd number of non-trivial passes
+// left it in (ks, vs).
+__global__ void k_copy_pairs(const uint32_t *__restrict__ ks, const uint32_t *__restrict__ vs, uint32_t *__restrict__ kd,
+                             uint32_t *__restrict__ vd, long long n, const uint32_t *__restrict__ d_n,
+                             const uint32_t *__restrict__ hist, int passes) {
+    if (d_n) n = *d_n;
+    int ord = 0;
+    for (int q = 0; q < passes; ++q) ord += rs_trivial(hist, q, n) ? 0 : 1;
+    if (!(ord & 1)) return;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        kd[i] = ks[i];
+        vd[i] = vs[i];
+    }
+}
+
+constexpr int RS_MAX_CTAS = 152 * 8;  // persistent grid: 8 CTAs of 256 threads per SM
+
+int radix_sort_pairs(uint32_t *keys, uint32_t *vals, long long n, int bits, const SortScratch &s, cudaStream_t st,
+                     const uint32_t *d_n) {
+    // n: the item count, or (d_n != NULL) the capacity, the count being read
+    // from device memory when the kernels run (graph-capturable)
+    if ((!d_n && n <= 1) || n <= 0 || bits <= 0) return 0;
     const int passes = (bits + 7) / 8;
     cudaMemsetAsync(s.hist, 0, sizeof(uint32_t) * 4 * 256, st);
     cudaMemsetAsync(s.counters, 0, sizeof(uint32_t) * 4, st);
     const long long parts = sort_parts_for(n);
+    // look-back words: two arrays of `parts` x 256, used by alternate passes;
+    // the histogram kernel clears the first, every pass clears the other
+    uint32_t *status[2] = {s.status, s.status + 256 * parts};
     int hb = (int)((n + RS_THREADS * 8 - 1) / (RS_THREADS * 8));
     if (hb > 152 * 8) hb = 152 * 8;
-    k_rs_hist<<<hb, RS_THREADS, 0, st>>>(keys, n, passes, s.hist);
+    k_rs_hist<<<hb, RS_THREADS, 0, st>>>(keys, n, d_n, passes, s.hist, status[0]);
     k_rs_hist_scan<<<passes, 256, 0, st>>>(s.hist);
-    uint32_t *ki = keys, *vi = vals, *ko = s.keys_alt, *vo = s.vals_alt;
-    for (int p = 0; p < passes; ++p) {
-        cudaMemsetAsync(s.status, 0, sizeof(uint32_t) * 256 * parts, st);
-        k_rs_pass<<<(unsigned)parts, RS_THREADS, 0, st>>>(ki, vi, ko, vo, n, 8 * p, s.hist + 256 * p, s.status,
-                                                          s.counters + p, s.err);
-        uint32_t *t;
-        t = ki; ki = ko; ko = t;
-        t = vi; vi = vo; vo = t;
-    }
-    if (passes & 1) {  // result sits in the alternate buffers
-        cudaMemcpyAsync(keys, ki, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st);
-        cudaMemcpyAsync(vals, vi, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st);
+    const unsigned grid = (unsigned)(parts < RS_MAX_CTAS ? parts : RS_MAX_CTAS);
+    const bool skip = d_n != nullptr;  // device-sized: key ranges unknown on the host
+    for (int p = 0; p < passes; ++p)
+        k_rs_pass<<<grid, RS_THREADS, 0, st>>>(keys, vals, s.keys_alt, s.vals_alt, n, d_n, p, s.hist, skip,
+                                               status[0], status[1], s.counters + p, s.err);
+    if (skip) {
+        k_copy_pairs<<<152 * 8, 256, 0, st>>>(s.keys_alt, s.vals_alt, keys, vals, n, d_n, s.hist, passes);
+    } else if (passes & 1) {  // result sits in the alternate buffers
+        cudaMemcpyAsync(keys, s.keys_alt, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(vals, s.vals_alt, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st);
     }
     return passes;
 }
@@ -208,8 +275,11 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *s_warp
 }
 
 __global__ void __launch_bounds__(SC_THREADS) k_scan_reduce(const uint32_t *__restrict__ in, long long n,
+                                                            const uint32_t *__restrict__ d_n,
                                                             uint32_t *__restrict__ partial) {
     __shared__ uint32_t s_warp[SC_THREADS / 32];
+    if (d_n) n = *d_n;
+    if (blockIdx.x * (long long)SC_TILE >= n && blockIdx.x > 0) return;
     const long long base = blockIdx.x * (long long)SC_TILE;
     uint32_t sum = 0;
 #pragma unroll
@@ -222,8 +292,10 @@ __global__ void __launch_bounds__(SC_THREADS) k_scan_reduce(const uint32_t *__re
     if (threadIdx.x == 0) partial[blockIdx.x] = tot;
 }
 
-__global__ void __launch_bounds__(SC_THREADS) k_scan_partials(uint32_t *partial, long long nb, uint32_t *total) {
+__global__ void __launch_bounds__(SC_THREADS) k_scan_partials(uint32_t *partial, long long nb,
+                                                              const uint32_t *__restrict__ d_n, uint32_t *total) {
     __shared__ uint32_t s_warp[SC_THREADS / 32];
+    if (d_n) nb = (*d_n + SC_TILE - 1) / SC_TILE;
     uint32_t carry = 0;
     for (long long b0 = 0; b0 < nb; b0 += SC_THREADS) {
         const long long b = b0 + threadIdx.x;
@@ -237,8 +309,11 @@ __global__ void __launch_bounds__(SC_THREADS) k_scan_partials(uint32_t *partial,
 }
 
 __global__ void __launch_bounds__(SC_THREADS) k_scan_down(const uint32_t *__restrict__ in, long long n,
+                                                          const uint32_t *__restrict__ d_n,
                                                           const uint32_t *__restrict__ partial, uint32_t *__restrict__ out) {
     __shared__ uint32_t s_warp[SC_THREADS / 32];
+    if (d_n) n = *d_n;
+    if (blockIdx.x * (long long)SC_TILE >= n) return;
     const long long base = blockIdx.x * (long long)SC_TILE + (long long)threadIdx.x * SC_ITEMS;  // blocked per thread
     uint32_t v[SC_ITEMS];
     uint32_t sum = 0;
@@ -259,15 +334,16 @@ __global__ void __launch_bounds__(SC_THREADS) k_scan_down(const uint32_t *__rest
 }
 
 void exclusive_scan_u32(const uint32_t *in, uint32_t *out, long long n, uint32_t *total, uint32_t *scratch,
-                        cudaStream_t st) {
+                        cudaStream_t st, const uint32_t *d_n) {
+    // n: the count, or (d_n != NULL) the capacity with the count in device memory
     if (n == 0) {
         cudaMemsetAsync(total, 0, sizeof(uint32_t), st);
         return;
     }
     const long long nb = (n + SC_TILE - 1) / SC_TILE;
-    k_scan_reduce<<<(unsigned)nb, SC_THREADS, 0, st>>>(in, n, scratch);
-    k_scan_partials<<<1, SC_THREADS, 0, st>>>(scratch, nb, total);
-    k_scan_down<<<(unsigned)nb, SC_THREADS, 0, st>>>(in, n, scratch, out);
+    k_scan_reduce<<<(unsigned)nb, SC_THREADS, 0, st>>>(in, n, d_n, scratch);
+    k_scan_partials<<<1, SC_THREADS, 0, st>>>(scratch, nb, d_n, total);
+    k_scan_down<<<(unsigned)nb, SC_THREADS, 0, st>>>(in, n, d_n, scratch, out);
 }
 
 }  // namespace dgs

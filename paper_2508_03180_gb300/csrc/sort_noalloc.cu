@@ -23,10 +23,10 @@ constexpr long long kMaxParts = (kMaxItems + 4095) / 4096; // sort partitions of
 constexpr size_t kOffKeys = 0;
 constexpr size_t kOffVals = kOffKeys + kMaxItems;
 constexpr size_t kOffHist = kOffVals + kMaxItems;          // 4 passes x 256 digits
-constexpr size_t kOffStatus = kOffHist + 4 * 256;          // kMaxParts x 256 look-back words
-constexpr size_t kOffCounters = kOffStatus + kMaxParts * 256;
+constexpr size_t kOffStatus = kOffHist + 4 * 256;          // 2 x kMaxParts x 256 look-back words
+constexpr size_t kOffCounters = kOffStatus + 2 * kMaxParts * 256;
 constexpr size_t kOffErr = kOffCounters + 4;
-constexpr size_t kWords = kOffErr + 60;                    // about 8.3 MB in total
+constexpr size_t kWords = kOffErr + 60;                    // about 8.6 MB in total
 
 // Device-side scratch.  In host code this name is only a stand-in: its
 // device address comes from cudaGetSymbolAddress, per device.

@@ -185,8 +185,15 @@ class Context:
         return {name: (p.ms[i], p.launches[i]) for i, name in enumerate(L.STAGES)}
 
     # ------------------------------------------------------------ serving
-    def serve_start(self, max_batch: int = 8, queue_cap: int = 1024):
-        L.dgs_serve_start(self.ctx, max_batch, queue_cap)
+    def serve_start(self, max_batch: int = 8, queue_cap: int = 1024, graphs: bool = True):
+        """graphs=False runs each batch as a plain launch chain instead of a
+        replay of a captured graph."""
+        L.dgs_serve_start(self.ctx, max_batch, queue_cap, 0 if graphs else L.DGS_SERVE_NO_GRAPHS)
+
+    def serve_stats(self) -> dict:
+        r = L.dgs_serve_read_stats(self.ctx)
+        return {"batches": r.batches, "graphs_captured": r.graphs_captured,
+                "overflow_retries": r.overflow_retries, "pairs_per_tile": r.pairs_per_tile}
 
     def serve_stop(self):
         L.dgs_serve_stop(self.ctx)

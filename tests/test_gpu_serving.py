@@ -1,6 +1,8 @@
 """Continuous-batching serving loop: results are the same alone and in a
-mixed batch, admission respects the HBM budget, and the host-side error
-paths (queue full, unknown ticket, timeout) behave."""
+mixed batch (as graph replays and as plain launch chains), a batch whose
+(tile, cell) pairs overflow the captured buffers is re-run after they grow,
+admission respects the HBM budget, and the host-side error paths (queue
+full, unknown ticket, timeout) behave."""
 import time
 
 import numpy as np
@@ -22,7 +24,8 @@ def _ctx(**cfg):
     return Context(**cfg)
 
 
-def test_same_result_alone_and_in_a_mixed_batch(scenes):
+@pytest.mark.parametrize("graphs", [True, False])
+def test_same_result_alone_and_in_a_mixed_batch(scenes, graphs):
     c = _ctx()
     sids = [c.upload_scene(s) for s in scenes]
     cams = [synth.sphere_cameras(1, 3.0, W, H, seed0=i)[0] for i, (W, H) in
@@ -33,18 +36,27 @@ def test_same_result_alone_and_in_a_mixed_batch(scenes):
         img, _, _ = c.render(sids[i % 2], [cam])
         ref.append(img.clone())
     torch.cuda.synchronize()
-    c.serve_start(max_batch=8)
+    c.serve_start(max_batch=8, graphs=graphs)
     outs = [torch.zeros_like(r) for r in ref]
     tickets = [c.submit(sids[i % 2], cam, outs[i]) for i, cam in enumerate(cams)]
     results = [c.poll(t, -1) for t in tickets]
+    # the same requests again: graphs of these scene sets are replayed
+    outs2 = [torch.zeros_like(r) for r in ref]
+    results += [c.poll(c.submit(sids[i % 2], cam, outs2[i]), -1) for i, cam in enumerate(cams)]
+    stats = c.serve_stats()
     c.serve_stop()
+    if graphs:
+        assert 1 <= stats["graphs_captured"] < stats["batches"]
+    else:
+        assert stats["graphs_captured"] == 0
     torch.cuda.synchronize()
     assert all(r.status == 0 for r in results)
     assert max(r.batch_size for r in results) > 1, "requests submitted together should share a batch"
-    for o, r in zip(outs, ref):
+    for o, o2, r in zip(outs, outs2, ref):
         assert torch.equal(o, r)
+        assert torch.equal(o2, r)
     # host outputs too
-    c.serve_start(max_batch=4)
+    c.serve_start(max_batch=4, graphs=graphs)
     host = [np.zeros(r.numel(), np.float32) for r in ref[:3]]
     ht = [c.submit(sids[i % 2], cams[i], torch.from_numpy(host[i])) for i in range(3)]
     for t in ht:
@@ -52,6 +64,29 @@ def test_same_result_alone_and_in_a_mixed_batch(scenes):
     c.serve_stop()
     for h, r in zip(host, ref[:3]):
         assert np.array_equal(h, r.cpu().numpy())
+    c.close()
+
+
+def test_pair_overflow_grows_buffers_and_reruns():
+    # thousands of large cells over a 48x32 view: far more (tile, cell) pairs
+    # per tile than the initial estimate that sizes the captured buffers
+    c = _ctx()
+    scene = synth.scene_small(seed=7, n_cells=3000)
+    sid = c.upload_scene(scene)
+    cams = [synth.sphere_cameras(1, 2.2, 48, 32, seed0=s)[0] for s in range(3)]
+    ref = [c.render(sid, [cam])[0].clone() for cam in cams]
+    _, _, st = c.render(sid, [cams[0]], stats=True)
+    assert st.sort_length > 200 * 6, "the scene must be dense enough to overflow"
+    torch.cuda.synchronize()
+    c.serve_start(max_batch=1)
+    outs = [torch.zeros_like(r) for r in ref]
+    rs = [c.poll(c.submit(sid, cam, o), -1) for cam, o in zip(cams, outs)]
+    stats = c.serve_stats()
+    c.serve_stop()
+    assert all(r.status == 0 for r in rs)
+    assert stats["overflow_retries"] >= 1
+    for o, r in zip(outs, ref):
+        assert torch.equal(o, r)
     c.close()
 
 
