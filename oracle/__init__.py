@@ -6,7 +6,9 @@ it; the product path must not import it.
 
 Pieces:
   dgs_oracle.c  FP32-exact decisions (cell footprint, tile lists, AABB inputs)
-                and the FP64 hybrid blend (Eq. 12-14) with its adjoint.
+                and the FP64 hybrid blend (Eq. 12-14) with its adjoint; the
+                comparators: per-Gaussian alpha-blending (Eq. 2-3) and
+                weighted-sum rendering (Eq. 4-6).
   project.py    FP64 projection of Gaussians (EWA, opacity, SH colour) in
                 plain PyTorch CPU ops; autograd gives its chain rule.
 
@@ -69,6 +71,12 @@ def lib():
         L.or_blend_grad.argtypes = [i32, i32, i32, i32, P, P, P, P, P, P, P, P, P, P, P, P, P, i32, i32,
                                     P, P, P, P, P]
         L.or_blend_grad.restype = None
+        L.or_gauss_rects.argtypes = [i64, P, P, P, P, P, i32, P, P]
+        L.or_gauss_rects.restype = None
+        L.or_alpha_blend.argtypes = [i32, i32, i32, P, P, P, P, P, P, P, P, P, P, P, i32, i32, P, P, P]
+        L.or_alpha_blend.restype = i64
+        L.or_wsr.argtypes = [i32, i32, i32, P, P, P, P, P, P, P, P, P, P, ctypes.c_double, P, i32, i32, P]
+        L.or_wsr.restype = None
         L.or_num_threads.argtypes = []
         L.or_num_threads.restype = i32
         _lib = L
@@ -271,3 +279,77 @@ def sort_length(scene, cam, opt: Options = Options()) -> int:
     rect, _ = cell_rects(scene, cam, opt)
     vis = rect[:, 0] >= 0
     return int(((rect[vis, 2] - rect[vis, 0] + 1).astype(np.int64) * (rect[vis, 3] - rect[vis, 1] + 1)).sum())
+
+
+# --------------------------------------------------------------------------
+# Comparators (per-Gaussian alpha-blending, weighted-sum rendering)
+
+
+def gauss_rects(scene, cam, opt: Options = Options()):
+    """Per Gaussian: tile rectangle of its FP32 AABB box (tx0 = -1 culled) and
+    FP32 view depth of its mean."""
+    mu2f, extf, valid = gauss_decisions(scene, cam, opt)
+    G = scene.G
+    rect = np.empty((G, 4), dtype=np.int32)
+    depth = np.empty(G, dtype=np.float32)
+    lib().or_gauss_rects(G, _p(_c(scene.g_mean, np.float32)), _p(mu2f), _p(extf), _p(valid),
+                         _p(_c(cam, np.float32)), opt.tile, _p(rect), _p(depth))
+    return rect, depth, (mu2f, extf, valid)
+
+
+def lc_wsr_weights(scene, depth64, tau: float):
+    """Eq. 5-6: w_i = max(0, 1 - d_i / tau) v_i with v_i the calibration
+    scalar of Gaussian i's cell; tau = inf gives w_i = v_i (plain WSR)."""
+    v = np.repeat(np.asarray(scene.cell_v, dtype=np.float64), scene.K)
+    if not np.isfinite(tau):
+        return v
+    return np.maximum(0.0, 1.0 - np.asarray(depth64, dtype=np.float64) / tau) * v
+
+
+def _prepare_gauss_view(scene, cam, opt, tile_rows, ordered):
+    rect, depth, (mu2f, extf, valid) = gauss_rects(scene, cam, opt)
+    if not ordered:  # weighted sums do not need a depth order: list in index order
+        depth = np.zeros_like(depth)
+    lst, rng = tile_lists(rect, depth, cam, opt)
+    W, H, Tx, Ty = grid(cam, opt.tile)
+    ty0, ty1 = (0, Ty) if tile_rows is None else tile_rows
+    used = np.zeros(scene.G, dtype=bool)
+    win = rng[ty0 * Tx: ty1 * Tx]
+    for b, e in win:
+        used[lst[b:e]] = True
+    proj, _ = project64(scene, cam, opt, used & (valid != 0))
+    return dict(rect=rect, list=lst, range=rng, mu2f=mu2f, extf=extf, valid=valid, proj=proj,
+                W=W, H=H, Tx=Tx, Ty=Ty, rows=(ty0, ty1))
+
+
+def render_alpha(scene, cam, opt: Options = Options(), forced_ndone=None, tile_rows=None):
+    """Per-Gaussian depth-sorted alpha-blending (Eq. 2-3) of one view.
+    Returns dict(C (3,H,W), T, ndone, bad, L (tile-Gaussian pairs))."""
+    pv = _prepare_gauss_view(scene, cam, opt, tile_rows, ordered=True)
+    W, H = pv["W"], pv["H"]
+    ty0, ty1 = pv["rows"]
+    pr = pv["proj"]
+    mu2, conic, opac, rgb = (_c(pr[k], np.float64) for k in ("mu2", "conic", "opac", "rgb"))
+    C = np.zeros((3, H, W)); T = np.ones((H, W)); nd = np.zeros((H, W), dtype=np.int32)
+    fn = None if forced_ndone is None else _c(forced_ndone, np.int32)
+    bad = lib().or_alpha_blend(W, H, opt.tile, _p(pv["range"]), _p(pv["list"]), _p(mu2), _p(conic), _p(opac),
+                               _p(rgb), _p(pv["mu2f"]), _p(pv["extf"]), _p(pv["valid"]), _p(opt.blend_opts()),
+                               _p(fn), ty0, ty1, _p(C), _p(T), _p(nd))
+    return dict(C=C, T=T, ndone=nd, bad=int(bad), L=int(len(pv["list"])))
+
+
+def render_wsr(scene, cam, tau: float = float("inf"), w_bg: float = 0.0, opt: Options = Options(),
+               tile_rows=None):
+    """Weighted-sum rendering (Eq. 4) with the LC-WSR weight (Eq. 5-6) of one
+    view.  Returns dict(C (3,H,W), L (tile-Gaussian pairs))."""
+    pv = _prepare_gauss_view(scene, cam, opt, tile_rows, ordered=False)
+    W, H = pv["W"], pv["H"]
+    ty0, ty1 = pv["rows"]
+    pr = pv["proj"]
+    mu2, conic, opac, rgb = (_c(pr[k], np.float64) for k in ("mu2", "conic", "opac", "rgb"))
+    w = _c(lc_wsr_weights(scene, pr["depth"], tau), np.float64)
+    C = np.zeros((3, H, W))
+    lib().or_wsr(W, H, opt.tile, _p(pv["range"]), _p(pv["list"]), _p(mu2), _p(conic), _p(opac), _p(rgb),
+                 _p(pv["mu2f"]), _p(pv["extf"]), _p(pv["valid"]), _p(w), float(w_bg), _p(opt.blend_opts()),
+                 ty0, ty1, _p(C))
+    return dict(C=C, L=int(len(pv["list"])))

@@ -12,6 +12,10 @@
  *   or_blend           hybrid renderer, Eq. 12-14, cell-level early
  *                      termination (Sec. V-B), AABB false-positive skip
  *   or_blend_grad      adjoint of or_blend (plain reverse mode), FP64
+ *   or_gauss_rects     per-Gaussian tile footprint and depth (comparators)
+ *   or_alpha_blend     per-Gaussian depth-ordered alpha-blending, Eq. 2-3
+ *   or_wsr             weighted-sum rendering, Eq. 4 with the LC-WSR weight
+ *                      of Eq. 5-6 supplied per Gaussian
  *
  * Discrete decisions (cull, tile rectangle, per-Gaussian AABB test) are taken
  * in FP32 with one prescribed operation order (no FMA contraction: build with
@@ -491,5 +495,150 @@ void or_blend_grad(int W, int H, int tile, int K, const int64_t *range, const in
                 }
             }
         free(Tn); free(An); free(Bn); free(dTn);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Comparators.  The two rendering models the paper sets Duplex-GS against  */
+/* (Sec. III-A): vanilla per-Gaussian alpha-blending over a global depth    */
+/* sort (Eq. 2-3), and sort-free weighted-sum rendering (Eq. 4) with the    */
+/* LC-WSR weight w_i = max(0, 1 - d_i / tau) v_i (Eq. 5-6).  Both use the   */
+/* same per-Gaussian alpha = min(sigma G', alpha_max), AABB skip and colour */
+/* as the hybrid renderer above; only the blending differs.                 */
+
+/*
+ * Per Gaussian of one view: the tiles its FP32 AABB box reaches and its
+ * depth.  lo = mu - ext, hi = mu + ext per axis (FP32), culled (rect = -1)
+ * when the Gaussian is invalid or the box misses the image; otherwise tiles
+ * [floor(max(lo, 0) / tile), floor(min(hi, size) / tile)] clamped to the
+ * grid.  depth = FP32 view-space z of the mean (the sort key of Eq. 3's
+ * order, and d_i of Eq. 6).
+ */
+void or_gauss_rects(int64_t G, const float *mean, const float *mu2f, const float *extf, const uint8_t *valid,
+                    const float *cam, int tile, int32_t *rect, float *depth) {
+    const int W = (int)cam[0], H = (int)cam[1];
+    const float *Rv = cam + 7, *tv = cam + 16;
+    const int Tx = (W + tile - 1) / tile, Ty = (H + tile - 1) / tile;
+    const float ftile = (float)tile;
+    for (int64_t g = 0; g < G; ++g) {
+        float t[3];
+        f32_xform(Rv, tv, mean + 3 * g, t);
+        depth[g] = t[2];
+        rect[4 * g] = rect[4 * g + 1] = rect[4 * g + 2] = rect[4 * g + 3] = -1;
+        if (!valid[g]) continue;
+        const float lox = mu2f[2 * g] - extf[2 * g], hix = mu2f[2 * g] + extf[2 * g];
+        const float loy = mu2f[2 * g + 1] - extf[2 * g + 1], hiy = mu2f[2 * g + 1] + extf[2 * g + 1];
+        if (!(hix >= 0.0f && lox < (float)W && hiy >= 0.0f && loy < (float)H)) continue;
+        int tx0 = (int)floorf(fmaxf(lox, 0.0f) / ftile);
+        int ty0 = (int)floorf(fmaxf(loy, 0.0f) / ftile);
+        int tx1 = (int)floorf(fminf(hix, (float)W) / ftile);
+        int ty1 = (int)floorf(fminf(hiy, (float)H) / ftile);
+        if (tx1 > Tx - 1) tx1 = Tx - 1;
+        if (ty1 > Ty - 1) ty1 = Ty - 1;
+        rect[4 * g] = tx0; rect[4 * g + 1] = ty0; rect[4 * g + 2] = tx1; rect[4 * g + 3] = ty1;
+    }
+}
+
+/* One pixel of Eq. 2-3: walk the tile's Gaussians front to back,
+ * C += T alpha c, T *= (1 - alpha).  Stopping rule as in the hybrid renderer
+ * at K = 1 (before entry i, stop if T_i < eps); count >= 0 forces the number
+ * of processed entries.  Returns the count; fills C, T (after), Tlast. */
+static int or_alpha_pixel(const or_scene_view *s, int64_t beg, int64_t end, int x, int y, int count,
+                          double C[3], double *Tout, double *Tlast) {
+    const float pxf = (float)x + 0.5f, pyf = (float)y + 0.5f;
+    const int len = (int)(end - beg);
+    double T = 1.0;
+    C[0] = C[1] = C[2] = 0.0;
+    *Tlast = 1.0;
+    int n = 0;
+    for (; n < len; ++n) {
+        if (count < 0 && T < s->eps) break;
+        if (count >= 0 && n >= count) break;
+        const int64_t g = s->cells[beg + n];
+        double G, dx, dy; int cl;
+        const double al = or_alpha(s, g, pxf, pyf, &G, &cl, &dx, &dy);
+        C[0] += T * al * s->rgb[3 * g]; C[1] += T * al * s->rgb[3 * g + 1]; C[2] += T * al * s->rgb[3 * g + 2];
+        *Tlast = T;
+        T *= (1.0 - al);
+    }
+    *Tout = T;
+    return n;
+}
+
+/*
+ * Per-Gaussian alpha-blending of tile rows [ty0, ty1) of one view; `list`
+ * and `range` are the tile lists of Gaussians ordered by (tile, depth,
+ * index).  out_C [3][H][W] = sum_i T_i alpha_i c_i + T_final bg (the 3DGS
+ * background convention); out_T, out_ndone [H][W].  forced_ndone as in
+ * or_blend (returns the number of invalid forced counts).
+ * opts: eps alpha_max d_min bg_r bg_g bg_b delta.
+ */
+int64_t or_alpha_blend(int W, int H, int tile, const int64_t *range, const int32_t *list,
+                       const double *mu2, const double *conic, const double *opac, const double *rgb,
+                       const float *mu2f, const float *extf, const uint8_t *valid, const double *opts,
+                       const int32_t *forced_ndone, int ty0, int ty1, double *out_C, double *out_T,
+                       int32_t *out_ndone) {
+    or_scene_view s;
+    or_unpack(&s, W, H, tile, 1, range, list, mu2, conic, opac, rgb, mu2f, extf, valid, NULL, opts);
+    const int Tx = (W + tile - 1) / tile;
+    const int64_t HW = (int64_t)H * W;
+    int64_t bad = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : bad)
+    for (int64_t tid = (int64_t)ty0 * Tx; tid < (int64_t)ty1 * Tx; ++tid) {
+        const int tx = (int)(tid % Tx), ty = (int)(tid / Tx);
+        const int64_t beg = range[2 * tid], end = range[2 * tid + 1];
+        for (int y = ty * tile; y < (ty + 1) * tile && y < H; ++y)
+            for (int x = tx * tile; x < (tx + 1) * tile && x < W; ++x) {
+                const int64_t p = (int64_t)y * W + x;
+                double C[3], T, Tl;
+                const int own = or_alpha_pixel(&s, beg, end, x, y, -1, C, &T, &Tl);
+                if (forced_ndone) {
+                    const int cnt = forced_ndone[p];
+                    or_alpha_pixel(&s, beg, end, x, y, cnt < 0 ? 0 : cnt, C, &T, &Tl);
+                    if (!or_count_ok(&s, (int)(end - beg), cnt, Tl, T)) bad += 1;
+                }
+                for (int c = 0; c < 3; ++c) out_C[c * HW + p] = C[c] + T * s.bg[c];
+                out_T[p] = T; out_ndone[p] = own;
+            }
+    }
+    return bad;
+}
+
+/*
+ * Weighted-sum rendering (Eq. 4) of tile rows [ty0, ty1) of one view over
+ * the Gaussians of each tile's list (any order: the sums commute):
+ *   C = (c_B w_B + sum_i c_i alpha_i w_i) / (w_B + sum_i alpha_i w_i),
+ * with w_i given per Gaussian (Eq. 5-6: max(0, 1 - d_i / tau) v_i) and the
+ * background weight w_bg; a pixel whose denominator is not above d_min
+ * shows the background.  No transmittance, no termination.
+ */
+void or_wsr(int W, int H, int tile, const int64_t *range, const int32_t *list, const double *mu2,
+            const double *conic, const double *opac, const double *rgb, const float *mu2f, const float *extf,
+            const uint8_t *valid, const double *w, double w_bg, const double *opts, int ty0, int ty1,
+            double *out_C) {
+    or_scene_view s;
+    or_unpack(&s, W, H, tile, 1, range, list, mu2, conic, opac, rgb, mu2f, extf, valid, NULL, opts);
+    const int Tx = (W + tile - 1) / tile;
+    const int64_t HW = (int64_t)H * W;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t tid = (int64_t)ty0 * Tx; tid < (int64_t)ty1 * Tx; ++tid) {
+        const int tx = (int)(tid % Tx), ty = (int)(tid / Tx);
+        const int64_t beg = range[2 * tid], end = range[2 * tid + 1];
+        for (int y = ty * tile; y < (ty + 1) * tile && y < H; ++y)
+            for (int x = tx * tile; x < (tx + 1) * tile && x < W; ++x) {
+                const int64_t p = (int64_t)y * W + x;
+                const float pxf = (float)x + 0.5f, pyf = (float)y + 0.5f;
+                double A[3] = {0, 0, 0}, B = 0.0;
+                for (int64_t e = beg; e < end; ++e) {
+                    const int64_t g = list[e];
+                    double G, dx, dy; int cl;
+                    const double aw = or_alpha(&s, g, pxf, pyf, &G, &cl, &dx, &dy) * w[g];
+                    A[0] += aw * rgb[3 * g]; A[1] += aw * rgb[3 * g + 1]; A[2] += aw * rgb[3 * g + 2];
+                    B += aw;
+                }
+                const double den = w_bg + B;
+                for (int c = 0; c < 3; ++c)
+                    out_C[c * HW + p] = den > s.d_min ? (s.bg[c] * w_bg + A[c]) / den : s.bg[c];
+            }
     }
 }
