@@ -261,6 +261,46 @@ dgs_status dgs_profile_read(dgs_ctx *ctx, dgs_profile *out);
  *     once at the end (to read the sort's error flag). */
 dgs_status dgs_sort_pairs_noalloc(uint32_t *keys, uint32_t *vals, int64_t n, int32_t bits, dgs_stream stream);
 
+/* ------------------------------------------------------------- comparators */
+
+/* The two rendering models Duplex-GS is set against (Sec. III-A), on the same
+ * resident scenes and per-Gaussian projection (record, AABB skip, colour,
+ * alpha = min(sigma G', alpha_max)) as dgs_render, for the sort-length and
+ * speed comparison of Tab. VI:
+ *
+ *   DGS_COMPARE_ALPHA  vanilla per-Gaussian alpha-blending, Eq. 2-3: every
+ *                      (view, Gaussian) is binned to the tiles its AABB box
+ *                      reaches and sorted by view depth (ties by index);
+ *                      C = sum_i T_i alpha_i c_i + T_final bg with
+ *                      T_i = prod_{j<i} (1 - alpha_j); a pixel stops before the
+ *                      entry at which T < eps (config eps).
+ *   DGS_COMPARE_WSR    sort-free weighted-sum rendering, Eq. 4, with the
+ *                      LC-WSR weight of Eq. 5-6, w_i = max(0, 1 - d_i / tau) v_i
+ *                      (d_i the view depth of the mean, v_i the v_n of its
+ *                      cell; tau <= 0 or non-finite: w_i = v_i):
+ *                      C = (bg w_bg + sum_i c_i alpha_i w_i) / (w_bg + sum_i alpha_i w_i),
+ *                      the background where that denominator is not above d_min.
+ *                      No depth sort, no termination.
+ *
+ * out_rgb: device, the images back to back as for dgs_render.  out_ndone
+ * (nullable, device, int32 [H][W] per view back to back; ALPHA only): the
+ * number of tile-list entries each pixel processed.  stats (nullable):
+ * sort_length = (tile, Gaussian) pairs, visible_cells = (view, Gaussian)
+ * entries kept.  Synchronises the stream once (to size the pair sort).
+ * Errors: INVALID_ARG (mode, w_bg < 0, NULL), NOT_FOUND (scene, camera),
+ * OOM, CAPACITY (views x Gaussians >= 2^32), TIMEOUT (sort wait gave up). */
+#define DGS_COMPARE_ALPHA 1
+#define DGS_COMPARE_WSR 2
+typedef struct {
+    int32_t mode;
+    float tau;
+    float w_bg;
+    int32_t reserved;
+} dgs_compare_config;
+dgs_status dgs_render_compare(dgs_ctx *ctx, uint32_t scene_id, int32_t n_views, const uint32_t *cam_slots,
+                              const dgs_compare_config *cfg, float *out_rgb, int32_t *out_ndone,
+                              dgs_stream stream, dgs_stats *stats);
+
 /* ---------------------------------------------------------------- serving */
 
 /* Continuous-batching request loop (not in the paper; serving workload).

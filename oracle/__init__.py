@@ -308,18 +308,23 @@ def lc_wsr_weights(scene, depth64, tau: float):
 
 def _prepare_gauss_view(scene, cam, opt, tile_rows, ordered):
     rect, depth, (mu2f, extf, valid) = gauss_rects(scene, cam, opt)
+    vis = rect[:, 0] >= 0
+    L = int(((rect[vis, 2] - rect[vis, 0] + 1).astype(np.int64) * (rect[vis, 3] - rect[vis, 1] + 1)).sum())
     if not ordered:  # weighted sums do not need a depth order: list in index order
         depth = np.zeros_like(depth)
-    lst, rng = tile_lists(rect, depth, cam, opt)
     W, H, Tx, Ty = grid(cam, opt.tile)
     ty0, ty1 = (0, Ty) if tile_rows is None else tile_rows
+    if tile_rows is not None:  # lists of the rendered rows only (the same lists for those tiles)
+        rect = rect.copy()
+        rect[(rect[:, 3] < ty0) | (rect[:, 1] >= ty1)] = -1
+    lst, rng = tile_lists(rect, depth, cam, opt)
     used = np.zeros(scene.G, dtype=bool)
     win = rng[ty0 * Tx: ty1 * Tx]
     for b, e in win:
         used[lst[b:e]] = True
     proj, _ = project64(scene, cam, opt, used & (valid != 0))
     return dict(rect=rect, list=lst, range=rng, mu2f=mu2f, extf=extf, valid=valid, proj=proj,
-                W=W, H=H, Tx=Tx, Ty=Ty, rows=(ty0, ty1))
+                W=W, H=H, Tx=Tx, Ty=Ty, rows=(ty0, ty1), L=L)
 
 
 def render_alpha(scene, cam, opt: Options = Options(), forced_ndone=None, tile_rows=None):
@@ -335,7 +340,7 @@ def render_alpha(scene, cam, opt: Options = Options(), forced_ndone=None, tile_r
     bad = lib().or_alpha_blend(W, H, opt.tile, _p(pv["range"]), _p(pv["list"]), _p(mu2), _p(conic), _p(opac),
                                _p(rgb), _p(pv["mu2f"]), _p(pv["extf"]), _p(pv["valid"]), _p(opt.blend_opts()),
                                _p(fn), ty0, ty1, _p(C), _p(T), _p(nd))
-    return dict(C=C, T=T, ndone=nd, bad=int(bad), L=int(len(pv["list"])))
+    return dict(C=C, T=T, ndone=nd, bad=int(bad), L=pv["L"])
 
 
 def render_wsr(scene, cam, tau: float = float("inf"), w_bg: float = 0.0, opt: Options = Options(),
@@ -352,4 +357,4 @@ def render_wsr(scene, cam, tau: float = float("inf"), w_bg: float = 0.0, opt: Op
     lib().or_wsr(W, H, opt.tile, _p(pv["range"]), _p(pv["list"]), _p(mu2), _p(conic), _p(opac), _p(rgb),
                  _p(pv["mu2f"]), _p(pv["extf"]), _p(pv["valid"]), _p(w), float(w_bg), _p(opt.blend_opts()),
                  ty0, ty1, _p(C))
-    return dict(C=C, L=int(len(pv["list"])))
+    return dict(C=C, L=pv["L"])

@@ -87,6 +87,12 @@ class dgs_serve_stats(C.Structure):
 
 
 DGS_SERVE_NO_GRAPHS = 1
+DGS_COMPARE_ALPHA = 1
+DGS_COMPARE_WSR = 2
+
+
+class dgs_compare_config(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("tau", C.c_float), ("w_bg", C.c_float), ("reserved", C.c_int32)]
 
 
 class dgs_result(C.Structure):
@@ -114,6 +120,8 @@ _SIGS = {
     "dgs_state_counts": (C.c_int32, [_P, _P, C.POINTER(dgs_counts)]),
     "dgs_profile_enable": (C.c_int32, [_P, C.c_int32]),
     "dgs_profile_read": (C.c_int32, [_P, C.POINTER(dgs_profile)]),
+    "dgs_render_compare": (C.c_int32, [_P, C.c_uint32, C.c_int32, C.POINTER(C.c_uint32),
+                                       C.POINTER(dgs_compare_config), _P, _P, _P, C.POINTER(dgs_stats)]),
     "dgs_serve_start": (C.c_int32, [_P, C.c_int32, C.c_int32, C.c_int32]),
     "dgs_serve_read_stats": (C.c_int32, [_P, C.POINTER(dgs_serve_stats)]),
     "dgs_serve_stop": (C.c_int32, [_P]),
@@ -211,6 +219,14 @@ def dgs_render(ctx, scene_id: int, cam_slots, out_ptr: int, out_location: int, w
                             C.byref(state) if want_state else None, _P(stream),
                             C.byref(stats) if stats is not None else None), ctx)
     return state if want_state else None
+
+
+def dgs_render_compare(ctx, scene_id: int, cam_slots, cfg: dgs_compare_config, out_ptr: int, ndone_ptr,
+                       stream: int = 0, stats: dgs_stats | None = None):
+    slots = (C.c_uint32 * len(cam_slots))(*cam_slots)
+    check(load().dgs_render_compare(ctx, scene_id, len(cam_slots), slots, C.byref(cfg), _P(out_ptr),
+                                    _P(ndone_ptr) if ndone_ptr else None, _P(stream),
+                                    C.byref(stats) if stats is not None else None), ctx)
 
 
 def dgs_render_backward(ctx, state, dl_ptr: int, location: int, grads: dgs_grads, stream: int = 0):

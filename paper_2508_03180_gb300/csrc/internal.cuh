@@ -139,6 +139,11 @@ void exclusive_scan_u32(const uint32_t *in, uint32_t *out, long long n, uint32_t
 // scene_slot differs from `slot` are skipped)
 void launch_project_fwd(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const uint32_t *count,
                         const BlendParams &bp, float4 *rec, float *g2d_zero, cudaStream_t st);
+// Comparator binning: one entry per (view, Gaussian), entry e = cell_base + g
+// (views with N = G, K = 1 entries); wsr selects the LC-WSR weight in r2.w.
+void launch_gauss_bin(const ViewDesc *views, int n_views, const SceneDev &sc, const BlendParams &bp, bool wsr,
+                      float tau, float4 *rec, uint32_t *zkey, uint32_t *zval, short4 *rect, uint32_t *count,
+                      uint32_t *visible, cudaStream_t st);
 // One launch for every scene of the device scene table (dsz->n_scenes
 // entries, Gaussian counts <= G_cap, which sizes the grid).
 void launch_project_fwd_table(const ViewDesc *views, const SceneDev *scenes, long long G_cap, const uint32_t *count,

@@ -166,6 +166,58 @@ __device__ __forceinline__ void proj_core(const ViewDesc &Vw, const GaussIn &p, 
     c.syy = fadd_s(fadd_s(fadd_s(fmul_s(c.V[3], c.T[3]), fmul_s(c.V[4], c.T[4])), fmul_s(c.V[5], c.T[5])), dilation);
 }
 
+// The 48-byte record of Gaussian p in view Vw (an invalid Gaussian, mean not
+// in front of the near plane, gets ext = -1 so no AABB test passes).  k: SH
+// coefficients, cv: the cell's v_n.  Returns c.valid; c keeps the view-space mean.
+__device__ __forceinline__ bool gauss_record(const ViewDesc &Vw, const GaussIn &p, const float (&k)[16][3],
+                                             int sh_degree, float opac, float cv, const BlendParams &bp,
+                                             ProjCore &c, float4 &r0, float4 &r1, float4 &r2) {
+    proj_core(Vw, p, bp.dilation, c);
+    if (!c.valid) {
+        r0 = make_float4(0.f, 0.f, -1.f, -1.f);
+        r1 = make_float4(0.f, 0.f, 0.f, 0.f);
+        r2 = make_float4(0.f, 0.f, 0.f, cv);
+        return false;
+    }
+    const float mx = fadd_s(fmul_s(Vw.fx, c.x), Vw.cx);
+    const float my = fadd_s(fmul_s(Vw.fy, c.y), Vw.cy);
+    const float ex = fmul_s(bp.ksigma, fsqrt_s(c.sxx));
+    const float ey = fmul_s(bp.ksigma, fsqrt_s(c.syy));
+    // conic Q = Sigma'^-1 = L L^T, L = [[p, 0], [r, t]]:
+    // p = sqrt(s_yy/det), r = -s_xy/sqrt(s_yy det), t = 1/sqrt(s_yy),
+    // so q(d) = (p dx + r dy)^2 + (t dy)^2 is a sum of squares
+    const ScreenCov sc2 = screen_cov(c, bp.dilation);
+    const float ip = rsqrtf(sc2.syy * sc2.det);
+    const float fp = sc2.syy * ip, fr = -sc2.sxy * ip, ft = rsqrtf(sc2.syy);
+    float d0 = p.mean[0] - Vw.eye[0], d1 = p.mean[1] - Vw.eye[1], d2 = p.mean[2] - Vw.eye[2];
+    const float il = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+    d0 *= il; d1 *= il; d2 *= il;
+    float Y[16];
+    sh_eval(d0, d1, d2, sh_degree, Y);
+    float col[3];
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        float s = 0.5f;
+#pragma unroll
+        for (int cidx = 0; cidx < 16; ++cidx) s += k[cidx][ch] * Y[cidx];
+        col[ch] = fmaxf(s, 0.0f);
+    }
+    r0 = make_float4(mx, my, ex, ey);
+    // L scaled by kappa = sqrt(log2(e)/2): G' = exp2(-(s1^2 + s2^2)),
+    // s1 = r1.x dx + r1.y dy, s2 = r1.z dy
+    r1 = make_float4(KAPPA * fp, KAPPA * fr, KAPPA * ft, opac);
+    r2 = make_float4(col[0], col[1], col[2], cv);
+    return true;
+}
+
+__device__ __forceinline__ void load_sh(const SceneDev &sc, long long g, float (&k)[16][3]) {
+    const int C = (sc.sh_degree + 1) * (sc.sh_degree + 1);
+#pragma unroll
+    for (int c = 0; c < 16; ++c)
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) k[c][ch] = c < C ? sc.sh[(c * 3 + ch) * sc.G + g] : 0.f;
+}
+
 // Records of every Gaussian of scene `slot` (grid-stride over its G) for each
 // view of that scene in which its cell survived culling.
 __device__ __forceinline__ void project_scene(const ViewDesc *__restrict__ views, int n_views, int slot,
@@ -173,7 +225,7 @@ __device__ __forceinline__ void project_scene(const ViewDesc *__restrict__ views
                                               const BlendParams &bp, float4 *__restrict__ rec,
                                               float *__restrict__ g2d_zero) {
     const long long G = sc.G, N = sc.N;
-    const int K = sc.K, C = (sc.sh_degree + 1) * (sc.sh_degree + 1);
+    const int K = sc.K;
     for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < G; g += (long long)gridDim.x * blockDim.x) {
         const long long cell = g / K;
         bool any = false;
@@ -182,52 +234,15 @@ __device__ __forceinline__ void project_scene(const ViewDesc *__restrict__ views
         if (!any) continue;  // cell culled in every view: nothing reads this Gaussian
         const GaussIn p = load_gauss(sc.gauss, G, g);
         float k[16][3];
-#pragma unroll
-        for (int c = 0; c < 16; ++c)
-#pragma unroll
-            for (int ch = 0; ch < 3; ++ch) k[c][ch] = c < C ? sc.sh[(c * 3 + ch) * G + g] : 0.f;
+        load_sh(sc, g, k);
         const float opac = 1.0f / (1.0f + expf(-p.logit));
         const float cv = sc.cell[10 * N + cell];
         for (int v = 0; v < n_views; ++v) {
             const ViewDesc &Vw = views[v];
             if (Vw.scene_slot != slot || count[Vw.cell_base + cell] == 0u) continue;
             ProjCore c;
-            proj_core(Vw, p, bp.dilation, c);
             float4 r0, r1, r2;
-            if (!c.valid) {
-                r0 = make_float4(0.f, 0.f, -1.f, -1.f);
-                r1 = make_float4(0.f, 0.f, 0.f, 0.f);
-                r2 = make_float4(0.f, 0.f, 0.f, cv);
-            } else {
-                const float mx = fadd_s(fmul_s(Vw.fx, c.x), Vw.cx);
-                const float my = fadd_s(fmul_s(Vw.fy, c.y), Vw.cy);
-                const float ex = fmul_s(bp.ksigma, fsqrt_s(c.sxx));
-                const float ey = fmul_s(bp.ksigma, fsqrt_s(c.syy));
-                // conic Q = Sigma'^-1 = L L^T, L = [[p, 0], [r, t]]:
-                // p = sqrt(s_yy/det), r = -s_xy/sqrt(s_yy det), t = 1/sqrt(s_yy),
-                // so q(d) = (p dx + r dy)^2 + (t dy)^2 is a sum of squares
-                const ScreenCov sc2 = screen_cov(c, bp.dilation);
-                const float ip = rsqrtf(sc2.syy * sc2.det);
-                const float fp = sc2.syy * ip, fr = -sc2.sxy * ip, ft = rsqrtf(sc2.syy);
-                float d0 = p.mean[0] - Vw.eye[0], d1 = p.mean[1] - Vw.eye[1], d2 = p.mean[2] - Vw.eye[2];
-                const float il = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
-                d0 *= il; d1 *= il; d2 *= il;
-                float Y[16];
-                sh_eval(d0, d1, d2, sc.sh_degree, Y);
-                float col[3];
-#pragma unroll
-                for (int ch = 0; ch < 3; ++ch) {
-                    float s = 0.5f;
-#pragma unroll
-                    for (int cidx = 0; cidx < 16; ++cidx) s += k[cidx][ch] * Y[cidx];
-                    col[ch] = fmaxf(s, 0.0f);
-                }
-                r0 = make_float4(mx, my, ex, ey);
-                // L scaled by kappa = sqrt(log2(e)/2): G' = exp2(-(s1^2 + s2^2)),
-                // s1 = r1.x dx + r1.y dy, s2 = r1.z dy
-                r1 = make_float4(KAPPA * fp, KAPPA * fr, KAPPA * ft, opac);
-                r2 = make_float4(col[0], col[1], col[2], cv);
-            }
+            gauss_record(Vw, p, k, sc.sh_degree, opac, cv, bp, c, r0, r1, r2);
             float4 *o = rec + (Vw.rec_base + g) * kRecF4;
             o[0] = r0; o[1] = r1; o[2] = r2;
             if (g2d_zero) {
@@ -236,6 +251,65 @@ __device__ __forceinline__ void project_scene(const ViewDesc *__restrict__ views
             }
         }
     }
+}
+
+// Comparator binning (per-Gaussian alpha-blending, Eq. 2-3, and weighted-sum
+// rendering, Eq. 4-6): every Gaussian of every view is an entry of its own.
+// Per entry e = cell_base + g of view v: the record (r2.w = the weight w_i:
+// v_n for alpha-blending, max(0, 1 - z / tau) v_n for LC-WSR, tau <= 0 meaning
+// no depth decay), the tiles its FP32 AABB box reaches, its depth key (FP32
+// view z; 0xFFFFFFFF when culled) and tile count.  Culled: invalid, box off
+// the image, or (weighted sums) w = 0.
+__global__ void __launch_bounds__(128) k_gauss_bin(const ViewDesc *__restrict__ views, int n_views, SceneDev sc,
+                                                   BlendParams bp, bool wsr, float tau, float4 *__restrict__ rec,
+                                                   uint32_t *__restrict__ zkey, uint32_t *__restrict__ zval,
+                                                   short4 *__restrict__ rect, uint32_t *__restrict__ count,
+                                                   uint32_t *__restrict__ visible) {
+    const long long G = sc.G, N = sc.N;
+    const int K = sc.K;
+    uint32_t nvis = 0;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < G; g += (long long)gridDim.x * blockDim.x) {
+        const GaussIn p = load_gauss(sc.gauss, G, g);
+        float k[16][3];
+        load_sh(sc, g, k);
+        const float opac = 1.0f / (1.0f + expf(-p.logit));
+        const float cv = sc.cell[10 * N + g / K];
+        for (int v = 0; v < n_views; ++v) {
+            const ViewDesc &Vw = views[v];
+            ProjCore c;
+            float4 r0, r1, r2;
+            bool vis = gauss_record(Vw, p, k, sc.sh_degree, opac, cv, bp, c, r0, r1, r2);
+            if (wsr) {
+                r2.w = tau > 0.f ? fmaxf(0.f, 1.f - c.t[2] / tau) * cv : cv;
+                vis = vis && r2.w > 0.f;
+            }
+            short4 r = make_short4(-1, -1, -1, -1);
+            if (vis) {
+                const float lox = fsub_s(r0.x, r0.z), hix = fadd_s(r0.x, r0.z);
+                const float loy = fsub_s(r0.y, r0.w), hiy = fadd_s(r0.y, r0.w);
+                const float fW = (float)Vw.W, fH = (float)Vw.H, ft = (float)kTile;
+                vis = hix >= 0.0f && lox < fW && hiy >= 0.0f && loy < fH;
+                if (vis) {
+                    const int tx0 = (int)floorf(fdiv_s(fmaxf(lox, 0.0f), ft));
+                    const int ty0 = (int)floorf(fdiv_s(fmaxf(loy, 0.0f), ft));
+                    const int tx1 = min((int)floorf(fdiv_s(fminf(hix, fW), ft)), Vw.Tx - 1);
+                    const int ty1 = min((int)floorf(fdiv_s(fminf(hiy, fH), ft)), Vw.Ty - 1);
+                    r = make_short4((short)tx0, (short)ty0, (short)tx1, (short)ty1);
+                }
+            }
+            const long long e = Vw.cell_base + g;
+            float4 *o = rec + (Vw.rec_base + g) * kRecF4;
+            o[0] = r0; o[1] = r1; o[2] = r2;
+            rect[e] = r;
+            zkey[e] = vis ? __float_as_uint(c.t[2]) : 0xFFFFFFFFu;
+            zval[e] = (uint32_t)e;
+            count[e] = vis ? (uint32_t)((r.z - r.x + 1) * (r.w - r.y + 1)) : 0u;
+            nvis += vis ? 1u : 0u;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nvis += __shfl_xor_sync(0xffffffffu, nvis, o);
+    if ((threadIdx.x & 31) == 0 && nvis) atomicAdd(visible, nvis);
 }
 
 __global__ void __launch_bounds__(128) k_project_fwd(const ViewDesc *__restrict__ views, int n_views, int slot,
@@ -268,6 +342,14 @@ void launch_project_fwd(const ViewDesc *views, int n_views, int slot, const Scen
                         const BlendParams &bp, float4 *rec, float *g2d_zero, cudaStream_t st) {
     if (sc.G == 0 || n_views == 0) return;
     k_project_fwd<<<grid_for(sc.G, 128), 128, 0, st>>>(views, n_views, slot, sc, count, bp, rec, g2d_zero);
+}
+
+void launch_gauss_bin(const ViewDesc *views, int n_views, const SceneDev &sc, const BlendParams &bp, bool wsr,
+                      float tau, float4 *rec, uint32_t *zkey, uint32_t *zval, short4 *rect, uint32_t *count,
+                      uint32_t *visible, cudaStream_t st) {
+    if (sc.G == 0 || n_views == 0) return;
+    k_gauss_bin<<<grid_for(sc.G, 128), 128, 0, st>>>(views, n_views, sc, bp, wsr, tau, rec, zkey, zval, rect, count,
+                                                     visible);
 }
 
 void launch_project_fwd_table(const ViewDesc *views, const SceneDev *scenes, long long G_cap, const uint32_t *count,

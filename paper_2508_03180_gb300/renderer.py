@@ -130,6 +130,25 @@ class Context:
         state = L.dgs_render(self.ctx, scene_id, slots, _ptr(out), L.DGS_DEVICE, want_state, _stream(), st)
         return out, state, st
 
+    def render_compare(self, scene_id: int, cams, mode: str = "alpha", tau: float = float("inf"),
+                       w_bg: float = 0.0, want_ndone: bool = False, stats: bool = False):
+        """Comparator renderers: mode "alpha" (per-Gaussian depth-sorted
+        alpha-blending) or "wsr" (weighted-sum rendering with the LC-WSR
+        weight; tau = inf for plain WSR).  Returns (flat image, ndone or None,
+        stats or None)."""
+        slots = self.set_cameras(cams)
+        sizes = self.image_sizes(cams)
+        out = torch.empty(sum(3 * h * w for h, w in sizes), dtype=torch.float32, device=self.device)
+        nd = torch.empty(sum(h * w for h, w in sizes), dtype=torch.int32, device=self.device) if want_ndone else None
+        cfg = L.dgs_compare_config()
+        cfg.mode = {"alpha": L.DGS_COMPARE_ALPHA, "wsr": L.DGS_COMPARE_WSR}[mode]
+        cfg.tau = tau if np.isfinite(tau) else 0.0
+        cfg.w_bg = w_bg
+        st = L.dgs_stats() if stats else None
+        L.dgs_render_compare(self.ctx, scene_id, slots, cfg, _ptr(out), _ptr(nd) if nd is not None else 0,
+                             _stream(), st)
+        return out, nd, st
+
     def render_host(self, scene_id: int, cams, out: np.ndarray):
         slots = self.set_cameras(cams)
         L.dgs_render(self.ctx, scene_id, slots, out.ctypes.data, L.DGS_HOST, False, _stream(), None)

@@ -43,9 +43,10 @@ def test_struct_sizes_match_the_header():
 #include "dgs.h"
 #include <stddef.h>
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(dgs_config), sizeof(dgs_scene_desc), sizeof(dgs_camera),
-         sizeof(dgs_stats), sizeof(dgs_grads), sizeof(dgs_request), sizeof(dgs_result),
-         offsetof(dgs_request, out_rgb));
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(dgs_config), sizeof(dgs_scene_desc),
+         sizeof(dgs_camera), sizeof(dgs_stats), sizeof(dgs_grads), sizeof(dgs_request), sizeof(dgs_result),
+         offsetof(dgs_request, out_rgb), sizeof(dgs_serve_stats), sizeof(dgs_compare_config),
+         offsetof(dgs_compare_config, w_bg));
   return 0;
 }
 '''
@@ -57,5 +58,6 @@ int main(void) {
         got = [int(x) for x in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
     want = [ctypes.sizeof(L.dgs_config), ctypes.sizeof(L.dgs_scene_desc), ctypes.sizeof(L.dgs_camera),
             ctypes.sizeof(L.dgs_stats), ctypes.sizeof(L.dgs_grads), ctypes.sizeof(L.dgs_request),
-            ctypes.sizeof(L.dgs_result), L.dgs_request.out_rgb.offset]
+            ctypes.sizeof(L.dgs_result), L.dgs_request.out_rgb.offset, ctypes.sizeof(L.dgs_serve_stats),
+            ctypes.sizeof(L.dgs_compare_config), L.dgs_compare_config.w_bg.offset]
     assert got == want

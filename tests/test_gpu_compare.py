@@ -1,0 +1,155 @@
+"""Comparator renderers on the GPU (dgs_render_compare) against their
+oracles: per-Gaussian alpha-blending (Eq. 2-3) under the same
+termination-count protocol as the hybrid renderer, and weighted-sum
+rendering with the LC-WSR weight (Eq. 4-6); pair counts bit-exact; batched
+views identical to single views; sampled bands at the large-scale size."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2508_03180_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+IMG_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def rctx():
+    from paper_2508_03180_gb300.renderer import Context
+    c = Context()
+    yield c
+    c.close()
+
+
+def _cams():
+    return [synth.small_camera(64, 48), synth.sphere_cameras(1, 3.0, 100, 70, seed0=4)[0],
+            synth.sphere_cameras(1, 2.5, 33, 17, seed0=9)[0]]
+
+
+def _alpha_check(scene, cam, img, nd, rows=None, opt=oracle.Options()):
+    W, H = cam.W, cam.H
+    r = oracle.render_alpha(scene, cam.as_array(), opt, forced_ndone=nd.reshape(H, W), tile_rows=rows)
+    y0, y1 = (0, H) if rows is None else (rows[0] * 16, min(rows[1] * 16, H))
+    assert r["bad"] == 0
+    diff = int((r["ndone"][y0:y1] != nd.reshape(H, W)[y0:y1]).sum())
+    assert diff <= max(2, int(5e-4 * (y1 - y0) * W))
+    err = float(np.abs(img.reshape(3, H, W)[:, y0:y1] - r["C"][:, y0:y1]).max())
+    assert err <= IMG_TOL, err
+    return r
+
+
+@pytest.mark.parametrize("sh", [0, 3])
+def test_alpha_blend_matches_oracle(rctx, sh):
+    scene = synth.scene_small(seed=1, sh_degree=sh)
+    sid = rctx.upload_scene(scene)
+    try:
+        for cam in _cams():
+            img, nd, st = rctx.render_compare(sid, [cam], "alpha", want_ndone=True, stats=True)
+            r = _alpha_check(scene, cam, img.cpu().numpy(), nd.cpu().numpy())
+            assert st.sort_length == r["L"]
+    finally:
+        rctx.release_scene(sid)
+
+
+def test_alpha_blend_terminates(rctx):
+    # an opaque scene: many pixels stop early, the counts still validate
+    s = synth.scene_small(seed=2, n_cells=4000)
+    s.g_logit[:] += 4.0
+    s.g_scale[:] *= 3.0
+    sid = rctx.upload_scene(s)
+    try:
+        cam = synth.small_camera(96, 64)
+        img, nd, _ = rctx.render_compare(sid, [cam], "alpha", want_ndone=True)
+        r = _alpha_check(s, cam, img.cpu().numpy(), nd.cpu().numpy())
+        assert (r["T"] < 1e-4).mean() > 0.05
+    finally:
+        rctx.release_scene(sid)
+
+
+@pytest.mark.parametrize("tau,w_bg", [(float("inf"), 0.0), (3.0, 0.0), (3.2, 0.05)])
+def test_wsr_matches_oracle(rctx, tau, w_bg):
+    scene = synth.scene_small(seed=3, sh_degree=3)
+    sid = rctx.upload_scene(scene)
+    try:
+        for cam in _cams():
+            img, _, st = rctx.render_compare(sid, [cam], "wsr", tau=tau, w_bg=w_bg, stats=True)
+            r = oracle.render_wsr(scene, cam.as_array(), tau=tau, w_bg=w_bg)
+            err = float(np.abs(img.cpu().numpy().reshape(r["C"].shape) - r["C"]).max())
+            assert err <= IMG_TOL, err
+            if not np.isfinite(tau):  # every drawable Gaussian is kept (w = v > 0)
+                assert st.sort_length == r["L"]
+    finally:
+        rctx.release_scene(sid)
+
+
+def test_background_and_batch(rctx):
+    from paper_2508_03180_gb300.renderer import Context
+    bg = (0.1, 0.2, 0.3)
+    c = Context(bg=bg)
+    scene = synth.scene_small(seed=4)
+    sid = c.upload_scene(scene)
+    cams = _cams()
+    opt = oracle.Options(bg=bg)
+    a_b, nd_b, _ = c.render_compare(sid, cams, "alpha", want_ndone=True)
+    w_b, _, _ = c.render_compare(sid, cams, "wsr", tau=3.0, w_bg=0.02)
+    a_v = c.split(a_b, cams)
+    w_v = c.split(w_b, cams)
+    o = 0
+    for i, cam in enumerate(cams):
+        a1, nd1, _ = c.render_compare(sid, [cam], "alpha", want_ndone=True)
+        w1, _, _ = c.render_compare(sid, [cam], "wsr", tau=3.0, w_bg=0.02)
+        assert torch.equal(a1, a_v[i].reshape(-1))
+        assert torch.equal(w1, w_v[i].reshape(-1))
+        n = cam.W * cam.H
+        assert torch.equal(nd1, nd_b[o:o + n])
+        o += n
+        _alpha_check(scene, cam, a1.cpu().numpy(), nd1.cpu().numpy(), opt=opt)
+        r = oracle.render_wsr(scene, cam.as_array(), tau=3.0, w_bg=0.02, opt=opt)
+        assert float(np.abs(w1.cpu().numpy().reshape(r["C"].shape) - r["C"]).max()) <= IMG_TOL
+    c.close()
+
+
+def test_errors(rctx):
+    from paper_2508_03180_gb300 import _lib as L
+    sid = rctx.upload_scene(synth.scene_small(seed=5, n_cells=64))
+    try:
+        with pytest.raises(L.DgsError):
+            rctx.render_compare(sid, [synth.small_camera(32, 32)], "wsr", w_bg=-1.0)
+        with pytest.raises(L.DgsError):
+            rctx.render_compare(sid + 1000, [synth.small_camera(32, 32)], "alpha")
+    finally:
+        rctx.release_scene(sid)
+
+
+_LARGE = {}
+
+
+def _large():
+    if "s" not in _LARGE:
+        _LARGE["s"] = synth.scene_large()
+    return _LARGE["s"]
+
+
+@pytest.mark.parametrize("mode", ["alpha", "wsr"])
+def test_large_scale_band(rctx, mode):
+    scene = _large()
+    cams = synth.street_cameras(1, 1920, 1080, seed0=3)
+    sid = rctx.upload_scene(scene)
+    try:
+        img, nd, st = rctx.render_compare(sid, cams, mode, tau=float("inf") if mode == "alpha" else 60.0,
+                                          want_ndone=mode == "alpha", stats=True)
+        cam = cams[0]
+        Ty = (cam.H + 15) // 16
+        rows = (Ty // 2 - 1, Ty // 2 + 1)
+        if mode == "alpha":
+            r = _alpha_check(scene, cam, img.cpu().numpy(), nd.cpu().numpy(), rows=rows)
+            assert st.sort_length == r["L"]
+        else:
+            r = oracle.render_wsr(scene, cam.as_array(), tau=60.0, tile_rows=rows)
+            y0, y1 = rows[0] * 16, rows[1] * 16
+            got = img.cpu().numpy().reshape(3, cam.H, cam.W)[:, y0:y1]
+            assert float(np.abs(got - r["C"][:, y0:y1]).max()) <= IMG_TOL
+    finally:
+        rctx.release_scene(sid)
