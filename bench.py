@@ -264,6 +264,112 @@ def serving_bench(rctx, rates=(200.0, 1000.0, 2500.0, 5000.0), n_req=400, seed=0
     return out
 
 
+def _timed(fn, reps=3):
+    """Median device time (ms) of fn() -> dgs_stats with timing, after one warm-up."""
+    fn()
+    return float(np.median([fn().ms_total for _ in range(reps)]))
+
+
+def comparators_bench(rctx, n_views=8):
+    """The large-scale workload (1M cells x 10 Gaussians on a ground plane,
+    SH 3) from 8 street-level cameras, forward only, rendered three ways in
+    the same library: Duplex-GS (cells sorted), per-Gaussian global-sort
+    alpha-blending, and sort-free weighted sums (plain WSR, tau = inf).  The
+    analogue of the paper's sort-length table: entries sorted by depth and
+    (tile, primitive) pairs sorted by tile, with device times."""
+    from paper_2508_03180_gb300 import _lib as L
+    from paper_2508_03180_gb300 import synth
+    scene = synth.scene_large()
+    sid = rctx.upload_scene(scene)
+    out = {"workload": "large-scale 1M cells x 10 Gaussians (10M), SH3, 8 street-level cameras, forward",
+           "resolutions": {}}
+    try:
+        for (W, H) in ((1920, 1080), (3840, 2160)):
+            cams = synth.street_cameras(n_views, W, H, seed0=0)
+            slots = rctx.set_cameras(cams)
+            img = torch_empty(n_views * 3 * W * H)
+            px = n_views * W * H
+
+            def duplex():
+                st = L.dgs_stats()
+                st.timing = 1
+                L.dgs_render(rctx.ctx, sid, slots, img.data_ptr(), L.DGS_DEVICE, False, 0, st)
+                return st
+
+            def comp(mode):
+                def f():
+                    cfg = L.dgs_compare_config()
+                    cfg.mode = mode
+                    st = L.dgs_stats()
+                    st.timing = 1
+                    L.dgs_render_compare(rctx.ctx, sid, slots, cfg, img.data_ptr(), 0, 0, st)
+                    return st
+                return f
+
+            res = {}
+            for name, fn, depth_entries in (("duplex", duplex, n_views * scene.N),
+                                            ("alpha_blend", comp(L.DGS_COMPARE_ALPHA), n_views * scene.G),
+                                            ("wsr", comp(L.DGS_COMPARE_WSR), 0)):
+                ms = _timed(fn)
+                st = fn()
+                res[name] = {"ms": ms, "mpix_s": px / (ms / 1e3) / 1e6, "depth_sort_entries": depth_entries,
+                             "tile_sort_pairs": int(st.sort_length), "kept_entries": int(st.visible_cells)}
+            for name in ("alpha_blend", "wsr"):
+                res[name]["time_vs_duplex"] = res[name]["ms"] / res["duplex"]["ms"]
+                res[name]["pairs_vs_duplex"] = res[name]["tile_sort_pairs"] / max(1, res["duplex"]["tile_sort_pairs"])
+            out["resolutions"][f"{W}x{H}"] = res
+    finally:
+        rctx.release_scene(sid)
+    return out
+
+
+def small_fwdbwd_bench(rctx, steps=10):
+    """The small scene (2,048 cells x 8 Gaussians, SH 3 from the RGB draws)
+    at 1920x1080, a batch of 4 views, L1 loss, forward + backward."""
+    import torch
+
+    from paper_2508_03180_gb300 import synth
+    scene = synth.scene_small(seed=0, sh_degree=3)
+    sid = rctx.upload_scene(scene)
+    try:
+        cams = synth.sphere_cameras(4, 3.0, 1920, 1080, seed0=0)
+        slots = rctx.set_cameras(cams)
+        n = 4 * 3 * 1080 * 1920
+        img, dl = torch.empty(n, device="cuda"), torch.empty(n, device="cuda")
+        loss = torch.empty(1, device="cuda")
+        target = torch.from_numpy(synth.target_image(4, 1080, 1920, seed=7)).cuda().reshape(-1)
+        G = scene.G
+        grads = dict(g_mean=torch.empty(G, 3, device="cuda"), g_log_scale=torch.empty(G, 3, device="cuda"),
+                     g_quat=torch.empty(G, 4, device="cuda"), g_logit=torch.empty(G, device="cuda"),
+                     g_sh=torch.empty(G, 16, 3, device="cuda"))
+
+        def step():
+            _, state, _ = rctx.render(sid, cams, want_state=True, out=img, slots=slots)
+            rctx.loss_l1(img, target, dl, loss)
+            rctx.backward(state, dl, grads)
+            rctx.release_state(state)
+
+        for _ in range(3):
+            step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            step()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        return {"workload": "small 2,048 cells x 8 Gaussians (16k), SH3, 4 views 1920x1080 fwd+bwd L1",
+                "ms_per_step": ms, "mpix_s": 4 * 1920 * 1080 / (ms / 1e3) / 1e6}
+    finally:
+        rctx.release_scene(sid)
+
+
+def torch_empty(n):
+    import torch
+    return torch.empty(n, device="cuda")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -273,6 +379,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--views", type=int, default=N_VIEWS, help="views per step (profiling of smaller cases)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -422,6 +529,12 @@ def main():
     # kernel launches per step: binning 11 + sort passes + projection + blend + backward 2 + loss 2
     line["gpu_launches"] = int(args.steps * launches_per_step(stats))
 
+    if rank == 0 and not args.no_compare:
+        try:
+            line["comparators"] = comparators_bench(rctx)
+            line["small_fwd_bwd"] = small_fwdbwd_bench(rctx)
+        except Exception as e:  # reported beside the headline, never instead of it
+            line["comparators"] = {"error": str(e)}
     if rank == 0 and not args.no_serve:
         try:
             line["serving"] = serving_bench(rctx)
