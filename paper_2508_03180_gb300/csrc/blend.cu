@@ -506,17 +506,15 @@ __global__ void __launch_bounds__(WT, 32) k_blend_bwd(const ViewDesc *__restrict
         const float4 *r = s_rec[buf];
         const float v = r[2].w;
         unsigned mask = __ballot_sync(0xffffffffu, lane < K && touches_block(r[kRecF4 * lane], bx0, by0));
+        const unsigned mask0 = mask;
         const int nhit = __popc(mask);
-        int kk[KR];
         float *G0 = &s_G[0][0][0], *G1 = &s_G[1][0][0];
         float A00 = 0.f, A01 = 0.f, A02 = 0.f, B0 = 0.f, P0 = 1.0f;
         float A10 = 0.f, A11 = 0.f, A12 = 0.f, B1 = 0.f, P1 = 1.0f;
-#pragma unroll
-        for (int i = 0; i < KR; ++i) {
-            if (i >= nhit) break;
+#pragma unroll 1
+        for (int i = 0; i < nhit; ++i) {
             const int k = __ffs(mask) - 1;
             mask &= mask - 1;
-            kk[i] = k;
             G0[i * WT + lane] = 0.f;
             G1[i * WT + lane] = 0.f;
             const float4 r0 = r[3 * k];
@@ -561,14 +559,15 @@ __global__ void __launch_bounds__(WT, 32) k_blend_bwd(const ViewDesc *__restrict
             for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
             if (lane == 0 && a != 0.f) atomicAdd(g_cell_v + cellid, a);
         }
-        // gradient terms per Gaussian reaching the sub-tile
-#pragma unroll
-        for (int i = 0; i < KR; ++i) {
-            if (i >= nhit) break;
+        // gradient terms per Gaussian reaching the sub-tile (not unrolled:
+        // the body is large and the instruction cache is the limit)
+        unsigned m2 = mask0;
+#pragma unroll 1
+        for (int i = 0; m2; ++i, m2 &= m2 - 1) {
             const float g0v = G0[i * WT + lane], g1v = G1[i * WT + lane];
             const bool hit0 = g0v > 0.f, hit1 = g1v > 0.f;
             if (!__any_sync(0xffffffffu, hit0 || hit1)) continue;
-            const int k = kk[i];
+            const int k = __ffs(m2) - 1;
             const float4 r0 = r[3 * k], r1 = r[3 * k + 1], r2 = r[3 * k + 2];
             float acc[16];
 #pragma unroll
