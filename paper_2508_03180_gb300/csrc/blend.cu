@@ -389,12 +389,17 @@ void launch_count_pairs(const ViewDesc *views, int n_views, int total_tiles, con
 
 // Sum v[0..15] over the warp.  On return lane L holds the total of value
 // 8 b1 + 4 b2 + 2 b3 + b4 (b_i = bit i of L); lanes with b0 = 1 duplicate it.
-__device__ __forceinline__ float transposed_warp_sum16(float v[16], int lane) {
+// Transposed warp reduction of eight per-lane values: three halving steps
+// (offsets 16, 8, 4) in which each lane keeps half of its slots and receives
+// its partner's other half, then two butterfly steps (offsets 2, 1).  Every
+// lane ends with the warp total of slot transposed_owner8(lane): 9 shuffles
+// instead of 8 x 5.
+__device__ __forceinline__ float transposed_warp_sum8(float v[8], int lane) {
 #pragma unroll
-    for (int step = 0; step < 4; ++step) {
+    for (int step = 0; step < 3; ++step) {
         const int bit = 16 >> step;
         const bool hi = lane & bit;
-        const int n = 8 >> step;  // pairs at this step
+        const int n = 4 >> step;  // pairs at this step
 #pragma unroll
         for (int i = 0; i < n; ++i) {
             const float keep = hi ? v[2 * i + 1] : v[2 * i];
@@ -402,30 +407,46 @@ __device__ __forceinline__ float transposed_warp_sum16(float v[16], int lane) {
             v[i] = keep + __shfl_xor_sync(0xffffffffu, send, bit);
         }
     }
-    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+    const float t = v[0] + __shfl_xor_sync(0xffffffffu, v[0], 2);
+    return t + __shfl_xor_sync(0xffffffffu, t, 1);
 }
 
-__device__ __forceinline__ int transposed_owner(int lane) {
-    return ((lane >> 1) & 1) * 8 + ((lane >> 2) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 4) & 1);
+__device__ __forceinline__ int transposed_owner8(int lane) {
+    return ((lane >> 2) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 4) & 1);
 }
 
-// Screen-space gradient terms of one (pixel, Gaussian) pair into acc[0..9]:
-// dmu_x dmu_y da db dc dsigma dr dg db, and the Gaussian's share of dL/dv.
-__device__ __forceinline__ void pair_grad(float acc[16], float Gv, float4 r0, float4 r1, float4 r2, float px, float py,
-                                          float Tn, float Sn, float e0, float e1, float e2, float eD, float alpha_max) {
+__device__ __forceinline__ float warp_sum(float a) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    return a;
+}
+
+// 1/x to ~1 ulp (MUFU); x = 1 - v alpha >= 1 - alpha_max here
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Screen-space gradient terms of one (pixel, Gaussian) pair: acc[0..7] =
+// dmu_x dmu_y da db dc dr dg db, dop = dsigma, and the pair's share of
+// dL/dv (summed per cell by the caller).
+__device__ __forceinline__ void pair_grad(float acc[8], float &dop, float &dv, float Gv, float4 r0, float4 r1,
+                                          float4 r2, float px, float py, float Tn, float Sn, float e0, float e1,
+                                          float e2, float eD, float alpha_max) {
     const float v = r2.w, op = r1.w;
     const float raw = op * Gv;
     const float al = fminf(raw, alpha_max);
     const float cA = v * Tn;
-    const float rom = __frcp_rn(1.0f - v * al);
+    const float rom = rcp_approx(1.0f - v * al);
     const float dal = cA * (e0 * r2.x + e1 * r2.y + e2 * r2.z + eD) - v * Sn * rom;
     const float ca_al = cA * al;
-    acc[6] += ca_al * e0;
-    acc[7] += ca_al * e1;
-    acc[8] += ca_al * e2;
-    acc[9] -= Sn * al * rom;
+    acc[5] += ca_al * e0;
+    acc[6] += ca_al * e1;
+    acc[7] += ca_al * e2;
+    dv -= Sn * al * rom;
     if (raw < alpha_max) {
-        acc[5] += dal * Gv;
+        dop += dal * Gv;
         const float dq = -0.5f * Gv * (dal * op);
         const float dx = px - r0.x, dy = py - r0.y;
         // q = |L^T d|^2 with the record's L scaled by kappa (kappa^2 = log2(e)/2):
@@ -439,6 +460,9 @@ __device__ __forceinline__ void pair_grad(float acc[16], float Gv, float4 r0, fl
         acc[4] += dq * dy * dy;
     }
 }
+
+// screen-space gradient slot (of kGradF) that reduction slot j feeds
+__device__ __forceinline__ int grad_slot(int j) { return j < 5 ? j : j + 1; }
 
 template <int KT>
 __global__ void __launch_bounds__(WT, 32) k_blend_bwd(const ViewDesc *__restrict__ views, int n_views,
@@ -553,12 +577,10 @@ __global__ void __launch_bounds__(WT, 32) k_blend_bwd(const ViewDesc *__restrict
         if (a0) { S[0] -= v * Tn0 * X0; T[0] *= P0; }
         if (a1) { S[1] -= v * Tn1 * X1; T[1] *= P1; }
         const uint32_t cellid = __ldg(cells + e);
-        if (want_v) {  // cell term of dL/dv: sum over pixels of T_n X_n
-            float a = (a0 ? Tn0 * X0 : 0.f) + (a1 ? Tn1 * X1 : 0.f);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-            if (lane == 0 && a != 0.f) atomicAdd(g_cell_v + cellid, a);
-        }
+        // cell term of dL/dv: sum over pixels of T_n X_n; the Gaussians' terms
+        // join it below, so one reduction per cell carries dL/dv
+        float dv = (a0 ? Tn0 * X0 : 0.f) + (a1 ? Tn1 * X1 : 0.f);
+        float *gbase = g2d + (V.rec_base + (long long)cellid * K) * kGradF;
         // gradient terms per Gaussian reaching the sub-tile (not unrolled:
         // the body is large and the instruction cache is the limit)
         unsigned m2 = mask0;
@@ -569,17 +591,25 @@ __global__ void __launch_bounds__(WT, 32) k_blend_bwd(const ViewDesc *__restrict
             if (!__any_sync(0xffffffffu, hit0 || hit1)) continue;
             const int k = __ffs(m2) - 1;
             const float4 r0 = r[3 * k], r1 = r[3 * k + 1], r2 = r[3 * k + 2];
-            float acc[16];
+            float acc[8];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) acc[j] = 0.f;
-            if (hit0) pair_grad(acc, g0v, r0, r1, r2, px, py[0], Tn0, S[0], e0[0], e1[0], e2[0], eD[0], bp.alpha_max);
-            if (hit1) pair_grad(acc, g1v, r0, r1, r2, px, py[1], Tn1, S[1], e0[1], e1[1], e2[1], eD[1], bp.alpha_max);
-            const float tot = transposed_warp_sum16(acc, lane);
-            const int idx = transposed_owner(lane);
-            if ((lane & 1) == 0 && tot != 0.f) {
-                if (idx < 9) atomicAdd(g2d + (V.rec_base + (long long)cellid * K + k) * kGradF + idx, tot);
-                else if (idx == 9 && want_v) atomicAdd(g_cell_v + cellid, tot);
-            }
+            for (int j = 0; j < 8; ++j) acc[j] = 0.f;
+            float dop = 0.f;
+            if (hit0)
+                pair_grad(acc, dop, dv, g0v, r0, r1, r2, px, py[0], Tn0, S[0], e0[0], e1[0], e2[0], eD[0],
+                          bp.alpha_max);
+            if (hit1)
+                pair_grad(acc, dop, dv, g1v, r0, r1, r2, px, py[1], Tn1, S[1], e0[1], e1[1], e2[1], eD[1],
+                          bp.alpha_max);
+            const float tot = transposed_warp_sum8(acc, lane);
+            const float dop_tot = warp_sum(dop);
+            float *gk = gbase + k * kGradF;
+            if ((lane & 3) == 0 && tot != 0.f) atomicAdd(gk + grad_slot(transposed_owner8(lane)), tot);
+            if (lane == 1 && dop_tot != 0.f) atomicAdd(gk + 5, dop_tot);
+        }
+        if (want_v) {
+            dv = warp_sum(dv);
+            if (lane == 0 && dv != 0.f) atomicAdd(g_cell_v + cellid, dv);
         }
         __syncwarp();
         if (e + 1 < end) stash_cell(s_rec[buf ^ 1], per, lane, pre);
