@@ -428,37 +428,50 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return y;
 }
 
-// Screen-space gradient terms of one (pixel, Gaussian) pair: acc[0..7] =
-// dmu_x dmu_y da db dc dr dg db, dop = dsigma, and the pair's share of
-// dL/dv (summed per cell by the caller).
+// Screen-space gradient terms of one (pixel, Gaussian) pair, with the
+// constant factors left to the caller (applied once per reduced total):
+//   acc[0..1] = sum L (s1, s2) dq'     (dmu = 2 ln 2 acc, see below)
+//   acc[2..4] = sum dq' (dx^2, dx dy, dy^2)  (da, db, dc = -1/2, -1, -1/2 x acc)
+//   acc[5..7] = sum v T alpha e       (drgb)
+//   dop       = sum dalpha G          (dsigma)
+//   dv       -= S alpha / (1 - v alpha)  (the pair's share of dL/dv, per cell)
+// with dq' = G dalpha sigma = -2 dL/dq.  cA = v T_n and vS = v S_n are the
+// pixel's per-cell factors.
 __device__ __forceinline__ void pair_grad(float acc[8], float &dop, float &dv, float Gv, float4 r0, float4 r1,
-                                          float4 r2, float px, float py, float Tn, float Sn, float e0, float e1,
-                                          float e2, float eD, float alpha_max) {
+                                          float4 r2, float px, float py, float cA, float Sn, float vS, float e0,
+                                          float e1, float e2, float eD, float alpha_max) {
     const float v = r2.w, op = r1.w;
     const float raw = op * Gv;
     const float al = fminf(raw, alpha_max);
-    const float cA = v * Tn;
     const float rom = rcp_approx(1.0f - v * al);
-    const float dal = cA * (e0 * r2.x + e1 * r2.y + e2 * r2.z + eD) - v * Sn * rom;
+    const float dal = cA * (e0 * r2.x + e1 * r2.y + e2 * r2.z + eD) - vS * rom;
     const float ca_al = cA * al;
     acc[5] += ca_al * e0;
     acc[6] += ca_al * e1;
     acc[7] += ca_al * e2;
     dv -= Sn * al * rom;
     if (raw < alpha_max) {
-        dop += dal * Gv;
-        const float dq = -0.5f * Gv * (dal * op);
+        const float dG = dal * Gv;
+        dop += dG;
+        const float dq = dG * op;
         const float dx = px - r0.x, dy = py - r0.y;
         // q = |L^T d|^2 with the record's L scaled by kappa (kappa^2 = log2(e)/2):
-        // dq/dmu = -2 Q d = -(2/kappa^2) L (s1, s2)
+        // dq/dmu = -2 Q d = -(2/kappa^2) L (s1, s2), 2/kappa^2 = 4 ln 2
         const float s1 = fmaf(r1.y, dy, r1.x * dx), s2 = r1.z * dy;
-        const float dqs = dq * (2.0f * 2.0f * LN2);  // 2 / kappa^2 = 4 ln 2
-        acc[0] -= dqs * (r1.x * s1);
-        acc[1] -= dqs * fmaf(r1.y, s1, r1.z * s2);
-        acc[2] += dq * dx * dx;
-        acc[3] += dq * 2.0f * dx * dy;
+        acc[0] += dq * (r1.x * s1);
+        acc[1] += dq * fmaf(r1.y, s1, r1.z * s2);
+        const float dqx = dq * dx;
+        acc[2] += dqx * dx;
+        acc[3] += dqx * dy;
         acc[4] += dq * dy * dy;
     }
+}
+
+// Constant factor of reduction slot j (see pair_grad): dL/dq = -dq'/2, so
+// dmu = -(4 ln 2)(-1/2) acc = 2 ln 2 acc, da = -acc/2, db = -acc (the 2 dx dy
+// term), dc = -acc/2; rgb unchanged.
+__device__ __forceinline__ float slot_scale(int j) {
+    return j < 2 ? 2.0f * LN2 : (j == 3 ? -1.0f : (j < 5 ? -0.5f : 1.0f));
 }
 
 // screen-space gradient slot (of kGradF) that reduction slot j feeds
@@ -580,6 +593,7 @@ __global__ void __launch_bounds__(WT, 32) k_blend_bwd(const ViewDesc *__restrict
         // cell term of dL/dv: sum over pixels of T_n X_n; the Gaussians' terms
         // join it below, so one reduction per cell carries dL/dv
         float dv = (a0 ? Tn0 * X0 : 0.f) + (a1 ? Tn1 * X1 : 0.f);
+        const float cA0 = v * Tn0, cA1 = v * Tn1, vS0 = v * S[0], vS1 = v * S[1];
         float *gbase = g2d + (V.rec_base + (long long)cellid * K) * kGradF;
         // gradient terms per Gaussian reaching the sub-tile (not unrolled:
         // the body is large and the instruction cache is the limit)
@@ -596,15 +610,16 @@ __global__ void __launch_bounds__(WT, 32) k_blend_bwd(const ViewDesc *__restrict
             for (int j = 0; j < 8; ++j) acc[j] = 0.f;
             float dop = 0.f;
             if (hit0)
-                pair_grad(acc, dop, dv, g0v, r0, r1, r2, px, py[0], Tn0, S[0], e0[0], e1[0], e2[0], eD[0],
+                pair_grad(acc, dop, dv, g0v, r0, r1, r2, px, py[0], cA0, S[0], vS0, e0[0], e1[0], e2[0], eD[0],
                           bp.alpha_max);
             if (hit1)
-                pair_grad(acc, dop, dv, g1v, r0, r1, r2, px, py[1], Tn1, S[1], e0[1], e1[1], e2[1], eD[1],
+                pair_grad(acc, dop, dv, g1v, r0, r1, r2, px, py[1], cA1, S[1], vS1, e0[1], e1[1], e2[1], eD[1],
                           bp.alpha_max);
             const float tot = transposed_warp_sum8(acc, lane);
             const float dop_tot = warp_sum(dop);
             float *gk = gbase + k * kGradF;
-            if ((lane & 3) == 0 && tot != 0.f) atomicAdd(gk + grad_slot(transposed_owner8(lane)), tot);
+            const int slot = transposed_owner8(lane);
+            if ((lane & 3) == 0 && tot != 0.f) atomicAdd(gk + grad_slot(slot), tot * slot_scale(slot));
             if (lane == 1 && dop_tot != 0.f) atomicAdd(gk + 5, dop_tot);
         }
         if (want_v) {
