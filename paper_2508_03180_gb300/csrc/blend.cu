@@ -119,34 +119,54 @@ __device__ __forceinline__ void stash_cell(float4 *dst, int per, int lane, const
     }
 }
 
-// One work unit (sub-tile `unit` of the chain) of the forward blend.
-template <int KT>
+// Can record piece r0 pass the AABB test at some pixel centre of the 16-wide,
+// `rows`-high block whose first pixel is (x0, y0)?  (As touches_block.)
+__device__ __forceinline__ bool touches_rows(float4 r0, float x0, float y0, float rows) {
+    const float lx = x0 + 0.5f, hx = x0 + (float)kTile - 0.5f;
+    const float ly = y0 + 0.5f, hy = y0 + rows - 0.5f;
+    return !(lx - r0.x > r0.z || r0.x - hx > r0.z || ly - r0.y > r0.w || r0.y - hy > r0.w);
+}
+
+// The forward's work unit: one warp per 16 x (2 PPL) sub-tile, lane l
+// blending the PPL vertically adjacent pixels (x, PPL h .. PPL h + PPL - 1),
+// x = l mod 16, h = l / 16.  FWD_PPL = 2 (16x4 sub-tiles, 68 registers):
+// 16x8 sub-tiles halve the (sub-tile, Gaussian) pairs on the benchmark scene
+// but need ~95 registers (21 warps/SM) and measured no faster.
+constexpr int FWD_PPL = 2;
+constexpr int FWD_SUB = kTile / (2 * FWD_PPL);  // sub-tiles per tile
+
+template <int KT, int PPL>
 __device__ __forceinline__ void blend_fwd_unit(int unit, const ViewDesc *__restrict__ views, int n_views,
                                                const uint2 *__restrict__ ranges, const uint32_t *__restrict__ cells,
                                                const float4 *__restrict__ rec, const BlendParams &bp,
                                                float *__restrict__ out_rgb, float *__restrict__ out_rgb2,
                                                float *__restrict__ out_D, int *__restrict__ out_nd,
                                                float4 (*s_rec)[MAXPER]) {
+    constexpr int ROWS = 2 * PPL, NSUB = kTile / ROWS;
     const int lane = threadIdx.x;
-    const int tile = unit / WSUB, sub = unit % WSUB;
+    const int tile = unit / NSUB, sub = unit % NSUB;
     const int vi = find_view(views, n_views, tile);
     const ViewDesc &V = views[vi];
     const int local = tile - V.tile_base;
     const int tx = local % V.Tx, ty = local / V.Tx;
-    const float bx0 = (float)(tx * kTile), by0 = (float)(ty * kTile + WSUB * sub);
+    const float bx0 = (float)(tx * kTile), by0 = (float)(ty * kTile + ROWS * sub);
     const int xi = tx * kTile + (lane & (kTile - 1));
-    const int yi0 = ty * kTile + WSUB * sub + 2 * (lane >> 4), yi1 = yi0 + 1;
-    const bool in0 = xi < V.W && yi0 < V.H, in1 = xi < V.W && yi1 < V.H;
-    const float px = (float)xi + 0.5f, py0 = (float)yi0 + 0.5f, py1 = (float)yi1 + 0.5f;
+    const int yb = ty * kTile + ROWS * sub + PPL * (lane >> 4);
+    const float px = (float)xi + 0.5f;
     const int K = KT > 0 ? KT : V.K;
     const int per = kRecF4 * K;
     const float4 *vrec = rec + V.rec_base * kRecF4;
     const uint2 rg = ranges[tile];
 
-    float T0 = 1.0f, N00 = 0.f, N01 = 0.f, N02 = 0.f, D0 = 0.f;
-    float T1 = 1.0f, N10 = 0.f, N11 = 0.f, N12 = 0.f, D1 = 0.f;
-    int n0 = 0, n1 = 0;
-    bool done0 = !in0, done1 = !in1;
+    float T[PPL], N0[PPL], N1[PPL], N2[PPL], D[PPL], py[PPL];
+    int n[PPL];
+    bool done[PPL];
+#pragma unroll
+    for (int q = 0; q < PPL; ++q) {
+        T[q] = 1.0f; N0[q] = N1[q] = N2[q] = D[q] = 0.f; n[q] = 0;
+        py[q] = (float)(yb + q) + 0.5f;
+        done[q] = !(xi < V.W && yb + q < V.H);
+    }
     float4 pre[3];
     if (rg.x < rg.y) {
         stage_cell(s_rec[0], vrec, cells, rg.x, per, lane, pre);
@@ -156,55 +176,57 @@ __device__ __forceinline__ void blend_fwd_unit(int unit, const ViewDesc *__restr
     int buf = 0;
     for (uint32_t e = rg.x; e < rg.y; ++e) {
         // before cell n a pixel stops if T_n < eps (Sec. V-B)
-        done0 = done0 || T0 < bp.eps;
-        done1 = done1 || T1 < bp.eps;
-        if (__all_sync(0xffffffffu, done0 && done1)) break;
+        bool all = true;
+#pragma unroll
+        for (int q = 0; q < PPL; ++q) {
+            done[q] = done[q] || T[q] < bp.eps;
+            all = all && done[q];
+        }
+        if (__all_sync(0xffffffffu, all)) break;
         if (e + 1 < rg.y) stage_cell(s_rec[buf ^ 1], vrec, cells, e + 1, per, lane, pre);
         const float4 *r = s_rec[buf];
         const float v = r[2].w;
-        unsigned mask = __ballot_sync(0xffffffffu, lane < K && touches_block(r[kRecF4 * lane], bx0, by0));
-        float A00 = 0.f, A01 = 0.f, A02 = 0.f, B0 = 0.f, P0 = 1.0f;
-        float A10 = 0.f, A11 = 0.f, A12 = 0.f, B1 = 0.f, P1 = 1.0f;
+        unsigned mask = __ballot_sync(0xffffffffu, lane < K && touches_rows(r[kRecF4 * lane], bx0, by0, (float)ROWS));
+        float A0[PPL], A1[PPL], A2[PPL], B[PPL], P[PPL];
+#pragma unroll
+        for (int q = 0; q < PPL; ++q) { A0[q] = A1[q] = A2[q] = B[q] = 0.f; P[q] = 1.0f; }
         for (; mask; mask &= mask - 1) {
             const int k = __ffs(mask) - 1;
             const float4 r0 = r[3 * k];
             const float dx = px - r0.x;
             if (!(fabsf(dx) <= r0.z)) continue;
-            const float dy0 = py0 - r0.y, dy1 = py1 - r0.y;
-            const bool h0 = !done0 && fabsf(dy0) <= r0.w;
-            const bool h1 = !done1 && fabsf(dy1) <= r0.w;
-            if (!(h0 || h1)) continue;
+            bool h[PPL], any = false;
+            float dy[PPL];
+#pragma unroll
+            for (int q = 0; q < PPL; ++q) {
+                dy[q] = py[q] - r0.y;
+                h[q] = !done[q] && fabsf(dy[q]) <= r0.w;
+                any = any || h[q];
+            }
+            if (!any) continue;
             const float4 r1 = r[3 * k + 1];
             const float4 r2 = r[3 * k + 2];
             const float pdx = r1.x * dx;
-            if (h0) {
-                const float s1 = fmaf(r1.y, dy0, pdx), s2 = r1.z * dy0;
-                const float al = fminf(r1.w * ex2_approx(-fmaf(s1, s1, s2 * s2)), bp.alpha_max);
-                A00 += al * r2.x; A01 += al * r2.y; A02 += al * r2.z;
-                B0 += al;
-                P0 -= P0 * (v * al);
-            }
-            if (h1) {
-                const float s1 = fmaf(r1.y, dy1, pdx), s2 = r1.z * dy1;
-                const float al = fminf(r1.w * ex2_approx(-fmaf(s1, s1, s2 * s2)), bp.alpha_max);
-                A10 += al * r2.x; A11 += al * r2.y; A12 += al * r2.z;
-                B1 += al;
-                P1 -= P1 * (v * al);
+#pragma unroll
+            for (int q = 0; q < PPL; ++q) {
+                if (h[q]) {
+                    const float s1 = fmaf(r1.y, dy[q], pdx), s2 = r1.z * dy[q];
+                    const float al = fminf(r1.w * ex2_approx(-fmaf(s1, s1, s2 * s2)), bp.alpha_max);
+                    A0[q] += al * r2.x; A1[q] += al * r2.y; A2[q] += al * r2.z;
+                    B[q] += al;
+                    P[q] -= P[q] * (v * al);
+                }
             }
         }
-        if (!done0) {
-            const float w = v * T0;
-            N00 += w * A00; N01 += w * A01; N02 += w * A02;
-            D0 += w * B0;
-            T0 *= P0;
-            ++n0;
-        }
-        if (!done1) {
-            const float w = v * T1;
-            N10 += w * A10; N11 += w * A11; N12 += w * A12;
-            D1 += w * B1;
-            T1 *= P1;
-            ++n1;
+#pragma unroll
+        for (int q = 0; q < PPL; ++q) {
+            if (!done[q]) {
+                const float w = v * T[q];
+                N0[q] += w * A0[q]; N1[q] += w * A1[q]; N2[q] += w * A2[q];
+                D[q] += w * B[q];
+                T[q] *= P[q];
+                ++n[q];
+            }
         }
         __syncwarp();
         if (e + 1 < rg.y) stash_cell(s_rec[buf ^ 1], per, lane, pre);
@@ -215,14 +237,13 @@ __device__ __forceinline__ void blend_fwd_unit(int unit, const ViewDesc *__restr
     float *img = V.out ? V.out : out_rgb + 3 * V.pix_base;
     float *im2 = out_rgb2 ? out_rgb2 + 3 * V.pix_base : nullptr;
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        if (!(q == 0 ? in0 : in1)) continue;
-        const float D = q == 0 ? D0 : D1;
-        const long long pin = (long long)(q == 0 ? yi0 : yi1) * V.W + xi;
-        const bool hit = D > bp.d_min;
-        const float c0 = hit ? (q == 0 ? N00 : N10) / D : bp.bg0;
-        const float c1 = hit ? (q == 0 ? N01 : N11) / D : bp.bg1;
-        const float c2 = hit ? (q == 0 ? N02 : N12) / D : bp.bg2;
+    for (int q = 0; q < PPL; ++q) {
+        if (!(xi < V.W && yb + q < V.H)) continue;
+        const long long pin = (long long)(yb + q) * V.W + xi;
+        const bool hit = D[q] > bp.d_min;
+        const float c0 = hit ? N0[q] / D[q] : bp.bg0;
+        const float c1 = hit ? N1[q] / D[q] : bp.bg1;
+        const float c2 = hit ? N2[q] / D[q] : bp.bg2;
         img[pin] = c0;
         img[HW + pin] = c1;
         img[2 * HW + pin] = c2;
@@ -231,8 +252,8 @@ __device__ __forceinline__ void blend_fwd_unit(int unit, const ViewDesc *__restr
             im2[HW + pin] = c1;
             im2[2 * HW + pin] = c2;
         }
-        out_D[V.pix_base + pin] = D;
-        out_nd[V.pix_base + pin] = q == 0 ? n0 : n1;
+        out_D[V.pix_base + pin] = D[q];
+        out_nd[V.pix_base + pin] = n[q];
     }
 }
 
@@ -243,12 +264,13 @@ __global__ void __launch_bounds__(WT) k_blend_fwd(const ViewDesc *__restrict__ v
                                                   float *__restrict__ out_rgb, float *__restrict__ out_rgb2,
                                                   float *__restrict__ out_D, int *__restrict__ out_nd) {
     __shared__ float4 s_rec[2][MAXPER];
-    blend_fwd_unit<KT>(blockIdx.x, views, n_views, ranges, cells, rec, bp, out_rgb, out_rgb2, out_D, out_nd, s_rec);
+    blend_fwd_unit<KT, FWD_PPL>(blockIdx.x, views, n_views, ranges, cells, rec, bp, out_rgb, out_rgb2, out_D, out_nd,
+                                s_rec);
 }
 
 // Persistent form for chains whose sizes live on the device: a fixed grid of
 // exactly the resident warps pulls sub-tiles from an atomic counter (*work
-// starts at 0) until the chain's total_tiles * WSUB units are taken, so the
+// starts at 0) until the chain's total_tiles * FWD_SUB units are taken, so the
 // dense and the empty regions of the images balance dynamically.  One
 // atomic per sub-tile: their rate is bounded by the blend work between them.
 template <int KT>
@@ -261,13 +283,14 @@ __global__ void __launch_bounds__(WT) k_blend_fwd_pull(const ViewDesc *__restric
                                                        uint32_t *__restrict__ work) {
     __shared__ float4 s_rec[2][MAXPER];
     const int n_views = dsz->n_views;
-    const uint32_t units = (uint32_t)dsz->total_tiles * WSUB;
+    const uint32_t units = (uint32_t)dsz->total_tiles * FWD_SUB;
     for (;;) {
         uint32_t u = 0;
         if (threadIdx.x == 0) u = atomicAdd(work, 1u);
         u = __shfl_sync(0xffffffffu, u, 0);
         if (u >= units) break;
-        blend_fwd_unit<KT>((int)u, views, n_views, ranges, cells, rec, bp, out_rgb, nullptr, out_D, out_nd, s_rec);
+        blend_fwd_unit<KT, FWD_PPL>((int)u, views, n_views, ranges, cells, rec, bp, out_rgb, nullptr, out_D, out_nd,
+                                    s_rec);
         __syncwarp();
     }
 }
@@ -283,7 +306,7 @@ static unsigned pull_grid(int total_tiles) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_blend_fwd_pull<KT>, WT, 0);
         per_grid = std::max(1, sms * std::max(1, per_sm));
     }
-    return (unsigned)std::min<long long>((long long)total_tiles * WSUB, per_grid);
+    return (unsigned)std::min<long long>((long long)total_tiles * FWD_SUB, per_grid);
 }
 
 void launch_blend_fwd(const ViewDesc *views, int n_views, int total_tiles, const uint2 *ranges,
@@ -304,7 +327,7 @@ void launch_blend_fwd(const ViewDesc *views, int n_views, int total_tiles, const
 #undef DGS_PULL
         return;
     }
-    const unsigned grid = (unsigned)total_tiles * WSUB;
+    const unsigned grid = (unsigned)total_tiles * FWD_SUB;
 #define DGS_FWD(KV)                                                                                          \
     k_blend_fwd<KV><<<grid, WT, 0, st>>>(views, n_views, ranges, tile_cells, rec, bp, out_rgb, out_rgb2, out_D, \
                                          out_nd)
