@@ -358,6 +358,65 @@ void launch_project_fwd_table(const ViewDesc *views, const SceneDev *scenes, lon
     k_project_fwd_table<<<grid_for(G_cap, 128), 128, 0, st>>>(views, scenes, count, bp, rec, dsz);
 }
 
+// a*b - c*d to about one rounding (Kahan's compensated form)
+__device__ __forceinline__ float diff_of_products(float a, float b, float c, float d) {
+    const float cd = c * d;
+    const float err = fmaf(-c, d, cd);
+    return fmaf(a, b, -cd) + err;
+}
+
+// dL/dU (2x3, rows u, w) of a loss depending on Q = (U U^T + d I)^-1 through
+// G_Q = dL/dQ = [[ga, gb/2], [gb/2, gc]] (see the comment at the call).
+__device__ __forceinline__ void adjoint_U(const float u[3], const float w[3], float d, float ga, float gb, float gc,
+                                          float gU[6]) {
+    const float x0 = diff_of_products(u[1], w[2], u[2], w[1]);
+    const float x1 = diff_of_products(u[2], w[0], u[0], w[2]);
+    const float x2 = diff_of_products(u[0], w[1], u[1], w[0]);
+    const float uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const float ww = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+    const float uw = u[0] * w[0] + u[1] * w[1] + u[2] * w[2];
+    const float xx = x0 * x0 + x1 * x1 + x2 * x2;
+    const float hd = 0.5f * (uu - ww);
+    const float s1sq = 0.5f * (uu + ww) + sqrtf(hd * hd + uw * uw);
+    if (!(s1sq > 0.f)) {  // U = 0: dL/dU = -2 Q G_Q Q U = 0
+#pragma unroll
+        for (int i = 0; i < 6; ++i) gU[i] = 0.f;
+        return;
+    }
+    const float s2sq = xx / s1sq;
+    // major eigenvector of [[uu, uw], [uw, ww]]: (s1^2 - ww, uw) or (uw, s1^2 - uu),
+    // whichever does not cancel; any unit vector when the eigenvalues coincide
+    float p1x, p1y;
+    if (uu >= ww) { p1x = s1sq - ww; p1y = uw; } else { p1x = uw; p1y = s1sq - uu; }
+    const float pn = p1x * p1x + p1y * p1y;
+    if (pn > 0.f) {
+        const float ip = rsqrtf(pn);
+        p1x *= ip; p1y *= ip;
+    } else {
+        p1x = 1.f; p1y = 0.f;
+    }
+    const float p2x = -p1y, p2y = p1x;
+    float r1[3], r2[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) r1[i] = p1x * u[i] + p1y * w[i];
+    const float is1 = 1.0f / s1sq;
+    r2[0] = (x1 * r1[2] - x2 * r1[1]) * is1;
+    r2[1] = (x2 * r1[0] - x0 * r1[2]) * is1;
+    r2[2] = (x0 * r1[1] - x1 * r1[0]) * is1;
+    const float g00 = fmaf(ga * p1x, p1x, fmaf(gb * p1x, p1y, gc * p1y * p1y));
+    const float g11 = fmaf(ga * p2x, p2x, fmaf(gb * p2x, p2y, gc * p2y * p2y));
+    const float g01 = fmaf(ga * p1x, p2x, fmaf(0.5f * gb, fmaf(p1x, p2y, p1y * p2x), gc * p1y * p2y));
+    const float il1 = 1.0f / (s1sq + d), il2 = 1.0f / (s2sq + d);
+    const float n00 = g00 * il1 * il1, n01 = g01 * il1 * il2, n11 = g11 * il2 * il2;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float y0 = fmaf(n00, r1[i], n01 * r2[i]);
+        const float y1 = fmaf(n01, r1[i], n11 * r2[i]);
+        gU[i] = -2.0f * fmaf(p1x, y0, p2x * y1);
+        gU[3 + i] = -2.0f * fmaf(p1y, y0, p2y * y1);
+    }
+}
+
 // ---------------------------------------------------------------- adjoint
 // Input per (view, Gaussian): dL/d(mu2 x, y), dL/d(conic a, b, c) with
 // q = a dx^2 + 2 b dx dy + c dy^2, dL/d(opacity), dL/d(rgb).  Chain rule
@@ -432,33 +491,17 @@ __global__ void __launch_bounds__(128) k_project_bwd(const ViewDesc *__restrict_
                     gm[1] += (gd[1] - dd * d1) * il;
                     gm[2] += (gd[2] - dd * d2) * il;
                 }
-                // conic -> Sigma' (H = -Q G_Q Q, G_Q = [[ga, gb/2], [gb/2, gc]]), then
-                // dL/dU = 2 H U.  For needle-like Gaussians the rows of U are nearly
-                // parallel and H U cancels heavily, so this block runs in FP64.
+                // conic -> Sigma' -> U:  dL/dU = 2 H U with H = -Q G_Q Q,
+                // G_Q = [[ga, gb/2], [gb/2, gc]], Q = Sigma'^-1, Sigma' = U U^T + d I.
+                // Needle-like Gaussians make U nearly rank one, so Q is nearly
+                // singular and Q G_Q Q U cancels heavily in the pixel frame.  In
+                // the eigenframe P of U U^T (eigenvalues s1^2 >= s2^2) it does
+                // not: with R = P^T U (rows r1 = p1^T U and r2 = x × r1 / s1^2,
+                // x = u × w, an exact identity free of cancellation) and
+                // lambda_i = s_i^2 + d,  dL/dU = -2 P N R,  N_ij = (P^T G_Q P)_ij / (lambda_i lambda_j).
                 const ScreenCov sc2 = screen_cov(c, bp.dilation);
                 float gU[6];
-                {
-                    const double u0 = sc2.u[0], u1 = sc2.u[1], u2 = sc2.u[2];
-                    const double w0 = sc2.w[0], w1 = sc2.w[1], w2 = sc2.w[2];
-                    const double uu = u0 * u0 + u1 * u1 + u2 * u2, ww = w0 * w0 + w1 * w1 + w2 * w2;
-                    const double uw = u0 * w0 + u1 * w1 + u2 * w2;
-                    const double x0 = u1 * w2 - u2 * w1, x1 = u2 * w0 - u0 * w2, x2 = u0 * w1 - u1 * w0;
-                    const double dd = bp.dilation;
-                    const double det = (x0 * x0 + x1 * x1 + x2 * x2) + dd * (uu + ww) + dd * dd;
-                    const double inv = 1.0 / det;
-                    const double qa = (ww + dd) * inv, qb = -uw * inv, qc = (uu + dd) * inv;
-                    const double ga = gca, gb = gcb, gc = gcc;
-                    const double P00 = ga * qa + 0.5 * gb * qb, P01 = ga * qb + 0.5 * gb * qc;
-                    const double P10 = 0.5 * gb * qa + gc * qb, P11 = 0.5 * gb * qb + gc * qc;
-                    const double H00 = -(qa * P00 + qb * P10), H01 = -(qa * P01 + qb * P11);
-                    const double H11 = -(qb * P01 + qc * P11);
-                    gU[0] = (float)(2.0 * (H00 * u0 + H01 * w0));
-                    gU[1] = (float)(2.0 * (H00 * u1 + H01 * w1));
-                    gU[2] = (float)(2.0 * (H00 * u2 + H01 * w2));
-                    gU[3] = (float)(2.0 * (H01 * u0 + H11 * w0));
-                    gU[4] = (float)(2.0 * (H01 * u1 + H11 * w1));
-                    gU[5] = (float)(2.0 * (H01 * u2 + H11 * w2));
-                }
+                adjoint_U(sc2.u, sc2.w, bp.dilation, gca, gcb, gcc, gU);
                 // Sigma' = U U^T + d I, U = T M:  dL/dT = dL/dU M^T,  dL/dM = T^T dL/dU
                 float gT[6];
 #pragma unroll
