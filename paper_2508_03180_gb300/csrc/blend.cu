@@ -500,37 +500,51 @@ __device__ __forceinline__ float slot_scale(int j) {
 // screen-space gradient slot (of kGradF) that reduction slot j feeds
 __device__ __forceinline__ int grad_slot(int j) { return j < 5 ? j : j + 1; }
 
-template <int KT>
-__global__ void __launch_bounds__(WT, 32) k_blend_bwd(const ViewDesc *__restrict__ views, int n_views,
+// The adjoint's work unit: one warp per 16 x (2 PPL) sub-tile, lane l
+// handling the PPL pixels (x, PPL h + q), x = l mod 16, h = l / 16, as in the
+// forward.  Per cell: pass 1 replays the forward (keeping G' of the Gaussians
+// that reach the sub-tile in warp-private shared memory) and updates T and
+// S; pass 2 forms each such Gaussian's screen-space gradient over the
+// sub-tile's pixels and adds the warp total with global atomics.
+constexpr int BWD_PPL = 4;
+constexpr int BWD_SUB = kTile / (2 * BWD_PPL);  // sub-tiles per tile
+constexpr int BWD_MINB = 24;  // resident one-warp CTAs per SM the register budget is set for
+
+template <int KT, int PPL>
+__global__ void __launch_bounds__(WT, BWD_MINB) k_blend_bwd(const ViewDesc *__restrict__ views, int n_views,
                                                   const uint2 *__restrict__ ranges, const uint32_t *__restrict__ cells,
                                                   const float4 *__restrict__ rec, BlendParams bp,
                                                   const float *__restrict__ rgb, const float *__restrict__ Dpix,
                                                   const int *__restrict__ ndpix, const float *__restrict__ dL_drgb,
                                                   float *__restrict__ g2d, float *__restrict__ g_cell_v) {
+    constexpr int ROWS = 2 * PPL, NSUB = kTile / ROWS;
     __shared__ float4 s_rec[2][MAXPER];
     constexpr int KRS = KT > 0 ? KT : kMaxK;
-    __shared__ float s_G[2][KRS][WT];
+    __shared__ float s_G[PPL][KRS][WT];
     const int lane = threadIdx.x;
-    const int tile = blockIdx.x / WSUB, sub = blockIdx.x % WSUB;
+    const int tile = blockIdx.x / NSUB, sub = blockIdx.x % NSUB;
     const int vi = find_view(views, n_views, tile);
     const ViewDesc &V = views[vi];
     const int local = tile - V.tile_base;
     const int tx = local % V.Tx, ty = local / V.Tx;
-    const float bx0 = (float)(tx * kTile), by0 = (float)(ty * kTile + WSUB * sub);
+    const float bx0 = (float)(tx * kTile), by0 = (float)(ty * kTile + ROWS * sub);
     const int xi = tx * kTile + (lane & (kTile - 1));
-    const int yi[2] = {ty * kTile + WSUB * sub + 2 * (lane >> 4), ty * kTile + WSUB * sub + 2 * (lane >> 4) + 1};
+    const int yb = ty * kTile + ROWS * sub + PPL * (lane >> 4);
     const float px = (float)xi + 0.5f;
-    const float py[2] = {(float)yi[0] + 0.5f, (float)yi[1] + 0.5f};
     const long long HW = (long long)V.W * V.H;
     const int K = KT > 0 ? KT : V.K;
     const int per = kRecF4 * K;
 
-    int nd[2] = {0, 0};
-    float e0[2] = {0.f, 0.f}, e1[2] = {0.f, 0.f}, e2[2] = {0.f, 0.f}, eD[2] = {0.f, 0.f};
+    int nd[PPL];
+    float e0[PPL], e1[PPL], e2[PPL], eD[PPL], py[PPL];
+    int ndm = 0;
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        if (xi < V.W && yi[q] < V.H) {
-            const long long pin = (long long)yi[q] * V.W + xi;
+    for (int q = 0; q < PPL; ++q) {
+        nd[q] = 0;
+        e0[q] = e1[q] = e2[q] = eD[q] = 0.f;
+        py[q] = (float)(yb + q) + 0.5f;
+        if (xi < V.W && yb + q < V.H) {
+            const long long pin = (long long)(yb + q) * V.W + xi;
             const float Dv = Dpix[V.pix_base + pin];
             if (Dv > bp.d_min) {
                 nd[q] = ndpix[V.pix_base + pin];
@@ -543,15 +557,17 @@ __global__ void __launch_bounds__(WT, 32) k_blend_bwd(const ViewDesc *__restrict
                 eD[q] = -(g0 * c0 + g1 * c1 + g2 * c2) * iD;
             }
         }
+        ndm = max(ndm, nd[q]);
     }
-    const int ndmax = __reduce_max_sync(0xffffffffu, max(nd[0], nd[1]));
+    const int ndmax = __reduce_max_sync(0xffffffffu, ndm);
     const uint2 rg = ranges[tile];
     const uint32_t end = rg.x + min((uint32_t)ndmax, rg.y - rg.x);
     const float4 *vrec = rec + V.rec_base * kRecF4;
     const bool want_v = g_cell_v != nullptr;
-    constexpr int KR = KT > 0 ? KT : kMaxK;
 
-    float T[2] = {1.0f, 1.0f}, S[2] = {0.f, 0.f};
+    float T[PPL], S[PPL];
+#pragma unroll
+    for (int q = 0; q < PPL; ++q) { T[q] = 1.0f; S[q] = 0.f; }
     float4 pre[3];
     if (rg.x < end) {
         stage_cell(s_rec[0], vrec, cells, rg.x, per, lane, pre);
@@ -562,82 +578,94 @@ __global__ void __launch_bounds__(WT, 32) k_blend_bwd(const ViewDesc *__restrict
     for (uint32_t e = rg.x; e < end; ++e) {
         if (e + 1 < end) stage_cell(s_rec[buf ^ 1], vrec, cells, e + 1, per, lane, pre);
         const int n = (int)(e - rg.x);
-        const bool a0 = n < nd[0], a1 = n < nd[1];
+        bool act[PPL];
+#pragma unroll
+        for (int q = 0; q < PPL; ++q) act[q] = n < nd[q];
         const float4 *r = s_rec[buf];
         const float v = r[2].w;
-        unsigned mask = __ballot_sync(0xffffffffu, lane < K && touches_block(r[kRecF4 * lane], bx0, by0));
+        unsigned mask = __ballot_sync(0xffffffffu, lane < K && touches_rows(r[kRecF4 * lane], bx0, by0, (float)ROWS));
         const unsigned mask0 = mask;
         const int nhit = __popc(mask);
-        float *G0 = &s_G[0][0][0], *G1 = &s_G[1][0][0];
-        float A00 = 0.f, A01 = 0.f, A02 = 0.f, B0 = 0.f, P0 = 1.0f;
-        float A10 = 0.f, A11 = 0.f, A12 = 0.f, B1 = 0.f, P1 = 1.0f;
+        // pass 1: replay the cell, keep G'; per pixel P_n and
+        // X_n = dN.A_n + dD B_n = sum_k alpha_k (dN.c_k + dD)
+        float X[PPL], P[PPL];
+        {
+#pragma unroll
+            for (int q = 0; q < PPL; ++q) { X[q] = 0.f; P[q] = 1.0f; }
 #pragma unroll 1
-        for (int i = 0; i < nhit; ++i) {
-            const int k = __ffs(mask) - 1;
-            mask &= mask - 1;
-            G0[i * WT + lane] = 0.f;
-            G1[i * WT + lane] = 0.f;
-            const float4 r0 = r[3 * k];
-            const float dx = px - r0.x;
-            if (!(fabsf(dx) <= r0.z)) continue;
-            const float dy0 = py[0] - r0.y, dy1 = py[1] - r0.y;
-            const bool h0 = a0 && fabsf(dy0) <= r0.w;
-            const bool h1 = a1 && fabsf(dy1) <= r0.w;
-            if (!(h0 || h1)) continue;
-            const float4 r1 = r[3 * k + 1];
-            const float4 r2 = r[3 * k + 2];
-            const float pdx = r1.x * dx;
-            if (h0) {
-                const float s1 = fmaf(r1.y, dy0, pdx), s2 = r1.z * dy0;
-                const float Gv = ex2_approx(-fmaf(s1, s1, s2 * s2));
-                G0[i * WT + lane] = Gv;
-                const float al = fminf(r1.w * Gv, bp.alpha_max);
-                A00 += al * r2.x; A01 += al * r2.y; A02 += al * r2.z;
-                B0 += al;
-                P0 -= P0 * (v * al);
-            }
-            if (h1) {
-                const float s1 = fmaf(r1.y, dy1, pdx), s2 = r1.z * dy1;
-                const float Gv = ex2_approx(-fmaf(s1, s1, s2 * s2));
-                G1[i * WT + lane] = Gv;
-                const float al = fminf(r1.w * Gv, bp.alpha_max);
-                A10 += al * r2.x; A11 += al * r2.y; A12 += al * r2.z;
-                B1 += al;
-                P1 -= P1 * (v * al);
+            for (int i = 0; i < nhit; ++i) {
+                const int k = __ffs(mask) - 1;
+                mask &= mask - 1;
+#pragma unroll
+                for (int q = 0; q < PPL; ++q) s_G[q][i][lane] = 0.f;
+                const float4 r0 = r[3 * k];
+                const float dx = px - r0.x;
+                if (!(fabsf(dx) <= r0.z)) continue;
+                bool h[PPL], any = false;
+                float dy[PPL];
+#pragma unroll
+                for (int q = 0; q < PPL; ++q) {
+                    dy[q] = py[q] - r0.y;
+                    h[q] = act[q] && fabsf(dy[q]) <= r0.w;
+                    any = any || h[q];
+                }
+                if (!any) continue;
+                const float4 r1 = r[3 * k + 1];
+                const float4 r2 = r[3 * k + 2];
+                const float pdx = r1.x * dx;
+#pragma unroll
+                for (int q = 0; q < PPL; ++q) {
+                    if (h[q]) {
+                        const float s1 = fmaf(r1.y, dy[q], pdx), s2 = r1.z * dy[q];
+                        const float Gv = ex2_approx(-fmaf(s1, s1, s2 * s2));
+                        s_G[q][i][lane] = Gv;
+                        const float al = fminf(r1.w * Gv, bp.alpha_max);
+                        X[q] += al * fmaf(e0[q], r2.x, fmaf(e1[q], r2.y, fmaf(e2[q], r2.z, eD[q])));
+                        P[q] -= P[q] * (v * al);
+                    }
+                }
             }
         }
-        // per-pixel transmittance bookkeeping (S_n includes x_n)
-        const float X0 = e0[0] * A00 + e1[0] * A01 + e2[0] * A02 + eD[0] * B0;
-        const float X1 = e0[1] * A10 + e1[1] * A11 + e2[1] * A12 + eD[1] * B1;
-        const float Tn0 = T[0], Tn1 = T[1];
-        if (a0) { S[0] -= v * Tn0 * X0; T[0] *= P0; }
-        if (a1) { S[1] -= v * Tn1 * X1; T[1] *= P1; }
+        // per-pixel transmittance bookkeeping (S_n includes x_n); the cell
+        // term of dL/dv, sum over pixels of T_n X_n, joins the Gaussians'
+        // terms below so one reduction per cell carries dL/dv
+        float Tn[PPL];
+        float dv = 0.f;
+#pragma unroll
+        for (int q = 0; q < PPL; ++q) {
+            Tn[q] = T[q];
+            if (act[q]) {
+                S[q] -= v * Tn[q] * X[q];
+                T[q] *= P[q];
+                dv += Tn[q] * X[q];
+            }
+        }
         const uint32_t cellid = __ldg(cells + e);
-        // cell term of dL/dv: sum over pixels of T_n X_n; the Gaussians' terms
-        // join it below, so one reduction per cell carries dL/dv
-        float dv = (a0 ? Tn0 * X0 : 0.f) + (a1 ? Tn1 * X1 : 0.f);
-        const float cA0 = v * Tn0, cA1 = v * Tn1, vS0 = v * S[0], vS1 = v * S[1];
         float *gbase = g2d + (V.rec_base + (long long)cellid * K) * kGradF;
-        // gradient terms per Gaussian reaching the sub-tile (not unrolled:
-        // the body is large and the instruction cache is the limit)
+        // pass 2: gradient terms per Gaussian reaching the sub-tile (not
+        // unrolled: the body is large and the instruction cache is the limit)
         unsigned m2 = mask0;
 #pragma unroll 1
         for (int i = 0; m2; ++i, m2 &= m2 - 1) {
-            const float g0v = G0[i * WT + lane], g1v = G1[i * WT + lane];
-            const bool hit0 = g0v > 0.f, hit1 = g1v > 0.f;
-            if (!__any_sync(0xffffffffu, hit0 || hit1)) continue;
+            float gv[PPL];
+            bool any = false;
+#pragma unroll
+            for (int q = 0; q < PPL; ++q) {
+                gv[q] = s_G[q][i][lane];
+                any = any || gv[q] > 0.f;
+            }
+            if (!__any_sync(0xffffffffu, any)) continue;
             const int k = __ffs(m2) - 1;
             const float4 r0 = r[3 * k], r1 = r[3 * k + 1], r2 = r[3 * k + 2];
             float acc[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) acc[j] = 0.f;
             float dop = 0.f;
-            if (hit0)
-                pair_grad(acc, dop, dv, g0v, r0, r1, r2, px, py[0], cA0, S[0], vS0, e0[0], e1[0], e2[0], eD[0],
-                          bp.alpha_max);
-            if (hit1)
-                pair_grad(acc, dop, dv, g1v, r0, r1, r2, px, py[1], cA1, S[1], vS1, e0[1], e1[1], e2[1], eD[1],
-                          bp.alpha_max);
+#pragma unroll
+            for (int q = 0; q < PPL; ++q)
+                if (gv[q] > 0.f)
+                    pair_grad(acc, dop, dv, gv[q], r0, r1, r2, px, py[q], v * Tn[q], S[q], v * S[q], e0[q], e1[q],
+                              e2[q], eD[q], bp.alpha_max);
             const float tot = transposed_warp_sum8(acc, lane);
             const float dop_tot = warp_sum(dop);
             float *gk = gbase + k * kGradF;
@@ -662,10 +690,10 @@ void launch_blend_bwd(const ViewDesc *views, int n_views, int total_tiles, int K
                       const float *D, const int *nd, const float *dL_drgb, float *g2d, float *g_cell_v,
                       cudaStream_t st) {
     if (total_tiles == 0) return;
-    const unsigned grid = (unsigned)total_tiles * WSUB;
-#define DGS_BWD(KV)                                                                                       \
-    k_blend_bwd<KV><<<grid, WT, 0, st>>>(views, n_views, ranges, tile_cells, rec, bp, rgb, D, nd, dL_drgb, g2d, \
-                                         g_cell_v)
+    const unsigned grid = (unsigned)total_tiles * BWD_SUB;
+#define DGS_BWD(KV)                                                                                             \
+    k_blend_bwd<KV, BWD_PPL><<<grid, WT, 0, st>>>(views, n_views, ranges, tile_cells, rec, bp, rgb, D, nd, dL_drgb, \
+                                                  g2d, g_cell_v)
     switch (K_all) {
         case 8: DGS_BWD(8); break;
         case 10: DGS_BWD(10); break;
