@@ -119,15 +119,22 @@ class Clocks:
                 "samples": len(rows)}
 
 
-def dist_setup(args):
-    import torch
+def dist_setup(args, backend=None):
+    """One process per GPU under torchrun (RANK / LOCAL_RANK / WORLD_SIZE /
+    MASTER_* from the environment): NCCL on GPUs, gloo otherwise."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
+        import torch
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if backend is None:
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group(backend)
     return world, rank, local
 
 
@@ -142,9 +149,16 @@ def max_over_ranks(x, world):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def weak_value(ms_total, world, px_per_rank_step, steps):
+    """Whole-job Mpix/s: every rank renders its own views (weak scaling), so
+    the job processed world x px x steps pixels in the slowest rank's time."""
+    return world * px_per_rank_step * steps / (ms_total / 1e3) / 1e6
 
 
 def cameras_for(rank, n_views=N_VIEWS):
@@ -421,6 +435,7 @@ def main():
     rctx.release_state(st0)
     torch.cuda.synchronize()
 
+    alu = rctx.probe_alu()  # measured FP32 and exp2 issue rates (outside the timed region)
     stream = torch.cuda.current_stream()
     clocks = Clocks(local)
     barrier(world)
@@ -441,7 +456,7 @@ def main():
     ms = e0.elapsed_time(e1)
     ms = max_over_ranks(ms, world)
     px_step = nv * W_IMG * H_IMG
-    value = world * px_step * args.steps / (ms / 1e3) / 1e6
+    value = weak_value(ms, world, px_step, args.steps)
 
     # dominant kernel and its roofline
     stage_ms = {k: v[0] / max(1, v[1]) for k, v in prof.items() if v[1] > 0}
@@ -452,13 +467,23 @@ def main():
     if dom in ("blend_fwd", "blend_bwd"):
         flop = cnt["inbox_rendered"] * (FLOP_FWD if dom == "blend_fwd" else FLOP_BWD)
         ach = flop / (stage_ms[dom] / 1e3) / 1e12
-        peak = fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+        derived = fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+        peak = alu["fp32_tflops"]
+        # SFU work: one exp2 per in-AABB pair (forward); exp2 and a reciprocal (adjoint)
+        sfu = cnt["inbox_rendered"] * (1 if dom == "blend_fwd" else 2)
+        traffic = measured_traffic(dom, nv)
         roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": measured_traffic(dom, nv),
-                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x max SM clock (2070 MHz)",
+                "traffic": traffic,
+                "peak_source": "measured: FP32 FMA rate of dgs_probe_alu on this GPU (of measured); derived "
+                               f"152 SM x 128 lanes x 2 x 2070 MHz = {derived:.1f}",
                 "flop_per_launch": flop, "flop_per_unit": FLOP_FWD if dom == "blend_fwd" else FLOP_BWD,
                 "units_per_launch": cnt["inbox_rendered"], "unit_def": "(pixel, Gaussian) pairs inside the AABB of "
-                                                                        "blended cells"}
+                                                                        "blended cells",
+                "sfu": {"ops_per_launch": sfu, "achieved_per_s": sfu / (stage_ms[dom] / 1e3),
+                        "peak_per_s": alu["ex2_per_s"], "frac": sfu / (stage_ms[dom] / 1e3) / alu["ex2_per_s"]},
+                "hbm": None if traffic is None else
+                {"bytes_per_launch": traffic, "achieved_gbs": traffic / (stage_ms[dom] / 1e3) / 1e9,
+                 "peak_gbs": peaks["hbm_gbs"], "frac": traffic / (stage_ms[dom] / 1e3) / 1e9 / peaks["hbm_gbs"]}}
     else:
         nbytes = {"project_fwd": G * (59 * 4) + nv * G * 48, "project_bwd": G * (59 * 4) * 2 + nv * G * 96}
         b = nbytes.get(dom, 0)
@@ -526,6 +551,9 @@ def main():
     fwd_ms = sum(prof[k][0] for k in ("cell_project", "depth_sort", "count_scan", "emit", "tile_sort",
                                        "tile_ranges", "project_fwd", "blend_fwd")) / args.steps
     line["fwd_mpix_s"] = px_step / (fwd_ms / 1e3) / 1e6 if fwd_ms > 0 else None
+    line["fps"] = {"fwd_bwd": world * nv * args.steps / (ms / 1e3), "fwd": nv / (fwd_ms / 1e3) if fwd_ms > 0 else None}
+    line["alu_probe"] = alu
+    line["streaming"] = streaming_stages(prof, args.steps, nv, scene, stats, peaks)
     # kernel launches per step: binning 11 + sort passes + projection + blend + backward 2 + loss 2
     line["gpu_launches"] = int(args.steps * launches_per_step(stats))
 
@@ -556,6 +584,38 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def streaming_stages(prof, steps, nv, scene, stats, peaks):
+    """Algorithmic HBM bytes of the memory-bound stages of one step and their
+    fraction of the measured copy bandwidth (CUDA-event stage times)."""
+    E = nv * scene.N                          # (view, cell) entries
+    L = int(stats.sort_length)                # (tile, cell) pairs
+    T = int(stats.num_tiles)
+    vis_rec = int(stats.visible_cells) * scene.K  # records of Gaussians of visible cells
+    G, P = scene.G, 59 * 4                    # parameter bytes per Gaussian
+    tile_passes = max(1, math.ceil(max(1, math.ceil(math.log2(max(2, T)))) / 8))
+    algo = {
+        "cell_project": E * (44 + 24),                     # cell parameters read, key/val/rect/depth/count written
+        "depth_sort": E * (4 + 4 * 16),                    # histogram read + 4 passes of 8 B read + 8 B written
+        "count_scan": E * 28,                              # gather and two-pass scan
+        "emit": L * 8 + E * 12,                            # pairs written, entry offsets/rects read
+        "tile_sort": L * (4 + tile_passes * 16),
+        "tile_ranges": L * 4 + T * 8,
+        "project_fwd": G * P + vis_rec * 48,               # parameters once per batch, one record per view
+        "project_bwd": 2 * G * P + vis_rec * 48,           # parameters read, gradients written, records' grads read
+    }
+    out = {}
+    for k, b in algo.items():
+        if k not in prof or prof[k][1] == 0:
+            continue
+        ms = prof[k][0] / steps
+        gbs = b / (ms / 1e3) / 1e9
+        out[k] = {"bytes": int(b), "ms": ms, "gbs": gbs, "frac": gbs / peaks["hbm_gbs"]}
+    tb = sum(v["bytes"] for v in out.values())
+    tm = sum(v["ms"] for v in out.values())
+    out["all"] = {"bytes": int(tb), "ms": tm, "gbs": tb / (tm / 1e3) / 1e9, "frac": tb / (tm / 1e3) / 1e9 / peaks["hbm_gbs"]}
+    return out
 
 
 def launches_per_step(stats):

@@ -301,6 +301,23 @@ dgs_status dgs_render_compare(dgs_ctx *ctx, uint32_t scene_id, int32_t n_views, 
                               const dgs_compare_config *cfg, float *out_rgb, int32_t *out_ndone,
                               dgs_stream stream, dgs_stats *stats);
 
+/* ------------------------------------------------------------------ probes */
+
+/* Measured issue rates for the blend kernels' roofline (they are bound by
+ * FP32 and SFU instruction issue, not by memory): fp32_tflops from eight
+ * independent FMA chains per thread on a full-occupancy grid (2 FLOP per
+ * FMA), ex2_per_s from eight independent ex2.approx.f32 chains; ms_* are
+ * the timed launches' device times.  Runs on the context's device,
+ * synchronises it, takes about 100 ms.  Errors: INVALID_ARG, CUDA, OOM. */
+typedef struct {
+    double fp32_tflops;
+    double ex2_per_s;
+    float ms_fma, ms_ex2;
+    int32_t sm_count;
+    int32_t reserved;
+} dgs_alu_peaks;
+dgs_status dgs_probe_alu(dgs_ctx *ctx, dgs_alu_peaks *out);
+
 /* ---------------------------------------------------------------- serving */
 
 /* Continuous-batching request loop (not in the paper; serving workload).

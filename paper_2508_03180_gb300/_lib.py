@@ -86,6 +86,11 @@ class dgs_serve_stats(C.Structure):
                 ("pairs_per_tile", C.c_double)]
 
 
+class dgs_alu_peaks(C.Structure):
+    _fields_ = [("fp32_tflops", C.c_double), ("ex2_per_s", C.c_double), ("ms_fma", C.c_float),
+                ("ms_ex2", C.c_float), ("sm_count", C.c_int32), ("reserved", C.c_int32)]
+
+
 DGS_SERVE_NO_GRAPHS = 1
 DGS_COMPARE_ALPHA = 1
 DGS_COMPARE_WSR = 2
@@ -122,6 +127,7 @@ _SIGS = {
     "dgs_profile_read": (C.c_int32, [_P, C.POINTER(dgs_profile)]),
     "dgs_render_compare": (C.c_int32, [_P, C.c_uint32, C.c_int32, C.POINTER(C.c_uint32),
                                        C.POINTER(dgs_compare_config), _P, _P, _P, C.POINTER(dgs_stats)]),
+    "dgs_probe_alu": (C.c_int32, [_P, C.POINTER(dgs_alu_peaks)]),
     "dgs_serve_start": (C.c_int32, [_P, C.c_int32, C.c_int32, C.c_int32]),
     "dgs_serve_read_stats": (C.c_int32, [_P, C.POINTER(dgs_serve_stats)]),
     "dgs_serve_stop": (C.c_int32, [_P]),
@@ -270,6 +276,12 @@ def dgs_profile_read(ctx) -> dgs_profile:
     p = dgs_profile()
     check(load().dgs_profile_read(ctx, C.byref(p)), ctx)
     return p
+
+
+def dgs_probe_alu(ctx) -> dgs_alu_peaks:
+    r = dgs_alu_peaks()
+    check(load().dgs_probe_alu(ctx, C.byref(r)), ctx)
+    return r
 
 
 def dgs_serve_start(ctx, max_batch: int, queue_cap: int, flags: int = 0):

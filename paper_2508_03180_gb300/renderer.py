@@ -203,6 +203,11 @@ class Context:
         p = L.dgs_profile_read(self.ctx)
         return {name: (p.ms[i], p.launches[i]) for i, name in enumerate(L.STAGES)}
 
+    def probe_alu(self) -> dict:
+        r = L.dgs_probe_alu(self.ctx)
+        return {"fp32_tflops": r.fp32_tflops, "ex2_per_s": r.ex2_per_s, "ms_fma": r.ms_fma, "ms_ex2": r.ms_ex2,
+                "sm_count": r.sm_count}
+
     # ------------------------------------------------------------ serving
     def serve_start(self, max_batch: int = 8, queue_cap: int = 1024, graphs: bool = True):
         """graphs=False runs each batch as a plain launch chain instead of a

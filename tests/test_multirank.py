@@ -1,0 +1,55 @@
+"""The N > 1 host path of bench.py on CPU ranks (gloo, world size 2): each
+rank renders its own seeded views (no data-path collective), the timing is
+the maximum over ranks, the value is the whole-job pixel rate, and only
+rank 0 reports."""
+import os
+import sys
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _rank_main(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), LOCAL_RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    sys.path.insert(0, ROOT)
+    import bench
+    w, r, local = bench.dist_setup(None, backend="gloo")
+    cams = [c.as_array().tolist() for c in bench.cameras_for(r, n_views=2)]
+    bench.barrier(w)
+    ms = bench.max_over_ranks(10.0 + 5.0 * r, w)  # rank 1 is the slow one
+    value = bench.weak_value(ms, w, 1000, 4)
+    q.put((r, w, cams, ms, value))
+    import torch.distributed as dist
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks():
+    import socket
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    (r0, w0, cams0, ms0, v0), (r1, w1, cams1, ms1, v1) = res
+    assert (r0, r1, w0, w1) == (0, 1, 2, 2)
+    assert cams0 != cams1                     # every rank its own views
+    assert ms0 == ms1 == 15.0                 # the slowest rank's time
+    assert v0 == v1 == pytest.approx(2 * 1000 * 4 / 15e-3 / 1e6)
+
+
+def test_single_rank_needs_no_process_group():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks(3.0, 1) == 3.0
+    assert bench.weak_value(1000.0, 1, 2_000_000, 10) == pytest.approx(20.0)
