@@ -128,8 +128,9 @@ __device__ __forceinline__ bool touches_rows(float4 r0, float x0, float y0, floa
 }
 
 // The forward's work unit: one warp per 16 x (2 PPL) sub-tile, lane l
-// blending the PPL vertically adjacent pixels (x, PPL h .. PPL h + PPL - 1),
-// x = l mod 16, h = l / 16.  FWD_PPL = 2 (16x4 sub-tiles, 68 registers):
+// blending the PPL pixels (x, h + 2 q), x = l mod 16, h = l / 16 (rows
+// interleaved so that a Gaussian reaching only some rows keeps more lanes
+// busy).  FWD_PPL = 2 (16x4 sub-tiles, 68 registers):
 // 16x8 sub-tiles halve the (sub-tile, Gaussian) pairs on the benchmark scene
 // but need ~95 registers (21 warps/SM) and measured no faster.
 constexpr int FWD_PPL = 2;
@@ -151,7 +152,7 @@ __device__ __forceinline__ void blend_fwd_unit(int unit, const ViewDesc *__restr
     const int tx = local % V.Tx, ty = local / V.Tx;
     const float bx0 = (float)(tx * kTile), by0 = (float)(ty * kTile + ROWS * sub);
     const int xi = tx * kTile + (lane & (kTile - 1));
-    const int yb = ty * kTile + ROWS * sub + PPL * (lane >> 4);
+    const int yb = ty * kTile + ROWS * sub + (lane >> 4);
     const float px = (float)xi + 0.5f;
     const int K = KT > 0 ? KT : V.K;
     const int per = kRecF4 * K;
@@ -164,8 +165,8 @@ __device__ __forceinline__ void blend_fwd_unit(int unit, const ViewDesc *__restr
 #pragma unroll
     for (int q = 0; q < PPL; ++q) {
         T[q] = 1.0f; N0[q] = N1[q] = N2[q] = D[q] = 0.f; n[q] = 0;
-        py[q] = (float)(yb + q) + 0.5f;
-        done[q] = !(xi < V.W && yb + q < V.H);
+        py[q] = (float)(yb + 2 * q) + 0.5f;
+        done[q] = !(xi < V.W && yb + 2 * q < V.H);
     }
     float4 pre[3];
     if (rg.x < rg.y) {
@@ -238,8 +239,8 @@ __device__ __forceinline__ void blend_fwd_unit(int unit, const ViewDesc *__restr
     float *im2 = out_rgb2 ? out_rgb2 + 3 * V.pix_base : nullptr;
 #pragma unroll
     for (int q = 0; q < PPL; ++q) {
-        if (!(xi < V.W && yb + q < V.H)) continue;
-        const long long pin = (long long)(yb + q) * V.W + xi;
+        if (!(xi < V.W && yb + 2 * q < V.H)) continue;
+        const long long pin = (long long)(yb + 2 * q) * V.W + xi;
         const bool hit = D[q] > bp.d_min;
         const float c0 = hit ? N0[q] / D[q] : bp.bg0;
         const float c1 = hit ? N1[q] / D[q] : bp.bg1;
@@ -501,8 +502,7 @@ __device__ __forceinline__ float slot_scale(int j) {
 __device__ __forceinline__ int grad_slot(int j) { return j < 5 ? j : j + 1; }
 
 // The adjoint's work unit: one warp per 16 x (2 PPL) sub-tile, lane l
-// handling the PPL pixels (x, PPL h + q), x = l mod 16, h = l / 16, as in the
-// forward.  Per cell: pass 1 replays the forward (keeping G' of the Gaussians
+// handling the PPL pixels (x, h + 2 q), x = l mod 16, h = l / 16.  Per cell: pass 1 replays the forward (keeping G' of the Gaussians
 // that reach the sub-tile in warp-private shared memory) and updates T and
 // S; pass 2 forms each such Gaussian's screen-space gradient over the
 // sub-tile's pixels and adds the warp total with global atomics.
@@ -529,7 +529,10 @@ __global__ void __launch_bounds__(WT, BWD_MINB) k_blend_bwd(const ViewDesc *__re
     const int tx = local % V.Tx, ty = local / V.Tx;
     const float bx0 = (float)(tx * kTile), by0 = (float)(ty * kTile + ROWS * sub);
     const int xi = tx * kTile + (lane & (kTile - 1));
-    const int yb = ty * kTile + ROWS * sub + PPL * (lane >> 4);
+    // lane (x, h) takes rows h, h + 2, ..., h + 2 (PPL - 1) of the sub-tile:
+    // a Gaussian reaching only some rows then keeps more lanes busy than with
+    // PPL adjacent rows per lane
+    const int yb = ty * kTile + ROWS * sub + (lane >> 4);
     const float px = (float)xi + 0.5f;
     const long long HW = (long long)V.W * V.H;
     const int K = KT > 0 ? KT : V.K;
@@ -542,9 +545,9 @@ __global__ void __launch_bounds__(WT, BWD_MINB) k_blend_bwd(const ViewDesc *__re
     for (int q = 0; q < PPL; ++q) {
         nd[q] = 0;
         e0[q] = e1[q] = e2[q] = eD[q] = 0.f;
-        py[q] = (float)(yb + q) + 0.5f;
-        if (xi < V.W && yb + q < V.H) {
-            const long long pin = (long long)(yb + q) * V.W + xi;
+        py[q] = (float)(yb + 2 * q) + 0.5f;
+        if (xi < V.W && yb + 2 * q < V.H) {
+            const long long pin = (long long)(yb + 2 * q) * V.W + xi;
             const float Dv = Dpix[V.pix_base + pin];
             if (Dv > bp.d_min) {
                 nd[q] = ndpix[V.pix_base + pin];
