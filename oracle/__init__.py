@@ -187,6 +187,22 @@ def project64(scene, cam, opt: Options = Options(), mask=None, requires_grad=Fal
     return full, graph
 
 
+def cell_v_view(scene, cam):
+    """v_n of every cell as rendered from camera `cam` (FP64), and for a
+    view-dependent v (Sec. V-A: v parameterised by spherical harmonics) the
+    basis values and the unclamped mask: v_n = clamp(sum_lm k_lm Y_lm(d), 0, 1)
+    with d the unit vector from the eye to the cell centre."""
+    vsh = getattr(scene, "cell_v_sh", None)
+    if vsh is None:
+        return np.asarray(scene.cell_v, dtype=np.float64), None
+    eye = np.asarray(cam, dtype=np.float64)[19:22]
+    d = np.asarray(scene.cell_center, dtype=np.float64) - eye[None, :]
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    Y = _project.sh_basis(torch.from_numpy(d), scene.v_sh_degree).numpy()
+    raw = (np.asarray(vsh, dtype=np.float64) * Y).sum(1)
+    return np.clip(raw, 0.0, 1.0), dict(Y=Y, mask=(raw > 0.0) & (raw < 1.0))
+
+
 def prepare_view(scene, cam, opt: Options = Options(), tile_rows=None, requires_grad=False):
     """All per-view inputs of the blend: tile lists, FP32 decisions, FP64
     projected values (only for valid Gaussians of cells that reach the
@@ -204,15 +220,17 @@ def prepare_view(scene, cam, opt: Options = Options(), tile_rows=None, requires_
     mask = np.repeat(used_cells, scene.K) & (valid != 0)
     proj, graph = project64(scene, cam, opt, mask, requires_grad)
     return dict(rect=rect, depth=depth, cells=cells, range=rng, mu2f=mu2f, extf=extf, valid=valid,
-                proj=proj, graph=graph, W=W, H=H, Tx=Tx, Ty=Ty, rows=(ty0, ty1), mask=mask)
+                proj=proj, graph=graph, W=W, H=H, Tx=Tx, Ty=Ty, rows=(ty0, ty1), mask=mask,
+                cam=np.asarray(cam, dtype=np.float32))
 
 
 def _blend_args(scene, pv, opt):
     pr = pv["proj"]
+    pv["_v"] = _c(cell_v_view(scene, pv["cam"])[0], np.float64)  # kept alive during the call
     return (pv["W"], pv["H"], opt.tile, scene.K, _p(pv["range"]), _p(pv["cells"]),
             _p(_c(pr["mu2"], np.float64)), _p(_c(pr["conic"], np.float64)), _p(_c(pr["opac"], np.float64)),
             _p(_c(pr["rgb"], np.float64)), _p(pv["mu2f"]), _p(pv["extf"]), _p(pv["valid"]),
-            _p(_c(scene.cell_v, np.float64)), _p(opt.blend_opts()))
+            _p(pv["_v"]), _p(opt.blend_opts()))
 
 
 def render_view(scene, cam, opt: Options = Options(), forced_ndone=None, tile_rows=None, pv=None):
@@ -265,6 +283,9 @@ def param_grads(scene, pv, g2d):
         res[name] = arr
     res["log_scale"] = res["scale"] * np.asarray(scene.g_scale, dtype=np.float64)
     res["cell_v"] = g2d["v"]
+    _, info = cell_v_view(scene, pv["cam"])
+    if info is not None:  # through the clamp and the SH basis
+        res["cell_v_sh"] = (g2d["v"] * info["mask"])[:, None] * info["Y"]
     return res
 
 

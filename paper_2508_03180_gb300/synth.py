@@ -82,6 +82,8 @@ class Scene:
     g_sh: np.ndarray
     name: str = ""
     meta: dict = field(default_factory=dict)
+    cell_v_sh: np.ndarray | None = None  # (N, (v_sh_degree+1)^2) view-dependent v_n, or None
+    v_sh_degree: int = -1
 
     @property
     def N(self) -> int:
@@ -100,7 +102,9 @@ class Scene:
                      self.cell_quat[idx].copy(), self.cell_v[idx].copy(),
                      self.g_mean[gidx].copy(), self.g_scale[gidx].copy(),
                      self.g_quat[gidx].copy(), self.g_logit[gidx].copy(),
-                     self.g_sh[gidx].copy(), name=self.name + "-subset", meta=dict(self.meta))
+                     self.g_sh[gidx].copy(), name=self.name + "-subset", meta=dict(self.meta),
+                     cell_v_sh=None if self.cell_v_sh is None else self.cell_v_sh[idx].copy(),
+                     v_sh_degree=self.v_sh_degree)
 
 
 # ----------------------------------------------------------------------------
@@ -179,6 +183,21 @@ def make_scene(n_cells: int, K: int, centers_fn, axes_lo: float, axes_hi: float,
                  g_mean=f32(mean), g_scale=f32(scale), g_quat=f32(gq),
                  g_logit=f32(logit), g_sh=np.ascontiguousarray(sh), name=name,
                  meta=dict(seed=seed, n_cells=N, K=K))
+
+
+def with_view_dependent_v(scene: Scene, degree: int = 2, seed: int = 0, base: float = 0.8,
+                          band_std: float = 0.15) -> Scene:
+    """A copy of `scene` whose calibration v_n is given by real SH
+    coefficients of the given degree: DC = base / Y_00 (so v is `base` with
+    no view dependence), higher bands N(0, band_std), drawn from `seed`."""
+    import dataclasses
+    rng = np.random.default_rng(seed)
+    nco = (degree + 1) ** 2
+    k = np.zeros((scene.N, nco), dtype=np.float32)
+    k[:, 0] = np.float32(base * _INV_Y00)
+    if nco > 1:
+        k[:, 1:] = rng.standard_normal((scene.N, nco - 1), dtype=np.float32) * np.float32(band_std)
+    return dataclasses.replace(scene, cell_v_sh=k, v_sh_degree=degree, name=scene.name + f"-vsh{degree}")
 
 
 def _box(lo, hi):
