@@ -88,7 +88,15 @@ const char *dgs_last_error(dgs_ctx *ctx);
  *   g_sh [G][(sh_degree+1)^2][3] real spherical-harmonic colour
  *   coefficients (colour = max(0, 0.5 + sum_lm k_lm Y_lm(view dir))).
  * The data are copied into context memory.  K in [1, 32], sh_degree in 0..3,
- * N >= 0 (an empty scene renders the background). */
+ * N >= 0 (an empty scene renders the background).
+ *
+ * View-dependent v_n (Sec. V-A: v is parameterised by spherical harmonics
+ * because cell occlusion depends on the view): with cell_v_sh
+ * [N][(v_sh_degree+1)^2] (v_sh_degree in 0..3) the renderer uses, per view,
+ *   v_n = clamp(sum_lm k_lm Y_lm(d), 0, 1),  d = (c_n - eye) / |c_n - eye|,
+ * (the colour's real SH basis; c_n the cell centre); cell_v is then used
+ * only by the comparators (dgs_render_compare).  cell_v_sh = NULL: the
+ * scalar cell_v. */
 typedef struct {
     int64_t num_cells;
     int32_t K;
@@ -97,11 +105,14 @@ typedef struct {
     int32_t reserved;
     const float *cell_center, *cell_axes, *cell_quat, *cell_v;
     const float *g_mean, *g_scale, *g_quat, *g_logit, *g_sh;
+    const float *cell_v_sh;
+    int32_t v_sh_degree;
+    int32_t reserved2;
 } dgs_scene_desc;
 
 dgs_status dgs_scene_upload(dgs_ctx *ctx, const dgs_scene_desc *desc, uint32_t *scene_id);
-/* Overwrite the Gaussian parameters (and v) of an existing scene in place,
- * same N, K and degree (a training step's update).  Asynchronous on stream
+/* Overwrite the Gaussian parameters (and v, or its SH coefficients) of an
+ * existing scene in place, same N, K and degrees (a training step's update).  Asynchronous on stream
  * for device inputs. */
 dgs_status dgs_scene_update(dgs_ctx *ctx, uint32_t scene_id, const dgs_scene_desc *desc, dgs_stream stream);
 dgs_status dgs_scene_release(dgs_ctx *ctx, uint32_t scene_id);
@@ -149,13 +160,16 @@ dgs_status dgs_render(dgs_ctx *ctx, uint32_t scene_id, int32_t n_views, const ui
  * OVERWRITTEN (not accumulated), same layout as the scene arrays:
  *   g_mean [G][3], g_scale [G][3] (dL/dscale), g_log_scale [G][3]
  *   (= scale * dL/dscale), g_quat [G][4], g_logit [G], g_sh [G][C][3],
- *   g_cell_v [N].
+ *   g_cell_v [N] (dL/dv_n summed over the views, v_n as rendered in each),
+ *   g_cell_v_sh [N][(v_sh_degree+1)^2] (scenes with view-dependent v only:
+ *   sum over views of dL/dv_n Y_lm(d), zero where the clamp was active).
  * Discrete choices of the forward (culling, tile lists, AABB skips, alpha
  * clamp, the per-pixel number of blended cells) are held fixed. */
 typedef struct {
     int32_t location;
     int32_t reserved;
     float *g_mean, *g_scale, *g_log_scale, *g_quat, *g_logit, *g_sh, *g_cell_v;
+    float *g_cell_v_sh;
 } dgs_grads;
 
 dgs_status dgs_render_backward(dgs_ctx *ctx, dgs_fwd_state *state, const float *dL_drgb, int32_t location,
@@ -179,6 +193,7 @@ dgs_status dgs_loss_l1(dgs_ctx *ctx, const float *rgb, const float *target, int6
  *   DGS_BUF_PIX_D       float [P]        per-pixel weight sum D (P = all views' pixels)
  *   DGS_BUF_PIX_NDONE   int32 [P]        per-pixel number of blended cells
  *   DGS_BUF_GRAD2D      float [V][G][12] after backward: dmu_x dmu_y da db dc dsigma dr dg db 0 0 0
+ *   DGS_BUF_CELL_V      float [V][N]     v_n as rendered in each view
  * *needed receives the byte size; nothing is copied if bytes < needed.
  * Synchronises the stream the state was rendered on. */
 enum {
@@ -189,7 +204,8 @@ enum {
     DGS_BUF_GAUSS_REC = 5,
     DGS_BUF_PIX_D = 6,
     DGS_BUF_PIX_NDONE = 7,
-    DGS_BUF_GRAD2D = 8
+    DGS_BUF_GRAD2D = 8,
+    DGS_BUF_CELL_V = 9
 };
 dgs_status dgs_state_read(dgs_ctx *ctx, const dgs_fwd_state *state, int32_t what, void *host_dst, int64_t bytes,
                           int64_t *needed);

@@ -31,6 +31,7 @@ DGS_BUF_GAUSS_REC = 5
 DGS_BUF_PIX_D = 6
 DGS_BUF_PIX_NDONE = 7
 DGS_BUF_GRAD2D = 8
+DGS_BUF_CELL_V = 9
 
 _P = C.c_void_p
 _FP = C.POINTER(C.c_float)
@@ -45,7 +46,8 @@ class dgs_config(C.Structure):
 class dgs_scene_desc(C.Structure):
     _fields_ = [("num_cells", C.c_int64), ("K", C.c_int32), ("sh_degree", C.c_int32), ("location", C.c_int32),
                 ("reserved", C.c_int32), ("cell_center", _P), ("cell_axes", _P), ("cell_quat", _P), ("cell_v", _P),
-                ("g_mean", _P), ("g_scale", _P), ("g_quat", _P), ("g_logit", _P), ("g_sh", _P)]
+                ("g_mean", _P), ("g_scale", _P), ("g_quat", _P), ("g_logit", _P), ("g_sh", _P),
+                ("cell_v_sh", _P), ("v_sh_degree", C.c_int32), ("reserved2", C.c_int32)]
 
 
 class dgs_camera(C.Structure):
@@ -61,7 +63,7 @@ class dgs_stats(C.Structure):
 
 class dgs_grads(C.Structure):
     _fields_ = [("location", C.c_int32), ("reserved", C.c_int32), ("g_mean", _P), ("g_scale", _P), ("g_log_scale", _P),
-                ("g_quat", _P), ("g_logit", _P), ("g_sh", _P), ("g_cell_v", _P)]
+                ("g_quat", _P), ("g_logit", _P), ("g_sh", _P), ("g_cell_v", _P), ("g_cell_v_sh", _P)]
 
 
 class dgs_counts(C.Structure):

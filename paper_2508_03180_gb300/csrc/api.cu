@@ -75,7 +75,7 @@ Workspace::~Workspace() {
 
 std::vector<DevBuf *> Workspace::all() {
     return {&views, &scenes, &zkey, &zval, &rect, &depth, &count, &cnt_sorted, &offs, &tkey, &tval, &ranges, &rec,
-            &Dpix, &ndpix, &rgb, &g2d, &gstage, &sort_k, &sort_v, &sort_hist, &sort_status, &sort_ctr, &small, &scan, &sizes};
+            &Dpix, &ndpix, &rgb, &g2d, &gstage, &sort_k, &sort_v, &sort_hist, &sort_status, &sort_ctr, &small, &scan, &sizes, &vview, &gvview};
 }
 
 dgs_status Workspace::init() {
@@ -160,10 +160,13 @@ SceneDev Scene::dev() const {
     d.cell = (const float *)cell.p;
     d.gauss = (const float *)gauss.p;
     d.sh = (const float *)sh.p;
+    d.vsh = vdeg >= 0 ? (const float *)vsh.p : nullptr;
     d.N = N;
     d.G = G;
     d.K = K;
     d.sh_degree = deg;
+    d.v_sh_degree = vdeg;
+    d.pad = 0;
     return d;
 }
 
@@ -258,6 +261,9 @@ static dgs_status fill_scene(dgs_ctx *ctx, Scene &sc, const dgs_scene_desc *d, c
     } else if (cells_too) {
         launch_fill_f32(cell + 10 * N, N, 1.0f, st);
     }
+    if (sc.vdeg >= 0 && d->cell_v_sh) {
+        if ((s = upload_param(ctx, d->cell_v_sh, d->location, N, sc.Cv, (float *)sc.vsh.p, N, st))) return s;
+    }
     if ((s = upload_param(ctx, d->g_mean, d->location, G, 3, gs, G, st))) return s;
     if ((s = upload_param(ctx, d->g_scale, d->location, G, 3, gs + 3 * G, G, st))) return s;
     if ((s = upload_param(ctx, d->g_quat, d->location, G, 4, gs + 6 * G, G, st))) return s;
@@ -276,6 +282,8 @@ static dgs_status check_desc(const dgs_scene_desc *d, bool need_cells = true) {
     if (d->num_cells > 0 && ((need_cells && (!d->cell_center || !d->cell_axes || !d->cell_quat)) || !d->g_mean ||
                              !d->g_scale || !d->g_quat || !d->g_logit || !d->g_sh))
         return set_error(DGS_ERR_INVALID_ARG, "a scene array is NULL");
+    if (d->cell_v_sh && (d->v_sh_degree < 0 || d->v_sh_degree > 3))
+        return set_error(DGS_ERR_INVALID_ARG, "v_sh_degree must be in 0..3 with cell_v_sh");
     return DGS_OK;
 }
 
@@ -291,6 +299,9 @@ extern "C" dgs_status dgs_scene_upload(dgs_ctx *ctx, const dgs_scene_desc *d, ui
     sc->G = sc->N * sc->K;
     sc->deg = d->sh_degree;
     sc->C = (sc->deg + 1) * (sc->deg + 1);
+    sc->vdeg = d->cell_v_sh ? d->v_sh_degree : -1;
+    sc->Cv = sc->vdeg >= 0 ? (sc->vdeg + 1) * (sc->vdeg + 1) : 0;
+    if (sc->vdeg >= 0 && (s = sc->vsh.ensure(sizeof(float) * sc->Cv * std::max<int64_t>(1, sc->N)))) return s;
     if ((s = sc->cell.ensure(sizeof(float) * 11 * std::max<int64_t>(1, sc->N)))) return s;
     if ((s = sc->gauss.ensure(sizeof(float) * 11 * std::max<int64_t>(1, sc->G)))) return s;
     if ((s = sc->sh.ensure(sizeof(float) * 3 * sc->C * std::max<int64_t>(1, sc->G)))) return s;
@@ -312,8 +323,9 @@ extern "C" dgs_status dgs_scene_update(dgs_ctx *ctx, uint32_t scene_id, const dg
     auto it = ctx->scenes.find(scene_id);
     if (it == ctx->scenes.end()) return set_error(DGS_ERR_NOT_FOUND, "unknown scene id");
     Scene &sc = *it->second;
-    if (d->num_cells != sc.N || d->K != sc.K || d->sh_degree != sc.deg)
-        return set_error(DGS_ERR_INVALID_ARG, "update must keep N, K and sh_degree");
+    if (d->num_cells != sc.N || d->K != sc.K || d->sh_degree != sc.deg ||
+        (d->cell_v_sh && d->v_sh_degree != sc.vdeg))
+        return set_error(DGS_ERR_INVALID_ARG, "update must keep N, K, sh_degree and v_sh_degree");
     return fill_scene(ctx, sc, d, (cudaStream_t)stream, false);
 }
 
@@ -420,7 +432,8 @@ static dgs_status run_binning(dgs_ctx *ctx, Workspace &ws, cudaStream_t st) {
     CK(cudaMemsetAsync(ws.small.p, 0, 256, st));
     if ((s = ws.zkey.ensure(4 * n1)) || (s = ws.zval.ensure(4 * n1)) || (s = ws.rect.ensure(8 * n1)) ||
         (s = ws.depth.ensure(4 * n1)) || (s = ws.count.ensure(4 * n1)) || (s = ws.cnt_sorted.ensure(4 * n1)) ||
-        (s = ws.offs.ensure(4 * n1)) || (s = ws.scan.ensure(4 * scan_scratch_words(n1))))
+        (s = ws.offs.ensure(4 * n1)) || (s = ws.scan.ensure(4 * scan_scratch_words(n1))) ||
+        (s = ws.vview.ensure(4 * n1)))
         return s;
     if ((s = ensure_sort_scratch(ws, n))) return s;
     uint32_t *small = (uint32_t *)ws.small.p;
@@ -428,7 +441,8 @@ static dgs_status run_binning(dgs_ctx *ctx, Workspace &ws, cudaStream_t st) {
     {
         StageTimer t(pf, DGS_STAGE_CELL_PROJECT, st);
         launch_cell_project(dv, V, (const SceneDev *)ws.scenes.p, n, (uint32_t *)ws.zkey.p, (uint32_t *)ws.zval.p,
-                            (short4 *)ws.rect.p, (float *)ws.depth.p, (uint32_t *)ws.count.p, small + kSmallVisible, st);
+                            (short4 *)ws.rect.p, (float *)ws.depth.p, (uint32_t *)ws.count.p, small + kSmallVisible,
+                            (float *)ws.vview.p, st);
     }
     {
         StageTimer t(pf, DGS_STAGE_DEPTH_SORT, st);
@@ -533,8 +547,8 @@ dgs_status chain_forward(dgs_ctx *ctx, Workspace &ws, const std::vector<ChainVie
     {
         StageTimer t(ctx->prof, DGS_STAGE_PROJECT_FWD, st);
         for (int k = 0; k < S; ++k)
-            launch_project_fwd(dv, V, k, slots[k]->dev(), (const uint32_t *)ws.count.p, bp, (float4 *)ws.rec.p,
-                               grad_buffers ? (float *)ws.g2d.p : nullptr, st);
+            launch_project_fwd(dv, V, k, slots[k]->dev(), (const uint32_t *)ws.count.p, (const float *)ws.vview.p,
+                               bp, (float4 *)ws.rec.p, grad_buffers ? (float *)ws.g2d.p : nullptr, st);
     }
     float *img = out_img ? out_img : (float *)ws.rgb.p;
     float *img2 = (keep_rgb && out_img) ? (float *)ws.rgb.p : nullptr;
@@ -631,10 +645,12 @@ extern "C" dgs_status dgs_render_backward(dgs_ctx *ctx, dgs_fwd_state *state, co
     cudaStream_t st = (cudaStream_t)stream;
     CK(cudaStreamWaitEvent(st, ws.done, 0));
     const long long px = ws.total_px, G = sc.G, N = sc.N;
-    const int C = sc.C;
+    const int C = sc.C, Cv = sc.Cv;
+    if (out->g_cell_v_sh && sc.vdeg < 0)
+        return set_error(DGS_ERR_INVALID_ARG, "g_cell_v_sh given for a scene without view-dependent v");
     dgs_status s;
-    // staging: dL/drgb (3 px), then the six gradient outputs
-    const long long n_out = 3 * G + 3 * G + 3 * G + 4 * G + G + 3LL * C * G + N;
+    // staging: dL/drgb (3 px), then the gradient outputs
+    const long long n_out = 3 * G + 3 * G + 3 * G + 4 * G + G + 3LL * C * G + N + (long long)Cv * N;
     const long long n_stage = (location == DGS_HOST ? 3 * px : 0) + (out->location == DGS_HOST ? n_out : 0) + 1;
     if ((s = ws.gstage.ensure(sizeof(float) * n_stage))) return s;
     float *stage = (float *)ws.gstage.p;
@@ -645,7 +661,7 @@ extern "C" dgs_status dgs_render_backward(dgs_ctx *ctx, dgs_fwd_state *state, co
         stage += 3 * px;
     }
     float *o_mean = out->g_mean, *o_s = out->g_scale, *o_ls = out->g_log_scale, *o_q = out->g_quat,
-          *o_lg = out->g_logit, *o_sh = out->g_sh, *o_v = out->g_cell_v;
+          *o_lg = out->g_logit, *o_sh = out->g_sh, *o_v = out->g_cell_v, *o_vsh = out->g_cell_v_sh;
     if (out->location == DGS_HOST) {
         o_mean = out->g_mean ? stage : nullptr; stage += 3 * G;
         o_s = out->g_scale ? stage : nullptr; stage += 3 * G;
@@ -654,8 +670,15 @@ extern "C" dgs_status dgs_render_backward(dgs_ctx *ctx, dgs_fwd_state *state, co
         o_lg = out->g_logit ? stage : nullptr; stage += G;
         o_sh = out->g_sh ? stage : nullptr; stage += 3LL * C * G;
         o_v = out->g_cell_v ? stage : nullptr; stage += N;
+        o_vsh = out->g_cell_v_sh ? stage : nullptr; stage += (long long)Cv * N;
     }
-    if (o_v) CK(cudaMemsetAsync(o_v, 0, sizeof(float) * N, st));
+    // dL/dv per (view, cell) entry, chained to the outputs after the blend adjoint
+    float *gv = nullptr;
+    if (o_v || o_vsh) {
+        if ((s = ws.gvview.ensure(sizeof(float) * std::max(1LL, ws.n_entries)))) return s;
+        gv = (float *)ws.gvview.p;
+        CK(cudaMemsetAsync(gv, 0, sizeof(float) * ws.n_entries, st));
+    }
     const BlendParams bp = blend_params(ctx->cfg);
     if (ws.bwd_done) {  // a second backward on the same state: clear the screen-space accumulators
         CK(cudaMemsetAsync(ws.g2d.p, 0, sizeof(float) * kGradF * (size_t)ws.n_records, st));
@@ -664,7 +687,8 @@ extern "C" dgs_status dgs_render_backward(dgs_ctx *ctx, dgs_fwd_state *state, co
         StageTimer t(ctx->prof, DGS_STAGE_BLEND_BWD, st);
         launch_blend_bwd((const ViewDesc *)ws.views.p, ws.V, ws.total_tiles, sc.K, (const uint2 *)ws.ranges.p,
                          (const uint32_t *)ws.tval.p, (const float4 *)ws.rec.p, bp, (const float *)ws.rgb.p,
-                         (const float *)ws.Dpix.p, (const int *)ws.ndpix.p, dl, (float *)ws.g2d.p, o_v, st);
+                         (const float *)ws.Dpix.p, (const int *)ws.ndpix.p, dl, (float *)ws.g2d.p, gv, st);
+        if (gv) launch_cell_v_grad((const ViewDesc *)ws.views.p, ws.V, sc.dev(), gv, o_v, o_vsh, st);
     }
     {
         StageTimer t(ctx->prof, DGS_STAGE_PROJECT_BWD, st);
@@ -677,7 +701,8 @@ extern "C" dgs_status dgs_render_backward(dgs_ctx *ctx, dgs_fwd_state *state, co
         struct { float *h, *d; long long n; } cp[] = {{out->g_mean, o_mean, 3 * G}, {out->g_scale, o_s, 3 * G},
                                                       {out->g_log_scale, o_ls, 3 * G},
                                                       {out->g_quat, o_q, 4 * G}, {out->g_logit, o_lg, G},
-                                                      {out->g_sh, o_sh, 3LL * C * G}, {out->g_cell_v, o_v, N}};
+                                                      {out->g_sh, o_sh, 3LL * C * G}, {out->g_cell_v, o_v, N},
+                                                      {out->g_cell_v_sh, o_vsh, (long long)Cv * N}};
         for (auto &c : cp)
             if (c.h && c.n) CK(cudaMemcpyAsync(c.h, c.d, sizeof(float) * c.n, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
@@ -720,6 +745,7 @@ extern "C" dgs_status dgs_state_read(dgs_ctx *ctx, const dgs_fwd_state *state, i
         case DGS_BUF_PIX_D: need = 4 * ws.total_px; break;
         case DGS_BUF_PIX_NDONE: need = 4 * ws.total_px; break;
         case DGS_BUF_GRAD2D: need = ws.g2d.p ? 48 * VG : 0; break;
+        case DGS_BUF_CELL_V: need = 4 * VN; break;
         default: return set_error(DGS_ERR_INVALID_ARG, "unknown buffer id");
     }
     if (needed) *needed = need;
@@ -744,6 +770,7 @@ extern "C" dgs_status dgs_state_read(dgs_ctx *ctx, const dgs_fwd_state *state, i
         case DGS_BUF_PIX_D: src = ws.Dpix.p; break;
         case DGS_BUF_PIX_NDONE: src = ws.ndpix.p; break;
         case DGS_BUF_GRAD2D: src = ws.g2d.p; break;
+        case DGS_BUF_CELL_V: src = ws.vview.p; break;
     }
     CK(cudaMemcpy(dst, src, need, cudaMemcpyDeviceToHost));
     return DGS_OK;

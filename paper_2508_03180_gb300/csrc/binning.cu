@@ -3,6 +3,7 @@
 // and emit one (tile, cell) pair per covered tile.  Depth ordering comes from
 // a radix sort over cells (sort.cu); a second stable sort groups by tile.
 #include "internal.cuh"
+#include "sh.cuh"
 
 namespace dgs {
 
@@ -19,12 +20,13 @@ __global__ void __launch_bounds__(256) k_cell_project(const ViewDesc *__restrict
                                                       uint32_t *__restrict__ zkey, uint32_t *__restrict__ zval,
                                                       short4 *__restrict__ rect, float *__restrict__ depth,
                                                       uint32_t *__restrict__ count, uint32_t *__restrict__ visible,
-                                                      const ChainSizes *__restrict__ dsz) {
+                                                      float *__restrict__ vview, const ChainSizes *__restrict__ dsz) {
     if (dsz) n_views = dsz->n_views;
     uint32_t nvis = 0;
     for (int v = 0; v < n_views; ++v) {
     const ViewDesc &V = views[v];
-    const float *__restrict__ cell = scenes[V.scene_slot].cell;
+    const SceneDev &SC = scenes[V.scene_slot];
+    const float *__restrict__ cell = SC.cell;
     const long long N = V.N;
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
          n += (long long)gridDim.x * blockDim.x) {
@@ -82,6 +84,21 @@ __global__ void __launch_bounds__(256) k_cell_project(const ViewDesc *__restrict
             }
         }
         rect[i] = r;
+        // v_n of this view (Sec. V-A): the scalar, or clamp(sum_lm k_lm Y_lm(d), 0, 1)
+        // with d the unit vector from the eye to the cell centre
+        float vn = cell[10 * N + n];
+        if (SC.vsh) {
+            float d0 = cell[n] - V.eye[0], d1 = cell[N + n] - V.eye[1], d2 = cell[2 * N + n] - V.eye[2];
+            const float il = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+            d0 *= il; d1 *= il; d2 *= il;
+            float Y[16];
+            sh_eval(d0, d1, d2, SC.v_sh_degree, Y);
+            const int Cv = (SC.v_sh_degree + 1) * (SC.v_sh_degree + 1);
+            float raw = 0.f;
+            for (int c = 0; c < Cv; ++c) raw += SC.vsh[c * N + n] * Y[c];
+            vn = fminf(fmaxf(raw, 0.f), 1.f);
+        }
+        vview[i] = vn;
         // depth key: positive float bits order like the floats; culled last
         zkey[i] = vis ? __float_as_uint(c[2]) : 0xFFFFFFFFu;
         zval[i] = (uint32_t)i;
@@ -104,10 +121,10 @@ static int grid_for(long long n, int threads) {
 
 void launch_cell_project(const ViewDesc *views, int n_views, const SceneDev *scenes, long long n_entries,
                          uint32_t *zkey, uint32_t *zval, short4 *rect, float *depth, uint32_t *count,
-                         uint32_t *visible, cudaStream_t st, const ChainSizes *dsz) {
+                         uint32_t *visible, float *vview, cudaStream_t st, const ChainSizes *dsz) {
     if (n_entries == 0) return;
     k_cell_project<<<grid_for(n_entries / n_views + 1, 256), 256, 0, st>>>(views, n_views, scenes, zkey, zval, rect,
-                                                                          depth, count, visible, dsz);
+                                                                          depth, count, visible, vview, dsz);
 }
 
 __global__ void k_gather_counts(const uint32_t *__restrict__ idx, const uint32_t *__restrict__ count, long long n,

@@ -717,9 +717,9 @@ __global__ void __launch_bounds__(WT, BWD_MINB) k_blend_bwd(const ViewDesc *__re
             if ((lane & 3) == 0 && tot != 0.f) atomicAdd(gk + grad_slot(slot), tot * slot_scale(slot));
             if (lane == 1 && dop_tot != 0.f) atomicAdd(gk + 5, dop_tot);
         }
-        if (want_v) {
+        if (want_v) {  // per (view, cell) entry: v_n may differ between views
             dv = warp_sum(dv);
-            if (lane == 0 && dv != 0.f) atomicAdd(g_cell_v + cellid, dv);
+            if (lane == 0 && dv != 0.f) atomicAdd(g_cell_v + V.cell_base + cellid, dv);
         }
         __syncwarp();
         if (e + 1 < end) stash_cell(s_rec[buf ^ 1], per, lane, pre);

@@ -38,8 +38,11 @@ struct SceneDev {
     const float *cell;     // [11][N]: centre xyz, axes xyz, quat wxyz, v
     const float *gauss;    // [11][G]: mean xyz, scale xyz, quat wxyz, logit
     const float *sh;       // [C*3][G]: coefficient c, channel ch at plane c*3+ch
+    const float *vsh;      // [Cv][N]: SH coefficients of a view-dependent v_n, or NULL (scalar v_n)
     long long N, G;
     int K, sh_degree;
+    int v_sh_degree;       // -1 without vsh
+    int pad;
 };
 
 // Sizes of one launch chain kept in device memory.  A captured CUDA graph
@@ -100,9 +103,11 @@ __device__ __forceinline__ void xform_s(const float R[9], const float t[3], floa
 // binning.cu
 // Every launcher taking `dsz` (nullable) reads the sizes from it at run time;
 // `d_L` likewise points at the device-side pair count.
+// vview[entry]: v_n as rendered in that view (the scalar, or the clamped SH
+// value of a view-dependent v_n).
 void launch_cell_project(const ViewDesc *views, int n_views, const SceneDev *scenes, long long n_entries,
                          uint32_t *zkey, uint32_t *zval, short4 *rect, float *depth, uint32_t *count,
-                         uint32_t *visible, cudaStream_t st, const ChainSizes *dsz = nullptr);
+                         uint32_t *visible, float *vview, cudaStream_t st, const ChainSizes *dsz = nullptr);
 void launch_gather_counts(const uint32_t *zval_sorted, const uint32_t *count, long long n, uint32_t *out,
                           cudaStream_t st, const uint32_t *d_n = nullptr);
 void launch_emit(const uint32_t *offs, const uint32_t *zval_sorted, const short4 *rect, const ViewDesc *views,
@@ -138,7 +143,13 @@ void exclusive_scan_u32(const uint32_t *in, uint32_t *out, long long n, uint32_t
 // project.cu  (one launch per distinct scene of the chain: views whose
 // scene_slot differs from `slot` are skipped)
 void launch_project_fwd(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const uint32_t *count,
-                        const BlendParams &bp, float4 *rec, float *g2d_zero, cudaStream_t st);
+                        const float *vview, const BlendParams &bp, float4 *rec, float *g2d_zero, cudaStream_t st);
+// dL/dv per cell from the per-(view, cell) values gv of views [0, n_views)
+// (all of scene sc): g_cell_v[n] = sum over views (nullable), and for a
+// view-dependent v_n g_vsh[n][lm] = sum over views of gv Y_lm(d) where the
+// clamp was inactive (nullable).  Outputs overwritten.
+void launch_cell_v_grad(const ViewDesc *views, int n_views, const SceneDev &sc, const float *gv, float *g_cell_v,
+                        float *g_vsh, cudaStream_t st);
 // Comparator binning: one entry per (view, Gaussian), entry e = cell_base + g
 // (views with N = G, K = 1 entries); wsr selects the LC-WSR weight in r2.w.
 void launch_gauss_bin(const ViewDesc *views, int n_views, const SceneDev &sc, const BlendParams &bp, bool wsr,
@@ -147,7 +158,8 @@ void launch_gauss_bin(const ViewDesc *views, int n_views, const SceneDev &sc, co
 // One launch for every scene of the device scene table (dsz->n_scenes
 // entries, Gaussian counts <= G_cap, which sizes the grid).
 void launch_project_fwd_table(const ViewDesc *views, const SceneDev *scenes, long long G_cap, const uint32_t *count,
-                              const BlendParams &bp, float4 *rec, cudaStream_t st, const ChainSizes *dsz);
+                              const float *vview, const BlendParams &bp, float4 *rec, cudaStream_t st,
+                              const ChainSizes *dsz);
 void launch_project_bwd(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const uint32_t *count,
                         const BlendParams &bp, const float *g2d, float *g_mean, float *g_scale,
                         float *g_log_scale, float *g_quat, float *g_logit, float *g_sh, cudaStream_t st);
@@ -157,9 +169,10 @@ void launch_blend_fwd(const ViewDesc *views, int n_views, int total_tiles, const
                       const uint32_t *tile_cells, const float4 *rec, const BlendParams &bp, float *out_rgb,
                       float *out_rgb2, float *out_D, int *out_nd, int K_all, cudaStream_t st,
                       const ChainSizes *dsz = nullptr, uint32_t *work = nullptr);
+// g_v_entry (nullable): dL/dv_n accumulated per (view, cell) entry [cell_base + cell].
 void launch_blend_bwd(const ViewDesc *views, int n_views, int total_tiles, int K, const uint2 *ranges,
                       const uint32_t *tile_cells, const float4 *rec, const BlendParams &bp, const float *rgb,
-                      const float *D, const int *nd, const float *dL_drgb, float *g2d, float *g_cell_v,
+                      const float *D, const int *nd, const float *dL_drgb, float *g2d, float *g_v_entry,
                       cudaStream_t st);
 
 void launch_count_pairs(const ViewDesc *views, int n_views, int total_tiles, const uint2 *ranges,

@@ -15,64 +15,13 @@
 // and writes one 48-byte record per view, so a batch of views costs one pass
 // over the 236 B/Gaussian of parameters.
 #include "internal.cuh"
+#include "sh.cuh"
 
 namespace dgs {
 
-// Real spherical harmonics without the Condon-Shortley phase, index l^2+l+m;
-// each constant is the normalisation of Y_lm (1/(2 sqrt(pi)), sqrt(3/(4 pi)), ...).
-constexpr float SH_C0 = 0.28209479177387814f;
-constexpr float SH_C1 = 0.4886025119029199f;
-constexpr float SH_C2a = 1.0925484305920792f;   // (1/2) sqrt(15/pi)
-constexpr float SH_C2b = 0.31539156525252005f;  // (1/4) sqrt(5/pi)
-constexpr float SH_C2c = 0.5462742152960396f;   // (1/4) sqrt(15/pi)
-constexpr float SH_C3a = 0.5900435899266435f;   // (1/4) sqrt(35/(2 pi))
-constexpr float SH_C3b = 2.890611442640554f;    // (1/2) sqrt(105/pi)
-constexpr float SH_C3c = 0.4570457994644658f;   // (1/4) sqrt(21/(2 pi))
-constexpr float SH_C3d = 0.3731763325901154f;   // (1/4) sqrt(7/pi)
-constexpr float SH_C3e = 1.445305721320277f;    // (1/4) sqrt(105/pi)
 constexpr float KAPPA = 0.8493218002880191f;  // sqrt(log2(e) / 2), log2(e) = 1/ln 2
 
-__device__ __forceinline__ void sh_eval(float x, float y, float z, int deg, float Y[16]) {
-#pragma unroll
-    for (int i = 0; i < 16; ++i) Y[i] = 0.f;
-    Y[0] = SH_C0;
-    if (deg < 1) return;
-    Y[1] = SH_C1 * y; Y[2] = SH_C1 * z; Y[3] = SH_C1 * x;
-    if (deg < 2) return;
-    const float xx = x * x, yy = y * y, zz = z * z;
-    Y[4] = SH_C2a * x * y; Y[5] = SH_C2a * y * z; Y[6] = SH_C2b * (3.0f * zz - 1.0f);
-    Y[7] = SH_C2a * x * z; Y[8] = SH_C2c * (xx - yy);
-    if (deg < 3) return;
-    Y[9] = SH_C3a * y * (3.0f * xx - yy); Y[10] = SH_C3b * x * y * z;
-    Y[11] = SH_C3c * y * (5.0f * zz - 1.0f); Y[12] = SH_C3d * z * (5.0f * zz - 3.0f);
-    Y[13] = SH_C3c * x * (5.0f * zz - 1.0f); Y[14] = SH_C3e * z * (xx - yy);
-    Y[15] = SH_C3a * x * (xx - 3.0f * yy);
-}
 
-// Partial derivatives of the formulas above in x, y, z (treated as free).
-__device__ __forceinline__ void sh_grad(float x, float y, float z, int deg, float dX[16], float dY[16], float dZ[16]) {
-#pragma unroll
-    for (int i = 0; i < 16; ++i) dX[i] = dY[i] = dZ[i] = 0.f;
-    if (deg < 1) return;
-    dX[1] = 0.f; dY[1] = SH_C1; dZ[1] = 0.f;
-    dX[2] = 0.f; dY[2] = 0.f; dZ[2] = SH_C1;
-    dX[3] = SH_C1; dY[3] = 0.f; dZ[3] = 0.f;
-    if (deg < 2) return;
-    dX[4] = SH_C2a * y; dY[4] = SH_C2a * x; dZ[4] = 0.f;
-    dX[5] = 0.f; dY[5] = SH_C2a * z; dZ[5] = SH_C2a * y;
-    dX[6] = 0.f; dY[6] = 0.f; dZ[6] = SH_C2b * 6.0f * z;
-    dX[7] = SH_C2a * z; dY[7] = 0.f; dZ[7] = SH_C2a * x;
-    dX[8] = SH_C2c * 2.0f * x; dY[8] = -SH_C2c * 2.0f * y; dZ[8] = 0.f;
-    if (deg < 3) return;
-    const float xx = x * x, yy = y * y, zz = z * z;
-    dX[9] = SH_C3a * 6.0f * x * y; dY[9] = SH_C3a * 3.0f * (xx - yy); dZ[9] = 0.f;
-    dX[10] = SH_C3b * y * z; dY[10] = SH_C3b * x * z; dZ[10] = SH_C3b * x * y;
-    dX[11] = 0.f; dY[11] = SH_C3c * (5.0f * zz - 1.0f); dZ[11] = SH_C3c * 10.0f * y * z;
-    dX[12] = 0.f; dY[12] = 0.f; dZ[12] = SH_C3d * (15.0f * zz - 3.0f);
-    dX[13] = SH_C3c * (5.0f * zz - 1.0f); dY[13] = 0.f; dZ[13] = SH_C3c * 10.0f * x * z;
-    dX[14] = SH_C3e * 2.0f * x * z; dY[14] = -SH_C3e * 2.0f * y * z; dZ[14] = SH_C3e * (xx - yy);
-    dX[15] = SH_C3a * 3.0f * (xx - yy); dY[15] = -SH_C3a * 6.0f * x * y; dZ[15] = 0.f;
-}
 
 struct GaussIn {
     float mean[3], scale[3], quat[4], logit;
@@ -222,8 +171,8 @@ __device__ __forceinline__ void load_sh(const SceneDev &sc, long long g, float (
 // view of that scene in which its cell survived culling.
 __device__ __forceinline__ void project_scene(const ViewDesc *__restrict__ views, int n_views, int slot,
                                               const SceneDev &sc, const uint32_t *__restrict__ count,
-                                              const BlendParams &bp, float4 *__restrict__ rec,
-                                              float *__restrict__ g2d_zero) {
+                                              const float *__restrict__ vview, const BlendParams &bp,
+                                              float4 *__restrict__ rec, float *__restrict__ g2d_zero) {
     const long long G = sc.G, N = sc.N;
     const int K = sc.K;
     for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < G; g += (long long)gridDim.x * blockDim.x) {
@@ -236,13 +185,12 @@ __device__ __forceinline__ void project_scene(const ViewDesc *__restrict__ views
         float k[16][3];
         load_sh(sc, g, k);
         const float opac = 1.0f / (1.0f + expf(-p.logit));
-        const float cv = sc.cell[10 * N + cell];
         for (int v = 0; v < n_views; ++v) {
             const ViewDesc &Vw = views[v];
             if (Vw.scene_slot != slot || count[Vw.cell_base + cell] == 0u) continue;
             ProjCore c;
             float4 r0, r1, r2;
-            gauss_record(Vw, p, k, sc.sh_degree, opac, cv, bp, c, r0, r1, r2);
+            gauss_record(Vw, p, k, sc.sh_degree, opac, vview[Vw.cell_base + cell], bp, c, r0, r1, r2);
             float4 *o = rec + (Vw.rec_base + g) * kRecF4;
             o[0] = r0; o[1] = r1; o[2] = r2;
             if (g2d_zero) {
@@ -313,21 +261,56 @@ __global__ void __launch_bounds__(128) k_gauss_bin(const ViewDesc *__restrict__ 
 }
 
 __global__ void __launch_bounds__(128) k_project_fwd(const ViewDesc *__restrict__ views, int n_views, int slot,
-                                                     SceneDev sc, const uint32_t *__restrict__ count, BlendParams bp,
+                                                     SceneDev sc, const uint32_t *__restrict__ count,
+                                                     const float *__restrict__ vview, BlendParams bp,
                                                      float4 *__restrict__ rec, float *__restrict__ g2d_zero) {
-    project_scene(views, n_views, slot, sc, count, bp, rec, g2d_zero);
+    project_scene(views, n_views, slot, sc, count, vview, bp, rec, g2d_zero);
 }
 
 // Every scene of a device scene table in one launch (sizes read at run time).
 __global__ void __launch_bounds__(128) k_project_fwd_table(const ViewDesc *__restrict__ views,
                                                            const SceneDev *__restrict__ scenes,
-                                                           const uint32_t *__restrict__ count, BlendParams bp,
+                                                           const uint32_t *__restrict__ count,
+                                                           const float *__restrict__ vview, BlendParams bp,
                                                            float4 *__restrict__ rec,
                                                            const ChainSizes *__restrict__ dsz) {
     const int n_views = dsz->n_views, n_scenes = dsz->n_scenes;
     for (int s = 0; s < n_scenes; ++s) {
         const SceneDev sc = scenes[s];
-        project_scene(views, n_views, s, sc, count, bp, rec, nullptr);
+        project_scene(views, n_views, s, sc, count, vview, bp, rec, nullptr);
+    }
+}
+
+// One thread per cell: sums the views' dL/dv_n and chains it to the SH
+// coefficients of a view-dependent v_n (d, Y and the clamp recomputed as in
+// the cell projection).
+__global__ void k_cell_v_grad(const ViewDesc *__restrict__ views, int n_views, SceneDev sc,
+                              const float *__restrict__ gv, float *__restrict__ g_cell_v, float *__restrict__ g_vsh) {
+    const long long N = sc.N;
+    const int Cv = sc.vsh ? (sc.v_sh_degree + 1) * (sc.v_sh_degree + 1) : 0;
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
+        float tot = 0.f, acc[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) acc[c] = 0.f;
+        for (int v = 0; v < n_views; ++v) {
+            const ViewDesc &Vw = views[v];
+            const float g = gv[Vw.cell_base + n];
+            tot += g;
+            if (Cv == 0 || g == 0.f) continue;
+            float d0 = sc.cell[n] - Vw.eye[0], d1 = sc.cell[N + n] - Vw.eye[1], d2 = sc.cell[2 * N + n] - Vw.eye[2];
+            const float il = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+            d0 *= il; d1 *= il; d2 *= il;
+            float Y[16];
+            sh_eval(d0, d1, d2, sc.v_sh_degree, Y);
+            float raw = 0.f;
+            for (int c = 0; c < Cv; ++c) raw += sc.vsh[c * N + n] * Y[c];
+            if (!(raw > 0.f && raw < 1.f)) continue;  // clamped: no gradient
+#pragma unroll
+            for (int c = 0; c < 16; ++c) acc[c] += g * Y[c];
+        }
+        if (g_cell_v) g_cell_v[n] = tot;
+        if (g_vsh)
+            for (int c = 0; c < Cv; ++c) g_vsh[n * Cv + c] = acc[c];
     }
 }
 
@@ -339,9 +322,15 @@ static int grid_for(long long n, int threads) {
 }
 
 void launch_project_fwd(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const uint32_t *count,
-                        const BlendParams &bp, float4 *rec, float *g2d_zero, cudaStream_t st) {
+                        const float *vview, const BlendParams &bp, float4 *rec, float *g2d_zero, cudaStream_t st) {
     if (sc.G == 0 || n_views == 0) return;
-    k_project_fwd<<<grid_for(sc.G, 128), 128, 0, st>>>(views, n_views, slot, sc, count, bp, rec, g2d_zero);
+    k_project_fwd<<<grid_for(sc.G, 128), 128, 0, st>>>(views, n_views, slot, sc, count, vview, bp, rec, g2d_zero);
+}
+
+void launch_cell_v_grad(const ViewDesc *views, int n_views, const SceneDev &sc, const float *gv, float *g_cell_v,
+                        float *g_vsh, cudaStream_t st) {
+    if (sc.N == 0 || (!g_cell_v && !g_vsh)) return;
+    k_cell_v_grad<<<grid_for(sc.N, 128), 128, 0, st>>>(views, n_views, sc, gv, g_cell_v, g_vsh);
 }
 
 void launch_gauss_bin(const ViewDesc *views, int n_views, const SceneDev &sc, const BlendParams &bp, bool wsr,
@@ -353,9 +342,10 @@ void launch_gauss_bin(const ViewDesc *views, int n_views, const SceneDev &sc, co
 }
 
 void launch_project_fwd_table(const ViewDesc *views, const SceneDev *scenes, long long G_cap, const uint32_t *count,
-                              const BlendParams &bp, float4 *rec, cudaStream_t st, const ChainSizes *dsz) {
+                              const float *vview, const BlendParams &bp, float4 *rec, cudaStream_t st,
+                              const ChainSizes *dsz) {
     if (G_cap == 0) return;
-    k_project_fwd_table<<<grid_for(G_cap, 128), 128, 0, st>>>(views, scenes, count, bp, rec, dsz);
+    k_project_fwd_table<<<grid_for(G_cap, 128), 128, 0, st>>>(views, scenes, count, vview, bp, rec, dsz);
 }
 
 // a*b - c*d to about one rounding (Kahan's compensated form)

@@ -45,7 +45,8 @@ struct DevBuf {
 struct Scene {
     int64_t N = 0, G = 0;
     int K = 1, deg = 0, C = 1;
-    DevBuf cell, gauss, sh;
+    int vdeg = -1, Cv = 0;  // SH degree / coefficients of a view-dependent v_n (-1: scalar v_n)
+    DevBuf cell, gauss, sh, vsh;
     SceneDev dev() const;
 };
 
@@ -68,6 +69,7 @@ struct Workspace {
     DevBuf Dpix, ndpix, rgb;                                 // per pixel
     DevBuf gstage;                                           // backward staging
     DevBuf sort_k, sort_v, sort_hist, sort_status, sort_ctr, small, scan;
+    DevBuf vview, gvview;         // per (view, cell): v_n as rendered, dL/dv_n
     DevBuf sizes;                 // ChainSizes of a captured chain
     uint32_t *h_small = nullptr;  // pinned mirror of `small`
     ChainSizes *h_sizes = nullptr;

@@ -108,7 +108,7 @@ dgs_status plan_batch(dgs_ctx *ctx, const std::vector<PendingReq> &reqs, BatchPl
 // Device bytes of a slot workspace with capacities c.
 long long slot_bytes(const ChainCaps &c) {
     const long long n = std::max(c.E, c.L);
-    return (long long)sizeof(ViewDesc) * c.V + (long long)sizeof(SceneDev) * c.S + 32 * c.E + 4 * c.E / 1024 +
+    return (long long)sizeof(ViewDesc) * c.V + (long long)sizeof(SceneDev) * c.S + 36 * c.E + 4 * c.E / 1024 +
            8 * n + 1024 * (n / 4096 + 1) + 8 * c.L + 8 * c.T + 48 * c.R + 20 * c.P;
 }
 
@@ -173,7 +173,7 @@ dgs_status fit_slot(dgs_ctx *ctx, ServeState &S, GraphSlot &g, const BatchPlan &
         (s = ws.scan.ensure(4 * scan_scratch_words(c.E))) || (s = ensure_sort_scratch(ws, std::max(c.E, c.L))) ||
         (s = ws.tkey.ensure(4 * c.L)) || (s = ws.tval.ensure(4 * c.L)) || (s = ws.ranges.ensure(8 * c.T)) ||
         (s = ws.rec.ensure(sizeof(float4) * kRecF4 * c.R)) || (s = ws.Dpix.ensure(4 * c.P)) ||
-        (s = ws.ndpix.ensure(4 * c.P)) || (s = ws.rgb.ensure(12 * c.P)))
+        (s = ws.ndpix.ensure(4 * c.P)) || (s = ws.rgb.ensure(12 * c.P)) || (s = ws.vview.ensure(4 * c.E)))
         return s;
     if (ws.h_views_cap < (size_t)c.V) {
         if (ws.h_views) cudaFreeHost(ws.h_views);
@@ -217,8 +217,8 @@ dgs_status record_chain(dgs_ctx *ctx, Workspace &ws, const ChainCaps &c, const B
     CKR(cudaMemcpyAsync(ws.sizes.p, ws.h_sizes, sizeof(ChainSizes), cudaMemcpyHostToDevice, st));
     CKR(cudaMemsetAsync(small, 0, 256, st));
     launch_cell_project(dv, c.V, (const SceneDev *)ws.scenes.p, c.E, (uint32_t *)ws.zkey.p, (uint32_t *)ws.zval.p,
-                        (short4 *)ws.rect.p, (float *)ws.depth.p, (uint32_t *)ws.count.p, small + kSmallVisible, st,
-                        dsz);
+                        (short4 *)ws.rect.p, (float *)ws.depth.p, (uint32_t *)ws.count.p, small + kSmallVisible,
+                        (float *)ws.vview.p, st, dsz);
     radix_sort_pairs((uint32_t *)ws.zkey.p, (uint32_t *)ws.zval.p, c.E, 32, sc, st, d_E);
     launch_gather_counts((const uint32_t *)ws.zval.p, (const uint32_t *)ws.count.p, c.E, (uint32_t *)ws.cnt_sorted.p,
                          st, d_E);
@@ -232,8 +232,8 @@ dgs_status record_chain(dgs_ctx *ctx, Workspace &ws, const ChainCaps &c, const B
     radix_sort_pairs((uint32_t *)ws.tkey.p, (uint32_t *)ws.tval.p, c.L, bits, sc, st, d_L);
     CKR(cudaMemsetAsync(ws.ranges.p, 0, 8 * (size_t)c.T, st));
     launch_tile_ranges((const uint32_t *)ws.tkey.p, c.L, (uint2 *)ws.ranges.p, st, d_L);
-    launch_project_fwd_table(dv, (const SceneDev *)ws.scenes.p, c.G, (const uint32_t *)ws.count.p, bp,
-                             (float4 *)ws.rec.p, st, dsz);
+    launch_project_fwd_table(dv, (const SceneDev *)ws.scenes.p, c.G, (const uint32_t *)ws.count.p,
+                             (const float *)ws.vview.p, bp, (float4 *)ws.rec.p, st, dsz);
     launch_blend_fwd(dv, c.V, (int)c.T, (const uint2 *)ws.ranges.p, (const uint32_t *)ws.tval.p,
                      (const float4 *)ws.rec.p, bp, (float *)ws.rgb.p, nullptr, (float *)ws.Dpix.p, (int *)ws.ndpix.p,
                      p.K_all, st, dsz, small + kSmallWork);

@@ -62,10 +62,12 @@ class Context:
             pass
 
     # ------------------------------------------------------------ scenes
-    def _desc(self, arrays: dict, N: int, K: int, deg: int, location: int, cell_v=True) -> L.dgs_scene_desc:
+    def _desc(self, arrays: dict, N: int, K: int, deg: int, location: int, v_sh_degree: int = -1) -> L.dgs_scene_desc:
         d = L.dgs_scene_desc()
         d.num_cells, d.K, d.sh_degree, d.location = N, K, deg, location
-        for f in ("cell_center", "cell_axes", "cell_quat", "cell_v", "g_mean", "g_scale", "g_quat", "g_logit", "g_sh"):
+        d.v_sh_degree = v_sh_degree
+        for f in ("cell_center", "cell_axes", "cell_quat", "cell_v", "g_mean", "g_scale", "g_quat", "g_logit", "g_sh",
+                  "cell_v_sh"):
             a = arrays.get(f)
             if a is None:
                 setattr(d, f, None)
@@ -78,12 +80,16 @@ class Context:
         with the same field names plus N, K, sh_degree."""
         if isinstance(scene, dict):
             arrays = {k: v.contiguous() for k, v in scene.items() if isinstance(v, torch.Tensor)}
-            d = self._desc(arrays, scene["N"], scene["K"], scene["sh_degree"], L.DGS_DEVICE)
+            d = self._desc(arrays, scene["N"], scene["K"], scene["sh_degree"], L.DGS_DEVICE,
+                           scene.get("v_sh_degree", -1))
         else:
             arrays = {f: np.ascontiguousarray(getattr(scene, f), dtype=np.float32)
                       for f in ("cell_center", "cell_axes", "cell_quat", "cell_v", "g_mean", "g_scale", "g_quat",
                                 "g_logit", "g_sh")}
-            d = self._desc(arrays, scene.N, scene.K, scene.sh_degree, L.DGS_HOST)
+            vdeg = getattr(scene, "v_sh_degree", -1)
+            if getattr(scene, "cell_v_sh", None) is not None:
+                arrays["cell_v_sh"] = np.ascontiguousarray(scene.cell_v_sh, dtype=np.float32)
+            d = self._desc(arrays, scene.N, scene.K, scene.sh_degree, L.DGS_HOST, vdeg)
         return L.dgs_scene_upload(self.ctx, d)
 
     def update_scene(self, scene_id: int, N: int, K: int, deg: int, **tensors):
@@ -167,7 +173,7 @@ class Context:
         g_log_scale, g_quat, g_logit, g_sh, g_cell_v (any subset)."""
         g = L.dgs_grads()
         g.location = location
-        for f in ("g_mean", "g_scale", "g_log_scale", "g_quat", "g_logit", "g_sh", "g_cell_v"):
+        for f in ("g_mean", "g_scale", "g_log_scale", "g_quat", "g_logit", "g_sh", "g_cell_v", "g_cell_v_sh"):
             a = grads.get(f)
             setattr(g, f, None if a is None else (a.data_ptr() if isinstance(a, torch.Tensor) else a.ctypes.data))
         dl_ptr = dL.data_ptr() if isinstance(dL, torch.Tensor) else dL.ctypes.data
