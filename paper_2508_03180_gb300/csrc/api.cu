@@ -230,46 +230,60 @@ extern "C" const char *dgs_last_error(dgs_ctx *) { return g_last_error.c_str(); 
 
 // ------------------------------------------------------------------ scenes
 
-static dgs_status upload_param(dgs_ctx *ctx, const float *src, int location, int64_t rows, int cols, float *dst_planes,
-                               int64_t plane_stride, cudaStream_t st) {
+// One parameter array (rows x cols, row-major, in `location` memory) into
+// its structure-of-arrays planes.  Host arrays go through `stage` (device,
+// rows x cols floats); the caller synchronises before the host memory or
+// the staging is reused.
+static dgs_status upload_param(const float *src, int location, int64_t rows, int cols, float *dst_planes,
+                               int64_t plane_stride, float *stage, cudaStream_t st) {
     const size_t bytes = sizeof(float) * (size_t)rows * cols;
     if (bytes == 0) return DGS_OK;
     const float *dsrc = src;
     if (location == DGS_HOST) {
-        dgs_status s = ctx->aux.ensure(bytes);
-        if (s) return s;
-        CK(cudaMemcpyAsync(ctx->aux.p, src, bytes, cudaMemcpyHostToDevice, st));
-        dsrc = (const float *)ctx->aux.p;
+        CK(cudaMemcpyAsync(stage, src, bytes, cudaMemcpyHostToDevice, st));
+        dsrc = stage;
     }
     launch_aos_to_soa(dsrc, rows, cols, dst_planes, plane_stride, st);
     CK(cudaGetLastError());
-    if (location == DGS_HOST) CK(cudaStreamSynchronize(st));  // staging buffer is reused by the next parameter
     return DGS_OK;
 }
 
 static dgs_status fill_scene(dgs_ctx *ctx, Scene &sc, const dgs_scene_desc *d, cudaStream_t st, bool cells_too) {
     const int64_t N = sc.N, G = sc.G;
     float *cell = (float *)sc.cell.p, *gs = (float *)sc.gauss.p, *sh = (float *)sc.sh.p;
-    dgs_status s;
+    struct Part { const float *src; int64_t rows; int cols; float *dst; int64_t stride; };
+    std::vector<Part> parts;
     if (cells_too) {
-        if ((s = upload_param(ctx, d->cell_center, d->location, N, 3, cell, N, st))) return s;
-        if ((s = upload_param(ctx, d->cell_axes, d->location, N, 3, cell + 3 * N, N, st))) return s;
-        if ((s = upload_param(ctx, d->cell_quat, d->location, N, 4, cell + 6 * N, N, st))) return s;
+        parts.push_back({d->cell_center, N, 3, cell, N});
+        parts.push_back({d->cell_axes, N, 3, cell + 3 * N, N});
+        parts.push_back({d->cell_quat, N, 4, cell + 6 * N, N});
     }
-    if (d->cell_v) {
-        if ((s = upload_param(ctx, d->cell_v, d->location, N, 1, cell + 10 * N, N, st))) return s;
-    } else if (cells_too) {
-        launch_fill_f32(cell + 10 * N, N, 1.0f, st);
+    if (d->cell_v) parts.push_back({d->cell_v, N, 1, cell + 10 * N, N});
+    if (sc.vdeg >= 0 && d->cell_v_sh) parts.push_back({d->cell_v_sh, N, sc.Cv, (float *)sc.vsh.p, N});
+    parts.push_back({d->g_mean, G, 3, gs, G});
+    parts.push_back({d->g_scale, G, 3, gs + 3 * G, G});
+    parts.push_back({d->g_quat, G, 4, gs + 6 * G, G});
+    parts.push_back({d->g_logit, G, 1, gs + 10 * G, G});
+    parts.push_back({d->g_sh, G, 3 * sc.C, sh, G});
+    // host inputs: every array gets its own staging region, one synchronisation at the end
+    float *stage = nullptr;
+    if (d->location == DGS_HOST) {
+        int64_t total = 0;
+        for (auto &p : parts)
+            if (p.src) total += p.rows * p.cols;
+        dgs_status s = ctx->aux.ensure(sizeof(float) * std::max<int64_t>(1, total));
+        if (s) return s;
+        stage = (float *)ctx->aux.p;
     }
-    if (sc.vdeg >= 0 && d->cell_v_sh) {
-        if ((s = upload_param(ctx, d->cell_v_sh, d->location, N, sc.Cv, (float *)sc.vsh.p, N, st))) return s;
+    if (!d->cell_v && cells_too) launch_fill_f32(cell + 10 * N, N, 1.0f, st);
+    for (auto &p : parts) {
+        if (!p.src) continue;
+        dgs_status s = upload_param(p.src, d->location, p.rows, p.cols, p.dst, p.stride, stage, st);
+        if (s) return s;
+        if (stage) stage += p.rows * p.cols;
     }
-    if ((s = upload_param(ctx, d->g_mean, d->location, G, 3, gs, G, st))) return s;
-    if ((s = upload_param(ctx, d->g_scale, d->location, G, 3, gs + 3 * G, G, st))) return s;
-    if ((s = upload_param(ctx, d->g_quat, d->location, G, 4, gs + 6 * G, G, st))) return s;
-    if ((s = upload_param(ctx, d->g_logit, d->location, G, 1, gs + 10 * G, G, st))) return s;
-    if ((s = upload_param(ctx, d->g_sh, d->location, G, 3 * sc.C, sh, G, st))) return s;
     CK(cudaGetLastError());
+    if (d->location == DGS_HOST) CK(cudaStreamSynchronize(st));  // host arrays and staging free again
     return DGS_OK;
 }
 

@@ -5,8 +5,28 @@
 namespace dgs {
 
 // src [rows][cols] -> dst plane j at dst + j * dst_stride (column j of src).
-__global__ void k_aos_to_soa(const float *__restrict__ src, int64_t rows, int cols, float *__restrict__ dst,
-                             int64_t dst_stride) {
+// A block moves 32 rows at a time through shared memory: the rows are read
+// as one contiguous run and every plane receives 32 consecutive floats.
+constexpr int TR_ROWS = 32, TR_MAXC = 64;
+__global__ void __launch_bounds__(256) k_aos_to_soa(const float *__restrict__ src, int64_t rows, int cols,
+                                                    float *__restrict__ dst, int64_t dst_stride) {
+    __shared__ float t[TR_ROWS][TR_MAXC + 1];
+    for (int64_t r0 = blockIdx.x * (int64_t)TR_ROWS; r0 < rows; r0 += (int64_t)gridDim.x * TR_ROWS) {
+        const int nr = (int)min((int64_t)TR_ROWS, rows - r0);
+        const float *s = src + r0 * cols;
+        for (int i = threadIdx.x; i < nr * cols; i += blockDim.x) t[i / cols][i % cols] = s[i];
+        __syncthreads();
+        for (int i = threadIdx.x; i < cols * TR_ROWS; i += blockDim.x) {
+            const int c = i / TR_ROWS, r = i % TR_ROWS;
+            if (r < nr) dst[c * dst_stride + r0 + r] = t[r][c];
+        }
+        __syncthreads();
+    }
+}
+
+// Fallback for more than TR_MAXC columns: one element per thread.
+__global__ void k_aos_to_soa_wide(const float *__restrict__ src, int64_t rows, int cols, float *__restrict__ dst,
+                                  int64_t dst_stride) {
     const int64_t total = rows * cols;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = i / cols;
@@ -38,7 +58,13 @@ static int grid_for(int64_t n) {
 
 void launch_aos_to_soa(const float *src, int64_t rows, int cols, float *dst, int64_t dst_stride, cudaStream_t st) {
     if (rows * cols == 0) return;
-    k_aos_to_soa<<<grid_for(rows * cols), 256, 0, st>>>(src, rows, cols, dst, dst_stride);
+    if (cols > TR_MAXC) {
+        k_aos_to_soa_wide<<<grid_for(rows * cols), 256, 0, st>>>(src, rows, cols, dst, dst_stride);
+        return;
+    }
+    int64_t b = (rows + TR_ROWS - 1) / TR_ROWS;
+    if (b > 152 * 8) b = 152 * 8;
+    k_aos_to_soa<<<(int)b, 256, 0, st>>>(src, rows, cols, dst, dst_stride);
 }
 
 void launch_soa_to_aos(const float *src, int64_t rows, int cols, int64_t src_stride, float *dst, cudaStream_t st) {

@@ -156,3 +156,27 @@ def test_requests_arriving_during_a_render_join_later_batches(scenes):
     starts = sorted({round(r.t_start_ms, 6) for r in rs})
     assert len(starts) >= 2  # more than one batch ran
     c.close()
+
+
+@pytest.mark.parametrize("graphs", [True, False])
+def test_mixed_cells_per_gaussian_and_view_dependent_v(graphs):
+    # K = 8 and K = 10 scenes in one batch take the blend's generic-K path;
+    # the third scene has a view-dependent v_n
+    c = _ctx()
+    scs = [synth.scene_small(seed=5, n_cells=600),
+           synth.make_scene(500, 10, synth._box(-1.0, 1.0), 0.02, 0.1, 1, seed=6),
+           synth.with_view_dependent_v(synth.scene_small(seed=7, n_cells=700), degree=2, seed=1)]
+    sids = [c.upload_scene(s) for s in scs]
+    cams = [synth.sphere_cameras(1, 3.0, W, H, seed0=20 + i)[0] for i, (W, H) in
+            enumerate([(64, 48), (80, 60), (50, 70), (96, 40), (64, 64), (40, 40)])]
+    ref = [c.render(sids[i % 3], [cam])[0].clone() for i, cam in enumerate(cams)]
+    torch.cuda.synchronize()
+    c.serve_start(max_batch=8, graphs=graphs)
+    outs = [torch.zeros_like(r) for r in ref]
+    ts = [c.submit(sids[i % 3], cam, outs[i]) for i, cam in enumerate(cams)]
+    rs = [c.poll(t, -1) for t in ts]
+    c.serve_stop()
+    assert all(r.status == 0 for r in rs)
+    for o, r in zip(outs, ref):
+        assert torch.equal(o, r)
+    c.close()
