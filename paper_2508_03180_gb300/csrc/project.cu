@@ -173,7 +173,7 @@ __device__ __forceinline__ void project_scene(const ViewDesc *__restrict__ views
                                               const SceneDev &sc, const uint32_t *__restrict__ count,
                                               const float *__restrict__ vview, const BlendParams &bp,
                                               float4 *__restrict__ rec, float *__restrict__ g2d_zero) {
-    const long long G = sc.G, N = sc.N;
+    const long long G = sc.G;
     const int K = sc.K;
     for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < G; g += (long long)gridDim.x * blockDim.x) {
         const long long cell = g / K;
@@ -412,75 +412,36 @@ __device__ __forceinline__ void adjoint_U(const float u[3], const float w[3], fl
 // q = a dx^2 + 2 b dx dy + c dy^2, dL/d(opacity), dL/d(rgb).  Chain rule
 // through the forward above (clamp masks as in the forward), summed over
 // views; outputs are written, not accumulated.
-__global__ void __launch_bounds__(128) k_project_bwd(const ViewDesc *__restrict__ views, int n_views, int slot,
+__global__ void __launch_bounds__(128) k_project_bwd_geom(const ViewDesc *__restrict__ views, int n_views, int slot,
                                                      SceneDev sc, const uint32_t *__restrict__ count, BlendParams bp,
                                                      const float *__restrict__ g2d, float *__restrict__ g_mean,
                                                      float *__restrict__ g_scale,
                                                      float *__restrict__ g_log_scale, float *__restrict__ g_quat,
-                                                     float *__restrict__ g_logit, float *__restrict__ g_sh) {
+                                                     float *__restrict__ g_logit) {
     const long long G = sc.G;
-    const int K = sc.K, C = (sc.sh_degree + 1) * (sc.sh_degree + 1);
+    const int K = sc.K;
     for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < G; g += (long long)gridDim.x * blockDim.x) {
         const long long cell = g / K;
         float gm[3] = {0.f, 0.f, 0.f}, gs[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f};
         float gq[4] = {0.f, 0.f, 0.f, 0.f}, glog = 0.f;
-        float gk[16][3];
-#pragma unroll
-        for (int c = 0; c < 16; ++c) gk[c][0] = gk[c][1] = gk[c][2] = 0.f;
         bool any = false;
         for (int v = 0; v < n_views; ++v)
             any |= views[v].scene_slot == slot && count[views[v].cell_base + cell] != 0u;
         if (any) {
             const GaussIn p = load_gauss(sc.gauss, G, g);
-            float k[16][3];
-#pragma unroll
-            for (int c = 0; c < 16; ++c)
-#pragma unroll
-                for (int ch = 0; ch < 3; ++ch) k[c][ch] = c < C ? sc.sh[(c * 3 + ch) * G + g] : 0.f;
             const float opac = 1.0f / (1.0f + expf(-p.logit));
             for (int v = 0; v < n_views; ++v) {
                 const ViewDesc &Vw = views[v];
                 if (Vw.scene_slot != slot || count[Vw.cell_base + cell] == 0u) continue;
                 const float4 *gr = reinterpret_cast<const float4 *>(g2d + (Vw.rec_base + g) * kGradF);
-                const float4 a0 = gr[0], a1 = gr[1], a2 = gr[2];
+                const float4 a0 = gr[0], a1 = gr[1];
                 const float gmx = a0.x, gmy = a0.y, gca = a0.z, gcb = a0.w, gcc = a1.x, gop = a1.y;
-                const float grgb[3] = {a1.z, a1.w, a2.x};
-                if (gmx == 0.f && gmy == 0.f && gca == 0.f && gcb == 0.f && gcc == 0.f && gop == 0.f &&
-                    grgb[0] == 0.f && grgb[1] == 0.f && grgb[2] == 0.f)
-                    continue;
+                if (gmx == 0.f && gmy == 0.f && gca == 0.f && gcb == 0.f && gcc == 0.f && gop == 0.f) continue;
                 ProjCore c;
                 proj_core(Vw, p, bp.dilation, c);
                 if (!c.valid) continue;
                 // opacity
                 glog += gop * opac * (1.0f - opac);
-                // colour
-                {
-                    float u0 = p.mean[0] - Vw.eye[0], u1 = p.mean[1] - Vw.eye[1], u2 = p.mean[2] - Vw.eye[2];
-                    const float il = rsqrtf(u0 * u0 + u1 * u1 + u2 * u2);
-                    const float d0 = u0 * il, d1 = u1 * il, d2 = u2 * il;
-                    float Y[16], dX[16], dY[16], dZ[16];
-                    sh_eval(d0, d1, d2, sc.sh_degree, Y);
-                    sh_grad(d0, d1, d2, sc.sh_degree, dX, dY, dZ);
-                    float gd[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-                    for (int ch = 0; ch < 3; ++ch) {
-                        float s = 0.5f;
-#pragma unroll
-                        for (int ci = 0; ci < 16; ++ci) s += k[ci][ch] * Y[ci];
-                        if (s <= 0.0f) continue;  // clamped at 0
-                        const float gc = grgb[ch];
-#pragma unroll
-                        for (int ci = 0; ci < 16; ++ci) {
-                            gk[ci][ch] += gc * Y[ci];
-                            const float w = gc * k[ci][ch];
-                            gd[0] += w * dX[ci]; gd[1] += w * dY[ci]; gd[2] += w * dZ[ci];
-                        }
-                    }
-                    const float dd = gd[0] * d0 + gd[1] * d1 + gd[2] * d2;
-                    gm[0] += (gd[0] - dd * d0) * il;
-                    gm[1] += (gd[1] - dd * d1) * il;
-                    gm[2] += (gd[2] - dd * d2) * il;
-                }
                 // conic -> Sigma' -> U:  dL/dU = 2 H U with H = -Q G_Q Q,
                 // G_Q = [[ga, gb/2], [gb/2, gc]], Q = Sigma'^-1, Sigma' = U U^T + d I.
                 // Needle-like Gaussians make U nearly rank one, so Q is nearly
@@ -567,13 +528,82 @@ __global__ void __launch_bounds__(128) k_project_bwd(const ViewDesc *__restrict_
             for (int i = 0; i < 4; ++i) g_quat[4 * g + i] = gq[i];
         }
         if (g_logit) g_logit[g] = glog;
-        if (g_sh) {
+    }
+}
+
+// Colour adjoint: colour_ch = max(0, 0.5 + sum_c k_c,ch Y_c(d)),
+// d = (mu - eye)/|mu - eye|: dL/dk and the view direction's share of
+// dL/dmu (added to g_mean, which the geometry kernel wrote).  One channel at
+// a time keeps 16 coefficients and 16 accumulators live.  Gaussians that no
+// view rendered (and invalid ones) have zero screen-space gradients.
+__global__ void __launch_bounds__(128) k_project_bwd_colour(const ViewDesc *__restrict__ views, int n_views, int slot,
+                                                            SceneDev sc, const uint32_t *__restrict__ count,
+                                                            const float *__restrict__ g2d, float *__restrict__ g_mean,
+                                                            float *__restrict__ g_sh) {
+    __shared__ float s_out[128 * 48];  // the block's g_sh rows, written back coalesced
+    const long long G = sc.G;
+    const int K = sc.K, C = (sc.sh_degree + 1) * (sc.sh_degree + 1), row = 3 * C;
+    for (long long g0 = (long long)blockIdx.x * blockDim.x; g0 < G; g0 += (long long)gridDim.x * blockDim.x) {
+        const long long g = g0 + threadIdx.x;
+        const bool live = g < G;
+        const long long cell = live ? g / K : 0;
+        bool any = false;
+        for (int v = 0; live && v < n_views; ++v)
+            any |= views[v].scene_slot == slot && count[views[v].cell_base + cell] != 0u;
+        float gdm[3] = {0.f, 0.f, 0.f};
+        const float m0 = any ? sc.gauss[g] : 0.f, m1 = any ? sc.gauss[G + g] : 0.f, m2 = any ? sc.gauss[2 * G + g] : 0.f;
+#pragma unroll 1
+        for (int ch = 0; ch < 3; ++ch) {
+            float k[16], gk[16];
 #pragma unroll
-            for (int ci = 0; ci < 16; ++ci)
-                if (ci < C) {
+            for (int c = 0; c < 16; ++c) {
+                k[c] = any && c < C ? sc.sh[(c * 3 + ch) * G + g] : 0.f;
+                gk[c] = 0.f;
+            }
+            for (int v = 0; any && v < n_views; ++v) {
+                const ViewDesc &Vw = views[v];
+                if (Vw.scene_slot != slot || count[Vw.cell_base + cell] == 0u) continue;
+                const float gc = g2d[(Vw.rec_base + g) * kGradF + 6 + ch];
+                if (gc == 0.f) continue;
+                float u0 = m0 - Vw.eye[0], u1 = m1 - Vw.eye[1], u2 = m2 - Vw.eye[2];
+                const float il = rsqrtf(u0 * u0 + u1 * u1 + u2 * u2);
+                const float d0 = u0 * il, d1 = u1 * il, d2 = u2 * il;
+                float Y[16];
+                sh_eval(d0, d1, d2, sc.sh_degree, Y);
+                float sv = 0.5f;
 #pragma unroll
-                    for (int ch = 0; ch < 3; ++ch) g_sh[(g * C + ci) * 3 + ch] = gk[ci][ch];
+                for (int c = 0; c < 16; ++c) sv += k[c] * Y[c];
+                if (sv <= 0.0f) continue;  // clamped at 0
+                float w[16];
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    gk[c] += gc * Y[c];
+                    w[c] = gc * k[c];
                 }
+                if (g_mean) {
+                    float gd[3] = {0.f, 0.f, 0.f};
+                    sh_grad_dot(d0, d1, d2, sc.sh_degree, w, gd);
+                    const float dd = gd[0] * d0 + gd[1] * d1 + gd[2] * d2;
+                    gdm[0] += (gd[0] - dd * d0) * il;
+                    gdm[1] += (gd[1] - dd * d1) * il;
+                    gdm[2] += (gd[2] - dd * d2) * il;
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 16; ++c)
+                if (c < C) s_out[threadIdx.x * row + c * 3 + ch] = gk[c];
+        }
+        __syncthreads();
+        if (g_sh) {
+            const long long nb = min((long long)blockDim.x, G - g0) * row;
+            float *dst = g_sh + g0 * row;
+            for (int i = threadIdx.x; i < nb; i += blockDim.x) dst[i] = s_out[i];
+        }
+        __syncthreads();
+        if (live && g_mean) {
+            g_mean[3 * g] += gdm[0];
+            g_mean[3 * g + 1] += gdm[1];
+            g_mean[3 * g + 2] += gdm[2];
         }
     }
 }
@@ -582,8 +612,10 @@ void launch_project_bwd(const ViewDesc *views, int n_views, int slot, const Scen
                         const BlendParams &bp, const float *g2d, float *g_mean, float *g_scale, float *g_log_scale,
                         float *g_quat, float *g_logit, float *g_sh, cudaStream_t st) {
     if (sc.G == 0) return;
-    k_project_bwd<<<grid_for(sc.G, 128), 128, 0, st>>>(views, n_views, slot, sc, count, bp, g2d, g_mean, g_scale,
-                                                       g_log_scale, g_quat, g_logit, g_sh);
+    k_project_bwd_geom<<<grid_for(sc.G, 128), 128, 0, st>>>(views, n_views, slot, sc, count, bp, g2d, g_mean,
+                                                            g_scale, g_log_scale, g_quat, g_logit);
+    if (g_mean || g_sh)
+        k_project_bwd_colour<<<grid_for(sc.G, 128), 128, 0, st>>>(views, n_views, slot, sc, count, g2d, g_mean, g_sh);
 }
 
 }  // namespace dgs

@@ -59,4 +59,24 @@ __device__ __forceinline__ void sh_grad(float x, float y, float z, int deg, floa
     dX[15] = SH_C3a * 3.0f * (xx - yy); dY[15] = -SH_C3a * 6.0f * x * y; dZ[15] = 0.f;
 }
 
+// g += sum_c w[c] grad Y_c(x, y, z) (the formulas of sh_grad, without the arrays).
+__device__ __forceinline__ void sh_grad_dot(float x, float y, float z, int deg, const float w[16], float g[3]) {
+    if (deg < 1) return;
+    g[1] += SH_C1 * w[1];
+    g[2] += SH_C1 * w[2];
+    g[0] += SH_C1 * w[3];
+    if (deg < 2) return;
+    g[0] += SH_C2a * (y * w[4] + z * w[7]) + SH_C2c * 2.0f * x * w[8];
+    g[1] += SH_C2a * (x * w[4] + z * w[5]) - SH_C2c * 2.0f * y * w[8];
+    g[2] += SH_C2a * (y * w[5] + x * w[7]) + SH_C2b * 6.0f * z * w[6];
+    if (deg < 3) return;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    g[0] += SH_C3a * 6.0f * x * y * w[9] + SH_C3b * y * z * w[10] + SH_C3c * (5.0f * zz - 1.0f) * w[13] +
+            SH_C3e * 2.0f * x * z * w[14] + SH_C3a * 3.0f * (xx - yy) * w[15];
+    g[1] += SH_C3a * 3.0f * (xx - yy) * w[9] + SH_C3b * x * z * w[10] + SH_C3c * (5.0f * zz - 1.0f) * w[11] -
+            SH_C3e * 2.0f * y * z * w[14] - SH_C3a * 6.0f * x * y * w[15];
+    g[2] += SH_C3b * x * y * w[10] + SH_C3c * 10.0f * y * z * w[11] + SH_C3d * (15.0f * zz - 3.0f) * w[12] +
+            SH_C3c * 10.0f * x * z * w[13] + SH_C3e * (xx - yy) * w[14];
+}
+
 }  // namespace dgs
