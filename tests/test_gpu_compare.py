@@ -153,3 +153,24 @@ def test_large_scale_band(rctx, mode):
             assert float(np.abs(got - r["C"][:, y0:y1]).max()) <= IMG_TOL
     finally:
         rctx.release_scene(sid)
+
+
+@pytest.mark.parametrize("mode", ["alpha", "wsr"])
+def test_empty_and_culled_scenes_render_background(rctx, mode):
+    from paper_2508_03180_gb300.renderer import Context
+    bg = (0.25, 0.5, 0.75)
+    c = Context(bg=bg)
+    try:
+        empty = c.upload_scene(synth.scene_small(n_cells=0))
+        behind = synth.scene_small(seed=8, n_cells=200)
+        behind.g_mean[:, 1] -= 10.0  # every Gaussian behind the camera at (0, -3, 0)
+        culled = c.upload_scene(behind)
+        cams = [synth.small_camera(40, 24), synth.small_camera(1, 1)]
+        for sid in (empty, culled):
+            img, nd, st = c.render_compare(sid, cams, mode, want_ndone=mode == "alpha", stats=True)
+            assert st.sort_length == 0
+            for v in c.split(img, cams):
+                for ch in range(3):
+                    assert torch.all(v[ch] == bg[ch])
+    finally:
+        c.close()

@@ -180,3 +180,23 @@ def test_mixed_cells_per_gaussian_and_view_dependent_v(graphs):
     for o, r in zip(outs, ref):
         assert torch.equal(o, r)
     c.close()
+
+
+def test_empty_scene_in_a_served_batch():
+    from paper_2508_03180_gb300.renderer import Context
+    bg = (0.1, 0.2, 0.3)
+    c = Context(bg=bg)
+    sids = [c.upload_scene(synth.scene_small(n_cells=0)), c.upload_scene(synth.scene_small(seed=9, n_cells=300))]
+    cams = [synth.small_camera(48, 32), synth.small_camera(64, 40), synth.small_camera(16, 16)]
+    ref = [c.render(sids[i % 2], [cam])[0].clone() for i, cam in enumerate(cams)]
+    torch.cuda.synchronize()
+    c.serve_start(max_batch=4)
+    outs = [torch.zeros_like(r) for r in ref]
+    rs = [c.poll(c.submit(sids[i % 2], cam, outs[i]), -1) for i, cam in enumerate(cams)]
+    c.serve_stop()
+    assert all(r.status == 0 for r in rs)
+    for o, r in zip(outs, ref):
+        assert torch.equal(o, r)
+    for ch in range(3):
+        assert torch.all(outs[0].view(3, -1)[ch] == bg[ch])
+    c.close()
