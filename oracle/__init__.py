@@ -11,6 +11,8 @@ Pieces:
                 weighted-sum rendering (Eq. 4-6).
   project.py    FP64 projection of Gaussians (EWA, opacity, SH colour) in
                 plain PyTorch CPU ops; autograd gives its chain rule.
+  decode.py     FP64 decode of neural cells into Gaussians (the MLP step
+                before the path).
 
 Parity protocol helpers live here too: `render(..., forced_ndone=...)`
 renders with a given per-pixel processed-cell count and reports how many of
@@ -379,3 +381,30 @@ def render_wsr(scene, cam, tau: float = float("inf"), w_bg: float = 0.0, opt: Op
                  _p(pv["mu2f"]), _p(pv["extf"]), _p(pv["valid"]), _p(w), float(w_bg), _p(opt.blend_opts()),
                  ty0, ty1, _p(C))
     return dict(C=C, L=pv["L"])
+
+
+# --------------------------------------------------------------------------
+# Neural cells
+
+
+def decode_view(scene, cam):
+    """FP64 Gaussians of every cell of a neural scene as seen from `cam`."""
+    from . import decode as _decode
+    return _decode.decode64(scene.neural, scene.cell_center, scene.cell_axes, scene.cell_quat, scene.K,
+                            np.asarray(cam, dtype=np.float64)[19:22])
+
+
+def explicit_scene(scene, mean, scale, quat, opac, rgb):
+    """An explicit-Gaussian scene with the given per-Gaussian values ((G,...)
+    arrays): colour as SH degree 0 with 0.5 + k_00 Y_00 = rgb, opacity as the
+    logit of sigma (sigma <= 0: opacity 0, never contributing)."""
+    import dataclasses
+    y00 = 0.5 / np.sqrt(np.pi)
+    G = scene.G
+    op = np.asarray(opac, dtype=np.float64).reshape(G)
+    with np.errstate(divide="ignore"):
+        logit = np.where(op > 0, np.log(np.clip(op, 1e-300, None)) - np.log1p(-np.clip(op, None, 1 - 1e-16)), -np.inf)
+    sh = ((np.asarray(rgb, dtype=np.float64).reshape(G, 1, 3) - 0.5) / y00)
+    return dataclasses.replace(scene, neural=None, g_mean=np.asarray(mean).reshape(G, 3),
+                               g_scale=np.asarray(scale).reshape(G, 3), g_quat=np.asarray(quat).reshape(G, 4),
+                               g_logit=logit, g_sh=sh, sh_degree=0)

@@ -84,6 +84,7 @@ class Scene:
     meta: dict = field(default_factory=dict)
     cell_v_sh: np.ndarray | None = None  # (N, (v_sh_degree+1)^2) view-dependent v_n, or None
     v_sh_degree: int = -1
+    neural: dict | None = None  # neural cells: F, H, feat (N,F), offset (G,3), mlp (packed float32)
 
     @property
     def N(self) -> int:
@@ -198,6 +199,40 @@ def with_view_dependent_v(scene: Scene, degree: int = 2, seed: int = 0, base: fl
     if nco > 1:
         k[:, 1:] = rng.standard_normal((scene.N, nco - 1), dtype=np.float32) * np.float32(band_std)
     return dataclasses.replace(scene, cell_v_sh=k, v_sh_degree=degree, name=scene.name + f"-vsh{degree}")
+
+
+def neural_scene(n_cells: int = 2048, K: int = 10, F: int = 32, H: int = 32, seed: int = 0,
+                  box: float = 1.0, axes_lo: float = 0.02, axes_hi: float = 0.1) -> Scene:
+    """Neural cells: centres uniform in [-box, box]^3, semi-axes log-uniform,
+    random unit quaternions, latent features N(0, 1), per-Gaussian offsets
+    uniform in the unit ball, and random decoder weights (normal with
+    standard deviation 1/sqrt(fan-in); output biases that give a mean opacity
+    near tanh(1), colour near 0.5 and scale ratios near 0.3).  The explicit
+    Gaussian arrays are placeholders (zeros): the renderer decodes the
+    Gaussians of visible cells per view.  Draw order: centres, axes, cell
+    quaternions, features, offsets, weights."""
+    rng = np.random.default_rng(seed)
+    N, G = n_cells, n_cells * K
+    center = rng.uniform(-box, box, (N, 3))
+    axes = log_uniform(rng, axes_lo, axes_hi, (N, 3))
+    cq = random_unit_quats(rng, N)
+    feat = rng.standard_normal((N, F))
+    off = uniform_in_ball(rng, G)
+    parts = []
+    for n_out, b_out in ((K, 1.0), (3 * K, 0.0), (3 * K, -0.85), (4 * K, 0.0)):
+        W1 = rng.standard_normal((H, F + 4)) / np.sqrt(F + 4)
+        b1 = np.zeros(H)
+        W2 = rng.standard_normal((n_out, H)) / np.sqrt(H)
+        b2 = np.full(n_out, b_out)
+        parts += [W1.ravel(), b1, W2.ravel(), b2]
+    mlp = np.concatenate(parts).astype(np.float32)
+    f32 = lambda a: np.ascontiguousarray(a, dtype=np.float32)
+    return Scene(K=K, sh_degree=0, cell_center=f32(center), cell_axes=f32(axes), cell_quat=f32(cq),
+                 cell_v=np.ones(N, dtype=np.float32), g_mean=np.zeros((G, 3), np.float32),
+                 g_scale=np.zeros((G, 3), np.float32), g_quat=np.zeros((G, 4), np.float32),
+                 g_logit=np.zeros(G, np.float32), g_sh=np.zeros((G, 1, 3), np.float32),
+                 name=f"neural-{N}x{K}-F{F}H{H}", meta=dict(seed=seed, n_cells=N, K=K),
+                 neural=dict(F=F, H=H, feat=f32(feat), offset=f32(off), mlp=mlp))
 
 
 def _box(lo, hi):
