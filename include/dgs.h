@@ -97,6 +97,31 @@ const char *dgs_last_error(dgs_ctx *ctx);
  * (the colour's real SH basis; c_n the cell centre); cell_v is then used
  * only by the comparators (dgs_render_compare).  cell_v_sh = NULL: the
  * scalar cell_v. */
+/* Neural cells (the decode step before the path, Sec. III Eq. 1-7 and Sec.
+ * IV-A Eq. 8-11): the K Gaussians of every visible cell are decoded per view
+ * from the cell's latent feature f_n, the viewing distance delta_n = |x_n - eye|
+ * and direction d_n = (x_n - eye) / delta_n by four MLPs with one ReLU hidden
+ * layer of width `hidden` on z = [f_n, delta_n, d_n]:
+ *   opacity  sigma_{n,k} = tanh(o_sigma[k])        (sigma <= 0: not drawn)
+ *   colour   c_{n,k} = sigmoid(o_c[3k .. 3k+2])     (used directly, no SH)
+ *   scale    s_{n,k} = min(sigmoid(o_s[3k .. 3k+2]), 1 - |O_pos|) * S_n
+ *   rotation q_{n,k} = o_q[4k .. 4k+3] normalised
+ *   centre   mu_{n,k} = x_n + R(Q_n) (O_pos * S_n), O_pos moved into the unit ball
+ * Arrays (float32, in the scene's location memory): cell_feat [N][feat_dim],
+ * g_offset [G][3] (O_pos), mlp: decoder after decoder (opacity, colour,
+ * scale, rotation; output widths K, 3K, 3K, 4K): W1 [hidden][feat_dim+4]
+ * row-major, b1 [hidden], W2 [out][hidden] row-major, b2 [out].
+ * 1 <= feat_dim <= 64, 1 <= hidden <= 64.  Neural scenes render through
+ * dgs_render; their backward, serving and the comparators are not built
+ * (INVALID_ARG). */
+typedef struct {
+    int32_t feat_dim;
+    int32_t hidden;
+    const float *cell_feat;
+    const float *g_offset;
+    const float *mlp;
+} dgs_neural_desc;
+
 typedef struct {
     int64_t num_cells;
     int32_t K;
@@ -104,10 +129,11 @@ typedef struct {
     int32_t location; /* DGS_HOST or DGS_DEVICE */
     int32_t reserved;
     const float *cell_center, *cell_axes, *cell_quat, *cell_v;
-    const float *g_mean, *g_scale, *g_quat, *g_logit, *g_sh;
+    const float *g_mean, *g_scale, *g_quat, *g_logit, *g_sh;  /* ignored for neural scenes */
     const float *cell_v_sh;
     int32_t v_sh_degree;
     int32_t reserved2;
+    const dgs_neural_desc *neural; /* NULL: explicit Gaussians */
 } dgs_scene_desc;
 
 dgs_status dgs_scene_upload(dgs_ctx *ctx, const dgs_scene_desc *desc, uint32_t *scene_id);
@@ -194,6 +220,8 @@ dgs_status dgs_loss_l1(dgs_ctx *ctx, const float *rgb, const float *target, int6
  *   DGS_BUF_PIX_NDONE   int32 [P]        per-pixel number of blended cells
  *   DGS_BUF_GRAD2D      float [V][G][12] after backward: dmu_x dmu_y da db dc dsigma dr dg db 0 0 0
  *   DGS_BUF_CELL_V      float [V][N]     v_n as rendered in each view
+ *   DGS_BUF_DECODED     float [V][G][14] neural scenes: decoded mean(3) scale(3) quat(4) opacity
+ *                       rgb(3) of the Gaussians of visible cells (others unspecified)
  * *needed receives the byte size; nothing is copied if bytes < needed.
  * Synchronises the stream the state was rendered on. */
 enum {
@@ -205,7 +233,8 @@ enum {
     DGS_BUF_PIX_D = 6,
     DGS_BUF_PIX_NDONE = 7,
     DGS_BUF_GRAD2D = 8,
-    DGS_BUF_CELL_V = 9
+    DGS_BUF_CELL_V = 9,
+    DGS_BUF_DECODED = 10
 };
 dgs_status dgs_state_read(dgs_ctx *ctx, const dgs_fwd_state *state, int32_t what, void *host_dst, int64_t bytes,
                           int64_t *needed);

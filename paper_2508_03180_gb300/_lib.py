@@ -32,6 +32,7 @@ DGS_BUF_PIX_D = 6
 DGS_BUF_PIX_NDONE = 7
 DGS_BUF_GRAD2D = 8
 DGS_BUF_CELL_V = 9
+DGS_BUF_DECODED = 10
 
 _P = C.c_void_p
 _FP = C.POINTER(C.c_float)
@@ -43,11 +44,16 @@ class dgs_config(C.Structure):
                 ("hbm_budget_bytes", C.c_int64)]
 
 
+class dgs_neural_desc(C.Structure):
+    _fields_ = [("feat_dim", C.c_int32), ("hidden", C.c_int32), ("cell_feat", _P), ("g_offset", _P), ("mlp", _P)]
+
+
 class dgs_scene_desc(C.Structure):
     _fields_ = [("num_cells", C.c_int64), ("K", C.c_int32), ("sh_degree", C.c_int32), ("location", C.c_int32),
                 ("reserved", C.c_int32), ("cell_center", _P), ("cell_axes", _P), ("cell_quat", _P), ("cell_v", _P),
                 ("g_mean", _P), ("g_scale", _P), ("g_quat", _P), ("g_logit", _P), ("g_sh", _P),
-                ("cell_v_sh", _P), ("v_sh_degree", C.c_int32), ("reserved2", C.c_int32)]
+                ("cell_v_sh", _P), ("v_sh_degree", C.c_int32), ("reserved2", C.c_int32),
+                ("neural", C.POINTER(dgs_neural_desc))]
 
 
 class dgs_camera(C.Structure):

@@ -75,7 +75,7 @@ Workspace::~Workspace() {
 
 std::vector<DevBuf *> Workspace::all() {
     return {&views, &scenes, &zkey, &zval, &rect, &depth, &count, &cnt_sorted, &offs, &tkey, &tval, &ranges, &rec,
-            &Dpix, &ndpix, &rgb, &g2d, &gstage, &sort_k, &sort_v, &sort_hist, &sort_status, &sort_ctr, &small, &scan, &sizes, &vview, &gvview};
+            &Dpix, &ndpix, &rgb, &g2d, &gstage, &sort_k, &sort_v, &sort_hist, &sort_status, &sort_ctr, &small, &scan, &sizes, &vview, &gvview, &dec};
 }
 
 dgs_status Workspace::init() {
@@ -166,6 +166,11 @@ SceneDev Scene::dev() const {
     d.K = K;
     d.sh_degree = deg;
     d.v_sh_degree = vdeg;
+    d.feat = F > 0 ? (const float *)feat.p : nullptr;
+    d.goff = F > 0 ? (const float *)goff.p : nullptr;
+    d.mlp = F > 0 ? (const float *)mlp.p : nullptr;
+    d.F = F;
+    d.H = H;
     d.pad = 0;
     return d;
 }
@@ -248,6 +253,14 @@ static dgs_status upload_param(const float *src, int location, int64_t rows, int
     return DGS_OK;
 }
 
+// Packed decoder weights of a neural scene (four decoders, outputs K, 3K, 3K, 4K).
+static int neural_weights(const Scene &sc) {
+    const int outs[4] = {sc.K, 3 * sc.K, 3 * sc.K, 4 * sc.K};
+    int n = 0;
+    for (int o : outs) n += sc.H * (sc.F + 4) + sc.H + o * sc.H + o;
+    return n;
+}
+
 static dgs_status fill_scene(dgs_ctx *ctx, Scene &sc, const dgs_scene_desc *d, cudaStream_t st, bool cells_too) {
     const int64_t N = sc.N, G = sc.G;
     float *cell = (float *)sc.cell.p, *gs = (float *)sc.gauss.p, *sh = (float *)sc.sh.p;
@@ -260,11 +273,17 @@ static dgs_status fill_scene(dgs_ctx *ctx, Scene &sc, const dgs_scene_desc *d, c
     }
     if (d->cell_v) parts.push_back({d->cell_v, N, 1, cell + 10 * N, N});
     if (sc.vdeg >= 0 && d->cell_v_sh) parts.push_back({d->cell_v_sh, N, sc.Cv, (float *)sc.vsh.p, N});
-    parts.push_back({d->g_mean, G, 3, gs, G});
-    parts.push_back({d->g_scale, G, 3, gs + 3 * G, G});
-    parts.push_back({d->g_quat, G, 4, gs + 6 * G, G});
-    parts.push_back({d->g_logit, G, 1, gs + 10 * G, G});
-    parts.push_back({d->g_sh, G, 3 * sc.C, sh, G});
+    if (sc.F > 0) {  // neural cells: features and offsets as planes, the weights as given (one row)
+        parts.push_back({d->neural->cell_feat, N, sc.F, (float *)sc.feat.p, N});
+        parts.push_back({d->neural->g_offset, G, 3, (float *)sc.goff.p, G});
+        parts.push_back({d->neural->mlp, 1, neural_weights(sc), (float *)sc.mlp.p, 1});
+    } else {
+        parts.push_back({d->g_mean, G, 3, gs, G});
+        parts.push_back({d->g_scale, G, 3, gs + 3 * G, G});
+        parts.push_back({d->g_quat, G, 4, gs + 6 * G, G});
+        parts.push_back({d->g_logit, G, 1, gs + 10 * G, G});
+        parts.push_back({d->g_sh, G, 3 * sc.C, sh, G});
+    }
     // host inputs: every array gets its own staging region, one synchronisation at the end
     float *stage = nullptr;
     if (d->location == DGS_HOST) {
@@ -293,9 +312,17 @@ static dgs_status check_desc(const dgs_scene_desc *d, bool need_cells = true) {
         return set_error(DGS_ERR_INVALID_ARG, "need num_cells >= 0, 1 <= K <= 32, 0 <= sh_degree <= 3");
     if (d->location != DGS_HOST && d->location != DGS_DEVICE) return set_error(DGS_ERR_INVALID_ARG, "bad location");
     if (d->num_cells * (int64_t)d->K >= (1LL << 31)) return set_error(DGS_ERR_CAPACITY, "more than 2^31 Gaussians");
-    if (d->num_cells > 0 && ((need_cells && (!d->cell_center || !d->cell_axes || !d->cell_quat)) || !d->g_mean ||
-                             !d->g_scale || !d->g_quat || !d->g_logit || !d->g_sh))
+    const bool explicit_g = d->neural == nullptr;
+    if (d->num_cells > 0 && ((need_cells && (!d->cell_center || !d->cell_axes || !d->cell_quat)) ||
+                             (explicit_g && (!d->g_mean || !d->g_scale || !d->g_quat || !d->g_logit || !d->g_sh))))
         return set_error(DGS_ERR_INVALID_ARG, "a scene array is NULL");
+    if (!explicit_g) {
+        const dgs_neural_desc *n = d->neural;
+        if (n->feat_dim < 1 || n->feat_dim > 64 || n->hidden < 1 || n->hidden > 64)
+            return set_error(DGS_ERR_INVALID_ARG, "neural cells need 1 <= feat_dim, hidden <= 64");
+        if (d->num_cells > 0 && (!n->cell_feat || !n->g_offset || !n->mlp))
+            return set_error(DGS_ERR_INVALID_ARG, "a neural scene array is NULL");
+    }
     if (d->cell_v_sh && (d->v_sh_degree < 0 || d->v_sh_degree > 3))
         return set_error(DGS_ERR_INVALID_ARG, "v_sh_degree must be in 0..3 with cell_v_sh");
     return DGS_OK;
@@ -315,6 +342,14 @@ extern "C" dgs_status dgs_scene_upload(dgs_ctx *ctx, const dgs_scene_desc *d, ui
     sc->C = (sc->deg + 1) * (sc->deg + 1);
     sc->vdeg = d->cell_v_sh ? d->v_sh_degree : -1;
     sc->Cv = sc->vdeg >= 0 ? (sc->vdeg + 1) * (sc->vdeg + 1) : 0;
+    if (d->neural) {
+        sc->F = d->neural->feat_dim;
+        sc->H = d->neural->hidden;
+        if ((s = sc->feat.ensure(sizeof(float) * sc->F * std::max<int64_t>(1, sc->N))) ||
+            (s = sc->goff.ensure(sizeof(float) * 3 * std::max<int64_t>(1, sc->G))) ||
+            (s = sc->mlp.ensure(sizeof(float) * neural_weights(*sc))))
+            return s;
+    }
     if (sc->vdeg >= 0 && (s = sc->vsh.ensure(sizeof(float) * sc->Cv * std::max<int64_t>(1, sc->N)))) return s;
     if ((s = sc->cell.ensure(sizeof(float) * 11 * std::max<int64_t>(1, sc->N)))) return s;
     if ((s = sc->gauss.ensure(sizeof(float) * 11 * std::max<int64_t>(1, sc->G)))) return s;
@@ -338,8 +373,9 @@ extern "C" dgs_status dgs_scene_update(dgs_ctx *ctx, uint32_t scene_id, const dg
     if (it == ctx->scenes.end()) return set_error(DGS_ERR_NOT_FOUND, "unknown scene id");
     Scene &sc = *it->second;
     if (d->num_cells != sc.N || d->K != sc.K || d->sh_degree != sc.deg ||
-        (d->cell_v_sh && d->v_sh_degree != sc.vdeg))
-        return set_error(DGS_ERR_INVALID_ARG, "update must keep N, K, sh_degree and v_sh_degree");
+        (d->cell_v_sh && d->v_sh_degree != sc.vdeg) || ((d->neural != nullptr) != (sc.F > 0)) ||
+        (d->neural && (d->neural->feat_dim != sc.F || d->neural->hidden != sc.H)))
+        return set_error(DGS_ERR_INVALID_ARG, "update must keep N, K, sh_degree, v_sh_degree and the neural widths");
     return fill_scene(ctx, sc, d, (cudaStream_t)stream, false);
 }
 
@@ -553,16 +589,28 @@ dgs_status chain_forward(dgs_ctx *ctx, Workspace &ws, const std::vector<ChainVie
     if ((s = run_binning(ctx, ws, st))) return s;
     const BlendParams bp = blend_params(ctx->cfg);
     const long long nrec = std::max(1LL, ws.n_records), px1 = std::max(1LL, px);
-    if ((s = ws.rec.ensure(sizeof(float4) * kRecF4 * nrec)) ||
+    bool any_neural = false;
+    for (const Scene *sc : slots) any_neural = any_neural || sc->F > 0;
+    if ((any_neural && (s = ws.dec.ensure(sizeof(float) * kDecF * nrec))) ||
+        (s = ws.rec.ensure(sizeof(float4) * kRecF4 * nrec)) ||
         (grad_buffers && (s = ws.g2d.ensure(sizeof(float) * kGradF * nrec))) || (s = ws.Dpix.ensure(4 * px1)) ||
         (s = ws.ndpix.ensure(4 * px1)) || ((keep_rgb || !out_img) && (s = ws.rgb.ensure(12 * px1))))
         return s;
     const ViewDesc *dv = (const ViewDesc *)ws.views.p;
     {
         StageTimer t(ctx->prof, DGS_STAGE_PROJECT_FWD, st);
-        for (int k = 0; k < S; ++k)
-            launch_project_fwd(dv, V, k, slots[k]->dev(), (const uint32_t *)ws.count.p, (const float *)ws.vview.p,
-                               bp, (float4 *)ws.rec.p, grad_buffers ? (float *)ws.g2d.p : nullptr, st);
+        for (int k = 0; k < S; ++k) {
+            const SceneDev sd = slots[k]->dev();
+            if (slots[k]->F > 0) {  // neural cells: decode the visible cells' Gaussians for every view first
+                launch_decode(dv, V, k, sd, (const uint32_t *)ws.count.p, (float *)ws.dec.p, st);
+                launch_project_neural(dv, V, k, sd, (const uint32_t *)ws.count.p, (const float *)ws.vview.p,
+                                      (const float *)ws.dec.p, bp, (float4 *)ws.rec.p,
+                                      grad_buffers ? (float *)ws.g2d.p : nullptr, st);
+            } else {
+                launch_project_fwd(dv, V, k, sd, (const uint32_t *)ws.count.p, (const float *)ws.vview.p, bp,
+                                   (float4 *)ws.rec.p, grad_buffers ? (float *)ws.g2d.p : nullptr, st);
+            }
+        }
     }
     float *img = out_img ? out_img : (float *)ws.rgb.p;
     float *img2 = (keep_rgb && out_img) ? (float *)ws.rgb.p : nullptr;
@@ -655,6 +703,7 @@ extern "C" dgs_status dgs_render_backward(dgs_ctx *ctx, dgs_fwd_state *state, co
     auto it = ctx->scenes.find(state->scene_id);
     if (it == ctx->scenes.end()) return set_error(DGS_ERR_NOT_FOUND, "scene of this state was released");
     const Scene &sc = *it->second;
+    if (sc.F > 0) return set_error(DGS_ERR_INVALID_ARG, "gradients through the neural-cell decode are not built");
     Workspace &ws = *state->ws;
     cudaStream_t st = (cudaStream_t)stream;
     CK(cudaStreamWaitEvent(st, ws.done, 0));
@@ -760,6 +809,7 @@ extern "C" dgs_status dgs_state_read(dgs_ctx *ctx, const dgs_fwd_state *state, i
         case DGS_BUF_PIX_NDONE: need = 4 * ws.total_px; break;
         case DGS_BUF_GRAD2D: need = ws.g2d.p ? 48 * VG : 0; break;
         case DGS_BUF_CELL_V: need = 4 * VN; break;
+        case DGS_BUF_DECODED: need = ws.dec.p ? 4LL * kDecF * VG : 0; break;
         default: return set_error(DGS_ERR_INVALID_ARG, "unknown buffer id");
     }
     if (needed) *needed = need;
@@ -785,6 +835,7 @@ extern "C" dgs_status dgs_state_read(dgs_ctx *ctx, const dgs_fwd_state *state, i
         case DGS_BUF_PIX_NDONE: src = ws.ndpix.p; break;
         case DGS_BUF_GRAD2D: src = ws.g2d.p; break;
         case DGS_BUF_CELL_V: src = ws.vview.p; break;
+        case DGS_BUF_DECODED: src = ws.dec.p; break;
     }
     CK(cudaMemcpy(dst, src, need, cudaMemcpyDeviceToHost));
     return DGS_OK;

@@ -260,6 +260,7 @@ extern "C" dgs_status dgs_render_compare(dgs_ctx *ctx, uint32_t scene_id, int32_
     CK(cudaSetDevice(ctx->cfg.device));
     auto it = ctx->scenes.find(scene_id);
     if (it == ctx->scenes.end()) return set_error(DGS_ERR_NOT_FOUND, "unknown scene id");
+    if (it->second->F > 0) return set_error(DGS_ERR_INVALID_ARG, "the comparators take explicit Gaussians");
     std::vector<dgs_camera> cams;
     for (int v = 0; v < n_views; ++v) {
         if (cam_slots[v] >= (uint32_t)kMaxCamSlots || !ctx->cam_set[cam_slots[v]])

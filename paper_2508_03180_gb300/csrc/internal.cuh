@@ -39,11 +39,17 @@ struct SceneDev {
     const float *gauss;    // [11][G]: mean xyz, scale xyz, quat wxyz, logit
     const float *sh;       // [C*3][G]: coefficient c, channel ch at plane c*3+ch
     const float *vsh;      // [Cv][N]: SH coefficients of a view-dependent v_n, or NULL (scalar v_n)
+    const float *feat;     // neural cells: [F][N] latent features, or NULL (explicit Gaussians)
+    const float *goff;     // neural cells: [3][G] position offsets O_pos
+    const float *mlp;      // neural cells: packed decoder weights
     long long N, G;
     int K, sh_degree;
     int v_sh_degree;       // -1 without vsh
+    int F, H;              // neural cells: feature and hidden widths
     int pad;
 };
+
+constexpr int kDecF = 14;  // floats per decoded Gaussian: mean 3, scale 3, quat 4, opacity, rgb 3
 
 // Sizes of one launch chain kept in device memory.  A captured CUDA graph
 // replays over batches of other sizes: kernels handed a non-NULL pointer read
@@ -155,6 +161,14 @@ void launch_cell_v_grad(const ViewDesc *views, int n_views, const SceneDev &sc, 
 void launch_gauss_bin(const ViewDesc *views, int n_views, const SceneDev &sc, const BlendParams &bp, bool wsr,
                       float tau, float4 *rec, uint32_t *zkey, uint32_t *zval, short4 *rect, uint32_t *count,
                       uint32_t *visible, cudaStream_t st);
+// Neural scenes: decode the Gaussians of every (view, cell) of scene `slot`
+// whose cell survived culling into dec [rec_base + g][kDecF], then their
+// records (colour and opacity as decoded).
+void launch_decode(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const uint32_t *count, float *dec,
+                   cudaStream_t st);
+void launch_project_neural(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const uint32_t *count,
+                           const float *vview, const float *dec, const BlendParams &bp, float4 *rec, float *g2d_zero,
+                           cudaStream_t st);
 // One launch for every scene of the device scene table (dsz->n_scenes
 // entries, Gaussian counts <= G_cap, which sizes the grid).
 void launch_project_fwd_table(const ViewDesc *views, const SceneDev *scenes, long long G_cap, const uint32_t *count,

@@ -118,9 +118,11 @@ __device__ __forceinline__ void proj_core(const ViewDesc &Vw, const GaussIn &p, 
 // The 48-byte record of Gaussian p in view Vw (an invalid Gaussian, mean not
 // in front of the near plane, gets ext = -1 so no AABB test passes).  k: SH
 // coefficients, cv: the cell's v_n.  Returns c.valid; c keeps the view-space mean.
+template <bool DIRECT_RGB = false>
 __device__ __forceinline__ bool gauss_record(const ViewDesc &Vw, const GaussIn &p, const float (&k)[16][3],
                                              int sh_degree, float opac, float cv, const BlendParams &bp,
-                                             ProjCore &c, float4 &r0, float4 &r1, float4 &r2) {
+                                             ProjCore &c, float4 &r0, float4 &r1, float4 &r2,
+                                             const float *rgb = nullptr) {
     proj_core(Vw, p, bp.dilation, c);
     if (!c.valid) {
         r0 = make_float4(0.f, 0.f, -1.f, -1.f);
@@ -138,18 +140,22 @@ __device__ __forceinline__ bool gauss_record(const ViewDesc &Vw, const GaussIn &
     const ScreenCov sc2 = screen_cov(c, bp.dilation);
     const float ip = rsqrtf(sc2.syy * sc2.det);
     const float fp = sc2.syy * ip, fr = -sc2.sxy * ip, ft = rsqrtf(sc2.syy);
-    float d0 = p.mean[0] - Vw.eye[0], d1 = p.mean[1] - Vw.eye[1], d2 = p.mean[2] - Vw.eye[2];
-    const float il = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
-    d0 *= il; d1 *= il; d2 *= il;
-    float Y[16];
-    sh_eval(d0, d1, d2, sh_degree, Y);
     float col[3];
+    if (DIRECT_RGB) {
+        col[0] = rgb[0]; col[1] = rgb[1]; col[2] = rgb[2];
+    } else {
+        float d0 = p.mean[0] - Vw.eye[0], d1 = p.mean[1] - Vw.eye[1], d2 = p.mean[2] - Vw.eye[2];
+        const float il = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+        d0 *= il; d1 *= il; d2 *= il;
+        float Y[16];
+        sh_eval(d0, d1, d2, sh_degree, Y);
 #pragma unroll
-    for (int ch = 0; ch < 3; ++ch) {
-        float s = 0.5f;
+        for (int ch = 0; ch < 3; ++ch) {
+            float s = 0.5f;
 #pragma unroll
-        for (int cidx = 0; cidx < 16; ++cidx) s += k[cidx][ch] * Y[cidx];
-        col[ch] = fmaxf(s, 0.0f);
+            for (int cidx = 0; cidx < 16; ++cidx) s += k[cidx][ch] * Y[cidx];
+            col[ch] = fmaxf(s, 0.0f);
+        }
     }
     r0 = make_float4(mx, my, ex, ey);
     // L scaled by kappa = sqrt(log2(e)/2): G' = exp2(-(s1^2 + s2^2)),
@@ -191,6 +197,43 @@ __device__ __forceinline__ void project_scene(const ViewDesc *__restrict__ views
             ProjCore c;
             float4 r0, r1, r2;
             gauss_record(Vw, p, k, sc.sh_degree, opac, vview[Vw.cell_base + cell], bp, c, r0, r1, r2);
+            float4 *o = rec + (Vw.rec_base + g) * kRecF4;
+            o[0] = r0; o[1] = r1; o[2] = r2;
+            if (g2d_zero) {
+                float4 *z = reinterpret_cast<float4 *>(g2d_zero + (Vw.rec_base + g) * kGradF);
+                z[0] = z[1] = z[2] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+    }
+}
+
+// Records of the decoded Gaussians of a neural scene (dec as written by
+// k_decode): colour and opacity as decoded; sigma <= 0 is not drawn.
+__global__ void __launch_bounds__(128) k_project_neural(const ViewDesc *__restrict__ views, int n_views, int slot,
+                                                        SceneDev sc, const uint32_t *__restrict__ count,
+                                                        const float *__restrict__ vview, const float *__restrict__ dec,
+                                                        BlendParams bp, float4 *__restrict__ rec,
+                                                        float *__restrict__ g2d_zero) {
+    const long long G = sc.G;
+    const int K = sc.K;
+    const float knone[16][3] = {};
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < G; g += (long long)gridDim.x * blockDim.x) {
+        const long long cell = g / K;
+        for (int v = 0; v < n_views; ++v) {
+            const ViewDesc &Vw = views[v];
+            if (Vw.scene_slot != slot || count[Vw.cell_base + cell] == 0u) continue;
+            const float *d = dec + (Vw.rec_base + g) * kDecF;
+            GaussIn p;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) { p.mean[i] = d[i]; p.scale[i] = d[3 + i]; }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) p.quat[i] = d[6 + i];
+            p.logit = 0.f;
+            const float opac = d[10];
+            ProjCore c;
+            float4 r0, r1, r2;
+            gauss_record<true>(Vw, p, knone, 0, opac, vview[Vw.cell_base + cell], bp, c, r0, r1, r2, d + 11);
+            if (!(opac > 0.f)) r0 = make_float4(0.f, 0.f, -1.f, -1.f);  // not drawn
             float4 *o = rec + (Vw.rec_base + g) * kRecF4;
             o[0] = r0; o[1] = r1; o[2] = r2;
             if (g2d_zero) {
@@ -325,6 +368,14 @@ void launch_project_fwd(const ViewDesc *views, int n_views, int slot, const Scen
                         const float *vview, const BlendParams &bp, float4 *rec, float *g2d_zero, cudaStream_t st) {
     if (sc.G == 0 || n_views == 0) return;
     k_project_fwd<<<grid_for(sc.G, 128), 128, 0, st>>>(views, n_views, slot, sc, count, vview, bp, rec, g2d_zero);
+}
+
+void launch_project_neural(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const uint32_t *count,
+                           const float *vview, const float *dec, const BlendParams &bp, float4 *rec, float *g2d_zero,
+                           cudaStream_t st) {
+    if (sc.G == 0 || n_views == 0) return;
+    k_project_neural<<<grid_for(sc.G, 128), 128, 0, st>>>(views, n_views, slot, sc, count, vview, dec, bp, rec,
+                                                          g2d_zero);
 }
 
 void launch_cell_v_grad(const ViewDesc *views, int n_views, const SceneDev &sc, const float *gv, float *g_cell_v,

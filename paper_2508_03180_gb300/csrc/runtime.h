@@ -46,7 +46,9 @@ struct Scene {
     int64_t N = 0, G = 0;
     int K = 1, deg = 0, C = 1;
     int vdeg = -1, Cv = 0;  // SH degree / coefficients of a view-dependent v_n (-1: scalar v_n)
+    int F = 0, H = 0;       // neural cells: feature width, hidden width (0: explicit Gaussians)
     DevBuf cell, gauss, sh, vsh;
+    DevBuf feat, goff, mlp; // neural cells: [F][N] features, [3][G] offsets, packed decoder weights
     SceneDev dev() const;
 };
 
@@ -70,6 +72,7 @@ struct Workspace {
     DevBuf gstage;                                           // backward staging
     DevBuf sort_k, sort_v, sort_hist, sort_status, sort_ctr, small, scan;
     DevBuf vview, gvview;         // per (view, cell): v_n as rendered, dL/dv_n
+    DevBuf dec;                   // per (view, Gaussian) of neural scenes: decoded values
     DevBuf sizes;                 // ChainSizes of a captured chain
     uint32_t *h_small = nullptr;  // pinned mirror of `small`
     ChainSizes *h_sizes = nullptr;

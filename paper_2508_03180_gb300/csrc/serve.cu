@@ -512,6 +512,7 @@ extern "C" dgs_status dgs_submit(dgs_ctx *ctx, const dgs_request *req, uint64_t 
         std::lock_guard<std::mutex> lk(ctx->mu);
         auto it = ctx->scenes.find(req->scene_id);
         if (it == ctx->scenes.end()) return set_error(DGS_ERR_NOT_FOUND, "unknown scene id");
+        if (it->second->F > 0) return set_error(DGS_ERR_INVALID_ARG, "serving of neural-cell scenes is not built");
         bytes = request_bytes(*it->second, c);
     }
     ServeState &S = *ctx->serve;

@@ -90,6 +90,14 @@ class Context:
             if getattr(scene, "cell_v_sh", None) is not None:
                 arrays["cell_v_sh"] = np.ascontiguousarray(scene.cell_v_sh, dtype=np.float32)
             d = self._desc(arrays, scene.N, scene.K, scene.sh_degree, L.DGS_HOST, vdeg)
+            if getattr(scene, "neural", None) is not None:
+                nr = scene.neural
+                keep = {k: np.ascontiguousarray(nr[k], dtype=np.float32) for k in ("feat", "offset", "mlp")}
+                nd = L.dgs_neural_desc()
+                nd.feat_dim, nd.hidden = nr["F"], nr["H"]
+                nd.cell_feat, nd.g_offset, nd.mlp = (keep[k].ctypes.data for k in ("feat", "offset", "mlp"))
+                d.neural = C.pointer(nd)
+                arrays["_neural"] = (nd, keep)  # alive during the call
         return L.dgs_scene_upload(self.ctx, d)
 
     def update_scene(self, scene_id: int, N: int, K: int, deg: int, **tensors):

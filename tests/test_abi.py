@@ -43,10 +43,10 @@ def test_struct_sizes_match_the_header():
 #include "dgs.h"
 #include <stddef.h>
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(dgs_config), sizeof(dgs_scene_desc),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(dgs_config), sizeof(dgs_scene_desc),
          sizeof(dgs_camera), sizeof(dgs_stats), sizeof(dgs_grads), sizeof(dgs_request), sizeof(dgs_result),
          offsetof(dgs_request, out_rgb), sizeof(dgs_serve_stats), sizeof(dgs_compare_config),
-         offsetof(dgs_compare_config, w_bg));
+         offsetof(dgs_compare_config, w_bg), sizeof(dgs_neural_desc), offsetof(dgs_scene_desc, neural));
   return 0;
 }
 '''
@@ -59,5 +59,6 @@ int main(void) {
     want = [ctypes.sizeof(L.dgs_config), ctypes.sizeof(L.dgs_scene_desc), ctypes.sizeof(L.dgs_camera),
             ctypes.sizeof(L.dgs_stats), ctypes.sizeof(L.dgs_grads), ctypes.sizeof(L.dgs_request),
             ctypes.sizeof(L.dgs_result), L.dgs_request.out_rgb.offset, ctypes.sizeof(L.dgs_serve_stats),
-            ctypes.sizeof(L.dgs_compare_config), L.dgs_compare_config.w_bg.offset]
+            ctypes.sizeof(L.dgs_compare_config), L.dgs_compare_config.w_bg.offset, ctypes.sizeof(L.dgs_neural_desc),
+            L.dgs_scene_desc.neural.offset]
     assert got == want
