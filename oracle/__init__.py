@@ -408,3 +408,40 @@ def explicit_scene(scene, mean, scale, quat, opac, rgb):
     return dataclasses.replace(scene, neural=None, g_mean=np.asarray(mean).reshape(G, 3),
                                g_scale=np.asarray(scale).reshape(G, 3), g_quat=np.asarray(quat).reshape(G, 4),
                                g_logit=logit, g_sh=sh, sh_degree=0)
+
+
+def neural_render_and_grad(scene, cam, dL_dC, decided=None, opt: Options = Options(), ndone=None, tile_rows=None):
+    """FP64 image and gradients of sum(dL_dC * C) for a neural scene in one
+    view: dL/d(packed weights), dL/d(features) (N,F), dL/d(offsets) (G,3),
+    and dL/d(decoded mean, scale, quat, opacity, rgb) per Gaussian.
+    decided: (mean, scale, quat) float32 arrays (G,...) whose FP32 AABB
+    decisions and tile lists to use (the renderer's own decoded values);
+    default: the FP64 decode rounded to FP32."""
+    from . import decode as _decode
+    d = _decode.decode_t(scene.neural, scene.cell_center, scene.cell_axes, scene.cell_quat, scene.K,
+                         np.asarray(cam, dtype=np.float64)[19:22], requires_grad=True)
+    G = scene.G
+    flat = {k: d[k].reshape(G, -1) for k in ("mean", "scale", "quat", "opac", "rgb")}
+    if decided is None:
+        decided = tuple(flat[k].detach().numpy().astype(np.float32) for k in ("mean", "scale", "quat"))
+    ex = explicit_scene(scene, decided[0], decided[1], decided[2], flat["opac"].detach().numpy().reshape(G),
+                        flat["rgb"].detach().numpy())
+    pv = prepare_view(ex, cam, opt, tile_rows)
+    # sigma <= 0 is not drawn: zero opacity, no gradient
+    proj = _project.project_direct(flat["mean"], flat["scale"], flat["quat"], torch.clamp_min(flat["opac"].reshape(G), 0.0),
+                                   flat["rgb"], cam, opt.dilation)
+    pv["proj"] = {k: v.detach().numpy() for k, v in proj.items()}
+    img = render_view(ex, cam, opt, pv=pv, forced_ndone=ndone)
+    g2d = blend_grad_view(ex, pv, dL_dC, opt, ndone=ndone)
+    outs = [proj["mu2"], proj["conic"], proj["opac"], proj["rgb"]]
+    gos = [torch.tensor(g2d[k], dtype=torch.float64) for k in ("mu2", "conic", "opac", "rgb")]
+    dec_vals = [flat[k] for k in ("mean", "scale", "quat", "opac", "rgb")]
+    leaves = d["leaves"]
+    grads = torch.autograd.grad(outs, [leaves["mlp"], leaves["feat"], leaves["offset"]] + dec_vals, gos,
+                                allow_unused=True, retain_graph=False)
+    z = lambda t, ref: np.zeros(tuple(ref.shape)) if t is None else t.numpy()
+    res = dict(mlp=z(grads[0], leaves["mlp"]), feat=z(grads[1], leaves["feat"]),
+               offset=z(grads[2], leaves["offset"]).reshape(G, 3))
+    for name, g_, ref in zip(("mean", "scale", "quat", "opac", "rgb"), grads[3:], dec_vals):
+        res["dec_" + name] = z(g_, ref).reshape(G, -1)
+    return img, res

@@ -50,6 +50,19 @@ def unpack(mlp, F: int, H: int, K: int):
     return out
 
 
+def unpack_t(w, F: int, H: int, K: int):
+    """unpack() of a float64 tensor (keeps its autograd graph)."""
+    out, o = [], 0
+    for n_out in out_widths(K):
+        W1 = w[o:o + H * (F + 4)].reshape(H, F + 4); o += H * (F + 4)
+        b1 = w[o:o + H]; o += H
+        W2 = w[o:o + n_out * H].reshape(n_out, H); o += n_out * H
+        b2 = w[o:o + n_out]; o += n_out
+        out.append((W1, b1, W2, b2))
+    assert o == w.numel(), (o, w.numel())
+    return out
+
+
 def packed_size(F: int, H: int, K: int) -> int:
     return sum(H * (F + 4) + H + n * H + n for n in out_widths(K))
 
@@ -57,18 +70,29 @@ def packed_size(F: int, H: int, K: int) -> int:
 def decode64(neural: dict, cell_center, cell_axes, cell_quat, K: int, eye):
     """Gaussians of every cell for one eye position.  Returns float64 numpy
     arrays: mean (N,K,3), scale (N,K,3), quat (N,K,4), opac (N,K), rgb (N,K,3)."""
+    out = decode_t(neural, cell_center, cell_axes, cell_quat, K, eye)
+    return {k: v.detach().numpy() for k, v in out.items() if k in ("mean", "scale", "quat", "opac", "rgb")}
+
+
+def decode_t(neural: dict, cell_center, cell_axes, cell_quat, K: int, eye, requires_grad: bool = False):
+    """decode64 as torch float64 tensors; with requires_grad the leaves
+    (out["leaves"]: mlp, feat, offset) carry gradients."""
     F, H = neural["F"], neural["H"]
     x = torch.as_tensor(np.asarray(cell_center, dtype=np.float64))
     S = torch.as_tensor(np.asarray(cell_axes, dtype=np.float64))
     N = x.shape[0]
-    f = torch.as_tensor(np.asarray(neural["feat"], dtype=np.float64)).reshape(N, F)
-    off = torch.as_tensor(np.asarray(neural["offset"], dtype=np.float64)).reshape(N, K, 3)
+    leaves = dict(mlp=torch.tensor(np.asarray(neural["mlp"], dtype=np.float64), requires_grad=requires_grad),
+                  feat=torch.tensor(np.asarray(neural["feat"], dtype=np.float64).reshape(N, F),
+                                    requires_grad=requires_grad),
+                  offset=torch.tensor(np.asarray(neural["offset"], dtype=np.float64).reshape(N, K, 3),
+                                      requires_grad=requires_grad))
+    f, off = leaves["feat"], leaves["offset"]
     e = torch.as_tensor(np.asarray(eye, dtype=np.float64))
     rel = x - e[None, :]
     delta = torch.linalg.norm(rel, dim=1, keepdim=True)
     z = torch.cat([f, delta, rel / delta], dim=1)                   # (N, F+4)
     outs = []
-    for W1, b1, W2, b2 in unpack(neural["mlp"], F, H, K):
+    for W1, b1, W2, b2 in unpack_t(leaves["mlp"], F, H, K):
         h = torch.relu(z @ W1.T + b1)
         outs.append(h @ W2.T + b2)
     o_sig, o_col, o_sc, o_q = outs
@@ -83,4 +107,4 @@ def decode64(neural: dict, cell_center, cell_axes, cell_quat, K: int, eye):
     Rc = quat_to_rotmat(torch.as_tensor(np.asarray(cell_quat, dtype=np.float64)))  # (N,3,3)
     local = off_b * S[:, None, :]
     mean = x[:, None, :] + torch.einsum("nij,nkj->nki", Rc, local)
-    return dict(mean=mean.numpy(), scale=scale.numpy(), quat=quat.numpy(), opac=opac.numpy(), rgb=rgb.numpy())
+    return dict(mean=mean, scale=scale, quat=quat, opac=opac, rgb=rgb, leaves=leaves)

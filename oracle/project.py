@@ -71,6 +71,16 @@ def camera_tensors(cam):
                 cy=float(c[5]), znear=float(c[6]), R=c[7:16].reshape(3, 3), t=c[16:19], eye=c[19:22])
 
 
+def project_direct(mean, scale, quat, opac, rgb, cam, dilation: float = 0.3):
+    """As project(), with opacity and colour given directly (decoded neural
+    Gaussians): the same geometry, opac and rgb passed through."""
+    out = project(mean, scale, quat, torch.zeros_like(opac), torch.zeros(mean.shape[0], 1, 3, dtype=mean.dtype), 0,
+                  cam, dilation)
+    out["opac"] = opac
+    out["rgb"] = rgb
+    return out
+
+
 def project(mean, scale, quat, logit, sh, sh_degree: int, cam, dilation: float = 0.3):
     """Screen-space quantities of Gaussians (all float64 tensors; gradients
     flow to every input).  Returns dict(mu2 (G,2), conic (G,3), opac (G,),

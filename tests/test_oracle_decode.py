@@ -8,7 +8,9 @@
 * every Gaussian centre lies inside its cell ellipsoid, and the scale ratio
   obeys Eq. 11;
 * the view direction enters only through its input columns, the distance
-  only through its own.
+  only through its own;
+* gradients of a rendered loss through the decode (autograd of the FP64
+  decode and projection) match FP64 central differences.
 """
 import math
 
@@ -136,3 +138,39 @@ def test_view_inputs():
 def dict_scene(sc, mlp):
     import dataclasses
     return dataclasses.replace(sc, neural=dict(sc.neural, mlp=mlp))
+
+
+def test_neural_gradients_match_central_differences():
+    """dL/d(weights, features, offsets) of a rendered loss through the decode,
+    against FP64 central differences with the decisions held fixed."""
+    import dataclasses
+    sc = synth.neural_scene(n_cells=24, K=3, F=6, H=5, seed=11, box=0.5, axes_lo=0.15, axes_hi=0.4)
+    cam = synth.small_camera(24, 24).as_array()
+    g = np.random.default_rng(5).standard_normal((3, 24, 24))
+    img, an = oracle.neural_render_and_grad(sc, cam, g)
+    nd = img["ndone"]
+    dec = oracle.decode_view(sc, cam)
+    decided = tuple(dec[k].reshape(sc.G, -1).astype(np.float32) for k in ("mean", "scale", "quat"))
+
+    def loss(s2):
+        im, _ = oracle.neural_render_and_grad(s2, cam, g, decided=decided, ndone=nd)
+        return float((im["C"] * g).sum())
+
+    rng = np.random.default_rng(0)
+    h = 1e-6
+    checked = 0
+    for key, arr in (("mlp", sc.neural["mlp"]), ("feat", sc.neural["feat"]), ("offset", sc.neural["offset"])):
+        a = an[key].reshape(-1)
+        cand = np.nonzero(np.abs(a) > 1e-4 * np.abs(a).max())[0]
+        assert len(cand) >= 5, key
+        for i in rng.choice(cand, 6, replace=False):
+            vals = []
+            for s in (+1, -1):
+                pert = arr.astype(np.float64).copy().reshape(-1)
+                pert[i] += s * h
+                s2 = dataclasses.replace(sc, neural=dict(sc.neural, **{key: pert.reshape(arr.shape)}))
+                vals.append(loss(s2))
+            fd = (vals[0] - vals[1]) / (2 * h)
+            assert abs(fd - a[i]) <= 1e-6 * np.abs(a).max() + 1e-9, (key, i, fd, a[i])
+            checked += 1
+    assert checked == 18
