@@ -13,7 +13,8 @@ names their activations but not their shape.  Readings:
 * colour           c_{n,k} = sigmoid(o_c[3k .. 3k+2])
 * scale            ratio = min(sigmoid(o_s[3k .. 3k+2]), 1 - |O_pos|)   (Eq. 11),
                    s_{n,k} = ratio * S_n                                 (Eq. 8)
-* rotation         q_{n,k} = o_q[4k .. 4k+3] / |o_q[4k .. 4k+3]|
+* rotation         q_{n,k} = o_q[4k .. 4k+3] / |o_q[4k .. 4k+3]|; an output of exactly zero
+                   (no direction to normalise) is the identity rotation (1, 0, 0, 0)
 * position         mu_{n,k} = x_n + R(Q_n) (O_pos * S_n), O_pos moved into the unit ball
                    (O / max(1, |O|)): the offset is taken in the cell's frame, so the
                    Gaussian centre lies inside the cell ellipsoid (Sec. IV-A)
@@ -103,7 +104,9 @@ def decode_t(neural: dict, cell_center, cell_axes, cell_quat, K: int, eye, requi
     ratio = torch.minimum(torch.sigmoid(o_sc).reshape(N, K, 3), 1.0 - torch.linalg.norm(off_b, dim=2, keepdim=True))
     scale = ratio * S[:, None, :]
     q = o_q.reshape(N, K, 4)
-    quat = q / torch.linalg.norm(q, dim=2, keepdim=True)
+    qn = torch.linalg.norm(q, dim=2, keepdim=True)
+    ident = torch.tensor([1.0, 0.0, 0.0, 0.0], dtype=torch.float64).expand_as(q)
+    quat = torch.where(qn > 0, q / torch.where(qn > 0, qn, torch.ones_like(qn)), ident)
     Rc = quat_to_rotmat(torch.as_tensor(np.asarray(cell_quat, dtype=np.float64)))  # (N,3,3)
     local = off_b * S[:, None, :]
     mean = x[:, None, :] + torch.einsum("nij,nkj->nki", Rc, local)

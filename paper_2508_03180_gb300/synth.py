@@ -207,7 +207,8 @@ def neural_scene(n_cells: int = 2048, K: int = 10, F: int = 32, H: int = 32, see
     random unit quaternions, latent features N(0, 1), per-Gaussian offsets
     uniform in the unit ball, and random decoder weights (normal with
     standard deviation 1/sqrt(fan-in); output biases that give a mean opacity
-    near tanh(1), colour near 0.5 and scale ratios near 0.3).  The explicit
+    near tanh(1), colour near 0.5, scale ratios near 0.3 and rotations
+    around the identity).  The explicit
     Gaussian arrays are placeholders (zeros): the renderer decodes the
     Gaussians of visible cells per view.  Draw order: centres, axes, cell
     quaternions, features, offsets, weights."""
@@ -219,11 +220,12 @@ def neural_scene(n_cells: int = 2048, K: int = 10, F: int = 32, H: int = 32, see
     feat = rng.standard_normal((N, F))
     off = uniform_in_ball(rng, G)
     parts = []
-    for n_out, b_out in ((K, 1.0), (3 * K, 0.0), (3 * K, -0.85), (4 * K, 0.0)):
+    identity = np.tile([1.0, 0.0, 0.0, 0.0], K)
+    for n_out, b_out in ((K, 1.0), (3 * K, 0.0), (3 * K, -0.85), (4 * K, identity)):
         W1 = rng.standard_normal((H, F + 4)) / np.sqrt(F + 4)
         b1 = np.zeros(H)
         W2 = rng.standard_normal((n_out, H)) / np.sqrt(H)
-        b2 = np.full(n_out, b_out)
+        b2 = np.broadcast_to(np.asarray(b_out, dtype=np.float64), (n_out,)).copy()
         parts += [W1.ravel(), b1, W2.ravel(), b2]
     mlp = np.concatenate(parts).astype(np.float32)
     f32 = lambda a: np.ascontiguousarray(a, dtype=np.float32)

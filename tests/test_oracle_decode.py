@@ -174,3 +174,30 @@ def test_neural_gradients_match_central_differences():
             assert abs(fd - a[i]) <= 1e-6 * np.abs(a).max() + 1e-9, (key, i, fd, a[i])
             checked += 1
     assert checked == 18
+
+
+def test_zero_rotation_output_is_the_identity():
+    """All weights and the rotation decoder's biases zero: every rotation
+    output is exactly zero and decodes to (1, 0, 0, 0); its gradient is zero
+    and finite, while the other decoders' gradients stay finite."""
+    sc = _tiny(seed=4)
+    K, F, H = sc.K, sc.neural["F"], sc.neural["H"]
+    mlp = np.zeros(odec.packed_size(F, H, K), dtype=np.float32)
+    o = 0
+    for i, n_out in enumerate(odec.out_widths(K)):
+        o += H * (F + 4) + H + n_out * H
+        if i < 3:
+            mlp[o:o + n_out] = 0.3
+        o += n_out
+    import dataclasses
+    sc = dataclasses.replace(sc, neural=dict(sc.neural, mlp=mlp))
+    eye = synth.small_camera(16, 16).as_array()[19:22]
+    d = odec.decode_t(sc.neural, sc.cell_center, sc.cell_axes, sc.cell_quat, K, eye, requires_grad=True)
+    np.testing.assert_array_equal(d["quat"].detach().numpy(), np.tile([1.0, 0.0, 0.0, 0.0], (sc.N, K, 1)))
+    loss = d["quat"].sum() + d["opac"].sum() + d["scale"].sum()
+    g, = __import__("torch").autograd.grad(loss, [d["leaves"]["mlp"]])
+    g = g.numpy()
+    assert np.isfinite(g).all()
+    o_rot = sum(H * (F + 4) + H + n * H + n for n in odec.out_widths(K)[:3])
+    assert np.all(g[o_rot:] == 0.0)       # the rotation decoder gets nothing
+    assert np.abs(g[:o_rot]).max() > 0.0  # the others do
