@@ -189,6 +189,14 @@ dgs_status dgs_render(dgs_ctx *ctx, uint32_t scene_id, int32_t n_views, const ui
  *   g_cell_v [N] (dL/dv_n summed over the views, v_n as rendered in each),
  *   g_cell_v_sh [N][(v_sh_degree+1)^2] (scenes with view-dependent v only:
  *   sum over views of dL/dv_n Y_lm(d), zero where the clamp was active).
+ * Neural scenes (Sec. III, Eq. 1-7; Sec. IV-A, Eq. 8-11) take the gradients
+ * through the per-view decode instead of the explicit Gaussian outputs,
+ * which must then be NULL (and these NULL for explicit scenes):
+ *   g_mlp [packed weight count] in the layout of dgs_neural_desc.mlp,
+ *   g_feat [N][feat_dim], g_offset [G][3] (dL/d of the raw offsets),
+ * each summed over the views in which the cell was decoded.  The decode's
+ * own decisions (the ReLU masks, the Eq. 11 bound, sigma <= 0 not drawn)
+ * are held fixed with the others.
  * Discrete choices of the forward (culling, tile lists, AABB skips, alpha
  * clamp, the per-pixel number of blended cells) are held fixed. */
 typedef struct {
@@ -196,6 +204,7 @@ typedef struct {
     int32_t reserved;
     float *g_mean, *g_scale, *g_log_scale, *g_quat, *g_logit, *g_sh, *g_cell_v;
     float *g_cell_v_sh;
+    float *g_mlp, *g_feat, *g_offset;
 } dgs_grads;
 
 dgs_status dgs_render_backward(dgs_ctx *ctx, dgs_fwd_state *state, const float *dL_drgb, int32_t location,

@@ -703,7 +703,11 @@ extern "C" dgs_status dgs_render_backward(dgs_ctx *ctx, dgs_fwd_state *state, co
     auto it = ctx->scenes.find(state->scene_id);
     if (it == ctx->scenes.end()) return set_error(DGS_ERR_NOT_FOUND, "scene of this state was released");
     const Scene &sc = *it->second;
-    if (sc.F > 0) return set_error(DGS_ERR_INVALID_ARG, "gradients through the neural-cell decode are not built");
+    const bool neural = sc.F > 0;
+    if (neural && (out->g_mean || out->g_scale || out->g_log_scale || out->g_quat || out->g_logit || out->g_sh))
+        return set_error(DGS_ERR_INVALID_ARG, "a neural scene has no explicit Gaussian parameters to differentiate");
+    if (!neural && (out->g_mlp || out->g_feat || out->g_offset))
+        return set_error(DGS_ERR_INVALID_ARG, "g_mlp, g_feat and g_offset need a neural scene");
     Workspace &ws = *state->ws;
     cudaStream_t st = (cudaStream_t)stream;
     CK(cudaStreamWaitEvent(st, ws.done, 0));
@@ -713,7 +717,9 @@ extern "C" dgs_status dgs_render_backward(dgs_ctx *ctx, dgs_fwd_state *state, co
         return set_error(DGS_ERR_INVALID_ARG, "g_cell_v_sh given for a scene without view-dependent v");
     dgs_status s;
     // staging: dL/drgb (3 px), then the gradient outputs
-    const long long n_out = 3 * G + 3 * G + 3 * G + 4 * G + G + 3LL * C * G + N + (long long)Cv * N;
+    const long long P = neural ? neural_weights(sc) : 0, NF = neural ? N * sc.F : 0, GO = neural ? 3 * G : 0;
+    const long long n_out =
+        3 * G + 3 * G + 3 * G + 4 * G + G + 3LL * C * G + N + (long long)Cv * N + P + NF + GO;
     const long long n_stage = (location == DGS_HOST ? 3 * px : 0) + (out->location == DGS_HOST ? n_out : 0) + 1;
     if ((s = ws.gstage.ensure(sizeof(float) * n_stage))) return s;
     float *stage = (float *)ws.gstage.p;
@@ -724,7 +730,8 @@ extern "C" dgs_status dgs_render_backward(dgs_ctx *ctx, dgs_fwd_state *state, co
         stage += 3 * px;
     }
     float *o_mean = out->g_mean, *o_s = out->g_scale, *o_ls = out->g_log_scale, *o_q = out->g_quat,
-          *o_lg = out->g_logit, *o_sh = out->g_sh, *o_v = out->g_cell_v, *o_vsh = out->g_cell_v_sh;
+          *o_lg = out->g_logit, *o_sh = out->g_sh, *o_v = out->g_cell_v, *o_vsh = out->g_cell_v_sh,
+          *o_mlp = out->g_mlp, *o_f = out->g_feat, *o_off = out->g_offset;
     if (out->location == DGS_HOST) {
         o_mean = out->g_mean ? stage : nullptr; stage += 3 * G;
         o_s = out->g_scale ? stage : nullptr; stage += 3 * G;
@@ -734,6 +741,9 @@ extern "C" dgs_status dgs_render_backward(dgs_ctx *ctx, dgs_fwd_state *state, co
         o_sh = out->g_sh ? stage : nullptr; stage += 3LL * C * G;
         o_v = out->g_cell_v ? stage : nullptr; stage += N;
         o_vsh = out->g_cell_v_sh ? stage : nullptr; stage += (long long)Cv * N;
+        o_mlp = out->g_mlp ? stage : nullptr; stage += P;
+        o_f = out->g_feat ? stage : nullptr; stage += NF;
+        o_off = out->g_offset ? stage : nullptr; stage += GO;
     }
     // dL/dv per (view, cell) entry, chained to the outputs after the blend adjoint
     float *gv = nullptr;
@@ -753,7 +763,22 @@ extern "C" dgs_status dgs_render_backward(dgs_ctx *ctx, dgs_fwd_state *state, co
                          (const float *)ws.Dpix.p, (const int *)ws.ndpix.p, dl, (float *)ws.g2d.p, gv, st);
         if (gv) launch_cell_v_grad((const ViewDesc *)ws.views.p, ws.V, sc.dev(), gv, o_v, o_vsh, st);
     }
-    {
+    if (neural && (o_mlp || o_f || o_off)) {
+        StageTimer t(ctx->prof, DGS_STAGE_PROJECT_BWD, st);
+        if ((s = ws.gdec.ensure(sizeof(float) * kDecF * std::max(1LL, ws.n_records)))) return s;
+        // the decode writes every output of every cell; unrequested ones go to scratch
+        float *gscr = nullptr;
+        if (!o_mlp || !o_f || !o_off) {
+            if ((s = ws.gscratch.ensure(sizeof(float) * std::max(1LL, P + NF + GO)))) return s;
+            gscr = (float *)ws.gscratch.p;
+        }
+        float *m = o_mlp ? o_mlp : gscr, *f = o_f ? o_f : gscr + P, *off = o_off ? o_off : gscr + P + NF;
+        CK(cudaMemsetAsync(m, 0, sizeof(float) * P, st));
+        launch_project_bwd_neural((const ViewDesc *)ws.views.p, ws.V, 0, sc.dev(), (const uint32_t *)ws.count.p, bp,
+                                  (const float *)ws.dec.p, (const float *)ws.g2d.p, (float *)ws.gdec.p, st);
+        launch_decode_bwd((const ViewDesc *)ws.views.p, ws.V, 0, sc.dev(), (const uint32_t *)ws.count.p,
+                          (const float *)ws.gdec.p, m, f, off, st);
+    } else if (!neural) {
         StageTimer t(ctx->prof, DGS_STAGE_PROJECT_BWD, st);
         launch_project_bwd((const ViewDesc *)ws.views.p, ws.V, 0, sc.dev(), (const uint32_t *)ws.count.p, bp,
                            (const float *)ws.g2d.p, o_mean, o_s, o_ls, o_q, o_lg, o_sh, st);
@@ -765,7 +790,9 @@ extern "C" dgs_status dgs_render_backward(dgs_ctx *ctx, dgs_fwd_state *state, co
                                                       {out->g_log_scale, o_ls, 3 * G},
                                                       {out->g_quat, o_q, 4 * G}, {out->g_logit, o_lg, G},
                                                       {out->g_sh, o_sh, 3LL * C * G}, {out->g_cell_v, o_v, N},
-                                                      {out->g_cell_v_sh, o_vsh, (long long)Cv * N}};
+                                                      {out->g_cell_v_sh, o_vsh, (long long)Cv * N},
+                                                      {out->g_mlp, o_mlp, P}, {out->g_feat, o_f, NF},
+                                                      {out->g_offset, o_off, GO}};
         for (auto &c : cp)
             if (c.h && c.n) CK(cudaMemcpyAsync(c.h, c.d, sizeof(float) * c.n, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));

@@ -169,6 +169,16 @@ void launch_decode(const ViewDesc *views, int n_views, int slot, const SceneDev 
 void launch_project_neural(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const uint32_t *count,
                            const float *vview, const float *dec, const BlendParams &bp, float4 *rec, float *g2d_zero,
                            cudaStream_t st);
+// Adjoints of a neural scene: the records' gradients with respect to the
+// decoded values of every decoded (view, Gaussian) (gdec, layout of dec),
+// then through the decode to the packed weights (g_mlp, accumulated: zero it
+// first), the features g_feat [N][F] and the raw offsets g_offset [G][3]
+// (both written), summed over views.
+void launch_project_bwd_neural(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const uint32_t *count,
+                               const BlendParams &bp, const float *dec, const float *g2d, float *gdec,
+                               cudaStream_t st);
+void launch_decode_bwd(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const uint32_t *count,
+                       const float *gdec, float *g_mlp, float *g_feat, float *g_offset, cudaStream_t st);
 // One launch for every scene of the device scene table (dsz->n_scenes
 // entries, Gaussian counts <= G_cap, which sizes the grid).
 void launch_project_fwd_table(const ViewDesc *views, const SceneDev *scenes, long long G_cap, const uint32_t *count,

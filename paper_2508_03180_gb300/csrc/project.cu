@@ -463,6 +463,92 @@ __device__ __forceinline__ void adjoint_U(const float u[3], const float w[3], fl
 // q = a dx^2 + 2 b dx dy + c dy^2, dL/d(opacity), dL/d(rgb).  Chain rule
 // through the forward above (clamp masks as in the forward), summed over
 // views; outputs are written, not accumulated.
+// Geometry adjoint of one (view, Gaussian): from dL/d(mu2) (gmx, gmy) and
+// dL/d(conic a, b, c) to dL/d(mean, linear scale, quaternion), accumulated
+// into gm, gs, gq.  False if the Gaussian's mean is not in front of the near
+// plane (never drawn).
+__device__ __forceinline__ bool view_geom_adjoint(const ViewDesc &Vw, const GaussIn &p, const BlendParams &bp,
+                                                  float gmx, float gmy, float gca, float gcb, float gcc, float gm[3],
+                                                  float gs[3], float gq[4]) {
+    ProjCore c;
+    proj_core(Vw, p, bp.dilation, c);
+    if (!c.valid) return false;
+    // conic -> Sigma' -> U:  dL/dU = 2 H U with H = -Q G_Q Q,
+    // G_Q = [[ga, gb/2], [gb/2, gc]], Q = Sigma'^-1, Sigma' = U U^T + d I.
+    // Needle-like Gaussians make U nearly rank one, so Q is nearly
+    // singular and Q G_Q Q U cancels heavily in the pixel frame.  In
+    // the eigenframe P of U U^T (eigenvalues s1^2 >= s2^2) it does
+    // not: with R = P^T U (rows r1 = p1^T U and r2 = x × r1 / s1^2,
+    // x = u × w, an exact identity free of cancellation) and
+    // lambda_i = s_i^2 + d,  dL/dU = -2 P N R,  N_ij = (P^T G_Q P)_ij / (lambda_i lambda_j).
+    const ScreenCov sc2 = screen_cov(c, bp.dilation);
+    float gU[6];
+    adjoint_U(sc2.u, sc2.w, bp.dilation, gca, gcb, gcc, gU);
+    // Sigma' = U U^T + d I, U = T M:  dL/dT = dL/dU M^T,  dL/dM = T^T dL/dU
+    float gT[6];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            gT[3 * a + j] = gU[3 * a] * c.M[3 * j] + gU[3 * a + 1] * c.M[3 * j + 1] + gU[3 * a + 2] * c.M[3 * j + 2];
+    float gMm[9];
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) gMm[3 * j + k] = c.T[j] * gU[k] + c.T[3 + j] * gU[3 + k];
+    // T = J R_view
+    const float gJ00 = gT[0] * Vw.R[0] + gT[1] * Vw.R[1] + gT[2] * Vw.R[2];
+    const float gJ02 = gT[0] * Vw.R[6] + gT[1] * Vw.R[7] + gT[2] * Vw.R[8];
+    const float gJ11 = gT[3] * Vw.R[3] + gT[4] * Vw.R[4] + gT[5] * Vw.R[5];
+    const float gJ12 = gT[3] * Vw.R[6] + gT[4] * Vw.R[7] + gT[5] * Vw.R[8];
+    const float tz = c.t[2], itz = 1.0f / tz, itz2 = itz * itz;
+    float gt[3] = {0.f, 0.f, 0.f};
+    gt[2] += -gJ00 * Vw.fx * itz2 - gJ11 * Vw.fy * itz2;
+    const float limx = 1.3f * (0.5f * (float)Vw.W / Vw.fx), limy = 1.3f * (0.5f * (float)Vw.H / Vw.fy);
+    if (c.x >= -limx && c.x <= limx) {  // J02 = -fx t_x / t_z^2
+        gt[0] += -gJ02 * Vw.fx * itz2;
+        gt[2] += gJ02 * 2.0f * Vw.fx * c.t[0] * itz2 * itz;
+    } else {                              // J02 = -fx xc / t_z
+        gt[2] += gJ02 * Vw.fx * c.xc * itz2;
+    }
+    if (c.y >= -limy && c.y <= limy) {
+        gt[1] += -gJ12 * Vw.fy * itz2;
+        gt[2] += gJ12 * 2.0f * Vw.fy * c.t[1] * itz2 * itz;
+    } else {
+        gt[2] += gJ12 * Vw.fy * c.yc * itz2;
+    }
+    // projected mean
+    gt[0] += gmx * Vw.fx * itz;
+    gt[1] += gmy * Vw.fy * itz;
+    gt[2] += -(gmx * Vw.fx * c.t[0] + gmy * Vw.fy * c.t[1]) * itz2;
+    // t = R mu + t_cam
+#pragma unroll
+    for (int j = 0; j < 3; ++j) gm[j] += Vw.R[j] * gt[0] + Vw.R[3 + j] * gt[1] + Vw.R[6 + j] * gt[2];
+    // M = R(q) diag(s)
+    float gR[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            gs[j] += gMm[3 * i + j] * c.Rg[3 * i + j];
+            gR[3 * i + j] = gMm[3 * i + j] * p.scale[j];
+        }
+    // R(q_hat), then q_hat = q / |q|
+    const float qn = sqrtf(p.quat[0] * p.quat[0] + p.quat[1] * p.quat[1] + p.quat[2] * p.quat[2] + p.quat[3] * p.quat[3]);
+    const float w = p.quat[0] / qn, x = p.quat[1] / qn, y = p.quat[2] / qn, z = p.quat[3] / qn;
+    float gh[4];
+    gh[0] = 2.0f * (-z * gR[1] + y * gR[2] + z * gR[3] - x * gR[5] - y * gR[6] + x * gR[7]);
+    gh[1] = 2.0f * (y * gR[1] + z * gR[2] + y * gR[3] - 2.0f * x * gR[4] - w * gR[5] + z * gR[6] + w * gR[7] - 2.0f * x * gR[8]);
+    gh[2] = 2.0f * (-2.0f * y * gR[0] + x * gR[1] + w * gR[2] + x * gR[3] + z * gR[5] - w * gR[6] + z * gR[7] - 2.0f * y * gR[8]);
+    gh[3] = 2.0f * (-2.0f * z * gR[0] - w * gR[1] + x * gR[2] + w * gR[3] - 2.0f * z * gR[4] + y * gR[5] + x * gR[6] + y * gR[7]);
+    const float hq = (gh[0] * w + gh[1] * x + gh[2] * y + gh[3] * z);
+    gq[0] += (gh[0] - hq * w) / qn;
+    gq[1] += (gh[1] - hq * x) / qn;
+    gq[2] += (gh[2] - hq * y) / qn;
+    gq[3] += (gh[3] - hq * z) / qn;
+    return true;
+}
+
 __global__ void __launch_bounds__(128) k_project_bwd_geom(const ViewDesc *__restrict__ views, int n_views, int slot,
                                                      SceneDev sc, const uint32_t *__restrict__ count, BlendParams bp,
                                                      const float *__restrict__ g2d, float *__restrict__ g_mean,
@@ -493,79 +579,7 @@ __global__ void __launch_bounds__(128) k_project_bwd_geom(const ViewDesc *__rest
                 if (!c.valid) continue;
                 // opacity
                 glog += gop * opac * (1.0f - opac);
-                // conic -> Sigma' -> U:  dL/dU = 2 H U with H = -Q G_Q Q,
-                // G_Q = [[ga, gb/2], [gb/2, gc]], Q = Sigma'^-1, Sigma' = U U^T + d I.
-                // Needle-like Gaussians make U nearly rank one, so Q is nearly
-                // singular and Q G_Q Q U cancels heavily in the pixel frame.  In
-                // the eigenframe P of U U^T (eigenvalues s1^2 >= s2^2) it does
-                // not: with R = P^T U (rows r1 = p1^T U and r2 = x × r1 / s1^2,
-                // x = u × w, an exact identity free of cancellation) and
-                // lambda_i = s_i^2 + d,  dL/dU = -2 P N R,  N_ij = (P^T G_Q P)_ij / (lambda_i lambda_j).
-                const ScreenCov sc2 = screen_cov(c, bp.dilation);
-                float gU[6];
-                adjoint_U(sc2.u, sc2.w, bp.dilation, gca, gcb, gcc, gU);
-                // Sigma' = U U^T + d I, U = T M:  dL/dT = dL/dU M^T,  dL/dM = T^T dL/dU
-                float gT[6];
-#pragma unroll
-                for (int a = 0; a < 2; ++a)
-#pragma unroll
-                    for (int j = 0; j < 3; ++j)
-                        gT[3 * a + j] = gU[3 * a] * c.M[3 * j] + gU[3 * a + 1] * c.M[3 * j + 1] + gU[3 * a + 2] * c.M[3 * j + 2];
-                float gMm[9];
-#pragma unroll
-                for (int j = 0; j < 3; ++j)
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) gMm[3 * j + k] = c.T[j] * gU[k] + c.T[3 + j] * gU[3 + k];
-                // T = J R_view
-                const float gJ00 = gT[0] * Vw.R[0] + gT[1] * Vw.R[1] + gT[2] * Vw.R[2];
-                const float gJ02 = gT[0] * Vw.R[6] + gT[1] * Vw.R[7] + gT[2] * Vw.R[8];
-                const float gJ11 = gT[3] * Vw.R[3] + gT[4] * Vw.R[4] + gT[5] * Vw.R[5];
-                const float gJ12 = gT[3] * Vw.R[6] + gT[4] * Vw.R[7] + gT[5] * Vw.R[8];
-                const float tz = c.t[2], itz = 1.0f / tz, itz2 = itz * itz;
-                float gt[3] = {0.f, 0.f, 0.f};
-                gt[2] += -gJ00 * Vw.fx * itz2 - gJ11 * Vw.fy * itz2;
-                const float limx = 1.3f * (0.5f * (float)Vw.W / Vw.fx), limy = 1.3f * (0.5f * (float)Vw.H / Vw.fy);
-                if (c.x >= -limx && c.x <= limx) {  // J02 = -fx t_x / t_z^2
-                    gt[0] += -gJ02 * Vw.fx * itz2;
-                    gt[2] += gJ02 * 2.0f * Vw.fx * c.t[0] * itz2 * itz;
-                } else {                              // J02 = -fx xc / t_z
-                    gt[2] += gJ02 * Vw.fx * c.xc * itz2;
-                }
-                if (c.y >= -limy && c.y <= limy) {
-                    gt[1] += -gJ12 * Vw.fy * itz2;
-                    gt[2] += gJ12 * 2.0f * Vw.fy * c.t[1] * itz2 * itz;
-                } else {
-                    gt[2] += gJ12 * Vw.fy * c.yc * itz2;
-                }
-                // projected mean
-                gt[0] += gmx * Vw.fx * itz;
-                gt[1] += gmy * Vw.fy * itz;
-                gt[2] += -(gmx * Vw.fx * c.t[0] + gmy * Vw.fy * c.t[1]) * itz2;
-                // t = R mu + t_cam
-#pragma unroll
-                for (int j = 0; j < 3; ++j) gm[j] += Vw.R[j] * gt[0] + Vw.R[3 + j] * gt[1] + Vw.R[6 + j] * gt[2];
-                // M = R(q) diag(s)
-                float gR[9];
-#pragma unroll
-                for (int i = 0; i < 3; ++i)
-#pragma unroll
-                    for (int j = 0; j < 3; ++j) {
-                        gs[j] += gMm[3 * i + j] * c.Rg[3 * i + j];
-                        gR[3 * i + j] = gMm[3 * i + j] * p.scale[j];
-                    }
-                // R(q_hat), then q_hat = q / |q|
-                const float qn = sqrtf(p.quat[0] * p.quat[0] + p.quat[1] * p.quat[1] + p.quat[2] * p.quat[2] + p.quat[3] * p.quat[3]);
-                const float w = p.quat[0] / qn, x = p.quat[1] / qn, y = p.quat[2] / qn, z = p.quat[3] / qn;
-                float gh[4];
-                gh[0] = 2.0f * (-z * gR[1] + y * gR[2] + z * gR[3] - x * gR[5] - y * gR[6] + x * gR[7]);
-                gh[1] = 2.0f * (y * gR[1] + z * gR[2] + y * gR[3] - 2.0f * x * gR[4] - w * gR[5] + z * gR[6] + w * gR[7] - 2.0f * x * gR[8]);
-                gh[2] = 2.0f * (-2.0f * y * gR[0] + x * gR[1] + w * gR[2] + x * gR[3] + z * gR[5] - w * gR[6] + z * gR[7] - 2.0f * y * gR[8]);
-                gh[3] = 2.0f * (-2.0f * z * gR[0] - w * gR[1] + x * gR[2] + w * gR[3] - 2.0f * z * gR[4] + y * gR[5] + x * gR[6] + y * gR[7]);
-                const float hq = (gh[0] * w + gh[1] * x + gh[2] * y + gh[3] * z);
-                gq[0] += (gh[0] - hq * w) / qn;
-                gq[1] += (gh[1] - hq * x) / qn;
-                gq[2] += (gh[2] - hq * y) / qn;
-                gq[3] += (gh[3] - hq * z) / qn;
+                view_geom_adjoint(Vw, p, bp, gmx, gmy, gca, gcb, gcc, gm, gs, gq);
             }
             // d/d log s = s d/ds
 #pragma unroll
@@ -579,6 +593,49 @@ __global__ void __launch_bounds__(128) k_project_bwd_geom(const ViewDesc *__rest
             for (int i = 0; i < 4; ++i) g_quat[4 * g + i] = gq[i];
         }
         if (g_logit) g_logit[g] = glog;
+    }
+}
+
+// Adjoint of a neural scene's records with respect to the decoded values
+// of every (view, Gaussian) whose cell was decoded in that view: gdec rows
+// in the layout of dec (mean 3, scale 3, quaternion 4, opacity 1, rgb 3).
+// The colour enters the record as decoded, so its gradient passes through;
+// a Gaussian with sigma <= 0 was not drawn and gets zeros.
+__global__ void __launch_bounds__(128) k_project_bwd_neural(const ViewDesc *__restrict__ views, int n_views, int slot,
+                                                            SceneDev sc, const uint32_t *__restrict__ count,
+                                                            BlendParams bp, const float *__restrict__ dec,
+                                                            const float *__restrict__ g2d, float *__restrict__ gdec) {
+    const long long G = sc.G;
+    const int K = sc.K;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < G; g += (long long)gridDim.x * blockDim.x) {
+        const long long cell = g / K;
+        for (int v = 0; v < n_views; ++v) {
+            const ViewDesc &Vw = views[v];
+            if (Vw.scene_slot != slot || count[Vw.cell_base + cell] == 0u) continue;
+            const long long row = Vw.rec_base + g;
+            const float *d = dec + row * kDecF;
+            const float4 *gr = reinterpret_cast<const float4 *>(g2d + row * kGradF);
+            const float4 a0 = gr[0], a1 = gr[1], a2 = gr[2];
+            float o[kDecF];
+#pragma unroll
+            for (int i = 0; i < kDecF; ++i) o[i] = 0.f;
+            if (d[10] > 0.f && (a0.x != 0.f || a0.y != 0.f || a0.z != 0.f || a0.w != 0.f || a1.x != 0.f ||
+                                a1.y != 0.f || a1.z != 0.f || a1.w != 0.f || a2.x != 0.f)) {
+                GaussIn p;
+#pragma unroll
+                for (int i = 0; i < 3; ++i) { p.mean[i] = d[i]; p.scale[i] = d[3 + i]; }
+#pragma unroll
+                for (int i = 0; i < 4; ++i) p.quat[i] = d[6 + i];
+                p.logit = 0.f;
+                if (view_geom_adjoint(Vw, p, bp, a0.x, a0.y, a0.z, a0.w, a1.x, o, o + 3, o + 6)) {
+                    o[10] = a1.y;
+                    o[11] = a1.z; o[12] = a1.w; o[13] = a2.x;
+                }
+            }
+            float2 *dst = reinterpret_cast<float2 *>(gdec + row * kDecF);
+#pragma unroll
+            for (int i = 0; i < kDecF / 2; ++i) dst[i] = make_float2(o[2 * i], o[2 * i + 1]);
+        }
     }
 }
 
@@ -657,6 +714,13 @@ __global__ void __launch_bounds__(128) k_project_bwd_colour(const ViewDesc *__re
             g_mean[3 * g + 2] += gdm[2];
         }
     }
+}
+
+void launch_project_bwd_neural(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const uint32_t *count,
+                               const BlendParams &bp, const float *dec, const float *g2d, float *gdec,
+                               cudaStream_t st) {
+    if (sc.G == 0) return;
+    k_project_bwd_neural<<<grid_for(sc.G, 128), 128, 0, st>>>(views, n_views, slot, sc, count, bp, dec, g2d, gdec);
 }
 
 void launch_project_bwd(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const uint32_t *count,

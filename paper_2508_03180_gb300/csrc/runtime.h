@@ -73,6 +73,8 @@ struct Workspace {
     DevBuf sort_k, sort_v, sort_hist, sort_status, sort_ctr, small, scan;
     DevBuf vview, gvview;         // per (view, cell): v_n as rendered, dL/dv_n
     DevBuf dec;                   // per (view, Gaussian) of neural scenes: decoded values
+    DevBuf gdec;                  // and dL/d of them in the backward
+    DevBuf gscratch;              // sink of the decode adjoint's unrequested outputs
     DevBuf sizes;                 // ChainSizes of a captured chain
     uint32_t *h_small = nullptr;  // pinned mirror of `small`
     ChainSizes *h_sizes = nullptr;

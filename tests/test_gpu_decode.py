@@ -2,7 +2,8 @@
 oracle: the decoded Gaussians of every visible (view, cell) against the FP64
 decode, then the image against the oracle rendering of the GPU's decoded
 FP32 values (so the AABB decisions compare bit for bit), under the
-termination-count protocol; the paths not built refuse neural scenes."""
+termination-count protocol; gradients through the decode against the FP64
+oracle; the paths not built refuse neural scenes."""
 import numpy as np
 import pytest
 import torch
@@ -80,6 +81,92 @@ def test_paths_not_built_refuse_neural_scenes(rctx):
         finally:
             rctx.serve_stop()
         assert e1.value.code == e2.value.code == e3.value.code == L.DGS_ERR_INVALID_ARG
+    finally:
+        rctx.release_state(state)
+        rctx.release_scene(sid)
+
+
+def _neural_oracle_grads(sc, cams, dl_flat, gs, dec):
+    """Per-view oracle gradients through the decode, summed over views; the
+    AABB decisions and tile lists come from the GPU's decoded FP32 values
+    (the oracle's own where nothing was decoded), the per-pixel cell counts
+    from the GPU's forward."""
+    tot, off = None, 0
+    for v, cam in enumerate(cams):
+        gv = view_slices(gs, v)
+        n = 3 * cam.H * cam.W
+        g = dl_flat[off:off + n].astype(np.float64).reshape(3, cam.H, cam.W)
+        off += n
+        vis = np.repeat(gv["rect"][:, 0] >= 0, sc.K)
+        ref = oracle.decode_view(sc, cam.as_array())
+        take = lambda a, b, w: np.where(vis[:, None], a, b.reshape(-1, w)).astype(np.float32)
+        d = dec[v]
+        decided = (take(d[:, 0:3], ref["mean"], 3), take(d[:, 3:6], ref["scale"], 3), take(d[:, 6:10], ref["quat"], 4))
+        _, r = oracle.neural_render_and_grad(sc, cam.as_array(), g, decided=decided, ndone=gv["nd"])
+        r = {k: r[k] for k in ("mlp", "feat", "offset")}
+        tot = r if tot is None else {k: tot[k] + r[k] for k in tot}
+    return tot
+
+
+@pytest.mark.parametrize("F,H,K,stretch,location", [(8, 12, 4, 1.0, "device"), (12, 16, 6, 1.6, "host")])
+def test_gradients_through_the_decode(rctx, F, H, K, stretch, location):
+    """dL/d(weights, features, offsets) summed over two views against the
+    FP64 oracle.  stretch > 1 pushes some offsets outside the unit ball (the
+    projection onto it); host outputs go through the staging path."""
+    from paper_2508_03180_gb300 import _lib as L
+    from oracle import decode as odec
+    from tests.test_gpu_grad import assert_close_group
+    sc = synth.neural_scene(n_cells=160, K=K, F=F, H=H, seed=7 + K, box=0.5, axes_lo=0.15, axes_hi=0.4)
+    sc.neural["offset"][:] *= stretch
+    cams = synth.sphere_cameras(2, 3.0, 48, 40, seed0=5)
+    P = odec.packed_size(F, H, K)
+    sid = rctx.upload_scene(sc)
+    flat, state, _ = rctx.render(sid, cams, want_state=True)
+    dl = torch.randn(flat.numel(), generator=torch.Generator().manual_seed(K)).cuda()
+    if location == "device":
+        gr = dict(g_mlp=torch.zeros(P, device="cuda"), g_feat=torch.zeros(sc.N, F, device="cuda"),
+                  g_offset=torch.zeros(sc.G, 3, device="cuda"))
+        rctx.backward(state, dl, gr)
+    else:
+        gr = dict(g_mlp=np.zeros(P, np.float32), g_feat=np.zeros((sc.N, F), np.float32),
+                  g_offset=np.zeros((sc.G, 3), np.float32))
+        rctx.backward(state, dl, gr, location=L.DGS_HOST)
+    torch.cuda.synchronize()
+    try:
+        gs = read_state(rctx, state, sc, cams)
+        dec = rctx.read(state, L.DGS_BUF_DECODED, np.float32, (len(cams), sc.G, 14))
+        ref = _neural_oracle_grads(sc, cams, dl.cpu().numpy(), gs, dec)
+        got = {k: (v.cpu().numpy() if isinstance(v, torch.Tensor) else v) for k, v in gr.items()}
+        for k, name in (("g_mlp", "mlp"), ("g_feat", "feat"), ("g_offset", "offset")):
+            assert np.abs(ref[name]).max() > 0, name
+            assert_close_group(name, got[k], ref[name])
+        if stretch > 1.0:
+            on = np.linalg.norm(sc.neural["offset"].astype(np.float64).reshape(-1, 3), axis=1)
+            assert (on > 1.0).any() and (on < 1.0).any()
+    finally:
+        rctx.release_state(state)
+        rctx.release_scene(sid)
+
+
+def test_second_backward_and_partial_outputs(rctx):
+    """A second backward on the same state gives the same gradients; asking
+    for the weights alone gives the same weights."""
+    sc = synth.neural_scene(n_cells=120, K=3, F=6, H=8, seed=21, box=0.5, axes_lo=0.15, axes_hi=0.4)
+    from oracle import decode as odec
+    P = odec.packed_size(6, 8, 3)
+    cams = [synth.small_camera(40, 32)]
+    sid = rctx.upload_scene(sc)
+    flat, state, _ = rctx.render(sid, cams, want_state=True)
+    dl = torch.randn(flat.numel(), generator=torch.Generator().manual_seed(3)).cuda()
+    try:
+        a = dict(g_mlp=torch.zeros(P, device="cuda"), g_feat=torch.zeros(sc.N, 6, device="cuda"),
+                 g_offset=torch.zeros(sc.G, 3, device="cuda"), g_cell_v=torch.zeros(sc.N, device="cuda"))
+        rctx.backward(state, dl, a)
+        b = dict(g_mlp=torch.zeros(P, device="cuda"))
+        rctx.backward(state, dl, b)
+        torch.cuda.synchronize()
+        assert a["g_mlp"].abs().max() > 0 and a["g_cell_v"].abs().max() > 0
+        assert torch.allclose(a["g_mlp"], b["g_mlp"], rtol=1e-5, atol=1e-6 * float(a["g_mlp"].abs().max()))
     finally:
         rctx.release_state(state)
         rctx.release_scene(sid)
