@@ -379,6 +379,71 @@ def small_fwdbwd_bench(rctx, steps=10):
         rctx.release_scene(sid)
 
 
+def neural_fwdbwd_bench(rctx, fp32_tflops, steps=5, F=32, H=32, K=10):
+    """Neural cells (Sec. III-IV: four one-hidden-layer decoders per cell,
+    random weights) on the multi-scale layout (100,000 cells x 10 Gaussians
+    in [-10,10]^3, semi-axes over [0.001, 1]), the headline's 8 views at
+    1920x1080, L1 loss, forward + backward to the weights, features and
+    offsets.  The decode and its adjoint are FP32-issue bound; their FLOPs per
+    decoded (view, cell) are counted from the kernels' loops."""
+    import torch
+
+    from paper_2508_03180_gb300 import _lib as L
+    from paper_2508_03180_gb300 import synth
+    scene = synth.neural_scene(n_cells=100_000, K=K, F=F, H=H, seed=0, box=10.0, axes_lo=0.001, axes_hi=1.0)
+    sid = rctx.upload_scene(scene)
+    try:
+        cams = cameras_for(0)
+        slots = rctx.set_cameras(cams)
+        n = len(cams) * 3 * H_IMG * W_IMG
+        img, dl = torch.empty(n, device="cuda"), torch.empty(n, device="cuda")
+        loss = torch.empty(1, device="cuda")
+        target = torch.from_numpy(synth.target_image(len(cams), H_IMG, W_IMG, seed=7)).cuda().reshape(-1)
+        P = sum(H * (F + 4) + H + o * H + o for o in (K, 3 * K, 3 * K, 4 * K))  # packed decoder weights
+        grads = dict(g_mlp=torch.empty(P, device="cuda"), g_feat=torch.empty(scene.N, F, device="cuda"),
+                     g_offset=torch.empty(scene.G, 3, device="cuda"))
+        stats = {}
+
+        def step():
+            _, state, st = rctx.render(sid, cams, want_state=True, out=img, slots=slots, stats=True)
+            stats["visible"] = int(st.visible_cells)
+            rctx.loss_l1(img, target, dl, loss)
+            rctx.backward(state, dl, grads)
+            rctx.release_state(state)
+
+        for _ in range(3):
+            step()
+        torch.cuda.synchronize()
+        rctx.profile_enable(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            step()
+        e1.record()
+        torch.cuda.synchronize()
+        prof = rctx.profile_read()
+        rctx.profile_enable(False)
+        ms = e0.elapsed_time(e1) / steps
+        vis = stats["visible"]
+        fma_fwd = 4 * H * (F + 4) + 11 * K * H
+        fma_bwd = 4 * H * (F + 4) + 2 * 11 * K * H + 4 * H * F + 4 * H * (F + 5) + 11 * K * (H + 1)
+        out = {"workload": f"neural 100,000 cells x {K} Gaussians, F={F}, H={H}, multi-scale layout, "
+                           f"{len(cams)} views {W_IMG}x{H_IMG} fwd+bwd L1",
+               "ms_per_step": ms, "mpix_s": len(cams) * W_IMG * H_IMG / (ms / 1e3) / 1e6,
+               "decoded_view_cells_per_step": vis,
+               "stage_ms_per_step": {k: v[0] / steps for k, v in prof.items() if v[1] > 0}}
+        for name, fma in (("decode", fma_fwd), ("decode_bwd", fma_bwd)):
+            t = prof[name][0] / steps
+            if vis and t > 0:
+                tf = 2.0 * fma * vis / (t / 1e3) / 1e12
+                out[name] = {"ms": t, "flop_per_view_cell": 2 * fma, "tflops": tf,
+                             "frac": tf / fp32_tflops if fp32_tflops else None,
+                             "peak": "FP32 FMA rate of measured (dgs_probe_alu)"}
+        return out
+    finally:
+        rctx.release_scene(sid)
+
+
 def torch_empty(n):
     import torch
     return torch.empty(n, device="cuda")
@@ -561,6 +626,7 @@ def main():
         try:
             line["comparators"] = comparators_bench(rctx)
             line["small_fwd_bwd"] = small_fwdbwd_bench(rctx)
+            line["neural_fwd_bwd"] = neural_fwdbwd_bench(rctx, alu.get("fp32_tflops") if alu else None)
         except Exception as e:  # reported beside the headline, never instead of it
             line["comparators"] = {"error": str(e)}
     if rank == 0 and not args.no_serve:
@@ -621,10 +687,10 @@ def streaming_stages(prof, steps, nv, scene, stats, peaks):
 def launches_per_step(stats):
     # kernels of one fwd+bwd step: cell projection 1; depth sort 2 + 4 passes; gather 1; scan 3;
     # emit 1; tile sort 2 + ceil(bits/8) passes; ranges 1; projection 1; blend 1; loss 2;
-    # blend adjoint 1; projection adjoint 1
+    # blend adjoint 1; projection adjoint 2 (geometry, then colour)
     tiles = int(stats.num_tiles)
     bits = max(1, math.ceil(math.log2(max(2, tiles))))
-    return 1 + (2 + 4) + 1 + 3 + 1 + (2 + math.ceil(bits / 8)) + 1 + 1 + 1 + 2 + 1 + 1
+    return 1 + (2 + 4) + 1 + 3 + 1 + (2 + math.ceil(bits / 8)) + 1 + 1 + 1 + 2 + 1 + 2
 
 
 if __name__ == "__main__":

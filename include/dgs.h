@@ -285,7 +285,9 @@ enum {
     DGS_STAGE_BLEND_FWD = 7,    /* a7 */
     DGS_STAGE_BLEND_BWD = 8,    /* a8 */
     DGS_STAGE_PROJECT_BWD = 9,  /* a9 */
-    DGS_STAGE_COUNT = 10
+    DGS_STAGE_DECODE = 10,      /* neural scenes: per-view decode of the visible cells' Gaussians */
+    DGS_STAGE_DECODE_BWD = 11,  /* neural scenes: gradients through the decode */
+    DGS_STAGE_COUNT = 12
 };
 typedef struct {
     double ms[16];

@@ -83,7 +83,7 @@ class dgs_profile(C.Structure):
 
 
 STAGES = ["cell_project", "depth_sort", "count_scan", "emit", "tile_sort", "tile_ranges", "project_fwd",
-          "blend_fwd", "blend_bwd", "project_bwd"]
+          "blend_fwd", "blend_bwd", "project_bwd", "decode", "decode_bwd"]
 
 
 class dgs_request(C.Structure):

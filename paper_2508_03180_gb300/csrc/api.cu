@@ -597,19 +597,21 @@ dgs_status chain_forward(dgs_ctx *ctx, Workspace &ws, const std::vector<ChainVie
         (s = ws.ndpix.ensure(4 * px1)) || ((keep_rgb || !out_img) && (s = ws.rgb.ensure(12 * px1))))
         return s;
     const ViewDesc *dv = (const ViewDesc *)ws.views.p;
-    {
-        StageTimer t(ctx->prof, DGS_STAGE_PROJECT_FWD, st);
-        for (int k = 0; k < S; ++k) {
-            const SceneDev sd = slots[k]->dev();
-            if (slots[k]->F > 0) {  // neural cells: decode the visible cells' Gaussians for every view first
+    for (int k = 0; k < S; ++k) {
+        const SceneDev sd = slots[k]->dev();
+        if (slots[k]->F > 0) {  // neural cells: decode the visible cells' Gaussians for every view first
+            {
+                StageTimer t(ctx->prof, DGS_STAGE_DECODE, st);
                 launch_decode(dv, V, k, sd, (const uint32_t *)ws.count.p, (float *)ws.dec.p, st);
-                launch_project_neural(dv, V, k, sd, (const uint32_t *)ws.count.p, (const float *)ws.vview.p,
-                                      (const float *)ws.dec.p, bp, (float4 *)ws.rec.p,
-                                      grad_buffers ? (float *)ws.g2d.p : nullptr, st);
-            } else {
-                launch_project_fwd(dv, V, k, sd, (const uint32_t *)ws.count.p, (const float *)ws.vview.p, bp,
-                                   (float4 *)ws.rec.p, grad_buffers ? (float *)ws.g2d.p : nullptr, st);
             }
+            StageTimer t(ctx->prof, DGS_STAGE_PROJECT_FWD, st);
+            launch_project_neural(dv, V, k, sd, (const uint32_t *)ws.count.p, (const float *)ws.vview.p,
+                                  (const float *)ws.dec.p, bp, (float4 *)ws.rec.p,
+                                  grad_buffers ? (float *)ws.g2d.p : nullptr, st);
+        } else {
+            StageTimer t(ctx->prof, DGS_STAGE_PROJECT_FWD, st);
+            launch_project_fwd(dv, V, k, sd, (const uint32_t *)ws.count.p, (const float *)ws.vview.p, bp,
+                               (float4 *)ws.rec.p, grad_buffers ? (float *)ws.g2d.p : nullptr, st);
         }
     }
     float *img = out_img ? out_img : (float *)ws.rgb.p;
@@ -764,7 +766,6 @@ extern "C" dgs_status dgs_render_backward(dgs_ctx *ctx, dgs_fwd_state *state, co
         if (gv) launch_cell_v_grad((const ViewDesc *)ws.views.p, ws.V, sc.dev(), gv, o_v, o_vsh, st);
     }
     if (neural && (o_mlp || o_f || o_off)) {
-        StageTimer t(ctx->prof, DGS_STAGE_PROJECT_BWD, st);
         if ((s = ws.gdec.ensure(sizeof(float) * kDecF * std::max(1LL, ws.n_records)))) return s;
         // the decode writes every output of every cell; unrequested ones go to scratch
         float *gscr = nullptr;
@@ -773,9 +774,13 @@ extern "C" dgs_status dgs_render_backward(dgs_ctx *ctx, dgs_fwd_state *state, co
             gscr = (float *)ws.gscratch.p;
         }
         float *m = o_mlp ? o_mlp : gscr, *f = o_f ? o_f : gscr + P, *off = o_off ? o_off : gscr + P + NF;
+        {
+            StageTimer t(ctx->prof, DGS_STAGE_PROJECT_BWD, st);
+            launch_project_bwd_neural((const ViewDesc *)ws.views.p, ws.V, 0, sc.dev(), (const uint32_t *)ws.count.p,
+                                      bp, (const float *)ws.dec.p, (const float *)ws.g2d.p, (float *)ws.gdec.p, st);
+        }
+        StageTimer t(ctx->prof, DGS_STAGE_DECODE_BWD, st);
         CK(cudaMemsetAsync(m, 0, sizeof(float) * P, st));
-        launch_project_bwd_neural((const ViewDesc *)ws.views.p, ws.V, 0, sc.dev(), (const uint32_t *)ws.count.p, bp,
-                                  (const float *)ws.dec.p, (const float *)ws.g2d.p, (float *)ws.gdec.p, st);
         launch_decode_bwd((const ViewDesc *)ws.views.p, ws.V, 0, sc.dev(), (const uint32_t *)ws.count.p,
                           (const float *)ws.gdec.p, m, f, off, st);
     } else if (!neural) {
