@@ -445,3 +445,15 @@ def neural_render_and_grad(scene, cam, dL_dC, decided=None, opt: Options = Optio
     for name, g_, ref in zip(("mean", "scale", "quat", "opac", "rgb"), grads[3:], dec_vals):
         res["dec_" + name] = z(g_, ref).reshape(G, -1)
     return img, res
+
+
+# --------------------------------------------------------------------------
+# Cell alignment (Sec. IV-B, Eq. 10 and the centre update)
+
+
+def cell_align(scene, cam=None):
+    """New (centre (N,3), quaternion (N,4)) of every cell in FP64; neural
+    scenes decode sigma and q for the eye of `cam`."""
+    from . import align as _align
+    eye = None if cam is None else np.asarray(cam, dtype=np.float64)[19:22]
+    return _align.align(scene, eye)
