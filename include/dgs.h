@@ -357,6 +357,31 @@ dgs_status dgs_render_compare(dgs_ctx *ctx, uint32_t scene_id, int32_t n_views, 
                               const dgs_compare_config *cfg, float *out_rgb, int32_t *out_ndone,
                               dgs_stream stream, dgs_stats *stats);
 
+/* -------------------------------------------------------- cell alignment */
+
+/* Cell alignment (Sec. IV-B), in place on the device: for every cell n,
+ *   DGS_ALIGN_QUAT    Q_n = norm( sum_k sigma_{n,k} q_{n,k} )          (Eq. 10)
+ *   DGS_ALIGN_CENTER  x_n = (1/K) sum_k mu_{n,k}
+ * (what = either or both), computed from the values before the call.
+ * q_{n,k} is the Gaussian's unit quaternion; quaternions are summed as
+ * stored (no hemisphere alignment), and a cell whose weighted sum is the
+ * zero vector keeps its Q_n.  Explicit scenes: sigma = sigmoid(logit),
+ * mu = the Gaussian's mean; their Gaussians do not move.  Neural scenes:
+ * mu = x_n + R(Q_n)(O_pos S_n) (view-independent); sigma and q are decoded
+ * for the eye of camera slot cam_slot (required with DGS_ALIGN_QUAT,
+ * ignored otherwise), sigma <= 0 weighing 0; their Gaussians move with the
+ * cell (the offsets are in the cell's frame).
+ * out_center [N][3], out_quat [N][4] (nullable): the new values, in
+ * out_location memory (host outputs synchronise the stream).  Runs on
+ * `stream`; renders of the scene on other streams must be ordered against
+ * it by the caller (as for dgs_scene_update).
+ * Errors: INVALID_ARG (what, location, camera slot unset for a neural
+ * DGS_ALIGN_QUAT), NOT_FOUND (scene), OOM. */
+#define DGS_ALIGN_QUAT 1
+#define DGS_ALIGN_CENTER 2
+dgs_status dgs_cell_align(dgs_ctx *ctx, uint32_t scene_id, int32_t what, int32_t cam_slot, float *out_center,
+                          float *out_quat, int32_t out_location, dgs_stream stream);
+
 /* ------------------------------------------------------------------ probes */
 
 /* Measured issue rates for the blend kernels' roofline (they are bound by

@@ -103,6 +103,8 @@ class dgs_alu_peaks(C.Structure):
 DGS_SERVE_NO_GRAPHS = 1
 DGS_COMPARE_ALPHA = 1
 DGS_COMPARE_WSR = 2
+DGS_ALIGN_QUAT = 1
+DGS_ALIGN_CENTER = 2
 
 
 class dgs_compare_config(C.Structure):
@@ -137,6 +139,7 @@ _SIGS = {
     "dgs_render_compare": (C.c_int32, [_P, C.c_uint32, C.c_int32, C.POINTER(C.c_uint32),
                                        C.POINTER(dgs_compare_config), _P, _P, _P, C.POINTER(dgs_stats)]),
     "dgs_probe_alu": (C.c_int32, [_P, C.POINTER(dgs_alu_peaks)]),
+    "dgs_cell_align": (C.c_int32, [_P, C.c_uint32, C.c_int32, C.c_int32, _P, _P, C.c_int32, _P]),
     "dgs_serve_start": (C.c_int32, [_P, C.c_int32, C.c_int32, C.c_int32]),
     "dgs_serve_read_stats": (C.c_int32, [_P, C.POINTER(dgs_serve_stats)]),
     "dgs_serve_stop": (C.c_int32, [_P]),
@@ -285,6 +288,11 @@ def dgs_profile_read(ctx) -> dgs_profile:
     p = dgs_profile()
     check(load().dgs_profile_read(ctx, C.byref(p)), ctx)
     return p
+
+
+def dgs_cell_align(ctx, scene_id: int, what: int, cam_slot: int, center_ptr, quat_ptr, location: int, stream):
+    check(load().dgs_cell_align(ctx, scene_id, what, cam_slot, _P(center_ptr) if center_ptr else None,
+                                _P(quat_ptr) if quat_ptr else None, location, stream), ctx)
 
 
 def dgs_probe_alu(ctx) -> dgs_alu_peaks:

@@ -34,11 +34,6 @@ dgs_status cuda_error(cudaError_t e, const char *what) {
                      std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-#define CK(x)                                                 \
-    do {                                                      \
-        cudaError_t e_ = (x);                                 \
-        if (e_ != cudaSuccess) return cuda_error(e_, #x);     \
-    } while (0)
 
 dgs_status DevBuf::ensure(size_t bytes) {
     if (bytes <= cap) return DGS_OK;

@@ -155,11 +155,6 @@ __global__ void __launch_bounds__(CT) k_gauss_blend(const ViewDesc *__restrict__
 
 using namespace dgs;
 
-#define CK(x)                                                 \
-    do {                                                      \
-        cudaError_t e_ = (x);                                 \
-        if (e_ != cudaSuccess) return cuda_error(e_, #x);     \
-    } while (0)
 
 namespace {
 

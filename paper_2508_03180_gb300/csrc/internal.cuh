@@ -177,6 +177,11 @@ void launch_project_neural(const ViewDesc *views, int n_views, int slot, const S
 void launch_project_bwd_neural(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const uint32_t *count,
                                const BlendParams &bp, const float *dec, const float *g2d, float *gdec,
                                cudaStream_t st);
+// Cell alignment (Sec. IV-B, Eq. 10 and the centre update) of every cell,
+// in place in `cell` (the scene's writable cell planes); dec: decoded values
+// of one view for every Gaussian (neural scenes with DGS_ALIGN_QUAT).
+void launch_cell_align(const SceneDev &sc, float *cell, const float *dec, int what, float *out_center, float *out_quat,
+                       cudaStream_t st);
 void launch_decode_bwd(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const uint32_t *count,
                        const float *gdec, float *g_mlp, float *g_feat, float *g_offset, cudaStream_t st);
 // One launch for every scene of the device scene table (dsz->n_scenes

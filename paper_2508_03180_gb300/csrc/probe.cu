@@ -50,11 +50,6 @@ __global__ void __launch_bounds__(PROBE_THREADS) k_probe_ex2(float *out, int ite
 
 using namespace dgs;
 
-#define CK(x)                                                 \
-    do {                                                      \
-        cudaError_t e_ = (x);                                 \
-        if (e_ != cudaSuccess) return cuda_error(e_, #x);     \
-    } while (0)
 
 namespace {
 

@@ -32,6 +32,14 @@ constexpr int kSmallWork = 5;     // work counter of the pulling blend (captured
 dgs_status set_error(dgs_status code, const std::string &msg);
 dgs_status cuda_error(cudaError_t e, const char *what);
 
+// Returns the recorded error status from the enclosing ABI function when a
+// CUDA call fails.
+#define CK(x)                                                 \
+    do {                                                      \
+        cudaError_t e_ = (x);                                 \
+        if (e_ != cudaSuccess) return cuda_error(e_, #x);     \
+    } while (0)
+
 // Grow-only device allocation.
 struct DevBuf {
     void *p = nullptr;
@@ -207,6 +215,7 @@ struct dgs_ctx {
     std::vector<std::unique_ptr<dgs::Workspace>> pool;
     std::set<dgs_fwd_state *> live_states;
     dgs::DevBuf aux, loss_partial;
+    dgs::DevBuf align_tmp;  // dgs_cell_align: one view's decode and host staging
     std::unique_ptr<dgs::Workspace> sort_ws;
     std::unique_ptr<dgs::ServeState> serve;
     uint64_t scene_epoch = 0;  // bumped when a scene's buffers go away

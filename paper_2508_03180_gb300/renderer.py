@@ -219,6 +219,20 @@ class Context:
         p = L.dgs_profile_read(self.ctx)
         return {name: (p.ms[i], p.launches[i]) for i, name in enumerate(L.STAGES)}
 
+    def cell_align(self, scene_id: int, quat: bool = True, center: bool = True, cam=None,
+                   out_center=None, out_quat=None):
+        """Cell alignment (Sec. IV-B) in place: Q_n by Eq. 10 and/or x_n as the
+        mean of the Gaussians' centres.  Neural scenes need `cam` for Eq. 10.
+        out_center [N][3] / out_quat [N][4]: optional tensors (device) or
+        arrays (host) that receive the new values."""
+        what = (L.DGS_ALIGN_QUAT if quat else 0) | (L.DGS_ALIGN_CENTER if center else 0)
+        slot = self.set_cameras([cam])[0] if cam is not None else -1
+        outs = [a for a in (out_center, out_quat) if a is not None]
+        host = bool(outs) and not isinstance(outs[0], torch.Tensor)
+        ptr = lambda a: None if a is None else (a.ctypes.data if host else a.data_ptr())
+        L.dgs_cell_align(self.ctx, scene_id, what, slot, ptr(out_center), ptr(out_quat),
+                         L.DGS_HOST if host else L.DGS_DEVICE, _stream())
+
     def probe_alu(self) -> dict:
         r = L.dgs_probe_alu(self.ctx)
         return {"fp32_tflops": r.fp32_tflops, "ex2_per_s": r.ex2_per_s, "ms_fma": r.ms_fma, "ms_ex2": r.ms_ex2,
