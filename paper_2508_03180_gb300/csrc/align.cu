@@ -130,9 +130,10 @@ extern "C" dgs_status dgs_cell_align(dgs_ctx *ctx, uint32_t scene_id, int32_t wh
     const long long N = sc.N, G = sc.G;
     if (N == 0) return DGS_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    // scratch: [view][count N][decoded G][host staging 7 N], each 256-byte aligned
+    // scratch: [view][packed weights][decoded G][host staging 7 N], each 256-byte aligned
     auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
-    const size_t o_cnt = up(sizeof(ViewDesc)), o_dec = o_cnt + up(decode ? 4 * N : 0),
+    const size_t o_pk = up(sizeof(ViewDesc)),
+                 o_dec = o_pk + up(decode ? sizeof(float) * decode_pack_floats(sc.F, sc.H, sc.K) : 0),
                  o_stg = o_dec + up(decode ? sizeof(float) * kDecF * G : 0),
                  total = o_stg + (out_location == DGS_HOST ? sizeof(float) * 7 * N : 0);
     dgs_status s;
@@ -143,9 +144,8 @@ extern "C" dgs_status dgs_cell_align(dgs_ctx *ctx, uint32_t scene_id, int32_t wh
     if (decode) {
         const ViewDesc v = make_view(ctx->cams[cam_slot], 0, 0, 0, sc, 0, 0);
         CK(cudaMemcpyAsync(base, &v, sizeof(v), cudaMemcpyHostToDevice, st));  // pageable: staged before return
-        CK(cudaMemsetAsync(base + o_cnt, 1, 4 * N, st));                        // every cell decoded
         dec = (float *)(base + o_dec);
-        launch_decode((const ViewDesc *)base, 1, 0, sd, (const uint32_t *)(base + o_cnt), dec, st);
+        launch_decode((const ViewDesc *)base, 1, 0, sd, nullptr, N, dec, (float *)(base + o_pk), st);  // every cell
     }
     float *oc = out_center, *oq = out_quat;
     if (out_location == DGS_HOST) {

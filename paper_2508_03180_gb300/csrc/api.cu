@@ -269,7 +269,7 @@ static dgs_status fill_scene(dgs_ctx *ctx, Scene &sc, const dgs_scene_desc *d, c
     if (d->cell_v) parts.push_back({d->cell_v, N, 1, cell + 10 * N, N});
     if (sc.vdeg >= 0 && d->cell_v_sh) parts.push_back({d->cell_v_sh, N, sc.Cv, (float *)sc.vsh.p, N});
     if (sc.F > 0) {  // neural cells: features and offsets as planes, the weights as given (one row)
-        parts.push_back({d->neural->cell_feat, N, sc.F, (float *)sc.feat.p, N});
+        parts.push_back({d->neural->cell_feat, N * sc.F, 1, (float *)sc.feat.p, N * sc.F});  // rows [N][F]
         parts.push_back({d->neural->g_offset, G, 3, (float *)sc.goff.p, G});
         parts.push_back({d->neural->mlp, 1, neural_weights(sc), (float *)sc.mlp.p, 1});
     } else {
@@ -506,6 +506,7 @@ static dgs_status run_binning(dgs_ctx *ctx, Workspace &ws, cudaStream_t st) {
     if (ws.h_small[kSmallSortErr]) return set_error(DGS_ERR_TIMEOUT, "radix sort look-back wait gave up");
     const long long L = ws.h_small[kSmallTotal];
     ws.L = L;
+    ws.n_vis = ws.h_small[kSmallVisible];
     if ((s = ws.tkey.ensure(4 * std::max(1LL, L))) || (s = ws.tval.ensure(4 * std::max(1LL, L)))) return s;
     if ((s = ensure_sort_scratch(ws, L))) return s;
     if ((s = ws.ranges.ensure(8 * (size_t)std::max(1, ws.total_tiles)))) return s;
@@ -586,7 +587,11 @@ dgs_status chain_forward(dgs_ctx *ctx, Workspace &ws, const std::vector<ChainVie
     const long long nrec = std::max(1LL, ws.n_records), px1 = std::max(1LL, px);
     bool any_neural = false;
     for (const Scene *sc : slots) any_neural = any_neural || sc->F > 0;
+    long long npk = 0;
+    for (const Scene *sc : slots)
+        if (sc->F > 0) npk = std::max(npk, decode_pack_floats(sc->F, sc->H, sc->K));
     if ((any_neural && (s = ws.dec.ensure(sizeof(float) * kDecF * nrec))) ||
+        (any_neural && (s = ws.wpack.ensure(sizeof(float) * npk))) ||
         (s = ws.rec.ensure(sizeof(float4) * kRecF4 * nrec)) ||
         (grad_buffers && (s = ws.g2d.ensure(sizeof(float) * kGradF * nrec))) || (s = ws.Dpix.ensure(4 * px1)) ||
         (s = ws.ndpix.ensure(4 * px1)) || ((keep_rgb || !out_img) && (s = ws.rgb.ensure(12 * px1))))
@@ -597,7 +602,8 @@ dgs_status chain_forward(dgs_ctx *ctx, Workspace &ws, const std::vector<ChainVie
         if (slots[k]->F > 0) {  // neural cells: decode the visible cells' Gaussians for every view first
             {
                 StageTimer t(ctx->prof, DGS_STAGE_DECODE, st);
-                launch_decode(dv, V, k, sd, (const uint32_t *)ws.count.p, (float *)ws.dec.p, st);
+                launch_decode(dv, V, k, sd, (const uint32_t *)ws.zval.p, ws.n_vis, (float *)ws.dec.p,
+                              (float *)ws.wpack.p, st);
             }
             StageTimer t(ctx->prof, DGS_STAGE_PROJECT_FWD, st);
             launch_project_neural(dv, V, k, sd, (const uint32_t *)ws.count.p, (const float *)ws.vview.p,
@@ -762,12 +768,12 @@ extern "C" dgs_status dgs_render_backward(dgs_ctx *ctx, dgs_fwd_state *state, co
     }
     if (neural && (o_mlp || o_f || o_off)) {
         if ((s = ws.gdec.ensure(sizeof(float) * kDecF * std::max(1LL, ws.n_records)))) return s;
-        // the decode writes every output of every cell; unrequested ones go to scratch
-        float *gscr = nullptr;
-        if (!o_mlp || !o_f || !o_off) {
-            if ((s = ws.gscratch.ensure(sizeof(float) * std::max(1LL, P + NF + GO)))) return s;
-            gscr = (float *)ws.gscratch.p;
-        }
+        // the decode adjoint forms every output; unrequested ones go to scratch after its rows
+        const long long nrow = decode_bwd_scratch_floats(sc.F, sc.H, sc.K, ws.n_vis);
+        if ((s = ws.gscratch.ensure(sizeof(float) * (nrow + P + NF + GO))) ||
+            (s = ws.wpack.ensure(sizeof(float) * decode_pack_floats(sc.F, sc.H, sc.K))))
+            return s;
+        float *rows = (float *)ws.gscratch.p, *gscr = rows + nrow;
         float *m = o_mlp ? o_mlp : gscr, *f = o_f ? o_f : gscr + P, *off = o_off ? o_off : gscr + P + NF;
         {
             StageTimer t(ctx->prof, DGS_STAGE_PROJECT_BWD, st);
@@ -776,8 +782,10 @@ extern "C" dgs_status dgs_render_backward(dgs_ctx *ctx, dgs_fwd_state *state, co
         }
         StageTimer t(ctx->prof, DGS_STAGE_DECODE_BWD, st);
         CK(cudaMemsetAsync(m, 0, sizeof(float) * P, st));
-        launch_decode_bwd((const ViewDesc *)ws.views.p, ws.V, 0, sc.dev(), (const uint32_t *)ws.count.p,
-                          (const float *)ws.gdec.p, m, f, off, st);
+        CK(cudaMemsetAsync(f, 0, sizeof(float) * NF, st));
+        CK(cudaMemsetAsync(off, 0, sizeof(float) * GO, st));
+        launch_decode_bwd((const ViewDesc *)ws.views.p, ws.V, 0, sc.dev(), (const uint32_t *)ws.zval.p, ws.n_vis,
+                          (const float *)ws.gdec.p, m, f, off, rows, (float *)ws.wpack.p, st);
     } else if (!neural) {
         StageTimer t(ctx->prof, DGS_STAGE_PROJECT_BWD, st);
         launch_project_bwd((const ViewDesc *)ws.views.p, ws.V, 0, sc.dev(), (const uint32_t *)ws.count.p, bp,

@@ -5,362 +5,729 @@
 // 8-11).  Activations: opacity tanh (sigma <= 0 is not drawn), colour
 // sigmoid, scale ratio sigmoid bounded by 1 - |O_pos| (Eq. 11) times the cell
 // semi-axes S_n (Eq. 8), rotation normalised (a zero output is the identity
-// rotation); centre x_n + R(Q_n)(O_pos * S_n)
-// with O_pos moved into the unit ball (the centre stays inside the cell).
+// rotation); centre x_n + R(Q_n)(O_pos * S_n) with O_pos moved into the unit
+// ball (the centre stays inside the cell).
+//
+// The unit of work is a sample: one (view, cell) entry that survived culling
+// (the first entries of the depth-sorted entry list).  A CTA takes M samples
+// at a time (8 per warp: 64 with eight warps, fewer where the widths need
+// more shared memory) and runs the four decoders as two dense products from
+// shared memory:
+//   layer 1  H[M x 4Hp] = relu(Z[M x I] W1^T + b1)   (the decoders side by side)
+//   layer 2  O[M x Rp]  = H_D W2_D^T + b2 per decoder  (block diagonal)
+// with I = F + 4 inputs, Hp = H rounded up (zero hidden units) and the
+// decoders' output blocks rounded up to 4 (zero outputs), Rp in total.  A
+// lane keeps 8 samples x 4 (or 8) outputs in registers; the inputs of a
+// sample are broadcast to the warp, the weights are read as float4 rows.
+// Sample-minor arrays keep one row per unit with the M samples contiguous
+// (row stride M + 4 floats); decoder blocks are staggered by 8 floats so lanes
+// of different decoders reading the same row index hit distinct banks.
 #include <algorithm>
 
 #include "internal.cuh"
 
 namespace dgs {
 
-constexpr int DEC_THREADS = 64;
-constexpr int DEC_MAXW = 64;  // maximum feature / hidden width
+constexpr int DINFO = 20;     // words of per-sample information
+constexpr int kSmemMax = 227 * 1024;
+
+struct MlpShape {
+    int W, M, LD;                        // warps per CTA, samples per tile (8 per warp), sample-row stride
+    int F, H, K, I, Hp, HW, P;
+    int nout[4], rb[5];                  // output widths; padded output block bases (rb[4] = Rp)
+    int w1o[4], b1o[4], w2o[4], b2o[4];  // packed weight offsets per decoder
+    // shared-memory layout (floats)
+    int s_w, s_b1, s_b2, s_z, s_h, s_o, s_dh, s_info, s_total;
+    // backward rows per sample: Z [I], H [4Hp], dL/dh [4Hp], dL/do [Rp]
+    int row_z, row_h, row_dh, row_do, row_all;
+    // the weights in their shared-memory layouts, packed once per call in global memory:
+    // W1^T [I][4Hp], b1 [4Hp], b2 [Rp], W2^T [Hp][Rp], W2 [Rp][Hp], W1 [4Hp][I]
+    int g_w1t, g_b1, g_b2, g_w2t, g_w2, g_w1r, g_total;
+};
+
+static int up_to(int x, int m) { return (x + m - 1) / m * m; }
+
+// Layout for W warps per CTA (W = 8, 4 or 2: the largest whose shared memory fits).
+static MlpShape mlp_shape_w(int F, int H, int K, bool bwd, int W) {
+    MlpShape S{};
+    S.W = W; S.M = 8 * W; S.LD = S.M + 4;
+    const int DM = S.M, DLM = S.LD;
+    S.F = F; S.H = H; S.K = K; S.I = F + 4;
+    S.HW = 4 * up_to(H, 4) <= 128 ? 4 : 8;
+    S.Hp = up_to(H, S.HW);
+    const int outs[4] = {K, 3 * K, 3 * K, 4 * K};
+    int o = 0;
+    S.rb[0] = 0;
+    for (int D = 0; D < 4; ++D) {
+        S.nout[D] = outs[D];
+        S.rb[D + 1] = S.rb[D] + up_to(outs[D], 4);
+        S.w1o[D] = o; S.b1o[D] = o + H * S.I; S.w2o[D] = S.b1o[D] + H; S.b2o[D] = S.w2o[D] + outs[D] * H;
+        o = S.b2o[D] + outs[D];
+    }
+    S.P = o;
+    const int Rp = S.rb[4], H4 = 4 * S.Hp;
+    int at = 0;
+    auto take = [&](int n) { const int r = at; at += up_to(n, 4); return r; };
+    S.s_w = take(std::max(S.I * H4, S.Hp * Rp));
+    S.s_b1 = take(H4);
+    S.s_b2 = take(Rp);
+    S.s_z = take(S.I * DLM);
+    S.s_h = take(4 * (S.Hp * DLM + 8));
+    S.s_o = take(Rp * DLM + 32);
+    S.s_dh = bwd ? take(4 * (S.Hp * DLM + 8)) : 0;
+    S.s_info = take(DM * DINFO);
+    S.s_total = at;
+    S.row_z = 0; S.row_h = S.I; S.row_dh = S.row_h + H4; S.row_do = S.row_dh + H4; S.row_all = S.row_do + Rp;
+    at = 0;
+    S.g_w1t = take(S.I * H4);
+    S.g_b1 = take(H4);
+    S.g_b2 = take(Rp);
+    S.g_w2t = take(S.Hp * Rp);
+    S.g_w2 = take(Rp * S.Hp);
+    S.g_w1r = take(H4 * S.I);
+    S.g_total = at;
+    return S;
+}
+
+static MlpShape mlp_shape(int F, int H, int K, bool bwd) {
+    MlpShape S = mlp_shape_w(F, H, K, bwd, 8);
+    for (int W = 4; W >= 2 && (size_t)S.s_total * sizeof(float) > (size_t)kSmemMax; W /= 2)
+        S = mlp_shape_w(F, H, K, bwd, W);
+    return S;
+}
 
 __device__ __forceinline__ float sigmoidf_(float x) { return 1.0f / (1.0f + expf(-x)); }
+__device__ __forceinline__ int hrow(const MlpShape &S, int D, int j) { return D * (S.Hp * S.LD + 8) + j * S.LD; }
+__device__ __forceinline__ int orow(const MlpShape &S, int D, int r) { return (S.rb[D] + r) * S.LD + 8 * D; }
+__device__ __forceinline__ int out_block(const MlpShape &S, int rr) {
+    return rr >= S.rb[3] ? 3 : (rr >= S.rb[2] ? 2 : (rr >= S.rb[1] ? 1 : 0));
+}
 
-// One thread per cell of scene `slot`, looping over the views in which the
-// cell survived culling.  The thread's input vector z and hidden vector h
-// live in shared memory columns (z[i] at s_z[i][tid]); the weights are read
-// from global memory, where all threads of a warp read the same address.
-__global__ void __launch_bounds__(DEC_THREADS) k_decode(const ViewDesc *__restrict__ views, int n_views, int slot,
-                                                        SceneDev sc, const uint32_t *__restrict__ count,
-                                                        float *__restrict__ dec) {
-    __shared__ float s_z[DEC_MAXW + 4][DEC_THREADS];
-    __shared__ float s_h[DEC_MAXW][DEC_THREADS];
+// Per-sample information in shared memory.
+struct SampleInfo {
+    int n, valid;
+    long long rec;   // first record (Gaussian k = 0) of this (view, cell)
+    float x[3], S[3], R[9];
+};
+__device__ __forceinline__ void put_info(float *s_info, int s, const SampleInfo &a) {
+    float *p = s_info + s * DINFO;
+    p[0] = __int_as_float(a.n);
+    p[1] = __int_as_float(a.valid);
+    p[2] = __int_as_float((int)(a.rec & 0xffffffffLL));
+    p[3] = __int_as_float((int)(a.rec >> 32));
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { p[4 + i] = a.x[i]; p[7 + i] = a.S[i]; }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) p[10 + i] = a.R[i];
+}
+__device__ __forceinline__ SampleInfo get_info(const float *s_info, int s) {
+    const float *p = s_info + s * DINFO;
+    SampleInfo a;
+    a.n = __float_as_int(p[0]);
+    a.valid = __float_as_int(p[1]);
+    a.rec = (long long)(unsigned)__float_as_int(p[2]) | ((long long)__float_as_int(p[3]) << 32);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { a.x[i] = p[4 + i]; a.S[i] = p[7 + i]; }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) a.R[i] = p[10 + i];
+    return a;
+}
+
+// Stage the samples [q0, q0 + S.M): their information and the input columns
+// Z[i][s] (zero for samples past the end or of another scene slot).
+__device__ void stage_samples(const MlpShape &S, float *sm, const ViewDesc *__restrict__ views, int n_views, int slot,
+                              const SceneDev &sc, const uint32_t *__restrict__ samples, long long nsamp,
+                              long long q0) {
     const int t = threadIdx.x;
-    const long long N = sc.N, G = sc.G;
-    const int K = sc.K, F = sc.F, H = sc.H;
-    const int outs[4] = {K, 3 * K, 3 * K, 4 * K};
-    for (long long n = blockIdx.x * (long long)blockDim.x + t; n < N; n += (long long)gridDim.x * blockDim.x) {
-        const float x0 = sc.cell[n], x1 = sc.cell[N + n], x2 = sc.cell[2 * N + n];
-        const float S[3] = {sc.cell[3 * N + n], sc.cell[4 * N + n], sc.cell[5 * N + n]};
-        float Rq[9];
-        {
-            const float qw = sc.cell[6 * N + n], qx = sc.cell[7 * N + n], qy = sc.cell[8 * N + n],
-                        qz = sc.cell[9 * N + n];
-            const float in = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
-            const float w = qw * in, x = qx * in, y = qy * in, z = qz * in;
-            Rq[0] = 1.f - 2.f * (y * y + z * z); Rq[1] = 2.f * (x * y - w * z); Rq[2] = 2.f * (x * z + w * y);
-            Rq[3] = 2.f * (x * y + w * z); Rq[4] = 1.f - 2.f * (x * x + z * z); Rq[5] = 2.f * (y * z - w * x);
-            Rq[6] = 2.f * (x * z - w * y); Rq[7] = 2.f * (y * z + w * x); Rq[8] = 1.f - 2.f * (x * x + y * y);
-        }
-        for (int i = 0; i < F; ++i) s_z[i][t] = sc.feat[(long long)i * N + n];
-        for (int v = 0; v < n_views; ++v) {
-            const ViewDesc &Vw = views[v];
-            if (Vw.scene_slot != slot || count[Vw.cell_base + n] == 0u) continue;
-            const float r0 = x0 - Vw.eye[0], r1 = x1 - Vw.eye[1], r2 = x2 - Vw.eye[2];
-            const float delta = sqrtf(r0 * r0 + r1 * r1 + r2 * r2);
-            s_z[F][t] = delta;
-            s_z[F + 1][t] = r0 / delta;
-            s_z[F + 2][t] = r1 / delta;
-            s_z[F + 3][t] = r2 / delta;
-            float *out = dec + (Vw.rec_base + n * K) * kDecF;
-            // centres (no MLP) and the offsets' Eq. 11 bound
-            for (int k = 0; k < K; ++k) {
-                const long long g = n * K + k;
-                float o0 = sc.goff[g], o1 = sc.goff[G + g], o2 = sc.goff[2 * G + g];
-                const float on = sqrtf(o0 * o0 + o1 * o1 + o2 * o2);
-                if (on > 1.0f) { o0 /= on; o1 /= on; o2 /= on; }
-                const float l0 = o0 * S[0], l1 = o1 * S[1], l2 = o2 * S[2];
-                float *o = out + k * kDecF;
-                o[0] = x0 + Rq[0] * l0 + Rq[1] * l1 + Rq[2] * l2;
-                o[1] = x1 + Rq[3] * l0 + Rq[4] * l1 + Rq[5] * l2;
-                o[2] = x2 + Rq[6] * l0 + Rq[7] * l1 + Rq[8] * l2;
-                o[3] = 1.0f - fminf(on, 1.0f);  // the ratio bound, consumed by the scale decoder below
+    float *Zt = sm + S.s_z, *info = sm + S.s_info;
+    const long long N = sc.N;
+    if (t < S.M) {
+        const long long q = q0 + t;
+        SampleInfo a{};
+        a.valid = 0;
+        float z4[4] = {0.f, 0.f, 0.f, 0.f};
+        if (q < nsamp) {
+            const long long e = samples ? (long long)samples[q] : q;
+            int lo = 0, hi = n_views - 1;  // the view whose entries contain e
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (views[mid].cell_base <= e) lo = mid; else hi = mid - 1;
             }
-            const float *w = sc.mlp;
-            for (int D = 0; D < 4; ++D) {
-                const float *W1 = w, *b1 = w + H * (F + 4), *W2 = b1 + H, *b2 = W2 + outs[D] * H;
-                for (int j = 0; j < H; ++j) {
-                    float a = b1[j];
-                    for (int i = 0; i < F + 4; ++i) a = fmaf(W1[j * (F + 4) + i], s_z[i][t], a);
-                    s_h[j][t] = fmaxf(a, 0.0f);
-                }
-                for (int k = 0; k < K; ++k) {
-                    float *o = out + k * kDecF;
-                    const int nv = D == 0 ? 1 : (D == 3 ? 4 : 3);
-                    float val[4];
-                    for (int c = 0; c < nv; ++c) {
-                        const int r = k * nv + c;
-                        float a = b2[r];
-                        for (int j = 0; j < H; ++j) a = fmaf(W2[r * H + j], s_h[j][t], a);
-                        val[c] = a;
-                    }
-                    if (D == 0) {
-                        o[10] = tanhf(val[0]);
-                    } else if (D == 1) {
-                        o[11] = sigmoidf_(val[0]); o[12] = sigmoidf_(val[1]); o[13] = sigmoidf_(val[2]);
-                    } else if (D == 2) {
-                        const float lim = o[3];
-                        o[3] = fminf(sigmoidf_(val[0]), lim) * S[0];
-                        o[4] = fminf(sigmoidf_(val[1]), lim) * S[1];
-                        o[5] = fminf(sigmoidf_(val[2]), lim) * S[2];
-                    } else {
-                        const float qn2 = val[0] * val[0] + val[1] * val[1] + val[2] * val[2] + val[3] * val[3];
-                        if (qn2 > 0.f) {
-                            const float qn = rsqrtf(qn2);
-                            o[6] = val[0] * qn; o[7] = val[1] * qn; o[8] = val[2] * qn; o[9] = val[3] * qn;
-                        } else {  // no direction to normalise: the identity rotation
-                            o[6] = 1.f; o[7] = 0.f; o[8] = 0.f; o[9] = 0.f;
-                        }
-                    }
-                }
-                w = b2 + outs[D];
+            const ViewDesc &Vw = views[lo];
+            const long long n = e - Vw.cell_base;
+            if (Vw.scene_slot == slot && n >= 0 && n < N) {
+                a.valid = 1;
+                a.n = (int)n;
+                a.rec = Vw.rec_base + n * sc.K;
+#pragma unroll
+                for (int i = 0; i < 3; ++i) { a.x[i] = sc.cell[i * N + n]; a.S[i] = sc.cell[(3 + i) * N + n]; }
+                const float qw = sc.cell[6 * N + n], qx = sc.cell[7 * N + n], qy = sc.cell[8 * N + n],
+                            qz = sc.cell[9 * N + n];
+                const float in = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+                const float w = qw * in, x = qx * in, y = qy * in, z = qz * in;
+                a.R[0] = 1.f - 2.f * (y * y + z * z); a.R[1] = 2.f * (x * y - w * z); a.R[2] = 2.f * (x * z + w * y);
+                a.R[3] = 2.f * (x * y + w * z); a.R[4] = 1.f - 2.f * (x * x + z * z); a.R[5] = 2.f * (y * z - w * x);
+                a.R[6] = 2.f * (x * z - w * y); a.R[7] = 2.f * (y * z + w * x); a.R[8] = 1.f - 2.f * (x * x + y * y);
+                const float r0 = a.x[0] - Vw.eye[0], r1 = a.x[1] - Vw.eye[1], r2 = a.x[2] - Vw.eye[2];
+                const float delta = sqrtf(r0 * r0 + r1 * r1 + r2 * r2);
+                z4[0] = delta; z4[1] = r0 / delta; z4[2] = r1 / delta; z4[3] = r2 / delta;
             }
         }
+        put_info(info, t, a);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) Zt[(S.F + i) * S.LD + t] = z4[i];
+    }
+    __syncthreads();
+    // latent features: row n of the [N][F] feature matrix into column s
+    // (a warp per sample, lanes along the row)
+    const int nw = blockDim.x >> 5;
+    for (int s = t >> 5; s < S.M; s += nw) {
+        const float *p = info + s * DINFO;
+        const bool v = __float_as_int(p[1]) != 0;
+        const float *row = sc.feat + (long long)__float_as_int(p[0]) * S.F;
+        for (int i = t & 31; i < S.F; i += 32) Zt[i * S.LD + s] = v ? row[i] : 0.f;
+    }
+}
+
+// The packed weights in their shared-memory layouts (zero for padded hidden
+// units and outputs); one thread per packed float.
+__global__ void k_mlp_pack(const float *__restrict__ w, MlpShape S, float *__restrict__ pk) {
+    const int H4 = 4 * S.Hp, Rp = S.rb[4];
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < S.g_total; idx += gridDim.x * blockDim.x) {
+        float v = 0.f;
+        if (idx >= S.g_w1t && idx < S.g_w1t + S.I * H4) {              // W1^T [k][jj]
+            const int e = idx - S.g_w1t, k = e / H4, jj = e - k * H4, D = jj / S.Hp, j = jj - D * S.Hp;
+            if (j < S.H) v = w[S.w1o[D] + j * S.I + k];
+        } else if (idx >= S.g_b1 && idx < S.g_b1 + H4) {               // b1 [jj]
+            const int jj = idx - S.g_b1, D = jj / S.Hp, j = jj - D * S.Hp;
+            if (j < S.H) v = w[S.b1o[D] + j];
+        } else if (idx >= S.g_b2 && idx < S.g_b2 + Rp) {               // b2 [rr]
+            const int rr = idx - S.g_b2, D = out_block(S, rr), r = rr - S.rb[D];
+            if (r < S.nout[D]) v = w[S.b2o[D] + r];
+        } else if (idx >= S.g_w2t && idx < S.g_w2t + S.Hp * Rp) {      // W2^T [k][rr]
+            const int e = idx - S.g_w2t, k = e / Rp, rr = e - k * Rp, D = out_block(S, rr), r = rr - S.rb[D];
+            if (r < S.nout[D] && k < S.H) v = w[S.w2o[D] + r * S.H + k];
+        } else if (idx >= S.g_w2 && idx < S.g_w2 + Rp * S.Hp) {        // W2 [rr][j]
+            const int e = idx - S.g_w2, rr = e / S.Hp, j = e - rr * S.Hp, D = out_block(S, rr), r = rr - S.rb[D];
+            if (r < S.nout[D] && j < S.H) v = w[S.w2o[D] + r * S.H + j];
+        } else if (idx >= S.g_w1r && idx < S.g_w1r + H4 * S.I) {       // W1 [jj][i]
+            const int e = idx - S.g_w1r, jj = e / S.I, i = e - jj * S.I, D = jj / S.Hp, j = jj - D * S.Hp;
+            if (j < S.H) v = w[S.w1o[D] + j * S.I + i];
+        }
+        pk[idx] = v;
+    }
+}
+
+// n floats (a multiple of 4, both ends 16-byte aligned) from global to shared memory.
+__device__ __forceinline__ void copy_f4(float *dst, const float *__restrict__ src, int n) {
+    const float4 *s4 = reinterpret_cast<const float4 *>(src);
+    float4 *d4 = reinterpret_cast<float4 *>(dst);
+    for (int i = threadIdx.x; i < (n >> 2); i += blockDim.x) d4[i] = __ldg(s4 + i);
+}
+
+// Layer 1: H = relu(Z W1^T + b1) into the decoder-staggered rows of s_h.
+template <int HW>
+__device__ __forceinline__ void layer1(const MlpShape &S, float *sm) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, j0 = lane * HW;
+    if (j0 >= 4 * S.Hp) return;
+    const float *Zt = sm + S.s_z, *W = sm + S.s_w, *b1 = sm + S.s_b1;
+    const int H4 = 4 * S.Hp;
+    float acc[8][HW];
+#pragma unroll
+    for (int c = 0; c < HW; ++c) {
+        const float b = b1[j0 + c];
+#pragma unroll
+        for (int s = 0; s < 8; ++s) acc[s][c] = b;
+    }
+#pragma unroll 2
+    for (int k = 0; k < S.I; ++k) {
+        const float4 za = *reinterpret_cast<const float4 *>(Zt + k * S.LD + 8 * warp);
+        const float4 zb = *reinterpret_cast<const float4 *>(Zt + k * S.LD + 8 * warp + 4);
+        const float z[8] = {za.x, za.y, za.z, za.w, zb.x, zb.y, zb.z, zb.w};
+        float wv[HW];
+#pragma unroll
+        for (int c = 0; c < HW; c += 4) {
+            const float4 q = *reinterpret_cast<const float4 *>(W + k * H4 + j0 + c);
+            wv[c] = q.x; wv[c + 1] = q.y; wv[c + 2] = q.z; wv[c + 3] = q.w;
+        }
+#pragma unroll
+        for (int s = 0; s < 8; ++s)
+#pragma unroll
+            for (int c = 0; c < HW; ++c) acc[s][c] = fmaf(z[s], wv[c], acc[s][c]);
+    }
+    const int D = j0 / S.Hp, j = j0 - D * S.Hp;
+    float *Ht = sm + S.s_h;
+#pragma unroll
+    for (int c = 0; c < HW; ++c) {
+        float *dst = Ht + hrow(S, D, j + c) + 8 * warp;
+        *reinterpret_cast<float4 *>(dst) = make_float4(fmaxf(acc[0][c], 0.f), fmaxf(acc[1][c], 0.f),
+                                                       fmaxf(acc[2][c], 0.f), fmaxf(acc[3][c], 0.f));
+        *reinterpret_cast<float4 *>(dst + 4) = make_float4(fmaxf(acc[4][c], 0.f), fmaxf(acc[5][c], 0.f),
+                                                           fmaxf(acc[6][c], 0.f), fmaxf(acc[7][c], 0.f));
+    }
+}
+
+// Layer 2: O = H_D W2_D^T + b2 per decoder into the rows of s_o (W2^T staged).
+__device__ __forceinline__ void layer2(const MlpShape &S, float *sm) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, Rp = S.rb[4];
+    const float *Ht = sm + S.s_h, *W = sm + S.s_w, *b2 = sm + S.s_b2;
+    float *Ot = sm + S.s_o;
+    for (int rr = 4 * lane; rr < Rp; rr += 128) {
+        const int D = out_block(S, rr);
+        float acc[8][4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const float b = b2[rr + c];
+#pragma unroll
+            for (int s = 0; s < 8; ++s) acc[s][c] = b;
+        }
+        const float *hb = Ht + hrow(S, D, 0) + 8 * warp;
+#pragma unroll 2
+        for (int k = 0; k < S.Hp; ++k) {
+            const float4 ha = *reinterpret_cast<const float4 *>(hb + k * S.LD);
+            const float4 hc = *reinterpret_cast<const float4 *>(hb + k * S.LD + 4);
+            const float h[8] = {ha.x, ha.y, ha.z, ha.w, hc.x, hc.y, hc.z, hc.w};
+            const float4 q = *reinterpret_cast<const float4 *>(W + k * Rp + rr);
+            const float wv[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int s = 0; s < 8; ++s)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[s][c] = fmaf(h[s], wv[c], acc[s][c]);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            float *dst = Ot + (rr + c) * S.LD + 8 * D + 8 * warp;
+            *reinterpret_cast<float4 *>(dst) = make_float4(acc[0][c], acc[1][c], acc[2][c], acc[3][c]);
+            *reinterpret_cast<float4 *>(dst + 4) = make_float4(acc[4][c], acc[5][c], acc[6][c], acc[7][c]);
+        }
+    }
+}
+
+// The offset of Gaussian g moved into the unit ball, and the Eq. 11 bound.
+__device__ __forceinline__ void ball_offset(const SceneDev &sc, long long g, float Ob[3], float O[3], float &on) {
+    const long long G = sc.G;
+    O[0] = sc.goff[g]; O[1] = sc.goff[G + g]; O[2] = sc.goff[2 * G + g];
+    on = sqrtf(O[0] * O[0] + O[1] * O[1] + O[2] * O[2]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) Ob[c] = on > 1.0f ? O[c] / on : O[c];
+}
+
+template <int HW>
+__global__ void __launch_bounds__(256) k_decode(const ViewDesc *__restrict__ views, int n_views, int slot,
+                                                    SceneDev sc, MlpShape S, const float *__restrict__ pk,
+                                                    const uint32_t *__restrict__ samples, long long nsamp,
+                                                    float *__restrict__ dec) {
+    extern __shared__ float4 smem4[];
+    float *sm = reinterpret_cast<float *>(smem4);
+    const int K = S.K;
+    for (long long q0 = (long long)blockIdx.x * S.M; q0 < nsamp; q0 += (long long)gridDim.x * S.M) {
+        copy_f4(sm + S.s_w, pk + S.g_w1t, S.I * 4 * S.Hp);
+        copy_f4(sm + S.s_b1, pk + S.g_b1, 4 * S.Hp);
+        copy_f4(sm + S.s_b2, pk + S.g_b2, S.rb[4]);
+        stage_samples(S, sm, views, n_views, slot, sc, samples, nsamp, q0);
+        __syncthreads();
+        layer1<HW>(S, sm);
+        __syncthreads();
+        copy_f4(sm + S.s_w, pk + S.g_w2t, S.Hp * S.rb[4]);
+        __syncthreads();
+        layer2(S, sm);
+        __syncthreads();
+        // activations and the centres, one (sample, Gaussian) per thread
+        const float *Ot = sm + S.s_o, *info = sm + S.s_info;
+        for (int idx = threadIdx.x; idx < S.M * K; idx += blockDim.x) {
+            const int s = idx / K, k = idx - s * K;
+            const SampleInfo a = get_info(info, s);
+            if (!a.valid) continue;
+            const long long g = (long long)a.n * K + k;
+            float Ob[3], O[3], on;
+            ball_offset(sc, g, Ob, O, on);
+            const float lim = 1.0f - fminf(on, 1.0f);
+            float o[kDecF];
+            const float l0 = Ob[0] * a.S[0], l1 = Ob[1] * a.S[1], l2 = Ob[2] * a.S[2];
+            o[0] = a.x[0] + a.R[0] * l0 + a.R[1] * l1 + a.R[2] * l2;
+            o[1] = a.x[1] + a.R[3] * l0 + a.R[4] * l1 + a.R[5] * l2;
+            o[2] = a.x[2] + a.R[6] * l0 + a.R[7] * l1 + a.R[8] * l2;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) o[3 + c] = fminf(sigmoidf_(Ot[orow(S, 2, 3 * k + c) + s]), lim) * a.S[c];
+            float qv[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) qv[c] = Ot[orow(S, 3, 4 * k + c) + s];
+            const float qn2 = qv[0] * qv[0] + qv[1] * qv[1] + qv[2] * qv[2] + qv[3] * qv[3];
+            if (qn2 > 0.f) {
+                const float iq = rsqrtf(qn2);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) o[6 + c] = qv[c] * iq;
+            } else {  // no direction to normalise: the identity rotation
+                o[6] = 1.f; o[7] = 0.f; o[8] = 0.f; o[9] = 0.f;
+            }
+            o[10] = tanhf(Ot[orow(S, 0, k) + s]);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) o[11 + c] = sigmoidf_(Ot[orow(S, 1, 3 * k + c) + s]);
+            float2 *dst = reinterpret_cast<float2 *>(dec + (a.rec + k) * kDecF);
+#pragma unroll
+            for (int i = 0; i < kDecF / 2; ++i) dst[i] = make_float2(o[2 * i], o[2 * i + 1]);
+        }
+        __syncthreads();
     }
 }
 
 // ---------------------------------------------------------------- adjoint
-// Gradients through the decode, summed over the views in which each cell was
-// decoded, from gdec (dL/d of the decoded values, layout of dec).  One thread
-// per cell recomputes its decoders' hidden layers and outputs; the block
-// keeps, in shared memory, the columns of its cells' inputs z, hidden values
-// h, dL/dh (pre-activation) and dL/do of the decoder at hand, and the
-// block's partial sums of every weight gradient (the packed layout).  Per
-// decoder and view the block adds sum over its cells of dh z^T (W1, b1) and
-// do h^T (W2, b2) to those sums, one weight per thread at a time; at the end
-// they go to g_mlp with one atomic add per weight and block.  Columns are
-// blockDim.x + 1 floats apart, so lanes reading consecutive rows at the same
-// cell hit distinct banks.  Decisions held fixed: the ReLU masks, the Eq. 11
-// bound (which of sigmoid and 1 - |O_pos| is smaller), sigma <= 0.
-struct DecBwdSmem {
-    int T, LD, F, H, K, P;
-    __host__ __device__ int z_off() const { return 0; }
-    __host__ __device__ int h_off() const { return (F + 4) * LD; }
-    __host__ __device__ int dh_off() const { return h_off() + H * LD; }
-    __host__ __device__ int do_off() const { return dh_off() + H * LD; }
-    __host__ __device__ int gf_off() const { return do_off() + 4 * K * LD; }
-    __host__ __device__ int acc_off() const { return gf_off() + F * LD; }
-    __host__ __device__ int floats() const { return acc_off() + P; }
-};
-
-__host__ __device__ inline int dec_packed_size(int F, int H, int K) {
-    return 4 * (H * (F + 4) + H) + (K + 3 * K + 3 * K + 4 * K) * (H + 1);
-}
-
-__global__ void __launch_bounds__(64) k_decode_bwd(const ViewDesc *__restrict__ views, int n_views, int slot,
-                                                   SceneDev sc, const uint32_t *__restrict__ count,
-                                                   const float *__restrict__ gdec, float *__restrict__ g_mlp,
-                                                   float *__restrict__ g_feat, float *__restrict__ g_offset) {
-    extern __shared__ float smem[];
-    const int T = blockDim.x, t = threadIdx.x;
-    const long long N = sc.N, G = sc.G;
-    const int K = sc.K, F = sc.F, H = sc.H;
-    const DecBwdSmem L{T, T + 1, F, H, K, dec_packed_size(F, H, K)};
-    float *s_z = smem + L.z_off(), *s_h = smem + L.h_off(), *s_dh = smem + L.dh_off(), *s_do = smem + L.do_off(),
-          *s_gf = smem + L.gf_off(), *s_acc = smem + L.acc_off();
-    const int LD = L.LD;
-    const int outs[4] = {K, 3 * K, 3 * K, 4 * K};
-    for (int i = t; i < L.P; i += T) s_acc[i] = 0.f;
-    for (long long base = (long long)blockIdx.x * T; base < N; base += (long long)gridDim.x * T) {
-        const long long n = base + t;
-        const bool live = n < N;
-        float x0 = 0.f, x1 = 0.f, x2 = 0.f, S[3] = {0.f, 0.f, 0.f}, Rq[9];
-        if (live) {
-            x0 = sc.cell[n]; x1 = sc.cell[N + n]; x2 = sc.cell[2 * N + n];
-            S[0] = sc.cell[3 * N + n]; S[1] = sc.cell[4 * N + n]; S[2] = sc.cell[5 * N + n];
+// Per tile of samples: the forward again (layers 1 and 2), then
+//   dL/do (in place of O) from gdec through the activations, the offsets'
+//     gradients (atomic adds to g_offset: mu = x + R(Q)(O_pos S) and the
+//     Eq. 11 bound);
+//   dL/dh = relu'(h) (dL/do_D W2_D) per decoder;
+//   dL/df = sum over decoders of dL/dh_D W1_D[:, :F]  (atomic adds to g_feat);
+// and the rows Z, H, dL/dh, dL/do of every sample to `rows` for the weight
+// gradients (k_mlp_wgrad).  Decisions held fixed: the ReLU masks, the side of
+// the Eq. 11 minimum, sigma <= 0 (gdec is zero there).
+template <int HW>
+__global__ void __launch_bounds__(256) k_decode_bwd(const ViewDesc *__restrict__ views, int n_views, int slot,
+                                                        SceneDev sc, MlpShape S, const float *__restrict__ pk,
+                                                        const uint32_t *__restrict__ samples, long long nsamp,
+                                                        const float *__restrict__ gdec,
+                                                        float *__restrict__ g_feat, float *__restrict__ g_offset,
+                                                        float *__restrict__ rows) {
+    extern __shared__ float4 smem4[];
+    float *sm = reinterpret_cast<float *>(smem4);
+    const int K = S.K, F = S.F, Hp = S.Hp, H4 = 4 * S.Hp;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (long long q0 = (long long)blockIdx.x * S.M; q0 < nsamp; q0 += (long long)gridDim.x * S.M) {
+        copy_f4(sm + S.s_w, pk + S.g_w1t, S.I * 4 * S.Hp);
+        copy_f4(sm + S.s_b1, pk + S.g_b1, 4 * S.Hp);
+        copy_f4(sm + S.s_b2, pk + S.g_b2, S.rb[4]);
+        stage_samples(S, sm, views, n_views, slot, sc, samples, nsamp, q0);
+        __syncthreads();
+        layer1<HW>(S, sm);
+        __syncthreads();
+        copy_f4(sm + S.s_w, pk + S.g_w2t, S.Hp * S.rb[4]);
+        __syncthreads();
+        layer2(S, sm);
+        __syncthreads();
+        float *Ot = sm + S.s_o;
+        const float *info = sm + S.s_info;
+        // dL/do through the activations, in place; offsets' gradients
+        for (int idx = threadIdx.x; idx < S.M * K; idx += blockDim.x) {
+            const int s = idx / K, k = idx - s * K;
+            const SampleInfo a = get_info(info, s);
+            float *po = Ot + orow(S, 0, k) + s;
+            float *pc[3], *ps[3], *pq[4];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) { pc[c] = Ot + orow(S, 1, 3 * k + c) + s; ps[c] = Ot + orow(S, 2, 3 * k + c) + s; }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) pq[c] = Ot + orow(S, 3, 4 * k + c) + s;
+            if (!a.valid) {
+                *po = 0.f;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) { *pc[c] = 0.f; *ps[c] = 0.f; }
+#pragma unroll
+                for (int c = 0; c < 4; ++c) *pq[c] = 0.f;
+                continue;
+            }
+            const long long g = (long long)a.n * K + k;
+            float gk[kDecF];
+            {
+                const float2 *src = reinterpret_cast<const float2 *>(gdec + (a.rec + k) * kDecF);
+#pragma unroll
+                for (int i = 0; i < kDecF / 2; ++i) { const float2 v = src[i]; gk[2 * i] = v.x; gk[2 * i + 1] = v.y; }
+            }
+            // opacity
+            {
+                const float sg = tanhf(*po);
+                *po = gk[10] * (1.0f - sg * sg);
+            }
+            // colour
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float cc = sigmoidf_(*pc[c]);
+                *pc[c] = gk[11 + c] * cc * (1.0f - cc);
+            }
+            // scale and the Eq. 11 bound; then the offset
+            float Ob[3], O[3], on;
+            ball_offset(sc, g, Ob, O, on);
+            const float lim = 1.0f - fminf(on, 1.0f);
+            float dlim = 0.f;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float sg = sigmoidf_(*ps[c]);
+                if (sg < lim) {
+                    *ps[c] = gk[3 + c] * a.S[c] * sg * (1.0f - sg);
+                } else {
+                    *ps[c] = 0.f;
+                    dlim += gk[3 + c] * a.S[c];
+                }
+            }
+            float dOb[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) dOb[c] = a.S[c] * (a.R[c] * gk[0] + a.R[3 + c] * gk[1] + a.R[6 + c] * gk[2]);
+            float dO[3];
+            if (on > 1.0f) {  // O_pos = O / |O| has unit length: lim = 0 does not move
+                const float io = 1.0f / on;
+                const float pr = (dOb[0] * O[0] + dOb[1] * O[1] + dOb[2] * O[2]) * io * io;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) dO[c] = (dOb[c] - pr * O[c]) * io;
+            } else {
+                const float io = on > 0.f ? dlim / on : 0.f;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) dO[c] = dOb[c] - io * O[c];
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                if (dO[c] != 0.f) atomicAdd(g_offset + 3 * g + c, dO[c]);
+            // rotation (a zero output decodes to a constant)
+            float qv[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) qv[c] = *pq[c];
+            const float qn2 = qv[0] * qv[0] + qv[1] * qv[1] + qv[2] * qv[2] + qv[3] * qv[3];
+            if (qn2 > 0.f) {
+                const float iq = rsqrtf(qn2);
+                float pr = 0.f;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) pr += gk[6 + c] * qv[c] * iq;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) *pq[c] = (gk[6 + c] - pr * qv[c] * iq) * iq;
+            } else {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) *pq[c] = 0.f;
+            }
         }
+        __syncthreads();
+        copy_f4(sm + S.s_w, pk + S.g_w2, S.rb[4] * S.Hp);
+        __syncthreads();
+        // dL/dh = relu'(h) * (dL/do_D W2_D)
+        const int j0 = lane * HW;
+        float *DHt = sm + S.s_dh;
+        const float *Ht = sm + S.s_h;
+        if (j0 < H4) {
+            const int D = j0 / Hp, j = j0 - D * Hp;
+            const float *W = sm + S.s_w;
+            float acc[8][HW];
+#pragma unroll
+            for (int s = 0; s < 8; ++s)
+#pragma unroll
+                for (int c = 0; c < HW; ++c) acc[s][c] = 0.f;
+            const float *db = Ot + orow(S, D, 0) + 8 * warp;
+#pragma unroll 2
+            for (int r = 0; r < S.nout[D]; ++r) {
+                const float4 da = *reinterpret_cast<const float4 *>(db + r * S.LD);
+                const float4 dc = *reinterpret_cast<const float4 *>(db + r * S.LD + 4);
+                const float d[8] = {da.x, da.y, da.z, da.w, dc.x, dc.y, dc.z, dc.w};
+                float wv[HW];
+#pragma unroll
+                for (int c = 0; c < HW; c += 4) {
+                    const float4 q = *reinterpret_cast<const float4 *>(W + (S.rb[D] + r) * Hp + j + c);
+                    wv[c] = q.x; wv[c + 1] = q.y; wv[c + 2] = q.z; wv[c + 3] = q.w;
+                }
+#pragma unroll
+                for (int s = 0; s < 8; ++s)
+#pragma unroll
+                    for (int c = 0; c < HW; ++c) acc[s][c] = fmaf(d[s], wv[c], acc[s][c]);
+            }
+#pragma unroll
+            for (int c = 0; c < HW; ++c) {
+                const int hr = hrow(S, D, j + c) + 8 * warp;
+                const float4 ha = *reinterpret_cast<const float4 *>(Ht + hr);
+                const float4 hc = *reinterpret_cast<const float4 *>(Ht + hr + 4);
+                *reinterpret_cast<float4 *>(DHt + hr) =
+                    make_float4(ha.x > 0.f ? acc[0][c] : 0.f, ha.y > 0.f ? acc[1][c] : 0.f,
+                                ha.z > 0.f ? acc[2][c] : 0.f, ha.w > 0.f ? acc[3][c] : 0.f);
+                *reinterpret_cast<float4 *>(DHt + hr + 4) =
+                    make_float4(hc.x > 0.f ? acc[4][c] : 0.f, hc.y > 0.f ? acc[5][c] : 0.f,
+                                hc.z > 0.f ? acc[6][c] : 0.f, hc.w > 0.f ? acc[7][c] : 0.f);
+            }
+        }
+        __syncthreads();
+        copy_f4(sm + S.s_w, pk + S.g_w1r, 4 * S.Hp * S.I);
+        __syncthreads();
+        // dL/df = sum_jj dL/dh[jj] W1[jj][:F]; lanes take features lane and lane + 32
         {
-            const float qw = live ? sc.cell[6 * N + n] : 1.f, qx = live ? sc.cell[7 * N + n] : 0.f,
-                        qy = live ? sc.cell[8 * N + n] : 0.f, qz = live ? sc.cell[9 * N + n] : 0.f;
-            const float in = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
-            const float w = qw * in, x = qx * in, y = qy * in, z = qz * in;
-            Rq[0] = 1.f - 2.f * (y * y + z * z); Rq[1] = 2.f * (x * y - w * z); Rq[2] = 2.f * (x * z + w * y);
-            Rq[3] = 2.f * (x * y + w * z); Rq[4] = 1.f - 2.f * (x * x + z * z); Rq[5] = 2.f * (y * z - w * x);
-            Rq[6] = 2.f * (x * z - w * y); Rq[7] = 2.f * (y * z + w * x); Rq[8] = 1.f - 2.f * (x * x + y * y);
-        }
-        for (int i = 0; i < F; ++i) {
-            s_z[i * LD + t] = live ? sc.feat[(long long)i * N + n] : 0.f;
-            s_gf[i * LD + t] = 0.f;
-        }
-        for (int i = F; i < F + 4; ++i) s_z[i * LD + t] = 0.f;
-        if (live)
-            for (int k = 0; k < K; ++k) {
-                const long long g = n * K + k;
-                g_offset[3 * g] = 0.f; g_offset[3 * g + 1] = 0.f; g_offset[3 * g + 2] = 0.f;
-            }
-        for (int v = 0; v < n_views; ++v) {
-            const ViewDesc &Vw = views[v];
-            if (Vw.scene_slot != slot) continue;  // uniform over the block
-            const bool act = live && count[Vw.cell_base + n] != 0u;
-            if (!__syncthreads_or(act)) continue;
-            if (act) {
-                const float r0 = x0 - Vw.eye[0], r1 = x1 - Vw.eye[1], r2 = x2 - Vw.eye[2];
-                const float delta = sqrtf(r0 * r0 + r1 * r1 + r2 * r2);
-                s_z[F * LD + t] = delta;
-                s_z[(F + 1) * LD + t] = r0 / delta;
-                s_z[(F + 2) * LD + t] = r1 / delta;
-                s_z[(F + 3) * LD + t] = r2 / delta;
-            }
-            const float *gd = gdec + (Vw.rec_base + (live ? n : 0) * K) * kDecF;
-            const float *w = sc.mlp;
-            int off = 0;  // packed offset of decoder D
-            for (int D = 0; D < 4; ++D) {
-                const int nout = outs[D], I = F + 4;
-                const float *W1 = w, *b1 = w + H * I, *W2 = b1 + H, *b2 = W2 + nout * H;
-                // hidden layer
-                for (int j = 0; j < H; ++j) {
-                    float a = 0.f;
-                    if (act) {
-                        a = b1[j];
-                        for (int i = 0; i < I; ++i) a = fmaf(W1[j * I + i], s_z[i * LD + t], a);
-                        a = fmaxf(a, 0.0f);
-                    }
-                    s_h[j * LD + t] = a;
-                }
-                // outputs and dL/do through the activation
-                const int nv = D == 0 ? 1 : (D == 3 ? 4 : 3);
-                for (int k = 0; k < K; ++k) {
-                    float val[4] = {0.f, 0.f, 0.f, 0.f}, dov[4] = {0.f, 0.f, 0.f, 0.f};
-                    if (act) {
-                        for (int c = 0; c < nv; ++c) {
-                            const int r = k * nv + c;
-                            float a = b2[r];
-                            for (int j = 0; j < H; ++j) a = fmaf(W2[r * H + j], s_h[j * LD + t], a);
-                            val[c] = a;
-                        }
-                        const float *gk = gd + k * kDecF;
-                        if (D == 0) {
-                            const float sg = tanhf(val[0]);
-                            dov[0] = gk[10] * (1.0f - sg * sg);
-                        } else if (D == 1) {
+            const float *W = sm + S.s_w;
+            const int i0 = lane, i1 = lane + 32;
+            const bool u1 = i1 < F;
+            if (i0 < F) {
+                float acc[8][2];
 #pragma unroll
-                            for (int c = 0; c < 3; ++c) {
-                                const float cc = sigmoidf_(val[c]);
-                                dov[c] = gk[11 + c] * cc * (1.0f - cc);
-                            }
-                        } else if (D == 2) {
-                            const long long g = n * K + k;
-                            const float O[3] = {sc.goff[g], sc.goff[G + g], sc.goff[2 * G + g]};
-                            const float on = sqrtf(O[0] * O[0] + O[1] * O[1] + O[2] * O[2]);
-                            const float lim = 1.0f - fminf(on, 1.0f);
-                            float dlim = 0.f;
+                for (int s = 0; s < 8; ++s) acc[s][0] = acc[s][1] = 0.f;
+                for (int jj = 0; jj < H4; ++jj) {
+                    const int D = jj / Hp, j = jj - D * Hp;
+                    const float *dh = DHt + hrow(S, D, j) + 8 * warp;
+                    const float4 da = *reinterpret_cast<const float4 *>(dh);
+                    const float4 dc = *reinterpret_cast<const float4 *>(dh + 4);
+                    const float d[8] = {da.x, da.y, da.z, da.w, dc.x, dc.y, dc.z, dc.w};
+                    const float w0 = W[jj * S.I + i0], w1 = u1 ? W[jj * S.I + i1] : 0.f;
 #pragma unroll
-                            for (int c = 0; c < 3; ++c) {
-                                const float sg = sigmoidf_(val[c]);
-                                if (sg < lim) dov[c] = gk[3 + c] * S[c] * sg * (1.0f - sg);
-                                else dlim += gk[3 + c] * S[c];
-                            }
-                            // offset: mu = x + R(Q) (O_pos * S), lim = 1 - |O_pos|
-                            float dOb[3];
-#pragma unroll
-                            for (int c = 0; c < 3; ++c)
-                                dOb[c] = S[c] * (Rq[c] * gk[0] + Rq[3 + c] * gk[1] + Rq[6 + c] * gk[2]);
-                            float dO[3];
-                            if (on > 1.0f) {  // O_pos = O / |O| (unit length, so lim = 0 is constant)
-                                const float io = 1.0f / on;
-                                const float pr = (dOb[0] * O[0] + dOb[1] * O[1] + dOb[2] * O[2]) * io * io;
-#pragma unroll
-                                for (int c = 0; c < 3; ++c) dO[c] = (dOb[c] - pr * O[c]) * io;
-                            } else {
-                                const float io = on > 0.f ? dlim / on : 0.f;
-#pragma unroll
-                                for (int c = 0; c < 3; ++c) dO[c] = dOb[c] - io * O[c];
-                            }
-#pragma unroll
-                            for (int c = 0; c < 3; ++c) g_offset[3 * g + c] += dO[c];
-                        } else {
-                            const float qn2 = val[0] * val[0] + val[1] * val[1] + val[2] * val[2] + val[3] * val[3];
-                            if (qn2 > 0.f) {  // a zero output decodes to the constant identity
-                                const float iq = rsqrtf(qn2);
-                                float pr = 0.f;
-#pragma unroll
-                                for (int c = 0; c < 4; ++c) pr += gk[6 + c] * val[c] * iq;
-#pragma unroll
-                                for (int c = 0; c < 4; ++c) dov[c] = (gk[6 + c] - pr * val[c] * iq) * iq;
-                            }
-                        }
-                    }
-                    for (int c = 0; c < nv; ++c) s_do[(k * nv + c) * LD + t] = dov[c];
-                }
-                // dL/dh (pre-activation) and the feature part of dL/dz
-                for (int j = 0; j < H; ++j) {
-                    float a = 0.f;
-                    if (act && s_h[j * LD + t] > 0.f)
-                        for (int r = 0; r < nout; ++r) a = fmaf(W2[r * H + j], s_do[r * LD + t], a);
-                    s_dh[j * LD + t] = a;
-                }
-                if (act)
-                    for (int i = 0; i < F; ++i) {
-                        float a = s_gf[i * LD + t];
-                        for (int j = 0; j < H; ++j) a = fmaf(W1[j * I + i], s_dh[j * LD + t], a);
-                        s_gf[i * LD + t] = a;
-                    }
-                __syncthreads();
-                // the block's weight gradients: W1 | b1 = sum dh [z | 1]^T, W2 | b2 = sum do [h | 1]^T
-                {
-                    const int n1 = H * (I + 1);
-                    for (int idx = t; idx < n1; idx += T) {
-                        const int j = idx / (I + 1), i = idx - j * (I + 1);
-                        const float *a = s_dh + j * LD;
-                        float acc = 0.f;
-                        if (i < I) {
-                            const float *b = s_z + i * LD;
-                            for (int c = 0; c < T; ++c) acc = fmaf(a[c], b[c], acc);
-                            s_acc[off + j * I + i] += acc;
-                        } else {
-                            for (int c = 0; c < T; ++c) acc += a[c];
-                            s_acc[off + H * I + j] += acc;
-                        }
-                    }
-                    const int o2 = off + H * I + H, n2 = nout * (H + 1);
-                    for (int idx = t; idx < n2; idx += T) {
-                        const int r = idx / (H + 1), j = idx - r * (H + 1);
-                        const float *a = s_do + r * LD;
-                        float acc = 0.f;
-                        if (j < H) {
-                            const float *b = s_h + j * LD;
-                            for (int c = 0; c < T; ++c) acc = fmaf(a[c], b[c], acc);
-                            s_acc[o2 + r * H + j] += acc;
-                        } else {
-                            for (int c = 0; c < T; ++c) acc += a[c];
-                            s_acc[o2 + nout * H + r] += acc;
-                        }
+                    for (int s = 0; s < 8; ++s) {
+                        acc[s][0] = fmaf(d[s], w0, acc[s][0]);
+                        acc[s][1] = fmaf(d[s], w1, acc[s][1]);
                     }
                 }
-                __syncthreads();
-                off += H * I + H + nout * H + nout;
-                w = b2 + nout;
+#pragma unroll
+                for (int s = 0; s < 8; ++s) {
+                    const float *p = info + (8 * warp + s) * DINFO;
+                    if (__float_as_int(p[1]) == 0) continue;
+                    const long long n = __float_as_int(p[0]);
+                    if (acc[s][0] != 0.f) atomicAdd(g_feat + n * F + i0, acc[s][0]);
+                    if (u1 && acc[s][1] != 0.f) atomicAdd(g_feat + n * F + i1, acc[s][1]);
+                }
             }
         }
-        if (live)
-            for (int i = 0; i < F; ++i) g_feat[n * F + i] = s_gf[i * LD + t];
+        // the rows of this tile's samples for the weight gradients
+        {
+            const int nv = (int)min((long long)S.M, nsamp - q0);
+            const float *Zt = sm + S.s_z;
+            for (int s = warp; s < nv; s += S.W)
+                for (int c = lane; c < S.row_all; c += 32) {
+                float v;
+                if (c < S.row_h) {
+                    v = Zt[c * S.LD + s];
+                } else if (c < S.row_dh) {
+                    const int jj = c - S.row_h, D = jj / Hp;
+                    v = Ht[hrow(S, D, jj - D * Hp) + s];
+                } else if (c < S.row_do) {
+                    const int jj = c - S.row_dh, D = jj / Hp;
+                    v = DHt[hrow(S, D, jj - D * Hp) + s];
+                } else {
+                    const int rr = c - S.row_do;
+                    v = Ot[rr * S.LD + 8 * out_block(S, rr) + s];
+                }
+                rows[(q0 + s) * S.row_all + c] = v;
+                }
+        }
+        __syncthreads();
     }
-    __syncthreads();
-    for (int i = t; i < L.P; i += T)
-        if (s_acc[i] != 0.f) atomicAdd(g_mlp + i, s_acc[i]);
 }
 
-void launch_decode_bwd(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const uint32_t *count,
-                       const float *gdec, float *g_mlp, float *g_feat, float *g_offset, cudaStream_t st) {
-    if (sc.N == 0 || !sc.feat) return;
-    // 64 cells per block while the shared memory fits, else 32
-    int T = 64;
-    DecBwdSmem L{T, T + 1, sc.F, sc.H, sc.K, dec_packed_size(sc.F, sc.H, sc.K)};
-    if (L.floats() * 4 > 227 * 1024) {
-        T = 32;
-        L = DecBwdSmem{T, T + 1, sc.F, sc.H, sc.K, dec_packed_size(sc.F, sc.H, sc.K)};
+// Weight gradients from the per-sample rows: for every decoder D
+//   dW1_D [H][I] | db1_D = sum_s dh_D(s) [z(s) | 1]^T
+//   dW2_D [nout][H] | db2_D = sum_s do_D(s) [h_D(s) | 1]^T
+// Eight products C[a][b] = sum_s A[s][a] B[s][b] (b = nb: the ones column,
+// i.e. the bias).  A CTA takes one 64 x 64 tile of one product over a chunk
+// of samples (32 rows at a time through shared memory, 4 x 4 outputs per
+// thread) and adds its tile to g_mlp with one atomic add per output.
+struct WgProblem {
+    int a_off, na, b_off, nb, wo, bo;  // column offsets in A and B rows, sizes, packed output offsets
+    int a_is_dh;                        // A = dL/dh rows and B = Z rows (else dL/do and H rows)
+};
+struct WgProblems { WgProblem p[8]; };
+
+__global__ void __launch_bounds__(256) k_mlp_wgrad(const float *__restrict__ rows, MlpShape S, long long nsamp,
+                                                   int chunk, WgProblems probs, float *__restrict__ g_mlp) {
+    __shared__ float4 sA4[32 * 17], sB4[32 * 17];
+    float *sA = reinterpret_cast<float *>(sA4), *sB = reinterpret_cast<float *>(sB4);
+    const WgProblem P = probs.p[blockIdx.z];
+    const int ta = blockIdx.y >> 1, tb = blockIdx.y & 1;
+    const int a_base = 64 * ta, b_base = 64 * tb;
+    if (a_base >= P.na || b_base > P.nb) return;
+    const long long s0 = (long long)blockIdx.x * chunk, s1 = min(nsamp, s0 + chunk);
+    const int t = threadIdx.x, ra = (t >> 4) * 4, rb = (t & 15) * 4;
+    const int acol = P.a_is_dh ? S.row_dh : S.row_do;
+    const int bcol = P.a_is_dh ? S.row_z : S.row_h;
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    for (long long sb = s0; sb < s1; sb += 32) {
+        for (int idx = t; idx < 32 * 64; idx += 256) {
+            const int r = idx >> 6, c = idx & 63;
+            const long long s = sb + r;
+            const int a = a_base + c, b = b_base + c;
+            float va = 0.f, vb = 0.f;
+            if (s < s1) {
+                const float *row = rows + s * S.row_all;
+                if (a < P.na) va = row[acol + P.a_off + a];
+                vb = b < P.nb ? row[bcol + P.b_off + b] : (b == P.nb ? 1.0f : 0.f);
+            }
+            sA[r * 68 + c] = va;
+            sB[r * 68 + c] = vb;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int r = 0; r < 32; ++r) {
+            const float4 av = *reinterpret_cast<const float4 *>(sA + r * 68 + ra);
+            const float4 bv = *reinterpret_cast<const float4 *>(sB + r * 68 + rb);
+            const float x[4] = {av.x, av.y, av.z, av.w}, y[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(x[i], y[j], acc[i][j]);
+        }
+        __syncthreads();
     }
-    const size_t bytes = sizeof(float) * (size_t)L.floats();
-    cudaFuncSetAttribute(k_decode_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_decode_bwd, T, bytes);
-    int dev = 0, sms = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int a = a_base + ra + i, b = b_base + rb + j;
+            if (a < P.na && b <= P.nb && acc[i][j] != 0.f)
+                atomicAdd(g_mlp + (b < P.nb ? P.wo + a * P.nb + b : P.bo + a), acc[i][j]);
+        }
+}
+
+// ---------------------------------------------------------------- launchers
+
+template <typename Kern>
+static int persistent_grid(Kern k, int threads, size_t smem, long long tiles) {
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem);
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    long long b = (sc.N + T - 1) / T;
     const long long cap = (long long)std::max(1, per_sm) * std::max(1, sms);
-    if (b > cap) b = cap;
-    k_decode_bwd<<<(unsigned)b, T, bytes, st>>>(views, n_views, slot, sc, count, gdec, g_mlp, g_feat, g_offset);
+    return (int)std::max(1LL, std::min(tiles, cap));
 }
 
-void launch_decode(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const uint32_t *count, float *dec,
-                   cudaStream_t st) {
-    if (sc.N == 0 || n_views == 0 || !sc.feat) return;
-    long long b = (sc.N + DEC_THREADS - 1) / DEC_THREADS;
-    if (b > 152LL * 16) b = 152LL * 16;
-    k_decode<<<(unsigned)b, DEC_THREADS, 0, st>>>(views, n_views, slot, sc, count, dec);
+long long decode_pack_floats(int F, int H, int K) { return mlp_shape(F, H, K, true).g_total; }
+
+static void pack_weights(const MlpShape &S, const float *mlp, float *pk, cudaStream_t st) {
+    k_mlp_pack<<<(S.g_total + 255) / 256, 256, 0, st>>>(mlp, S, pk);
+}
+
+void launch_decode(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const uint32_t *samples,
+                   long long nsamp, float *dec, float *pk, cudaStream_t st) {
+    if (nsamp <= 0 || !sc.feat) return;
+    const MlpShape S = mlp_shape(sc.F, sc.H, sc.K, false);
+    pack_weights(S, sc.mlp, pk, st);
+    const size_t smem = sizeof(float) * (size_t)S.s_total;
+    const long long tiles = (nsamp + S.M - 1) / S.M;
+    if (S.HW == 4) {
+        const int b = persistent_grid(k_decode<4>, 32 * S.W, smem, tiles);
+        k_decode<4><<<b, 32 * S.W, smem, st>>>(views, n_views, slot, sc, S, pk, samples, nsamp, dec);
+    } else {
+        const int b = persistent_grid(k_decode<8>, 32 * S.W, smem, tiles);
+        k_decode<8><<<b, 32 * S.W, smem, st>>>(views, n_views, slot, sc, S, pk, samples, nsamp, dec);
+    }
+}
+
+long long decode_bwd_scratch_floats(int F, int H, int K, long long nsamp) {
+    return (long long)mlp_shape(F, H, K, true).row_all * std::max(1LL, nsamp);
+}
+
+void launch_decode_bwd(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const uint32_t *samples,
+                       long long nsamp, const float *gdec, float *g_mlp, float *g_feat, float *g_offset, float *rows,
+                       float *pk, cudaStream_t st) {
+    if (nsamp <= 0 || !sc.feat) return;
+    const MlpShape S = mlp_shape(sc.F, sc.H, sc.K, true);
+    pack_weights(S, sc.mlp, pk, st);
+    const size_t smem = sizeof(float) * (size_t)S.s_total;
+    const long long tiles = (nsamp + S.M - 1) / S.M;
+    if (S.HW == 4) {
+        const int b = persistent_grid(k_decode_bwd<4>, 32 * S.W, smem, tiles);
+        k_decode_bwd<4><<<b, 32 * S.W, smem, st>>>(views, n_views, slot, sc, S, pk, samples, nsamp, gdec, g_feat,
+                                                  g_offset, rows);
+    } else {
+        const int b = persistent_grid(k_decode_bwd<8>, 32 * S.W, smem, tiles);
+        k_decode_bwd<8><<<b, 32 * S.W, smem, st>>>(views, n_views, slot, sc, S, pk, samples, nsamp, gdec, g_feat,
+                                                  g_offset, rows);
+    }
+    WgProblems pr{};
+    for (int D = 0; D < 4; ++D) {
+        pr.p[D] = WgProblem{D * S.Hp, S.H, 0, S.I, S.w1o[D], S.b1o[D], 1};
+        pr.p[4 + D] = WgProblem{S.rb[D], S.nout[D], D * S.Hp, S.H, S.w2o[D], S.b2o[D], 0};
+    }
+    const int chunk = 2048;
+    const dim3 grid((unsigned)((nsamp + chunk - 1) / chunk), 4, 8);
+    k_mlp_wgrad<<<grid, 256, 0, st>>>(rows, S, nsamp, chunk, pr, g_mlp);
 }
 
 }  // namespace dgs

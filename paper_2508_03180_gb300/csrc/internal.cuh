@@ -39,7 +39,7 @@ struct SceneDev {
     const float *gauss;    // [11][G]: mean xyz, scale xyz, quat wxyz, logit
     const float *sh;       // [C*3][G]: coefficient c, channel ch at plane c*3+ch
     const float *vsh;      // [Cv][N]: SH coefficients of a view-dependent v_n, or NULL (scalar v_n)
-    const float *feat;     // neural cells: [F][N] latent features, or NULL (explicit Gaussians)
+    const float *feat;     // neural cells: [N][F] latent features (rows), or NULL (explicit Gaussians)
     const float *goff;     // neural cells: [3][G] position offsets O_pos
     const float *mlp;      // neural cells: packed decoder weights
     long long N, G;
@@ -161,19 +161,23 @@ void launch_cell_v_grad(const ViewDesc *views, int n_views, const SceneDev &sc, 
 void launch_gauss_bin(const ViewDesc *views, int n_views, const SceneDev &sc, const BlendParams &bp, bool wsr,
                       float tau, float4 *rec, uint32_t *zkey, uint32_t *zval, short4 *rect, uint32_t *count,
                       uint32_t *visible, cudaStream_t st);
-// Neural scenes: decode the Gaussians of every (view, cell) of scene `slot`
-// whose cell survived culling into dec [rec_base + g][kDecF], then their
-// records (colour and opacity as decoded).
-void launch_decode(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const uint32_t *count, float *dec,
-                   cudaStream_t st);
+// Neural scenes: decode the Gaussians of the (view, cell) entries
+// samples[0 .. nsamp) (entry e = cell_base of its view + cell; NULL: entry q
+// for sample q) of scene `slot` into dec [rec_base + g][kDecF], then their
+// records (colour and opacity as decoded).  Features are rows [N][F].
+void launch_decode(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const uint32_t *samples,
+                   long long nsamp, float *dec, float *pk, cudaStream_t st);
+// Scratch floats for the weights repacked once per decode call (pk above).
+long long decode_pack_floats(int F, int H, int K);
 void launch_project_neural(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const uint32_t *count,
                            const float *vview, const float *dec, const BlendParams &bp, float4 *rec, float *g2d_zero,
                            cudaStream_t st);
 // Adjoints of a neural scene: the records' gradients with respect to the
 // decoded values of every decoded (view, Gaussian) (gdec, layout of dec),
-// then through the decode to the packed weights (g_mlp, accumulated: zero it
-// first), the features g_feat [N][F] and the raw offsets g_offset [G][3]
-// (both written), summed over views.
+// then through the decode of the same samples to the packed weights g_mlp,
+// the features g_feat [N][F] and the raw offsets g_offset [G][3], summed
+// over views; all three are accumulated (zero them first).  rows: scratch of
+// decode_bwd_scratch_floats() floats.
 void launch_project_bwd_neural(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const uint32_t *count,
                                const BlendParams &bp, const float *dec, const float *g2d, float *gdec,
                                cudaStream_t st);
@@ -182,8 +186,10 @@ void launch_project_bwd_neural(const ViewDesc *views, int n_views, int slot, con
 // of one view for every Gaussian (neural scenes with DGS_ALIGN_QUAT).
 void launch_cell_align(const SceneDev &sc, float *cell, const float *dec, int what, float *out_center, float *out_quat,
                        cudaStream_t st);
-void launch_decode_bwd(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const uint32_t *count,
-                       const float *gdec, float *g_mlp, float *g_feat, float *g_offset, cudaStream_t st);
+void launch_decode_bwd(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const uint32_t *samples,
+                       long long nsamp, const float *gdec, float *g_mlp, float *g_feat, float *g_offset, float *rows,
+                       float *pk, cudaStream_t st);
+long long decode_bwd_scratch_floats(int F, int H, int K, long long nsamp);
 // One launch for every scene of the device scene table (dsz->n_scenes
 // entries, Gaussian counts <= G_cap, which sizes the grid).
 void launch_project_fwd_table(const ViewDesc *views, const SceneDev *scenes, long long G_cap, const uint32_t *count,

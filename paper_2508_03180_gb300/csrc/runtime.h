@@ -82,6 +82,7 @@ struct Workspace {
     DevBuf vview, gvview;         // per (view, cell): v_n as rendered, dL/dv_n
     DevBuf dec;                   // per (view, Gaussian) of neural scenes: decoded values
     DevBuf gdec;                  // and dL/d of them in the backward
+    DevBuf wpack;                 // decoder weights repacked for the decode kernels
     DevBuf gscratch;              // sink of the decode adjoint's unrequested outputs
     DevBuf sizes;                 // ChainSizes of a captured chain
     uint32_t *h_small = nullptr;  // pinned mirror of `small`
@@ -97,6 +98,7 @@ struct Workspace {
     std::vector<uint32_t> scene_ids;  // slot -> scene id
     int V = 0, total_tiles = 0;
     long long total_px = 0, L = 0, n_entries = 0, n_records = 0;
+    long long n_vis = 0;  // (view, cell) entries that survived culling: the first n_vis of zval after the depth sort
     bool bwd_done = false;
     dgs_status init();
     std::vector<DevBuf *> all();
