@@ -133,7 +133,7 @@ extern "C" dgs_status dgs_cell_align(dgs_ctx *ctx, uint32_t scene_id, int32_t wh
     // scratch: [view][packed weights][decoded G][host staging 7 N], each 256-byte aligned
     auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
     const size_t o_pk = up(sizeof(ViewDesc)),
-                 o_dec = o_pk + up(decode ? sizeof(float) * decode_pack_floats(sc.F, sc.H, sc.K) : 0),
+                 o_dec = o_pk + up(decode ? sizeof(float) * decode_scratch_floats(sc.F, sc.H, sc.K, N, G, false) : 0),
                  o_stg = o_dec + up(decode ? sizeof(float) * kDecF * G : 0),
                  total = o_stg + (out_location == DGS_HOST ? sizeof(float) * 7 * N : 0);
     dgs_status s;

@@ -589,7 +589,7 @@ dgs_status chain_forward(dgs_ctx *ctx, Workspace &ws, const std::vector<ChainVie
     for (const Scene *sc : slots) any_neural = any_neural || sc->F > 0;
     long long npk = 0;
     for (const Scene *sc : slots)
-        if (sc->F > 0) npk = std::max(npk, decode_pack_floats(sc->F, sc->H, sc->K));
+        if (sc->F > 0) npk = std::max(npk, decode_scratch_floats(sc->F, sc->H, sc->K, ws.n_vis, sc->G, false));
     if ((any_neural && (s = ws.dec.ensure(sizeof(float) * kDecF * nrec))) ||
         (any_neural && (s = ws.wpack.ensure(sizeof(float) * npk))) ||
         (s = ws.rec.ensure(sizeof(float4) * kRecF4 * nrec)) ||
@@ -769,11 +769,10 @@ extern "C" dgs_status dgs_render_backward(dgs_ctx *ctx, dgs_fwd_state *state, co
     if (neural && (o_mlp || o_f || o_off)) {
         if ((s = ws.gdec.ensure(sizeof(float) * kDecF * std::max(1LL, ws.n_records)))) return s;
         // the decode adjoint forms every output; unrequested ones go to scratch after its rows
-        const long long nrow = decode_bwd_scratch_floats(sc.F, sc.H, sc.K, ws.n_vis);
-        if ((s = ws.gscratch.ensure(sizeof(float) * (nrow + P + NF + GO))) ||
-            (s = ws.wpack.ensure(sizeof(float) * decode_pack_floats(sc.F, sc.H, sc.K))))
+        if ((s = ws.gscratch.ensure(sizeof(float) * std::max(1LL, P + NF + GO))) ||
+            (s = ws.wpack.ensure(sizeof(float) * decode_scratch_floats(sc.F, sc.H, sc.K, ws.n_vis, G, true))))
             return s;
-        float *rows = (float *)ws.gscratch.p, *gscr = rows + nrow;
+        float *gscr = (float *)ws.gscratch.p;
         float *m = o_mlp ? o_mlp : gscr, *f = o_f ? o_f : gscr + P, *off = o_off ? o_off : gscr + P + NF;
         {
             StageTimer t(ctx->prof, DGS_STAGE_PROJECT_BWD, st);
@@ -785,7 +784,7 @@ extern "C" dgs_status dgs_render_backward(dgs_ctx *ctx, dgs_fwd_state *state, co
         CK(cudaMemsetAsync(f, 0, sizeof(float) * NF, st));
         CK(cudaMemsetAsync(off, 0, sizeof(float) * GO, st));
         launch_decode_bwd((const ViewDesc *)ws.views.p, ws.V, 0, sc.dev(), (const uint32_t *)ws.zval.p, ws.n_vis,
-                          (const float *)ws.gdec.p, m, f, off, rows, (float *)ws.wpack.p, st);
+                          (const float *)ws.gdec.p, m, f, off, (float *)ws.wpack.p, st);
     } else if (!neural) {
         StageTimer t(ctx->prof, DGS_STAGE_PROJECT_BWD, st);
         launch_project_bwd((const ViewDesc *)ws.views.p, ws.V, 0, sc.dev(), (const uint32_t *)ws.count.p, bp,

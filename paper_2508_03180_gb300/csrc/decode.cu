@@ -28,7 +28,7 @@
 
 namespace dgs {
 
-constexpr int DINFO = 20;     // words of per-sample information
+constexpr int DINFO = 24;     // words of per-sample information (a record of k_decode_samples)
 constexpr int kSmemMax = 227 * 1024;
 
 struct MlpShape {
@@ -89,11 +89,18 @@ static MlpShape mlp_shape_w(int F, int H, int K, bool bwd, int W) {
     return S;
 }
 
+// Two CTAs per SM where the shared memory allows (one CTA's barrier waits
+// overlap the other's products), else the largest tile that fits.
 static MlpShape mlp_shape(int F, int H, int K, bool bwd) {
-    MlpShape S = mlp_shape_w(F, H, K, bwd, 8);
-    for (int W = 4; W >= 2 && (size_t)S.s_total * sizeof(float) > (size_t)kSmemMax; W /= 2)
-        S = mlp_shape_w(F, H, K, bwd, W);
-    return S;
+    for (int W = 8; W >= 2; W /= 2) {
+        const MlpShape S = mlp_shape_w(F, H, K, bwd, W);
+        if (2 * sizeof(float) * (size_t)S.s_total <= (size_t)kSmemMax) return S;
+    }
+    for (int W = 8; W >= 2; W /= 2) {
+        const MlpShape S = mlp_shape_w(F, H, K, bwd, W);
+        if (sizeof(float) * (size_t)S.s_total <= (size_t)kSmemMax) return S;
+    }
+    return mlp_shape_w(F, H, K, bwd, 2);
 }
 
 __device__ __forceinline__ float sigmoidf_(float x) { return 1.0f / (1.0f + expf(-x)); }
@@ -108,6 +115,7 @@ struct SampleInfo {
     int n, valid;
     long long rec;   // first record (Gaussian k = 0) of this (view, cell)
     float x[3], S[3], R[9];
+    float z4[4];     // distance and unit direction from the eye (the last four inputs)
 };
 __device__ __forceinline__ void put_info(float *s_info, int s, const SampleInfo &a) {
     float *p = s_info + s * DINFO;
@@ -119,6 +127,9 @@ __device__ __forceinline__ void put_info(float *s_info, int s, const SampleInfo 
     for (int i = 0; i < 3; ++i) { p[4 + i] = a.x[i]; p[7 + i] = a.S[i]; }
 #pragma unroll
     for (int i = 0; i < 9; ++i) p[10 + i] = a.R[i];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) p[19 + i] = a.z4[i];
+    p[23] = 0.f;
 }
 __device__ __forceinline__ SampleInfo get_info(const float *s_info, int s) {
     const float *p = s_info + s * DINFO;
@@ -130,54 +141,97 @@ __device__ __forceinline__ SampleInfo get_info(const float *s_info, int s) {
     for (int i = 0; i < 3; ++i) { a.x[i] = p[4 + i]; a.S[i] = p[7 + i]; }
 #pragma unroll
     for (int i = 0; i < 9; ++i) a.R[i] = p[10 + i];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a.z4[i] = p[19 + i];
     return a;
 }
 
-// Stage the samples [q0, q0 + S.M): their information and the input columns
-// Z[i][s] (zero for samples past the end or of another scene slot).
-__device__ void stage_samples(const MlpShape &S, float *sm, const ViewDesc *__restrict__ views, int n_views, int slot,
-                              const SceneDev &sc, const uint32_t *__restrict__ samples, long long nsamp,
-                              long long q0) {
-    const int t = threadIdx.x;
-    float *Zt = sm + S.s_z, *info = sm + S.s_info;
+// One record per sample (DINFO words): the view holding entry e (binary
+// search over the views' first entries), the cell, its first record, frame
+// and the last four inputs; invalid for entries of another scene slot.
+__global__ void __launch_bounds__(128) k_decode_samples(const ViewDesc *__restrict__ views, int n_views, int slot,
+                                                        SceneDev sc, const uint32_t *__restrict__ samples,
+                                                        long long nsamp, float *__restrict__ srec) {
     const long long N = sc.N;
-    if (t < S.M) {
-        const long long q = q0 + t;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nsamp;
+         q += (long long)gridDim.x * blockDim.x) {
         SampleInfo a{};
         a.valid = 0;
-        float z4[4] = {0.f, 0.f, 0.f, 0.f};
-        if (q < nsamp) {
-            const long long e = samples ? (long long)samples[q] : q;
-            int lo = 0, hi = n_views - 1;  // the view whose entries contain e
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (views[mid].cell_base <= e) lo = mid; else hi = mid - 1;
-            }
-            const ViewDesc &Vw = views[lo];
-            const long long n = e - Vw.cell_base;
-            if (Vw.scene_slot == slot && n >= 0 && n < N) {
-                a.valid = 1;
-                a.n = (int)n;
-                a.rec = Vw.rec_base + n * sc.K;
-#pragma unroll
-                for (int i = 0; i < 3; ++i) { a.x[i] = sc.cell[i * N + n]; a.S[i] = sc.cell[(3 + i) * N + n]; }
-                const float qw = sc.cell[6 * N + n], qx = sc.cell[7 * N + n], qy = sc.cell[8 * N + n],
-                            qz = sc.cell[9 * N + n];
-                const float in = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
-                const float w = qw * in, x = qx * in, y = qy * in, z = qz * in;
-                a.R[0] = 1.f - 2.f * (y * y + z * z); a.R[1] = 2.f * (x * y - w * z); a.R[2] = 2.f * (x * z + w * y);
-                a.R[3] = 2.f * (x * y + w * z); a.R[4] = 1.f - 2.f * (x * x + z * z); a.R[5] = 2.f * (y * z - w * x);
-                a.R[6] = 2.f * (x * z - w * y); a.R[7] = 2.f * (y * z + w * x); a.R[8] = 1.f - 2.f * (x * x + y * y);
-                const float r0 = a.x[0] - Vw.eye[0], r1 = a.x[1] - Vw.eye[1], r2 = a.x[2] - Vw.eye[2];
-                const float delta = sqrtf(r0 * r0 + r1 * r1 + r2 * r2);
-                z4[0] = delta; z4[1] = r0 / delta; z4[2] = r1 / delta; z4[3] = r2 / delta;
-            }
+        const long long e = samples ? (long long)samples[q] : q;
+        int lo = 0, hi = n_views - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (views[mid].cell_base <= e) lo = mid; else hi = mid - 1;
         }
-        put_info(info, t, a);
+        const ViewDesc &Vw = views[lo];
+        const long long n = e - Vw.cell_base;
+        if (Vw.scene_slot == slot && n >= 0 && n < N) {
+            a.valid = 1;
+            a.n = (int)n;
+            a.rec = Vw.rec_base + n * sc.K;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) Zt[(S.F + i) * S.LD + t] = z4[i];
+            for (int i = 0; i < 3; ++i) { a.x[i] = sc.cell[i * N + n]; a.S[i] = sc.cell[(3 + i) * N + n]; }
+            const float qw = sc.cell[6 * N + n], qx = sc.cell[7 * N + n], qy = sc.cell[8 * N + n],
+                        qz = sc.cell[9 * N + n];
+            const float in = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+            const float w = qw * in, x = qx * in, y = qy * in, z = qz * in;
+            a.R[0] = 1.f - 2.f * (y * y + z * z); a.R[1] = 2.f * (x * y - w * z); a.R[2] = 2.f * (x * z + w * y);
+            a.R[3] = 2.f * (x * y + w * z); a.R[4] = 1.f - 2.f * (x * x + z * z); a.R[5] = 2.f * (y * z - w * x);
+            a.R[6] = 2.f * (x * z - w * y); a.R[7] = 2.f * (y * z + w * x); a.R[8] = 1.f - 2.f * (x * x + y * y);
+            const float r0 = a.x[0] - Vw.eye[0], r1 = a.x[1] - Vw.eye[1], r2 = a.x[2] - Vw.eye[2];
+            const float delta = sqrtf(r0 * r0 + r1 * r1 + r2 * r2);
+            a.z4[0] = delta; a.z4[1] = r0 / delta; a.z4[2] = r1 / delta; a.z4[3] = r2 / delta;
+        }
+        float rec[DINFO];
+        put_info(rec, 0, a);
+        float4 *dst = reinterpret_cast<float4 *>(srec + q * DINFO);
+#pragma unroll
+        for (int i = 0; i < DINFO / 4; ++i) dst[i] = make_float4(rec[4 * i], rec[4 * i + 1], rec[4 * i + 2], rec[4 * i + 3]);
+    }
+}
+
+// Every Gaussian's centre x_n + R(Q_n)(O_pos S_n) and Eq. 11 bound 1 - |O_pos|
+// (the same in every view), for the forward's epilogue.
+__global__ void __launch_bounds__(128) k_decode_centres(SceneDev sc, float4 *__restrict__ gc) {
+    const long long N = sc.N, G = sc.G;
+    const int K = sc.K;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < G; g += (long long)gridDim.x * blockDim.x) {
+        const long long n = g / K;
+        const float qw = sc.cell[6 * N + n], qx = sc.cell[7 * N + n], qy = sc.cell[8 * N + n], qz = sc.cell[9 * N + n];
+        const float in = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+        const float w = qw * in, x = qx * in, y = qy * in, z = qz * in;
+        float o0 = sc.goff[g], o1 = sc.goff[G + g], o2 = sc.goff[2 * G + g];
+        const float on = sqrtf(o0 * o0 + o1 * o1 + o2 * o2);
+        if (on > 1.0f) { o0 /= on; o1 /= on; o2 /= on; }
+        const float l0 = o0 * sc.cell[3 * N + n], l1 = o1 * sc.cell[4 * N + n], l2 = o2 * sc.cell[5 * N + n];
+        const float R0 = 1.f - 2.f * (y * y + z * z), R1 = 2.f * (x * y - w * z), R2 = 2.f * (x * z + w * y);
+        const float R3 = 2.f * (x * y + w * z), R4 = 1.f - 2.f * (x * x + z * z), R5 = 2.f * (y * z - w * x);
+        const float R6 = 2.f * (x * z - w * y), R7 = 2.f * (y * z + w * x), R8 = 1.f - 2.f * (x * x + y * y);
+        gc[g] = make_float4(sc.cell[n] + R0 * l0 + R1 * l1 + R2 * l2, sc.cell[N + n] + R3 * l0 + R4 * l1 + R5 * l2,
+                            sc.cell[2 * N + n] + R6 * l0 + R7 * l1 + R8 * l2, 1.0f - fminf(on, 1.0f));
+    }
+}
+
+// Stage the samples [q0, q0 + S.M): their records (invalid past the end) and
+// the input columns Z[i][s] (zero for invalid samples).
+__device__ void stage_samples(const MlpShape &S, float *sm, const SceneDev &sc, const float *__restrict__ srec,
+                              long long nsamp, long long q0) {
+    const int t = threadIdx.x;
+    float *Zt = sm + S.s_z, *info = sm + S.s_info;
+    const int nv = (int)min((long long)S.M, nsamp - q0);
+    {
+        const float4 *s4 = reinterpret_cast<const float4 *>(srec + q0 * DINFO);
+        float4 *d4 = reinterpret_cast<float4 *>(info);
+        for (int i = t; i < S.M * (DINFO / 4); i += blockDim.x)
+            d4[i] = i < nv * (DINFO / 4) ? __ldg(s4 + i) : make_float4(0.f, 0.f, 0.f, 0.f);  // valid = 0 past the end
     }
     __syncthreads();
+    if (t < S.M) {
+        const float *p = info + t * DINFO;
+        const bool v = __float_as_int(p[1]) != 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) Zt[(S.F + i) * S.LD + t] = v ? p[19 + i] : 0.f;
+    }
     // latent features: row n of the [N][F] feature matrix into column s
     // (a warp per sample, lanes along the row)
     const int nw = blockDim.x >> 5;
@@ -313,10 +367,9 @@ __device__ __forceinline__ void ball_offset(const SceneDev &sc, long long g, flo
 }
 
 template <int HW>
-__global__ void __launch_bounds__(256) k_decode(const ViewDesc *__restrict__ views, int n_views, int slot,
-                                                    SceneDev sc, MlpShape S, const float *__restrict__ pk,
-                                                    const uint32_t *__restrict__ samples, long long nsamp,
-                                                    float *__restrict__ dec) {
+__global__ void __launch_bounds__(256) k_decode(SceneDev sc, MlpShape S, const float *__restrict__ pk,
+                                                const float *__restrict__ srec, const float4 *__restrict__ gc,
+                                                long long nsamp, float *__restrict__ dec) {
     extern __shared__ float4 smem4[];
     float *sm = reinterpret_cast<float *>(smem4);
     const int K = S.K;
@@ -324,7 +377,7 @@ __global__ void __launch_bounds__(256) k_decode(const ViewDesc *__restrict__ vie
         copy_f4(sm + S.s_w, pk + S.g_w1t, S.I * 4 * S.Hp);
         copy_f4(sm + S.s_b1, pk + S.g_b1, 4 * S.Hp);
         copy_f4(sm + S.s_b2, pk + S.g_b2, S.rb[4]);
-        stage_samples(S, sm, views, n_views, slot, sc, samples, nsamp, q0);
+        stage_samples(S, sm, sc, srec, nsamp, q0);
         __syncthreads();
         layer1<HW>(S, sm);
         __syncthreads();
@@ -336,19 +389,15 @@ __global__ void __launch_bounds__(256) k_decode(const ViewDesc *__restrict__ vie
         const float *Ot = sm + S.s_o, *info = sm + S.s_info;
         for (int idx = threadIdx.x; idx < S.M * K; idx += blockDim.x) {
             const int s = idx / K, k = idx - s * K;
-            const SampleInfo a = get_info(info, s);
-            if (!a.valid) continue;
-            const long long g = (long long)a.n * K + k;
-            float Ob[3], O[3], on;
-            ball_offset(sc, g, Ob, O, on);
-            const float lim = 1.0f - fminf(on, 1.0f);
+            const float *p = info + s * DINFO;
+            if (__float_as_int(p[1]) == 0) continue;
+            const long long g = (long long)__float_as_int(p[0]) * K + k;
+            const long long rec = (long long)(unsigned)__float_as_int(p[2]) | ((long long)__float_as_int(p[3]) << 32);
+            const float4 c4 = __ldg(gc + g);  // centre and the Eq. 11 bound
             float o[kDecF];
-            const float l0 = Ob[0] * a.S[0], l1 = Ob[1] * a.S[1], l2 = Ob[2] * a.S[2];
-            o[0] = a.x[0] + a.R[0] * l0 + a.R[1] * l1 + a.R[2] * l2;
-            o[1] = a.x[1] + a.R[3] * l0 + a.R[4] * l1 + a.R[5] * l2;
-            o[2] = a.x[2] + a.R[6] * l0 + a.R[7] * l1 + a.R[8] * l2;
+            o[0] = c4.x; o[1] = c4.y; o[2] = c4.z;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) o[3 + c] = fminf(sigmoidf_(Ot[orow(S, 2, 3 * k + c) + s]), lim) * a.S[c];
+            for (int c = 0; c < 3; ++c) o[3 + c] = fminf(sigmoidf_(Ot[orow(S, 2, 3 * k + c) + s]), c4.w) * p[7 + c];
             float qv[4];
 #pragma unroll
             for (int c = 0; c < 4; ++c) qv[c] = Ot[orow(S, 3, 4 * k + c) + s];
@@ -363,7 +412,7 @@ __global__ void __launch_bounds__(256) k_decode(const ViewDesc *__restrict__ vie
             o[10] = tanhf(Ot[orow(S, 0, k) + s]);
 #pragma unroll
             for (int c = 0; c < 3; ++c) o[11 + c] = sigmoidf_(Ot[orow(S, 1, 3 * k + c) + s]);
-            float2 *dst = reinterpret_cast<float2 *>(dec + (a.rec + k) * kDecF);
+            float2 *dst = reinterpret_cast<float2 *>(dec + (rec + k) * kDecF);
 #pragma unroll
             for (int i = 0; i < kDecF / 2; ++i) dst[i] = make_float2(o[2 * i], o[2 * i + 1]);
         }
@@ -382,10 +431,9 @@ __global__ void __launch_bounds__(256) k_decode(const ViewDesc *__restrict__ vie
 // gradients (k_mlp_wgrad).  Decisions held fixed: the ReLU masks, the side of
 // the Eq. 11 minimum, sigma <= 0 (gdec is zero there).
 template <int HW>
-__global__ void __launch_bounds__(256) k_decode_bwd(const ViewDesc *__restrict__ views, int n_views, int slot,
-                                                        SceneDev sc, MlpShape S, const float *__restrict__ pk,
-                                                        const uint32_t *__restrict__ samples, long long nsamp,
-                                                        const float *__restrict__ gdec,
+__global__ void __launch_bounds__(256) k_decode_bwd(SceneDev sc, MlpShape S, const float *__restrict__ pk,
+                                                    const float *__restrict__ srec, long long nsamp,
+                                                    const float *__restrict__ gdec,
                                                         float *__restrict__ g_feat, float *__restrict__ g_offset,
                                                         float *__restrict__ rows) {
     extern __shared__ float4 smem4[];
@@ -396,7 +444,7 @@ __global__ void __launch_bounds__(256) k_decode_bwd(const ViewDesc *__restrict__
         copy_f4(sm + S.s_w, pk + S.g_w1t, S.I * 4 * S.Hp);
         copy_f4(sm + S.s_b1, pk + S.g_b1, 4 * S.Hp);
         copy_f4(sm + S.s_b2, pk + S.g_b2, S.rb[4]);
-        stage_samples(S, sm, views, n_views, slot, sc, samples, nsamp, q0);
+        stage_samples(S, sm, sc, srec, nsamp, q0);
         __syncthreads();
         layer1<HW>(S, sm);
         __syncthreads();
@@ -548,17 +596,20 @@ __global__ void __launch_bounds__(256) k_decode_bwd(const ViewDesc *__restrict__
                 float acc[8][2];
 #pragma unroll
                 for (int s = 0; s < 8; ++s) acc[s][0] = acc[s][1] = 0.f;
-                for (int jj = 0; jj < H4; ++jj) {
-                    const int D = jj / Hp, j = jj - D * Hp;
-                    const float *dh = DHt + hrow(S, D, j) + 8 * warp;
-                    const float4 da = *reinterpret_cast<const float4 *>(dh);
-                    const float4 dc = *reinterpret_cast<const float4 *>(dh + 4);
-                    const float d[8] = {da.x, da.y, da.z, da.w, dc.x, dc.y, dc.z, dc.w};
-                    const float w0 = W[jj * S.I + i0], w1 = u1 ? W[jj * S.I + i1] : 0.f;
+                for (int D = 0; D < 4; ++D) {
+                    const float *dh = DHt + hrow(S, D, 0) + 8 * warp;
+                    const float *wd = W + D * Hp * S.I;
+#pragma unroll 2
+                    for (int j = 0; j < Hp; ++j) {
+                        const float4 da = *reinterpret_cast<const float4 *>(dh + j * S.LD);
+                        const float4 dc = *reinterpret_cast<const float4 *>(dh + j * S.LD + 4);
+                        const float d[8] = {da.x, da.y, da.z, da.w, dc.x, dc.y, dc.z, dc.w};
+                        const float w0 = wd[j * S.I + i0], w1 = u1 ? wd[j * S.I + i1] : 0.f;
 #pragma unroll
-                    for (int s = 0; s < 8; ++s) {
-                        acc[s][0] = fmaf(d[s], w0, acc[s][0]);
-                        acc[s][1] = fmaf(d[s], w1, acc[s][1]);
+                        for (int s = 0; s < 8; ++s) {
+                            acc[s][0] = fmaf(d[s], w0, acc[s][0]);
+                            acc[s][1] = fmaf(d[s], w1, acc[s][1]);
+                        }
                     }
                 }
 #pragma unroll
@@ -571,97 +622,126 @@ __global__ void __launch_bounds__(256) k_decode_bwd(const ViewDesc *__restrict__
                 }
             }
         }
-        // the rows of this tile's samples for the weight gradients
+        // the rows of this tile's samples for the weight gradients: Z, H, dL/dh, dL/do
         {
             const int nv = (int)min((long long)S.M, nsamp - q0);
             const float *Zt = sm + S.s_z;
-            for (int s = warp; s < nv; s += S.W)
-                for (int c = lane; c < S.row_all; c += 32) {
-                float v;
-                if (c < S.row_h) {
-                    v = Zt[c * S.LD + s];
-                } else if (c < S.row_dh) {
-                    const int jj = c - S.row_h, D = jj / Hp;
-                    v = Ht[hrow(S, D, jj - D * Hp) + s];
-                } else if (c < S.row_do) {
-                    const int jj = c - S.row_dh, D = jj / Hp;
-                    v = DHt[hrow(S, D, jj - D * Hp) + s];
-                } else {
-                    const int rr = c - S.row_do;
-                    v = Ot[rr * S.LD + 8 * out_block(S, rr) + s];
-                }
-                rows[(q0 + s) * S.row_all + c] = v;
-                }
+            for (int s = warp; s < nv; s += S.W) {
+                float *row = rows + (q0 + s) * S.row_all;
+                for (int c = lane; c < S.I; c += 32) row[S.row_z + c] = Zt[c * S.LD + s];
+                for (int D = 0; D < 4; ++D)
+                    for (int j = lane; j < Hp; j += 32) {
+                        row[S.row_h + D * Hp + j] = Ht[hrow(S, D, j) + s];
+                        row[S.row_dh + D * Hp + j] = DHt[hrow(S, D, j) + s];
+                    }
+                for (int D = 0; D < 4; ++D)
+                    for (int r = lane; r < S.rb[D + 1] - S.rb[D]; r += 32)
+                        row[S.row_do + S.rb[D] + r] = Ot[orow(S, D, r) + s];
+            }
         }
         __syncthreads();
     }
 }
 
-// Weight gradients from the per-sample rows: for every decoder D
-//   dW1_D [H][I] | db1_D = sum_s dh_D(s) [z(s) | 1]^T
-//   dW2_D [nout][H] | db2_D = sum_s do_D(s) [h_D(s) | 1]^T
-// Eight products C[a][b] = sum_s A[s][a] B[s][b] (b = nb: the ones column,
-// i.e. the bias).  A CTA takes one 64 x 64 tile of one product over a chunk
-// of samples (32 rows at a time through shared memory, 4 x 4 outputs per
-// thread) and adds its tile to g_mlp with one atomic add per output.
+// Weight gradients from the per-sample rows:
+//   dW1 | db1 of all decoders at once: C[jj][b] = sum_s dh_s[jj] [z_s | 1][b]  (jj over 4Hp)
+//   dW2_D | db2_D per decoder:       C[r][b]  = sum_s do_s[rb_D + r] [h_D,s | 1][b]
+// (the ones column gives the biases).  A CTA takes one 32 x 48 tile of one
+// product over a chunk of samples: slabs of 32 samples pass through shared
+// memory (double-buffered; the next slab is loaded into registers while the
+// current one is multiplied), 4 x 4 outputs per thread, and the tile goes to
+// g_mlp with one atomic add per output at the end.
+constexpr int WT_A = 32, WT_B = 48, WT_S = 32, WT_T = 96;
+constexpr int WT_LA = (WT_S * WT_A + WT_T - 1) / WT_T, WT_LB = WT_S * WT_B / WT_T;
 struct WgProblem {
-    int a_off, na, b_off, nb, wo, bo;  // column offsets in A and B rows, sizes, packed output offsets
-    int a_is_dh;                        // A = dL/dh rows and B = Z rows (else dL/do and H rows)
+    int a_col, na, b_col, nb;  // first column of A and of B in a row, their widths
+    int kind;                  // -1: W1 of all decoders; D >= 0: W2 of decoder D
 };
-struct WgProblems { WgProblem p[8]; };
+struct WgProblems { WgProblem p[5]; };
 
-__global__ void __launch_bounds__(256) k_mlp_wgrad(const float *__restrict__ rows, MlpShape S, long long nsamp,
-                                                   int chunk, WgProblems probs, float *__restrict__ g_mlp) {
-    __shared__ float4 sA4[32 * 17], sB4[32 * 17];
-    float *sA = reinterpret_cast<float *>(sA4), *sB = reinterpret_cast<float *>(sB4);
+__global__ void __launch_bounds__(WT_T) k_mlp_wgrad(const float *__restrict__ rows, MlpShape S, long long nsamp,
+                                                    int chunk, WgProblems probs, float *__restrict__ g_mlp) {
+    __shared__ __align__(16) float sA[2][WT_S][WT_A + 4];
+    __shared__ __align__(16) float sB[2][WT_S][WT_B + 4];
     const WgProblem P = probs.p[blockIdx.z];
-    const int ta = blockIdx.y >> 1, tb = blockIdx.y & 1;
-    const int a_base = 64 * ta, b_base = 64 * tb;
-    if (a_base >= P.na || b_base > P.nb) return;
+    const int a0 = WT_A * (blockIdx.y >> 1), b0 = WT_B * (blockIdx.y & 1);
+    if (a0 >= P.na || b0 > P.nb) return;
     const long long s0 = (long long)blockIdx.x * chunk, s1 = min(nsamp, s0 + chunk);
-    const int t = threadIdx.x, ra = (t >> 4) * 4, rb = (t & 15) * 4;
-    const int acol = P.a_is_dh ? S.row_dh : S.row_do;
-    const int bcol = P.a_is_dh ? S.row_z : S.row_h;
+    if (s0 >= s1) return;
+    const int t = threadIdx.x, ga = t / 12, gb = t - 12 * ga;
+    float ra[WT_LA], rb[WT_LB];
+    auto load = [&](long long sb) {
+#pragma unroll
+        for (int u = 0; u < WT_LA; ++u) {
+            const int idx = t + WT_T * u, r = idx >> 5, c = idx & 31;
+            const long long s = sb + r;
+            ra[u] = (idx < WT_S * WT_A && s < s1 && a0 + c < P.na) ? rows[s * S.row_all + P.a_col + a0 + c] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < WT_LB; ++u) {
+            const int idx = t + WT_T * u, r = idx / WT_B, c = idx - r * WT_B, b = b0 + c;
+            const long long s = sb + r;
+            rb[u] = s < s1 ? (b < P.nb ? rows[s * S.row_all + P.b_col + b] : (b == P.nb ? 1.0f : 0.f)) : 0.f;
+        }
+    };
+    auto store = [&](int buf) {
+#pragma unroll
+        for (int u = 0; u < WT_LA; ++u) {
+            const int idx = t + WT_T * u;
+            if (idx < WT_S * WT_A) sA[buf][idx >> 5][idx & 31] = ra[u];
+        }
+#pragma unroll
+        for (int u = 0; u < WT_LB; ++u) {
+            const int idx = t + WT_T * u, r = idx / WT_B;
+            sB[buf][r][idx - r * WT_B] = rb[u];
+        }
+    };
     float acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-    for (long long sb = s0; sb < s1; sb += 32) {
-        for (int idx = t; idx < 32 * 64; idx += 256) {
-            const int r = idx >> 6, c = idx & 63;
-            const long long s = sb + r;
-            const int a = a_base + c, b = b_base + c;
-            float va = 0.f, vb = 0.f;
-            if (s < s1) {
-                const float *row = rows + s * S.row_all;
-                if (a < P.na) va = row[acol + P.a_off + a];
-                vb = b < P.nb ? row[bcol + P.b_off + b] : (b == P.nb ? 1.0f : 0.f);
-            }
-            sA[r * 68 + c] = va;
-            sB[r * 68 + c] = vb;
-        }
-        __syncthreads();
-#pragma unroll 4
-        for (int r = 0; r < 32; ++r) {
-            const float4 av = *reinterpret_cast<const float4 *>(sA + r * 68 + ra);
-            const float4 bv = *reinterpret_cast<const float4 *>(sB + r * 68 + rb);
+    load(s0);
+    store(0);
+    __syncthreads();
+    int buf = 0;
+    for (long long sb = s0; sb < s1; sb += WT_S) {
+        const bool more = sb + WT_S < s1;
+        if (more) load(sb + WT_S);
+#pragma unroll 8
+        for (int r = 0; r < WT_S; ++r) {
+            const float4 av = *reinterpret_cast<const float4 *>(&sA[buf][r][4 * ga]);
+            const float4 bv = *reinterpret_cast<const float4 *>(&sB[buf][r][4 * gb]);
             const float x[4] = {av.x, av.y, av.z, av.w}, y[4] = {bv.x, bv.y, bv.z, bv.w};
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(x[i], y[j], acc[i][j]);
         }
+        if (more) store(buf ^ 1);
         __syncthreads();
+        buf ^= 1;
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 4; ++i) {
+        const int a = a0 + 4 * ga + i;
+        if (a >= P.na) continue;
+        int wrow, brow;  // packed offsets of row a's weights and of its bias
+        if (P.kind < 0) {
+            const int D = a / S.Hp, j = a - D * S.Hp;
+            if (j >= S.H) continue;
+            wrow = S.w1o[D] + j * S.I;
+            brow = S.b1o[D] + j;
+        } else {
+            wrow = S.w2o[P.kind] + a * S.H;
+            brow = S.b2o[P.kind] + a;
+        }
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const int a = a_base + ra + i, b = b_base + rb + j;
-            if (a < P.na && b <= P.nb && acc[i][j] != 0.f)
-                atomicAdd(g_mlp + (b < P.nb ? P.wo + a * P.nb + b : P.bo + a), acc[i][j]);
+            const int b = b0 + 4 * gb + j;
+            if (b <= P.nb && acc[i][j] != 0.f) atomicAdd(g_mlp + (b < P.nb ? wrow + b : brow), acc[i][j]);
         }
+    }
 }
 
 // ---------------------------------------------------------------- launchers
@@ -677,57 +757,63 @@ static int persistent_grid(Kern k, int threads, size_t smem, long long tiles) {
     return (int)std::max(1LL, std::min(tiles, cap));
 }
 
-long long decode_pack_floats(int F, int H, int K) { return mlp_shape(F, H, K, true).g_total; }
+// Scratch of one decode call: [packed weights][sample records][forward: centres
+// and bounds per Gaussian | adjoint: per-sample rows].
+long long decode_scratch_floats(int F, int H, int K, long long nsamp, long long G, bool bwd) {
+    const MlpShape S = mlp_shape(F, H, K, bwd);
+    const long long n = std::max(1LL, nsamp);
+    return up_to(S.g_total, 4) + n * DINFO + (bwd ? (long long)S.row_all * n : 4 * std::max(1LL, G));
+}
 
-static void pack_weights(const MlpShape &S, const float *mlp, float *pk, cudaStream_t st) {
-    k_mlp_pack<<<(S.g_total + 255) / 256, 256, 0, st>>>(mlp, S, pk);
+static void decode_prep(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const MlpShape &S,
+                        const uint32_t *samples, long long nsamp, float *pk, float *srec, cudaStream_t st) {
+    k_mlp_pack<<<(S.g_total + 255) / 256, 256, 0, st>>>(sc.mlp, S, pk);
+    const long long b = std::min((nsamp + 127) / 128, 152LL * 16);
+    k_decode_samples<<<(unsigned)std::max(1LL, b), 128, 0, st>>>(views, n_views, slot, sc, samples, nsamp, srec);
 }
 
 void launch_decode(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const uint32_t *samples,
-                   long long nsamp, float *dec, float *pk, cudaStream_t st) {
+                   long long nsamp, float *dec, float *scratch, cudaStream_t st) {
     if (nsamp <= 0 || !sc.feat) return;
     const MlpShape S = mlp_shape(sc.F, sc.H, sc.K, false);
-    pack_weights(S, sc.mlp, pk, st);
+    float *pk = scratch, *srec = scratch + up_to(S.g_total, 4);
+    float4 *gc = reinterpret_cast<float4 *>(srec + nsamp * DINFO);
+    decode_prep(views, n_views, slot, sc, S, samples, nsamp, pk, srec, st);
+    const long long bg = std::min((sc.G + 127) / 128, 152LL * 16);
+    k_decode_centres<<<(unsigned)std::max(1LL, bg), 128, 0, st>>>(sc, gc);
     const size_t smem = sizeof(float) * (size_t)S.s_total;
     const long long tiles = (nsamp + S.M - 1) / S.M;
     if (S.HW == 4) {
         const int b = persistent_grid(k_decode<4>, 32 * S.W, smem, tiles);
-        k_decode<4><<<b, 32 * S.W, smem, st>>>(views, n_views, slot, sc, S, pk, samples, nsamp, dec);
+        k_decode<4><<<b, 32 * S.W, smem, st>>>(sc, S, pk, srec, gc, nsamp, dec);
     } else {
         const int b = persistent_grid(k_decode<8>, 32 * S.W, smem, tiles);
-        k_decode<8><<<b, 32 * S.W, smem, st>>>(views, n_views, slot, sc, S, pk, samples, nsamp, dec);
+        k_decode<8><<<b, 32 * S.W, smem, st>>>(sc, S, pk, srec, gc, nsamp, dec);
     }
 }
 
-long long decode_bwd_scratch_floats(int F, int H, int K, long long nsamp) {
-    return (long long)mlp_shape(F, H, K, true).row_all * std::max(1LL, nsamp);
-}
-
 void launch_decode_bwd(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const uint32_t *samples,
-                       long long nsamp, const float *gdec, float *g_mlp, float *g_feat, float *g_offset, float *rows,
-                       float *pk, cudaStream_t st) {
+                       long long nsamp, const float *gdec, float *g_mlp, float *g_feat, float *g_offset,
+                       float *scratch, cudaStream_t st) {
     if (nsamp <= 0 || !sc.feat) return;
     const MlpShape S = mlp_shape(sc.F, sc.H, sc.K, true);
-    pack_weights(S, sc.mlp, pk, st);
+    float *pk = scratch, *srec = scratch + up_to(S.g_total, 4), *rows = srec + nsamp * DINFO;
+    decode_prep(views, n_views, slot, sc, S, samples, nsamp, pk, srec, st);
     const size_t smem = sizeof(float) * (size_t)S.s_total;
     const long long tiles = (nsamp + S.M - 1) / S.M;
     if (S.HW == 4) {
         const int b = persistent_grid(k_decode_bwd<4>, 32 * S.W, smem, tiles);
-        k_decode_bwd<4><<<b, 32 * S.W, smem, st>>>(views, n_views, slot, sc, S, pk, samples, nsamp, gdec, g_feat,
-                                                  g_offset, rows);
+        k_decode_bwd<4><<<b, 32 * S.W, smem, st>>>(sc, S, pk, srec, nsamp, gdec, g_feat, g_offset, rows);
     } else {
         const int b = persistent_grid(k_decode_bwd<8>, 32 * S.W, smem, tiles);
-        k_decode_bwd<8><<<b, 32 * S.W, smem, st>>>(views, n_views, slot, sc, S, pk, samples, nsamp, gdec, g_feat,
-                                                  g_offset, rows);
+        k_decode_bwd<8><<<b, 32 * S.W, smem, st>>>(sc, S, pk, srec, nsamp, gdec, g_feat, g_offset, rows);
     }
     WgProblems pr{};
-    for (int D = 0; D < 4; ++D) {
-        pr.p[D] = WgProblem{D * S.Hp, S.H, 0, S.I, S.w1o[D], S.b1o[D], 1};
-        pr.p[4 + D] = WgProblem{S.rb[D], S.nout[D], D * S.Hp, S.H, S.w2o[D], S.b2o[D], 0};
-    }
-    const int chunk = 2048;
-    const dim3 grid((unsigned)((nsamp + chunk - 1) / chunk), 4, 8);
-    k_mlp_wgrad<<<grid, 256, 0, st>>>(rows, S, nsamp, chunk, pr, g_mlp);
+    pr.p[0] = WgProblem{S.row_dh, 4 * S.Hp, S.row_z, S.I, -1};
+    for (int D = 0; D < 4; ++D) pr.p[1 + D] = WgProblem{S.row_do + S.rb[D], S.nout[D], S.row_h + D * S.Hp, S.H, D};
+    const int chunk = 4096;
+    const dim3 grid((unsigned)((nsamp + chunk - 1) / chunk), 16, 5);
+    k_mlp_wgrad<<<grid, WT_T, 0, st>>>(rows, S, nsamp, chunk, pr, g_mlp);
 }
 
 }  // namespace dgs

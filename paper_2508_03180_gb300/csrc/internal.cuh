@@ -166,9 +166,10 @@ void launch_gauss_bin(const ViewDesc *views, int n_views, const SceneDev &sc, co
 // for sample q) of scene `slot` into dec [rec_base + g][kDecF], then their
 // records (colour and opacity as decoded).  Features are rows [N][F].
 void launch_decode(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const uint32_t *samples,
-                   long long nsamp, float *dec, float *pk, cudaStream_t st);
-// Scratch floats for the weights repacked once per decode call (pk above).
-long long decode_pack_floats(int F, int H, int K);
+                   long long nsamp, float *dec, float *scratch, cudaStream_t st);
+// Floats of scratch (16-byte aligned) that one launch_decode (bwd = false)
+// or launch_decode_bwd (bwd = true) call needs.
+long long decode_scratch_floats(int F, int H, int K, long long nsamp, long long G, bool bwd);
 void launch_project_neural(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const uint32_t *count,
                            const float *vview, const float *dec, const BlendParams &bp, float4 *rec, float *g2d_zero,
                            cudaStream_t st);
@@ -176,8 +177,7 @@ void launch_project_neural(const ViewDesc *views, int n_views, int slot, const S
 // decoded values of every decoded (view, Gaussian) (gdec, layout of dec),
 // then through the decode of the same samples to the packed weights g_mlp,
 // the features g_feat [N][F] and the raw offsets g_offset [G][3], summed
-// over views; all three are accumulated (zero them first).  rows: scratch of
-// decode_bwd_scratch_floats() floats.
+// over views; all three are accumulated (zero them first).
 void launch_project_bwd_neural(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const uint32_t *count,
                                const BlendParams &bp, const float *dec, const float *g2d, float *gdec,
                                cudaStream_t st);
@@ -187,9 +187,8 @@ void launch_project_bwd_neural(const ViewDesc *views, int n_views, int slot, con
 void launch_cell_align(const SceneDev &sc, float *cell, const float *dec, int what, float *out_center, float *out_quat,
                        cudaStream_t st);
 void launch_decode_bwd(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const uint32_t *samples,
-                       long long nsamp, const float *gdec, float *g_mlp, float *g_feat, float *g_offset, float *rows,
-                       float *pk, cudaStream_t st);
-long long decode_bwd_scratch_floats(int F, int H, int K, long long nsamp);
+                       long long nsamp, const float *gdec, float *g_mlp, float *g_feat, float *g_offset,
+                       float *scratch, cudaStream_t st);
 // One launch for every scene of the device scene table (dsz->n_scenes
 // entries, Gaussian counts <= G_cap, which sizes the grid).
 void launch_project_fwd_table(const ViewDesc *views, const SceneDev *scenes, long long G_cap, const uint32_t *count,
