@@ -460,6 +460,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--views", type=int, default=N_VIEWS, help="views per step (profiling of smaller cases)")
+    ap.add_argument("--leg", default="all", choices=["all", "neural"],
+                    help="neural: only the neural-cell fwd+bwd leg (its JSON object), for profiling the decode")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -471,6 +473,12 @@ def main():
     world, rank, local = dist_setup(args)
     torch.cuda.set_device(local)
     rctx = Context(device=local)
+    if args.leg == "neural":
+        if rank == 0:
+            alu = rctx.probe_alu()
+            print(json.dumps(neural_fwdbwd_bench(rctx, alu["fp32_tflops"], steps=args.steps)), flush=True)
+        rctx.close()
+        return
     scene = synth.scene_multiscale()
     sid = rctx.upload_scene(scene)
     nv = args.views
