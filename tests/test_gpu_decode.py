@@ -23,7 +23,7 @@ def rctx():
     c.close()
 
 
-@pytest.mark.parametrize("F,H,K", [(32, 32, 6), (16, 24, 10)])
+@pytest.mark.parametrize("F,H,K", [(32, 32, 6), (16, 24, 10), (20, 36, 7), (64, 64, 32)])
 def test_decode_and_render(rctx, F, H, K):
     from paper_2508_03180_gb300 import _lib as L
     sc = synth.neural_scene(n_cells=900, K=K, F=F, H=H, seed=F + K)
@@ -108,7 +108,8 @@ def _neural_oracle_grads(sc, cams, dl_flat, gs, dec):
     return tot
 
 
-@pytest.mark.parametrize("F,H,K,stretch,location", [(8, 12, 4, 1.0, "device"), (12, 16, 6, 1.6, "host")])
+@pytest.mark.parametrize("F,H,K,stretch,location", [(8, 12, 4, 1.0, "device"), (12, 16, 6, 1.6, "host"),
+                                                     (20, 36, 7, 1.0, "device"), (64, 64, 32, 1.2, "device")])
 def test_gradients_through_the_decode(rctx, F, H, K, stretch, location):
     """dL/d(weights, features, offsets) summed over two views against the
     FP64 oracle.  stretch > 1 pushes some offsets outside the unit ball (the
