@@ -204,9 +204,15 @@ __device__ __forceinline__ void blend_fwd_unit(int unit, const ViewDesc *__restr
         const float4 *r = s_rec[buf];
         const float v = r[2].w;
         unsigned mask = __ballot_sync(0xffffffffu, lane < K && touches_rows(r[kRecF4 * lane], bx0, by0, (float)ROWS));
-        float A0[PPL], A1[PPL], A2[PPL], B[PPL], P[PPL];
+        // the lane's two pixels of a row as packed pairs (one f32x2 operation
+        // per pair; per component the same IEEE operations as one pixel)
+        float2 A0[NR], A1[NR], A2[NR], B[NR], P[NR];
 #pragma unroll
-        for (int q = 0; q < PPL; ++q) { A0[q] = A1[q] = A2[q] = B[q] = 0.f; P[q] = 1.0f; }
+        for (int rr = 0; rr < NR; ++rr) {
+            A0[rr] = A1[rr] = A2[rr] = B[rr] = make_float2(0.f, 0.f);
+            P[rr] = make_float2(1.0f, 1.0f);
+        }
+        const float2 v2 = make_float2(v, v);
         for (; mask; mask &= mask - 1) {
             const int k = __ffs(mask) - 1;
             const float4 r0 = r[3 * k];
@@ -231,26 +237,35 @@ __device__ __forceinline__ void blend_fwd_unit(int unit, const ViewDesc *__restr
             if (!any) continue;
             const float4 r1 = r[3 * k + 1];
             const float4 r2 = r[3 * k + 2];
-            const float pdx[2] = {r1.x * dx[0], r1.x * dx[1]};
+            const float2 pdx = __fmul2_rn(make_float2(r1.x, r1.x), make_float2(dx[0], dx[1]));
 #pragma unroll
-            for (int q = 0; q < PPL; ++q) {
-                if (h[q]) {
-                    const float dyq = dy[q >> 1];
-                    const float s1 = fmaf(r1.y, dyq, pdx[q & 1]), s2 = r1.z * dyq;
-                    const float al = fminf(r1.w * ex2_approx(-fmaf(s1, s1, s2 * s2)), bp.alpha_max);
-                    A0[q] += al * r2.x; A1[q] += al * r2.y; A2[q] += al * r2.z;
-                    B[q] += al;
-                    P[q] -= P[q] * (v * al);
-                }
+            for (int rr = 0; rr < NR; ++rr) {
+                const float dyq = dy[rr];
+                const float s2 = r1.z * dyq, s22 = s2 * s2;
+                const float2 s1 = __ffma2_rn(make_float2(r1.y, r1.y), make_float2(dyq, dyq), pdx);
+                const float2 qd = __ffma2_rn(s1, s1, make_float2(s22, s22));
+                float2 al = __fmul2_rn(make_float2(r1.w, r1.w), make_float2(ex2_approx(-qd.x), ex2_approx(-qd.y)));
+                // a pixel the Gaussian does not reach takes alpha 0: every update below leaves it unchanged
+                al.x = h[2 * rr] ? fminf(al.x, bp.alpha_max) : 0.f;
+                al.y = h[2 * rr + 1] ? fminf(al.y, bp.alpha_max) : 0.f;
+                A0[rr] = __ffma2_rn(al, make_float2(r2.x, r2.x), A0[rr]);
+                A1[rr] = __ffma2_rn(al, make_float2(r2.y, r2.y), A1[rr]);
+                A2[rr] = __ffma2_rn(al, make_float2(r2.z, r2.z), A2[rr]);
+                B[rr] = __fadd2_rn(B[rr], al);
+                P[rr] = __ffma2_rn(make_float2(-P[rr].x, -P[rr].y), __fmul2_rn(v2, al), P[rr]);
             }
         }
 #pragma unroll
         for (int q = 0; q < PPL; ++q) {
             if (!done[q]) {
+                const int rr = q >> 1;
+                const bool hi = q & 1;
                 const float w = v * T[q];
-                N0[q] += w * A0[q]; N1[q] += w * A1[q]; N2[q] += w * A2[q];
-                D[q] += w * B[q];
-                T[q] *= P[q];
+                N0[q] = fmaf(w, hi ? A0[rr].y : A0[rr].x, N0[q]);
+                N1[q] = fmaf(w, hi ? A1[rr].y : A1[rr].x, N1[q]);
+                N2[q] = fmaf(w, hi ? A2[rr].y : A2[rr].x, N2[q]);
+                D[q] = fmaf(w, hi ? B[rr].y : B[rr].x, D[q]);
+                T[q] *= hi ? P[rr].y : P[rr].x;
                 ++n[q];
             }
         }
@@ -477,7 +492,8 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return y;
 }
 
-// Screen-space gradient terms of one (pixel, Gaussian) pair, with the
+// Screen-space gradient terms of (pixel, Gaussian) pairs for the two pixels
+// of one lane row at once (one f32x2 operation per pixel pair), with the
 // constant factors left to the caller (applied once per reduced total):
 //   acc[0..1] = sum L (s1, s2) dq'     (dmu = 2 ln 2 acc, see below)
 //   acc[2..4] = sum dq' (dx^2, dx dy, dy^2)  (da, db, dc = -1/2, -1, -1/2 x acc)
@@ -485,38 +501,49 @@ __device__ __forceinline__ float rcp_approx(float x) {
 //   dop       = sum dalpha G          (dsigma)
 //   dv       -= S alpha / (1 - v alpha)  (the pair's share of dL/dv, per cell)
 // with dq' = G dalpha sigma = -2 dL/dq.  cA = v T_n and vS = v S_n are the
-// pixel's per-cell factors.
-__device__ __forceinline__ void pair_grad(float acc[8], float &dop, float &dv, float Gv, float4 r0, float4 r1,
-                                          float4 r2, float px, float py, float cA, float Sn, float vS, float e0,
-                                          float e1, float e2, float eD, float alpha_max) {
+// pixels' per-cell factors; dx and pdx = L_00 dx the lane's column offsets
+// (shared by its rows).  A pixel with G' = 0 (not reached, or inactive) adds
+// exactly 0, and the opacity-clamped branch is a select, so no per-pixel
+// branch remains.
+__device__ __forceinline__ void pair_grad2(float2 acc[8], float2 &dop, float2 &dv, float2 Gv, float4 r0, float4 r1,
+                                           float4 r2, float2 dx, float2 pdx, float py, float2 cA, float2 Sn, float2 vS,
+                                           float2 e0, float2 e1, float2 e2, float2 eD, float alpha_max) {
     const float v = r2.w, op = r1.w;
-    const float raw = op * Gv;
-    const float al = fminf(raw, alpha_max);
-    const float rom = rcp_approx(1.0f - v * al);
-    const float dal = cA * (e0 * r2.x + e1 * r2.y + e2 * r2.z + eD) - vS * rom;
-    const float ca_al = cA * al;
-    acc[5] += ca_al * e0;
-    acc[6] += ca_al * e1;
-    acc[7] += ca_al * e2;
-    dv -= Sn * al * rom;
-    if (raw < alpha_max) {
-        const float dG = dal * Gv;
-        dop += dG;
-        const float dq = dG * op;
-        const float dx = px - r0.x, dy = py - r0.y;
-        // q = |L^T d|^2 with the record's L scaled by kappa (kappa^2 = log2(e)/2):
-        // dq/dmu = -2 Q d = -(2/kappa^2) L (s1, s2), 2/kappa^2 = 4 ln 2
-        const float s1 = fmaf(r1.y, dy, r1.x * dx), s2 = r1.z * dy;
-        acc[0] += dq * (r1.x * s1);
-        acc[1] += dq * fmaf(r1.y, s1, r1.z * s2);
-        const float dqx = dq * dx;
-        acc[2] += dqx * dx;
-        acc[3] += dqx * dy;
-        acc[4] += dq * dy * dy;
-    }
+    const float2 raw = __fmul2_rn(make_float2(op, op), Gv);
+    const float2 al = make_float2(fminf(raw.x, alpha_max), fminf(raw.y, alpha_max));
+    const float2 om = __ffma2_rn(make_float2(-v, -v), al, make_float2(1.0f, 1.0f));
+    const float2 rom = make_float2(rcp_approx(om.x), rcp_approx(om.y));
+    const float2 inner = __fadd2_rn(
+        __ffma2_rn(e2, make_float2(r2.z, r2.z),
+                   __ffma2_rn(e1, make_float2(r2.y, r2.y), __fmul2_rn(e0, make_float2(r2.x, r2.x)))),
+        eD);
+    const float2 dal = __ffma2_rn(make_float2(-vS.x, -vS.y), rom, __fmul2_rn(cA, inner));
+    const float2 ca_al = __fmul2_rn(cA, al);
+    acc[5] = __ffma2_rn(ca_al, e0, acc[5]);
+    acc[6] = __ffma2_rn(ca_al, e1, acc[6]);
+    acc[7] = __ffma2_rn(ca_al, e2, acc[7]);
+    const float2 sa = __fmul2_rn(Sn, al);
+    dv = __ffma2_rn(make_float2(-sa.x, -sa.y), rom, dv);
+    float2 dG = __fmul2_rn(dal, Gv);
+    dG.x = raw.x < alpha_max ? dG.x : 0.f;
+    dG.y = raw.y < alpha_max ? dG.y : 0.f;
+    dop = __fadd2_rn(dop, dG);
+    const float2 dq = __fmul2_rn(dG, make_float2(op, op));
+    const float dys = py - r0.y;
+    const float2 dy = make_float2(dys, dys);
+    // q = |L^T d|^2 with the record's L scaled by kappa (kappa^2 = log2(e)/2):
+    // dq/dmu = -2 Q d = -(2/kappa^2) L (s1, s2), 2/kappa^2 = 4 ln 2
+    const float2 s1 = __ffma2_rn(make_float2(r1.y, r1.y), dy, pdx);
+    const float s2 = r1.z * dys, zs2 = r1.z * s2;
+    acc[0] = __ffma2_rn(dq, __fmul2_rn(make_float2(r1.x, r1.x), s1), acc[0]);
+    acc[1] = __ffma2_rn(dq, __ffma2_rn(make_float2(r1.y, r1.y), s1, make_float2(zs2, zs2)), acc[1]);
+    const float2 dqx = __fmul2_rn(dq, dx);
+    acc[2] = __ffma2_rn(dqx, dx, acc[2]);
+    acc[3] = __ffma2_rn(dqx, dy, acc[3]);
+    acc[4] = __ffma2_rn(__fmul2_rn(dq, dy), dy, acc[4]);
 }
 
-// Constant factor of reduction slot j (see pair_grad): dL/dq = -dq'/2, so
+// Constant factor of reduction slot j (see pair_grad2): dL/dq = -dq'/2, so
 // dmu = -(4 ln 2)(-1/2) acc = 2 ln 2 acc, da = -acc/2, db = -acc (the 2 dx dy
 // term), dc = -acc/2; rgb unchanged.
 __device__ __forceinline__ float slot_scale(int j) {
@@ -571,12 +598,12 @@ __global__ void __launch_bounds__(WT, BWD_MINB) k_blend_bwd(const ViewDesc *__re
     const int per = kRecF4 * K;
 
     int nd[PPL];
-    float e0[PPL], e1[PPL], e2[PPL], eD[PPL];
+    float e0s[PPL], e1s[PPL], e2s[PPL], eDs[PPL];
     int ndm = 0;
 #pragma unroll
     for (int q = 0; q < PPL; ++q) {
         nd[q] = 0;
-        e0[q] = e1[q] = e2[q] = eD[q] = 0.f;
+        e0s[q] = e1s[q] = e2s[q] = eDs[q] = 0.f;
         if (xs[q & 1] < V.W && ys[q >> 1] < V.H) {
             const long long pin = (long long)ys[q >> 1] * V.W + xs[q & 1];
             const float Dv = Dpix[V.pix_base + pin];
@@ -587,11 +614,21 @@ __global__ void __launch_bounds__(WT, BWD_MINB) k_blend_bwd(const ViewDesc *__re
                 const float g0 = gi[pin], g1 = gi[HW + pin], g2 = gi[2 * HW + pin];
                 const float c0 = ci[pin], c1 = ci[HW + pin], c2 = ci[2 * HW + pin];
                 const float iD = 1.0f / Dv;
-                e0[q] = g0 * iD; e1[q] = g1 * iD; e2[q] = g2 * iD;
-                eD[q] = -(g0 * c0 + g1 * c1 + g2 * c2) * iD;
+                e0s[q] = g0 * iD; e1s[q] = g1 * iD; e2s[q] = g2 * iD;
+                eDs[q] = -(g0 * c0 + g1 * c1 + g2 * c2) * iD;
             }
         }
         ndm = max(ndm, nd[q]);
+    }
+    // the lane's pixels as row pairs (columns 0 and 1 of lane row rr)
+    float2 e0[NR], e1[NR], e2[NR], eD[NR];
+    const float2 px2 = make_float2(pxs[0], pxs[1]);
+#pragma unroll
+    for (int rr = 0; rr < NR; ++rr) {
+        e0[rr] = make_float2(e0s[2 * rr], e0s[2 * rr + 1]);
+        e1[rr] = make_float2(e1s[2 * rr], e1s[2 * rr + 1]);
+        e2[rr] = make_float2(e2s[2 * rr], e2s[2 * rr + 1]);
+        eD[rr] = make_float2(eDs[2 * rr], eDs[2 * rr + 1]);
     }
     const int ndmax = __reduce_max_sync(0xffffffffu, ndm);
     const uint2 rg = ranges[tile];
@@ -599,9 +636,9 @@ __global__ void __launch_bounds__(WT, BWD_MINB) k_blend_bwd(const ViewDesc *__re
     const float4 *vrec = rec + V.rec_base * kRecF4;
     const bool want_v = g_cell_v != nullptr;
 
-    float T[PPL], S[PPL];
+    float2 T[NR], S[NR];
 #pragma unroll
-    for (int q = 0; q < PPL; ++q) { T[q] = 1.0f; S[q] = 0.f; }
+    for (int rr = 0; rr < NR; ++rr) { T[rr] = make_float2(1.0f, 1.0f); S[rr] = make_float2(0.f, 0.f); }
     float4 pre[3];
     if (rg.x < end) {
         stage_cell(s_rec[0], vrec, cells, rg.x, per, lane, pre);
@@ -622,10 +659,11 @@ __global__ void __launch_bounds__(WT, BWD_MINB) k_blend_bwd(const ViewDesc *__re
         const int nhit = __popc(mask);
         // pass 1: replay the cell, keep G'; per pixel P_n and
         // X_n = dN.A_n + dD B_n = sum_k alpha_k (dN.c_k + dD)
-        float X[PPL], P[PPL];
+        float2 X[NR], P[NR];
+        const float2 v2 = make_float2(v, v);
         {
 #pragma unroll
-            for (int q = 0; q < PPL; ++q) { X[q] = 0.f; P[q] = 1.0f; }
+            for (int rr = 0; rr < NR; ++rr) { X[rr] = make_float2(0.f, 0.f); P[rr] = make_float2(1.0f, 1.0f); }
 #pragma unroll 1
             for (int i = 0; i < nhit; ++i) {
                 const int k = __ffs(mask) - 1;
@@ -654,35 +692,48 @@ __global__ void __launch_bounds__(WT, BWD_MINB) k_blend_bwd(const ViewDesc *__re
                 if (!any) continue;
                 const float4 r1 = r[3 * k + 1];
                 const float4 r2 = r[3 * k + 2];
-                const float pdx[2] = {r1.x * dx[0], r1.x * dx[1]};
+                const float2 pdx = __fmul2_rn(make_float2(r1.x, r1.x), make_float2(dx[0], dx[1]));
 #pragma unroll
-                for (int q = 0; q < PPL; ++q) {
-                    if (h[q]) {
-                        const float dyq = dy[q >> 1];
-                        const float s1 = fmaf(r1.y, dyq, pdx[q & 1]), s2 = r1.z * dyq;
-                        const float Gv = ex2_approx(-fmaf(s1, s1, s2 * s2));
-                        s_G[q][i][lane] = Gv;
-                        const float al = fminf(r1.w * Gv, bp.alpha_max);
-                        X[q] += al * fmaf(e0[q], r2.x, fmaf(e1[q], r2.y, fmaf(e2[q], r2.z, eD[q])));
-                        P[q] -= P[q] * (v * al);
-                    }
+                for (int rr = 0; rr < NR; ++rr) {
+                    const float dyq = dy[rr];
+                    const float s2 = r1.z * dyq, s22 = s2 * s2;
+                    const float2 s1 = __ffma2_rn(make_float2(r1.y, r1.y), make_float2(dyq, dyq), pdx);
+                    const float2 qd = __ffma2_rn(s1, s1, make_float2(s22, s22));
+                    float2 Gv = make_float2(ex2_approx(-qd.x), ex2_approx(-qd.y));
+                    Gv.x = h[2 * rr] ? Gv.x : 0.f;       // not reached: G' = 0 leaves X and P as they are
+                    Gv.y = h[2 * rr + 1] ? Gv.y : 0.f;
+                    s_G[2 * rr][i][lane] = Gv.x;
+                    s_G[2 * rr + 1][i][lane] = Gv.y;
+                    const float2 rw = __fmul2_rn(make_float2(r1.w, r1.w), Gv);
+                    const float2 al = make_float2(fminf(rw.x, bp.alpha_max), fminf(rw.y, bp.alpha_max));
+                    const float2 inner = __ffma2_rn(
+                        e0[rr], make_float2(r2.x, r2.x),
+                        __ffma2_rn(e1[rr], make_float2(r2.y, r2.y), __ffma2_rn(e2[rr], make_float2(r2.z, r2.z), eD[rr])));
+                    X[rr] = __ffma2_rn(al, inner, X[rr]);
+                    P[rr] = __ffma2_rn(make_float2(-P[rr].x, -P[rr].y), __fmul2_rn(v2, al), P[rr]);
                 }
             }
         }
         // per-pixel transmittance bookkeeping (S_n includes x_n); the cell
         // term of dL/dv, sum over pixels of T_n X_n, joins the Gaussians'
         // terms below so one reduction per cell carries dL/dv
-        float Tn[PPL];
+        float2 Tn[NR];
         float dv = 0.f;
 #pragma unroll
-        for (int q = 0; q < PPL; ++q) {
-            Tn[q] = T[q];
-            if (act[q]) {
-                S[q] -= v * Tn[q] * X[q];
-                T[q] *= P[q];
-                dv += Tn[q] * X[q];
+        for (int rr = 0; rr < NR; ++rr) {
+            Tn[rr] = T[rr];
+            if (act[2 * rr]) {
+                S[rr].x -= v * Tn[rr].x * X[rr].x;
+                T[rr].x *= P[rr].x;
+                dv += Tn[rr].x * X[rr].x;
+            }
+            if (act[2 * rr + 1]) {
+                S[rr].y -= v * Tn[rr].y * X[rr].y;
+                T[rr].y *= P[rr].y;
+                dv += Tn[rr].y * X[rr].y;
             }
         }
+        float2 dv2 = make_float2(0.f, 0.f);
         const uint32_t cellid = __ldg(cells + e);
         float *gbase = g2d + (V.rec_base + (long long)cellid * K) * kGradF;
         // pass 2: gradient terms per Gaussian reaching the sub-tile (not
@@ -690,35 +741,38 @@ __global__ void __launch_bounds__(WT, BWD_MINB) k_blend_bwd(const ViewDesc *__re
         unsigned m2 = mask0;
 #pragma unroll 1
         for (int i = 0; m2; ++i, m2 &= m2 - 1) {
-            float gv[PPL];
+            float2 gv[NR];
             bool any = false;
 #pragma unroll
-            for (int q = 0; q < PPL; ++q) {
-                gv[q] = s_G[q][i][lane];
-                any = any || gv[q] > 0.f;
+            for (int rr = 0; rr < NR; ++rr) {
+                gv[rr] = make_float2(s_G[2 * rr][i][lane], s_G[2 * rr + 1][i][lane]);
+                any = any || gv[rr].x > 0.f || gv[rr].y > 0.f;
             }
             if (!__any_sync(0xffffffffu, any)) continue;
             const int k = __ffs(m2) - 1;
             const float4 r0 = r[3 * k], r1 = r[3 * k + 1], r2 = r[3 * k + 2];
+            float2 acc2[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc2[j] = make_float2(0.f, 0.f);
+            float2 dop2 = make_float2(0.f, 0.f);
+            const float2 gdx = __fadd2_rn(px2, make_float2(-r0.x, -r0.x));
+            const float2 gpdx = __fmul2_rn(make_float2(r1.x, r1.x), gdx);
+#pragma unroll
+            for (int rr = 0; rr < NR; ++rr)
+                pair_grad2(acc2, dop2, dv2, gv[rr], r0, r1, r2, gdx, gpdx, pys[rr], __fmul2_rn(v2, Tn[rr]), S[rr],
+                           __fmul2_rn(v2, S[rr]), e0[rr], e1[rr], e2[rr], eD[rr], bp.alpha_max);
             float acc[8];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) acc[j] = 0.f;
-            float dop = 0.f;
-#pragma unroll
-            for (int q = 0; q < PPL; ++q)
-                if (gv[q] > 0.f)
-                    pair_grad(acc, dop, dv, gv[q], r0, r1, r2, pxs[q & 1], pys[q >> 1], v * Tn[q], S[q], v * S[q],
-                              e0[q], e1[q],
-                              e2[q], eD[q], bp.alpha_max);
+            for (int j = 0; j < 8; ++j) acc[j] = acc2[j].x + acc2[j].y;
             const float tot = transposed_warp_sum8(acc, lane);
-            const float dop_tot = warp_sum(dop);
+            const float dop_tot = warp_sum(dop2.x + dop2.y);
             float *gk = gbase + k * kGradF;
             const int slot = transposed_owner8(lane);
             if ((lane & 3) == 0 && tot != 0.f) atomicAdd(gk + grad_slot(slot), tot * slot_scale(slot));
             if (lane == 1 && dop_tot != 0.f) atomicAdd(gk + 5, dop_tot);
         }
         if (want_v) {  // per (view, cell) entry: v_n may differ between views
-            dv = warp_sum(dv);
+            dv = warp_sum(dv + (dv2.x + dv2.y));
             if (lane == 0 && dv != 0.f) atomicAdd(g_cell_v + V.cell_base + cellid, dv);
         }
         __syncwarp();
