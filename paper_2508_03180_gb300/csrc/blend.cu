@@ -620,16 +620,23 @@ __global__ void __launch_bounds__(WT, BWD_MINB) k_blend_bwd(const ViewDesc *__re
         }
         ndm = max(ndm, nd[q]);
     }
-    // the lane's pixels as row pairs (columns 0 and 1 of lane row rr)
-    float2 e0[NR], e1[NR], e2[NR], eD[NR];
+    // the lane's pixels as row pairs (columns 0 and 1 of lane row rr); half of
+    // the per-pixel factors, (e2, eD), wait in warp-private shared memory
+    // (registers are the adjoint's limit: this keeps it from spilling)
+    __shared__ float4 s_E[NR][WT];
+    float2 e0r[NR], e1r[NR];
     const float2 px2 = make_float2(pxs[0], pxs[1]);
 #pragma unroll
     for (int rr = 0; rr < NR; ++rr) {
-        e0[rr] = make_float2(e0s[2 * rr], e0s[2 * rr + 1]);
-        e1[rr] = make_float2(e1s[2 * rr], e1s[2 * rr + 1]);
-        e2[rr] = make_float2(e2s[2 * rr], e2s[2 * rr + 1]);
-        eD[rr] = make_float2(eDs[2 * rr], eDs[2 * rr + 1]);
+        e0r[rr] = make_float2(e0s[2 * rr], e0s[2 * rr + 1]);
+        e1r[rr] = make_float2(e1s[2 * rr], e1s[2 * rr + 1]);
+        s_E[rr][lane] = make_float4(e2s[2 * rr], e2s[2 * rr + 1], eDs[2 * rr], eDs[2 * rr + 1]);
     }
+    auto efac = [&](int rr, float2 &e0, float2 &e1, float2 &e2, float2 &eD) {
+        const float4 b = s_E[rr][lane];
+        e0 = e0r[rr]; e1 = e1r[rr];
+        e2 = make_float2(b.x, b.y); eD = make_float2(b.z, b.w);
+    };
     const int ndmax = __reduce_max_sync(0xffffffffu, ndm);
     const uint2 rg = ranges[tile];
     const uint32_t end = rg.x + min((uint32_t)ndmax, rg.y - rg.x);
@@ -706,9 +713,11 @@ __global__ void __launch_bounds__(WT, BWD_MINB) k_blend_bwd(const ViewDesc *__re
                     s_G[2 * rr + 1][i][lane] = Gv.y;
                     const float2 rw = __fmul2_rn(make_float2(r1.w, r1.w), Gv);
                     const float2 al = make_float2(fminf(rw.x, bp.alpha_max), fminf(rw.y, bp.alpha_max));
+                    float2 e0, e1, e2, eD;
+                    efac(rr, e0, e1, e2, eD);
                     const float2 inner = __ffma2_rn(
-                        e0[rr], make_float2(r2.x, r2.x),
-                        __ffma2_rn(e1[rr], make_float2(r2.y, r2.y), __ffma2_rn(e2[rr], make_float2(r2.z, r2.z), eD[rr])));
+                        e0, make_float2(r2.x, r2.x),
+                        __ffma2_rn(e1, make_float2(r2.y, r2.y), __ffma2_rn(e2, make_float2(r2.z, r2.z), eD)));
                     X[rr] = __ffma2_rn(al, inner, X[rr]);
                     P[rr] = __ffma2_rn(make_float2(-P[rr].x, -P[rr].y), __fmul2_rn(v2, al), P[rr]);
                 }
@@ -758,9 +767,12 @@ __global__ void __launch_bounds__(WT, BWD_MINB) k_blend_bwd(const ViewDesc *__re
             const float2 gdx = __fadd2_rn(px2, make_float2(-r0.x, -r0.x));
             const float2 gpdx = __fmul2_rn(make_float2(r1.x, r1.x), gdx);
 #pragma unroll
-            for (int rr = 0; rr < NR; ++rr)
+            for (int rr = 0; rr < NR; ++rr) {
+                float2 e0, e1, e2, eD;
+                efac(rr, e0, e1, e2, eD);
                 pair_grad2(acc2, dop2, dv2, gv[rr], r0, r1, r2, gdx, gpdx, pys[rr], __fmul2_rn(v2, Tn[rr]), S[rr],
-                           __fmul2_rn(v2, S[rr]), e0[rr], e1[rr], e2[rr], eD[rr], bp.alpha_max);
+                           __fmul2_rn(v2, S[rr]), e0, e1, e2, eD, bp.alpha_max);
+            }
             float acc[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) acc[j] = acc2[j].x + acc2[j].y;
