@@ -137,11 +137,14 @@ __device__ __forceinline__ bool touches_rows(float4 r0, float x0, float y0, floa
 __device__ __forceinline__ int lane_col(int lane, int c) { return (lane & 7) + 8 * c; }
 __device__ __forceinline__ int lane_row(int lane, int r) { return (lane >> 3) + 4 * r; }
 
-// The forward's work unit: one warp per 16 x (2 PPL) sub-tile.  FWD_PPL = 2 (16x4 sub-tiles, 68 registers):
-// 16x8 sub-tiles halve the (sub-tile, Gaussian) pairs on the benchmark scene
-// but need ~95 registers (21 warps/SM) and measured no faster.
-constexpr int FWD_PPL = 2;
+// The forward's work unit: one warp per 16 x (2 PPL) sub-tile.  FWD_PPL = 4
+// (16x8 sub-tiles, the adjoint's): with the pixel math in packed pairs, the
+// per-Gaussian work of a lane (ballot, record loads, AABB tests) spread over
+// four pixels outweighs the register cost; the kernels are held to 72
+// registers (28 one-warp CTAs per SM), which measured as fast as 64-80.
+constexpr int FWD_PPL = 4;
 constexpr int FWD_SUB = kTile / (2 * FWD_PPL);  // sub-tiles per tile
+constexpr int FWD_MINB = 28;
 
 template <int KT, int PPL>
 __device__ __forceinline__ void blend_fwd_unit(int unit, const ViewDesc *__restrict__ views, int n_views,
@@ -299,7 +302,7 @@ __device__ __forceinline__ void blend_fwd_unit(int unit, const ViewDesc *__restr
 }
 
 template <int KT>
-__global__ void __launch_bounds__(WT) k_blend_fwd(const ViewDesc *__restrict__ views, int n_views,
+__global__ void __launch_bounds__(WT, FWD_MINB) k_blend_fwd(const ViewDesc *__restrict__ views, int n_views,
                                                   const uint2 *__restrict__ ranges, const uint32_t *__restrict__ cells,
                                                   const float4 *__restrict__ rec, BlendParams bp,
                                                   float *__restrict__ out_rgb, float *__restrict__ out_rgb2,
@@ -315,7 +318,7 @@ __global__ void __launch_bounds__(WT) k_blend_fwd(const ViewDesc *__restrict__ v
 // dense and the empty regions of the images balance dynamically.  One
 // atomic per sub-tile: their rate is bounded by the blend work between them.
 template <int KT>
-__global__ void __launch_bounds__(WT) k_blend_fwd_pull(const ViewDesc *__restrict__ views,
+__global__ void __launch_bounds__(WT, FWD_MINB) k_blend_fwd_pull(const ViewDesc *__restrict__ views,
                                                        const uint2 *__restrict__ ranges,
                                                        const uint32_t *__restrict__ cells,
                                                        const float4 *__restrict__ rec, BlendParams bp,
