@@ -103,7 +103,11 @@ static MlpShape mlp_shape(int F, int H, int K, bool bwd) {
     return mlp_shape_w(F, H, K, bwd, 2);
 }
 
-__device__ __forceinline__ float sigmoidf_(float x) { return 1.0f / (1.0f + expf(-x)); }
+// Logistic and tanh from the fast exponential and a fast divide (about 1e-6
+// relative error; the decode and its adjoint use the same functions, so the
+// adjoint sees the forward's values and decisions).
+__device__ __forceinline__ float sigmoid_fast(float x) { return __fdividef(1.0f, 1.0f + __expf(-x)); }
+__device__ __forceinline__ float tanh_fast(float x) { return 1.0f - __fdividef(2.0f, 1.0f + __expf(2.0f * x)); }
 __device__ __forceinline__ int hrow(const MlpShape &S, int D, int j) { return D * (S.Hp * S.LD + 8) + j * S.LD; }
 __device__ __forceinline__ int orow(const MlpShape &S, int D, int r) { return (S.rb[D] + r) * S.LD + 8 * D; }
 __device__ __forceinline__ int out_block(const MlpShape &S, int rr) {
@@ -222,6 +226,7 @@ __device__ void stage_samples(const MlpShape &S, float *sm, const SceneDev &sc, 
     {
         const float4 *s4 = reinterpret_cast<const float4 *>(srec + q0 * DINFO);
         float4 *d4 = reinterpret_cast<float4 *>(info);
+#pragma unroll 2
         for (int i = t; i < S.M * (DINFO / 4); i += blockDim.x)
             d4[i] = i < nv * (DINFO / 4) ? __ldg(s4 + i) : make_float4(0.f, 0.f, 0.f, 0.f);  // valid = 0 past the end
     }
@@ -232,14 +237,25 @@ __device__ void stage_samples(const MlpShape &S, float *sm, const SceneDev &sc, 
 #pragma unroll
         for (int i = 0; i < 4; ++i) Zt[(S.F + i) * S.LD + t] = v ? p[19 + i] : 0.f;
     }
-    // latent features: row n of the [N][F] feature matrix into column s
-    // (a warp per sample, lanes along the row)
-    const int nw = blockDim.x >> 5;
-    for (int s = t >> 5; s < S.M; s += nw) {
-        const float *p = info + s * DINFO;
-        const bool v = __float_as_int(p[1]) != 0;
-        const float *row = sc.feat + (long long)__float_as_int(p[0]) * S.F;
-        for (int i = t & 31; i < S.F; i += 32) Zt[i * S.LD + s] = v ? row[i] : 0.f;
+    // latent features: row n of the [N][F] feature matrix into column s; each
+    // warp fetches the rows of its own 8 samples, all loads in flight at once
+    // (lanes along the row, features lane and lane + 32)
+    {
+        const int w = t >> 5, l = t & 31;
+        float fv[8][2];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const float *p = info + (8 * w + u) * DINFO;
+            const bool v = __float_as_int(p[1]) != 0;
+            const float *row = sc.feat + (long long)__float_as_int(p[0]) * S.F;
+            fv[u][0] = v && l < S.F ? __ldg(row + l) : 0.f;
+            fv[u][1] = v && l + 32 < S.F ? __ldg(row + l + 32) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            if (l < S.F) Zt[l * S.LD + 8 * w + u] = fv[u][0];
+            if (l + 32 < S.F) Zt[(l + 32) * S.LD + 8 * w + u] = fv[u][1];
+        }
     }
 }
 
@@ -276,6 +292,7 @@ __global__ void k_mlp_pack(const float *__restrict__ w, MlpShape S, float *__res
 __device__ __forceinline__ void copy_f4(float *dst, const float *__restrict__ src, int n) {
     const float4 *s4 = reinterpret_cast<const float4 *>(src);
     float4 *d4 = reinterpret_cast<float4 *>(dst);
+#pragma unroll 4
     for (int i = threadIdx.x; i < (n >> 2); i += blockDim.x) d4[i] = __ldg(s4 + i);
 }
 
@@ -397,7 +414,7 @@ __global__ void __launch_bounds__(256) k_decode(SceneDev sc, MlpShape S, const f
             float o[kDecF];
             o[0] = c4.x; o[1] = c4.y; o[2] = c4.z;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) o[3 + c] = fminf(sigmoidf_(Ot[orow(S, 2, 3 * k + c) + s]), c4.w) * p[7 + c];
+            for (int c = 0; c < 3; ++c) o[3 + c] = fminf(sigmoid_fast(Ot[orow(S, 2, 3 * k + c) + s]), c4.w) * p[7 + c];
             float qv[4];
 #pragma unroll
             for (int c = 0; c < 4; ++c) qv[c] = Ot[orow(S, 3, 4 * k + c) + s];
@@ -409,9 +426,9 @@ __global__ void __launch_bounds__(256) k_decode(SceneDev sc, MlpShape S, const f
             } else {  // no direction to normalise: the identity rotation
                 o[6] = 1.f; o[7] = 0.f; o[8] = 0.f; o[9] = 0.f;
             }
-            o[10] = tanhf(Ot[orow(S, 0, k) + s]);
+            o[10] = tanh_fast(Ot[orow(S, 0, k) + s]);
 #pragma unroll
-            for (int c = 0; c < 3; ++c) o[11 + c] = sigmoidf_(Ot[orow(S, 1, 3 * k + c) + s]);
+            for (int c = 0; c < 3; ++c) o[11 + c] = sigmoid_fast(Ot[orow(S, 1, 3 * k + c) + s]);
             float2 *dst = reinterpret_cast<float2 *>(dec + (rec + k) * kDecF);
 #pragma unroll
             for (int i = 0; i < kDecF / 2; ++i) dst[i] = make_float2(o[2 * i], o[2 * i + 1]);
@@ -428,7 +445,8 @@ __global__ void __launch_bounds__(256) k_decode(SceneDev sc, MlpShape S, const f
 //   dL/dh = relu'(h) (dL/do_D W2_D) per decoder;
 //   dL/df = sum over decoders of dL/dh_D W1_D[:, :F]  (atomic adds to g_feat);
 // and the rows Z, H, dL/dh, dL/do of every sample to `rows` for the weight
-// gradients (k_mlp_wgrad).  Decisions held fixed: the ReLU masks, the side of
+// gradients (k_mlp_wgrad), stored per tile of M samples as unit rows of M
+// values (the tile's shared-memory layout, so they leave as float4 copies).  Decisions held fixed: the ReLU masks, the side of
 // the Eq. 11 minimum, sigma <= 0 (gdec is zero there).
 template <int HW>
 __global__ void __launch_bounds__(256) k_decode_bwd(SceneDev sc, MlpShape S, const float *__restrict__ pk,
@@ -481,13 +499,13 @@ __global__ void __launch_bounds__(256) k_decode_bwd(SceneDev sc, MlpShape S, con
             }
             // opacity
             {
-                const float sg = tanhf(*po);
+                const float sg = tanh_fast(*po);
                 *po = gk[10] * (1.0f - sg * sg);
             }
             // colour
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                const float cc = sigmoidf_(*pc[c]);
+                const float cc = sigmoid_fast(*pc[c]);
                 *pc[c] = gk[11 + c] * cc * (1.0f - cc);
             }
             // scale and the Eq. 11 bound; then the offset
@@ -497,7 +515,7 @@ __global__ void __launch_bounds__(256) k_decode_bwd(SceneDev sc, MlpShape S, con
             float dlim = 0.f;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                const float sg = sigmoidf_(*ps[c]);
+                const float sg = sigmoid_fast(*ps[c]);
                 if (sg < lim) {
                     *ps[c] = gk[3 + c] * a.S[c] * sg * (1.0f - sg);
                 } else {
@@ -599,16 +617,28 @@ __global__ void __launch_bounds__(256) k_decode_bwd(SceneDev sc, MlpShape S, con
                 for (int D = 0; D < 4; ++D) {
                     const float *dh = DHt + hrow(S, D, 0) + 8 * warp;
                     const float *wd = W + D * Hp * S.I;
+                    if (F > 32) {  // (uniform) two features per lane
 #pragma unroll 2
-                    for (int j = 0; j < Hp; ++j) {
-                        const float4 da = *reinterpret_cast<const float4 *>(dh + j * S.LD);
-                        const float4 dc = *reinterpret_cast<const float4 *>(dh + j * S.LD + 4);
-                        const float d[8] = {da.x, da.y, da.z, da.w, dc.x, dc.y, dc.z, dc.w};
-                        const float w0 = wd[j * S.I + i0], w1 = u1 ? wd[j * S.I + i1] : 0.f;
+                        for (int j = 0; j < Hp; ++j) {
+                            const float4 da = *reinterpret_cast<const float4 *>(dh + j * S.LD);
+                            const float4 dc = *reinterpret_cast<const float4 *>(dh + j * S.LD + 4);
+                            const float d[8] = {da.x, da.y, da.z, da.w, dc.x, dc.y, dc.z, dc.w};
+                            const float w0 = wd[j * S.I + i0], w1 = u1 ? wd[j * S.I + i1] : 0.f;
 #pragma unroll
-                        for (int s = 0; s < 8; ++s) {
-                            acc[s][0] = fmaf(d[s], w0, acc[s][0]);
-                            acc[s][1] = fmaf(d[s], w1, acc[s][1]);
+                            for (int s = 0; s < 8; ++s) {
+                                acc[s][0] = fmaf(d[s], w0, acc[s][0]);
+                                acc[s][1] = fmaf(d[s], w1, acc[s][1]);
+                            }
+                        }
+                    } else {
+#pragma unroll 4
+                        for (int j = 0; j < Hp; ++j) {
+                            const float4 da = *reinterpret_cast<const float4 *>(dh + j * S.LD);
+                            const float4 dc = *reinterpret_cast<const float4 *>(dh + j * S.LD + 4);
+                            const float d[8] = {da.x, da.y, da.z, da.w, dc.x, dc.y, dc.z, dc.w};
+                            const float w0 = wd[j * S.I + i0];
+#pragma unroll
+                            for (int s = 0; s < 8; ++s) acc[s][0] = fmaf(d[s], w0, acc[s][0]);
                         }
                     }
                 }
@@ -622,21 +652,24 @@ __global__ void __launch_bounds__(256) k_decode_bwd(SceneDev sc, MlpShape S, con
                 }
             }
         }
-        // the rows of this tile's samples for the weight gradients: Z, H, dL/dh, dL/do
+        // this tile's rows for the weight gradients, in the tile's own layout
+        // (unit rows of M samples: Z, H, dL/dh, dL/do), as float4 copies
         {
-            const int nv = (int)min((long long)S.M, nsamp - q0);
+            float *blk = rows + (q0 / S.M) * (long long)S.row_all * S.M;
+            const int M4 = S.M >> 2;
             const float *Zt = sm + S.s_z;
-            for (int s = warp; s < nv; s += S.W) {
-                float *row = rows + (q0 + s) * S.row_all;
-                for (int c = lane; c < S.I; c += 32) row[S.row_z + c] = Zt[c * S.LD + s];
-                for (int D = 0; D < 4; ++D)
-                    for (int j = lane; j < Hp; j += 32) {
-                        row[S.row_h + D * Hp + j] = Ht[hrow(S, D, j) + s];
-                        row[S.row_dh + D * Hp + j] = DHt[hrow(S, D, j) + s];
-                    }
-                for (int D = 0; D < 4; ++D)
-                    for (int r = lane; r < S.rb[D + 1] - S.rb[D]; r += 32)
-                        row[S.row_do + S.rb[D] + r] = Ot[orow(S, D, r) + s];
+            auto put = [&](int unit, const float *src, int n_rows, int src_stride) {
+                for (int idx = threadIdx.x; idx < n_rows * M4; idx += blockDim.x) {
+                    const int u = idx / M4, c = idx - u * M4;
+                    reinterpret_cast<float4 *>(blk + (long long)(unit + u) * S.M)[c] =
+                        reinterpret_cast<const float4 *>(src + u * src_stride)[c];
+                }
+            };
+            put(S.row_z, Zt, S.I, S.LD);
+            for (int D = 0; D < 4; ++D) {
+                put(S.row_h + D * Hp, Ht + hrow(S, D, 0), Hp, S.LD);
+                put(S.row_dh + D * Hp, DHt + hrow(S, D, 0), Hp, S.LD);
+                put(S.row_do + S.rb[D], Ot + orow(S, D, 0), S.rb[D + 1] - S.rb[D], S.LD);
             }
         }
         __syncthreads();
@@ -670,30 +703,36 @@ __global__ void __launch_bounds__(WT_T) k_mlp_wgrad(const float *__restrict__ ro
     if (s0 >= s1) return;
     const int t = threadIdx.x, ga = t / 12, gb = t - 12 * ga;
     float ra[WT_LA], rb[WT_LB];
+    // element (sample s, column col) of the rows, stored per tile of S.M samples as unit rows
+    const int lgM = __ffs(S.M) - 1;
+    auto at = [&](long long s, int col) -> float {
+        return rows[((s >> lgM) * S.row_all + col) * S.M + (s & (S.M - 1))];
+    };
     auto load = [&](long long sb) {
+    // consecutive threads take consecutive samples of one column (contiguous in the rows' layout)
 #pragma unroll
         for (int u = 0; u < WT_LA; ++u) {
-            const int idx = t + WT_T * u, r = idx >> 5, c = idx & 31;
+            const int idx = t + WT_T * u, r = idx & 31, c = idx >> 5;
             const long long s = sb + r;
-            ra[u] = (idx < WT_S * WT_A && s < s1 && a0 + c < P.na) ? rows[s * S.row_all + P.a_col + a0 + c] : 0.f;
+            ra[u] = (idx < WT_S * WT_A && s < s1 && a0 + c < P.na) ? at(s, P.a_col + a0 + c) : 0.f;
         }
 #pragma unroll
         for (int u = 0; u < WT_LB; ++u) {
-            const int idx = t + WT_T * u, r = idx / WT_B, c = idx - r * WT_B, b = b0 + c;
+            const int idx = t + WT_T * u, r = idx & 31, c = idx >> 5, b = b0 + c;
             const long long s = sb + r;
-            rb[u] = s < s1 ? (b < P.nb ? rows[s * S.row_all + P.b_col + b] : (b == P.nb ? 1.0f : 0.f)) : 0.f;
+            rb[u] = s < s1 ? (b < P.nb ? at(s, P.b_col + b) : (b == P.nb ? 1.0f : 0.f)) : 0.f;
         }
     };
     auto store = [&](int buf) {
 #pragma unroll
         for (int u = 0; u < WT_LA; ++u) {
             const int idx = t + WT_T * u;
-            if (idx < WT_S * WT_A) sA[buf][idx >> 5][idx & 31] = ra[u];
+            if (idx < WT_S * WT_A) sA[buf][idx & 31][idx >> 5] = ra[u];
         }
 #pragma unroll
         for (int u = 0; u < WT_LB; ++u) {
-            const int idx = t + WT_T * u, r = idx / WT_B;
-            sB[buf][r][idx - r * WT_B] = rb[u];
+            const int idx = t + WT_T * u;
+            sB[buf][idx & 31][idx >> 5] = rb[u];
         }
     };
     float acc[4][4];
@@ -762,7 +801,8 @@ static int persistent_grid(Kern k, int threads, size_t smem, long long tiles) {
 long long decode_scratch_floats(int F, int H, int K, long long nsamp, long long G, bool bwd) {
     const MlpShape S = mlp_shape(F, H, K, bwd);
     const long long n = std::max(1LL, nsamp);
-    return up_to(S.g_total, 4) + n * DINFO + (bwd ? (long long)S.row_all * n : 4 * std::max(1LL, G));
+    const long long tiles = (n + S.M - 1) / S.M;
+    return up_to(S.g_total, 4) + n * DINFO + (bwd ? (long long)S.row_all * S.M * tiles : 4 * std::max(1LL, G));
 }
 
 static void decode_prep(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const MlpShape &S,
