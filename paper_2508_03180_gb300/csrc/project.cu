@@ -641,71 +641,79 @@ __global__ void __launch_bounds__(128) k_project_bwd_neural(const ViewDesc *__re
 
 // Colour adjoint: colour_ch = max(0, 0.5 + sum_c k_c,ch Y_c(d)),
 // d = (mu - eye)/|mu - eye|: dL/dk and the view direction's share of
-// dL/dmu (added to g_mean, which the geometry kernel wrote).  One channel at
-// a time keeps 16 coefficients and 16 accumulators live.  Gaussians that no
-// view rendered (and invalid ones) have zero screen-space gradients.
-__global__ void __launch_bounds__(128) k_project_bwd_colour(const ViewDesc *__restrict__ views, int n_views, int slot,
-                                                            SceneDev sc, const uint32_t *__restrict__ count,
-                                                            const float *__restrict__ g2d, float *__restrict__ g_mean,
-                                                            float *__restrict__ g_sh) {
-    __shared__ float s_out[128 * 48];  // the block's g_sh rows, written back coalesced
+// dL/dmu (added to g_mean, which the geometry kernel wrote).  Views outer:
+// per view one SH basis Y(d) and, the direction gradient being linear in the
+// weights, one sh_grad_dot with w_c = sum over unclamped channels of
+// dL/dcolour_ch k_c,ch.  The 48 coefficients stay in registers; dL/dk
+// accumulates in shared memory, transposed (column t of the block's thread t,
+// stride 129: conflict-free both when accumulating and when the rows leave
+// coalesced).  Gaussians that no view rendered (and invalid ones) have zero
+// screen-space gradients.
+constexpr int COL_T = 128, COL_LD = COL_T + 1;
+__global__ void __launch_bounds__(COL_T) k_project_bwd_colour(const ViewDesc *__restrict__ views, int n_views, int slot,
+                                                              SceneDev sc, const uint32_t *__restrict__ count,
+                                                              const float *__restrict__ g2d, float *__restrict__ g_mean,
+                                                              float *__restrict__ g_sh) {
+    __shared__ float s_acc[48 * COL_LD];  // dL/dk[c * 3 + ch] of thread t at [c * 3 + ch][t]
     const long long G = sc.G;
     const int K = sc.K, C = (sc.sh_degree + 1) * (sc.sh_degree + 1), row = 3 * C;
-    for (long long g0 = (long long)blockIdx.x * blockDim.x; g0 < G; g0 += (long long)gridDim.x * blockDim.x) {
-        const long long g = g0 + threadIdx.x;
+    const int t = threadIdx.x;
+    for (long long g0 = (long long)blockIdx.x * COL_T; g0 < G; g0 += (long long)gridDim.x * COL_T) {
+        const long long g = g0 + t;
         const bool live = g < G;
         const long long cell = live ? g / K : 0;
-        bool any = false;
-        for (int v = 0; live && v < n_views; ++v)
-            any |= views[v].scene_slot == slot && count[views[v].cell_base + cell] != 0u;
-        float gdm[3] = {0.f, 0.f, 0.f};
-        const float m0 = any ? sc.gauss[g] : 0.f, m1 = any ? sc.gauss[G + g] : 0.f, m2 = any ? sc.gauss[2 * G + g] : 0.f;
-#pragma unroll 1
-        for (int ch = 0; ch < 3; ++ch) {
-            float k[16], gk[16];
+        for (int j = 0; j < row; ++j) s_acc[j * COL_LD + t] = 0.f;
+        float k[16][3];
 #pragma unroll
-            for (int c = 0; c < 16; ++c) {
-                k[c] = any && c < C ? sc.sh[(c * 3 + ch) * G + g] : 0.f;
-                gk[c] = 0.f;
-            }
-            for (int v = 0; any && v < n_views; ++v) {
-                const ViewDesc &Vw = views[v];
-                if (Vw.scene_slot != slot || count[Vw.cell_base + cell] == 0u) continue;
-                const float gc = g2d[(Vw.rec_base + g) * kGradF + 6 + ch];
-                if (gc == 0.f) continue;
-                float u0 = m0 - Vw.eye[0], u1 = m1 - Vw.eye[1], u2 = m2 - Vw.eye[2];
-                const float il = rsqrtf(u0 * u0 + u1 * u1 + u2 * u2);
-                const float d0 = u0 * il, d1 = u1 * il, d2 = u2 * il;
-                float Y[16];
-                sh_eval(d0, d1, d2, sc.sh_degree, Y);
+        for (int c = 0; c < 16; ++c)
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) k[c][ch] = live && c < C ? sc.sh[(c * 3 + ch) * G + g] : 0.f;
+        const float m0 = live ? sc.gauss[g] : 0.f, m1 = live ? sc.gauss[G + g] : 0.f,
+                    m2 = live ? sc.gauss[2 * G + g] : 0.f;
+        float gdm[3] = {0.f, 0.f, 0.f};
+        for (int v = 0; live && v < n_views; ++v) {
+            const ViewDesc &Vw = views[v];
+            if (Vw.scene_slot != slot || count[Vw.cell_base + cell] == 0u) continue;
+            const float *gr = g2d + (Vw.rec_base + g) * kGradF + 6;
+            const float gc[3] = {gr[0], gr[1], gr[2]};
+            if (gc[0] == 0.f && gc[1] == 0.f && gc[2] == 0.f) continue;
+            const float u0 = m0 - Vw.eye[0], u1 = m1 - Vw.eye[1], u2 = m2 - Vw.eye[2];
+            const float il = rsqrtf(u0 * u0 + u1 * u1 + u2 * u2);
+            const float d0 = u0 * il, d1 = u1 * il, d2 = u2 * il;
+            float Y[16];
+            sh_eval(d0, d1, d2, sc.sh_degree, Y);
+            float w[16];
+#pragma unroll
+            for (int c = 0; c < 16; ++c) w[c] = 0.f;
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
                 float sv = 0.5f;
 #pragma unroll
-                for (int c = 0; c < 16; ++c) sv += k[c] * Y[c];
-                if (sv <= 0.0f) continue;  // clamped at 0
-                float w[16];
+                for (int c = 0; c < 16; ++c) sv += k[c][ch] * Y[c];
+                if (sv <= 0.0f || gc[ch] == 0.f) continue;  // clamped at 0, or no gradient
 #pragma unroll
                 for (int c = 0; c < 16; ++c) {
-                    gk[c] += gc * Y[c];
-                    w[c] = gc * k[c];
-                }
-                if (g_mean) {
-                    float gd[3] = {0.f, 0.f, 0.f};
-                    sh_grad_dot(d0, d1, d2, sc.sh_degree, w, gd);
-                    const float dd = gd[0] * d0 + gd[1] * d1 + gd[2] * d2;
-                    gdm[0] += (gd[0] - dd * d0) * il;
-                    gdm[1] += (gd[1] - dd * d1) * il;
-                    gdm[2] += (gd[2] - dd * d2) * il;
+                    if (c < C) s_acc[(c * 3 + ch) * COL_LD + t] += gc[ch] * Y[c];
+                    w[c] += gc[ch] * k[c][ch];
                 }
             }
-#pragma unroll
-            for (int c = 0; c < 16; ++c)
-                if (c < C) s_out[threadIdx.x * row + c * 3 + ch] = gk[c];
+            if (g_mean) {
+                float gd[3] = {0.f, 0.f, 0.f};
+                sh_grad_dot(d0, d1, d2, sc.sh_degree, w, gd);
+                const float dd = gd[0] * d0 + gd[1] * d1 + gd[2] * d2;
+                gdm[0] += (gd[0] - dd * d0) * il;
+                gdm[1] += (gd[1] - dd * d1) * il;
+                gdm[2] += (gd[2] - dd * d2) * il;
+            }
         }
         __syncthreads();
         if (g_sh) {
-            const long long nb = min((long long)blockDim.x, G - g0) * row;
+            const long long nb = min((long long)COL_T, G - g0) * row;
             float *dst = g_sh + g0 * row;
-            for (int i = threadIdx.x; i < nb; i += blockDim.x) dst[i] = s_out[i];
+            for (int i = t; i < nb; i += COL_T) {
+                const int gl = i / row, j = i - gl * row;
+                dst[i] = s_acc[j * COL_LD + gl];
+            }
         }
         __syncthreads();
         if (live && g_mean) {
