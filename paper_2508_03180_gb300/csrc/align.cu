@@ -145,7 +145,8 @@ extern "C" dgs_status dgs_cell_align(dgs_ctx *ctx, uint32_t scene_id, int32_t wh
         const ViewDesc v = make_view(ctx->cams[cam_slot], 0, 0, 0, sc, 0, 0);
         CK(cudaMemcpyAsync(base, &v, sizeof(v), cudaMemcpyHostToDevice, st));  // pageable: staged before return
         dec = (float *)(base + o_dec);
-        launch_decode((const ViewDesc *)base, 1, 0, sd, nullptr, N, dec, (float *)(base + o_pk), st);  // every cell
+        launch_decode((const ViewDesc *)base, 1, 0, sd, nullptr, N, dec, (float *)(base + o_pk), nullptr,
+                      BlendParams{}, nullptr, nullptr, st);  // every cell of the one view; no records
     }
     float *oc = out_center, *oq = out_quat;
     if (out_location == DGS_HOST) {

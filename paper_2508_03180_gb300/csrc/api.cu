@@ -600,15 +600,11 @@ dgs_status chain_forward(dgs_ctx *ctx, Workspace &ws, const std::vector<ChainVie
     for (int k = 0; k < S; ++k) {
         const SceneDev sd = slots[k]->dev();
         if (slots[k]->F > 0) {  // neural cells: decode the visible cells' Gaussians for every view first
-            {
-                StageTimer t(ctx->prof, DGS_STAGE_DECODE, st);
-                launch_decode(dv, V, k, sd, (const uint32_t *)ws.zval.p, ws.n_vis, (float *)ws.dec.p,
-                              (float *)ws.wpack.p, st);
-            }
-            StageTimer t(ctx->prof, DGS_STAGE_PROJECT_FWD, st);
-            launch_project_neural(dv, V, k, sd, (const uint32_t *)ws.count.p, (const float *)ws.vview.p,
-                                  (const float *)ws.dec.p, bp, (float4 *)ws.rec.p,
-                                  grad_buffers ? (float *)ws.g2d.p : nullptr, st);
+            // the decode writes the records too (the projection fused into it)
+            StageTimer t(ctx->prof, DGS_STAGE_DECODE, st);
+            launch_decode(dv, V, k, sd, (const uint32_t *)ws.zval.p, ws.n_vis, (float *)ws.dec.p,
+                          (float *)ws.wpack.p, (const float *)ws.vview.p, bp, (float4 *)ws.rec.p,
+                          grad_buffers ? (float *)ws.g2d.p : nullptr, st);
         } else {
             StageTimer t(ctx->prof, DGS_STAGE_PROJECT_FWD, st);
             launch_project_fwd(dv, V, k, sd, (const uint32_t *)ws.count.p, (const float *)ws.vview.p, bp,

@@ -24,7 +24,7 @@
 // of different decoders reading the same row index hit distinct banks.
 #include <algorithm>
 
-#include "internal.cuh"
+#include "project.cuh"
 
 namespace dgs {
 
@@ -120,6 +120,7 @@ struct SampleInfo {
     long long rec;   // first record (Gaussian k = 0) of this (view, cell)
     float x[3], S[3], R[9];
     float z4[4];     // distance and unit direction from the eye (the last four inputs)
+    int v;           // the view
 };
 __device__ __forceinline__ void put_info(float *s_info, int s, const SampleInfo &a) {
     float *p = s_info + s * DINFO;
@@ -133,7 +134,7 @@ __device__ __forceinline__ void put_info(float *s_info, int s, const SampleInfo 
     for (int i = 0; i < 9; ++i) p[10 + i] = a.R[i];
 #pragma unroll
     for (int i = 0; i < 4; ++i) p[19 + i] = a.z4[i];
-    p[23] = 0.f;
+    p[23] = __int_as_float(a.v);
 }
 __device__ __forceinline__ SampleInfo get_info(const float *s_info, int s) {
     const float *p = s_info + s * DINFO;
@@ -147,6 +148,7 @@ __device__ __forceinline__ SampleInfo get_info(const float *s_info, int s) {
     for (int i = 0; i < 9; ++i) a.R[i] = p[10 + i];
 #pragma unroll
     for (int i = 0; i < 4; ++i) a.z4[i] = p[19 + i];
+    a.v = __float_as_int(p[23]);
     return a;
 }
 
@@ -172,6 +174,7 @@ __global__ void __launch_bounds__(128) k_decode_samples(const ViewDesc *__restri
         if (Vw.scene_slot == slot && n >= 0 && n < N) {
             a.valid = 1;
             a.n = (int)n;
+            a.v = lo;
             a.rec = Vw.rec_base + n * sc.K;
 #pragma unroll
             for (int i = 0; i < 3; ++i) { a.x[i] = sc.cell[i * N + n]; a.S[i] = sc.cell[(3 + i) * N + n]; }
@@ -384,9 +387,12 @@ __device__ __forceinline__ void ball_offset(const SceneDev &sc, long long g, flo
 }
 
 template <int HW>
-__global__ void __launch_bounds__(256) k_decode(SceneDev sc, MlpShape S, const float *__restrict__ pk,
-                                                const float *__restrict__ srec, const float4 *__restrict__ gc,
-                                                long long nsamp, float *__restrict__ dec) {
+__global__ void __launch_bounds__(256) k_decode(const ViewDesc *__restrict__ views, SceneDev sc, MlpShape S,
+                                                const float *__restrict__ pk, const float *__restrict__ srec,
+                                                const float4 *__restrict__ gc, long long nsamp,
+                                                float *__restrict__ dec, const float *__restrict__ vview,
+                                                BlendParams bp, float4 *__restrict__ rec,
+                                                float *__restrict__ g2d_zero) {
     extern __shared__ float4 smem4[];
     float *sm = reinterpret_cast<float *>(smem4);
     const int K = S.K;
@@ -409,7 +415,7 @@ __global__ void __launch_bounds__(256) k_decode(SceneDev sc, MlpShape S, const f
             const float *p = info + s * DINFO;
             if (__float_as_int(p[1]) == 0) continue;
             const long long g = (long long)__float_as_int(p[0]) * K + k;
-            const long long rec = (long long)(unsigned)__float_as_int(p[2]) | ((long long)__float_as_int(p[3]) << 32);
+            const long long rid = (long long)(unsigned)__float_as_int(p[2]) | ((long long)__float_as_int(p[3]) << 32);
             const float4 c4 = __ldg(gc + g);  // centre and the Eq. 11 bound
             float o[kDecF];
             o[0] = c4.x; o[1] = c4.y; o[2] = c4.z;
@@ -429,9 +435,30 @@ __global__ void __launch_bounds__(256) k_decode(SceneDev sc, MlpShape S, const f
             o[10] = tanh_fast(Ot[orow(S, 0, k) + s]);
 #pragma unroll
             for (int c = 0; c < 3; ++c) o[11 + c] = sigmoid_fast(Ot[orow(S, 1, 3 * k + c) + s]);
-            float2 *dst = reinterpret_cast<float2 *>(dec + (rec + k) * kDecF);
+            float2 *dst = reinterpret_cast<float2 *>(dec + (rid + k) * kDecF);
 #pragma unroll
             for (int i = 0; i < kDecF / 2; ++i) dst[i] = make_float2(o[2 * i], o[2 * i + 1]);
+            if (rec) {  // the Gaussian's record for the blend (the projection fused into the decode)
+                const ViewDesc &Vw = views[__float_as_int(p[23])];
+                GaussIn gi;
+#pragma unroll
+                for (int i = 0; i < 3; ++i) { gi.mean[i] = o[i]; gi.scale[i] = o[3 + i]; }
+#pragma unroll
+                for (int i = 0; i < 4; ++i) gi.quat[i] = o[6 + i];
+                gi.logit = 0.f;
+                const float knone[16][3] = {};
+                ProjCore c;
+                float4 r0, r1, r2;
+                gauss_record<true>(Vw, gi, knone, 0, o[10], vview[Vw.cell_base + __float_as_int(p[0])], bp, c, r0,
+                                   r1, r2, o + 11);
+                if (!(o[10] > 0.f)) r0 = make_float4(0.f, 0.f, -1.f, -1.f);  // sigma <= 0: not drawn
+                float4 *rp = rec + (rid + k) * kRecF4;
+                rp[0] = r0; rp[1] = r1; rp[2] = r2;
+                if (g2d_zero) {
+                    float4 *z = reinterpret_cast<float4 *>(g2d_zero + (rid + k) * kGradF);
+                    z[0] = z[1] = z[2] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
         }
         __syncthreads();
     }
@@ -813,7 +840,8 @@ static void decode_prep(const ViewDesc *views, int n_views, int slot, const Scen
 }
 
 void launch_decode(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const uint32_t *samples,
-                   long long nsamp, float *dec, float *scratch, cudaStream_t st) {
+                   long long nsamp, float *dec, float *scratch, const float *vview, const BlendParams &bp,
+                   float4 *rec, float *g2d_zero, cudaStream_t st) {
     if (nsamp <= 0 || !sc.feat) return;
     const MlpShape S = mlp_shape(sc.F, sc.H, sc.K, false);
     float *pk = scratch, *srec = scratch + up_to(S.g_total, 4);
@@ -825,10 +853,10 @@ void launch_decode(const ViewDesc *views, int n_views, int slot, const SceneDev 
     const long long tiles = (nsamp + S.M - 1) / S.M;
     if (S.HW == 4) {
         const int b = persistent_grid(k_decode<4>, 32 * S.W, smem, tiles);
-        k_decode<4><<<b, 32 * S.W, smem, st>>>(sc, S, pk, srec, gc, nsamp, dec);
+        k_decode<4><<<b, 32 * S.W, smem, st>>>(views, sc, S, pk, srec, gc, nsamp, dec, vview, bp, rec, g2d_zero);
     } else {
         const int b = persistent_grid(k_decode<8>, 32 * S.W, smem, tiles);
-        k_decode<8><<<b, 32 * S.W, smem, st>>>(sc, S, pk, srec, gc, nsamp, dec);
+        k_decode<8><<<b, 32 * S.W, smem, st>>>(views, sc, S, pk, srec, gc, nsamp, dec, vview, bp, rec, g2d_zero);
     }
 }
 

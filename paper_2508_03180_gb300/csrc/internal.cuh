@@ -163,16 +163,16 @@ void launch_gauss_bin(const ViewDesc *views, int n_views, const SceneDev &sc, co
                       uint32_t *visible, cudaStream_t st);
 // Neural scenes: decode the Gaussians of the (view, cell) entries
 // samples[0 .. nsamp) (entry e = cell_base of its view + cell; NULL: entry q
-// for sample q) of scene `slot` into dec [rec_base + g][kDecF], then their
-// records (colour and opacity as decoded).  Features are rows [N][F].
+// for sample q) of scene `slot` into dec [rec_base + g][kDecF] and, with rec
+// non-NULL, write their records (colour and opacity as decoded, sigma <= 0
+// not drawn; v_n from vview) and zero their g2d rows (g2d_zero non-NULL).
+// Features are rows [N][F].
 void launch_decode(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const uint32_t *samples,
-                   long long nsamp, float *dec, float *scratch, cudaStream_t st);
+                   long long nsamp, float *dec, float *scratch, const float *vview, const BlendParams &bp,
+                   float4 *rec, float *g2d_zero, cudaStream_t st);
 // Floats of scratch (16-byte aligned) that one launch_decode (bwd = false)
 // or launch_decode_bwd (bwd = true) call needs.
 long long decode_scratch_floats(int F, int H, int K, long long nsamp, long long G, bool bwd);
-void launch_project_neural(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const uint32_t *count,
-                           const float *vview, const float *dec, const BlendParams &bp, float4 *rec, float *g2d_zero,
-                           cudaStream_t st);
 // Adjoints of a neural scene: the records' gradients with respect to the
 // decoded values of every decoded (view, Gaussian) (gdec, layout of dec),
 // then through the decode of the same samples to the packed weights g_mlp,

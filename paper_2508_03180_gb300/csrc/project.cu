@@ -14,156 +14,9 @@
 // One thread per Gaussian reads its parameters once (SoA planes, coalesced)
 // and writes one 48-byte record per view, so a batch of views costs one pass
 // over the 236 B/Gaussian of parameters.
-#include "internal.cuh"
-#include "sh.cuh"
+#include "project.cuh"
 
 namespace dgs {
-
-constexpr float KAPPA = 0.8493218002880191f;  // sqrt(log2(e) / 2), log2(e) = 1/ln 2
-
-
-
-struct GaussIn {
-    float mean[3], scale[3], quat[4], logit;
-};
-
-__device__ __forceinline__ GaussIn load_gauss(const float *__restrict__ gp, long long G, long long g) {
-    GaussIn p;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) p.mean[i] = gp[i * G + g];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) p.scale[i] = gp[(3 + i) * G + g];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) p.quat[i] = gp[(6 + i) * G + g];
-    p.logit = gp[10 * G + g];
-    return p;
-}
-
-// Fixed-order FP32 part shared by forward and backward: view-space mean,
-// J, T = J R_view, 3D covariance, and the diagonal of Sigma'.
-struct ProjCore {
-    float t[3], x, y, xc, yc, J00, J02, J11, J12, T[6], Rg[9], M[9], S[9], V[6], sxx, syy;
-    bool valid;
-};
-
-// Screen covariance without cancellation: with U = T M (2x3, rows u and w),
-// Sigma' = U U^T + dilation I, so s_xx = |u|^2 + d, s_yy = |w|^2 + d, s_xy = u.w
-// and det = |u x w|^2 + d (|u|^2 + |w|^2) + d^2 (Lagrange's identity), a sum of
-// non-negative terms.  (The fixed-order s_xx, s_yy of ProjCore serve only the
-// AABB extents.)
-struct ScreenCov {
-    float u[3], w[3], sxx, syy, sxy, det;
-};
-
-__device__ __forceinline__ ScreenCov screen_cov(const ProjCore &c, float dilation) {
-    ScreenCov q;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        q.u[j] = c.T[0] * c.M[j] + c.T[1] * c.M[3 + j] + c.T[2] * c.M[6 + j];
-        q.w[j] = c.T[3] * c.M[j] + c.T[4] * c.M[3 + j] + c.T[5] * c.M[6 + j];
-    }
-    const float uu = q.u[0] * q.u[0] + q.u[1] * q.u[1] + q.u[2] * q.u[2];
-    const float ww = q.w[0] * q.w[0] + q.w[1] * q.w[1] + q.w[2] * q.w[2];
-    q.sxy = q.u[0] * q.w[0] + q.u[1] * q.w[1] + q.u[2] * q.w[2];
-    const float x0 = q.u[1] * q.w[2] - q.u[2] * q.w[1];
-    const float x1 = q.u[2] * q.w[0] - q.u[0] * q.w[2];
-    const float x2 = q.u[0] * q.w[1] - q.u[1] * q.w[0];
-    q.sxx = uu + dilation;
-    q.syy = ww + dilation;
-    q.det = (x0 * x0 + x1 * x1 + x2 * x2) + dilation * (uu + ww) + dilation * dilation;
-    return q;
-}
-
-__device__ __forceinline__ void proj_core(const ViewDesc &Vw, const GaussIn &p, float dilation, ProjCore &c) {
-    xform_s(Vw.R, Vw.t, p.mean[0], p.mean[1], p.mean[2], c.t);
-    c.valid = c.t[2] > Vw.znear;
-    if (!c.valid) return;
-    c.x = fdiv_s(c.t[0], c.t[2]);
-    c.y = fdiv_s(c.t[1], c.t[2]);
-    rot_from_quat_s(p.quat[0], p.quat[1], p.quat[2], p.quat[3], c.Rg);
-    float *M = c.M;
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) M[3 * i + j] = fmul_s(c.Rg[3 * i + j], p.scale[j]);
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-            c.S[3 * i + j] = fadd_s(fadd_s(fmul_s(M[3 * i], M[3 * j]), fmul_s(M[3 * i + 1], M[3 * j + 1])),
-                                    fmul_s(M[3 * i + 2], M[3 * j + 2]));
-    const float limx = fmul_s(1.3f, fdiv_s(fmul_s(0.5f, (float)Vw.W), Vw.fx));
-    const float limy = fmul_s(1.3f, fdiv_s(fmul_s(0.5f, (float)Vw.H), Vw.fy));
-    c.xc = fminf(fmaxf(c.x, -limx), limx);
-    c.yc = fminf(fmaxf(c.y, -limy), limy);
-    c.J00 = fdiv_s(Vw.fx, c.t[2]);
-    c.J02 = -fdiv_s(fmul_s(Vw.fx, c.xc), c.t[2]);
-    c.J11 = fdiv_s(Vw.fy, c.t[2]);
-    c.J12 = -fdiv_s(fmul_s(Vw.fy, c.yc), c.t[2]);
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        c.T[j] = fadd_s(fmul_s(c.J00, Vw.R[j]), fmul_s(c.J02, Vw.R[6 + j]));
-        c.T[3 + j] = fadd_s(fmul_s(c.J11, Vw.R[3 + j]), fmul_s(c.J12, Vw.R[6 + j]));
-    }
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-            c.V[3 * a + j] = fadd_s(fadd_s(fmul_s(c.T[3 * a], c.S[j]), fmul_s(c.T[3 * a + 1], c.S[3 + j])),
-                                    fmul_s(c.T[3 * a + 2], c.S[6 + j]));
-    c.sxx = fadd_s(fadd_s(fadd_s(fmul_s(c.V[0], c.T[0]), fmul_s(c.V[1], c.T[1])), fmul_s(c.V[2], c.T[2])), dilation);
-    c.syy = fadd_s(fadd_s(fadd_s(fmul_s(c.V[3], c.T[3]), fmul_s(c.V[4], c.T[4])), fmul_s(c.V[5], c.T[5])), dilation);
-}
-
-// The 48-byte record of Gaussian p in view Vw (an invalid Gaussian, mean not
-// in front of the near plane, gets ext = -1 so no AABB test passes).  k: SH
-// coefficients, cv: the cell's v_n.  Returns c.valid; c keeps the view-space mean.
-template <bool DIRECT_RGB = false>
-__device__ __forceinline__ bool gauss_record(const ViewDesc &Vw, const GaussIn &p, const float (&k)[16][3],
-                                             int sh_degree, float opac, float cv, const BlendParams &bp,
-                                             ProjCore &c, float4 &r0, float4 &r1, float4 &r2,
-                                             const float *rgb = nullptr) {
-    proj_core(Vw, p, bp.dilation, c);
-    if (!c.valid) {
-        r0 = make_float4(0.f, 0.f, -1.f, -1.f);
-        r1 = make_float4(0.f, 0.f, 0.f, 0.f);
-        r2 = make_float4(0.f, 0.f, 0.f, cv);
-        return false;
-    }
-    const float mx = fadd_s(fmul_s(Vw.fx, c.x), Vw.cx);
-    const float my = fadd_s(fmul_s(Vw.fy, c.y), Vw.cy);
-    const float ex = fmul_s(bp.ksigma, fsqrt_s(c.sxx));
-    const float ey = fmul_s(bp.ksigma, fsqrt_s(c.syy));
-    // conic Q = Sigma'^-1 = L L^T, L = [[p, 0], [r, t]]:
-    // p = sqrt(s_yy/det), r = -s_xy/sqrt(s_yy det), t = 1/sqrt(s_yy),
-    // so q(d) = (p dx + r dy)^2 + (t dy)^2 is a sum of squares
-    const ScreenCov sc2 = screen_cov(c, bp.dilation);
-    const float ip = rsqrtf(sc2.syy * sc2.det);
-    const float fp = sc2.syy * ip, fr = -sc2.sxy * ip, ft = rsqrtf(sc2.syy);
-    float col[3];
-    if (DIRECT_RGB) {
-        col[0] = rgb[0]; col[1] = rgb[1]; col[2] = rgb[2];
-    } else {
-        float d0 = p.mean[0] - Vw.eye[0], d1 = p.mean[1] - Vw.eye[1], d2 = p.mean[2] - Vw.eye[2];
-        const float il = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
-        d0 *= il; d1 *= il; d2 *= il;
-        float Y[16];
-        sh_eval(d0, d1, d2, sh_degree, Y);
-#pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-            float s = 0.5f;
-#pragma unroll
-            for (int cidx = 0; cidx < 16; ++cidx) s += k[cidx][ch] * Y[cidx];
-            col[ch] = fmaxf(s, 0.0f);
-        }
-    }
-    r0 = make_float4(mx, my, ex, ey);
-    // L scaled by kappa = sqrt(log2(e)/2): G' = exp2(-(s1^2 + s2^2)),
-    // s1 = r1.x dx + r1.y dy, s2 = r1.z dy
-    r1 = make_float4(KAPPA * fp, KAPPA * fr, KAPPA * ft, opac);
-    r2 = make_float4(col[0], col[1], col[2], cv);
-    return true;
-}
 
 __device__ __forceinline__ void load_sh(const SceneDev &sc, long long g, float (&k)[16][3]) {
     const int C = (sc.sh_degree + 1) * (sc.sh_degree + 1);
@@ -197,43 +50,6 @@ __device__ __forceinline__ void project_scene(const ViewDesc *__restrict__ views
             ProjCore c;
             float4 r0, r1, r2;
             gauss_record(Vw, p, k, sc.sh_degree, opac, vview[Vw.cell_base + cell], bp, c, r0, r1, r2);
-            float4 *o = rec + (Vw.rec_base + g) * kRecF4;
-            o[0] = r0; o[1] = r1; o[2] = r2;
-            if (g2d_zero) {
-                float4 *z = reinterpret_cast<float4 *>(g2d_zero + (Vw.rec_base + g) * kGradF);
-                z[0] = z[1] = z[2] = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-        }
-    }
-}
-
-// Records of the decoded Gaussians of a neural scene (dec as written by
-// k_decode): colour and opacity as decoded; sigma <= 0 is not drawn.
-__global__ void __launch_bounds__(128) k_project_neural(const ViewDesc *__restrict__ views, int n_views, int slot,
-                                                        SceneDev sc, const uint32_t *__restrict__ count,
-                                                        const float *__restrict__ vview, const float *__restrict__ dec,
-                                                        BlendParams bp, float4 *__restrict__ rec,
-                                                        float *__restrict__ g2d_zero) {
-    const long long G = sc.G;
-    const int K = sc.K;
-    const float knone[16][3] = {};
-    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < G; g += (long long)gridDim.x * blockDim.x) {
-        const long long cell = g / K;
-        for (int v = 0; v < n_views; ++v) {
-            const ViewDesc &Vw = views[v];
-            if (Vw.scene_slot != slot || count[Vw.cell_base + cell] == 0u) continue;
-            const float *d = dec + (Vw.rec_base + g) * kDecF;
-            GaussIn p;
-#pragma unroll
-            for (int i = 0; i < 3; ++i) { p.mean[i] = d[i]; p.scale[i] = d[3 + i]; }
-#pragma unroll
-            for (int i = 0; i < 4; ++i) p.quat[i] = d[6 + i];
-            p.logit = 0.f;
-            const float opac = d[10];
-            ProjCore c;
-            float4 r0, r1, r2;
-            gauss_record<true>(Vw, p, knone, 0, opac, vview[Vw.cell_base + cell], bp, c, r0, r1, r2, d + 11);
-            if (!(opac > 0.f)) r0 = make_float4(0.f, 0.f, -1.f, -1.f);  // not drawn
             float4 *o = rec + (Vw.rec_base + g) * kRecF4;
             o[0] = r0; o[1] = r1; o[2] = r2;
             if (g2d_zero) {
@@ -368,14 +184,6 @@ void launch_project_fwd(const ViewDesc *views, int n_views, int slot, const Scen
                         const float *vview, const BlendParams &bp, float4 *rec, float *g2d_zero, cudaStream_t st) {
     if (sc.G == 0 || n_views == 0) return;
     k_project_fwd<<<grid_for(sc.G, 128), 128, 0, st>>>(views, n_views, slot, sc, count, vview, bp, rec, g2d_zero);
-}
-
-void launch_project_neural(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const uint32_t *count,
-                           const float *vview, const float *dec, const BlendParams &bp, float4 *rec, float *g2d_zero,
-                           cudaStream_t st) {
-    if (sc.G == 0 || n_views == 0) return;
-    k_project_neural<<<grid_for(sc.G, 128), 128, 0, st>>>(views, n_views, slot, sc, count, vview, dec, bp, rec,
-                                                          g2d_zero);
 }
 
 void launch_cell_v_grad(const ViewDesc *views, int n_views, const SceneDev &sc, const float *gv, float *g_cell_v,
