@@ -65,7 +65,7 @@ def lib():
         L.or_cell_rects.restype = None
         L.or_tile_lists.argtypes = [i64, P, P, i32, i32, P, i64, P]
         L.or_tile_lists.restype = i64
-        L.or_gauss_decisions.argtypes = [i64, P, P, P, P, ctypes.c_float, ctypes.c_float, P, P, P]
+        L.or_gauss_decisions.argtypes = [i64, P, P, P, P, ctypes.c_float, ctypes.c_float, ctypes.c_int, P, P, P]
         L.or_gauss_decisions.restype = None
         L.or_blend.argtypes = [i32, i32, i32, i32, P, P, P, P, P, P, P, P, P, P, P, P, i32, i32,
                                P, P, P, P, P]
@@ -102,6 +102,13 @@ class Options:
     weight sum D is not above this keeps the background; dilation: EWA
     low-pass 0.3 px^2; ksigma: AABB half extent in standard deviations;
     delta: relative slack on T when checking a given termination count.
+    Variants of the hybrid renderer (off by default; the same meaning as the
+    renderer's config flags): w_bg, a background weight in the normalisation
+    (Eq. 4's term: C = (N + w_bg bg) / (D + w_bg)); alpha_skip, alpha < 1/255
+    contributes nothing; term_exclude, a cell that would take T below eps is
+    not blended; aabb_square, the AABB is the square of radius
+    ceil(ksigma sqrt(lambda_max(Sigma'))); out_numerator, the output is the
+    numerator N of Eq. 12.
     """
     eps: float = 1e-4
     alpha_max: float = 0.99
@@ -111,9 +118,19 @@ class Options:
     ksigma: float = 3.0
     tile: int = 16
     delta: float = 1e-3
+    w_bg: float = 0.0
+    alpha_skip: bool = False
+    term_exclude: bool = False
+    aabb_square: bool = False
+    out_numerator: bool = False
+
+    def flags(self) -> int:
+        return (1 if self.alpha_skip else 0) | (2 if self.term_exclude else 0) | \
+            (4 if self.aabb_square else 0) | (8 if self.out_numerator else 0)
 
     def blend_opts(self) -> np.ndarray:
-        return np.array([self.eps, self.alpha_max, self.d_min, *self.bg, self.delta], dtype=np.float64)
+        return np.array([self.eps, self.alpha_max, self.d_min, *self.bg, self.delta, self.w_bg, float(self.flags())],
+                        dtype=np.float64)
 
 
 def num_threads() -> int:
@@ -161,7 +178,7 @@ def gauss_decisions(scene, cam, opt: Options = Options()):
     valid = np.empty(G, dtype=np.uint8)
     lib().or_gauss_decisions(G, _p(_c(scene.g_mean, np.float32)), _p(_c(scene.g_scale, np.float32)),
                              _p(_c(scene.g_quat, np.float32)), _p(_c(cam, np.float32)),
-                             opt.dilation, opt.ksigma, _p(mu2), _p(ext), _p(valid))
+                             opt.dilation, opt.ksigma, 1 if opt.aabb_square else 0, _p(mu2), _p(ext), _p(valid))
     return mu2, ext, valid
 
 

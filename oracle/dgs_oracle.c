@@ -199,7 +199,7 @@ int64_t or_tile_lists(int64_t N, const int32_t *rect, const float *depth, int Tx
  * Outputs (per Gaussian): mu2[2g..], ext[2g..] (half extents), valid[g].
  */
 void or_gauss_decisions(int64_t G, const float *mean, const float *scale, const float *quat,
-                        const float *cam, float dilation, float ksigma,
+                        const float *cam, float dilation, float ksigma, int square,
                         float *mu2, float *ext, uint8_t *valid) {
     const float W = cam[0], H = cam[1];
     const float fx = cam[2], fy = cam[3], ppx = cam[4], ppy = cam[5], znear = cam[6];
@@ -238,8 +238,19 @@ void or_gauss_decisions(int64_t G, const float *mean, const float *scale, const 
                 V[3 * a + j] = (T[3 * a] * S[j] + T[3 * a + 1] * S[3 + j]) + T[3 * a + 2] * S[6 + j];
         const float sxx = ((V[0] * T[0] + V[1] * T[1]) + V[2] * T[2]) + dilation;
         const float syy = ((V[3] * T[3] + V[4] * T[4]) + V[5] * T[5]) + dilation;
-        ext[2 * g] = ksigma * sqrtf(sxx);
-        ext[2 * g + 1] = ksigma * sqrtf(syy);
+        if (square) {
+            /* the 3DGS square box: radius ceil(k sqrt(lambda_max)) of Sigma' in both axes,
+             * lambda_max = (sxx + syy)/2 + sqrt(((sxx - syy)/2)^2 + sxy^2) */
+            const float sxy = (V[0] * T[3] + V[1] * T[4]) + V[2] * T[5];
+            const float mid = 0.5f * (sxx + syy), hd = 0.5f * (sxx - syy);
+            const float lam = mid + sqrtf(hd * hd + sxy * sxy);
+            const float r = ceilf(ksigma * sqrtf(lam));
+            ext[2 * g] = r;
+            ext[2 * g + 1] = r;
+        } else {
+            ext[2 * g] = ksigma * sqrtf(sxx);
+            ext[2 * g + 1] = ksigma * sqrtf(syy);
+        }
     }
 }
 
@@ -259,7 +270,14 @@ typedef struct {
     const uint8_t *valid;     /* G */
     const double *cell_v;     /* N   calibration scalar v_n */
     double eps, alpha_max, d_min, bg[3], delta;
+    double w_bg;              /* background weight of Eq. 4 in the hybrid's normalisation (0: none) */
+    int alpha_skip;           /* alpha < 1/255 contributes nothing (the 3DGS skip) */
+    int term_exclude;         /* a cell that would take T below eps is not blended (3DGS rule) */
+    int out_numerator;        /* output the numerator N of Eq. 12, not N / D */
 } or_scene_view;
+
+/* option bits of opts[8] (the same values as the renderer's config flags) */
+enum { OR_ALPHA_SKIP = 1, OR_TERM_EXCLUDE = 2, OR_AABB_SQUARE = 4, OR_NUMERATOR = 8 };
 
 static void or_unpack(or_scene_view *s, int W, int H, int tile, int K, const int64_t *range,
                       const int32_t *cells, const double *mu2, const double *conic, const double *opac,
@@ -270,6 +288,18 @@ static void or_unpack(or_scene_view *s, int W, int H, int tile, int K, const int
     s->valid = valid; s->cell_v = cell_v;
     s->eps = opts[0]; s->alpha_max = opts[1]; s->d_min = opts[2];
     s->bg[0] = opts[3]; s->bg[1] = opts[4]; s->bg[2] = opts[5]; s->delta = opts[6];
+    s->w_bg = opts[7];
+    const int flags = (int)opts[8];
+    s->alpha_skip = (flags & OR_ALPHA_SKIP) != 0;
+    s->term_exclude = (flags & OR_TERM_EXCLUDE) != 0;
+    s->out_numerator = (flags & OR_NUMERATOR) != 0;
+}
+
+/* The comparators take the hybrid renderer's shared settings only: its
+ * blending options (alpha skip, termination variant, background weight,
+ * numerator output) are the hybrid's own. */
+static void or_comparator_opts(or_scene_view *s) {
+    s->alpha_skip = 0; s->term_exclude = 0; s->out_numerator = 0; s->w_bg = 0.0;
 }
 
 /* alpha of Gaussian g at pixel centre (px, py); 0 when the AABB test fails
@@ -285,60 +315,101 @@ static double or_alpha(const or_scene_view *s, int64_t g, float pxf, float pyf, 
     const double a = s->conic[3 * g], b = s->conic[3 * g + 1], c = s->conic[3 * g + 2];
     const double q = a * dx * dx + 2.0 * b * dx * dy + c * dy * dy;
     const double G = exp(-0.5 * q);
-    *Gout = G; *dxo = dx; *dyo = dy;
     double al = s->opac[g] * G;
+    if (s->alpha_skip && al < 1.0 / 255.0) return 0.0; /* skipped like a failed AABB test */
+    *Gout = G; *dxo = dx; *dyo = dy;
     if (al >= s->alpha_max) { al = s->alpha_max; *clamped = 1; }
     return al;
+}
+
+/* A, B and P of cell entry n at pixel centre (pxf, pyf) (Eq. 12-14). */
+static void or_cell(const or_scene_view *s, int64_t beg, int n, float pxf, float pyf, double A[3], double *B,
+                    double *P) {
+    const int32_t cell = s->cells[beg + n];
+    const double v = s->cell_v[cell];
+    A[0] = A[1] = A[2] = 0.0; *B = 0.0; *P = 1.0;
+    for (int k = 0; k < s->K; ++k) {
+        const int64_t g = (int64_t)cell * s->K + k;
+        double G, dx, dy; int cl;
+        const double al = or_alpha(s, g, pxf, pyf, &G, &cl, &dx, &dy);
+        A[0] += al * s->rgb[3 * g]; A[1] += al * s->rgb[3 * g + 1]; A[2] += al * s->rgb[3 * g + 2];
+        *B += al;
+        *P *= (1.0 - v * al);
+    }
 }
 
 /* One pixel, Eq. 12-14.  Walk the tile's cells front to back.  With
  * count < 0 the paper's rule decides where to stop: before cell n, stop if
  * T_n < eps (Sec. V-B: blending halts once T^cell falls below eps, so the
- * cell that took T below eps is still blended).  With count >= 0 exactly
- * min(count, len) cells are processed instead (used to check a given choice).
- * Returns the number of cells processed; fills N (3), D, T (after the last
- * processed cell) and Tlast (T_n before the last processed cell, 1 if none). */
+ * cell that took T below eps is still blended); with term_exclude, a cell
+ * whose blending would take T below eps is not blended and ends the pixel
+ * (the 3DGS rule).  With count >= 0 exactly min(count, len) cells are
+ * processed instead (used to check a given choice).  Returns the number of
+ * cells processed; fills N (3), D, T (after the last processed cell), Tlast
+ * (T_n before the last processed cell, 1 if none) and Tpeek (T times the P of
+ * the first unprocessed cell; T if none). */
 static int or_pixel(const or_scene_view *s, int64_t beg, int64_t end, int x, int y, int count,
-                    double N[3], double *Dout, double *Tout, double *Tlast) {
+                    double N[3], double *Dout, double *Tout, double *Tlast, double *Tpeek) {
     const float pxf = (float)x + 0.5f, pyf = (float)y + 0.5f;
     const int len = (int)(end - beg);
     double T = 1.0, D = 0.0;
     N[0] = N[1] = N[2] = 0.0;
     *Tlast = 1.0;
+    *Tpeek = 1.0;
     int n = 0;
     for (; n < len; ++n) {
         if (count < 0 && T < s->eps) break;
         if (count >= 0 && n >= count) break;
-        const int32_t cell = s->cells[beg + n];
-        const double v = s->cell_v[cell];
-        double A[3] = {0, 0, 0}, B = 0.0, P = 1.0;
-        for (int k = 0; k < s->K; ++k) {
-            const int64_t g = (int64_t)cell * s->K + k;
-            double G, dx, dy; int cl;
-            const double al = or_alpha(s, g, pxf, pyf, &G, &cl, &dx, &dy);
-            A[0] += al * s->rgb[3 * g]; A[1] += al * s->rgb[3 * g + 1]; A[2] += al * s->rgb[3 * g + 2];
-            B += al;
-            P *= (1.0 - v * al);
-        }
+        double A[3], B, P;
+        or_cell(s, beg, n, pxf, pyf, A, &B, &P);
+        if (count < 0 && s->term_exclude && T * P < s->eps) break;
+        const double v = s->cell_v[s->cells[beg + n]];
         /* w_n = v_n T_n (Eq. 13); numerator and denominator of Eq. 12 */
         N[0] += v * T * A[0]; N[1] += v * T * A[1]; N[2] += v * T * A[2];
         D += v * T * B;
         *Tlast = T;
         T *= P; /* Eq. 14 */
     }
+    *Tpeek = T;
+    if (n < len) {
+        double A[3], B, P;
+        or_cell(s, beg, n, pxf, pyf, A, &B, &P);
+        *Tpeek = T * P;
+    }
     *Dout = D; *Tout = T;
     return n;
 }
 
 /* Is processing exactly `count` cells a valid outcome of the stopping rule
- * when transmittance is only known to relative accuracy delta?  Every
- * processed cell must have had T_n >= eps (1 - delta), and unless the list
- * ran out, the next T must be < eps (1 + delta). */
-static int or_count_ok(const or_scene_view *s, int len, int count, double Tlast, double Tafter) {
+ * when transmittance is only known to relative accuracy delta?  The paper's
+ * rule: every processed cell had T_n >= eps (1 - delta), and unless the list
+ * ran out, the next T is < eps (1 + delta).  With term_exclude: T after every
+ * processed cell is >= eps (1 - delta), and unless the list ran out, blending
+ * the next cell would take T below eps (1 + delta). */
+static int or_count_ok(const or_scene_view *s, int len, int count, double Tlast, double Tafter, double Tpeek) {
     if (count < 0 || count > len) return 0;
+    if (s->term_exclude) {
+        if (count > 0 && Tafter < s->eps * (1.0 - s->delta)) return 0;
+        if (count < len && !(Tpeek < s->eps * (1.0 + s->delta))) return 0;
+        return 1;
+    }
     if (count > 0 && Tlast < s->eps * (1.0 - s->delta)) return 0;
     if (count < len && !(Tafter < s->eps * (1.0 + s->delta))) return 0;
     return 1;
+}
+
+/* Output colour of a pixel from N and D: N / D (Eq. 12); with a background
+ * weight, (N + w_bg bg) / (D + w_bg) (Eq. 4's background term); the
+ * background where that denominator is not above d_min; N itself with
+ * out_numerator.  Returns the denominator used (0 with out_numerator). */
+static double or_colour(const or_scene_view *s, const double N[3], double D, double C[3]) {
+    if (s->out_numerator) {
+        C[0] = N[0]; C[1] = N[1]; C[2] = N[2];
+        return 0.0;
+    }
+    const double Dp = D + s->w_bg;
+    for (int c = 0; c < 3; ++c) C[c] = Dp > s->d_min ? (N[c] + s->w_bg * s->bg[c]) / Dp : s->bg[c];
+    return Dp;
 }
 
 /*
@@ -348,7 +419,7 @@ static int or_count_ok(const or_scene_view *s, int len, int count, double Tlast,
  * (Eq. 12 has no background term; a pixel that no Gaussian reaches keeps
  * the background colour).  forced_ndone (nullable): render with those
  * counts instead of the oracle's own and count the invalid ones (returned).
- * opts: eps alpha_max d_min bg_r bg_g bg_b delta.
+ * opts: eps alpha_max d_min bg_r bg_g bg_b delta w_bg flags.
  */
 int64_t or_blend(int W, int H, int tile, int K, const int64_t *range, const int32_t *cells,
                  const double *mu2, const double *conic, const double *opac, const double *rgb,
@@ -367,15 +438,16 @@ int64_t or_blend(int W, int H, int tile, int K, const int64_t *range, const int3
         for (int y = ty * tile; y < (ty + 1) * tile && y < H; ++y)
             for (int x = tx * tile; x < (tx + 1) * tile && x < W; ++x) {
                 const int64_t p = (int64_t)y * W + x;
-                double N[3], D, T, Tl;
-                const int own = or_pixel(&s, beg, end, x, y, -1, N, &D, &T, &Tl);
+                double N[3], D, T, Tl, Tp, C[3];
+                const int own = or_pixel(&s, beg, end, x, y, -1, N, &D, &T, &Tl, &Tp);
                 if (forced_ndone) {
                     const int cnt = forced_ndone[p];
-                    or_pixel(&s, beg, end, x, y, cnt < 0 ? 0 : cnt, N, &D, &T, &Tl);
-                    if (!or_count_ok(&s, (int)(end - beg), cnt, Tl, T)) bad += 1;
+                    or_pixel(&s, beg, end, x, y, cnt < 0 ? 0 : cnt, N, &D, &T, &Tl, &Tp);
+                    if (!or_count_ok(&s, (int)(end - beg), cnt, Tl, T, Tp)) bad += 1;
                 }
+                or_colour(&s, N, D, C);
                 for (int c = 0; c < 3; ++c) {
-                    out_C[c * HW + p] = D > s.d_min ? N[c] / D : s.bg[c];
+                    out_C[c * HW + p] = C[c];
                     if (out_N) out_N[c * HW + p] = N[c];
                 }
                 out_D[p] = D; out_T[p] = T; out_ndone[p] = own;
@@ -391,7 +463,8 @@ int64_t or_blend(int W, int H, int tile, int K, const int64_t *range, const int3
  * skip, alpha clamp, termination) are held fixed.  ndone (nullable) fixes the
  * processed-cell count per pixel, else the oracle's own is used.
  *
- * With C = N/D:  dL/dN = g/D,  dL/dD = -(g.C)/D.  For cell n with
+ * With C = N/D:  dL/dN = g/D,  dL/dD = -(g.C)/D (with a background weight
+ * D + w_bg in place of D; with out_numerator dL/dN = g, dL/dD = 0).  For cell n with
  * A_n = sum_k alpha c, B_n = sum_k alpha, P_n = prod_k (1 - v alpha):
  *   direct        dL/dT_n  = v_n (dN.A_n + dD B_n)
  *   T_m = prod_{i<m} P_i, so for i < m   dT_m/dalpha_{ik} = -v_i T_m / (1 - v_i alpha_{ik})
@@ -423,14 +496,15 @@ void or_blend_grad(int W, int H, int tile, int K, const int64_t *range, const in
             for (int x = tx * tile; x < (tx + 1) * tile && x < W; ++x) {
                 const int64_t p = (int64_t)y * W + x;
                 const float pxf = (float)x + 0.5f, pyf = (float)y + 0.5f;
-                double Nv[3], D, Tfin, Tl;
+                double Nv[3], D, Tfin, Tl, Tp, C[3];
                 const int nd = or_pixel(&s, beg, end, x, y, ndone ? (ndone[p] < 0 ? 0 : ndone[p]) : -1,
-                                        Nv, &D, &Tfin, &Tl);
-                if (!(D > s.d_min)) continue; /* background: constant output */
+                                        Nv, &D, &Tfin, &Tl, &Tp);
+                const double Dp = or_colour(&s, Nv, D, C);
+                if (!s.out_numerator && !(Dp > s.d_min)) continue; /* background: constant output */
                 const double g[3] = {dL_dC[p], dL_dC[HW + p], dL_dC[2 * HW + p]};
-                const double C[3] = {Nv[0] / D, Nv[1] / D, Nv[2] / D};
-                const double dN[3] = {g[0] / D, g[1] / D, g[2] / D};
-                const double dD = -(g[0] * C[0] + g[1] * C[1] + g[2] * C[2]) / D;
+                const double iD = s.out_numerator ? 1.0 : 1.0 / Dp;
+                const double dN[3] = {g[0] * iD, g[1] * iD, g[2] * iD};
+                const double dD = s.out_numerator ? 0.0 : -(g[0] * C[0] + g[1] * C[1] + g[2] * C[2]) * iD;
                 /* forward again, storing the per-cell quantities */
                 double T = 1.0;
                 for (int n = 0; n < nd; ++n) {
@@ -571,7 +645,7 @@ static int or_alpha_pixel(const or_scene_view *s, int64_t beg, int64_t end, int 
  * index).  out_C [3][H][W] = sum_i T_i alpha_i c_i + T_final bg (the 3DGS
  * background convention); out_T, out_ndone [H][W].  forced_ndone as in
  * or_blend (returns the number of invalid forced counts).
- * opts: eps alpha_max d_min bg_r bg_g bg_b delta.
+ * opts: as for or_blend (the hybrid-only options are ignored).
  */
 int64_t or_alpha_blend(int W, int H, int tile, const int64_t *range, const int32_t *list,
                        const double *mu2, const double *conic, const double *opac, const double *rgb,
@@ -580,6 +654,7 @@ int64_t or_alpha_blend(int W, int H, int tile, const int64_t *range, const int32
                        int32_t *out_ndone) {
     or_scene_view s;
     or_unpack(&s, W, H, tile, 1, range, list, mu2, conic, opac, rgb, mu2f, extf, valid, NULL, opts);
+    or_comparator_opts(&s);
     const int Tx = (W + tile - 1) / tile;
     const int64_t HW = (int64_t)H * W;
     int64_t bad = 0;
@@ -595,7 +670,7 @@ int64_t or_alpha_blend(int W, int H, int tile, const int64_t *range, const int32
                 if (forced_ndone) {
                     const int cnt = forced_ndone[p];
                     or_alpha_pixel(&s, beg, end, x, y, cnt < 0 ? 0 : cnt, C, &T, &Tl);
-                    if (!or_count_ok(&s, (int)(end - beg), cnt, Tl, T)) bad += 1;
+                    if (!or_count_ok(&s, (int)(end - beg), cnt, Tl, T, T)) bad += 1;
                 }
                 for (int c = 0; c < 3; ++c) out_C[c * HW + p] = C[c] + T * s.bg[c];
                 out_T[p] = T; out_ndone[p] = own;
@@ -618,6 +693,7 @@ void or_wsr(int W, int H, int tile, const int64_t *range, const int32_t *list, c
             double *out_C) {
     or_scene_view s;
     or_unpack(&s, W, H, tile, 1, range, list, mu2, conic, opac, rgb, mu2f, extf, valid, NULL, opts);
+    or_comparator_opts(&s);
     const int Tx = (W + tile - 1) / tile;
     const int64_t HW = (int64_t)H * W;
 #pragma omp parallel for schedule(dynamic, 1)
