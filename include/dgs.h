@@ -65,9 +65,34 @@ typedef struct {
     float dilation;   /* 0.3 px^2 added to the EWA screen covariance */
     float ksigma;     /* 3: AABB half extent in standard deviations (Sec. VI-A) */
     int32_t device;   /* CUDA device ordinal (0) */
-    int32_t reserved;
+    int32_t flags;    /* 0: variants of the hybrid renderer's readings, DGS_FLAG_* below */
     int64_t hbm_budget_bytes; /* serving admission budget; 0 = 90% of free memory at create */
+    float w_bg;       /* 0: background weight in the normalisation, C = (N + w_bg bg) / (D + w_bg)
+                       * (Eq. 4's background term applied to Eq. 12); the background where
+                       * D + w_bg <= d_min */
+    int32_t reserved;
 } dgs_config;
+
+/* dgs_config.flags (the defaults are the paper's reading; each flag is an
+ * alternative the paper leaves open):
+ *   DGS_FLAG_ALPHA_SKIP    alpha < 1/255 contributes nothing (the 3DGS skip)
+ *   DGS_FLAG_TERM_EXCLUDE  a cell whose blending would take the cell
+ *                          transmittance below eps is not blended and ends the
+ *                          pixel (the 3DGS rule; by default that cell is still
+ *                          blended, Sec. V-B)
+ *   DGS_FLAG_AABB_SQUARE   the per-Gaussian box is the square of radius
+ *                          ceil(ksigma sqrt(lambda_max(Sigma'))) (the 3DGS box)
+ *                          instead of ksigma sqrt(Sigma'_xx) by ksigma sqrt(Sigma'_yy)
+ *   DGS_FLAG_NUMERATOR     the image is the numerator N of Eq. 12 (no
+ *                          normalisation; with one Gaussian per cell and v = 1
+ *                          this is alpha-blending, Eq. 2-3)
+ * ALPHA_SKIP, TERM_EXCLUDE, NUMERATOR and w_bg apply to the hybrid renderer
+ * (dgs_render, serving); AABB_SQUARE also to the comparators (it changes the
+ * per-Gaussian records they share).  The adjoint follows every flag. */
+#define DGS_FLAG_ALPHA_SKIP 1
+#define DGS_FLAG_TERM_EXCLUDE 2
+#define DGS_FLAG_AABB_SQUARE 4
+#define DGS_FLAG_NUMERATOR 8
 
 void dgs_config_default(dgs_config *cfg);
 

@@ -40,8 +40,14 @@ _FP = C.POINTER(C.c_float)
 
 class dgs_config(C.Structure):
     _fields_ = [("eps", C.c_float), ("alpha_max", C.c_float), ("d_min", C.c_float), ("bg", C.c_float * 3),
-                ("dilation", C.c_float), ("ksigma", C.c_float), ("device", C.c_int32), ("reserved", C.c_int32),
-                ("hbm_budget_bytes", C.c_int64)]
+                ("dilation", C.c_float), ("ksigma", C.c_float), ("device", C.c_int32), ("flags", C.c_int32),
+                ("hbm_budget_bytes", C.c_int64), ("w_bg", C.c_float), ("reserved", C.c_int32)]
+
+
+DGS_FLAG_ALPHA_SKIP = 1
+DGS_FLAG_TERM_EXCLUDE = 2
+DGS_FLAG_AABB_SQUARE = 4
+DGS_FLAG_NUMERATOR = 8
 
 
 class dgs_neural_desc(C.Structure):

@@ -190,8 +190,11 @@ extern "C" dgs_status dgs_create(const dgs_config *cfg, dgs_ctx **out) {
     *out = nullptr;
     dgs_config c;
     if (cfg) c = *cfg; else dgs_config_default(&c);
-    if (!(c.eps >= 0.f) || !(c.alpha_max > 0.f && c.alpha_max < 1.f) || !(c.ksigma > 0.f) || !(c.dilation >= 0.f))
-        return set_error(DGS_ERR_INVALID_ARG, "config out of range (need eps >= 0, 0 < alpha_max < 1, ksigma > 0)");
+    if (!(c.eps >= 0.f) || !(c.alpha_max > 0.f && c.alpha_max < 1.f) || !(c.ksigma > 0.f) || !(c.dilation >= 0.f) ||
+        !(c.w_bg >= 0.f) || (c.flags & ~(DGS_FLAG_ALPHA_SKIP | DGS_FLAG_TERM_EXCLUDE | DGS_FLAG_AABB_SQUARE |
+                                         DGS_FLAG_NUMERATOR)) != 0)
+        return set_error(DGS_ERR_INVALID_ARG,
+                         "config out of range (need eps >= 0, 0 < alpha_max < 1, ksigma > 0, w_bg >= 0, known flags)");
     int ndev = 0;
     CK(cudaGetDeviceCount(&ndev));
     if (c.device < 0 || c.device >= ndev) return set_error(DGS_ERR_INVALID_ARG, "no such CUDA device");
@@ -440,6 +443,8 @@ BlendParams blend_params(const dgs_config &c) {
     b.bg2 = c.bg[2];
     b.dilation = c.dilation;
     b.ksigma = c.ksigma;
+    b.w_bg = c.w_bg;
+    b.flags = c.flags;
     return b;
 }
 

@@ -146,7 +146,9 @@ constexpr int FWD_PPL = 4;
 constexpr int FWD_SUB = kTile / (2 * FWD_PPL);  // sub-tiles per tile
 constexpr int FWD_MINB = 28;
 
-template <int KT, int PPL>
+// VAR: the variant flags and background weight are live (dgs_config.flags,
+// w_bg); without it the kernels are the paper's reading with no check left.
+template <int KT, int PPL, bool VAR>
 __device__ __forceinline__ void blend_fwd_unit(int unit, const ViewDesc *__restrict__ views, int n_views,
                                                const uint2 *__restrict__ ranges, const uint32_t *__restrict__ cells,
                                                const float4 *__restrict__ rec, const BlendParams &bp,
@@ -216,6 +218,7 @@ __device__ __forceinline__ void blend_fwd_unit(int unit, const ViewDesc *__restr
             P[rr] = make_float2(1.0f, 1.0f);
         }
         const float2 v2 = make_float2(v, v);
+        const float amin = VAR && (bp.flags & DGS_FLAG_ALPHA_SKIP) ? 1.0f / 255.0f : 0.0f;
         for (; mask; mask &= mask - 1) {
             const int k = __ffs(mask) - 1;
             const float4 r0 = r[3 * k];
@@ -248,9 +251,10 @@ __device__ __forceinline__ void blend_fwd_unit(int unit, const ViewDesc *__restr
                 const float2 s1 = __ffma2_rn(make_float2(r1.y, r1.y), make_float2(dyq, dyq), pdx);
                 const float2 qd = __ffma2_rn(s1, s1, make_float2(s22, s22));
                 float2 al = __fmul2_rn(make_float2(r1.w, r1.w), make_float2(ex2_approx(-qd.x), ex2_approx(-qd.y)));
-                // a pixel the Gaussian does not reach takes alpha 0: every update below leaves it unchanged
-                al.x = h[2 * rr] ? fminf(al.x, bp.alpha_max) : 0.f;
-                al.y = h[2 * rr + 1] ? fminf(al.y, bp.alpha_max) : 0.f;
+                // a pixel the Gaussian does not reach (or, with the alpha skip, an
+                // alpha below 1/255) takes alpha 0: every update below leaves it unchanged
+                al.x = h[2 * rr] && (!VAR || al.x >= amin) ? fminf(al.x, bp.alpha_max) : 0.f;
+                al.y = h[2 * rr + 1] && (!VAR || al.y >= amin) ? fminf(al.y, bp.alpha_max) : 0.f;
                 A0[rr] = __ffma2_rn(al, make_float2(r2.x, r2.x), A0[rr]);
                 A1[rr] = __ffma2_rn(al, make_float2(r2.y, r2.y), A1[rr]);
                 A2[rr] = __ffma2_rn(al, make_float2(r2.z, r2.z), A2[rr]);
@@ -258,17 +262,23 @@ __device__ __forceinline__ void blend_fwd_unit(int unit, const ViewDesc *__restr
                 P[rr] = __ffma2_rn(make_float2(-P[rr].x, -P[rr].y), __fmul2_rn(v2, al), P[rr]);
             }
         }
+        const bool exclude = VAR && (bp.flags & DGS_FLAG_TERM_EXCLUDE) != 0;
 #pragma unroll
         for (int q = 0; q < PPL; ++q) {
             if (!done[q]) {
                 const int rr = q >> 1;
                 const bool hi = q & 1;
+                const float Tnext = T[q] * (hi ? P[rr].y : P[rr].x);
+                if (exclude && Tnext < bp.eps) {  // the 3DGS rule: this cell is not blended
+                    done[q] = true;
+                    continue;
+                }
                 const float w = v * T[q];
                 N0[q] = fmaf(w, hi ? A0[rr].y : A0[rr].x, N0[q]);
                 N1[q] = fmaf(w, hi ? A1[rr].y : A1[rr].x, N1[q]);
                 N2[q] = fmaf(w, hi ? A2[rr].y : A2[rr].x, N2[q]);
                 D[q] = fmaf(w, hi ? B[rr].y : B[rr].x, D[q]);
-                T[q] *= hi ? P[rr].y : P[rr].x;
+                T[q] = Tnext;
                 ++n[q];
             }
         }
@@ -284,10 +294,21 @@ __device__ __forceinline__ void blend_fwd_unit(int unit, const ViewDesc *__restr
     for (int q = 0; q < PPL; ++q) {
         if (!(xs[q & 1] < V.W && ys[q >> 1] < V.H)) continue;
         const long long pin = (long long)ys[q >> 1] * V.W + xs[q & 1];
-        const bool hit = D[q] > bp.d_min;
-        const float c0 = hit ? N0[q] / D[q] : bp.bg0;
-        const float c1 = hit ? N1[q] / D[q] : bp.bg1;
-        const float c2 = hit ? N2[q] / D[q] : bp.bg2;
+        float c0, c1, c2;
+        if (VAR && (bp.flags & DGS_FLAG_NUMERATOR)) {  // the numerator of Eq. 12
+            c0 = N0[q]; c1 = N1[q]; c2 = N2[q];
+        } else if (VAR) {  // Eq. 12, with a background weight (N + w_bg bg) / (D + w_bg)
+            const float Dp = D[q] + bp.w_bg;
+            const bool hit = Dp > bp.d_min;
+            c0 = hit ? (N0[q] + bp.w_bg * bp.bg0) / Dp : bp.bg0;
+            c1 = hit ? (N1[q] + bp.w_bg * bp.bg1) / Dp : bp.bg1;
+            c2 = hit ? (N2[q] + bp.w_bg * bp.bg2) / Dp : bp.bg2;
+        } else {  // Eq. 12
+            const bool hit = D[q] > bp.d_min;
+            c0 = hit ? N0[q] / D[q] : bp.bg0;
+            c1 = hit ? N1[q] / D[q] : bp.bg1;
+            c2 = hit ? N2[q] / D[q] : bp.bg2;
+        }
         img[pin] = c0;
         img[HW + pin] = c1;
         img[2 * HW + pin] = c2;
@@ -301,14 +322,14 @@ __device__ __forceinline__ void blend_fwd_unit(int unit, const ViewDesc *__restr
     }
 }
 
-template <int KT>
+template <int KT, bool VAR>
 __global__ void __launch_bounds__(WT, FWD_MINB) k_blend_fwd(const ViewDesc *__restrict__ views, int n_views,
                                                   const uint2 *__restrict__ ranges, const uint32_t *__restrict__ cells,
                                                   const float4 *__restrict__ rec, BlendParams bp,
                                                   float *__restrict__ out_rgb, float *__restrict__ out_rgb2,
                                                   float *__restrict__ out_D, int *__restrict__ out_nd) {
     __shared__ float4 s_rec[2][MAXPER];
-    blend_fwd_unit<KT, FWD_PPL>(blockIdx.x, views, n_views, ranges, cells, rec, bp, out_rgb, out_rgb2, out_D, out_nd,
+    blend_fwd_unit<KT, FWD_PPL, VAR>(blockIdx.x, views, n_views, ranges, cells, rec, bp, out_rgb, out_rgb2, out_D, out_nd,
                                 s_rec);
 }
 
@@ -317,7 +338,7 @@ __global__ void __launch_bounds__(WT, FWD_MINB) k_blend_fwd(const ViewDesc *__re
 // starts at 0) until the chain's total_tiles * FWD_SUB units are taken, so the
 // dense and the empty regions of the images balance dynamically.  One
 // atomic per sub-tile: their rate is bounded by the blend work between them.
-template <int KT>
+template <int KT, bool VAR>
 __global__ void __launch_bounds__(WT, FWD_MINB) k_blend_fwd_pull(const ViewDesc *__restrict__ views,
                                                        const uint2 *__restrict__ ranges,
                                                        const uint32_t *__restrict__ cells,
@@ -333,21 +354,26 @@ __global__ void __launch_bounds__(WT, FWD_MINB) k_blend_fwd_pull(const ViewDesc 
         if (threadIdx.x == 0) u = atomicAdd(work, 1u);
         u = __shfl_sync(0xffffffffu, u, 0);
         if (u >= units) break;
-        blend_fwd_unit<KT, FWD_PPL>((int)u, views, n_views, ranges, cells, rec, bp, out_rgb, nullptr, out_D, out_nd,
+        blend_fwd_unit<KT, FWD_PPL, VAR>((int)u, views, n_views, ranges, cells, rec, bp, out_rgb, nullptr, out_D, out_nd,
                                     s_rec);
         __syncwarp();
     }
 }
 
-// min(units, SMs x resident CTAs of k_blend_fwd_pull<KT>), queried once.
-template <int KT>
+// min(units, SMs x resident CTAs of k_blend_fwd_pull<KT, VAR>), queried once.
+// Do the blend kernels need their variant form (a flag or a background weight)?
+static bool blend_variants(const BlendParams &bp) {
+    return (bp.flags & (DGS_FLAG_ALPHA_SKIP | DGS_FLAG_TERM_EXCLUDE | DGS_FLAG_NUMERATOR)) != 0 || bp.w_bg != 0.f;
+}
+
+template <int KT, bool VAR>
 static unsigned pull_grid(int total_tiles) {
     static int per_grid = 0;
     if (!per_grid) {
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_blend_fwd_pull<KT>, WT, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_blend_fwd_pull<KT, VAR>, WT, 0);
         per_grid = std::max(1, sms * std::max(1, per_sm));
     }
     return (unsigned)std::min<long long>((long long)total_tiles * FWD_SUB, per_grid);
@@ -360,25 +386,41 @@ void launch_blend_fwd(const ViewDesc *views, int n_views, int total_tiles, const
     if (total_tiles == 0) return;
     if (dsz) {
         // exactly the resident warps
-#define DGS_PULL(KV)                                                                                            \
-        k_blend_fwd_pull<KV><<<pull_grid<KV>(total_tiles), WT, 0, st>>>(views, ranges, tile_cells, rec, bp, out_rgb, \
-                                                                       out_D, out_nd, dsz, work)
-        switch (K_all) {
-            case 8: DGS_PULL(8); break;
-            case 10: DGS_PULL(10); break;
-            default: DGS_PULL(0); break;
+#define DGS_PULL(KV, VV)                                                                                     \
+        k_blend_fwd_pull<KV, VV><<<pull_grid<KV, VV>(total_tiles), WT, 0, st>>>(views, ranges, tile_cells, rec, bp, \
+                                                                               out_rgb, out_D, out_nd, dsz, work)
+        if (blend_variants(bp)) {
+            switch (K_all) {
+                case 8: DGS_PULL(8, true); break;
+                case 10: DGS_PULL(10, true); break;
+                default: DGS_PULL(0, true); break;
+            }
+        } else {
+            switch (K_all) {
+                case 8: DGS_PULL(8, false); break;
+                case 10: DGS_PULL(10, false); break;
+                default: DGS_PULL(0, false); break;
+            }
         }
 #undef DGS_PULL
         return;
     }
     const unsigned grid = (unsigned)total_tiles * FWD_SUB;
-#define DGS_FWD(KV)                                                                                          \
-    k_blend_fwd<KV><<<grid, WT, 0, st>>>(views, n_views, ranges, tile_cells, rec, bp, out_rgb, out_rgb2, out_D, \
-                                         out_nd)
-    switch (K_all) {
-        case 8: DGS_FWD(8); break;
-        case 10: DGS_FWD(10); break;
-        default: DGS_FWD(0); break;
+#define DGS_FWD(KV, VV)                                                                                      \
+    k_blend_fwd<KV, VV><<<grid, WT, 0, st>>>(views, n_views, ranges, tile_cells, rec, bp, out_rgb, out_rgb2, out_D, \
+                                             out_nd)
+    if (blend_variants(bp)) {
+        switch (K_all) {
+            case 8: DGS_FWD(8, true); break;
+            case 10: DGS_FWD(10, true); break;
+            default: DGS_FWD(0, true); break;
+        }
+    } else {
+        switch (K_all) {
+            case 8: DGS_FWD(8, false); break;
+            case 10: DGS_FWD(10, false); break;
+            default: DGS_FWD(0, false); break;
+        }
     }
 #undef DGS_FWD
 }
@@ -565,7 +607,7 @@ constexpr int BWD_PPL = 4;
 constexpr int BWD_SUB = kTile / (2 * BWD_PPL);  // sub-tiles per tile
 constexpr int BWD_MINB = 24;  // resident one-warp CTAs per SM the register budget is set for
 
-template <int KT, int PPL>
+template <int KT, int PPL, bool VAR>
 __global__ void __launch_bounds__(WT, BWD_MINB) k_blend_bwd(const ViewDesc *__restrict__ views, int n_views,
                                                   const uint2 *__restrict__ ranges, const uint32_t *__restrict__ cells,
                                                   const float4 *__restrict__ rec, BlendParams bp,
@@ -600,25 +642,36 @@ __global__ void __launch_bounds__(WT, BWD_MINB) k_blend_bwd(const ViewDesc *__re
     const int K = KT > 0 ? KT : V.K;
     const int per = kRecF4 * K;
 
+    // Per pixel: dL/dN = e, dL/dD = eD, and S's start value, the sum of x_n
+    // over the processed cells: 0 for C = N / D (degree-0 homogeneity), else
+    // w_bg g.(C - bg) / (D + w_bg) with a background weight, g.C for the
+    // numerator output (dL/dN = g, dL/dD = 0).
     int nd[PPL];
-    float e0s[PPL], e1s[PPL], e2s[PPL], eDs[PPL];
+    float e0s[PPL], e1s[PPL], e2s[PPL], eDs[PPL], S0[PPL];
     int ndm = 0;
+    const bool numer = VAR && (bp.flags & DGS_FLAG_NUMERATOR) != 0;
 #pragma unroll
     for (int q = 0; q < PPL; ++q) {
         nd[q] = 0;
-        e0s[q] = e1s[q] = e2s[q] = eDs[q] = 0.f;
+        e0s[q] = e1s[q] = e2s[q] = eDs[q] = S0[q] = 0.f;
         if (xs[q & 1] < V.W && ys[q >> 1] < V.H) {
             const long long pin = (long long)ys[q >> 1] * V.W + xs[q & 1];
-            const float Dv = Dpix[V.pix_base + pin];
-            if (Dv > bp.d_min) {
+            const float Dp = VAR ? Dpix[V.pix_base + pin] + bp.w_bg : Dpix[V.pix_base + pin];
+            if (numer || Dp > bp.d_min) {
                 nd[q] = ndpix[V.pix_base + pin];
                 const float *gi = dL_drgb + 3 * V.pix_base;
                 const float *ci = rgb + 3 * V.pix_base;
                 const float g0 = gi[pin], g1 = gi[HW + pin], g2 = gi[2 * HW + pin];
                 const float c0 = ci[pin], c1 = ci[HW + pin], c2 = ci[2 * HW + pin];
-                const float iD = 1.0f / Dv;
-                e0s[q] = g0 * iD; e1s[q] = g1 * iD; e2s[q] = g2 * iD;
-                eDs[q] = -(g0 * c0 + g1 * c1 + g2 * c2) * iD;
+                if (numer) {
+                    e0s[q] = g0; e1s[q] = g1; e2s[q] = g2;
+                    S0[q] = g0 * c0 + g1 * c1 + g2 * c2;
+                } else {
+                    const float iD = 1.0f / Dp;
+                    e0s[q] = g0 * iD; e1s[q] = g1 * iD; e2s[q] = g2 * iD;
+                    eDs[q] = -(g0 * c0 + g1 * c1 + g2 * c2) * iD;
+                    if (VAR) S0[q] = bp.w_bg * (g0 * (c0 - bp.bg0) + g1 * (c1 - bp.bg1) + g2 * (c2 - bp.bg2)) * iD;
+                }
             }
         }
         ndm = max(ndm, nd[q]);
@@ -648,7 +701,7 @@ __global__ void __launch_bounds__(WT, BWD_MINB) k_blend_bwd(const ViewDesc *__re
 
     float2 T[NR], S[NR];
 #pragma unroll
-    for (int rr = 0; rr < NR; ++rr) { T[rr] = make_float2(1.0f, 1.0f); S[rr] = make_float2(0.f, 0.f); }
+    for (int rr = 0; rr < NR; ++rr) { T[rr] = make_float2(1.0f, 1.0f); S[rr] = make_float2(S0[2 * rr], S0[2 * rr + 1]); }
     float4 pre[3];
     if (rg.x < end) {
         stage_cell(s_rec[0], vrec, cells, rg.x, per, lane, pre);
@@ -671,6 +724,7 @@ __global__ void __launch_bounds__(WT, BWD_MINB) k_blend_bwd(const ViewDesc *__re
         // X_n = dN.A_n + dD B_n = sum_k alpha_k (dN.c_k + dD)
         float2 X[NR], P[NR];
         const float2 v2 = make_float2(v, v);
+        const float amin = VAR && (bp.flags & DGS_FLAG_ALPHA_SKIP) ? 1.0f / 255.0f : 0.0f;
         {
 #pragma unroll
             for (int rr = 0; rr < NR; ++rr) { X[rr] = make_float2(0.f, 0.f); P[rr] = make_float2(1.0f, 1.0f); }
@@ -710,11 +764,12 @@ __global__ void __launch_bounds__(WT, BWD_MINB) k_blend_bwd(const ViewDesc *__re
                     const float2 s1 = __ffma2_rn(make_float2(r1.y, r1.y), make_float2(dyq, dyq), pdx);
                     const float2 qd = __ffma2_rn(s1, s1, make_float2(s22, s22));
                     float2 Gv = make_float2(ex2_approx(-qd.x), ex2_approx(-qd.y));
-                    Gv.x = h[2 * rr] ? Gv.x : 0.f;       // not reached: G' = 0 leaves X and P as they are
-                    Gv.y = h[2 * rr + 1] ? Gv.y : 0.f;
+                    float2 rw = __fmul2_rn(make_float2(r1.w, r1.w), Gv);
+                    // not reached (or alpha skipped as in the forward): G' = 0 leaves X and P as they are
+                    if (!h[2 * rr] || (VAR && rw.x < amin)) Gv.x = rw.x = 0.f;
+                    if (!h[2 * rr + 1] || (VAR && rw.y < amin)) Gv.y = rw.y = 0.f;
                     s_G[2 * rr][i][lane] = Gv.x;
                     s_G[2 * rr + 1][i][lane] = Gv.y;
-                    const float2 rw = __fmul2_rn(make_float2(r1.w, r1.w), Gv);
                     const float2 al = make_float2(fminf(rw.x, bp.alpha_max), fminf(rw.y, bp.alpha_max));
                     float2 e0, e1, e2, eD;
                     efac(rr, e0, e1, e2, eD);
@@ -804,13 +859,21 @@ void launch_blend_bwd(const ViewDesc *views, int n_views, int total_tiles, int K
                       cudaStream_t st) {
     if (total_tiles == 0) return;
     const unsigned grid = (unsigned)total_tiles * BWD_SUB;
-#define DGS_BWD(KV)                                                                                             \
-    k_blend_bwd<KV, BWD_PPL><<<grid, WT, 0, st>>>(views, n_views, ranges, tile_cells, rec, bp, rgb, D, nd, dL_drgb, \
-                                                  g2d, g_cell_v)
-    switch (K_all) {
-        case 8: DGS_BWD(8); break;
-        case 10: DGS_BWD(10); break;
-        default: DGS_BWD(0); break;
+#define DGS_BWD(KV, VV)                                                                                          \
+    k_blend_bwd<KV, BWD_PPL, VV><<<grid, WT, 0, st>>>(views, n_views, ranges, tile_cells, rec, bp, rgb, D, nd,     \
+                                                      dL_drgb, g2d, g_cell_v)
+    if (blend_variants(bp)) {
+        switch (K_all) {
+            case 8: DGS_BWD(8, true); break;
+            case 10: DGS_BWD(10, true); break;
+            default: DGS_BWD(0, true); break;
+        }
+    } else {
+        switch (K_all) {
+            case 8: DGS_BWD(8, false); break;
+            case 10: DGS_BWD(10, false); break;
+            default: DGS_BWD(0, false); break;
+        }
     }
 #undef DGS_BWD
 }

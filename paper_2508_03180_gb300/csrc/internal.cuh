@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "dgs.h"
+
 namespace dgs {
 
 constexpr int kTile = 16;          // tile edge in pixels (Sec. IV-B tile-based paradigm)
@@ -66,6 +68,8 @@ struct ChainSizes {
 
 struct BlendParams {
     float eps, alpha_max, d_min, bg0, bg1, bg2, dilation, ksigma;
+    float w_bg;  // background weight in the hybrid's normalisation
+    int flags;   // DGS_FLAG_* variants of the readings
 };
 
 // ---------------------------------------------------------------- FP32 with one prescribed rounding order

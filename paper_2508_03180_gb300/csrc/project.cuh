@@ -121,8 +121,18 @@ __device__ __forceinline__ bool gauss_record(const ViewDesc &Vw, const GaussIn &
     }
     const float mx = fadd_s(fmul_s(Vw.fx, c.x), Vw.cx);
     const float my = fadd_s(fmul_s(Vw.fy, c.y), Vw.cy);
-    const float ex = fmul_s(bp.ksigma, fsqrt_s(c.sxx));
-    const float ey = fmul_s(bp.ksigma, fsqrt_s(c.syy));
+    float ex, ey;
+    if (bp.flags & DGS_FLAG_AABB_SQUARE) {
+        // the square of radius ceil(k sqrt(lambda_max(Sigma'))),
+        // lambda_max = (sxx + syy)/2 + sqrt(((sxx - syy)/2)^2 + sxy^2), fixed order
+        const float sxy = fadd_s(fadd_s(fmul_s(c.V[0], c.T[3]), fmul_s(c.V[1], c.T[4])), fmul_s(c.V[2], c.T[5]));
+        const float mid = fmul_s(0.5f, fadd_s(c.sxx, c.syy)), hd = fmul_s(0.5f, fadd_s(c.sxx, -c.syy));
+        const float lam = fadd_s(mid, fsqrt_s(fadd_s(fmul_s(hd, hd), fmul_s(sxy, sxy))));
+        ex = ey = ceilf(fmul_s(bp.ksigma, fsqrt_s(lam)));
+    } else {
+        ex = fmul_s(bp.ksigma, fsqrt_s(c.sxx));
+        ey = fmul_s(bp.ksigma, fsqrt_s(c.syy));
+    }
     // conic Q = Sigma'^-1 = L L^T, L = [[p, 0], [r, t]]:
     // p = sqrt(s_yy/det), r = -s_xy/sqrt(s_yy det), t = 1/sqrt(s_yy),
     // so q(d) = (p dx + r dy)^2 + (t dy)^2 is a sum of squares
