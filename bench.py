@@ -627,6 +627,8 @@ def main():
     line["fps"] = {"fwd_bwd": world * nv * args.steps / (ms / 1e3), "fwd": nv / (fwd_ms / 1e3) if fwd_ms > 0 else None}
     line["alu_probe"] = alu
     line["streaming"] = streaming_stages(prof, args.steps, nv, scene, stats, peaks)
+    line["forward_chain"] = forward_chain(line["streaming"], prof, args.steps, px_step, stats, scene, cnt, peaks,
+                                          alu["fp32_tflops"] if alu else None)
     # kernel launches per step: binning 11 + sort passes + projection + blend + backward 2 + loss 2
     line["gpu_launches"] = int(args.steps * launches_per_step(stats))
 
@@ -689,6 +691,29 @@ def streaming_stages(prof, steps, nv, scene, stats, peaks):
     tb = sum(v["bytes"] for v in out.values())
     tm = sum(v["ms"] for v in out.values())
     out["all"] = {"bytes": int(tb), "ms": tm, "gbs": tb / (tm / 1e3) / 1e9, "frac": tb / (tm / 1e3) / 1e9 / peaks["hbm_gbs"]}
+    return out
+
+
+def forward_chain(streaming, prof, steps, px, stats, scene, cnt, peaks, fp32_tflops):
+    """The forward chain (binning, projection, blend) against the HBM roofline:
+    its algorithmic bytes (the streaming stages' bytes, plus the blend's
+    record read, image and per-pixel state writes) over its device time, and
+    the fraction it could reach at best with the blend at the measured FP32
+    rate (its counted FLOPs) and every streaming stage at the copy bandwidth:
+    the blend's arithmetic, not memory, bounds the chain."""
+    fwd = ("cell_project", "depth_sort", "count_scan", "emit", "tile_sort", "tile_ranges", "project_fwd")
+    stream_bytes = sum(streaming[k]["bytes"] for k in fwd if k in streaming)
+    blend_bytes = int(stats.visible_cells) * scene.K * 48 + px * (12 + 8)
+    total = stream_bytes + blend_bytes
+    t = sum(prof[k][0] for k in fwd + ("blend_fwd",)) / steps / 1e3
+    hbm = peaks["hbm_gbs"] * 1e9
+    out = {"bytes": int(total), "ms": t * 1e3, "gbs": total / t / 1e9, "frac": total / t / hbm,
+           "blend_ms": prof["blend_fwd"][0] / steps}
+    if fp32_tflops:
+        t_blend = cnt["inbox_rendered"] * FLOP_FWD / (fp32_tflops * 1e12)
+        t_min = t_blend + stream_bytes / hbm + blend_bytes / hbm
+        out["frac_ceiling_at_alu_bound"] = total / t_min / hbm
+        out["blend_ms_at_fp32_peak"] = t_blend * 1e3
     return out
 
 
