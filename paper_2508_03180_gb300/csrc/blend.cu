@@ -10,12 +10,10 @@
 // (false-positive skip, Sec. VI-A).  Inside a cell nothing depends on the
 // order of k (Eq. 12's inner sums and product commute).
 //
-// GB300 mapping: one 256-thread CTA per 16x16 tile, one pixel per thread.
-// The 48-byte records of the Gaussians of a chunk of cells are fetched with
-// one 16-byte load per thread into registers while the previous chunk is
-// blended from shared memory (double buffer), so every record is read from
-// L2/HBM once per tile and then broadcast from shared memory to 256 pixels.
-// A block-wide count of finished pixels ends the tile early.
+// GB300 mapping: one one-warp CTA per 16x8 half of a 16x16 tile, four
+// pixels per lane in packed pairs (f32x2 arithmetic).  The 48-byte records of
+// a cell's Gaussians are copied into the warp's shared memory asynchronously
+// two cells ahead and broadcast from there to the warp's 128 pixels.
 #include <algorithm>
 
 #include "internal.cuh"
@@ -31,43 +29,6 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
-// One 16-byte piece of the records of chunk [start, start + CH) for thread tid.
-__device__ __forceinline__ float4 fetch_rec(const float4 *__restrict__ vrec, const uint32_t *__restrict__ cells,
-                                            uint32_t start, uint32_t end, int tid, int nload, int per, float4 keep) {
-    if (tid < nload) {
-        const int c = tid / per, j = tid - c * per;
-        const uint32_t e = start + c;
-        if (e < end) return __ldg(vrec + (long long)cells[e] * per + j);
-    }
-    return keep;
-}
-
-// Can Gaussian record piece r0 = (mu_x, mu_y, ext_x, ext_y) pass the per-pixel
-// AABB test at any pixel centre of the tile whose first pixel is (x0, y0)?
-// Exactly conservative: FP32 subtraction is monotone, so if the nearest pixel
-// centre of the tile already fails |p - mu| <= ext, every pixel does.
-__device__ __forceinline__ bool touches_tile(float4 r0, float x0, float y0) {
-    const float lx = x0 + 0.5f, hx = x0 + (float)kTile - 0.5f;
-    const float ly = y0 + 0.5f, hy = y0 + (float)kTile - 0.5f;
-    return !(lx - r0.x > r0.z || r0.x - hx > r0.z || ly - r0.y > r0.w || r0.y - hy > r0.w);
-}
-
-// Rows of the tile (0..15) that can hold a pixel passing the AABB test of
-// record piece r0, packed as yl | yh << 8 (a superset with a one-row margin
-// over FP32 rounding; 0x00FF = no row, when the record misses the tile).
-// Warp w blends tile rows 2w and 2w+1 and skips the record if both lie
-// outside [yl, yh]: a warp-uniform branch that changes no pixel's result.
-__device__ __forceinline__ int row_span(float4 r0, float x0, float y0) {
-    if (!touches_tile(r0, x0, y0)) return 0x00FF;
-    const int yl = (int)fmaxf(floorf(r0.y - r0.w - 0.5f - y0) - 1.0f, 0.0f);
-    const int yh = (int)fminf(ceilf(r0.y + r0.w - 0.5f - y0) + 1.0f, (float)(kTile - 1));
-    return yl | (yh << 8);
-}
-
-__device__ __forceinline__ bool rows_hit(int span, int warp) {
-    return !(2 * warp + 1 < (span & 0xFF) || 2 * warp > (span >> 8));
-}
-
 __device__ __forceinline__ int find_view(const ViewDesc *views, int n_views, int tile) {
     int lo = 0, hi = n_views;
     while (hi - lo > 1) {
@@ -77,50 +38,58 @@ __device__ __forceinline__ int find_view(const ViewDesc *views, int n_views, int
     return lo;
 }
 
-// Work unit: one warp per 16x4-pixel sub-tile (a quarter of a 16x16 tile,
-// a one-warp CTA), each lane blending the two vertically adjacent pixels
-// (x, 2r) and (x, 2r+1).  Warps never wait for one another: each stages the
-// 48-byte records of one cell at a time in its own shared memory (double
-// buffered through registers), takes a ballot of the cell's Gaussians whose
-// AABB reaches its sub-tile and loops over those only, and stops as soon as
-// its own 64 pixels are done.  KT > 0 fixes K at compile time.
-constexpr int WT = 32;       // threads per work unit
-constexpr int WSUB = 4;      // sub-tiles per tile (rows 4s .. 4s+3)
-constexpr int MAXPER = kRecF4 * kMaxK;  // float4s of one cell's records
+// Work unit: one warp (a one-warp CTA) per 16 x (2 PPL)-pixel sub-tile of a
+// tile.  Warps never wait for one another: each stages the records of its
+// tile's cells in its own shared memory, takes a ballot of a cell's Gaussians
+// whose AABB reaches its sub-tile and loops over those only, and stops as soon
+// as its own pixels are done.  KT > 0 fixes K at compile time.
+constexpr int WT = 32;  // threads per work unit
 
-// Can record piece r0 pass the AABB test at some pixel centre of the 16-wide,
-// 4-high block whose first pixel is (x0, y0)?  Exactly conservative (FP32
-// subtraction is monotone, so testing the nearest centres suffices).
-__device__ __forceinline__ bool touches_block(float4 r0, float x0, float y0) {
-    const float lx = x0 + 0.5f, hx = x0 + (float)kTile - 0.5f;
-    const float ly = y0 + 0.5f, hy = y0 + (float)WSUB - 0.5f;
-    return !(lx - r0.x > r0.z || r0.x - hx > r0.z || ly - r0.y > r0.w || r0.y - hy > r0.w);
+// Records reach shared memory by asynchronous copies (cp.async, 16 bytes a
+// lane, one to three per lane for a cell), three cells deep: the copy of
+// entry e + 2 is issued while entry e is blended, so neither registers nor a
+// wait on the load's latency are spent on staging.  Every iteration commits one
+// copy group (empty past the list's end) and waits for all but the two
+// newest, which are the next two entries'.
+constexpr int NSTAGE = 3;
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// Stage the records of tile-list entry e (per float4s) into dst; one to three
-// 16-byte loads per lane.
-__device__ __forceinline__ void stage_cell(float4 *dst, const float4 *__restrict__ vrec,
-                                           const uint32_t *__restrict__ cells, uint32_t e, int per, int lane,
-                                           float4 pre[3]) {
-    const float4 *src = vrec + (long long)__ldg(cells + e) * per;
+// Issue the copy of the records of cell `id` (per float4s) into dst.
+__device__ __forceinline__ void issue_cell(float4 *dst, const float4 *__restrict__ vrec, uint32_t id, int per,
+                                           int lane) {
+    const float4 *src = vrec + (long long)id * per;
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
         const int i = lane + 32 * q;
-        if (i < per) pre[q] = __ldg(src + i);
+        if (i < per) cp_async16(dst + i, src + i);
     }
-    (void)dst;
 }
 
-__device__ __forceinline__ void stash_cell(float4 *dst, int per, int lane, const float4 pre[3]) {
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-        const int i = lane + 32 * q;
-        if (i < per) dst[i] = pre[q];
+// Cell ids of a tile list, read 32 at a time (lane j holds entry base + j)
+// and handed out by a shuffle; entries must be asked for in increasing order
+// from `first`, one at a time.
+struct CellFeed {
+    const uint32_t *__restrict__ cells;
+    uint32_t first, end, chunk;
+    __device__ __forceinline__ uint32_t id(uint32_t e, int lane) {
+        const int j = (int)((e - first) & 31u);
+        if (j == 0) chunk = e + lane < end ? __ldg(cells + e + lane) : 0u;
+        return __shfl_sync(0xffffffffu, chunk, j);
     }
-}
+};
 
 // Can record piece r0 pass the AABB test at some pixel centre of the 16-wide,
-// `rows`-high block whose first pixel is (x0, y0)?  (As touches_block.)
+// `rows`-high block whose first pixel is (x0, y0)?  Exactly conservative (FP32
+// subtraction is monotone, so testing the nearest pixel centres suffices).
 __device__ __forceinline__ bool touches_rows(float4 r0, float x0, float y0, float rows) {
     const float lx = x0 + 0.5f, hx = x0 + (float)kTile - 0.5f;
     const float ly = y0 + 0.5f, hy = y0 + rows - 0.5f;
@@ -154,7 +123,7 @@ __device__ __forceinline__ void blend_fwd_unit(int unit, const ViewDesc *__restr
                                                const float4 *__restrict__ rec, const BlendParams &bp,
                                                float *__restrict__ out_rgb, float *__restrict__ out_rgb2,
                                                float *__restrict__ out_D, int *__restrict__ out_nd,
-                                               float4 (*s_rec)[MAXPER]) {
+                                               float4 (*s_rec)[kRecF4 * (KT > 0 ? KT : kMaxK)]) {
     constexpr int ROWS = 2 * PPL, NSUB = kTile / ROWS;
     const int lane = threadIdx.x;
     const int tile = unit / NSUB, sub = unit % NSUB;
@@ -189,12 +158,12 @@ __device__ __forceinline__ void blend_fwd_unit(int unit, const ViewDesc *__restr
         T[q] = 1.0f; N0[q] = N1[q] = N2[q] = D[q] = 0.f; n[q] = 0;
         done[q] = !(xs[q & 1] < V.W && ys[q >> 1] < V.H);
     }
-    float4 pre[3];
-    if (rg.x < rg.y) {
-        stage_cell(s_rec[0], vrec, cells, rg.x, per, lane, pre);
-        stash_cell(s_rec[0], per, lane, pre);
+    CellFeed feed{cells, rg.x, rg.y, 0u};
+#pragma unroll
+    for (int b = 0; b < NSTAGE - 1; ++b) {
+        if (rg.x + b < rg.y) issue_cell(s_rec[b], vrec, feed.id(rg.x + b, lane), per, lane);
+        cp_async_commit();
     }
-    __syncwarp();
     int buf = 0;
     for (uint32_t e = rg.x; e < rg.y; ++e) {
         // before cell n a pixel stops if T_n < eps (Sec. V-B)
@@ -205,7 +174,11 @@ __device__ __forceinline__ void blend_fwd_unit(int unit, const ViewDesc *__restr
             all = all && done[q];
         }
         if (__all_sync(0xffffffffu, all)) break;
-        if (e + 1 < rg.y) stage_cell(s_rec[buf ^ 1], vrec, cells, e + 1, per, lane, pre);
+        const int fill = buf == 0 ? NSTAGE - 1 : buf - 1;  // the buffer of entry e - 1, read by now
+        if (e + NSTAGE - 1 < rg.y) issue_cell(s_rec[fill], vrec, feed.id(e + NSTAGE - 1, lane), per, lane);
+        cp_async_commit();
+        cp_async_wait<NSTAGE - 1>();
+        __syncwarp();
         const float4 *r = s_rec[buf];
         const float v = r[2].w;
         unsigned mask = __ballot_sync(0xffffffffu, lane < K && touches_rows(r[kRecF4 * lane], bx0, by0, (float)ROWS));
@@ -282,11 +255,11 @@ __device__ __forceinline__ void blend_fwd_unit(int unit, const ViewDesc *__restr
                 ++n[q];
             }
         }
-        __syncwarp();
-        if (e + 1 < rg.y) stash_cell(s_rec[buf ^ 1], per, lane, pre);
-        __syncwarp();
-        buf ^= 1;
+        __syncwarp();  // every lane is done with s_rec[buf] before it is refilled
+        buf = buf == NSTAGE - 1 ? 0 : buf + 1;
     }
+    cp_async_wait<0>();  // copies of entries past an early stop land before the buffers are reused
+    __syncwarp();
     const long long HW = (long long)V.W * V.H;
     float *img = V.out ? V.out : out_rgb + 3 * V.pix_base;
     float *im2 = out_rgb2 ? out_rgb2 + 3 * V.pix_base : nullptr;
@@ -328,7 +301,7 @@ __global__ void __launch_bounds__(WT, FWD_MINB) k_blend_fwd(const ViewDesc *__re
                                                   const float4 *__restrict__ rec, BlendParams bp,
                                                   float *__restrict__ out_rgb, float *__restrict__ out_rgb2,
                                                   float *__restrict__ out_D, int *__restrict__ out_nd) {
-    __shared__ float4 s_rec[2][MAXPER];
+    __shared__ float4 s_rec[NSTAGE][kRecF4 * (KT > 0 ? KT : kMaxK)];
     blend_fwd_unit<KT, FWD_PPL, VAR>(blockIdx.x, views, n_views, ranges, cells, rec, bp, out_rgb, out_rgb2, out_D, out_nd,
                                 s_rec);
 }
@@ -346,7 +319,7 @@ __global__ void __launch_bounds__(WT, FWD_MINB) k_blend_fwd_pull(const ViewDesc 
                                                        float *__restrict__ out_rgb, float *__restrict__ out_D,
                                                        int *__restrict__ out_nd, const ChainSizes *__restrict__ dsz,
                                                        uint32_t *__restrict__ work) {
-    __shared__ float4 s_rec[2][MAXPER];
+    __shared__ float4 s_rec[NSTAGE][kRecF4 * (KT > 0 ? KT : kMaxK)];
     const int n_views = dsz->n_views;
     const uint32_t units = (uint32_t)dsz->total_tiles * FWD_SUB;
     for (;;) {
@@ -487,17 +460,17 @@ void launch_count_pairs(const ViewDesc *views, int n_views, int total_tiles, con
 //     dL/dv_n   = T_n (dN.A_n + dD B_n) - S_n sum_k alpha_k / (1 - v alpha_k)
 // then alpha = sigma G' (unless clamped) and G' = exp(-q/2).
 //
-// Same work unit as the forward (one warp per 16x4 sub-tile, two pixels per
-// lane, no inter-warp waits).  Per cell, the warp replays its pixels keeping
-// G' of the Gaussians that reach the sub-tile in warp-private shared memory
-// (registers capped at 64 so 32 warps fit per SM), updates S and T,
+// Same work unit as the forward (one warp per 16x8 sub-tile, four pixels per
+// lane).  Per cell, the warp replays its pixels keeping G' of the Gaussians
+// that reach the sub-tile in warp-private shared memory, updates S and T,
 // then for each such Gaussian sums its pixels' nine screen-space gradient
 // terms across the warp with a transposed shuffle tree (each step halves the
 // values a lane carries) and adds the totals to global memory (one atomic
 // add per value per sub-tile).
 
-// Sum v[0..15] over the warp.  On return lane L holds the total of value
-// 8 b1 + 4 b2 + 2 b3 + b4 (b_i = bit i of L); lanes with b0 = 1 duplicate it.
+// Sum v[0..7] over the warp.  On return lane L holds the total of value
+// 4 b2 + 2 b3 + b4 (b_i = bit i of L; transposed_owner8); the four lanes that
+// differ only in b0 and b1 hold the same total.
 // Transposed warp reduction of eight per-lane values: three halving steps
 // (offsets 16, 8, 4) in which each lane keeps half of its slots and receives
 // its partner's other half, then two butterfly steps (offsets 2, 1).  Every
@@ -615,8 +588,8 @@ __global__ void __launch_bounds__(WT, BWD_MINB) k_blend_bwd(const ViewDesc *__re
                                                   const int *__restrict__ ndpix, const float *__restrict__ dL_drgb,
                                                   float *__restrict__ g2d, float *__restrict__ g_cell_v) {
     constexpr int ROWS = 2 * PPL, NSUB = kTile / ROWS;
-    __shared__ float4 s_rec[2][MAXPER];
     constexpr int KRS = KT > 0 ? KT : kMaxK;
+    __shared__ float4 s_rec[NSTAGE][kRecF4 * KRS];
     __shared__ float s_G[PPL][KRS][WT];
     const int lane = threadIdx.x;
     const int tile = blockIdx.x / NSUB, sub = blockIdx.x % NSUB;
@@ -702,15 +675,19 @@ __global__ void __launch_bounds__(WT, BWD_MINB) k_blend_bwd(const ViewDesc *__re
     float2 T[NR], S[NR];
 #pragma unroll
     for (int rr = 0; rr < NR; ++rr) { T[rr] = make_float2(1.0f, 1.0f); S[rr] = make_float2(S0[2 * rr], S0[2 * rr + 1]); }
-    float4 pre[3];
-    if (rg.x < end) {
-        stage_cell(s_rec[0], vrec, cells, rg.x, per, lane, pre);
-        stash_cell(s_rec[0], per, lane, pre);
+    CellFeed feed{cells, rg.x, end, 0u};
+#pragma unroll
+    for (int b = 0; b < NSTAGE - 1; ++b) {
+        if (rg.x + b < end) issue_cell(s_rec[b], vrec, feed.id(rg.x + b, lane), per, lane);
+        cp_async_commit();
     }
-    __syncwarp();
     int buf = 0;
     for (uint32_t e = rg.x; e < end; ++e) {
-        if (e + 1 < end) stage_cell(s_rec[buf ^ 1], vrec, cells, e + 1, per, lane, pre);
+        const int fill = buf == 0 ? NSTAGE - 1 : buf - 1;  // the buffer of entry e - 1, read by now
+        if (e + NSTAGE - 1 < end) issue_cell(s_rec[fill], vrec, feed.id(e + NSTAGE - 1, lane), per, lane);
+        cp_async_commit();
+        cp_async_wait<NSTAGE - 1>();
+        __syncwarp();
         const int n = (int)(e - rg.x);
         bool act[PPL];
 #pragma unroll
@@ -845,11 +822,10 @@ __global__ void __launch_bounds__(WT, BWD_MINB) k_blend_bwd(const ViewDesc *__re
             dv = warp_sum(dv + (dv2.x + dv2.y));
             if (lane == 0 && dv != 0.f) atomicAdd(g_cell_v + V.cell_base + cellid, dv);
         }
-        __syncwarp();
-        if (e + 1 < end) stash_cell(s_rec[buf ^ 1], per, lane, pre);
-        __syncwarp();
-        buf ^= 1;
+        __syncwarp();  // every lane is done with s_rec[buf] and s_G before they are refilled
+        buf = buf == NSTAGE - 1 ? 0 : buf + 1;
     }
+    cp_async_wait<0>();
 }
 
 // K_all: K of the chain's scene (compile-time loop for common values)
