@@ -50,6 +50,13 @@ enum {
     DGS_ERR_CAPACITY = -7     /* a size exceeds a fixed maximum of the call */
 };
 
+/* Where an argument array lives.  DGS_HOST arrays may be pageable or
+ * page-locked (cudaHostAlloc / cudaMallocHost / cudaHostRegister).
+ * Page-locked host arrays are read or written by the library's kernels
+ * directly over the host link (no device staging copy; the transfer runs
+ * while the kernel computes); pageable ones are staged through device
+ * memory.  Either way a call that takes a DGS_HOST array returns only after
+ * the transfer is complete, and the array is then the caller's again. */
 enum { DGS_HOST = 0, DGS_DEVICE = 1 };
 
 typedef struct dgs_ctx dgs_ctx;
@@ -164,7 +171,7 @@ typedef struct {
 dgs_status dgs_scene_upload(dgs_ctx *ctx, const dgs_scene_desc *desc, uint32_t *scene_id);
 /* Overwrite the Gaussian parameters (and v, or its SH coefficients) of an
  * existing scene in place, same N, K and degrees (a training step's update).  Asynchronous on stream
- * for device inputs. */
+ * for device inputs; host inputs synchronise the stream before return. */
 dgs_status dgs_scene_update(dgs_ctx *ctx, uint32_t scene_id, const dgs_scene_desc *desc, dgs_stream stream);
 dgs_status dgs_scene_release(dgs_ctx *ctx, uint32_t scene_id);
 
@@ -232,6 +239,9 @@ typedef struct {
     float *g_mlp, *g_feat, *g_offset;
 } dgs_grads;
 
+/* Asynchronous on stream when dL_drgb and the outputs are device memory;
+ * with host dL_drgb or host outputs (dgs_grads.location) the call
+ * synchronises the stream before return. */
 dgs_status dgs_render_backward(dgs_ctx *ctx, dgs_fwd_state *state, const float *dL_drgb, int32_t location,
                                const dgs_grads *out, dgs_stream stream);
 dgs_status dgs_state_release(dgs_ctx *ctx, dgs_fwd_state *state);

@@ -233,18 +233,38 @@ extern "C" const char *dgs_last_error(dgs_ctx *) { return g_last_error.c_str(); 
 
 // ------------------------------------------------------------------ scenes
 
+// Device address of host memory the GPU reaches directly (page-locked by
+// cudaHostAlloc / cudaMallocHost or registered with cudaHostRegister, hence
+// mapped into the device's address space), else nullptr (pageable memory).
+// Kernels read and write such memory over the host link themselves, so a
+// transfer overlaps the kernel's own work and needs no device staging copy.
+static const void *mapped_host(const void *h) {
+    if (!h) return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 // One parameter array (rows x cols, row-major, in `location` memory) into
-// its structure-of-arrays planes.  Host arrays go through `stage` (device,
-// rows x cols floats); the caller synchronises before the host memory or
-// the staging is reused.
+// its structure-of-arrays planes.  Mapped host arrays are read by the
+// transposing kernel over the host link; other host arrays go through
+// `stage` (device, rows x cols floats).  The caller synchronises before the
+// host memory or the staging is reused.
 static dgs_status upload_param(const float *src, int location, int64_t rows, int cols, float *dst_planes,
                                int64_t plane_stride, float *stage, cudaStream_t st) {
     const size_t bytes = sizeof(float) * (size_t)rows * cols;
     if (bytes == 0) return DGS_OK;
     const float *dsrc = src;
     if (location == DGS_HOST) {
-        CK(cudaMemcpyAsync(stage, src, bytes, cudaMemcpyHostToDevice, st));
-        dsrc = stage;
+        if (const void *m = mapped_host(src)) {
+            dsrc = (const float *)m;
+        } else {
+            CK(cudaMemcpyAsync(stage, src, bytes, cudaMemcpyHostToDevice, st));
+            dsrc = stage;
+        }
     }
     launch_aos_to_soa(dsrc, rows, cols, dst_planes, plane_stride, st);
     CK(cudaGetLastError());
@@ -282,22 +302,26 @@ static dgs_status fill_scene(dgs_ctx *ctx, Scene &sc, const dgs_scene_desc *d, c
         parts.push_back({d->g_logit, G, 1, gs + 10 * G, G});
         parts.push_back({d->g_sh, G, 3 * sc.C, sh, G});
     }
-    // host inputs: every array gets its own staging region, one synchronisation at the end
+    // host inputs that are not mapped: every such array gets its own staging
+    // region; one synchronisation at the end
     float *stage = nullptr;
     if (d->location == DGS_HOST) {
         int64_t total = 0;
         for (auto &p : parts)
-            if (p.src) total += p.rows * p.cols;
-        dgs_status s = ctx->aux.ensure(sizeof(float) * std::max<int64_t>(1, total));
-        if (s) return s;
-        stage = (float *)ctx->aux.p;
+            if (p.src && !mapped_host(p.src)) total += p.rows * p.cols;
+        if (total) {
+            dgs_status s = ctx->aux.ensure(sizeof(float) * total);
+            if (s) return s;
+            stage = (float *)ctx->aux.p;
+        }
     }
     if (!d->cell_v && cells_too) launch_fill_f32(cell + 10 * N, N, 1.0f, st);
     for (auto &p : parts) {
         if (!p.src) continue;
+        const bool staged = d->location == DGS_HOST && !mapped_host(p.src);
         dgs_status s = upload_param(p.src, d->location, p.rows, p.cols, p.dst, p.stride, stage, st);
         if (s) return s;
-        if (stage) stage += p.rows * p.cols;
+        if (staged) stage += p.rows * p.cols;
     }
     CK(cudaGetLastError());
     if (d->location == DGS_HOST) CK(cudaStreamSynchronize(st));  // host arrays and staging free again
@@ -720,35 +744,44 @@ extern "C" dgs_status dgs_render_backward(dgs_ctx *ctx, dgs_fwd_state *state, co
     if (out->g_cell_v_sh && sc.vdeg < 0)
         return set_error(DGS_ERR_INVALID_ARG, "g_cell_v_sh given for a scene without view-dependent v");
     dgs_status s;
-    // staging: dL/drgb (3 px), then the gradient outputs
+    // Host memory: mapped arrays are read (dL/drgb, by the blend adjoint) or
+    // written (the explicit Gaussians' gradients, by the projection adjoint)
+    // by the kernels over the host link; the others are staged in device
+    // memory: dL/drgb (3 px), then the gradient outputs, copied at the end.
+    const bool hin = location == DGS_HOST, hout = out->location == DGS_HOST;
+    const float *dl_mapped = hin ? (const float *)mapped_host(dL_drgb) : nullptr;
+    struct Out { float *user; long long n; bool direct; float *dev; };
     const long long P = neural ? neural_weights(sc) : 0, NF = neural ? N * sc.F : 0, GO = neural ? 3 * G : 0;
-    const long long n_out =
-        3 * G + 3 * G + 3 * G + 4 * G + G + 3LL * C * G + N + (long long)Cv * N + P + NF + GO;
-    const long long n_stage = (location == DGS_HOST ? 3 * px : 0) + (out->location == DGS_HOST ? n_out : 0) + 1;
+    Out o[] = {{out->g_mean, 3 * G, true, nullptr},     {out->g_scale, 3 * G, true, nullptr},
+               {out->g_log_scale, 3 * G, true, nullptr}, {out->g_quat, 4 * G, true, nullptr},
+               {out->g_logit, G, true, nullptr},         {out->g_sh, 3LL * C * G, true, nullptr},
+               {out->g_cell_v, N, false, nullptr},       {out->g_cell_v_sh, (long long)Cv * N, false, nullptr},
+               {out->g_mlp, P, false, nullptr},          {out->g_feat, NF, false, nullptr},
+               {out->g_offset, GO, false, nullptr}};
+    long long n_stage = (hin && !dl_mapped ? 3 * px : 0) + 1;
+    for (auto &q : o) {
+        if (!q.user) continue;
+        if (!hout) { q.dev = q.user; continue; }
+        if (q.direct) q.dev = (float *)mapped_host(q.user);
+        if (!q.dev) { q.direct = false; n_stage += q.n; }
+    }
     if ((s = ws.gstage.ensure(sizeof(float) * n_stage))) return s;
     float *stage = (float *)ws.gstage.p;
     const float *dl = dL_drgb;
-    if (location == DGS_HOST) {
-        CK(cudaMemcpyAsync(stage, dL_drgb, 12 * px, cudaMemcpyHostToDevice, st));
-        dl = stage;
-        stage += 3 * px;
+    if (hin) {
+        if (dl_mapped) {
+            dl = dl_mapped;
+        } else {
+            CK(cudaMemcpyAsync(stage, dL_drgb, 12 * px, cudaMemcpyHostToDevice, st));
+            dl = stage;
+            stage += 3 * px;
+        }
     }
-    float *o_mean = out->g_mean, *o_s = out->g_scale, *o_ls = out->g_log_scale, *o_q = out->g_quat,
-          *o_lg = out->g_logit, *o_sh = out->g_sh, *o_v = out->g_cell_v, *o_vsh = out->g_cell_v_sh,
-          *o_mlp = out->g_mlp, *o_f = out->g_feat, *o_off = out->g_offset;
-    if (out->location == DGS_HOST) {
-        o_mean = out->g_mean ? stage : nullptr; stage += 3 * G;
-        o_s = out->g_scale ? stage : nullptr; stage += 3 * G;
-        o_ls = out->g_log_scale ? stage : nullptr; stage += 3 * G;
-        o_q = out->g_quat ? stage : nullptr; stage += 4 * G;
-        o_lg = out->g_logit ? stage : nullptr; stage += G;
-        o_sh = out->g_sh ? stage : nullptr; stage += 3LL * C * G;
-        o_v = out->g_cell_v ? stage : nullptr; stage += N;
-        o_vsh = out->g_cell_v_sh ? stage : nullptr; stage += (long long)Cv * N;
-        o_mlp = out->g_mlp ? stage : nullptr; stage += P;
-        o_f = out->g_feat ? stage : nullptr; stage += NF;
-        o_off = out->g_offset ? stage : nullptr; stage += GO;
-    }
+    for (auto &q : o)
+        if (q.user && !q.dev) { q.dev = stage; stage += q.n; }
+    float *o_mean = o[0].dev, *o_s = o[1].dev, *o_ls = o[2].dev, *o_q = o[3].dev, *o_lg = o[4].dev,
+          *o_sh = o[5].dev, *o_v = o[6].dev, *o_vsh = o[7].dev, *o_mlp = o[8].dev, *o_f = o[9].dev,
+          *o_off = o[10].dev;
     // dL/dv per (view, cell) entry, chained to the outputs after the blend adjoint
     float *gv = nullptr;
     if (o_v || o_vsh) {
@@ -793,17 +826,11 @@ extern "C" dgs_status dgs_render_backward(dgs_ctx *ctx, dgs_fwd_state *state, co
     }
     CK(cudaGetLastError());
     ws.bwd_done = true;
-    if (out->location == DGS_HOST) {
-        struct { float *h, *d; long long n; } cp[] = {{out->g_mean, o_mean, 3 * G}, {out->g_scale, o_s, 3 * G},
-                                                      {out->g_log_scale, o_ls, 3 * G},
-                                                      {out->g_quat, o_q, 4 * G}, {out->g_logit, o_lg, G},
-                                                      {out->g_sh, o_sh, 3LL * C * G}, {out->g_cell_v, o_v, N},
-                                                      {out->g_cell_v_sh, o_vsh, (long long)Cv * N},
-                                                      {out->g_mlp, o_mlp, P}, {out->g_feat, o_f, NF},
-                                                      {out->g_offset, o_off, GO}};
-        for (auto &c : cp)
-            if (c.h && c.n) CK(cudaMemcpyAsync(c.h, c.d, sizeof(float) * c.n, cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
+    if (hin || hout) {
+        for (auto &q : o)
+            if (hout && q.user && q.n && !q.direct)
+                CK(cudaMemcpyAsync(q.user, q.dev, sizeof(float) * q.n, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));  // host arrays complete (and free again) on return
     }
     CK(cudaEventRecord(ws.done, st));
     return DGS_OK;
