@@ -590,7 +590,8 @@ __global__ void __launch_bounds__(WT, BWD_MINB) k_blend_bwd(const ViewDesc *__re
     constexpr int ROWS = 2 * PPL, NSUB = kTile / ROWS;
     constexpr int KRS = KT > 0 ? KT : kMaxK;
     __shared__ float4 s_rec[NSTAGE][kRecF4 * KRS];
-    __shared__ float s_G[PPL][KRS][WT];
+    static_assert(PPL == 4, "G' of a lane's four pixels is kept as one float4");
+    __shared__ float4 s_G[KRS][WT];  // G' of hit i at the lane's pixels q = 0..3
     const int lane = threadIdx.x;
     const int tile = blockIdx.x / NSUB, sub = blockIdx.x % NSUB;
     const int vi = find_view(views, n_views, tile);
@@ -709,8 +710,6 @@ __global__ void __launch_bounds__(WT, BWD_MINB) k_blend_bwd(const ViewDesc *__re
             for (int i = 0; i < nhit; ++i) {
                 const int k = __ffs(mask) - 1;
                 mask &= mask - 1;
-#pragma unroll
-                for (int q = 0; q < PPL; ++q) s_G[q][i][lane] = 0.f;
                 const float4 r0 = r[3 * k];
                 float dx[2], dy[NR];
                 bool hx[2], hy[NR];
@@ -730,10 +729,14 @@ __global__ void __launch_bounds__(WT, BWD_MINB) k_blend_bwd(const ViewDesc *__re
                     h[q] = act[q] && hx[q & 1] && hy[q >> 1];
                     any = any || h[q];
                 }
-                if (!any) continue;
+                if (!any) {
+                    s_G[i][lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    continue;
+                }
                 const float4 r1 = r[3 * k + 1];
                 const float4 r2 = r[3 * k + 2];
                 const float2 pdx = __fmul2_rn(make_float2(r1.x, r1.x), make_float2(dx[0], dx[1]));
+                float2 gq[NR];
 #pragma unroll
                 for (int rr = 0; rr < NR; ++rr) {
                     const float dyq = dy[rr];
@@ -745,8 +748,7 @@ __global__ void __launch_bounds__(WT, BWD_MINB) k_blend_bwd(const ViewDesc *__re
                     // not reached (or alpha skipped as in the forward): G' = 0 leaves X and P as they are
                     if (!h[2 * rr] || (VAR && rw.x < amin)) Gv.x = rw.x = 0.f;
                     if (!h[2 * rr + 1] || (VAR && rw.y < amin)) Gv.y = rw.y = 0.f;
-                    s_G[2 * rr][i][lane] = Gv.x;
-                    s_G[2 * rr + 1][i][lane] = Gv.y;
+                    gq[rr] = Gv;
                     const float2 al = make_float2(fminf(rw.x, bp.alpha_max), fminf(rw.y, bp.alpha_max));
                     float2 e0, e1, e2, eD;
                     efac(rr, e0, e1, e2, eD);
@@ -756,6 +758,7 @@ __global__ void __launch_bounds__(WT, BWD_MINB) k_blend_bwd(const ViewDesc *__re
                     X[rr] = __ffma2_rn(al, inner, X[rr]);
                     P[rr] = __ffma2_rn(make_float2(-P[rr].x, -P[rr].y), __fmul2_rn(v2, al), P[rr]);
                 }
+                s_G[i][lane] = make_float4(gq[0].x, gq[0].y, gq[1].x, gq[1].y);
             }
         }
         // per-pixel transmittance bookkeeping (S_n includes x_n); the cell
@@ -785,13 +788,9 @@ __global__ void __launch_bounds__(WT, BWD_MINB) k_blend_bwd(const ViewDesc *__re
         unsigned m2 = mask0;
 #pragma unroll 1
         for (int i = 0; m2; ++i, m2 &= m2 - 1) {
-            float2 gv[NR];
-            bool any = false;
-#pragma unroll
-            for (int rr = 0; rr < NR; ++rr) {
-                gv[rr] = make_float2(s_G[2 * rr][i][lane], s_G[2 * rr + 1][i][lane]);
-                any = any || gv[rr].x > 0.f || gv[rr].y > 0.f;
-            }
+            const float4 g4 = s_G[i][lane];
+            const float2 gv[NR] = {make_float2(g4.x, g4.y), make_float2(g4.z, g4.w)};
+            const bool any = g4.x > 0.f || g4.y > 0.f || g4.z > 0.f || g4.w > 0.f;
             if (!__any_sync(0xffffffffu, any)) continue;
             const int k = __ffs(m2) - 1;
             const float4 r0 = r[3 * k], r1 = r[3 * k + 1], r2 = r[3 * k + 2];
