@@ -667,6 +667,8 @@ __global__ void __launch_bounds__(WT, BWD_MINB) k_blend_bwd(const ViewDesc *__re
         e0 = e0r[rr]; e1 = e1r[rr];
         e2 = make_float2(b.x, b.y); eD = make_float2(b.z, b.w);
     };
+    __shared__ int4 s_nd[WT];  // the lane's per-pixel cell counts, read once per cell
+    s_nd[lane] = make_int4(nd[0], nd[1], nd[2], nd[3]);
     const int ndmax = __reduce_max_sync(0xffffffffu, ndm);
     const uint2 rg = ranges[tile];
     const uint32_t end = rg.x + min((uint32_t)ndmax, rg.y - rg.x);
@@ -691,8 +693,10 @@ __global__ void __launch_bounds__(WT, BWD_MINB) k_blend_bwd(const ViewDesc *__re
         __syncwarp();
         const int n = (int)(e - rg.x);
         bool act[PPL];
-#pragma unroll
-        for (int q = 0; q < PPL; ++q) act[q] = n < nd[q];
+        {
+            const int4 nd4 = s_nd[lane];
+            act[0] = n < nd4.x; act[1] = n < nd4.y; act[2] = n < nd4.z; act[3] = n < nd4.w;
+        }
         const float4 *r = s_rec[buf];
         const float v = r[2].w;
         unsigned mask = __ballot_sync(0xffffffffu, lane < K && touches_rows(r[kRecF4 * lane], bx0, by0, (float)ROWS));
