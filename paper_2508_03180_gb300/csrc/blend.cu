@@ -50,18 +50,8 @@ constexpr int WT = 32;  // threads per work unit
 // entry e + 2 is issued while entry e is blended, so neither registers nor a
 // wait on the load's latency are spent on staging.  Every iteration commits one
 // copy group (empty past the list's end) and waits for all but the two
-// newest, which are the next two entries'.
+// newest, which are the next two entries' (cp_async16 and friends: internal.cuh).
 constexpr int NSTAGE = 3;
-
-__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
 
 // Issue the copy of the records of cell `id` (per float4s) into dst.
 __device__ __forceinline__ void issue_cell(float4 *dst, const float4 *__restrict__ vrec, uint32_t id, int per,

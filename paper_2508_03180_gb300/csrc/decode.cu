@@ -33,11 +33,12 @@ constexpr int kSmemMax = 227 * 1024;
 
 struct MlpShape {
     int W, M, LD;                        // warps per CTA, samples per tile (8 per warp), sample-row stride
+    int dbuf;                            // adjoint: two weight buffers (copies overlap the phase before)
     int F, H, K, I, Hp, HW, P;
     int nout[4], rb[5];                  // output widths; padded output block bases (rb[4] = Rp)
     int w1o[4], b1o[4], w2o[4], b2o[4];  // packed weight offsets per decoder
     // shared-memory layout (floats)
-    int s_w, s_b1, s_b2, s_z, s_h, s_o, s_dh, s_info, s_total;
+    int s_w, s_w2, s_b1, s_b2, s_z, s_h, s_o, s_dh, s_info, s_total;
     // backward rows per sample: Z [I], H [4Hp], dL/dh [4Hp], dL/do [Rp]
     int row_z, row_h, row_dh, row_do, row_all;
     // the weights in their shared-memory layouts, packed once per call in global memory:
@@ -48,9 +49,10 @@ struct MlpShape {
 static int up_to(int x, int m) { return (x + m - 1) / m * m; }
 
 // Layout for W warps per CTA (W = 8, 4 or 2: the largest whose shared memory fits).
-static MlpShape mlp_shape_w(int F, int H, int K, bool bwd, int W) {
+static MlpShape mlp_shape_w(int F, int H, int K, bool bwd, int W, bool dbuf) {
     MlpShape S{};
     S.W = W; S.M = 8 * W; S.LD = S.M + 4;
+    S.dbuf = bwd && dbuf;
     const int DM = S.M, DLM = S.LD;
     S.F = F; S.H = H; S.K = K; S.I = F + 4;
     S.HW = 4 * up_to(H, 4) <= 128 ? 4 : 8;
@@ -69,6 +71,7 @@ static MlpShape mlp_shape_w(int F, int H, int K, bool bwd, int W) {
     int at = 0;
     auto take = [&](int n) { const int r = at; at += up_to(n, 4); return r; };
     S.s_w = take(std::max(S.I * H4, S.Hp * Rp));
+    S.s_w2 = S.dbuf ? take(std::max(S.I * H4, S.Hp * Rp)) : S.s_w;  // the adjoint's second weight buffer
     S.s_b1 = take(H4);
     S.s_b2 = take(Rp);
     S.s_z = take(S.I * DLM);
@@ -90,17 +93,20 @@ static MlpShape mlp_shape_w(int F, int H, int K, bool bwd, int W) {
 }
 
 // Two CTAs per SM where the shared memory allows (one CTA's barrier waits
-// overlap the other's products), else the largest tile that fits.
+// overlap the other's products), else the largest tile that fits; the
+// adjoint prefers two weight buffers, then one.
 static MlpShape mlp_shape(int F, int H, int K, bool bwd) {
-    for (int W = 8; W >= 2; W /= 2) {
-        const MlpShape S = mlp_shape_w(F, H, K, bwd, W);
-        if (2 * sizeof(float) * (size_t)S.s_total <= (size_t)kSmemMax) return S;
+    for (int db = bwd ? 1 : 0; db >= 0; --db) {
+        for (int W = 8; W >= 2; W /= 2) {
+            const MlpShape S = mlp_shape_w(F, H, K, bwd, W, db);
+            if (2 * sizeof(float) * (size_t)S.s_total <= (size_t)kSmemMax) return S;
+        }
+        for (int W = 8; W >= 2; W /= 2) {
+            const MlpShape S = mlp_shape_w(F, H, K, bwd, W, db);
+            if (sizeof(float) * (size_t)S.s_total <= (size_t)kSmemMax) return S;
+        }
     }
-    for (int W = 8; W >= 2; W /= 2) {
-        const MlpShape S = mlp_shape_w(F, H, K, bwd, W);
-        if (sizeof(float) * (size_t)S.s_total <= (size_t)kSmemMax) return S;
-    }
-    return mlp_shape_w(F, H, K, bwd, 2);
+    return mlp_shape_w(F, H, K, bwd, 2, false);
 }
 
 // Logistic and tanh from the fast exponential and a fast divide (about 1e-6
@@ -299,12 +305,19 @@ __device__ __forceinline__ void copy_f4(float *dst, const float *__restrict__ sr
     for (int i = threadIdx.x; i < (n >> 2); i += blockDim.x) d4[i] = __ldg(s4 + i);
 }
 
-// Layer 1: H = relu(Z W1^T + b1) into the decoder-staggered rows of s_h.
+// The same as one commit group of asynchronous copies: complete after the
+// issuing threads' cp_async_wait and a barrier.
+__device__ __forceinline__ void copy_f4_async(float *dst, const float *__restrict__ src, int n) {
+    for (int i = threadIdx.x; i < (n >> 2); i += blockDim.x) cp_async16(dst + 4 * i, src + 4 * i);
+    cp_async_commit();
+}
+
+// Layer 1: H = relu(Z W1^T + b1) into the decoder-staggered rows of s_h (W: W1^T).
 template <int HW>
-__device__ __forceinline__ void layer1(const MlpShape &S, float *sm) {
+__device__ __forceinline__ void layer1(const MlpShape &S, float *sm, const float *W) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, j0 = lane * HW;
     if (j0 >= 4 * S.Hp) return;
-    const float *Zt = sm + S.s_z, *W = sm + S.s_w, *b1 = sm + S.s_b1;
+    const float *Zt = sm + S.s_z, *b1 = sm + S.s_b1;
     const int H4 = 4 * S.Hp;
     float acc[8][HW];
 #pragma unroll
@@ -341,10 +354,10 @@ __device__ __forceinline__ void layer1(const MlpShape &S, float *sm) {
     }
 }
 
-// Layer 2: O = H_D W2_D^T + b2 per decoder into the rows of s_o (W2^T staged).
-__device__ __forceinline__ void layer2(const MlpShape &S, float *sm) {
+// Layer 2: O = H_D W2_D^T + b2 per decoder into the rows of s_o (W: W2^T).
+__device__ __forceinline__ void layer2(const MlpShape &S, float *sm, const float *W) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, Rp = S.rb[4];
-    const float *Ht = sm + S.s_h, *W = sm + S.s_w, *b2 = sm + S.s_b2;
+    const float *Ht = sm + S.s_h, *b2 = sm + S.s_b2;
     float *Ot = sm + S.s_o;
     for (int rr = 4 * lane; rr < Rp; rr += 128) {
         const int D = out_block(S, rr);
@@ -395,19 +408,23 @@ __global__ void __launch_bounds__(256) k_decode(const ViewDesc *__restrict__ vie
                                                 float *__restrict__ g2d_zero) {
     extern __shared__ float4 smem4[];
     float *sm = reinterpret_cast<float *>(smem4);
+    float *Wb = sm + S.s_w;
     const int K = S.K;
+    // W1^T of a CTA's next tile is copied while the tile's epilogue runs
+    copy_f4_async(Wb, pk + S.g_w1t, S.I * 4 * S.Hp);
     for (long long q0 = (long long)blockIdx.x * S.M; q0 < nsamp; q0 += (long long)gridDim.x * S.M) {
-        copy_f4(sm + S.s_w, pk + S.g_w1t, S.I * 4 * S.Hp);
         copy_f4(sm + S.s_b1, pk + S.g_b1, 4 * S.Hp);
         copy_f4(sm + S.s_b2, pk + S.g_b2, S.rb[4]);
         stage_samples(S, sm, sc, srec, nsamp, q0);
+        cp_async_wait<0>();
         __syncthreads();
-        layer1<HW>(S, sm);
+        layer1<HW>(S, sm, Wb);
         __syncthreads();
-        copy_f4(sm + S.s_w, pk + S.g_w2t, S.Hp * S.rb[4]);
+        copy_f4(Wb, pk + S.g_w2t, S.Hp * S.rb[4]);
         __syncthreads();
-        layer2(S, sm);
+        layer2(S, sm, Wb);
         __syncthreads();
+        if (q0 + (long long)gridDim.x * S.M < nsamp) copy_f4_async(Wb, pk + S.g_w1t, S.I * 4 * S.Hp);
         // activations and the centres, one (sample, Gaussian) per thread
         const float *Ot = sm + S.s_o, *info = sm + S.s_info;
         for (int idx = threadIdx.x; idx < S.M * K; idx += blockDim.x) {
@@ -462,6 +479,7 @@ __global__ void __launch_bounds__(256) k_decode(const ViewDesc *__restrict__ vie
         }
         __syncthreads();
     }
+    cp_async_wait<0>();
 }
 
 // ---------------------------------------------------------------- adjoint
@@ -483,19 +501,36 @@ __global__ void __launch_bounds__(256) k_decode_bwd(SceneDev sc, MlpShape S, con
                                                         float *__restrict__ rows) {
     extern __shared__ float4 smem4[];
     float *sm = reinterpret_cast<float *>(smem4);
-    const int K = S.K, F = S.F, Hp = S.Hp, H4 = 4 * S.Hp;
+    const int K = S.K, F = S.F, Hp = S.Hp, H4 = 4 * S.Hp, Rp = S.rb[4];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // With two weight buffers (S.dbuf) each phase's weights are copied
+    // asynchronously while the phase before it computes (A: W1^T, then W2;
+    // B: W2^T, then W1); with one (WA == WB) each is copied between barriers.
+    float *WA = sm + S.s_w, *WB = sm + S.s_w2;
+    auto prefetch = [&](float *dst, const float *src, int n) {
+        if (S.dbuf) copy_f4_async(dst, src, n);
+    };
+    auto ready = [&](float *dst, const float *src, int n) {
+        if (S.dbuf) {
+            cp_async_wait<0>();
+            __syncthreads();
+        } else {
+            __syncthreads();
+            copy_f4(dst, src, n);
+            __syncthreads();
+        }
+    };
+    copy_f4(sm + S.s_b1, pk + S.g_b1, H4);
+    copy_f4(sm + S.s_b2, pk + S.g_b2, Rp);
+    prefetch(WA, pk + S.g_w1t, S.I * H4);
     for (long long q0 = (long long)blockIdx.x * S.M; q0 < nsamp; q0 += (long long)gridDim.x * S.M) {
-        copy_f4(sm + S.s_w, pk + S.g_w1t, S.I * 4 * S.Hp);
-        copy_f4(sm + S.s_b1, pk + S.g_b1, 4 * S.Hp);
-        copy_f4(sm + S.s_b2, pk + S.g_b2, S.rb[4]);
         stage_samples(S, sm, sc, srec, nsamp, q0);
-        __syncthreads();
-        layer1<HW>(S, sm);
-        __syncthreads();
-        copy_f4(sm + S.s_w, pk + S.g_w2t, S.Hp * S.rb[4]);
-        __syncthreads();
-        layer2(S, sm);
+        ready(WA, pk + S.g_w1t, S.I * H4);
+        prefetch(WB, pk + S.g_w2t, Hp * Rp);
+        layer1<HW>(S, sm, WA);
+        ready(WB, pk + S.g_w2t, Hp * Rp);
+        prefetch(WA, pk + S.g_w2, Rp * Hp);
+        layer2(S, sm, WB);
         __syncthreads();
         float *Ot = sm + S.s_o;
         const float *info = sm + S.s_info;
@@ -584,16 +619,15 @@ __global__ void __launch_bounds__(256) k_decode_bwd(SceneDev sc, MlpShape S, con
                 for (int c = 0; c < 4; ++c) *pq[c] = 0.f;
             }
         }
-        __syncthreads();
-        copy_f4(sm + S.s_w, pk + S.g_w2, S.rb[4] * S.Hp);
-        __syncthreads();
+        ready(WA, pk + S.g_w2, Rp * Hp);
+        prefetch(WB, pk + S.g_w1r, H4 * S.I);
         // dL/dh = relu'(h) * (dL/do_D W2_D)
         const int j0 = lane * HW;
         float *DHt = sm + S.s_dh;
         const float *Ht = sm + S.s_h;
         if (j0 < H4) {
             const int D = j0 / Hp, j = j0 - D * Hp;
-            const float *W = sm + S.s_w;
+            const float *W = WA;
             float acc[8][HW];
 #pragma unroll
             for (int s = 0; s < 8; ++s)
@@ -629,12 +663,11 @@ __global__ void __launch_bounds__(256) k_decode_bwd(SceneDev sc, MlpShape S, con
                                 hc.z > 0.f ? acc[6][c] : 0.f, hc.w > 0.f ? acc[7][c] : 0.f);
             }
         }
-        __syncthreads();
-        copy_f4(sm + S.s_w, pk + S.g_w1r, 4 * S.Hp * S.I);
-        __syncthreads();
+        ready(WB, pk + S.g_w1r, H4 * S.I);
+        if (q0 + (long long)gridDim.x * S.M < nsamp) prefetch(WA, pk + S.g_w1t, S.I * H4);
         // dL/df = sum_jj dL/dh[jj] W1[jj][:F]; lanes take features lane and lane + 32
         {
-            const float *W = sm + S.s_w;
+            const float *W = WB;
             const int i0 = lane, i1 = lane + 32;
             const bool u1 = i1 < F;
             if (i0 < F) {
@@ -701,6 +734,7 @@ __global__ void __launch_bounds__(256) k_decode_bwd(SceneDev sc, MlpShape S, con
         }
         __syncthreads();
     }
+    cp_async_wait<0>();
 }
 
 // Weight gradients from the per-sample rows:

@@ -227,4 +227,18 @@ void launch_loss_l1(const float *rgb, const float *target, int64_t n, float *dL,
                     int nblocks, float *loss, cudaStream_t st);
 int loss_l1_blocks(int64_t n);
 
+// Asynchronous 16-byte global-to-shared copies (cp.async, cached in L2
+// only): both addresses 16-byte aligned.  A copy is complete for the issuing
+// thread after a cp_async_wait that covers its commit group, and visible to
+// the other threads of the CTA (or warp) after a barrier that follows it.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 }  // namespace dgs
