@@ -357,6 +357,21 @@ __device__ __forceinline__ bool view_geom_adjoint(const ViewDesc &Vw, const Gaus
     return true;
 }
 
+// The views among [v0, v0 + 32) of the chain (bit u: view v0 + u) in which
+// cell `cell` of scene `slot` survived culling.  The counts of all of them are
+// requested before any is used.
+__device__ __forceinline__ unsigned visible_views(const ViewDesc *__restrict__ views, int n_views, int v0, int slot,
+                                                  const uint32_t *__restrict__ count, long long cell) {
+    unsigned m = 0u;
+    const int n = min(32, n_views - v0);
+#pragma unroll 8
+    for (int u = 0; u < n; ++u) {
+        const ViewDesc &Vw = views[v0 + u];
+        if (Vw.scene_slot == slot && count[Vw.cell_base + cell] != 0u) m |= 1u << u;
+    }
+    return m;
+}
+
 __global__ void __launch_bounds__(128) k_project_bwd_geom(const ViewDesc *__restrict__ views, int n_views, int slot,
                                                      SceneDev sc, const uint32_t *__restrict__ count, BlendParams bp,
                                                      const float *__restrict__ g2d, float *__restrict__ g_mean,
@@ -369,26 +384,52 @@ __global__ void __launch_bounds__(128) k_project_bwd_geom(const ViewDesc *__rest
         const long long cell = g / K;
         float gm[3] = {0.f, 0.f, 0.f}, gs[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f};
         float gq[4] = {0.f, 0.f, 0.f, 0.f}, glog = 0.f;
-        bool any = false;
-        for (int v = 0; v < n_views; ++v)
-            any |= views[v].scene_slot == slot && count[views[v].cell_base + cell] != 0u;
-        if (any) {
-            const GaussIn p = load_gauss(sc.gauss, G, g);
-            const float opac = 1.0f / (1.0f + expf(-p.logit));
-            for (int v = 0; v < n_views; ++v) {
-                const ViewDesc &Vw = views[v];
-                if (Vw.scene_slot != slot || count[Vw.cell_base + cell] == 0u) continue;
-                const float4 *gr = reinterpret_cast<const float4 *>(g2d + (Vw.rec_base + g) * kGradF);
-                const float4 a0 = gr[0], a1 = gr[1];
-                const float gmx = a0.x, gmy = a0.y, gca = a0.z, gcb = a0.w, gcc = a1.x, gop = a1.y;
-                if (gmx == 0.f && gmy == 0.f && gca == 0.f && gcb == 0.f && gcc == 0.f && gop == 0.f) continue;
-                ProjCore c;
-                proj_core(Vw, p, bp.dilation, c);
-                if (!c.valid) continue;
-                // opacity
-                glog += gop * opac * (1.0f - opac);
-                view_geom_adjoint(Vw, p, bp, gmx, gmy, gca, gcb, gcc, gm, gs, gq);
+        GaussIn p;
+        float opac = 0.f;
+        bool loaded = false;
+        for (int v0 = 0; v0 < n_views; v0 += 32) {
+            unsigned m = visible_views(views, n_views, v0, slot, count, cell);
+            if (!m) continue;
+            if (!loaded) {
+                p = load_gauss(sc.gauss, G, g);
+                opac = 1.0f / (1.0f + expf(-p.logit));
+                loaded = true;
             }
+            // the next visible view's screen-space gradient is requested
+            // before the current one is processed
+            auto fetch = [&](int v, float4 &a0, float4 &a1) {
+                const float4 *gr = reinterpret_cast<const float4 *>(g2d + (views[v].rec_base + g) * kGradF);
+                a0 = gr[0];
+                a1 = gr[1];
+            };
+            int v = v0 + __ffs(m) - 1;
+            m &= m - 1;
+            float4 a0, a1;
+            fetch(v, a0, a1);
+            for (;;) {
+                const int vn = m ? v0 + __ffs(m) - 1 : -1;
+                float4 b0 = a0, b1 = a1;
+                if (vn >= 0) {
+                    m &= m - 1;
+                    fetch(vn, b0, b1);
+                }
+                const float gmx = a0.x, gmy = a0.y, gca = a0.z, gcb = a0.w, gcc = a1.x, gop = a1.y;
+                if (gmx != 0.f || gmy != 0.f || gca != 0.f || gcb != 0.f || gcc != 0.f || gop != 0.f) {
+                    const ViewDesc &Vw = views[v];
+                    ProjCore c;
+                    proj_core(Vw, p, bp.dilation, c);
+                    if (c.valid) {
+                        glog += gop * opac * (1.0f - opac);  // opacity
+                        view_geom_adjoint(Vw, p, bp, gmx, gmy, gca, gcb, gcc, gm, gs, gq);
+                    }
+                }
+                if (vn < 0) break;
+                v = vn;
+                a0 = b0;
+                a1 = b1;
+            }
+        }
+        if (loaded) {
             // d/d log s = s d/ds
 #pragma unroll
             for (int j = 0; j < 3; ++j) gls[j] = gs[j] * p.scale[j];
@@ -479,11 +520,36 @@ __global__ void __launch_bounds__(COL_T) k_project_bwd_colour(const ViewDesc *__
         const float m0 = live ? sc.gauss[g] : 0.f, m1 = live ? sc.gauss[G + g] : 0.f,
                     m2 = live ? sc.gauss[2 * G + g] : 0.f;
         float gdm[3] = {0.f, 0.f, 0.f};
-        for (int v = 0; live && v < n_views; ++v) {
+        // visible views in order, the next one's colour gradient requested
+        // before the current one is processed
+        int v0 = 0;
+        unsigned m = 0u;
+        auto next_view = [&]() -> int {
+            while (live && !m && v0 < n_views) {
+                m = visible_views(views, n_views, v0, slot, count, cell);
+                if (!m) v0 += 32;
+            }
+            if (!m) return -1;
+            const int v = v0 + __ffs(m) - 1;
+            m &= m - 1;
+            if (!m) v0 += 32;
+            return v;
+        };
+        auto fetch = [&](int v, float gc[3]) {
+            const float *gr = g2d + (views[v].rec_base + g) * kGradF + 6;
+            gc[0] = gr[0];
+            gc[1] = gr[1];
+            gc[2] = gr[2];
+        };
+        float gn[3] = {0.f, 0.f, 0.f};
+        int vn = next_view();
+        if (vn >= 0) fetch(vn, gn);
+        while (vn >= 0) {
+            const int v = vn;
+            const float gc[3] = {gn[0], gn[1], gn[2]};
+            vn = next_view();
+            if (vn >= 0) fetch(vn, gn);
             const ViewDesc &Vw = views[v];
-            if (Vw.scene_slot != slot || count[Vw.cell_base + cell] == 0u) continue;
-            const float *gr = g2d + (Vw.rec_base + g) * kGradF + 6;
-            const float gc[3] = {gr[0], gr[1], gr[2]};
             if (gc[0] == 0.f && gc[1] == 0.f && gc[2] == 0.f) continue;
             const float u0 = m0 - Vw.eye[0], u1 = m1 - Vw.eye[1], u2 = m2 - Vw.eye[2];
             const float il = rsqrtf(u0 * u0 + u1 * u1 + u2 * u2);
