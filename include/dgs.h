@@ -93,13 +93,21 @@ typedef struct {
  *   DGS_FLAG_NUMERATOR     the image is the numerator N of Eq. 12 (no
  *                          normalisation; with one Gaussian per cell and v = 1
  *                          this is alpha-blending, Eq. 2-3)
- * ALPHA_SKIP, TERM_EXCLUDE, NUMERATOR and w_bg apply to the hybrid renderer
- * (dgs_render, serving); AABB_SQUARE also to the comparators (it changes the
- * per-Gaussian records they share).  The adjoint follows every flag. */
+ *   DGS_FLAG_NEAR_FULL     a cell whose ellipsoid reaches the near plane
+ *                          (c_z - sqrt(S_zz) <= znear) without lying wholly
+ *                          behind it (c_z + sqrt(S_zz) > znear) covers every
+ *                          tile of the image, sorted at depth max(c_z, 0),
+ *                          instead of being culled (a conservative footprint;
+ *                          its Gaussians are still culled one by one at znear)
+ * ALPHA_SKIP, TERM_EXCLUDE, NUMERATOR, NEAR_FULL and w_bg apply to the hybrid
+ * renderer (dgs_render, serving); AABB_SQUARE also to the comparators (it
+ * changes the per-Gaussian records they share).  The adjoint follows every
+ * flag. */
 #define DGS_FLAG_ALPHA_SKIP 1
 #define DGS_FLAG_TERM_EXCLUDE 2
 #define DGS_FLAG_AABB_SQUARE 4
 #define DGS_FLAG_NUMERATOR 8
+#define DGS_FLAG_NEAR_FULL 16
 
 void dgs_config_default(dgs_config *cfg);
 

@@ -61,7 +61,7 @@ def lib():
         L = ctypes.CDLL(build())
         P = ctypes.c_void_p
         i64, i32 = ctypes.c_int64, ctypes.c_int
-        L.or_cell_rects.argtypes = [i64, P, P, P, P, i32, P, P, P]
+        L.or_cell_rects.argtypes = [i64, P, P, P, P, i32, i32, P, P, P]
         L.or_cell_rects.restype = None
         L.or_tile_lists.argtypes = [i64, P, P, i32, i32, P, i64, P]
         L.or_tile_lists.restype = i64
@@ -108,7 +108,9 @@ class Options:
     contributes nothing; term_exclude, a cell that would take T below eps is
     not blended; aabb_square, the AABB is the square of radius
     ceil(ksigma sqrt(lambda_max(Sigma'))); out_numerator, the output is the
-    numerator N of Eq. 12.
+    numerator N of Eq. 12; near_full, a cell reaching the near plane without
+    lying wholly behind it covers every tile (sort depth max(c_z, 0)) instead
+    of being culled.
     """
     eps: float = 1e-4
     alpha_max: float = 0.99
@@ -123,10 +125,11 @@ class Options:
     term_exclude: bool = False
     aabb_square: bool = False
     out_numerator: bool = False
+    near_full: bool = False
 
     def flags(self) -> int:
         return (1 if self.alpha_skip else 0) | (2 if self.term_exclude else 0) | \
-            (4 if self.aabb_square else 0) | (8 if self.out_numerator else 0)
+            (4 if self.aabb_square else 0) | (8 if self.out_numerator else 0) | (16 if self.near_full else 0)
 
     def blend_opts(self) -> np.ndarray:
         return np.array([self.eps, self.alpha_max, self.d_min, *self.bg, self.delta, self.w_bg, float(self.flags())],
@@ -145,7 +148,7 @@ def cell_rects(scene, cam, opt: Options = Options(), with_bounds=False):
     depth = np.empty(N, dtype=np.float32)
     bounds = np.empty((N, 4), dtype=np.float32) if with_bounds else None
     lib().or_cell_rects(N, _p(_c(scene.cell_center, np.float32)), _p(_c(scene.cell_axes, np.float32)),
-                        _p(_c(scene.cell_quat, np.float32)), _p(_c(cam, np.float32)), opt.tile,
+                        _p(_c(scene.cell_quat, np.float32)), _p(_c(cam, np.float32)), opt.tile, opt.flags(),
                         _p(rect), _p(depth), _p(bounds))
     if with_bounds:
         return rect, depth, bounds

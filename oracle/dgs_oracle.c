@@ -82,6 +82,9 @@ static void f32_xform(const float R[9], const float t[3], const float p[3], floa
  * Pixel bound u = fx t + cx; the same for y.  A cell whose ellipsoid reaches
  * the near plane (c_z - sqrt(S_zz) <= znear) or whose box misses the image
  * is culled.  Tiles [floor(lo/tile), floor(hi/tile)] clamped to the grid.
+ * Variant (flags & 16, the renderer's DGS_FLAG_NEAR_FULL): a cell that
+ * reaches the near plane without lying wholly behind it (c_z + sqrt(S_zz) >
+ * znear) is kept with every tile of the image, sort depth max(c_z, 0).
  *
  * rect[4n..4n+3] = tx0 ty0 tx1 ty1 (inclusive), tx0 = -1 when culled.
  * depth[n] = view-space z of the cell centre (the sort depth).
@@ -89,7 +92,7 @@ static void f32_xform(const float R[9], const float t[3], const float p[3], floa
  * near plane.
  */
 void or_cell_rects(int64_t N, const float *center, const float *axes, const float *quat,
-                   const float *cam, int tile, int32_t *rect, float *depth, float *bounds) {
+                   const float *cam, int tile, int flags, int32_t *rect, float *depth, float *bounds) {
     const int W = (int)cam[0], H = (int)cam[1];
     const float fx = cam[2], fy = cam[3], ppx = cam[4], ppy = cam[5], znear = cam[6];
     const float *Rv = cam + 7, *tv = cam + 16;
@@ -110,7 +113,13 @@ void or_cell_rects(int64_t N, const float *center, const float *axes, const floa
         depth[n] = c[2];
         rect[4 * n] = rect[4 * n + 1] = rect[4 * n + 2] = rect[4 * n + 3] = -1;
         if (bounds) bounds[4 * n] = bounds[4 * n + 1] = bounds[4 * n + 2] = bounds[4 * n + 3] = NAN;
-        if (!((c[2] - sqrtf(szz)) > znear)) continue;
+        if (!((c[2] - sqrtf(szz)) > znear)) {
+            if ((flags & 16) && (c[2] + sqrtf(szz)) > znear) {  /* straddles the near plane: every tile */
+                depth[n] = c[2] > 0.0f ? c[2] : 0.0f;
+                rect[4 * n] = 0; rect[4 * n + 1] = 0; rect[4 * n + 2] = Tx - 1; rect[4 * n + 3] = Ty - 1;
+            }
+            continue;
+        }
         const float czz = c[2] * c[2];
         const float a = czz - szz;
         float lo[2], hi[2];

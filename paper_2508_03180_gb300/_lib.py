@@ -48,6 +48,7 @@ DGS_FLAG_ALPHA_SKIP = 1
 DGS_FLAG_TERM_EXCLUDE = 2
 DGS_FLAG_AABB_SQUARE = 4
 DGS_FLAG_NUMERATOR = 8
+DGS_FLAG_NEAR_FULL = 16
 
 
 class dgs_neural_desc(C.Structure):

@@ -192,7 +192,7 @@ extern "C" dgs_status dgs_create(const dgs_config *cfg, dgs_ctx **out) {
     if (cfg) c = *cfg; else dgs_config_default(&c);
     if (!(c.eps >= 0.f) || !(c.alpha_max > 0.f && c.alpha_max < 1.f) || !(c.ksigma > 0.f) || !(c.dilation >= 0.f) ||
         !(c.w_bg >= 0.f) || (c.flags & ~(DGS_FLAG_ALPHA_SKIP | DGS_FLAG_TERM_EXCLUDE | DGS_FLAG_AABB_SQUARE |
-                                         DGS_FLAG_NUMERATOR)) != 0)
+                                         DGS_FLAG_NUMERATOR | DGS_FLAG_NEAR_FULL)) != 0)
         return set_error(DGS_ERR_INVALID_ARG,
                          "config out of range (need eps >= 0, 0 < alpha_max < 1, ksigma > 0, w_bg >= 0, known flags)");
     int ndev = 0;
@@ -516,7 +516,7 @@ static dgs_status run_binning(dgs_ctx *ctx, Workspace &ws, cudaStream_t st) {
         StageTimer t(pf, DGS_STAGE_CELL_PROJECT, st);
         launch_cell_project(dv, V, (const SceneDev *)ws.scenes.p, n, (uint32_t *)ws.zkey.p, (uint32_t *)ws.zval.p,
                             (short4 *)ws.rect.p, (float *)ws.depth.p, (uint32_t *)ws.count.p, small + kSmallVisible,
-                            (float *)ws.vview.p, st);
+                            (float *)ws.vview.p, ctx->cfg.flags, st);
     }
     {
         StageTimer t(pf, DGS_STAGE_DEPTH_SORT, st);

@@ -20,7 +20,8 @@ __global__ void __launch_bounds__(256) k_cell_project(const ViewDesc *__restrict
                                                       uint32_t *__restrict__ zkey, uint32_t *__restrict__ zval,
                                                       short4 *__restrict__ rect, float *__restrict__ depth,
                                                       uint32_t *__restrict__ count, uint32_t *__restrict__ visible,
-                                                      float *__restrict__ vview, const ChainSizes *__restrict__ dsz) {
+                                                      float *__restrict__ vview, int flags,
+                                                      const ChainSizes *__restrict__ dsz) {
     if (dsz) n_views = dsz->n_views;
     uint32_t nvis = 0;
     for (int v = 0; v < n_views; ++v) {
@@ -49,10 +50,15 @@ __global__ void __launch_bounds__(256) k_cell_project(const ViewDesc *__restrict
                           fmul_s(M[3 * a + 2], M[3 * b + 2]));
         };
         const float sxx = sig(0, 0), syy = sig(1, 1), szz = sig(2, 2), sxz = sig(0, 2), syz = sig(1, 2);
-        depth[i] = c[2];
+        float dz = c[2];  // the sort depth
         short4 r = make_short4(-1, -1, -1, -1);
         bool vis = fsub_s(c[2], fsqrt_s(szz)) > V.znear;
-        if (vis) {
+        if (!vis && (flags & DGS_FLAG_NEAR_FULL) && fadd_s(c[2], fsqrt_s(szz)) > V.znear) {
+            // straddles the near plane: conservatively every tile, nearest first
+            vis = true;
+            dz = c[2] > 0.0f ? c[2] : 0.0f;
+            r = make_short4(0, 0, (short)(V.Tx - 1), (short)(V.Ty - 1));
+        } else if (vis) {
             const float czz = fmul_s(c[2], c[2]);
             const float a = fsub_s(czz, szz);
             float lo[2], hi[2];
@@ -84,6 +90,7 @@ __global__ void __launch_bounds__(256) k_cell_project(const ViewDesc *__restrict
             }
         }
         rect[i] = r;
+        depth[i] = dz;
         // v_n of this view (Sec. V-A): the scalar, or clamp(sum_lm k_lm Y_lm(d), 0, 1)
         // with d the unit vector from the eye to the cell centre
         float vn = cell[10 * N + n];
@@ -100,7 +107,7 @@ __global__ void __launch_bounds__(256) k_cell_project(const ViewDesc *__restrict
         }
         vview[i] = vn;
         // depth key: positive float bits order like the floats; culled last
-        zkey[i] = vis ? __float_as_uint(c[2]) : 0xFFFFFFFFu;
+        zkey[i] = vis ? __float_as_uint(dz) : 0xFFFFFFFFu;
         zval[i] = (uint32_t)i;
         count[i] = vis ? (uint32_t)((r.z - r.x + 1) * (r.w - r.y + 1)) : 0u;
         nvis += vis ? 1u : 0u;
@@ -121,10 +128,10 @@ static int grid_for(long long n, int threads) {
 
 void launch_cell_project(const ViewDesc *views, int n_views, const SceneDev *scenes, long long n_entries,
                          uint32_t *zkey, uint32_t *zval, short4 *rect, float *depth, uint32_t *count,
-                         uint32_t *visible, float *vview, cudaStream_t st, const ChainSizes *dsz) {
+                         uint32_t *visible, float *vview, int flags, cudaStream_t st, const ChainSizes *dsz) {
     if (n_entries == 0) return;
     k_cell_project<<<grid_for(n_entries / n_views + 1, 256), 256, 0, st>>>(views, n_views, scenes, zkey, zval, rect,
-                                                                          depth, count, visible, vview, dsz);
+                                                                          depth, count, visible, vview, flags, dsz);
 }
 
 __global__ void k_gather_counts(const uint32_t *__restrict__ idx, const uint32_t *__restrict__ count, long long n,

@@ -115,9 +115,11 @@ __device__ __forceinline__ void xform_s(const float R[9], const float t[3], floa
 // `d_L` likewise points at the device-side pair count.
 // vview[entry]: v_n as rendered in that view (the scalar, or the clamped SH
 // value of a view-dependent v_n).
+// flags: dgs_config.flags (DGS_FLAG_NEAR_FULL changes the footprint of cells at the near plane).
 void launch_cell_project(const ViewDesc *views, int n_views, const SceneDev *scenes, long long n_entries,
                          uint32_t *zkey, uint32_t *zval, short4 *rect, float *depth, uint32_t *count,
-                         uint32_t *visible, float *vview, cudaStream_t st, const ChainSizes *dsz = nullptr);
+                         uint32_t *visible, float *vview, int flags, cudaStream_t st,
+                         const ChainSizes *dsz = nullptr);
 void launch_gather_counts(const uint32_t *zval_sorted, const uint32_t *count, long long n, uint32_t *out,
                           cudaStream_t st, const uint32_t *d_n = nullptr);
 void launch_emit(const uint32_t *offs, const uint32_t *zval_sorted, const short4 *rect, const ViewDesc *views,

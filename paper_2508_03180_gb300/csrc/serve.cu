@@ -218,7 +218,7 @@ dgs_status record_chain(dgs_ctx *ctx, Workspace &ws, const ChainCaps &c, const B
     CKR(cudaMemsetAsync(small, 0, 256, st));
     launch_cell_project(dv, c.V, (const SceneDev *)ws.scenes.p, c.E, (uint32_t *)ws.zkey.p, (uint32_t *)ws.zval.p,
                         (short4 *)ws.rect.p, (float *)ws.depth.p, (uint32_t *)ws.count.p, small + kSmallVisible,
-                        (float *)ws.vview.p, st, dsz);
+                        (float *)ws.vview.p, ctx->cfg.flags, st, dsz);
     radix_sort_pairs((uint32_t *)ws.zkey.p, (uint32_t *)ws.zval.p, c.E, 32, sc, st, d_E);
     launch_gather_counts((const uint32_t *)ws.zval.p, (const uint32_t *)ws.count.p, c.E, (uint32_t *)ws.cnt_sorted.p,
                          st, d_E);

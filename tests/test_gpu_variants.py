@@ -3,7 +3,8 @@ options: images under the termination-count protocol and the parameter
 gradients (gradient tolerance as for the default renderer), for a
 background weight, the numerator output, the 1/255 alpha skip, the 3DGS
 termination rule, the square AABB and a combination; and a served request
-with flags equals the direct render.
+with flags equals the direct render.  The near-plane footprint variant is
+checked with a camera inside the scene, its binning bit for bit.
 
 The alpha skip is decided in FP32 on the GPU and in FP64 in the oracle; the
 scene used for it keeps every alpha at least 1e-4 (relative) away from 1/255,
@@ -14,7 +15,7 @@ import torch
 
 import oracle
 from paper_2508_03180_gb300 import synth
-from tests.gpu_helpers import read_state, view_slices
+from tests.gpu_helpers import read_state, tile_lists_equal, view_slices
 from tests.test_gpu_grad import assert_close_group
 
 pytestmark = pytest.mark.gpu
@@ -49,15 +50,43 @@ def _alpha_margin(sc, cam, opt):
     return worst
 
 
-@pytest.mark.parametrize("name", list(VARIANTS))
-def test_variant_render_and_gradients(name):
-    from paper_2508_03180_gb300.renderer import Context
-    cfg, opt = VARIANTS[name]
+def _variant_scene():
     sc = synth.make_scene(60, 4, synth._box(-0.5, 0.5), 0.15, 0.4, 1, seed=22)
     sc.cell_v[:] = np.random.default_rng(4).uniform(0.3, 1.0, sc.N).astype(np.float32)
+    return sc
+
+
+@pytest.mark.parametrize("name", list(VARIANTS))
+def test_variant_render_and_gradients(name):
+    cfg, opt = VARIANTS[name]
+    sc = _variant_scene()
     cams = synth.sphere_cameras(2, 3.0, 48, 40, seed0=5)
     if opt.alpha_skip:
         assert min(_alpha_margin(sc, c.as_array(), opt) for c in cams) > 1e-4
+    _check_variant(name, sc, cams, cfg, opt)
+
+
+def test_near_full_binning_render_and_gradients():
+    """DGS_FLAG_NEAR_FULL with a camera inside the scene: cells straddling
+    the near plane cover every tile; rectangles, depths and tile lists bit for
+    bit, then the image and gradients as for the other variants."""
+    sc = _variant_scene()
+    cams = [synth.look_at((0.05, -0.42, 0.03), (0.0, 0.6, 0.0), 48, 40)]
+    opt = oracle.Options(near_full=True)
+    cam = cams[0].as_array()
+    rect0, _ = oracle.cell_rects(sc, cam)
+    rect, depth = oracle.cell_rects(sc, cam, opt)
+    assert ((rect0[:, 0] < 0) & (rect[:, 0] >= 0)).sum() >= 2  # the camera sits among the cells
+    gv = _check_variant("near_full", sc, cams, dict(flags=16), opt, keep_state=True)
+    assert np.array_equal(gv["rect"], rect)
+    vis = rect[:, 0] >= 0
+    assert np.array_equal(gv["depth"][vis].view(np.uint32), depth[vis].view(np.uint32))
+    ocells, orng = oracle.tile_lists(rect, depth, cam, opt)
+    assert tile_lists_equal(gv, gv["cells"], ocells, orng) == 0
+
+
+def _check_variant(name, sc, cams, cfg, opt, keep_state=False):
+    from paper_2508_03180_gb300.renderer import Context
     ctx = Context(**cfg)
     try:
         sid = ctx.upload_scene(sc)
@@ -88,6 +117,7 @@ def test_variant_render_and_gradients(name):
         assert_close_group(f"{name} cell_v", gr["g_cell_v"].cpu(), tot["cell_v"])
         ctx.release_state(state)
         ctx.release_scene(sid)
+        return view_slices(gs, 0) | {"cells": gs["cells"]} if keep_state else None
     finally:
         ctx.close()
 

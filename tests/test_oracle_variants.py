@@ -188,3 +188,43 @@ def test_variant_adjoint_matches_central_differences(name):
         fd = (vals[0] - vals[1]) / 2e-6
         assert abs(fd - an["v"][c]) <= 1e-6 * np.abs(an["v"]).max() + 1e-9, (name, c, fd, an["v"][c])
     assert n_checked >= 40 and len(cs) >= 2
+
+
+def _near_plane_scene():
+    """Four cells in front of a camera at the origin looking along +z (view
+    z = world z): one straddling the near plane (0.2) with its centre in
+    front, one wholly behind, one in front, one straddling with its centre
+    behind the eye."""
+    sc = synth.make_scene(4, 2, synth._box(-0.5, 0.5), 0.15, 0.4, 0, seed=1)
+    sc.cell_center[:] = np.array([[0.0, 0.0, 0.25], [0.0, 0.0, -1.0], [0.2, 0.1, 3.0], [0.1, 0.0, -0.1]],
+                                 np.float32)
+    sc.cell_axes[:] = np.array([[0.3] * 3, [0.3] * 3, [0.3] * 3, [0.5] * 3], np.float32)
+    sc.cell_quat[:] = np.array([1.0, 0.0, 0.0, 0.0], np.float32)
+    cam = synth.look_at((0.0, 0.0, 0.0), (0.0, 0.0, 1.0), 64, 48).as_array()
+    return sc, cam
+
+
+def test_near_full_footprint():
+    sc, cam = _near_plane_scene()
+    znear = float(cam[6])
+    cz = sc.cell_center[:, 2].astype(np.float64)
+    ext = sc.cell_axes[:, 2].astype(np.float64)  # sqrt(S_zz) of an axis-aligned cell
+    straddle = (cz - ext <= znear) & (cz + ext > znear)
+    assert list(straddle) == [True, False, False, True]
+    _, _, Tx, Ty = oracle.grid(cam)
+    rect, depth = oracle.cell_rects(sc, cam)
+    rect_f, depth_f = oracle.cell_rects(sc, cam, oracle.Options(near_full=True))
+    assert (rect[straddle] == -1).all() and (rect[1] == -1).all()       # default: culled
+    assert (rect_f[1] == -1).all()                                      # wholly behind: culled either way
+    for n in np.nonzero(straddle)[0]:                                   # variant: every tile
+        assert list(rect_f[n]) == [0, 0, Tx - 1, Ty - 1]
+        assert depth_f[n] == np.float32(max(cz[n], 0.0))
+    assert (rect_f[2] == rect[2]).all() and rect[2][0] >= 0 and depth_f[2] == depth[2]
+    # every tile's list starts with the straddlers, nearest first (depth 0 before 0.25)
+    cells, rng = oracle.tile_lists(rect_f, depth_f, cam, oracle.Options(near_full=True))
+    for t in range(Tx * Ty):
+        lst = list(cells[rng[t, 0]:rng[t, 1]])
+        assert lst[:2] == [3, 0]
+        tx, ty = t % Tx, t // Tx
+        in2 = rect[2][0] <= tx <= rect[2][2] and rect[2][1] <= ty <= rect[2][3]
+        assert lst[2:] == ([2] if in2 else [])
