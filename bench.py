@@ -155,6 +155,30 @@ def max_over_ranks(x, world):
     return float(t.item())
 
 
+def flat_grads(G, C, device):
+    """The explicit Gaussians' gradients (mean, log-scale, quaternion, logit,
+    SH: 59 floats per Gaussian at SH degree 3) as views of one flat buffer,
+    so a data-parallel step sums them across ranks with one all-reduce."""
+    import torch
+    shapes = dict(g_mean=(G, 3), g_log_scale=(G, 3), g_quat=(G, 4), g_logit=(G,), g_sh=(G, C, 3))
+    flat = torch.empty(sum(int(np.prod(v)) for v in shapes.values()), dtype=torch.float32, device=device)
+    out, o = {}, 0
+    for k, shp in shapes.items():
+        n = int(np.prod(shp))
+        out[k] = flat[o:o + n].view(shp)
+        o += n
+    return flat, out
+
+
+def reduce_grads(flat, world):
+    """Data-parallel fwd+bwd over views: every rank renders its own views of
+    the same scene, so the per-Gaussian gradients are summed across ranks
+    (the step's one exchange).  Nothing to do on one rank."""
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(flat, op=dist.ReduceOp.SUM)
+
+
 def weak_value(ms_total, world, px_per_rank_step, steps):
     """Whole-job Mpix/s: every rank renders its own views (weak scaling), so
     the job processed world x px x steps pixels in the slowest rank's time."""
@@ -489,15 +513,14 @@ def main():
     img = torch.empty(nv * 3 * H_IMG * W_IMG, device="cuda")
     dl = torch.empty_like(img)
     loss = torch.empty(1, device="cuda")
-    grads = dict(g_mean=torch.empty(G, 3, device="cuda"), g_log_scale=torch.empty(G, 3, device="cuda"),
-                 g_quat=torch.empty(G, 4, device="cuda"), g_logit=torch.empty(G, device="cuda"),
-                 g_sh=torch.empty(G, C, 3, device="cuda"))
+    gflat, grads = flat_grads(G, C, "cuda")
 
     def step():
         _, state, _ = rctx.render(sid, cams, want_state=True, out=img, slots=slots)
         rctx.loss_l1(img, target, dl, loss)
         rctx.backward(state, dl, grads)
         rctx.release_state(state)
+        reduce_grads(gflat, world)
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -571,7 +594,11 @@ def main():
     from paper_2508_03180_gb300 import _lib as L
     host = {k: torch.from_numpy(np.ascontiguousarray(getattr(scene, k))).pin_memory()
             for k in ("g_mean", "g_scale", "g_quat", "g_logit", "g_sh")}
-    hgr = {k: torch.empty(v.shape, dtype=torch.float32).pin_memory() for k, v in grads.items()}
+    hflat = torch.empty(gflat.numel(), dtype=torch.float32).pin_memory()
+    hgr, o = {}, 0
+    for k, v in grads.items():  # views of the pinned flat buffer, in the device buffer's order
+        hgr[k] = hflat[o:o + v.numel()].view(v.shape)
+        o += v.numel()
     hloss = torch.empty(1).pin_memory()
     desc = L.dgs_scene_desc()
     desc.num_cells, desc.K, desc.sh_degree, desc.location = N, scene.K, scene.sh_degree, L.DGS_HOST
@@ -588,7 +615,12 @@ def main():
         L.dgs_scene_update(rctx.ctx, sid, desc, stream.cuda_stream)
         _, state, _ = rctx.render(sid, cams, want_state=True, out=img, slots=slots)
         rctx.loss_l1(img, target, dl, loss)
-        L.dgs_render_backward(rctx.ctx, state, dl.data_ptr(), L.DGS_DEVICE, gstruct, stream.cuda_stream)
+        if world == 1:  # the adjoint writes the gradients straight into the pinned host arrays
+            L.dgs_render_backward(rctx.ctx, state, dl.data_ptr(), L.DGS_DEVICE, gstruct, stream.cuda_stream)
+        else:  # data parallel: summed across ranks on the device, then one download
+            rctx.backward(state, dl, grads)
+            reduce_grads(gflat, world)
+            hflat.copy_(gflat, non_blocking=True)
         hloss.copy_(loss, non_blocking=True)
         rctx.release_state(state)
 

@@ -1,7 +1,8 @@
 """The N > 1 host path of bench.py on CPU ranks (gloo, world size 2): each
-rank renders its own seeded views (no data-path collective), the timing is
-the maximum over ranks, the value is the whole-job pixel rate, and only
-rank 0 reports."""
+rank renders its own seeded views, the per-Gaussian gradients of the
+data-parallel step are summed across ranks with one all-reduce of the flat
+gradient buffer (the step's only exchange), the timing is the maximum over
+ranks, the value is the whole-job pixel rate, and only rank 0 reports."""
 import os
 import sys
 
@@ -21,7 +22,12 @@ def _rank_main(rank, world, port, q):
     bench.barrier(w)
     ms = bench.max_over_ranks(10.0 + 5.0 * r, w)  # rank 1 is the slow one
     value = bench.weak_value(ms, w, 1000, 4)
-    q.put((r, w, cams, ms, value))
+    # gradients of 7 Gaussians (SH degree 3): rank r's own are r + 1 + index
+    import torch
+    flat, g = bench.flat_grads(7, 16, "cpu")
+    flat.copy_(torch.arange(flat.numel(), dtype=torch.float32) + (r + 1))
+    bench.reduce_grads(flat, w)
+    q.put((r, w, cams, ms, value, flat.numpy().copy(), tuple(g["g_sh"].shape), g["g_logit"].numpy().copy()))
     import torch.distributed as dist
     dist.destroy_process_group()
 
@@ -41,11 +47,17 @@ def test_two_gloo_ranks():
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    (r0, w0, cams0, ms0, v0), (r1, w1, cams1, ms1, v1) = res
+    (r0, w0, cams0, ms0, v0, f0, sh0, lg0), (r1, w1, cams1, ms1, v1, f1, sh1, lg1) = res
     assert (r0, r1, w0, w1) == (0, 1, 2, 2)
     assert cams0 != cams1                     # every rank its own views
     assert ms0 == ms1 == 15.0                 # the slowest rank's time
     assert v0 == v1 == pytest.approx(2 * 1000 * 4 / 15e-3 / 1e6)
+    import numpy as np
+    n = 7 * 59
+    want = 2 * np.arange(n, dtype=np.float32) + 3  # (i + 1) + (i + 2)
+    assert f0.shape == (n,) and np.array_equal(f0, want) and np.array_equal(f1, want)
+    assert sh0 == sh1 == (7, 16, 3)
+    assert np.array_equal(lg0, want[7 * 10:7 * 11])  # logit block after mean, log-scale, quaternion
 
 
 def test_single_rank_needs_no_process_group():
@@ -53,3 +65,8 @@ def test_single_rank_needs_no_process_group():
     import bench
     assert bench.max_over_ranks(3.0, 1) == 3.0
     assert bench.weak_value(1000.0, 1, 2_000_000, 10) == pytest.approx(20.0)
+    import torch
+    flat, _ = bench.flat_grads(3, 16, "cpu")
+    flat.fill_(2.0)
+    bench.reduce_grads(flat, 1)  # one rank: no collective, unchanged
+    assert torch.all(flat == 2.0)
