@@ -92,10 +92,24 @@ static MlpShape mlp_shape_w(int F, int H, int K, bool bwd, int W, bool dbuf) {
     return S;
 }
 
+// The adjoint's weight gradients in registers (k_decode_bwd<4, true>): tiles
+// of FW_M samples, thread t holding row t of dW1 (over all decoders) and of
+// dW2, so 4Hp and Rp at most the CTA's threads, I <= FW_I, Hp <= FW_H.
+constexpr int FW_I = 40, FW_H = 32, FW_M = 32;
+static bool wgrad_fused(const MlpShape &S) {
+    const int threads = 32 * S.W;
+    return S.HW == 4 && S.M == FW_M && 4 * S.Hp <= threads && S.rb[4] <= threads && S.I <= FW_I && S.Hp <= FW_H;
+}
+
 // Two CTAs per SM where the shared memory allows (one CTA's barrier waits
 // overlap the other's products), else the largest tile that fits; the
-// adjoint prefers two weight buffers, then one.
+// adjoint prefers the fused weight gradients, then two weight buffers, then one.
 static MlpShape mlp_shape(int F, int H, int K, bool bwd) {
+    if (bwd)
+        for (int db = 1; db >= 0; --db) {
+            const MlpShape S = mlp_shape_w(F, H, K, true, FW_M / 8, db);
+            if (wgrad_fused(S) && 2 * sizeof(float) * (size_t)S.s_total <= (size_t)kSmemMax) return S;
+        }
     for (int db = bwd ? 1 : 0; db >= 0; --db) {
         for (int W = 8; W >= 2; W /= 2) {
             const MlpShape S = mlp_shape_w(F, H, K, bwd, W, db);
@@ -489,16 +503,22 @@ __global__ void __launch_bounds__(256) k_decode(const ViewDesc *__restrict__ vie
 //     Eq. 11 bound);
 //   dL/dh = relu'(h) (dL/do_D W2_D) per decoder;
 //   dL/df = sum over decoders of dL/dh_D W1_D[:, :F]  (atomic adds to g_feat);
-// and the rows Z, H, dL/dh, dL/do of every sample to `rows` for the weight
-// gradients (k_mlp_wgrad), stored per tile of M samples as unit rows of M
-// values (the tile's shared-memory layout, so they leave as float4 copies).  Decisions held fixed: the ReLU masks, the side of
-// the Eq. 11 minimum, sigma <= 0 (gdec is zero there).
-template <int HW>
+// and the weight gradients.  FUSE (the common widths, wgrad_fused: a tile of
+// 32 samples, 4Hp and the padded outputs Rp at most the CTA's threads,
+// I <= FW_I, Hp <= FW_H): thread t keeps row t of dW1 | db1 (over all decoders) and row
+// t of dW2 | db2 in registers, adds each tile's products from shared memory
+// and flushes them to g_mlp once, with atomic adds, at the end.  Otherwise
+// the rows Z, H, dL/dh, dL/do of every sample go to `rows` for k_mlp_wgrad,
+// stored per tile of M samples as unit rows of M values (the tile's
+// shared-memory layout, so they leave as float4 copies).  Decisions held
+// fixed: the ReLU masks, the side of the Eq. 11 minimum, sigma <= 0 (gdec is
+// zero there).
+template <int HW, bool FUSE>
 __global__ void __launch_bounds__(256) k_decode_bwd(SceneDev sc, MlpShape S, const float *__restrict__ pk,
                                                     const float *__restrict__ srec, long long nsamp,
                                                     const float *__restrict__ gdec,
                                                         float *__restrict__ g_feat, float *__restrict__ g_offset,
-                                                        float *__restrict__ rows) {
+                                                        float *__restrict__ rows, float *__restrict__ g_mlp) {
     extern __shared__ float4 smem4[];
     float *sm = reinterpret_cast<float *>(smem4);
     const int K = S.K, F = S.F, Hp = S.Hp, H4 = 4 * S.Hp, Rp = S.rb[4];
@@ -523,6 +543,11 @@ __global__ void __launch_bounds__(256) k_decode_bwd(SceneDev sc, MlpShape S, con
     copy_f4(sm + S.s_b1, pk + S.g_b1, H4);
     copy_f4(sm + S.s_b2, pk + S.g_b2, Rp);
     prefetch(WA, pk + S.g_w1t, S.I * H4);
+    float aw1[FUSE ? FW_I : 1], aw2[FUSE ? FW_H : 1], ab1 = 0.f, ab2 = 0.f;  // FUSE: this thread's rows of dW1, dW2
+#pragma unroll
+    for (int b = 0; b < (FUSE ? FW_I : 1); ++b) aw1[b] = 0.f;
+#pragma unroll
+    for (int b = 0; b < (FUSE ? FW_H : 1); ++b) aw2[b] = 0.f;
     for (long long q0 = (long long)blockIdx.x * S.M; q0 < nsamp; q0 += (long long)gridDim.x * S.M) {
         stage_samples(S, sm, sc, srec, nsamp, q0);
         ready(WA, pk + S.g_w1t, S.I * H4);
@@ -712,9 +737,50 @@ __global__ void __launch_bounds__(256) k_decode_bwd(SceneDev sc, MlpShape S, con
                 }
             }
         }
+        if (FUSE) {
+            // dW1 | db1 row t: sum over the tile's samples of dL/dh[t] [z | 1];
+            // dW2 | db2 row t (padded output t of decoder D): dL/do[t] [h_D | 1]
+            const int t = threadIdx.x;
+            const float *Zt = sm + S.s_z;
+            auto row_dot = [&](const float *a, const float *rowsrc, int n_rows, float *acc, int nmax, float &bias) {
+                float d[FW_M];
+#pragma unroll
+                for (int q = 0; q < FW_M / 4; ++q) {
+                    const float4 v = reinterpret_cast<const float4 *>(a)[q];
+                    d[4 * q] = v.x; d[4 * q + 1] = v.y; d[4 * q + 2] = v.z; d[4 * q + 3] = v.w;
+                }
+                float bs = 0.f;
+#pragma unroll
+                for (int q = 0; q < FW_M; ++q) bs += d[q];
+                bias += bs;
+#pragma unroll
+                for (int b = 0; b < nmax; ++b) {
+                    if (b < n_rows) {
+                        const float4 *z4 = reinterpret_cast<const float4 *>(rowsrc + b * S.LD);
+                        float sum = 0.f;
+#pragma unroll
+                        for (int q = 0; q < FW_M / 4; ++q) {
+                            const float4 z = z4[q];
+                            sum = fmaf(d[4 * q], z.x, sum);
+                            sum = fmaf(d[4 * q + 1], z.y, sum);
+                            sum = fmaf(d[4 * q + 2], z.z, sum);
+                            sum = fmaf(d[4 * q + 3], z.w, sum);
+                        }
+                        acc[b] += sum;
+                    }
+                }
+            };
+            if (t < H4) {
+                const int D = t / Hp, j = t - D * Hp;
+                row_dot(DHt + hrow(S, D, j), Zt, S.I, aw1, FUSE ? FW_I : 1, ab1);
+            }
+            if (t < Rp) {
+                const int D = out_block(S, t);
+                row_dot(Ot + orow(S, D, t - S.rb[D]), Ht + hrow(S, D, 0), Hp, aw2, FUSE ? FW_H : 1, ab2);
+            }
+        } else {
         // this tile's rows for the weight gradients, in the tile's own layout
         // (unit rows of M samples: Z, H, dL/dh, dL/do), as float4 copies
-        {
             float *blk = rows + (q0 / S.M) * (long long)S.row_all * S.M;
             const int M4 = S.M >> 2;
             const float *Zt = sm + S.s_z;
@@ -735,6 +801,27 @@ __global__ void __launch_bounds__(256) k_decode_bwd(SceneDev sc, MlpShape S, con
         __syncthreads();
     }
     cp_async_wait<0>();
+    if (FUSE) {  // this CTA's sums into the packed weight gradient (padded rows and columns dropped)
+        const int t = threadIdx.x;
+        if (t < H4) {
+            const int D = t / Hp, j = t - D * Hp;
+            if (j < S.H) {
+#pragma unroll
+                for (int b = 0; b < (FUSE ? FW_I : 1); ++b)
+                    if (b < S.I && aw1[b] != 0.f) atomicAdd(g_mlp + S.w1o[D] + j * S.I + b, aw1[b]);
+                if (ab1 != 0.f) atomicAdd(g_mlp + S.b1o[D] + j, ab1);
+            }
+        }
+        if (t < Rp) {
+            const int D = out_block(S, t), r = t - S.rb[D];
+            if (r < S.nout[D]) {
+#pragma unroll
+                for (int b = 0; b < (FUSE ? FW_H : 1); ++b)
+                    if (b < S.H && aw2[b] != 0.f) atomicAdd(g_mlp + S.w2o[D] + r * S.H + b, aw2[b]);
+                if (ab2 != 0.f) atomicAdd(g_mlp + S.b2o[D] + r, ab2);
+            }
+        }
+    }
 }
 
 // Weight gradients from the per-sample rows:
@@ -858,12 +945,13 @@ static int persistent_grid(Kern k, int threads, size_t smem, long long tiles) {
 }
 
 // Scratch of one decode call: [packed weights][sample records][forward: centres
-// and bounds per Gaussian | adjoint: per-sample rows].
+// and bounds per Gaussian | adjoint: per-sample rows, unless fused].
 long long decode_scratch_floats(int F, int H, int K, long long nsamp, long long G, bool bwd) {
     const MlpShape S = mlp_shape(F, H, K, bwd);
     const long long n = std::max(1LL, nsamp);
     const long long tiles = (n + S.M - 1) / S.M;
-    return up_to(S.g_total, 4) + n * DINFO + (bwd ? (long long)S.row_all * S.M * tiles : 4 * std::max(1LL, G));
+    return up_to(S.g_total, 4) + n * DINFO +
+           (bwd ? (wgrad_fused(S) ? 0LL : (long long)S.row_all * S.M * tiles) : 4 * std::max(1LL, G));
 }
 
 static void decode_prep(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const MlpShape &S,
@@ -903,12 +991,20 @@ void launch_decode_bwd(const ViewDesc *views, int n_views, int slot, const Scene
     decode_prep(views, n_views, slot, sc, S, samples, nsamp, pk, srec, st);
     const size_t smem = sizeof(float) * (size_t)S.s_total;
     const long long tiles = (nsamp + S.M - 1) / S.M;
+    if (wgrad_fused(S)) {
+        const int b = persistent_grid(k_decode_bwd<4, true>, 32 * S.W, smem, tiles);
+        k_decode_bwd<4, true><<<b, 32 * S.W, smem, st>>>(sc, S, pk, srec, nsamp, gdec, g_feat, g_offset, nullptr,
+                                                         g_mlp);
+        return;
+    }
     if (S.HW == 4) {
-        const int b = persistent_grid(k_decode_bwd<4>, 32 * S.W, smem, tiles);
-        k_decode_bwd<4><<<b, 32 * S.W, smem, st>>>(sc, S, pk, srec, nsamp, gdec, g_feat, g_offset, rows);
+        const int b = persistent_grid(k_decode_bwd<4, false>, 32 * S.W, smem, tiles);
+        k_decode_bwd<4, false><<<b, 32 * S.W, smem, st>>>(sc, S, pk, srec, nsamp, gdec, g_feat, g_offset, rows,
+                                                          g_mlp);
     } else {
-        const int b = persistent_grid(k_decode_bwd<8>, 32 * S.W, smem, tiles);
-        k_decode_bwd<8><<<b, 32 * S.W, smem, st>>>(sc, S, pk, srec, nsamp, gdec, g_feat, g_offset, rows);
+        const int b = persistent_grid(k_decode_bwd<8, false>, 32 * S.W, smem, tiles);
+        k_decode_bwd<8, false><<<b, 32 * S.W, smem, st>>>(sc, S, pk, srec, nsamp, gdec, g_feat, g_offset, rows,
+                                                          g_mlp);
     }
     WgProblems pr{};
     pr.p[0] = WgProblem{S.row_dh, 4 * S.Hp, S.row_z, S.I, -1};

@@ -109,11 +109,15 @@ def _neural_oracle_grads(sc, cams, dl_flat, gs, dec):
 
 
 @pytest.mark.parametrize("F,H,K,stretch,location", [(8, 12, 4, 1.0, "device"), (12, 16, 6, 1.6, "host"),
-                                                     (20, 36, 7, 1.0, "device"), (64, 64, 32, 1.2, "device")])
+                                                     (32, 32, 10, 1.0, "device"), (20, 36, 7, 1.0, "device"),
+                                                     (64, 64, 32, 1.2, "device")])
 def test_gradients_through_the_decode(rctx, F, H, K, stretch, location):
     """dL/d(weights, features, offsets) summed over two views against the
     FP64 oracle.  stretch > 1 pushes some offsets outside the unit ball (the
-    projection onto it); host outputs go through the staging path."""
+    projection onto it); host outputs go through the staging path.  The
+    first three shapes take the weight gradients fused into the adjoint's
+    tiles, the last two (a hidden layer wider than 32) the per-sample rows
+    and the separate product."""
     from paper_2508_03180_gb300 import _lib as L
     from oracle import decode as odec
     from tests.test_gpu_grad import assert_close_group
