@@ -757,16 +757,16 @@ __global__ void __launch_bounds__(256) k_decode_bwd(SceneDev sc, MlpShape S, con
                 for (int b = 0; b < nmax; ++b) {
                     if (b < n_rows) {
                         const float4 *z4 = reinterpret_cast<const float4 *>(rowsrc + b * S.LD);
-                        float sum = 0.f;
+                        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;  // four chains: latency, not issue
 #pragma unroll
                         for (int q = 0; q < FW_M / 4; ++q) {
                             const float4 z = z4[q];
-                            sum = fmaf(d[4 * q], z.x, sum);
-                            sum = fmaf(d[4 * q + 1], z.y, sum);
-                            sum = fmaf(d[4 * q + 2], z.z, sum);
-                            sum = fmaf(d[4 * q + 3], z.w, sum);
+                            s0 = fmaf(d[4 * q], z.x, s0);
+                            s1 = fmaf(d[4 * q + 1], z.y, s1);
+                            s2 = fmaf(d[4 * q + 2], z.z, s2);
+                            s3 = fmaf(d[4 * q + 3], z.w, s3);
                         }
-                        acc[b] += sum;
+                        acc[b] += (s0 + s1) + (s2 + s3);
                     }
                 }
             };
