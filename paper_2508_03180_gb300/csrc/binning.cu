@@ -147,42 +147,80 @@ void launch_gather_counts(const uint32_t *zval_sorted, const uint32_t *count, lo
     k_gather_counts<<<grid_for(n, 256), 256, 0, st>>>(zval_sorted, count, n, d_n, out);
 }
 
-// One thread per output slot j: the owning entry e is the last one with
-// offs[e] <= j (binary search), so every thread writes exactly one pair and
-// consecutive threads write consecutive addresses whatever the footprints.
-// Entries are in depth order, so the emitted sequence is (depth, cell)-ordered
-// within every tile; the stable tile sort keeps that order.
-__global__ void __launch_bounds__(256) k_emit(const uint32_t *__restrict__ offs, const uint32_t *__restrict__ zval,
-                                              const short4 *__restrict__ rect, const ViewDesc *__restrict__ views,
-                                              int n_views, long long n_entries, long long L,
-                                              uint32_t *__restrict__ tkey, uint32_t *__restrict__ tval,
-                                              const ChainSizes *__restrict__ dsz, const uint32_t *__restrict__ d_L) {
+// Output slot j belongs to the last entry e with offs[e] <= j.  A block takes
+// runs of EM_TB consecutive slots: thread 0 finds the run's first and last
+// owners by binary search in global memory; when at most EM_TB entries lie
+// between them (always for the depth-sorted cell entries, whose culled ones
+// come last, so every entry in a run owns a slot) their offsets are staged
+// in shared memory and each thread finds its slots' owners there, otherwise
+// (entries that own no slot interleaved, as in the weighted-sum comparator's
+// index order) it searches the run's entries in global memory.  Consecutive
+// threads write consecutive addresses whatever the footprints.  Entries are in depth order, so the emitted sequence is
+// (depth, cell)-ordered within every tile; the stable tile sort keeps that order.
+constexpr int EM_THREADS = 256, EM_ITEMS = 8, EM_TB = EM_THREADS * EM_ITEMS;
+__global__ void __launch_bounds__(EM_THREADS) k_emit(const uint32_t *__restrict__ offs,
+                                                     const uint32_t *__restrict__ zval,
+                                                     const short4 *__restrict__ rect,
+                                                     const ViewDesc *__restrict__ views, int n_views,
+                                                     long long n_entries, long long L, uint32_t *__restrict__ tkey,
+                                                     uint32_t *__restrict__ tval,
+                                                     const ChainSizes *__restrict__ dsz,
+                                                     const uint32_t *__restrict__ d_L) {
+    __shared__ uint32_t s_off[EM_TB];
+    __shared__ long long s_e0, s_ne;
     if (dsz) {
         n_views = dsz->n_views;
         n_entries = dsz->n_entries;
     }
     if (d_L) L = *d_L;
-    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < L; j += (long long)gridDim.x * blockDim.x) {
-        long long lo = 0, hi = n_entries;  // find last e with offs[e] <= j
-        while (hi - lo > 1) {
-            const long long mid = (lo + hi) >> 1;
-            if ((long long)offs[mid] <= j) lo = mid; else hi = mid;
+    for (long long j0 = blockIdx.x * (long long)EM_TB; j0 < L; j0 += (long long)gridDim.x * EM_TB) {
+        const long long j1 = min(j0 + (long long)EM_TB, L);  // this run: [j0, j1)
+        if (threadIdx.x == 0) {
+            auto owner = [&](long long j) {
+                long long lo = 0, hi = n_entries;
+                while (hi - lo > 1) {
+                    const long long mid = (lo + hi) >> 1;
+                    if ((long long)offs[mid] <= j) lo = mid; else hi = mid;
+                }
+                return lo;
+            };
+            const long long e0 = owner(j0);
+            s_e0 = e0;
+            s_ne = owner(j1 - 1) - e0 + 1;
         }
-        const uint32_t vi = zval[lo];
-        int vlo = 0, vhi = n_views;  // view owning entry vi
-        while (vhi - vlo > 1) {
-            const int mid = (vlo + vhi) >> 1;
-            if (views[mid].cell_base <= (long long)vi) vlo = mid; else vhi = mid;
+        __syncthreads();
+        const long long e0 = s_e0, ne = s_ne;  // the run's owners are entries [e0, e0 + ne)
+        const bool staged = ne <= EM_TB;
+        if (staged)
+            for (int i = threadIdx.x; i < (int)ne; i += EM_THREADS) s_off[i] = offs[e0 + i];
+        __syncthreads();
+#pragma unroll 2
+        for (int it = 0; it < EM_ITEMS; ++it) {
+            const long long j = j0 + it * EM_THREADS + threadIdx.x;
+            if (j >= j1) break;
+            long long lo = 0, hi = ne;  // last i in [0, ne) with offs[e0 + i] <= j
+            while (hi - lo > 1) {
+                const long long mid = (lo + hi) >> 1;
+                const uint32_t o = staged ? s_off[mid] : offs[e0 + mid];
+                if ((long long)o <= j) lo = mid; else hi = mid;
+            }
+            const uint32_t base = staged ? s_off[lo] : offs[e0 + lo];
+            const uint32_t vi = zval[e0 + lo];
+            int vlo = 0, vhi = n_views;  // view owning entry vi
+            while (vhi - vlo > 1) {
+                const int mid = (vlo + vhi) >> 1;
+                if (views[mid].cell_base <= (long long)vi) vlo = mid; else vhi = mid;
+            }
+            const ViewDesc &V = views[vlo];
+            const uint32_t cellid = (uint32_t)((long long)vi - V.cell_base);
+            const short4 r = rect[vi];
+            const int w = r.z - r.x + 1;
+            const int local = (int)(j - base);
+            const int ty = r.y + local / w, tx = r.x + local % w;
+            tkey[j] = (uint32_t)(V.tile_base + ty * V.Tx + tx);
+            tval[j] = cellid;
         }
-        const int v = vlo;
-        const uint32_t cellid = (uint32_t)((long long)vi - views[v].cell_base);
-        const short4 r = rect[vi];
-        const int w = r.z - r.x + 1;
-        const int local = (int)(j - offs[lo]);
-        const int ty = r.y + local / w, tx = r.x + local % w;
-        const ViewDesc &V = views[v];
-        tkey[j] = (uint32_t)(V.tile_base + ty * V.Tx + tx);
-        tval[j] = cellid;
+        __syncthreads();  // s_off is refilled for the next run
     }
 }
 
@@ -190,8 +228,8 @@ void launch_emit(const uint32_t *offs, const uint32_t *zval_sorted, const short4
                  int n_views, long long n_entries, long long L, uint32_t *tkey, uint32_t *tval, cudaStream_t st,
                  const ChainSizes *dsz, const uint32_t *d_L) {
     if (L == 0) return;
-    k_emit<<<grid_for(L, 256), 256, 0, st>>>(offs, zval_sorted, rect, views, n_views, n_entries, L, tkey, tval, dsz,
-                                             d_L);
+    k_emit<<<grid_for((L + EM_ITEMS - 1) / EM_ITEMS, EM_THREADS), EM_THREADS, 0, st>>>(
+        offs, zval_sorted, rect, views, n_views, n_entries, L, tkey, tval, dsz, d_L);
 }
 
 // [start, end) of every non-empty tile from the tile-sorted keys; empty
