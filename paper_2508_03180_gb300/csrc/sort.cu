@@ -2,7 +2,8 @@
 // one "onesweep" pass per digit: every CTA ranks a 4096-item partition
 // locally, then learns the global offset of each digit from its predecessors
 // through decoupled look-back (Merrill & Garland single-pass prefix scan,
-// applied per digit as in Adinets & Merrill's Onesweep).  The digit
+// applied per digit as in Adinets & Merrill's Onesweep), and writes the
+// partition out through shared memory in digit order (coalesced runs).  The digit
 // histograms of all passes come from one upfront read of the keys.
 //
 // Sec. IV-B sorts the cell sequence with a radix sort; its cost grows with
@@ -88,6 +89,9 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_pass(uint32_t *__restrict__ k
                                                         uint32_t *__restrict__ err) {
     __shared__ uint32_t s_warp[RS_WARPS][256];   // per-warp digit counts, then per-warp offsets
     __shared__ uint32_t s_base[256];             // global destination of the partition's first item per digit
+    __shared__ uint32_t s_local[256];            // partition-local start of each digit
+    __shared__ uint32_t s_wsum[RS_WARPS];
+    __shared__ uint32_t s_key[RS_TILE], s_val[RS_TILE];  // the partition in digit order
     __shared__ uint32_t s_part;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (d_n) n = *d_n;
@@ -158,6 +162,19 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_pass(uint32_t *__restrict__ k
             s_warp[w][d] = total;
             total += c;
         }
+        {  // partition-local digit starts: exclusive scan of the totals over the 256 digits
+            uint32_t x = total;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (lane == 31) s_wsum[warp] = x;
+            __syncthreads();
+            uint32_t wb = 0;
+            for (int w = 0; w < warp; ++w) wb += s_wsum[w];
+            s_local[d] = wb + x - total;
+        }
         uint32_t *my = status + part * 256 + d;
         if (part == 0) {
             atomicExch(my, FLAG_INC | total);
@@ -181,15 +198,25 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_pass(uint32_t *__restrict__ k
             s_base[d] = digit_base[d] + excl;
         }
         __syncthreads();
+        // the partition in digit order in shared memory, then out with
+        // consecutive threads on consecutive destinations within each digit
 #pragma unroll
         for (int it = 0; it < RS_ITEMS; ++it) {
             const long long idx = base + it * 32 + lane;
             if (idx < n) {
                 const uint32_t dg = (key[it] >> shift) & 255u;
-                const uint32_t dst = s_base[dg] + s_warp[warp][dg] + rank[it];
-                kout[dst] = key[it];
-                vout[dst] = val[it];
+                const uint32_t lp = s_local[dg] + s_warp[warp][dg] + rank[it];
+                s_key[lp] = key[it];
+                s_val[lp] = val[it];
             }
+        }
+        __syncthreads();
+        const int cnt = (int)min((long long)RS_TILE, n - part * RS_TILE);
+        for (int i = tid; i < cnt; i += RS_THREADS) {
+            const uint32_t k = s_key[i], dg = (k >> shift) & 255u;
+            const uint32_t dst = s_base[dg] + ((uint32_t)i - s_local[dg]);
+            kout[dst] = k;
+            vout[dst] = s_val[i];
         }
     }
 }
@@ -209,7 +236,18 @@ __global__ void k_copy_pairs(const uint32_t *__restrict__ ks, const uint32_t *__
     }
 }
 
-constexpr int RS_MAX_CTAS = 152 * 8;  // persistent grid: 8 CTAs of 256 threads per SM
+// Persistent grid: the CTAs of k_rs_pass every SM holds at once (queried once).
+static long long rs_max_ctas() {
+    static long long cap = 0;
+    if (!cap) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rs_pass, RS_THREADS, 0);
+        cap = (long long)std::max(1, sms) * std::max(1, per_sm);
+    }
+    return cap;
+}
 
 int radix_sort_pairs(uint32_t *keys, uint32_t *vals, long long n, int bits, const SortScratch &s, cudaStream_t st,
                      const uint32_t *d_n) {
@@ -227,7 +265,7 @@ int radix_sort_pairs(uint32_t *keys, uint32_t *vals, long long n, int bits, cons
     if (hb > 152 * 8) hb = 152 * 8;
     k_rs_hist<<<hb, RS_THREADS, 0, st>>>(keys, n, d_n, passes, s.hist, status[0]);
     k_rs_hist_scan<<<passes, 256, 0, st>>>(s.hist);
-    const unsigned grid = (unsigned)(parts < RS_MAX_CTAS ? parts : RS_MAX_CTAS);
+    const unsigned grid = (unsigned)std::min(parts, rs_max_ctas());
     const bool skip = d_n != nullptr;  // device-sized: key ranges unknown on the host
     for (int p = 0; p < passes; ++p)
         k_rs_pass<<<grid, RS_THREADS, 0, st>>>(keys, vals, s.keys_alt, s.vals_alt, n, d_n, p, s.hist, skip,
