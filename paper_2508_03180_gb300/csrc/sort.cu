@@ -23,6 +23,7 @@ constexpr int RS_THREADS = 256;
 constexpr int RS_WARPS = RS_THREADS / 32;
 constexpr int RS_ITEMS = 16;                       // per thread
 constexpr int RS_TILE = RS_THREADS * RS_ITEMS;      // 4096 items per partition
+static_assert(RS_TILE == kSortPartition, "the partition size is shared with the fixed scratch of sort_noalloc.cu");
 constexpr int RS_WARP_ITEMS = 32 * RS_ITEMS;        // 512 contiguous items per warp
 constexpr uint32_t FLAG_AGG = 1u << 30;             // partition's own count published
 constexpr uint32_t FLAG_INC = 2u << 30;             // inclusive prefix published
