@@ -18,7 +18,7 @@
 namespace {
 
 constexpr long long kMaxItems = 1LL << 20;                // 1,048,576 pairs per call at most
-constexpr long long kMaxParts = (kMaxItems + kSortPartition - 1) / kSortPartition;  // sort partitions
+constexpr long long kMaxParts = (kMaxItems + dgs::kSortPartition - 1) / dgs::kSortPartition;  // sort partitions
 // layout of the scratch array, in 32-bit words
 constexpr size_t kOffKeys = 0;
 constexpr size_t kOffVals = kOffKeys + kMaxItems;
