@@ -348,7 +348,7 @@ dgs_status dgs_profile_read(dgs_ctx *ctx, dgs_profile *out);
  * keys/vals device pointers sorted in place, no context needed), except:
  *   * n is at most 1,048,576; a larger n returns DGS_ERR_CAPACITY before any
  *     work is enqueued.
- *   * Scratch is a fixed file-scope device array (about 8.6 MB) that every
+ *   * Scratch is a fixed file-scope device array (about 9.1 MB) that every
  *     GPU loading this library holds until the process exits; this call
  *     calls no cudaMalloc, cudaFree or other allocating routine.
  *   * The first call on a device looks up that array's device address

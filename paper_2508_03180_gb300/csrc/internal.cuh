@@ -10,7 +10,7 @@
 namespace dgs {
 
 constexpr int kTile = 16;          // tile edge in pixels (Sec. IV-B tile-based paradigm)
-constexpr int kSortPartition = 4096;  // items per radix-sort partition (sort.cu; sizes the look-back words)
+constexpr int kSortPartition = 3072;  // items per radix-sort partition (sort.cu; sizes the look-back words)
 constexpr int kTilePix = kTile * kTile;
 constexpr int kMaxK = 32;          // Gaussians per cell supported
 constexpr int kRecF4 = 3;          // float4s per projected-Gaussian record (48 B)

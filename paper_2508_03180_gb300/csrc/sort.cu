@@ -1,5 +1,5 @@
 // Stable LSD radix sort of (uint32 key, uint32 value) pairs, 8-bit digits,
-// one "onesweep" pass per digit: every CTA ranks a 4096-item partition
+// one "onesweep" pass per digit: every CTA ranks a 3072-item partition
 // locally, then learns the global offset of each digit from its predecessors
 // through decoupled look-back (Merrill & Garland single-pass prefix scan,
 // applied per digit as in Adinets & Merrill's Onesweep), and writes the
@@ -21,10 +21,10 @@ namespace dgs {
 
 constexpr int RS_THREADS = 256;
 constexpr int RS_WARPS = RS_THREADS / 32;
-constexpr int RS_ITEMS = 16;                       // per thread
-constexpr int RS_TILE = RS_THREADS * RS_ITEMS;      // 4096 items per partition
+constexpr int RS_ITEMS = 12;                       // per thread
+constexpr int RS_TILE = RS_THREADS * RS_ITEMS;      // 3072 items per partition
 static_assert(RS_TILE == kSortPartition, "the partition size is shared with the fixed scratch of sort_noalloc.cu");
-constexpr int RS_WARP_ITEMS = 32 * RS_ITEMS;        // 512 contiguous items per warp
+constexpr int RS_WARP_ITEMS = 32 * RS_ITEMS;        // 384 contiguous items per warp
 constexpr uint32_t FLAG_AGG = 1u << 30;             // partition's own count published
 constexpr uint32_t FLAG_INC = 2u << 30;             // inclusive prefix published
 constexpr uint32_t COUNT_MASK = (1u << 30) - 1;

@@ -26,7 +26,7 @@ constexpr size_t kOffHist = kOffVals + kMaxItems;          // 4 passes x 256 dig
 constexpr size_t kOffStatus = kOffHist + 4 * 256;          // 2 x kMaxParts x 256 look-back words
 constexpr size_t kOffCounters = kOffStatus + 2 * kMaxParts * 256;
 constexpr size_t kOffErr = kOffCounters + 4;
-constexpr size_t kWords = kOffErr + 60;                    // about 8.6 MB in total
+constexpr size_t kWords = kOffErr + 60;                    // about 9.1 MB in total
 
 // Device-side scratch.  In host code this name is only a stand-in: its
 // device address comes from cudaGetSymbolAddress, per device.

@@ -186,7 +186,8 @@ def test_host_output_matches_device_output(rctx):
     rctx.release_scene(sid)
 
 
-@pytest.mark.parametrize("n,bits", [(0, 8), (1, 32), (4096, 32), (4097, 13), (1_000_003, 32), (300_001, 17)])
+@pytest.mark.parametrize("n,bits", [(0, 8), (1, 32), (3072, 32), (3073, 13), (6145, 9), (4096, 32), (4097, 13),
+                                    (1_000_003, 32), (300_001, 17)])
 def test_radix_sort_pairs_stable(rctx, n, bits):
     g = torch.Generator().manual_seed(n + bits)
     keys = torch.randint(0, 2 ** 31, (n,), generator=g, dtype=torch.int64)
