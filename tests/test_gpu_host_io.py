@@ -77,6 +77,16 @@ def test_backward_host_outputs_match_device(rctx):
     dl_np = dl.cpu().numpy().copy()
     got = _backward(rctx, state, dl_np.ctypes.data, L.DGS_HOST, pinned, L.DGS_HOST)
     _same_grads(got, ref, "pageable dL, pinned outputs")
+    # outputs that are views into one page-locked buffer (pointers inside an allocation)
+    flat = torch.full((sum(int(np.prod(v)) for v in shapes.values()) + 1,), 7.0).pin_memory()
+    views, o = {}, 1  # start one float in, so no output begins at the allocation's base
+    for k, shp in shapes.items():
+        n = int(np.prod(shp))
+        views[k] = flat[o:o + n].view(shp)
+        o += n
+    got = _backward(rctx, state, dl.data_ptr(), L.DGS_DEVICE, views, L.DGS_HOST)
+    _same_grads(got, ref, "views of one pinned buffer")
+    assert flat[0].item() == 7.0  # nothing written outside the outputs
     rctx.release_state(state)
     rctx.release_scene(sid)
 
