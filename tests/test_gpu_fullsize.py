@@ -51,7 +51,8 @@ def _check_band(scene, cam, gv, img, rows):
     # pixels where the FP64 oracle's own stopping cell differs from the GPU's
     # (both valid within the relative slack on T): a rounding statistic
     diff = int((r["ndone"][y0:y1] != gv["nd"][y0:y1]).sum())
-    assert diff <= max(2, int(5e-4 * n_px))
+    print(f"band rows {rows}: {diff} of {n_px} pixels stop at a different cell in the oracle's own rule")
+    assert diff <= max(1, int(1e-4 * n_px)), (diff, n_px)
     err = float(np.abs(img.reshape(3, H, W)[:, y0:y1] - r["C"][:, y0:y1]).max())
     assert err <= IMG_TOL, err
     return err

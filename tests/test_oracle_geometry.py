@@ -209,3 +209,103 @@ def test_tile_lists_match_per_tile_scan():
     vis = rect[:, 0] >= 0
     assert (rect[vis, 0] <= rect[vis, 2]).all() and (rect[vis, 2] < Tx).all()
     assert (rect[vis, 1] <= rect[vis, 3]).all() and (rect[vis, 3] < Ty).all()
+
+
+def _axis_camera(W, H):
+    """Camera at the origin looking along +z with R = I (view space = world
+    space), vertical FOV 60 deg."""
+    cam = synth.look_at((0.0, 0.0, 0.0), (0.0, 0.0, 1.0), W, H, 60.0, up=(0.0, -1.0, 0.0))
+    assert np.allclose(cam.R, np.eye(3)) and np.allclose(cam.t, 0.0)
+    return cam.as_array()
+
+
+@pytest.mark.parametrize("W,H", [(320, 240), (180, 300)])
+def test_ewa_jacobian_clamp_outside_the_view(W, H):
+    """Eq. 2's projected kernel with the EWA reading: the Jacobian of the
+    pinhole map is taken at the point of the same depth whose view direction
+    is clamped per axis to 1.3 x the tangent of that axis' half field of view.
+    The limits come from the camera's construction (vertical FOV 60 deg,
+    square pixels, so tan(half FOV_x) = tan(30 deg) W / H), the Jacobian from
+    central differences of the pinhole map at the clamped point, and the
+    covariance from the Hamilton sandwich rotation: none of it from the
+    oracle.  Directions inside, between the two axes' limits, and beyond
+    them, on both sides; the screen mean itself stays unclamped."""
+    cam = _axis_camera(W, H)
+    ty = math.tan(math.radians(30.0))
+    lim = np.array([1.3 * ty * W / H, 1.3 * ty])
+    lo, hi = lim.min(), lim.max()
+    # ratios t_x/t_z and t_y/t_z relative to each axis' own limit, plus ones
+    # that lie between the smaller and the larger limit (they tell the axes apart)
+    rel = np.array([-3.0, -1.2, -0.97, 0.0, 0.4, 0.96, 1.04, 2.5])
+    between = 0.5 * (lo + hi)
+    rng = np.random.default_rng(11)
+    pts = []
+    for rx in list(rel * lim[0]) + [between, -between]:
+        for ry in list(rel * lim[1]) + [between, -between]:
+            z = rng.uniform(1.0, 6.0)
+            pts.append([rx * z, ry * z, z])
+    tv = np.array(pts)
+    G = len(tv)
+    scale = np.exp(rng.normal(np.log(0.2), 0.5, (G, 3)))
+    quat = rng.standard_normal((G, 4))
+    out = P.project(torch.tensor(tv), torch.tensor(scale), torch.tensor(quat), torch.zeros(G),
+                    torch.zeros(G, 1, 3, dtype=torch.float64), 0, cam)
+    cov2 = out["cov2"].numpy()
+    mu2 = out["mu2"].numpy()
+    c = P.camera_tensors(cam)
+    h = 1e-6
+    clamped = 0
+    for g in range(G):
+        t = tv[g]
+        r = np.clip(t[:2] / t[2], -lim, lim)
+        clamped += int(np.any(np.abs(t[:2] / t[2]) > lim))
+        tc = np.array([r[0] * t[2], r[1] * t[2], t[2]])
+        J = np.zeros((2, 3))
+        for j in range(3):
+            e = np.zeros(3); e[j] = h * max(1.0, abs(tc[j]))
+            J[:, j] = (_pinhole(cam, tc + e) - _pinhole(cam, tc - e)) / (2 * e[j])
+        Rq = np.stack([_sandwich(quat[g], e) for e in np.eye(3)], 1)
+        Sigma = Rq @ np.diag(scale[g] ** 2) @ Rq.T
+        S2 = J @ Sigma @ J.T
+        ref = [S2[0, 0] + 0.3, S2[0, 1], S2[1, 1] + 0.3]
+        np.testing.assert_allclose(cov2[g], ref, rtol=1e-6, atol=1e-8 * abs(S2).max(), err_msg=str(t))
+        np.testing.assert_allclose(mu2[g], _pinhole(cam, t), rtol=1e-12)
+    assert clamped > G // 2 and clamped < G
+
+
+def test_colour_clamp_at_zero():
+    """Reading 8: c = max(0, 0.5 + sum_lm k_lm Y_lm(d)).  The raw sum is
+    evaluated with SciPy's spherical harmonics at d = (mu - eye)/|mu - eye|;
+    a channel whose raw value is negative is exactly 0 with zero gradient to
+    its coefficients and to the mean, and a positive one equals the raw value
+    with gradient Y_lm(d) to k_lm."""
+    rng = np.random.default_rng(4)
+    G = 400
+    cam = synth.small_camera(64, 64).as_array()
+    mean = rng.uniform(-1.0, 1.0, (G, 3))
+    sh = rng.normal(0.0, 0.3, (G, 16, 3))
+    sh[:, 0, :] = rng.uniform(-2.0, 1.0, (G, 3))  # DC pushes many channels below zero
+    sh[:3, 0, :] = -5.0                               # three Gaussians negative in every channel
+    eye = cam[19:22].astype(np.float64)
+    d = mean - eye
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    theta = np.arccos(np.clip(d[:, 2], -1, 1))
+    phi = np.arctan2(d[:, 1], d[:, 0])
+    Y = np.stack([_real_sh_scipy(l, m, theta, phi) for l in range(4) for m in range(-l, l + 1)], 1)
+    raw = 0.5 + np.einsum("gc,gck->gk", Y, sh)
+    neg = raw < 0.0
+    assert 0.2 < neg.mean() < 0.8 and np.abs(raw).min() > 1e-9
+    mt = torch.tensor(mean, requires_grad=True)
+    st = torch.tensor(sh, requires_grad=True)
+    out = P.project(mt, torch.full((G, 3), 0.05, dtype=torch.float64), torch.tensor([[1.0, 0, 0, 0]] * G),
+                    torch.zeros(G, dtype=torch.float64), st, 3, cam)
+    rgb = out["rgb"]
+    assert torch.all(rgb.detach()[torch.tensor(neg)] == 0.0)
+    np.testing.assert_allclose(rgb.detach().numpy()[~neg], raw[~neg], atol=1e-12)
+    for k in range(3):
+        gm, gs = torch.autograd.grad(rgb[:, k].sum(), (mt, st), retain_graph=True)
+        gs = gs.numpy()[:, :, k]
+        assert np.all(gs[neg[:, k]] == 0.0)
+        np.testing.assert_allclose(gs[~neg[:, k]], Y[~neg[:, k]], atol=1e-12)
+        assert np.all(gm.numpy()[neg[:, k]] == 0.0)
+    assert np.all(neg[:3])
