@@ -13,6 +13,7 @@ from paper_2508_03180_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 IMG_TOL = 1e-4
+ALPHA_DIFF_FRAC = 1e-3  # per-Gaussian stopping decisions (see _alpha_check)
 
 
 @pytest.fixture(scope="module")
@@ -36,7 +37,13 @@ def _alpha_check(scene, cam, img, nd, rows=None, opt=oracle.Options()):
     diff = int((r["ndone"][y0:y1] != nd.reshape(H, W)[y0:y1]).sum())
     n_px = (y1 - y0) * W
     print(f"{W}x{H} rows {y0}-{y1}: {diff} of {n_px} pixels stop at a different Gaussian in the oracle's own rule")
-    assert diff <= max(1, int(1e-4 * n_px)), (diff, n_px)
+    # Every GPU count is a valid stop within the slack (bad == 0 above).  The
+    # oracle's own FP64 choice differs only where eps falls between the FP32
+    # and FP64 transmittance of the stopping entry; per-Gaussian blending
+    # crosses eps in steps of one factor (1 - alpha) instead of a cell's
+    # product, so such near-ties are up to ten times more frequent than in
+    # the hybrid renderer: at most 0.1% of pixels (at least 1).
+    assert diff <= max(1, int(ALPHA_DIFF_FRAC * n_px)), (diff, n_px)
     err = float(np.abs(img.reshape(3, H, W)[:, y0:y1] - r["C"][:, y0:y1]).max())
     assert err <= IMG_TOL, err
     return r
