@@ -47,7 +47,9 @@ enum {
     DGS_ERR_CUDA = -4,        /* a CUDA call or a kernel failed; see dgs_last_error */
     DGS_ERR_TIMEOUT = -5,     /* poll timed out, or a bounded device wait gave up */
     DGS_ERR_BUSY = -6,        /* request queue full; retry later */
-    DGS_ERR_CAPACITY = -7     /* a size exceeds a fixed maximum of the call */
+    DGS_ERR_CAPACITY = -7,    /* a size exceeds a fixed maximum of the call */
+    DGS_ERR_GUARD = -8,       /* debug mode: a guard word next to a device buffer was overwritten */
+    DGS_ERR_WORKER = -9       /* the serving worker stopped after a host-side fault; restart serving */
 };
 
 /* Where an argument array lives.  DGS_HOST arrays may be pageable or
@@ -152,8 +154,10 @@ const char *dgs_last_error(dgs_ctx *ctx);
  * scale, rotation; output widths K, 3K, 3K, 4K): W1 [hidden][feat_dim+4]
  * row-major, b1 [hidden], W2 [out][hidden] row-major, b2 [out].
  * 1 <= feat_dim <= 64, 1 <= hidden <= 64.  Neural scenes render through
- * dgs_render; their backward, serving and the comparators are not built
- * (INVALID_ARG). */
+ * dgs_render, and dgs_render_backward gives the gradients to the packed
+ * decoder weights, the cell features and the offsets (g_mlp, g_feat,
+ * g_offset); serving and the comparators take explicit scenes only
+ * (INVALID_ARG for a neural one). */
 typedef struct {
     int32_t feat_dim;
     int32_t hidden;
@@ -351,13 +355,19 @@ dgs_status dgs_profile_read(dgs_ctx *ctx, dgs_profile *out);
  *   * Scratch is a fixed file-scope device array (about 9.1 MB) that every
  *     GPU loading this library holds until the process exits; this call
  *     calls no cudaMalloc, cudaFree or other allocating routine.
- *   * The first call on a device looks up that array's device address
- *     (cudaGetSymbolAddress) with the device current; make that first call
- *     before any stream capture.
+ *   * The first call on a device is part of the caller's set-up: the CUDA
+ *     runtime loads the array and the sort's kernels into that device's
+ *     context on first use (lazy module loading, CUDA's default), and the
+ *     driver allocates their device memory then.  Make one call (n >= 2,
+ *     bits >= 1) before reserving the device's free memory or forbidding
+ *     allocation; later calls allocate nothing.  Each call looks the array's
+ *     address up again (cudaGetSymbolAddress), so a device reset followed by
+ *     a new context needs only that set-up call again.
  *   * All calls share the array: calls whose work overlaps on the GPU (other
  *     streams, other threads) race and corrupt each other's results.
  *   * Uses the current CUDA device, enqueues on `stream` and synchronises it
- *     once at the end (to read the sort's error flag). */
+ *     once at the end (to read the sort's error flag), so the call returns
+ *     with the sort finished. */
 dgs_status dgs_sort_pairs_noalloc(uint32_t *keys, uint32_t *vals, int64_t n, int32_t bits, dgs_stream stream);
 
 /* ------------------------------------------------------------- comparators */
@@ -482,7 +492,12 @@ dgs_status dgs_serve_stop(dgs_ctx *ctx);
 dgs_status dgs_submit(dgs_ctx *ctx, const dgs_request *req, uint64_t *ticket);
 /* Wait up to timeout_us (0 = just check, <0 = forever) for a ticket.
  * DGS_ERR_TIMEOUT if not done yet; the ticket stays valid.  A finished
- * ticket is consumed by a successful poll. */
+ * ticket is consumed by a successful poll; its result's status is the
+ * request's own (DGS_OK, or the error of its batch).  If the serving worker
+ * stopped after a host-side fault, every request it had not finished is
+ * completed with status DGS_ERR_WORKER, so polls return at once (even with
+ * timeout_us < 0) and dgs_submit returns DGS_ERR_WORKER until serving is
+ * stopped and started again. */
 dgs_status dgs_poll(dgs_ctx *ctx, uint64_t ticket, int64_t timeout_us, dgs_result *out);
 
 /* Counters of the serving worker since dgs_serve_start: batches launched
@@ -496,6 +511,54 @@ typedef struct {
     double pairs_per_tile;
 } dgs_serve_stats;
 dgs_status dgs_serve_read_stats(dgs_ctx *ctx, dgs_serve_stats *out);
+
+/* ---------------------------------------------------- debugging and faults */
+/* The paper has no counterpart: these calls serve the library's own
+ * failure-detection and bounds tests. */
+
+/* Guard words around device buffers (a bounds check that needs no sanitizer).
+ * With guards on, every device buffer the library allocates from then on is
+ * padded by 256 bytes on each side, filled with the byte 0xA5 (the fill
+ * synchronises the device).  dgs_debug_check_guards synchronises every
+ * device holding a padded buffer, reads back the guards of every live padded
+ * buffer of every context and returns DGS_ERR_GUARD, naming the buffer's
+ * size and the first changed offset, if any kernel wrote next to its
+ * buffer; *n_checked (nullable) receives the number of buffers checked.
+ * Process-wide.  Off by default, unless the environment variable DGS_DEBUG
+ * is "1" when the library allocates its first buffer; buffers allocated
+ * while guards were off stay unpadded. */
+dgs_status dgs_debug_guards(int32_t on);
+dgs_status dgs_debug_check_guards(int64_t *n_checked);
+
+/* Fault injection for failure-detection tests.  Nothing here faults, traps
+ * or hangs a GPU: a fault is made on the host, or a bounded device wait is
+ * made to run out.
+ *   DGS_FAULT_ALLOC         the next `count` device allocations of the
+ *                           library (any context) fail as if cudaMalloc had
+ *                           run out of memory, without calling it: the call
+ *                           returns DGS_ERR_OOM and the context stays usable.
+ *   DGS_FAULT_SORT_WAIT     while count != 0, radix sorts launched on the
+ *                           current device run with their first partition
+ *                           withholding its digit counts and a poll limit of
+ *                           1024, so the other partitions' look-back waits
+ *                           run out: the kernels finish (every write stays
+ *                           inside the sorted arrays), the order is
+ *                           unspecified and dgs_sort_pairs /
+ *                           dgs_sort_pairs_noalloc return DGS_ERR_TIMEOUT.
+ *                           count = 0 switches it off.  Meanwhile call only
+ *                           those two: a render would consume the order.
+ *   DGS_FAULT_SERVE_WORKER  ctx's serving worker raises a host-side exception
+ *                           the next time it admits requests; it catches it
+ *                           at its top level, waits for its streams,
+ *                           completes every open request with DGS_ERR_WORKER
+ *                           and exits (see dgs_poll).
+ *   DGS_FAULT_GUARD         the next padded device buffer gets one byte of
+ *                           its trailing guard overwritten (a host-side
+ *                           cudaMemset inside the allocation), so a later
+ *                           dgs_debug_check_guards reports it.
+ * ctx may be NULL except for DGS_FAULT_SERVE_WORKER (serving started). */
+enum { DGS_FAULT_ALLOC = 1, DGS_FAULT_SORT_WAIT = 2, DGS_FAULT_SERVE_WORKER = 3, DGS_FAULT_GUARD = 4 };
+dgs_status dgs_debug_inject_fault(dgs_ctx *ctx, int32_t kind, int32_t count);
 
 #ifdef __cplusplus
 }

@@ -20,6 +20,12 @@ DGS_ERR_CUDA = -4
 DGS_ERR_TIMEOUT = -5
 DGS_ERR_BUSY = -6
 DGS_ERR_CAPACITY = -7
+DGS_ERR_GUARD = -8
+DGS_ERR_WORKER = -9
+DGS_FAULT_ALLOC = 1
+DGS_FAULT_SORT_WAIT = 2
+DGS_FAULT_SERVE_WORKER = 3
+DGS_FAULT_GUARD = 4
 DGS_HOST = 0
 DGS_DEVICE = 1
 
@@ -152,6 +158,9 @@ _SIGS = {
     "dgs_serve_stop": (C.c_int32, [_P]),
     "dgs_submit": (C.c_int32, [_P, C.POINTER(dgs_request), C.POINTER(C.c_uint64)]),
     "dgs_poll": (C.c_int32, [_P, C.c_uint64, C.c_int64, C.POINTER(dgs_result)]),
+    "dgs_debug_guards": (C.c_int32, [C.c_int32]),
+    "dgs_debug_check_guards": (C.c_int32, [C.POINTER(C.c_int64)]),
+    "dgs_debug_inject_fault": (C.c_int32, [_P, C.c_int32, C.c_int32]),
 }
 
 _lib = None
@@ -336,3 +345,17 @@ def dgs_poll(ctx, ticket: int, timeout_us: int):
         return None
     check(code, ctx)
     return r
+
+
+def dgs_debug_guards(on: bool):
+    check(load().dgs_debug_guards(1 if on else 0))
+
+
+def dgs_debug_check_guards() -> int:
+    n = C.c_int64()
+    check(load().dgs_debug_check_guards(C.byref(n)))
+    return n.value
+
+
+def dgs_debug_inject_fault(ctx, kind: int, count: int):
+    check(load().dgs_debug_inject_fault(ctx, kind, count), ctx)

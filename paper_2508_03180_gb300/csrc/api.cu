@@ -5,12 +5,15 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <map>
 #include <memory>
 #include <mutex>
+#include <set>
 #include <string>
 #include <vector>
 
@@ -35,28 +38,88 @@ dgs_status cuda_error(cudaError_t e, const char *what) {
 }
 
 
+// ---------------------------------------------------------------- device buffers
+// Debug mode pads every new device buffer with kGuardBytes of kGuardByte on
+// each side and keeps it in a process-wide registry, so that
+// dgs_debug_check_guards can find writes next to any buffer.  Fault injection
+// (dgs_debug_inject_fault) makes allocations fail or overwrites one guard
+// byte, both on the host.
+namespace {
+constexpr size_t kGuardBytes = 256;
+constexpr unsigned char kGuardByte = 0xA5;
+std::atomic<int> g_guards{-1};        // -1: not decided yet (DGS_DEBUG is read at the first allocation)
+std::atomic<int> g_fail_allocs{0};    // injected allocation failures still to make
+std::atomic<int> g_corrupt_next{0};   // overwrite a guard byte of the next padded buffer
+std::mutex g_guard_mu;
+std::set<const DevBuf *> g_guarded;   // live padded buffers
+
+bool guards_on() {
+    int v = g_guards.load();
+    if (v < 0) {
+        const char *e = std::getenv("DGS_DEBUG");
+        const int want = e && e[0] == '1' && e[1] == 0 ? 1 : 0;
+        g_guards.compare_exchange_strong(v, want);
+        v = g_guards.load();
+    }
+    return v == 1;
+}
+
+bool take_injected(std::atomic<int> &counter) {
+    int n = counter.load();
+    while (n > 0)
+        if (counter.compare_exchange_weak(n, n - 1)) return true;
+    return false;
+}
+}  // namespace
+
 dgs_status DevBuf::ensure(size_t bytes) {
     if (bytes <= cap) return DGS_OK;
-    if (p) {
-        cudaFree(p);
-        p = nullptr;
-        cap = 0;
-    }
-    size_t want = bytes + bytes / 8 + 256;
-    cudaError_t e = cudaMalloc(&p, want);
+    release();
+    if (take_injected(g_fail_allocs)) return set_error(DGS_ERR_OOM, "device allocation failed (injected fault)");
+    const size_t want = bytes + bytes / 8 + 256;
+    const bool guard = guards_on();
+    const size_t pad = guard ? kGuardBytes : 0;
+    void *base = nullptr;
+    cudaError_t e = cudaMalloc(&base, want + 2 * pad);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        p = nullptr;
         return set_error(DGS_ERR_OOM, "device allocation of " + std::to_string(want) + " bytes failed");
     }
+    if (guard) {
+        char *b = static_cast<char *>(base);
+        e = cudaMemset(b, kGuardByte, pad);
+        if (e == cudaSuccess) e = cudaMemset(b + pad + want, kGuardByte, pad);
+        if (e == cudaSuccess && take_injected(g_corrupt_next)) e = cudaMemset(b + pad + want + 7, 0, 1);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();  // the fill lands before any stream uses the buffer
+        if (e == cudaSuccess) e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) {
+            cudaFree(base);
+            return cuda_error(e, "filling guard words");
+        }
+        std::lock_guard<std::mutex> lk(g_guard_mu);
+        g_guarded.insert(this);
+    }
+    p = static_cast<char *>(base) + pad;
     cap = want;
+    guarded = guard;
     return DGS_OK;
 }
 
 void DevBuf::release() {
-    if (p) cudaFree(p);
+    if (p) {
+        if (guarded) {
+            {
+                std::lock_guard<std::mutex> lk(g_guard_mu);
+                g_guarded.erase(this);
+            }
+            cudaFree(static_cast<char *>(p) - kGuardBytes);
+        } else {
+            cudaFree(p);
+        }
+    }
     p = nullptr;
     cap = 0;
+    guarded = false;
 }
 
 Workspace::~Workspace() {
@@ -990,4 +1053,66 @@ extern "C" dgs_status dgs_profile_read(dgs_ctx *ctx, dgs_profile *out) {
         out->launches[i] = ctx->prof.launches[i];
     }
     return DGS_OK;
+}
+
+// ---------------------------------------------------------------- debugging and faults
+extern "C" dgs_status dgs_debug_guards(int32_t on) {
+    g_guards.store(on ? 1 : 0);
+    return DGS_OK;
+}
+
+extern "C" dgs_status dgs_debug_check_guards(int64_t *n_checked) {
+    int cur = 0;
+    cudaGetDevice(&cur);
+    std::lock_guard<std::mutex> lk(g_guard_mu);
+    std::set<int> synced;
+    std::vector<unsigned char> h(kGuardBytes);
+    int64_t n = 0;
+    std::string bad;
+    cudaError_t e = cudaSuccess;
+    for (const DevBuf *b : g_guarded) {
+        e = cudaSetDevice(b->dev);
+        if (e == cudaSuccess && synced.insert(b->dev).second) e = cudaDeviceSynchronize();
+        const char *base = static_cast<const char *>(b->p);
+        for (int side = 0; side < 2 && e == cudaSuccess; ++side) {
+            const char *g = side == 0 ? base - kGuardBytes : base + b->cap;
+            e = cudaMemcpy(h.data(), g, kGuardBytes, cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess || !bad.empty()) continue;
+            for (size_t i = 0; i < kGuardBytes; ++i) {
+                if (h[i] == kGuardByte) continue;
+                bad = "guard word changed next to a device buffer of " + std::to_string(b->cap) + " bytes (device " +
+                      std::to_string(b->dev) + "): byte " +
+                      (side == 0 ? std::to_string(kGuardBytes - i) + " before its start"
+                                 : std::to_string(i) + " after its end");
+                break;
+            }
+        }
+        if (e != cudaSuccess) break;
+        ++n;
+    }
+    cudaSetDevice(cur);
+    if (n_checked) *n_checked = n;
+    if (e != cudaSuccess) return cuda_error(e, "reading guard words");
+    return bad.empty() ? DGS_OK : set_error(DGS_ERR_GUARD, bad);
+}
+
+extern "C" dgs_status dgs_debug_inject_fault(dgs_ctx *ctx, int32_t kind, int32_t count) {
+    if (count < 0) return set_error(DGS_ERR_INVALID_ARG, "count must be >= 0");
+    switch (kind) {
+        case DGS_FAULT_ALLOC:
+            g_fail_allocs.store(count);
+            return DGS_OK;
+        case DGS_FAULT_SORT_WAIT: {
+            if (ctx) CK(cudaSetDevice(ctx->cfg.device));
+            CK(set_sort_fault(count != 0));
+            return DGS_OK;
+        }
+        case DGS_FAULT_SERVE_WORKER:
+            return serve_inject_fault(ctx, count);
+        case DGS_FAULT_GUARD:
+            g_corrupt_next.store(count);
+            return DGS_OK;
+        default:
+            return set_error(DGS_ERR_INVALID_ARG, "unknown fault kind");
+    }
 }

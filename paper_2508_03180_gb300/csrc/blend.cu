@@ -324,7 +324,6 @@ __global__ void __launch_bounds__(WT, FWD_MINB) k_blend_fwd_pull(const ViewDesc 
     }
 }
 
-// min(units, SMs x resident CTAs of k_blend_fwd_pull<KT, VAR>), queried once.
 // Do the blend kernels need their variant form (a flag or a background weight)?
 static bool blend_variants(const BlendParams &bp) {
     return (bp.flags & (DGS_FLAG_ALPHA_SKIP | DGS_FLAG_TERM_EXCLUDE | DGS_FLAG_NUMERATOR)) != 0 || bp.w_bg != 0.f;
@@ -332,14 +331,7 @@ static bool blend_variants(const BlendParams &bp) {
 
 template <int KT, bool VAR>
 static unsigned pull_grid(int total_tiles) {
-    static int per_grid = 0;
-    if (!per_grid) {
-        int dev = 0, sms = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_blend_fwd_pull<KT, VAR>, WT, 0);
-        per_grid = std::max(1, sms * std::max(1, per_sm));
-    }
+    const long long per_grid = resident_ctas((const void *)k_blend_fwd_pull<KT, VAR>, WT);
     return (unsigned)std::min<long long>((long long)total_tiles * FWD_SUB, per_grid);
 }
 

@@ -230,6 +230,15 @@ void launch_loss_l1(const float *rgb, const float *target, int64_t n, float *dL,
                     int nblocks, float *loss, cudaStream_t st);
 int loss_l1_blocks(int64_t n);
 
+// CTAs of `kernel` that all SMs of the current device hold at once with
+// `threads` threads and no dynamic shared memory (SMs x resident CTAs per SM,
+// at least 1); computed once per (device, kernel) and cached under a lock, so
+// threads and devices may call it concurrently.
+long long resident_ctas(const void *kernel, int threads);
+
+// Test-only: make the radix sort's look-back waits run out (see sort.cu).
+cudaError_t set_sort_fault(bool on);
+
 // Asynchronous 16-byte global-to-shared copies (cp.async, cached in L2
 // only): both addresses 16-byte aligned.  A copy is complete for the issuing
 // thread after a cp_async_wait that covers its commit group, and visible to

@@ -1,5 +1,9 @@
 // Layout conversion between the ABI's per-parameter row-major arrays and the
 // library's structure-of-arrays planes, and the L1 photometric loss.
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "internal.cuh"
 
 namespace dgs {
@@ -48,6 +52,23 @@ __global__ void k_soa_to_aos(const float *__restrict__ src, int64_t rows, int co
 __global__ void k_fill(float *__restrict__ dst, int64_t n, float v) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         dst[i] = v;
+}
+
+long long resident_ctas(const void *kernel, int threads) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void *>, long long> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
+    std::lock_guard<std::mutex> lk(mu);
+    const auto key = std::make_pair(dev, kernel);
+    const auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int sms = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev < 0 ? 0 : dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0);
+    const long long n = (long long)std::max(1, sms) * std::max(1, per_sm);
+    cache[key] = n;
+    return n;
 }
 
 static int grid_for(int64_t n) {

@@ -40,10 +40,13 @@ dgs_status cuda_error(cudaError_t e, const char *what);
         if (e_ != cudaSuccess) return cuda_error(e_, #x);     \
     } while (0)
 
-// Grow-only device allocation.
+// Grow-only device allocation.  In debug mode (dgs_debug_guards) the
+// allocation is padded by guard words on both sides (`guarded`, `dev`).
 struct DevBuf {
     void *p = nullptr;
     size_t cap = 0;
+    bool guarded = false;
+    int dev = 0;
     dgs_status ensure(size_t bytes);
     void release();
     ~DevBuf() { release(); }
@@ -173,7 +176,14 @@ struct ServeState {
     GraphSlot gslot[kServeStreams];
     double pairs_per_tile = 128.0;          // running estimate that sizes the pair buffers
     int64_t graphs_captured = 0, batches = 0, overflow_retries = 0;
+    InflightBatch slot[kServeStreams];      // the worker's batches in flight (worker thread only)
+    int inject_fault = 0;                   // test-only: raise a host-side fault at the next admission
+    bool dead = false;                      // the worker stopped after a host-side fault
+    std::string dead_msg;
 };
+
+// Test-only: arm a host-side fault in ctx's serving worker (dgs_debug_inject_fault).
+dgs_status serve_inject_fault(dgs_ctx *ctx, int count);
 
 }  // namespace dgs
 

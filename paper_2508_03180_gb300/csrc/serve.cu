@@ -11,6 +11,8 @@
 #include <algorithm>
 #include <chrono>
 #include <cstring>
+#include <stdexcept>
+#include <string>
 
 #include "runtime.h"
 
@@ -355,10 +357,10 @@ int check_graph_batch(ServeState &S, int si, dgs_status *err) {
     return 0;
 }
 
-void worker_main(dgs_ctx *ctx) {
+void worker_loop(dgs_ctx *ctx) {
     ServeState &S = *ctx->serve;
     cudaSetDevice(ctx->cfg.device);
-    InflightBatch slot[kServeStreams];
+    InflightBatch *slot = S.slot;
     for (;;) {
         bool progressed = false;
         {
@@ -398,6 +400,10 @@ void worker_main(dgs_ctx *ctx) {
             std::unique_lock<std::mutex> lk(S.m);
             if (S.stop && S.pending.empty() && !S.busy[0] && !S.busy[1]) break;
             const uint64_t seen = S.submits;
+            if (S.inject_fault > 0 && !S.pending.empty()) {
+                --S.inject_fault;
+                throw std::runtime_error("injected host-side fault in the serving worker");
+            }
             if (free_si >= 0) {
                 while (!S.pending.empty() && (int)nb.reqs.size() < S.max_batch) {
                     const PendingReq &r = S.pending.front();
@@ -437,7 +443,60 @@ void worker_main(dgs_ctx *ctx) {
     }
 }
 
+// The worker's top level: a host-side fault (an exception) stops the worker,
+// but first its streams finish the chains in flight (their buffers go back to
+// the pool only then), and every request it had not finished -- in flight or
+// pending -- completes with DGS_ERR_WORKER, so no poll waits for it.
+void worker_main(dgs_ctx *ctx) {
+    ServeState &S = *ctx->serve;
+    std::string why;
+    try {
+        worker_loop(ctx);
+        return;
+    } catch (const std::exception &e) {
+        why = e.what();
+    } catch (...) {
+        why = "unknown exception";
+    }
+    for (int si = 0; si < kServeStreams; ++si)
+        if (S.streams[si]) cudaStreamSynchronize(S.streams[si]);
+    for (int si = 0; si < kServeStreams; ++si) {
+        if (S.busy[si]) {
+            finish(S, S.slot[si], DGS_ERR_WORKER);
+            S.busy[si] = false;
+        }
+        if (S.slot[si].ws) {
+            std::lock_guard<std::mutex> lk(ctx->mu);
+            ctx->pool.push_back(std::move(S.slot[si].ws));
+        }
+        S.slot[si].reqs.clear();
+    }
+    std::lock_guard<std::mutex> lk(S.m);
+    const double t = now_ms();
+    for (const PendingReq &r : S.pending) {
+        dgs_result res;
+        res.status = DGS_ERR_WORKER;
+        res.batch_size = 0;
+        res.t_submit_ms = r.t_submit;
+        res.t_start_ms = res.t_done_ms = t;
+        S.finished[r.ticket] = res;
+    }
+    S.pending.clear();
+    S.dead = true;
+    S.dead_msg = "serving worker stopped: " + why;
+    S.cv_done.notify_all();
+}
+
 }  // namespace
+
+dgs_status dgs::serve_inject_fault(dgs_ctx *ctx, int count) {
+    if (!ctx || !ctx->serve) return set_error(DGS_ERR_INVALID_ARG, "serving is not started");
+    ServeState &S = *ctx->serve;
+    std::lock_guard<std::mutex> lk(S.m);
+    S.inject_fault = std::max(0, count);
+    S.cv_work.notify_all();
+    return DGS_OK;
+}
 
 extern "C" dgs_status dgs_serve_start(dgs_ctx *ctx, int32_t max_batch, int32_t queue_cap, int32_t flags) {
     if (!ctx || max_batch < 1 || queue_cap < 1 || (flags & ~DGS_SERVE_NO_GRAPHS))
@@ -517,6 +576,7 @@ extern "C" dgs_status dgs_submit(dgs_ctx *ctx, const dgs_request *req, uint64_t 
     }
     ServeState &S = *ctx->serve;
     std::lock_guard<std::mutex> lk(S.m);
+    if (S.dead) return set_error(DGS_ERR_WORKER, S.dead_msg);
     if ((int)S.pending.size() >= S.queue_cap) return set_error(DGS_ERR_BUSY, "request queue is full");
     PendingReq p;
     p.ticket = S.next_ticket++;

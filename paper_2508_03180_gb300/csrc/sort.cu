@@ -30,6 +30,20 @@ constexpr uint32_t FLAG_INC = 2u << 30;             // inclusive prefix publishe
 constexpr uint32_t COUNT_MASK = (1u << 30) - 1;
 constexpr int kSpinLimit = 1 << 22;
 
+// Fault injection for the failure-detection tests (dgs_debug_inject_fault,
+// DGS_FAULT_SORT_WAIT): while set, partition 0 never publishes its digit
+// counts and a wait gives up after kFaultSpinLimit polls, so the look-back
+// waits of the other partitions run out -- each one still bounded.  A wait
+// that gave up counts the missing partition as 0, so every destination stays
+// below the digit's true end: the kernels write inside the arrays.
+__device__ int g_rs_fault = 0;
+constexpr int kFaultSpinLimit = 1024;
+
+cudaError_t set_sort_fault(bool on) {
+    const int v = on ? 1 : 0;
+    return cudaMemcpyToSymbol(g_rs_fault, &v, sizeof(int));
+}
+
 long long sort_parts_for(long long n) { return (n + RS_TILE - 1) / RS_TILE; }
 
 // Histograms of every digit of every pass in one read of the keys.
@@ -177,10 +191,12 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_pass(uint32_t *__restrict__ k
             s_local[d] = wb + x - total;
         }
         uint32_t *my = status + part * 256 + d;
+        const bool fault = g_rs_fault != 0;
         if (part == 0) {
-            atomicExch(my, FLAG_INC | total);
+            if (!fault) atomicExch(my, FLAG_INC | total);
             s_base[d] = digit_base[d];
         } else {
+            const int limit = fault ? kFaultSpinLimit : kSpinLimit;
             atomicExch(my, FLAG_AGG | total);
             uint32_t excl = 0;
             for (long long p = part - 1; p >= 0; --p) {
@@ -188,7 +204,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_pass(uint32_t *__restrict__ k
                 uint32_t s = ld_volatile(q);
                 int spins = 0;
                 while ((s & (FLAG_AGG | FLAG_INC)) == 0u) {
-                    if (++spins > kSpinLimit) { atomicOr(err, 1u); s = FLAG_INC; break; }
+                    if (++spins > limit) { atomicOr(err, 1u); s = FLAG_INC; break; }
                     __nanosleep(64);
                     s = ld_volatile(q);
                 }
@@ -237,18 +253,8 @@ __global__ void k_copy_pairs(const uint32_t *__restrict__ ks, const uint32_t *__
     }
 }
 
-// Persistent grid: the CTAs of k_rs_pass every SM holds at once (queried once).
-static long long rs_max_ctas() {
-    static long long cap = 0;
-    if (!cap) {
-        int dev = 0, sms = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rs_pass, RS_THREADS, 0);
-        cap = (long long)std::max(1, sms) * std::max(1, per_sm);
-    }
-    return cap;
-}
+// Persistent grid: the CTAs of k_rs_pass every SM of the current device holds at once.
+static long long rs_max_ctas() { return resident_ctas((const void *)k_rs_pass, RS_THREADS); }
 
 int radix_sort_pairs(uint32_t *keys, uint32_t *vals, long long n, int bits, const SortScratch &s, cudaStream_t st,
                      const uint32_t *d_n) {

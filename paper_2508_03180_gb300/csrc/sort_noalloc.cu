@@ -5,11 +5,12 @@
 // cudaMalloc/cudaFree can block and synchronise the whole device.  Its scratch
 // (alternate key/value buffers, digit histograms, look-back status words,
 // partition counters, error flag) is one file-scope device array below, so
-// the call itself allocates nothing; the array is part of the loaded module
-// and every GPU that loads the library holds it until the process exits.
+// the call itself allocates nothing; the array is part of this file's module,
+// which the CUDA runtime loads into a device's context on first use (with
+// lazy loading, the default, at the first call on that device), and every
+// GPU that has loaded it holds it until the process exits.
 #include <cuda_runtime.h>
 
-#include <mutex>
 #include <string>
 
 #include "internal.cuh"
@@ -29,24 +30,20 @@ constexpr size_t kOffErr = kOffCounters + 4;
 constexpr size_t kWords = kOffErr + 60;                    // about 9.1 MB in total
 
 // Device-side scratch.  In host code this name is only a stand-in: its
-// device address comes from cudaGetSymbolAddress, per device.
+// device address in the current context comes from cudaGetSymbolAddress.
 static __device__ __align__(256) uint32_t g_sort_scratch[kWords];
 
-std::mutex g_addr_mu;
-constexpr int kMaxDevices = 64;
-uint32_t *g_addr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device; looked up once
-// per device (the first call on a device does this set-up).
-dgs_status scratch_address(int dev, uint32_t **out) {
-    std::lock_guard<std::mutex> lk(g_addr_mu);
-    if (!g_addr[dev]) {
-        void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_sort_scratch);
-        if (e != cudaSuccess) return dgs::cuda_error(e, "cudaGetSymbolAddress of the sort scratch");
-        g_addr[dev] = static_cast<uint32_t *>(p);
-    }
-    *out = g_addr[dev];
+// Device address of the scratch array in the current device's context.  It is
+// looked up on every call (a host-side lookup, no allocation once the module
+// is loaded), so a context that was reset and created again gets the array's
+// new address.  The first lookup in a context loads this file's module -- the
+// CUDA driver then allocates the array's device memory -- which is why the
+// first call on a device belongs to the caller's set-up.
+dgs_status scratch_address(uint32_t **out) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_sort_scratch);
+    if (e != cudaSuccess) return dgs::cuda_error(e, "cudaGetSymbolAddress of the sort scratch");
+    *out = static_cast<uint32_t *>(p);
     return DGS_OK;
 }
 
@@ -60,13 +57,10 @@ extern "C" dgs_status dgs_sort_pairs_noalloc(uint32_t *keys, uint32_t *vals, int
         return dgs::set_error(DGS_ERR_CAPACITY, "dgs_sort_pairs_noalloc: n = " + std::to_string(n) +
                                                     " exceeds the fixed maximum of 1048576 pairs");
     if (n <= 1 || bits == 0) return DGS_OK;
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return dgs::cuda_error(e, "cudaGetDevice");
-    if (dev < 0 || dev >= kMaxDevices) return dgs::set_error(DGS_ERR_INVALID_ARG, "device ordinal out of range");
     uint32_t *base = nullptr;
-    dgs_status s = scratch_address(dev, &base);
+    dgs_status s = scratch_address(&base);
     if (s) return s;
+    cudaError_t e;
     dgs::SortScratch sc;
     sc.keys_alt = base + kOffKeys;
     sc.vals_alt = base + kOffVals;

@@ -2,7 +2,8 @@
 device memory (a process whose caching allocator already holds the free
 memory, or a loop that forbids allocation after start-up) -- gives the same
 result as dgs_sort_pairs, on two calls in a row that share its fixed
-scratch array, and refuses sizes beyond its fixed maximum.
+scratch array, leaves the device's free memory unchanged once its first
+call has loaded that array, and refuses sizes beyond its fixed maximum.
 
 This file is collected last on purpose: it runs after every other test in a
 full run, and it also passes alone in a fresh process."""
@@ -55,3 +56,25 @@ def test_noalloc_sort_rejects_more_than_its_maximum():
         L.dgs_sort_pairs_noalloc(k.data_ptr(), v.data_ptr(), MAX_ITEMS + 1, 32, 0)
     assert ei.value.code == L.DGS_ERR_CAPACITY
     assert "1048576" in str(ei.value)
+
+
+def test_noalloc_sort_allocates_nothing_after_its_first_call():
+    """The call's defining property: once the first call on the device has
+    loaded the scratch array and the sort's kernels (the caller's set-up),
+    further calls of the largest size leave the device's free memory as it
+    was.  Inputs are created before the readings, and nothing else touches
+    the device between them."""
+    from paper_2508_03180_gb300 import _lib as L
+    keys, vals = _inputs(MAX_ITEMS, 32, seed=7)
+    k, v = keys.cuda(), vals.cuda()
+    stream = torch.cuda.current_stream().cuda_stream
+    L.dgs_sort_pairs_noalloc(k.data_ptr(), v.data_ptr(), MAX_ITEMS, 32, stream)  # set-up call
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(2):
+        L.dgs_sort_pairs_noalloc(k.data_ptr(), v.data_ptr(), MAX_ITEMS, 32, stream)
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    assert free1 == free0, (free0, free1)
+    order = np.argsort(keys.numpy().astype(np.uint32), kind="stable")
+    assert np.array_equal(v.cpu().numpy(), order.astype(np.int32))
