@@ -235,13 +235,32 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def serving_bench(rctx, rates=(200.0, 1000.0, 2500.0, 5000.0), n_req=400, seed=0):
+SERVE_RATES = (200.0, 500.0, 1000.0, 1500.0, 2000.0, 2500.0, 3000.0, 3500.0, 4000.0, 4500.0, 5000.0, 6000.0)
+SERVE_SLO_MS = (2.0, 5.0, 20.0)
+
+
+def at_p99(rows, slos=SERVE_SLO_MS):
+    """For each p99 target: the highest offered rate whose p99 latency stays
+    within it, with the frames/s and p99 measured there (None if no rate
+    does)."""
+    out = {}
+    for slo in slos:
+        ok = [r for r in rows if r["p99_ms"] <= slo]
+        best = max(ok, key=lambda r: r["offered_rps"]) if ok else None
+        out[f"{slo:g}ms"] = None if best is None else {"offered_rps": best["offered_rps"], "fps": best["fps"],
+                                                       "p99_ms": best["p99_ms"]}
+    return out
+
+
+def serving_bench(rctx, rates=SERVE_RATES, n_req=400, seed=0):
     """Open-loop Poisson arrivals over 3 resident scenes (100k, 500k, 2M
     Gaussians), resolutions uniform over {640x480, 1280x720, 1920x1080,
     3840x2160}.  The same request trace is served by continuous batching
     (up to 8 views per launch chain, 2 chains in flight) and one request at a
     time, at each offered rate; 200 req/s is the configured load, the higher
-    rates locate each system's saturation."""
+    rates locate each system's saturation.  `at_p99` compares the modes at
+    equal p99 latency: per p99 target, the highest rate each sustains within
+    it and the frames/s there."""
     import torch
 
     from paper_2508_03180_gb300 import synth
@@ -297,6 +316,7 @@ def serving_bench(rctx, rates=(200.0, 1000.0, 2500.0, 5000.0), n_req=400, seed=0
         out["batched"].append(run(8, rate))
         out["batched_no_graph"].append(run(8, rate, graphs=False))
         out["one_at_a_time"].append(run(1, rate))
+    out["at_p99"] = {m: at_p99(out[m]) for m in ("batched", "batched_no_graph", "one_at_a_time")}
     for s in sids:
         rctx.release_scene(s)
     return out

@@ -219,8 +219,22 @@ typedef struct {
  * 3 H W of the views before it), in out_location memory.
  * state (nullable): if non-NULL, *state receives a handle that keeps this
  * render's intermediate buffers for dgs_render_backward; it stays owned by
- * the context until dgs_state_release.  stats (nullable): filled on return;
- * this call synchronises the stream once after binning (to size the sort). */
+ * the context until dgs_state_release.  stats (nullable): filled on return.
+ *
+ * Synchronisation.  With device output and no stats the call is asynchronous
+ * on `stream`: it enqueues the whole chain and returns.  The number L of
+ * (tile, cell) pairs is then known on the device only; the pair buffers hold
+ * 1.5 x the largest pairs-per-tile seen in this context (at least 65,536)
+ * and the kernels stop at that capacity.  A render whose L exceeded it
+ * leaves an incomplete image and state; this is found once its chain has
+ * completed (when its buffers are reused, or by dgs_render_backward on its
+ * state if it has completed by then), the capacity grows to fit, and the next
+ * dgs_render or dgs_render_backward on the context returns DGS_ERR_CAPACITY
+ * (a radix sort that gave up: DGS_ERR_TIMEOUT) once; render it again.  The
+ * call synchronises the stream once after binning, and sizes the pairs
+ * exactly, when stats are requested, when the scene has neural cells (the
+ * decode needs the visible-cell count on the host), and on the context's first
+ * render (to learn its pairs per tile); host output synchronises at the end. */
 dgs_status dgs_render(dgs_ctx *ctx, uint32_t scene_id, int32_t n_views, const uint32_t *cam_slots,
                       float *out_rgb, int32_t out_location, dgs_fwd_state **state, dgs_stream stream,
                       dgs_stats *stats);
@@ -241,6 +255,18 @@ dgs_status dgs_render(dgs_ctx *ctx, uint32_t scene_id, int32_t n_views, const ui
  * each summed over the views in which the cell was decoded.  The decode's
  * own decisions (the ReLU masks, the Eq. 11 bound, sigma <= 0 not drawn)
  * are held fixed with the others.
+ * The cell proxies' own parameters (Sec. IV-A: centre x_n, semi-axes S_n,
+ * rotation Q_n; Sec. V-A: v_n), any scene:
+ *   g_cell_center [N][3]: through the direction d = (x_n - eye)/|x_n - eye|
+ *     of a view-dependent v_n, and for neural cells through the decoder
+ *     inputs delta_n, d_n and the centres mu = x_n + R(Q_n)(O_pos * S_n);
+ *   g_cell_axes [N][3]: neural cells, through the centres and the scales
+ *     s = min(sigmoid, 1 - |O_pos|) * S_n (Eq. 8, 11);
+ *   g_cell_quat [N][4]: neural cells, through R(Q_n) of the centres (Q_n as
+ *     stored, normalised by the renderer);
+ * each summed over the views.  The cells' footprints (culling, tile lists,
+ * depth order) are held fixed, so an explicit scene with a scalar v_n has
+ * zero gradients here.
  * Discrete choices of the forward (culling, tile lists, AABB skips, alpha
  * clamp, the per-pixel number of blended cells) are held fixed. */
 typedef struct {
@@ -249,6 +275,7 @@ typedef struct {
     float *g_mean, *g_scale, *g_log_scale, *g_quat, *g_logit, *g_sh, *g_cell_v;
     float *g_cell_v_sh;
     float *g_mlp, *g_feat, *g_offset;
+    float *g_cell_center, *g_cell_axes, *g_cell_quat;
 } dgs_grads;
 
 /* Asynchronous on stream when dL_drgb and the outputs are device memory;

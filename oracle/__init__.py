@@ -225,6 +225,25 @@ def cell_v_view(scene, cam):
     return np.clip(raw, 0.0, 1.0), dict(Y=Y, mask=(raw > 0.0) & (raw < 1.0))
 
 
+def cell_v_center_grad(scene, cam, g_v):
+    """dL/dx_n (N,3) of the cell centres through the direction d of a
+    view-dependent v_n, given dL/dv_n (N,) of one view (torch autograd
+    through the SH basis at d = (x_n - eye)/|x_n - eye|; zero where the clamp
+    holds v_n); zeros for a scalar v_n."""
+    vsh = getattr(scene, "cell_v_sh", None)
+    N = scene.N
+    if vsh is None or N == 0:
+        return np.zeros((N, 3))
+    eye = torch.as_tensor(np.asarray(cam, dtype=np.float64)[19:22])
+    x = torch.tensor(np.asarray(scene.cell_center, dtype=np.float64), requires_grad=True)
+    d = x - eye[None, :]
+    d = d / torch.linalg.norm(d, dim=1, keepdim=True)
+    raw = (torch.as_tensor(np.asarray(vsh, dtype=np.float64)) * _project.sh_basis(d, scene.v_sh_degree)).sum(1)
+    free = ((raw > 0.0) & (raw < 1.0)).detach().to(torch.float64)
+    (gx,) = torch.autograd.grad((raw * free * torch.as_tensor(np.asarray(g_v, dtype=np.float64))).sum(), x)
+    return gx.numpy()
+
+
 def prepare_view(scene, cam, opt: Options = Options(), tile_rows=None, requires_grad=False):
     """All per-view inputs of the blend: tile lists, FP32 decisions, FP64
     projected values (only for valid Gaussians of cells that reach the
@@ -308,6 +327,11 @@ def param_grads(scene, pv, g2d):
     _, info = cell_v_view(scene, pv["cam"])
     if info is not None:  # through the clamp and the SH basis
         res["cell_v_sh"] = (g2d["v"] * info["mask"])[:, None] * info["Y"]
+    # the cells' own parameters: with the footprints held fixed, explicit
+    # Gaussians see them only through a view-dependent v_n's direction
+    res["cell_center"] = cell_v_center_grad(scene, pv["cam"], g2d["v"])
+    res["cell_axes"] = np.zeros((scene.N, 3))
+    res["cell_quat"] = np.zeros((scene.N, 4))
     return res
 
 
@@ -433,7 +457,9 @@ def explicit_scene(scene, mean, scale, quat, opac, rgb):
 def neural_render_and_grad(scene, cam, dL_dC, decided=None, opt: Options = Options(), ndone=None, tile_rows=None):
     """FP64 image and gradients of sum(dL_dC * C) for a neural scene in one
     view: dL/d(packed weights), dL/d(features) (N,F), dL/d(offsets) (G,3),
-    and dL/d(decoded mean, scale, quat, opacity, rgb) per Gaussian.
+    dL/d of the cells' centres (N,3), semi-axes (N,3) and quaternions (N,4)
+    through the decode (and a view-dependent v_n's direction), and dL/d(decoded
+    mean, scale, quat, opacity, rgb) per Gaussian.
     decided: (mean, scale, quat) float32 arrays (G,...) whose FP32 AABB
     decisions and tile lists to use (the renderer's own decoded values);
     default: the FP64 decode rounded to FP32."""
@@ -457,12 +483,14 @@ def neural_render_and_grad(scene, cam, dL_dC, decided=None, opt: Options = Optio
     gos = [torch.tensor(g2d[k], dtype=torch.float64) for k in ("mu2", "conic", "opac", "rgb")]
     dec_vals = [flat[k] for k in ("mean", "scale", "quat", "opac", "rgb")]
     leaves = d["leaves"]
-    grads = torch.autograd.grad(outs, [leaves["mlp"], leaves["feat"], leaves["offset"]] + dec_vals, gos,
-                                allow_unused=True, retain_graph=False)
+    names = ("mlp", "feat", "offset", "cell_center", "cell_axes", "cell_quat")
+    grads = torch.autograd.grad(outs, [leaves[k] for k in names] + dec_vals, gos, allow_unused=True,
+                                retain_graph=False)
     z = lambda t, ref: np.zeros(tuple(ref.shape)) if t is None else t.numpy()
-    res = dict(mlp=z(grads[0], leaves["mlp"]), feat=z(grads[1], leaves["feat"]),
-               offset=z(grads[2], leaves["offset"]).reshape(G, 3))
-    for name, g_, ref in zip(("mean", "scale", "quat", "opac", "rgb"), grads[3:], dec_vals):
+    res = {k: z(g_, leaves[k]) for k, g_ in zip(names, grads)}
+    res["offset"] = res["offset"].reshape(G, 3)
+    res["cell_center"] = res["cell_center"] + cell_v_center_grad(scene, cam, g2d["v"])
+    for name, g_, ref in zip(("mean", "scale", "quat", "opac", "rgb"), grads[len(names):], dec_vals):
         res["dec_" + name] = z(g_, ref).reshape(G, -1)
     return img, res
 

@@ -77,12 +77,15 @@ def decode64(neural: dict, cell_center, cell_axes, cell_quat, K: int, eye):
 
 def decode_t(neural: dict, cell_center, cell_axes, cell_quat, K: int, eye, requires_grad: bool = False):
     """decode64 as torch float64 tensors; with requires_grad the leaves
-    (out["leaves"]: mlp, feat, offset) carry gradients."""
+    (out["leaves"]: mlp, feat, offset, and the cells' cell_center,
+    cell_axes, cell_quat) carry gradients."""
     F, H = neural["F"], neural["H"]
-    x = torch.as_tensor(np.asarray(cell_center, dtype=np.float64))
-    S = torch.as_tensor(np.asarray(cell_axes, dtype=np.float64))
+    x = torch.tensor(np.asarray(cell_center, dtype=np.float64), requires_grad=requires_grad)
+    S = torch.tensor(np.asarray(cell_axes, dtype=np.float64), requires_grad=requires_grad)
+    Qc = torch.tensor(np.asarray(cell_quat, dtype=np.float64), requires_grad=requires_grad)
     N = x.shape[0]
-    leaves = dict(mlp=torch.tensor(np.asarray(neural["mlp"], dtype=np.float64), requires_grad=requires_grad),
+    leaves = dict(cell_center=x, cell_axes=S, cell_quat=Qc,
+                  mlp=torch.tensor(np.asarray(neural["mlp"], dtype=np.float64), requires_grad=requires_grad),
                   feat=torch.tensor(np.asarray(neural["feat"], dtype=np.float64).reshape(N, F),
                                     requires_grad=requires_grad),
                   offset=torch.tensor(np.asarray(neural["offset"], dtype=np.float64).reshape(N, K, 3),
@@ -107,7 +110,7 @@ def decode_t(neural: dict, cell_center, cell_axes, cell_quat, K: int, eye, requi
     qn = torch.linalg.norm(q, dim=2, keepdim=True)
     ident = torch.tensor([1.0, 0.0, 0.0, 0.0], dtype=torch.float64).expand_as(q)
     quat = torch.where(qn > 0, q / torch.where(qn > 0, qn, torch.ones_like(qn)), ident)
-    Rc = quat_to_rotmat(torch.as_tensor(np.asarray(cell_quat, dtype=np.float64)))  # (N,3,3)
+    Rc = quat_to_rotmat(Qc)  # (N,3,3), Q_n normalised
     local = off_b * S[:, None, :]
     mean = x[:, None, :] + torch.einsum("nij,nkj->nki", Rc, local)
     return dict(mean=mean, scale=scale, quat=quat, opac=opac, rgb=rgb, leaves=leaves)

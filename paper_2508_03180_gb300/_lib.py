@@ -83,7 +83,8 @@ class dgs_stats(C.Structure):
 class dgs_grads(C.Structure):
     _fields_ = [("location", C.c_int32), ("reserved", C.c_int32), ("g_mean", _P), ("g_scale", _P), ("g_log_scale", _P),
                 ("g_quat", _P), ("g_logit", _P), ("g_sh", _P), ("g_cell_v", _P), ("g_cell_v_sh", _P),
-                ("g_mlp", _P), ("g_feat", _P), ("g_offset", _P)]
+                ("g_mlp", _P), ("g_feat", _P), ("g_offset", _P), ("g_cell_center", _P), ("g_cell_axes", _P),
+                ("g_cell_quat", _P)]
 
 
 class dgs_counts(C.Structure):

@@ -547,6 +547,7 @@ std::unique_ptr<Workspace> acquire_ws(dgs_ctx *ctx, cudaStream_t st, dgs_status 
             *err = cuda_error(e, "waiting for a workspace");
             return nullptr;
         }
+        if ((*err = observe_chain(ctx, *ws, true))) return nullptr;
     } else {
         ws = std::make_unique<Workspace>();
         if ((*err = ws->init())) return nullptr;
@@ -556,10 +557,47 @@ std::unique_ptr<Workspace> acquire_ws(dgs_ctx *ctx, cudaStream_t st, dgs_status 
     return ws;
 }
 
+dgs_status observe_chain(dgs_ctx *ctx, Workspace &ws, bool wait) {
+    if (!ws.async_pending) return DGS_OK;
+    if (wait) {
+        CK(cudaEventSynchronize(ws.done));
+    } else {
+        const cudaError_t q = cudaEventQuery(ws.done);
+        if (q == cudaErrorNotReady) return DGS_OK;
+        if (q != cudaSuccess) return cuda_error(q, "a render's launch chain");
+    }
+    ws.async_pending = false;
+    const uint32_t *h = ws.h_small;
+    const long long L = h[kSmallTotal];
+    ws.L = std::min(L, ws.L_cap);
+    ws.n_vis = h[kSmallVisible];
+    if (ws.total_tiles > 0) ctx->pairs_per_tile = std::max(ctx->pairs_per_tile, (double)L / ws.total_tiles);
+    if (h[kSmallSortErr]) {
+        ctx->pending_status = DGS_ERR_TIMEOUT;
+        ctx->pending_msg = "an earlier render's radix sort look-back wait gave up: its image and state are not valid";
+    } else if (h[kSmallOverflow]) {
+        ctx->pending_status = DGS_ERR_CAPACITY;
+        ctx->pending_msg = "an earlier render's " + std::to_string(L) + " (tile, cell) pairs exceeded its capacity of " +
+                           std::to_string(ws.L_cap) +
+                           ": its image and state are incomplete; the capacity has grown, render it again";
+    }
+    return DGS_OK;
+}
+
+// Pair capacity of a device-sized chain: 1.5 times the largest pairs per tile
+// seen in this context, at least 64 Ki pairs.
+static long long pair_capacity(const dgs_ctx *ctx, const Workspace &ws) {
+    const double want = 1.5 * ctx->pairs_per_tile * (double)std::max(1, ws.total_tiles);
+    return std::max<long long>(1LL << 16, (long long)std::ceil(want));
+}
+
 // Binning of all views of the chain (steps a1-a5): cell projection and cull,
 // depth sort over cells, count scan, key emission, tile sort, tile ranges.
-// Synchronises the stream once to learn the sort length L.
-static dgs_status run_binning(dgs_ctx *ctx, Workspace &ws, cudaStream_t st) {
+// Synchronises the stream once to learn the sort length L, unless
+// device_sized: then the pair count stays on the device, the pair buffers
+// are sized by pair_capacity and the kernels stop at that capacity (a
+// k_clamp_pairs flag records an overflow).
+static dgs_status run_binning(dgs_ctx *ctx, Workspace &ws, cudaStream_t st, bool device_sized) {
     Profiler &pf = ctx->prof;
     const int V = ws.V;
     const long long n = ws.n_entries;
@@ -573,6 +611,13 @@ static dgs_status run_binning(dgs_ctx *ctx, Workspace &ws, cudaStream_t st) {
         (s = ws.vview.ensure(4 * n1)))
         return s;
     if ((s = ensure_sort_scratch(ws, n))) return s;
+    // a device-sized chain sizes every buffer before its first launch, so no
+    // buffer is reallocated under the kernels in flight
+    const long long cap = device_sized ? pair_capacity(ctx, ws) : 0;
+    if (device_sized &&
+        ((s = ws.tkey.ensure(4 * cap)) || (s = ws.tval.ensure(4 * cap)) || (s = ensure_sort_scratch(ws, cap)) ||
+         (s = ws.ranges.ensure(8 * (size_t)std::max(1, ws.total_tiles))) || (s = ws.sizes.ensure(sizeof(ChainSizes)))))
+        return s;
     uint32_t *small = (uint32_t *)ws.small.p;
     const ViewDesc *dv = (const ViewDesc *)ws.views.p;
     {
@@ -593,12 +638,46 @@ static dgs_status run_binning(dgs_ctx *ctx, Workspace &ws, cudaStream_t st) {
                            (uint32_t *)ws.scan.p, st);
     }
     CK(cudaGetLastError());
+    int bits = 1;
+    while ((1LL << bits) < ws.total_tiles) ++bits;
+    if (device_sized) {
+        ws.L_cap = cap;
+        ws.L = -1;
+        ws.n_vis = -1;
+        *ws.h_sizes = ChainSizes{};
+        ws.h_sizes->n_entries = (uint32_t)n;
+        ws.h_sizes->n_views = V;
+        ws.h_sizes->total_tiles = ws.total_tiles;
+        ws.h_sizes->L_cap = (uint32_t)cap;
+        ws.h_sizes->n_scenes = (int32_t)ws.scene_ids.size();
+        CK(cudaMemcpyAsync(ws.sizes.p, ws.h_sizes, sizeof(ChainSizes), cudaMemcpyHostToDevice, st));
+        const uint32_t *d_L = small + kSmallPairs;  // min(L, cap), written on the device
+        launch_clamp_pairs(small, kSmallTotal, kSmallPairs, kSmallOverflow, (const ChainSizes *)ws.sizes.p, st);
+        {
+            StageTimer t(pf, DGS_STAGE_EMIT, st);
+            launch_emit((const uint32_t *)ws.offs.p, (const uint32_t *)ws.zval.p, (const short4 *)ws.rect.p, dv, V,
+                        n, cap, (uint32_t *)ws.tkey.p, (uint32_t *)ws.tval.p, st, nullptr, d_L);
+        }
+        {
+            StageTimer t(pf, DGS_STAGE_TILE_SORT, st);
+            radix_sort_pairs((uint32_t *)ws.tkey.p, (uint32_t *)ws.tval.p, cap, bits, sort_scratch_of(ws), st, d_L);
+        }
+        {
+            StageTimer t(pf, DGS_STAGE_TILE_RANGES, st);
+            CK(cudaMemsetAsync(ws.ranges.p, 0, 8 * (size_t)std::max(1, ws.total_tiles), st));
+            launch_tile_ranges((const uint32_t *)ws.tkey.p, cap, (uint2 *)ws.ranges.p, st, d_L);
+        }
+        CK(cudaGetLastError());
+        ws.async_pending = true;
+        return DGS_OK;
+    }
     CK(cudaMemcpyAsync(ws.h_small, small, 64, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (ws.h_small[kSmallSortErr]) return set_error(DGS_ERR_TIMEOUT, "radix sort look-back wait gave up");
     const long long L = ws.h_small[kSmallTotal];
     ws.L = L;
     ws.n_vis = ws.h_small[kSmallVisible];
+    if (ws.total_tiles > 0) ctx->pairs_per_tile = std::max(ctx->pairs_per_tile, (double)L / ws.total_tiles);
     if ((s = ws.tkey.ensure(4 * std::max(1LL, L))) || (s = ws.tval.ensure(4 * std::max(1LL, L)))) return s;
     if ((s = ensure_sort_scratch(ws, L))) return s;
     if ((s = ws.ranges.ensure(8 * (size_t)std::max(1, ws.total_tiles)))) return s;
@@ -607,8 +686,6 @@ static dgs_status run_binning(dgs_ctx *ctx, Workspace &ws, cudaStream_t st) {
         launch_emit((const uint32_t *)ws.offs.p, (const uint32_t *)ws.zval.p, (const short4 *)ws.rect.p, dv, V, n, L,
                     (uint32_t *)ws.tkey.p, (uint32_t *)ws.tval.p, st);
     }
-    int bits = 1;
-    while ((1LL << bits) < ws.total_tiles) ++bits;
     {
         StageTimer t(pf, DGS_STAGE_TILE_SORT, st);
         radix_sort_pairs((uint32_t *)ws.tkey.p, (uint32_t *)ws.tval.p, L, bits, sort_scratch_of(ws), st);
@@ -623,7 +700,7 @@ static dgs_status run_binning(dgs_ctx *ctx, Workspace &ws, cudaStream_t st) {
 }
 
 dgs_status chain_forward(dgs_ctx *ctx, Workspace &ws, const std::vector<ChainView> &req, float *out_img,
-                         bool keep_rgb, bool grad_buffers, cudaStream_t st) {
+                         bool keep_rgb, bool grad_buffers, cudaStream_t st, bool device_sized) {
     const int V = (int)req.size();
     ws.V = V;
     ws.hviews.clear();
@@ -674,7 +751,7 @@ dgs_status chain_forward(dgs_ctx *ctx, Workspace &ws, const std::vector<ChainVie
     for (int k = 0; k < S; ++k) ws.h_scenes[k] = slots[k]->dev();
     CK(cudaMemcpyAsync(ws.views.p, ws.h_views, sizeof(ViewDesc) * V, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(ws.scenes.p, ws.h_scenes, sizeof(SceneDev) * S, cudaMemcpyHostToDevice, st));
-    if ((s = run_binning(ctx, ws, st))) return s;
+    if ((s = run_binning(ctx, ws, st, device_sized))) return s;
     const BlendParams bp = blend_params(ctx->cfg);
     const long long nrec = std::max(1LL, ws.n_records), px1 = std::max(1LL, px);
     bool any_neural = false;
@@ -714,6 +791,8 @@ dgs_status chain_forward(dgs_ctx *ctx, Workspace &ws, const std::vector<ChainVie
                          (const float4 *)ws.rec.p, bp, img, img2, (float *)ws.Dpix.p, (int *)ws.ndpix.p, K_all, st);
     }
     CK(cudaGetLastError());
+    if (device_sized)  // the chain's sizes and flags, read once it has completed (observe_chain)
+        CK(cudaMemcpyAsync(ws.h_small, ws.small.p, 64, cudaMemcpyDeviceToHost, st));
     ws.stream = st;
     return DGS_OK;
 }
@@ -732,6 +811,16 @@ static dgs_status render_impl(dgs_ctx *ctx, uint32_t scene_id, int n_views, cons
     dgs_status s;
     std::unique_ptr<Workspace> ws = acquire_ws(ctx, st, &s);
     if (!ws) return s;
+    if (ctx->pending_status) {  // a completed earlier render overflowed (or its sort gave up)
+        s = set_error(ctx->pending_status, ctx->pending_msg);
+        ctx->pending_status = DGS_OK;
+        ctx->pool.push_back(std::move(ws));
+        return s;
+    }
+    // No host synchronisation unless stats are asked for, a neural scene needs
+    // its visible-cell count on the host (the decode), or this context has not
+    // rendered yet (no pairs-per-tile estimate to size the pair buffers).
+    const bool device_sized = !stats && ctx->scenes[scene_id]->F == 0 && ctx->pairs_per_tile > 0.0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     const bool timing = stats && stats->timing;
     if (timing) {
@@ -740,7 +829,8 @@ static dgs_status render_impl(dgs_ctx *ctx, uint32_t scene_id, int n_views, cons
         cudaEventRecord(e0, st);
     }
     const bool keep = state != nullptr;
-    s = chain_forward(ctx, *ws, req, out_location == DGS_DEVICE ? out_rgb : nullptr, keep, keep, st);
+    s = chain_forward(ctx, *ws, req, out_location == DGS_DEVICE ? out_rgb : nullptr, keep, keep, st,
+                      device_sized && out_location == DGS_DEVICE);
     if (!s && out_location == DGS_HOST) {
         cudaError_t e = cudaMemcpyAsync(out_rgb, ws->rgb.p, 12 * ws->total_px, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -801,12 +891,18 @@ extern "C" dgs_status dgs_render_backward(dgs_ctx *ctx, dgs_fwd_state *state, co
         return set_error(DGS_ERR_INVALID_ARG, "g_mlp, g_feat and g_offset need a neural scene");
     Workspace &ws = *state->ws;
     cudaStream_t st = (cudaStream_t)stream;
+    dgs_status s;
+    if ((s = observe_chain(ctx, ws, false))) return s;
+    if (ctx->pending_status) {  // this state's render, or an earlier one, overflowed (see dgs_render)
+        s = set_error(ctx->pending_status, ctx->pending_msg);
+        ctx->pending_status = DGS_OK;
+        return s;
+    }
     CK(cudaStreamWaitEvent(st, ws.done, 0));
     const long long px = ws.total_px, G = sc.G, N = sc.N;
     const int C = sc.C, Cv = sc.Cv;
     if (out->g_cell_v_sh && sc.vdeg < 0)
         return set_error(DGS_ERR_INVALID_ARG, "g_cell_v_sh given for a scene without view-dependent v");
-    dgs_status s;
     // Host memory: mapped arrays are read (dL/drgb, by the blend adjoint) or
     // written (the explicit Gaussians' gradients, by the projection adjoint)
     // by the kernels over the host link; the others are staged in device
@@ -820,7 +916,8 @@ extern "C" dgs_status dgs_render_backward(dgs_ctx *ctx, dgs_fwd_state *state, co
                {out->g_logit, G, true, nullptr},         {out->g_sh, 3LL * C * G, true, nullptr},
                {out->g_cell_v, N, false, nullptr},       {out->g_cell_v_sh, (long long)Cv * N, false, nullptr},
                {out->g_mlp, P, false, nullptr},          {out->g_feat, NF, false, nullptr},
-               {out->g_offset, GO, false, nullptr}};
+               {out->g_offset, GO, false, nullptr},      {out->g_cell_center, 3 * N, false, nullptr},
+               {out->g_cell_axes, 3 * N, false, nullptr}, {out->g_cell_quat, 4 * N, false, nullptr}};
     long long n_stage = (hin && !dl_mapped ? 3 * px : 0) + 1;
     for (auto &q : o) {
         if (!q.user) continue;
@@ -844,10 +941,14 @@ extern "C" dgs_status dgs_render_backward(dgs_ctx *ctx, dgs_fwd_state *state, co
         if (q.user && !q.dev) { q.dev = stage; stage += q.n; }
     float *o_mean = o[0].dev, *o_s = o[1].dev, *o_ls = o[2].dev, *o_q = o[3].dev, *o_lg = o[4].dev,
           *o_sh = o[5].dev, *o_v = o[6].dev, *o_vsh = o[7].dev, *o_mlp = o[8].dev, *o_f = o[9].dev,
-          *o_off = o[10].dev;
+          *o_off = o[10].dev, *o_cc = o[11].dev, *o_ca = o[12].dev, *o_cq = o[13].dev;
+    // the cell gradients are sums of several kernels' contributions
+    if (o_cc) CK(cudaMemsetAsync(o_cc, 0, sizeof(float) * 3 * N, st));
+    if (o_ca) CK(cudaMemsetAsync(o_ca, 0, sizeof(float) * 3 * N, st));
+    if (o_cq) CK(cudaMemsetAsync(o_cq, 0, sizeof(float) * 4 * N, st));
     // dL/dv per (view, cell) entry, chained to the outputs after the blend adjoint
     float *gv = nullptr;
-    if (o_v || o_vsh) {
+    if (o_v || o_vsh || (o_cc && sc.vdeg >= 0)) {
         if ((s = ws.gvview.ensure(sizeof(float) * std::max(1LL, ws.n_entries)))) return s;
         gv = (float *)ws.gvview.p;
         CK(cudaMemsetAsync(gv, 0, sizeof(float) * ws.n_entries, st));
@@ -861,9 +962,9 @@ extern "C" dgs_status dgs_render_backward(dgs_ctx *ctx, dgs_fwd_state *state, co
         launch_blend_bwd((const ViewDesc *)ws.views.p, ws.V, ws.total_tiles, sc.K, (const uint2 *)ws.ranges.p,
                          (const uint32_t *)ws.tval.p, (const float4 *)ws.rec.p, bp, (const float *)ws.rgb.p,
                          (const float *)ws.Dpix.p, (const int *)ws.ndpix.p, dl, (float *)ws.g2d.p, gv, st);
-        if (gv) launch_cell_v_grad((const ViewDesc *)ws.views.p, ws.V, sc.dev(), gv, o_v, o_vsh, st);
+        if (gv) launch_cell_v_grad((const ViewDesc *)ws.views.p, ws.V, sc.dev(), gv, o_v, o_vsh, o_cc, st);
     }
-    if (neural && (o_mlp || o_f || o_off)) {
+    if (neural && (o_mlp || o_f || o_off || o_cc || o_ca || o_cq)) {
         if ((s = ws.gdec.ensure(sizeof(float) * kDecF * std::max(1LL, ws.n_records)))) return s;
         // the decode adjoint forms every output; unrequested ones go to scratch after its rows
         if ((s = ws.gscratch.ensure(sizeof(float) * std::max(1LL, P + NF + GO))) ||
@@ -881,7 +982,7 @@ extern "C" dgs_status dgs_render_backward(dgs_ctx *ctx, dgs_fwd_state *state, co
         CK(cudaMemsetAsync(f, 0, sizeof(float) * NF, st));
         CK(cudaMemsetAsync(off, 0, sizeof(float) * GO, st));
         launch_decode_bwd((const ViewDesc *)ws.views.p, ws.V, 0, sc.dev(), (const uint32_t *)ws.zval.p, ws.n_vis,
-                          (const float *)ws.gdec.p, m, f, off, (float *)ws.wpack.p, st);
+                          (const float *)ws.gdec.p, m, f, off, CellGrads{o_cc, o_ca, o_cq}, (float *)ws.wpack.p, st);
     } else if (!neural) {
         StageTimer t(ctx->prof, DGS_STAGE_PROJECT_BWD, st);
         launch_project_bwd((const ViewDesc *)ws.views.p, ws.V, 0, sc.dev(), (const uint32_t *)ws.count.p, bp,
@@ -920,7 +1021,9 @@ extern "C" dgs_status dgs_state_read(dgs_ctx *ctx, const dgs_fwd_state *state, i
     auto it = ctx->scenes.find(state->scene_id);
     if (it == ctx->scenes.end()) return set_error(DGS_ERR_NOT_FOUND, "scene released");
     const Scene &sc = *it->second;
-    const Workspace &ws = *state->ws;
+    Workspace &ws = *state->ws;
+    dgs_status s = observe_chain(ctx, ws, true);  // L of a device-sized chain
+    if (s) return s;
     const long long VN = ws.n_entries, VG = ws.n_records;
     (void)sc;
     int64_t need = 0;

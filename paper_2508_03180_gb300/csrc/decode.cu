@@ -503,7 +503,11 @@ __global__ void __launch_bounds__(256) k_decode(const ViewDesc *__restrict__ vie
 //     Eq. 11 bound);
 //   dL/dh = relu'(h) (dL/do_D W2_D) per decoder;
 //   dL/df = sum over decoders of dL/dh_D W1_D[:, :F]  (atomic adds to g_feat);
-// and the weight gradients.  FUSE (the common widths, wgrad_fused: a tile of
+// and the weight gradients.  With cg: the cell's centre, semi-axes and
+// rotation through mu = x_n + R(Q_n)(O_pos S_n) and s = ratio S_n (atomic adds
+// per Gaussian), and the centre through the decoder inputs delta_n = |r|,
+// d_n = r / |r| (r = x_n - eye; columns F .. F+3 of W1, atomic adds per sample):
+//   dL/dx_n += dL/ddelta d_n + (I - d_n d_n^T) dL/dd_n / delta_n.  FUSE (the common widths, wgrad_fused: a tile of
 // 32 samples, 4Hp and the padded outputs Rp at most the CTA's threads,
 // I <= FW_I, Hp <= FW_H): thread t keeps row t of dW1 | db1 (over all decoders) and row
 // t of dW2 | db2 in registers, adds each tile's products from shared memory
@@ -518,7 +522,8 @@ __global__ void __launch_bounds__(256) k_decode_bwd(SceneDev sc, MlpShape S, con
                                                     const float *__restrict__ srec, long long nsamp,
                                                     const float *__restrict__ gdec,
                                                         float *__restrict__ g_feat, float *__restrict__ g_offset,
-                                                        float *__restrict__ rows, float *__restrict__ g_mlp) {
+                                                        float *__restrict__ rows, float *__restrict__ g_mlp,
+                                                        CellGrads cg) {
     extern __shared__ float4 smem4[];
     float *sm = reinterpret_cast<float *>(smem4);
     const int K = S.K, F = S.F, Hp = S.Hp, H4 = 4 * S.Hp, Rp = S.rb[4];
@@ -599,15 +604,17 @@ __global__ void __launch_bounds__(256) k_decode_bwd(SceneDev sc, MlpShape S, con
             float Ob[3], O[3], on;
             ball_offset(sc, g, Ob, O, on);
             const float lim = 1.0f - fminf(on, 1.0f);
-            float dlim = 0.f;
+            float dlim = 0.f, ratio[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 const float sg = sigmoid_fast(*ps[c]);
                 if (sg < lim) {
                     *ps[c] = gk[3 + c] * a.S[c] * sg * (1.0f - sg);
+                    ratio[c] = sg;
                 } else {
                     *ps[c] = 0.f;
                     dlim += gk[3 + c] * a.S[c];
+                    ratio[c] = lim;
                 }
             }
             float dOb[3];
@@ -627,6 +634,34 @@ __global__ void __launch_bounds__(256) k_decode_bwd(SceneDev sc, MlpShape S, con
 #pragma unroll
             for (int c = 0; c < 3; ++c)
                 if (dO[c] != 0.f) atomicAdd(g_offset + 3 * g + c, dO[c]);
+            // the cell's own parameters: mu = x + R (Ob S), s = ratio S
+            if (cg.center) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    if (gk[c] != 0.f) atomicAdd(cg.center + 3LL * a.n + c, gk[c]);
+            }
+            if (cg.axes) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float rt = a.R[c] * gk[0] + a.R[3 + c] * gk[1] + a.R[6 + c] * gk[2];
+                    const float v = Ob[c] * rt + gk[3 + c] * ratio[c];
+                    if (v != 0.f) atomicAdd(cg.axes + 3LL * a.n + c, v);
+                }
+            }
+            if (cg.quat) {
+                const long long N = sc.N;
+                const float cq[4] = {sc.cell[6 * N + a.n], sc.cell[7 * N + a.n], sc.cell[8 * N + a.n],
+                                     sc.cell[9 * N + a.n]};
+                float gR[9], gq[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) gR[3 * i + j] = gk[i] * Ob[j] * a.S[j];
+                rot_quat_adjoint(cq, gR, gq);
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    if (gq[c] != 0.f) atomicAdd(cg.quat + 4LL * a.n + c, gq[c]);
+            }
             // rotation (a zero output decodes to a constant)
             float qv[4];
 #pragma unroll
@@ -690,19 +725,22 @@ __global__ void __launch_bounds__(256) k_decode_bwd(SceneDev sc, MlpShape S, con
         }
         ready(WB, pk + S.g_w1r, H4 * S.I);
         if (q0 + (long long)gridDim.x * S.M < nsamp) prefetch(WA, pk + S.g_w1t, S.I * H4);
-        // dL/df = sum_jj dL/dh[jj] W1[jj][:F]; lanes take features lane and lane + 32
-        {
+        // dL/df = sum_jj dL/dh[jj] W1[jj][:F]; lanes take features cb + lane and
+        // cb + lane + 32 per group of 64 columns (and the view inputs F .. F+3
+        // when the cell centre's gradient is wanted)
+        for (int cb = 0; cb < (cg.center ? S.I : F); cb += 64) {
             const float *W = WB;
-            const int i0 = lane, i1 = lane + 32;
-            const bool u1 = i1 < F;
-            if (i0 < F) {
+            const int ncol = cg.center ? S.I : F;
+            const int i0 = cb + lane, i1 = cb + lane + 32;
+            const bool u1 = i1 < ncol;
+            if (i0 < ncol) {
                 float acc[8][2];
 #pragma unroll
                 for (int s = 0; s < 8; ++s) acc[s][0] = acc[s][1] = 0.f;
                 for (int D = 0; D < 4; ++D) {
                     const float *dh = DHt + hrow(S, D, 0) + 8 * warp;
                     const float *wd = W + D * Hp * S.I;
-                    if (F > 32) {  // (uniform) two features per lane
+                    if (ncol - cb > 32) {  // (uniform) two columns per lane
 #pragma unroll 2
                         for (int j = 0; j < Hp; ++j) {
                             const float4 da = *reinterpret_cast<const float4 *>(dh + j * S.LD);
@@ -727,13 +765,32 @@ __global__ void __launch_bounds__(256) k_decode_bwd(SceneDev sc, MlpShape S, con
                         }
                     }
                 }
+                // column i >= F: dL/d of the view input i - F (delta, then d) -> the centre
+                auto to_centre = [&](const float *p, long long n, int m, float gz) {
+                    const float delta = p[19], d[3] = {p[20], p[21], p[22]};
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        const float v = m == 0 ? gz * d[j] : gz * ((j == m - 1 ? 1.0f : 0.0f) - d[j] * d[m - 1]) / delta;
+                        if (v != 0.f) atomicAdd(cg.center + 3 * n + j, v);
+                    }
+                };
 #pragma unroll
                 for (int s = 0; s < 8; ++s) {
                     const float *p = info + (8 * warp + s) * DINFO;
                     if (__float_as_int(p[1]) == 0) continue;
                     const long long n = __float_as_int(p[0]);
-                    if (acc[s][0] != 0.f) atomicAdd(g_feat + n * F + i0, acc[s][0]);
-                    if (u1 && acc[s][1] != 0.f) atomicAdd(g_feat + n * F + i1, acc[s][1]);
+                    if (i0 < F) {
+                        if (acc[s][0] != 0.f) atomicAdd(g_feat + n * F + i0, acc[s][0]);
+                    } else {
+                        to_centre(p, n, i0 - F, acc[s][0]);
+                    }
+                    if (u1) {
+                        if (i1 < F) {
+                            if (acc[s][1] != 0.f) atomicAdd(g_feat + n * F + i1, acc[s][1]);
+                        } else {
+                            to_centre(p, n, i1 - F, acc[s][1]);
+                        }
+                    }
                 }
             }
         }
@@ -984,7 +1041,7 @@ void launch_decode(const ViewDesc *views, int n_views, int slot, const SceneDev 
 
 void launch_decode_bwd(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const uint32_t *samples,
                        long long nsamp, const float *gdec, float *g_mlp, float *g_feat, float *g_offset,
-                       float *scratch, cudaStream_t st) {
+                       CellGrads cg, float *scratch, cudaStream_t st) {
     if (nsamp <= 0 || !sc.feat) return;
     const MlpShape S = mlp_shape(sc.F, sc.H, sc.K, true);
     float *pk = scratch, *srec = scratch + up_to(S.g_total, 4), *rows = srec + nsamp * DINFO;
@@ -994,17 +1051,17 @@ void launch_decode_bwd(const ViewDesc *views, int n_views, int slot, const Scene
     if (wgrad_fused(S)) {
         const int b = persistent_grid(k_decode_bwd<4, true>, 32 * S.W, smem, tiles);
         k_decode_bwd<4, true><<<b, 32 * S.W, smem, st>>>(sc, S, pk, srec, nsamp, gdec, g_feat, g_offset, nullptr,
-                                                         g_mlp);
+                                                         g_mlp, cg);
         return;
     }
     if (S.HW == 4) {
         const int b = persistent_grid(k_decode_bwd<4, false>, 32 * S.W, smem, tiles);
         k_decode_bwd<4, false><<<b, 32 * S.W, smem, st>>>(sc, S, pk, srec, nsamp, gdec, g_feat, g_offset, rows,
-                                                          g_mlp);
+                                                          g_mlp, cg);
     } else {
         const int b = persistent_grid(k_decode_bwd<8, false>, 32 * S.W, smem, tiles);
         k_decode_bwd<8, false><<<b, 32 * S.W, smem, st>>>(sc, S, pk, srec, nsamp, gdec, g_feat, g_offset, rows,
-                                                          g_mlp);
+                                                          g_mlp, cg);
     }
     WgProblems pr{};
     pr.p[0] = WgProblem{S.row_dh, 4 * S.Hp, S.row_z, S.I, -1};

@@ -160,9 +160,15 @@ void launch_project_fwd(const ViewDesc *views, int n_views, int slot, const Scen
 // dL/dv per cell from the per-(view, cell) values gv of views [0, n_views)
 // (all of scene sc): g_cell_v[n] = sum over views (nullable), and for a
 // view-dependent v_n g_vsh[n][lm] = sum over views of gv Y_lm(d) where the
-// clamp was inactive (nullable).  Outputs overwritten.
+// clamp was inactive (nullable); both overwritten.  g_center [N][3]
+// (nullable, accumulated): the cell centres' gradient through d.
 void launch_cell_v_grad(const ViewDesc *views, int n_views, const SceneDev &sc, const float *gv, float *g_cell_v,
-                        float *g_vsh, cudaStream_t st);
+                        float *g_vsh, float *g_center, cudaStream_t st);
+// Gradients of the cell proxies' parameters ([N][3], [N][3], [N][4];
+// nullable, accumulated).
+struct CellGrads {
+    float *center, *axes, *quat;
+};
 // Comparator binning: one entry per (view, Gaussian), entry e = cell_base + g
 // (views with N = G, K = 1 entries); wsr selects the LC-WSR weight in r2.w.
 void launch_gauss_bin(const ViewDesc *views, int n_views, const SceneDev &sc, const BlendParams &bp, bool wsr,
@@ -193,9 +199,11 @@ void launch_project_bwd_neural(const ViewDesc *views, int n_views, int slot, con
 // of one view for every Gaussian (neural scenes with DGS_ALIGN_QUAT).
 void launch_cell_align(const SceneDev &sc, float *cell, const float *dec, int what, float *out_center, float *out_quat,
                        cudaStream_t st);
+// cg: the cell gradients through the decode (centre: the decoder inputs and
+// the Gaussian centres; axes: the centres and scales; rotation: the centres).
 void launch_decode_bwd(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const uint32_t *samples,
                        long long nsamp, const float *gdec, float *g_mlp, float *g_feat, float *g_offset,
-                       float *scratch, cudaStream_t st);
+                       CellGrads cg, float *scratch, cudaStream_t st);
 // One launch for every scene of the device scene table (dsz->n_scenes
 // entries, Gaussian counts <= G_cap, which sizes the grid).
 void launch_project_fwd_table(const ViewDesc *views, const SceneDev *scenes, long long G_cap, const uint32_t *count,

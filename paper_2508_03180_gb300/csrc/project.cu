@@ -143,12 +143,17 @@ __global__ void __launch_bounds__(128) k_project_fwd_table(const ViewDesc *__res
 // One thread per cell: sums the views' dL/dv_n and chains it to the SH
 // coefficients of a view-dependent v_n (d, Y and the clamp recomputed as in
 // the cell projection).
+//
+// g_center (nullable, accumulated): the cell centre's gradient through the
+// direction d = (x_n - eye)/|x_n - eye| of a view-dependent v_n,
+//   dL/dx_n += dL/dv_n (I - d d^T) grad_d(sum_lm k_lm Y_lm)(d) / |x_n - eye|.
 __global__ void k_cell_v_grad(const ViewDesc *__restrict__ views, int n_views, SceneDev sc,
-                              const float *__restrict__ gv, float *__restrict__ g_cell_v, float *__restrict__ g_vsh) {
+                              const float *__restrict__ gv, float *__restrict__ g_cell_v, float *__restrict__ g_vsh,
+                              float *__restrict__ g_center) {
     const long long N = sc.N;
     const int Cv = sc.vsh ? (sc.v_sh_degree + 1) * (sc.v_sh_degree + 1) : 0;
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
-        float tot = 0.f, acc[16];
+        float tot = 0.f, acc[16], gx[3] = {0.f, 0.f, 0.f};
 #pragma unroll
         for (int c = 0; c < 16; ++c) acc[c] = 0.f;
         for (int v = 0; v < n_views; ++v) {
@@ -166,10 +171,22 @@ __global__ void k_cell_v_grad(const ViewDesc *__restrict__ views, int n_views, S
             if (!(raw > 0.f && raw < 1.f)) continue;  // clamped: no gradient
 #pragma unroll
             for (int c = 0; c < 16; ++c) acc[c] += g * Y[c];
+            if (g_center) {
+                float k[16], gd[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+                for (int c = 0; c < 16; ++c) k[c] = c < Cv ? sc.vsh[c * N + n] : 0.f;
+                sh_grad_dot(d0, d1, d2, sc.v_sh_degree, k, gd);
+                const float dd = gd[0] * d0 + gd[1] * d1 + gd[2] * d2, s = g * il;
+                gx[0] += s * (gd[0] - dd * d0);
+                gx[1] += s * (gd[1] - dd * d1);
+                gx[2] += s * (gd[2] - dd * d2);
+            }
         }
         if (g_cell_v) g_cell_v[n] = tot;
         if (g_vsh)
             for (int c = 0; c < Cv; ++c) g_vsh[n * Cv + c] = acc[c];
+        if (g_center)
+            for (int j = 0; j < 3; ++j) g_center[3 * n + j] += gx[j];
     }
 }
 
@@ -187,9 +204,9 @@ void launch_project_fwd(const ViewDesc *views, int n_views, int slot, const Scen
 }
 
 void launch_cell_v_grad(const ViewDesc *views, int n_views, const SceneDev &sc, const float *gv, float *g_cell_v,
-                        float *g_vsh, cudaStream_t st) {
-    if (sc.N == 0 || (!g_cell_v && !g_vsh)) return;
-    k_cell_v_grad<<<grid_for(sc.N, 128), 128, 0, st>>>(views, n_views, sc, gv, g_cell_v, g_vsh);
+                        float *g_vsh, float *g_center, cudaStream_t st) {
+    if (sc.N == 0 || (!g_cell_v && !g_vsh && !g_center)) return;
+    k_cell_v_grad<<<grid_for(sc.N, 128), 128, 0, st>>>(views, n_views, sc, gv, g_cell_v, g_vsh, g_center);
 }
 
 void launch_gauss_bin(const ViewDesc *views, int n_views, const SceneDev &sc, const BlendParams &bp, bool wsr,
@@ -342,18 +359,7 @@ __device__ __forceinline__ bool view_geom_adjoint(const ViewDesc &Vw, const Gaus
             gR[3 * i + j] = gMm[3 * i + j] * p.scale[j];
         }
     // R(q_hat), then q_hat = q / |q|
-    const float qn = sqrtf(p.quat[0] * p.quat[0] + p.quat[1] * p.quat[1] + p.quat[2] * p.quat[2] + p.quat[3] * p.quat[3]);
-    const float w = p.quat[0] / qn, x = p.quat[1] / qn, y = p.quat[2] / qn, z = p.quat[3] / qn;
-    float gh[4];
-    gh[0] = 2.0f * (-z * gR[1] + y * gR[2] + z * gR[3] - x * gR[5] - y * gR[6] + x * gR[7]);
-    gh[1] = 2.0f * (y * gR[1] + z * gR[2] + y * gR[3] - 2.0f * x * gR[4] - w * gR[5] + z * gR[6] + w * gR[7] - 2.0f * x * gR[8]);
-    gh[2] = 2.0f * (-2.0f * y * gR[0] + x * gR[1] + w * gR[2] + x * gR[3] + z * gR[5] - w * gR[6] + z * gR[7] - 2.0f * y * gR[8]);
-    gh[3] = 2.0f * (-2.0f * z * gR[0] - w * gR[1] + x * gR[2] + w * gR[3] - 2.0f * z * gR[4] + y * gR[5] + x * gR[6] + y * gR[7]);
-    const float hq = (gh[0] * w + gh[1] * x + gh[2] * y + gh[3] * z);
-    gq[0] += (gh[0] - hq * w) / qn;
-    gq[1] += (gh[1] - hq * x) / qn;
-    gq[2] += (gh[2] - hq * y) / qn;
-    gq[3] += (gh[3] - hq * z) / qn;
+    rot_quat_adjoint(p.quat, gR, gq);
     return true;
 }
 

@@ -164,4 +164,23 @@ __device__ __forceinline__ bool gauss_record(const ViewDesc &Vw, const GaussIn &
     return true;
 }
 
+// dL/dq of a loss that depends on R(q / |q|) (q = (w, x, y, z) as stored)
+// through gR = dL/dR (row-major 3x3), added to gq: the derivative of each
+// entry of the rotation matrix in the unit quaternion, then the projection
+// of the normalisation, (I - q^ q^T) / |q|.
+__device__ __forceinline__ void rot_quat_adjoint(const float q[4], const float gR[9], float gq[4]) {
+    const float qn = sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    const float w = q[0] / qn, x = q[1] / qn, y = q[2] / qn, z = q[3] / qn;
+    float gh[4];
+    gh[0] = 2.0f * (-z * gR[1] + y * gR[2] + z * gR[3] - x * gR[5] - y * gR[6] + x * gR[7]);
+    gh[1] = 2.0f * (y * gR[1] + z * gR[2] + y * gR[3] - 2.0f * x * gR[4] - w * gR[5] + z * gR[6] + w * gR[7] - 2.0f * x * gR[8]);
+    gh[2] = 2.0f * (-2.0f * y * gR[0] + x * gR[1] + w * gR[2] + x * gR[3] + z * gR[5] - w * gR[6] + z * gR[7] - 2.0f * y * gR[8]);
+    gh[3] = 2.0f * (-2.0f * z * gR[0] - w * gR[1] + x * gR[2] + w * gR[3] - 2.0f * z * gR[4] + y * gR[5] + x * gR[6] + y * gR[7]);
+    const float hq = (gh[0] * w + gh[1] * x + gh[2] * y + gh[3] * z);
+    gq[0] += (gh[0] - hq * w) / qn;
+    gq[1] += (gh[1] - hq * x) / qn;
+    gq[2] += (gh[2] - hq * y) / qn;
+    gq[3] += (gh[3] - hq * z) / qn;
+}
+
 }  // namespace dgs

@@ -103,6 +103,11 @@ struct Workspace {
     long long total_px = 0, L = 0, n_entries = 0, n_records = 0;
     long long n_vis = 0;  // (view, cell) entries that survived culling: the first n_vis of zval after the depth sort
     bool bwd_done = false;
+    // A device-sized chain (dgs_render without stats): the pair count L lives
+    // on the device only (pair buffers sized L_cap), and L, n_vis and the
+    // chain's flags are read from h_small once it has completed (observe_chain).
+    bool async_pending = false;
+    long long L_cap = 0;
     dgs_status init();
     std::vector<DevBuf *> all();
     ~Workspace();
@@ -231,6 +236,9 @@ struct dgs_ctx {
     std::unique_ptr<dgs::Workspace> sort_ws;
     std::unique_ptr<dgs::ServeState> serve;
     uint64_t scene_epoch = 0;  // bumped when a scene's buffers go away
+    double pairs_per_tile = 0.0;         // largest (tile, cell) pairs per tile seen: sizes device-sized chains
+    dgs_status pending_status = DGS_OK;  // error of a completed device-sized chain, for the next render / backward
+    std::string pending_msg;
 };
 
 namespace dgs {
@@ -239,8 +247,15 @@ std::unique_ptr<Workspace> acquire_ws(dgs_ctx *ctx, cudaStream_t st, dgs_status 
 // holds ctx->mu).  Writes the images to out_img (device, [3][H][W] per view
 // back to back) and, if keep_rgb, also to ws.rgb.  grad_buffers: allocate and
 // zero the screen-space gradient accumulators for a later backward.
+// device_sized: no host synchronisation; the (tile, cell) pair buffers are
+// sized from ctx->pairs_per_tile and the kernels read the pair count from
+// device memory (see observe_chain).
 dgs_status chain_forward(dgs_ctx *ctx, Workspace &ws, const std::vector<ChainView> &views, float *out_img,
-                         bool keep_rgb, bool grad_buffers, cudaStream_t st);
+                         bool keep_rgb, bool grad_buffers, cudaStream_t st, bool device_sized = false);
+// Read a device-sized chain's sizes and flags once it has completed (wait:
+// block until then; otherwise look only if it has).  A pair overflow or a
+// sort that gave up becomes ctx->pending_status.
+dgs_status observe_chain(dgs_ctx *ctx, Workspace &ws, bool wait);
 ViewDesc make_view(const dgs_camera &c, int tile_base, long long pix_base, int slot, const Scene &sc,
                    long long cell_base, long long rec_base);
 }  // namespace dgs

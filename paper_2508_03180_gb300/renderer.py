@@ -178,12 +178,13 @@ class Context:
 
     def backward(self, state, dL: torch.Tensor, grads: dict, location: int = L.DGS_DEVICE):
         """grads: dict of preallocated tensors/arrays keyed g_mean, g_scale,
-        g_log_scale, g_quat, g_logit, g_sh, g_cell_v, g_cell_v_sh (any subset;
-        neural scenes: g_mlp, g_feat, g_offset, g_cell_v, g_cell_v_sh)."""
+        g_log_scale, g_quat, g_logit, g_sh, g_cell_v, g_cell_v_sh, g_cell_center,
+        g_cell_axes, g_cell_quat (any subset; neural scenes: g_mlp, g_feat,
+        g_offset and the cell gradients)."""
         g = L.dgs_grads()
         g.location = location
         for f in ("g_mean", "g_scale", "g_log_scale", "g_quat", "g_logit", "g_sh", "g_cell_v", "g_cell_v_sh",
-                  "g_mlp", "g_feat", "g_offset"):
+                  "g_mlp", "g_feat", "g_offset", "g_cell_center", "g_cell_axes", "g_cell_quat"):
             a = grads.get(f)
             setattr(g, f, None if a is None else (a.data_ptr() if isinstance(a, torch.Tensor) else a.ctypes.data))
         dl_ptr = dL.data_ptr() if isinstance(dL, torch.Tensor) else dL.ctypes.data

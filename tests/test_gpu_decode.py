@@ -103,7 +103,7 @@ def _neural_oracle_grads(sc, cams, dl_flat, gs, dec):
         d = dec[v]
         decided = (take(d[:, 0:3], ref["mean"], 3), take(d[:, 3:6], ref["scale"], 3), take(d[:, 6:10], ref["quat"], 4))
         _, r = oracle.neural_render_and_grad(sc, cam.as_array(), g, decided=decided, ndone=gv["nd"])
-        r = {k: r[k] for k in ("mlp", "feat", "offset")}
+        r = {k: r[k] for k in ("mlp", "feat", "offset", "cell_center", "cell_axes", "cell_quat")}
         tot = r if tot is None else {k: tot[k] + r[k] for k in tot}
     return tot
 
@@ -112,8 +112,8 @@ def _neural_oracle_grads(sc, cams, dl_flat, gs, dec):
                                                      (32, 32, 10, 1.0, "device"), (20, 36, 7, 1.0, "device"),
                                                      (64, 64, 32, 1.2, "device")])
 def test_gradients_through_the_decode(rctx, F, H, K, stretch, location):
-    """dL/d(weights, features, offsets) summed over two views against the
-    FP64 oracle.  stretch > 1 pushes some offsets outside the unit ball (the
+    """dL/d(weights, features, offsets) and of the cells' centres, semi-axes
+    and quaternions, summed over two views, against the FP64 oracle.  stretch > 1 pushes some offsets outside the unit ball (the
     projection onto it); host outputs go through the staging path.  The
     first three shapes take the weight gradients fused into the adjoint's
     tiles, the last two (a hidden layer wider than 32) the per-sample rows
@@ -130,11 +130,13 @@ def test_gradients_through_the_decode(rctx, F, H, K, stretch, location):
     dl = torch.randn(flat.numel(), generator=torch.Generator().manual_seed(K)).cuda()
     if location == "device":
         gr = dict(g_mlp=torch.zeros(P, device="cuda"), g_feat=torch.zeros(sc.N, F, device="cuda"),
-                  g_offset=torch.zeros(sc.G, 3, device="cuda"))
+                  g_offset=torch.zeros(sc.G, 3, device="cuda"), g_cell_center=torch.zeros(sc.N, 3, device="cuda"),
+                  g_cell_axes=torch.zeros(sc.N, 3, device="cuda"), g_cell_quat=torch.zeros(sc.N, 4, device="cuda"))
         rctx.backward(state, dl, gr)
     else:
         gr = dict(g_mlp=np.zeros(P, np.float32), g_feat=np.zeros((sc.N, F), np.float32),
-                  g_offset=np.zeros((sc.G, 3), np.float32))
+                  g_offset=np.zeros((sc.G, 3), np.float32), g_cell_center=np.zeros((sc.N, 3), np.float32),
+                  g_cell_axes=np.zeros((sc.N, 3), np.float32), g_cell_quat=np.zeros((sc.N, 4), np.float32))
         rctx.backward(state, dl, gr, location=L.DGS_HOST)
     torch.cuda.synchronize()
     try:
@@ -142,7 +144,8 @@ def test_gradients_through_the_decode(rctx, F, H, K, stretch, location):
         dec = rctx.read(state, L.DGS_BUF_DECODED, np.float32, (len(cams), sc.G, 14))
         ref = _neural_oracle_grads(sc, cams, dl.cpu().numpy(), gs, dec)
         got = {k: (v.cpu().numpy() if isinstance(v, torch.Tensor) else v) for k, v in gr.items()}
-        for k, name in (("g_mlp", "mlp"), ("g_feat", "feat"), ("g_offset", "offset")):
+        for k, name in (("g_mlp", "mlp"), ("g_feat", "feat"), ("g_offset", "offset"),
+                        ("g_cell_center", "cell_center"), ("g_cell_axes", "cell_axes"), ("g_cell_quat", "cell_quat")):
             assert np.abs(ref[name]).max() > 0, name
             assert_close_group(name, got[k], ref[name])
         if stretch > 1.0:

@@ -1,7 +1,8 @@
 """View-dependent calibration v_n (SH coefficients per cell, Sec. V-A) on the
 GPU against the oracle: v_n per (view, cell), images under the
 termination-count protocol, and dL/dv_n with its chain to the SH
-coefficients (gradient tolerance as for the other parameter groups)."""
+coefficients and to the cell centres through the view direction (gradient
+tolerance as for the other parameter groups)."""
 import numpy as np
 import pytest
 import torch
@@ -37,7 +38,8 @@ def test_view_dependent_v_render_and_gradients(rctx, deg):
     flat, state, _ = rctx.render(sid, cams, want_state=True)
     dl = torch.randn(flat.numel(), generator=torch.Generator().manual_seed(deg)).cuda()
     gr = dict(g_mean=torch.zeros(G, 3, device="cuda"), g_cell_v=torch.zeros(N, device="cuda"),
-              g_cell_v_sh=torch.zeros(N, Cv, device="cuda"))
+              g_cell_v_sh=torch.zeros(N, Cv, device="cuda"), g_cell_center=torch.full((N, 3), 7.0, device="cuda"),
+              g_cell_axes=torch.full((N, 3), 7.0, device="cuda"))
     rctx.backward(state, dl, gr)
     torch.cuda.synchronize()
     try:
@@ -56,7 +58,9 @@ def test_view_dependent_v_render_and_gradients(rctx, deg):
         assert_close_group("cell_v", gr["g_cell_v"].cpu(), ref["cell_v"])
         assert_close_group("cell_v_sh", gr["g_cell_v_sh"].cpu(), ref["cell_v_sh"])
         assert_close_group("mean", gr["g_mean"].cpu(), ref["mean"])
-        assert np.abs(ref["cell_v_sh"]).max() > 0
+        assert_close_group("cell_center", gr["g_cell_center"].cpu(), ref["cell_center"])
+        assert torch.all(gr["g_cell_axes"] == 0)  # overwritten: explicit cells reach the image only through v's direction
+        assert np.abs(ref["cell_v_sh"]).max() > 0 and np.abs(ref["cell_center"]).max() > 0
     finally:
         rctx.release_state(state)
         rctx.release_scene(sid)

@@ -70,3 +70,13 @@ def test_single_rank_needs_no_process_group():
     flat.fill_(2.0)
     bench.reduce_grads(flat, 1)  # one rank: no collective, unchanged
     assert torch.all(flat == 2.0)
+
+
+def test_serving_at_equal_p99_picks_the_highest_rate_within_each_target():
+    import bench
+    rows = [{"offered_rps": 200.0, "p99_ms": 1.0, "fps": 200.0}, {"offered_rps": 2500.0, "p99_ms": 2.3, "fps": 2490.0},
+            {"offered_rps": 3000.0, "p99_ms": 1.9, "fps": 2990.0}, {"offered_rps": 5000.0, "p99_ms": 14.0, "fps": 4300.0}]
+    got = bench.at_p99(rows, slos=(2.0, 5.0, 20.0, 0.5))
+    assert got["2ms"]["offered_rps"] == 3000.0 and got["5ms"]["offered_rps"] == 3000.0
+    assert got["20ms"] == {"offered_rps": 5000.0, "fps": 4300.0, "p99_ms": 14.0}
+    assert got["0.5ms"] is None

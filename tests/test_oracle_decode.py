@@ -201,3 +201,40 @@ def test_zero_rotation_output_is_the_identity():
     o_rot = sum(H * (F + 4) + H + n * H + n for n in odec.out_widths(K)[:3])
     assert np.all(g[o_rot:] == 0.0)       # the rotation decoder gets nothing
     assert np.abs(g[:o_rot]).max() > 0.0  # the others do
+
+
+def test_neural_cell_gradients_match_central_differences():
+    """dL/d of the cells' centres, semi-axes and quaternions through the
+    decode (decoder inputs delta_n and d_n, the centres x_n + R(Q_n)(O_pos S_n),
+    the scales ratio S_n) against FP64 central differences, with the decode's
+    decisions and the cells' footprints held fixed."""
+    import dataclasses
+    sc = synth.neural_scene(n_cells=24, K=3, F=6, H=5, seed=12, box=0.5, axes_lo=0.15, axes_hi=0.4)
+    cam = synth.small_camera(24, 24).as_array()
+    g = np.random.default_rng(7).standard_normal((3, 24, 24))
+    img, an = oracle.neural_render_and_grad(sc, cam, g)
+    nd = img["ndone"]
+    dec = oracle.decode_view(sc, cam)
+    decided = tuple(dec[k].reshape(sc.G, -1).astype(np.float32) for k in ("mean", "scale", "quat"))
+    rect0, _ = oracle.cell_rects(sc, cam)
+
+    def loss(s2):
+        assert np.array_equal(oracle.cell_rects(s2, cam)[0], rect0), "a footprint moved"
+        im, _ = oracle.neural_render_and_grad(s2, cam, g, decided=decided, ndone=nd)
+        return float((im["C"] * g).sum())
+
+    rng = np.random.default_rng(1)
+    h = 1e-6
+    for key in ("cell_center", "cell_axes", "cell_quat"):
+        arr = getattr(sc, key)
+        a = an[key].reshape(-1)
+        cand = np.nonzero(np.abs(a) > 1e-4 * np.abs(a).max())[0]
+        assert len(cand) >= 5, key
+        for i in rng.choice(cand, 6, replace=False):
+            vals = []
+            for s in (+1, -1):
+                pert = arr.astype(np.float64).copy().reshape(-1)
+                pert[i] += s * h
+                vals.append(loss(dataclasses.replace(sc, **{key: pert.reshape(arr.shape)})))
+            fd = (vals[0] - vals[1]) / (2 * h)
+            assert abs(fd - a[i]) <= 1e-6 * np.abs(a).max() + 1e-9, (key, i, fd, a[i])
