@@ -17,6 +17,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/dgs.h"
 #include "internal.cuh"
 #include "runtime.h"
@@ -200,13 +202,21 @@ Profiler::~Profiler() {
     for (auto e : spare) cudaEventDestroy(e);
 }
 
+// NVTX names of the stages (dgs_stage order): the host-side range around each
+// stage's launches, seen by nsys/ncu (--nvtx); a no-op without a tool attached.
+static const char *const kStageNames[] = {"dgs.cell_project", "dgs.depth_sort", "dgs.count_scan", "dgs.emit",
+                                          "dgs.tile_sort",    "dgs.tile_ranges", "dgs.project_fwd", "dgs.blend_fwd",
+                                          "dgs.blend_bwd",    "dgs.project_bwd", "dgs.decode",      "dgs.decode_bwd"};
+
 StageTimer::StageTimer(Profiler &p_, int s, cudaStream_t st_) : p(p_), stage(s), st(st_) {
+    if (s >= 0 && s < (int)(sizeof(kStageNames) / sizeof(kStageNames[0]))) nvtxRangePushA(kStageNames[s]);
     if (!p.on) return;
     a = p.take();
     cudaEventRecord(a, st);
 }
 
 StageTimer::~StageTimer() {
+    if (stage >= 0 && stage < (int)(sizeof(kStageNames) / sizeof(kStageNames[0]))) nvtxRangePop();
     if (!p.on || !a) return;
     cudaEvent_t b = p.take();
     cudaEventRecord(b, st);

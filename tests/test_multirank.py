@@ -60,6 +60,72 @@ def test_two_gloo_ranks():
     assert np.array_equal(lg0, want[7 * 10:7 * 11])  # logit block after mean, log-scale, quaternion
 
 
+_NAMES = (("g_mean", "mean"), ("g_log_scale", "log_scale"), ("g_quat", "quat"), ("g_logit", "logit"),
+          ("g_sh", "sh"))
+
+
+def _oracle_scene():
+    from paper_2508_03180_gb300 import synth
+    sc = synth.make_scene(30, 4, synth._box(-0.5, 0.5), 0.15, 0.4, 3, seed=5)
+    return sc, synth.sphere_cameras(2, 3.0, 24, 20, seed0=11)
+
+
+def _oracle_view_grads(sc, cam, rank):
+    import numpy as np
+    import oracle
+    g = np.random.default_rng(100 + rank).standard_normal((3, cam.H, cam.W))
+    return oracle.render_and_grad(sc, cam.as_array(), g)[2]
+
+
+def _oracle_rank_main(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), LOCAL_RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    sys.path.insert(0, ROOT)
+    import torch
+    import bench
+    w, r, _ = bench.dist_setup(None, backend="gloo")
+    sc, cams = _oracle_scene()
+    pg = _oracle_view_grads(sc, cams[r], r)  # this rank's view only
+    flat, gr = bench.flat_grads(sc.G, 16, "cpu")
+    for k, name in _NAMES:
+        gr[k].copy_(torch.from_numpy(pg[name].reshape(gr[k].shape)).float())
+    bench.reduce_grads(flat, w)
+    q.put((r, {k: v.numpy().copy() for k, v in gr.items()}))
+    import torch.distributed as dist
+    dist.destroy_process_group()
+
+
+def test_gradient_buffer_sums_the_ranks_views():
+    """Each of two gloo ranks writes the oracle's parameter gradients of its
+    own view into the data-parallel flat buffer; after the one all-reduce
+    every rank holds the gradients of the two-view loss (the oracle's sum over
+    both views) in the renderer's output layout."""
+    import socket
+    import numpy as np
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_oracle_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = dict(q.get(timeout=300) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    sys.path.insert(0, ROOT)
+    sc, cams = _oracle_scene()
+    both = [_oracle_view_grads(sc, cams[r], r) for r in range(2)]
+    for k, name in _NAMES:
+        want = both[0][name] + both[1][name]
+        assert np.abs(want).max() > 0, name
+        for r in range(2):
+            got = res[r][k].astype(np.float64).reshape(want.shape)
+            assert np.abs(got - want).max() <= 1e-6 * np.abs(want).max(), (r, name)
+
+
 def test_single_rank_needs_no_process_group():
     sys.path.insert(0, ROOT)
     import bench
