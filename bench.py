@@ -235,8 +235,9 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-SERVE_RATES = (200.0, 500.0, 1000.0, 1500.0, 2000.0, 2500.0, 3000.0, 3500.0, 4000.0, 4500.0, 5000.0, 6000.0)
-SERVE_SLO_MS = (2.0, 5.0, 20.0)
+SERVE_RATES = (200.0, 500.0, 1000.0, 1500.0, 2000.0, 2250.0, 2500.0, 2750.0, 3000.0, 3500.0, 4000.0, 4500.0,
+               5000.0, 6000.0)
+SERVE_SLO_MS = (2.0, 3.0, 5.0, 20.0)
 
 
 def at_p99(rows, slos=SERVE_SLO_MS):
@@ -769,13 +770,16 @@ def forward_chain(streaming, prof, steps, px, stats, scene, cnt, peaks, fp32_tfl
     return out
 
 
-def launches_per_step(stats):
+def launches_per_step(stats, device_sized=True):
     # kernels of one fwd+bwd step: cell projection 1; depth sort 2 + 4 passes; gather 1; scan 3;
     # emit 1; tile sort 2 + ceil(bits/8) passes; ranges 1; projection 1; blend 1; loss 2;
-    # blend adjoint 1; projection adjoint 2 (geometry, then colour)
+    # blend adjoint 1; projection adjoint 2 (geometry, then colour); a render without stats keeps
+    # the pair count on the device: + the pair-count clamp 1 and the tile sort's copy-back 1
+    # (which decides on the device whether the result needs it)
     tiles = int(stats.num_tiles)
     bits = max(1, math.ceil(math.log2(max(2, tiles))))
-    return 1 + (2 + 4) + 1 + 3 + 1 + (2 + math.ceil(bits / 8)) + 1 + 1 + 1 + 2 + 1 + 2
+    return (1 + (2 + 4) + 1 + 3 + 1 + (2 + math.ceil(bits / 8)) + 1 + 1 + 1 + 2 + 1 + 2
+            + (2 if device_sized else 0))
 
 
 if __name__ == "__main__":

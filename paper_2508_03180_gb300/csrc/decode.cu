@@ -516,8 +516,9 @@ __global__ void __launch_bounds__(256) k_decode(const ViewDesc *__restrict__ vie
 // stored per tile of M samples as unit rows of M values (the tile's
 // shared-memory layout, so they leave as float4 copies).  Decisions held
 // fixed: the ReLU masks, the side of the Eq. 11 minimum, sigma <= 0 (gdec is
-// zero there).
-template <int HW, bool FUSE>
+// zero there).  CELL: some cell gradient is requested (without, the cell
+// terms are compiled out).
+template <int HW, bool FUSE, bool CELL>
 __global__ void __launch_bounds__(256) k_decode_bwd(SceneDev sc, MlpShape S, const float *__restrict__ pk,
                                                     const float *__restrict__ srec, long long nsamp,
                                                     const float *__restrict__ gdec,
@@ -635,12 +636,12 @@ __global__ void __launch_bounds__(256) k_decode_bwd(SceneDev sc, MlpShape S, con
             for (int c = 0; c < 3; ++c)
                 if (dO[c] != 0.f) atomicAdd(g_offset + 3 * g + c, dO[c]);
             // the cell's own parameters: mu = x + R (Ob S), s = ratio S
-            if (cg.center) {
+            if (CELL && cg.center) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c)
                     if (gk[c] != 0.f) atomicAdd(cg.center + 3LL * a.n + c, gk[c]);
             }
-            if (cg.axes) {
+            if (CELL && cg.axes) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     const float rt = a.R[c] * gk[0] + a.R[3 + c] * gk[1] + a.R[6 + c] * gk[2];
@@ -648,7 +649,7 @@ __global__ void __launch_bounds__(256) k_decode_bwd(SceneDev sc, MlpShape S, con
                     if (v != 0.f) atomicAdd(cg.axes + 3LL * a.n + c, v);
                 }
             }
-            if (cg.quat) {
+            if (CELL && cg.quat) {
                 const long long N = sc.N;
                 const float cq[4] = {sc.cell[6 * N + a.n], sc.cell[7 * N + a.n], sc.cell[8 * N + a.n],
                                      sc.cell[9 * N + a.n]};
@@ -728,9 +729,10 @@ __global__ void __launch_bounds__(256) k_decode_bwd(SceneDev sc, MlpShape S, con
         // dL/df = sum_jj dL/dh[jj] W1[jj][:F]; lanes take features cb + lane and
         // cb + lane + 32 per group of 64 columns (and the view inputs F .. F+3
         // when the cell centre's gradient is wanted)
-        for (int cb = 0; cb < (cg.center ? S.I : F); cb += 64) {
+        const bool zin = CELL && cg.center != nullptr;  // the view inputs' columns too
+        for (int cb = 0; cb < (zin ? S.I : 1); cb += 64) {
             const float *W = WB;
-            const int ncol = cg.center ? S.I : F;
+            const int ncol = zin ? S.I : F;
             const int i0 = cb + lane, i1 = cb + lane + 32;
             const bool u1 = i1 < ncol;
             if (i0 < ncol) {
@@ -1048,21 +1050,23 @@ void launch_decode_bwd(const ViewDesc *views, int n_views, int slot, const Scene
     decode_prep(views, n_views, slot, sc, S, samples, nsamp, pk, srec, st);
     const size_t smem = sizeof(float) * (size_t)S.s_total;
     const long long tiles = (nsamp + S.M - 1) / S.M;
+    const bool cell = cg.center || cg.axes || cg.quat;
+#define DGS_DBWD(HWV, FUSEV, CELLV, ROWS)                                                                      \
+    do {                                                                                                      \
+        const int b = persistent_grid(k_decode_bwd<HWV, FUSEV, CELLV>, 32 * S.W, smem, tiles);                \
+        k_decode_bwd<HWV, FUSEV, CELLV><<<b, 32 * S.W, smem, st>>>(sc, S, pk, srec, nsamp, gdec, g_feat,      \
+                                                                   g_offset, ROWS, g_mlp, cg);                \
+    } while (0)
     if (wgrad_fused(S)) {
-        const int b = persistent_grid(k_decode_bwd<4, true>, 32 * S.W, smem, tiles);
-        k_decode_bwd<4, true><<<b, 32 * S.W, smem, st>>>(sc, S, pk, srec, nsamp, gdec, g_feat, g_offset, nullptr,
-                                                         g_mlp, cg);
+        if (cell) DGS_DBWD(4, true, true, nullptr); else DGS_DBWD(4, true, false, nullptr);
         return;
     }
     if (S.HW == 4) {
-        const int b = persistent_grid(k_decode_bwd<4, false>, 32 * S.W, smem, tiles);
-        k_decode_bwd<4, false><<<b, 32 * S.W, smem, st>>>(sc, S, pk, srec, nsamp, gdec, g_feat, g_offset, rows,
-                                                          g_mlp, cg);
+        if (cell) DGS_DBWD(4, false, true, rows); else DGS_DBWD(4, false, false, rows);
     } else {
-        const int b = persistent_grid(k_decode_bwd<8, false>, 32 * S.W, smem, tiles);
-        k_decode_bwd<8, false><<<b, 32 * S.W, smem, st>>>(sc, S, pk, srec, nsamp, gdec, g_feat, g_offset, rows,
-                                                          g_mlp, cg);
+        if (cell) DGS_DBWD(8, false, true, rows); else DGS_DBWD(8, false, false, rows);
     }
+#undef DGS_DBWD
     WgProblems pr{};
     pr.p[0] = WgProblem{S.row_dh, 4 * S.Hp, S.row_z, S.I, -1};
     for (int D = 0; D < 4; ++D) pr.p[1 + D] = WgProblem{S.row_do + S.rb[D], S.nout[D], S.row_h + D * S.Hp, S.H, D};
