@@ -85,3 +85,30 @@ def test_pair_overflow_is_reported_by_the_next_call_and_recovers():
         assert torch.equal(img, ref)
     finally:
         ctx.close()
+
+
+def test_backward_of_an_overflowed_state_reports_it():
+    """A state whose render overflowed the pair capacity: once its chain has
+    completed, dgs_render_backward on it returns DGS_ERR_CAPACITY instead of
+    gradients of the incomplete render."""
+    scene = synth.scene_small(n_cells=2048, sh_degree=1)
+    far = synth.sphere_cameras(1, 40.0, 1280, 720, seed0=7)
+    near = synth.sphere_cameras(4, 2.2, 1280, 720, seed0=7)
+    ctx = Context()
+    try:
+        sid = ctx.upload_scene(scene)
+        ctx.render(sid, far)
+        img, state, _ = ctx.render(sid, near, want_state=True)  # device-sized: overflows
+        torch.cuda.synchronize()
+        g = dict(g_mean=torch.zeros(scene.G, 3, device="cuda"))
+        with pytest.raises(L.DgsError) as ei:
+            ctx.backward(state, torch.ones_like(img), g)
+        assert ei.value.code == L.DGS_ERR_CAPACITY
+        ctx.release_state(state)
+        img2, state2, _ = ctx.render(sid, near, want_state=True)  # the capacity has grown
+        ctx.backward(state2, torch.ones_like(img2), g)
+        torch.cuda.synchronize()
+        assert g["g_mean"].abs().max() > 0
+        ctx.release_state(state2)
+    finally:
+        ctx.close()
