@@ -49,7 +49,8 @@ enum {
     DGS_ERR_BUSY = -6,        /* request queue full; retry later */
     DGS_ERR_CAPACITY = -7,    /* a size exceeds a fixed maximum of the call */
     DGS_ERR_GUARD = -8,       /* debug mode: a guard word next to a device buffer was overwritten */
-    DGS_ERR_WORKER = -9       /* the serving worker stopped after a host-side fault; restart serving */
+    DGS_ERR_WORKER = -9,      /* the serving worker stopped after a host-side fault; restart serving */
+    DGS_ERR_CANCELLED = -10   /* a serving request cancelled by dgs_cancel */
 };
 
 /* Where an argument array lives.  DGS_HOST arrays may be pageable or
@@ -186,6 +187,23 @@ dgs_status dgs_scene_upload(dgs_ctx *ctx, const dgs_scene_desc *desc, uint32_t *
  * for device inputs; host inputs synchronise the stream before return. */
 dgs_status dgs_scene_update(dgs_ctx *ctx, uint32_t scene_id, const dgs_scene_desc *desc, dgs_stream stream);
 dgs_status dgs_scene_release(dgs_ctx *ctx, uint32_t scene_id);
+
+/* Scene files (the one persisted state of the renderer).  Little-endian: a
+ * 40-byte header -- char magic[4] = "DGS1", uint32 version = 1, int64
+ * num_cells, int32 K, sh_degree, v_sh_degree (-1: scalar v_n), feat_dim and
+ * hidden (0: explicit Gaussians), uint32 reserved -- then the scene's float32
+ * arrays in the layouts of dgs_scene_desc, in this order: cell_center,
+ * cell_axes, cell_quat, cell_v; explicit Gaussians: g_mean, g_scale,
+ * g_quat, g_logit, g_sh; neural cells: cell_feat, g_offset, mlp; then
+ * cell_v_sh if v_sh_degree >= 0.
+ * dgs_scene_save writes scene_id's current parameters to `path`; it reads them
+ * on the legacy default stream and returns when the file is closed, so work on
+ * non-blocking streams that writes the scene must be synchronised first.
+ * dgs_scene_load reads such a file and uploads it as a new scene, as
+ * dgs_scene_upload would: NOT_FOUND if the file cannot be opened,
+ * INVALID_ARG if it is not a version-1 scene file of consistent size. */
+dgs_status dgs_scene_save(dgs_ctx *ctx, uint32_t scene_id, const char *path);
+dgs_status dgs_scene_load(dgs_ctx *ctx, const char *path, uint32_t *scene_id);
 
 /* ---------------------------------------------------------------- cameras */
 
@@ -526,6 +544,15 @@ dgs_status dgs_submit(dgs_ctx *ctx, const dgs_request *req, uint64_t *ticket);
  * timeout_us < 0) and dgs_submit returns DGS_ERR_WORKER until serving is
  * stopped and started again. */
 dgs_status dgs_poll(dgs_ctx *ctx, uint64_t ticket, int64_t timeout_us, dgs_result *out);
+
+/* Cancel a submitted request.  Still queued: it leaves the queue and its
+ * result (status DGS_ERR_CANCELLED) is ready at once.  Admitted into a batch
+ * that is on the GPU: the batch runs on (the request's output may be written),
+ * the other requests of the batch are not affected, and the request completes
+ * with status DGS_ERR_CANCELLED.  Already finished: nothing changes (the
+ * result keeps its own status).  NOT_FOUND for an unknown or consumed ticket;
+ * the ticket stays valid until polled. */
+dgs_status dgs_cancel(dgs_ctx *ctx, uint64_t ticket);
 
 /* Counters of the serving worker since dgs_serve_start: batches launched
  * (re-runs included), graphs captured, re-runs after a pair-buffer overflow,

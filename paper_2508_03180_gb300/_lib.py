@@ -22,6 +22,7 @@ DGS_ERR_BUSY = -6
 DGS_ERR_CAPACITY = -7
 DGS_ERR_GUARD = -8
 DGS_ERR_WORKER = -9
+DGS_ERR_CANCELLED = -10
 DGS_FAULT_ALLOC = 1
 DGS_FAULT_SORT_WAIT = 2
 DGS_FAULT_SERVE_WORKER = 3
@@ -138,6 +139,8 @@ _SIGS = {
     "dgs_scene_upload": (C.c_int32, [_P, C.POINTER(dgs_scene_desc), C.POINTER(C.c_uint32)]),
     "dgs_scene_update": (C.c_int32, [_P, C.c_uint32, C.POINTER(dgs_scene_desc), _P]),
     "dgs_scene_release": (C.c_int32, [_P, C.c_uint32]),
+    "dgs_scene_save": (C.c_int32, [_P, C.c_uint32, C.c_char_p]),
+    "dgs_scene_load": (C.c_int32, [_P, C.c_char_p, C.POINTER(C.c_uint32)]),
     "dgs_camera_set": (C.c_int32, [_P, C.c_uint32, C.POINTER(dgs_camera)]),
     "dgs_render": (C.c_int32, [_P, C.c_uint32, C.c_int32, C.POINTER(C.c_uint32), _P, C.c_int32, C.POINTER(_P), _P,
                                C.POINTER(dgs_stats)]),
@@ -159,6 +162,7 @@ _SIGS = {
     "dgs_serve_stop": (C.c_int32, [_P]),
     "dgs_submit": (C.c_int32, [_P, C.POINTER(dgs_request), C.POINTER(C.c_uint64)]),
     "dgs_poll": (C.c_int32, [_P, C.c_uint64, C.c_int64, C.POINTER(dgs_result)]),
+    "dgs_cancel": (C.c_int32, [_P, C.c_uint64]),
     "dgs_debug_guards": (C.c_int32, [C.c_int32]),
     "dgs_debug_check_guards": (C.c_int32, [C.POINTER(C.c_int64)]),
     "dgs_debug_inject_fault": (C.c_int32, [_P, C.c_int32, C.c_int32]),
@@ -240,6 +244,16 @@ def dgs_scene_update(ctx, scene_id: int, desc: dgs_scene_desc, stream: int = 0):
 
 def dgs_scene_release(ctx, scene_id: int):
     check(load().dgs_scene_release(ctx, scene_id), ctx)
+
+
+def dgs_scene_save(ctx, scene_id: int, path) -> None:
+    check(load().dgs_scene_save(ctx, scene_id, os.fsencode(path)), ctx)
+
+
+def dgs_scene_load(ctx, path) -> int:
+    sid = C.c_uint32()
+    check(load().dgs_scene_load(ctx, os.fsencode(path), C.byref(sid)), ctx)
+    return sid.value
 
 
 def dgs_camera_set(ctx, slot: int, cam: dgs_camera):
@@ -336,6 +350,10 @@ def dgs_submit(ctx, req: dgs_request) -> int:
     t = C.c_uint64()
     check(load().dgs_submit(ctx, C.byref(req), C.byref(t)), ctx)
     return t.value
+
+
+def dgs_cancel(ctx, ticket: int):
+    check(load().dgs_cancel(ctx, ticket), ctx)
 
 
 def dgs_poll(ctx, ticket: int, timeout_us: int):

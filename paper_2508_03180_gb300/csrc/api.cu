@@ -423,6 +423,158 @@ static dgs_status check_desc(const dgs_scene_desc *d, bool need_cells = true) {
     return DGS_OK;
 }
 
+// ------------------------------------------------------------------ scene files
+struct DgsFileHeader {
+    char magic[4];
+    uint32_t version;
+    int64_t num_cells;
+    int32_t K, sh_degree, v_sh_degree, feat_dim, hidden;
+    uint32_t reserved;
+};
+static_assert(sizeof(DgsFileHeader) == 40, "the scene file header is 40 bytes");
+
+extern "C" dgs_status dgs_scene_save(dgs_ctx *ctx, uint32_t scene_id, const char *path) {
+    if (!ctx || !path) return set_error(DGS_ERR_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    CK(cudaSetDevice(ctx->cfg.device));
+    auto it = ctx->scenes.find(scene_id);
+    if (it == ctx->scenes.end()) return set_error(DGS_ERR_NOT_FOUND, "unknown scene id");
+    const Scene &sc = *it->second;
+    const int64_t N = sc.N, G = sc.G;
+    DgsFileHeader h{};
+    memcpy(h.magic, "DGS1", 4);
+    h.version = 1;
+    h.num_cells = N;
+    h.K = sc.K;
+    h.sh_degree = sc.deg;
+    h.v_sh_degree = sc.vdeg;
+    h.feat_dim = sc.F;
+    h.hidden = sc.H;
+    // every array back to its row-major layout (the inverse of fill_scene's transposes)
+    struct Part { const float *planes; int64_t rows; int cols; int64_t stride; };
+    const float *cell = (const float *)sc.cell.p;
+    std::vector<Part> parts = {{cell, N, 3, N}, {cell + 3 * N, N, 3, N}, {cell + 6 * N, N, 4, N}, {cell + 10 * N, N, 1, N}};
+    if (sc.F > 0) {
+        parts.push_back({(const float *)sc.feat.p, N * sc.F, 1, N * sc.F});
+        parts.push_back({(const float *)sc.goff.p, G, 3, G});
+        parts.push_back({(const float *)sc.mlp.p, 1, neural_weights(sc), 1});
+    } else {
+        const float *gs = (const float *)sc.gauss.p;
+        parts.push_back({gs, G, 3, G});
+        parts.push_back({gs + 3 * G, G, 3, G});
+        parts.push_back({gs + 6 * G, G, 4, G});
+        parts.push_back({gs + 10 * G, G, 1, G});
+        parts.push_back({(const float *)sc.sh.p, G, 3 * sc.C, G});
+    }
+    if (sc.vdeg >= 0) parts.push_back({(const float *)sc.vsh.p, N, sc.Cv, N});
+    int64_t total = 0;
+    for (const Part &q : parts) total += q.rows * q.cols;
+    std::vector<float> host((size_t)total);
+    if (total > 0) {
+        dgs_status s = ctx->aux.ensure(sizeof(float) * total);
+        if (s) return s;
+        float *stage = (float *)ctx->aux.p;
+        int64_t o = 0;
+        for (const Part &q : parts) {
+            launch_soa_to_aos(q.planes, q.rows, q.cols, q.stride, stage + o, 0);
+            o += q.rows * q.cols;
+        }
+        CK(cudaGetLastError());
+        CK(cudaMemcpy(host.data(), stage, sizeof(float) * total, cudaMemcpyDeviceToHost));
+    }
+    FILE *f = fopen(path, "wb");
+    if (!f) return set_error(DGS_ERR_NOT_FOUND, std::string("cannot open ") + path + " for writing");
+    const bool ok = fwrite(&h, sizeof(h), 1, f) == 1 &&
+                    (total == 0 || fwrite(host.data(), sizeof(float), (size_t)total, f) == (size_t)total);
+    const bool closed = fclose(f) == 0;
+    if (!ok || !closed) return set_error(DGS_ERR_INVALID_ARG, std::string("writing ") + path + " failed");
+    return DGS_OK;
+}
+
+extern "C" dgs_status dgs_scene_load(dgs_ctx *ctx, const char *path, uint32_t *scene_id) {
+    if (!ctx || !path || !scene_id) return set_error(DGS_ERR_INVALID_ARG, "NULL argument");
+    FILE *f = fopen(path, "rb");
+    if (!f) return set_error(DGS_ERR_NOT_FOUND, std::string("cannot open ") + path);
+    DgsFileHeader h{};
+    const bool got = fread(&h, sizeof(h), 1, f) == 1;
+    const bool shape_ok = got && memcmp(h.magic, "DGS1", 4) == 0 && h.version == 1 && h.num_cells >= 0 &&
+                          h.num_cells < (1LL << 31) && h.K >= 1 && h.K <= kMaxK && h.sh_degree >= 0 &&
+                          h.sh_degree <= 3 && h.v_sh_degree >= -1 && h.v_sh_degree <= 3 &&
+                          ((h.feat_dim == 0 && h.hidden == 0) ||
+                           (h.feat_dim >= 1 && h.feat_dim <= 64 && h.hidden >= 1 && h.hidden <= 64));
+    if (!shape_ok) {
+        fclose(f);
+        return set_error(DGS_ERR_INVALID_ARG, std::string(path) + " is not a version-1 scene file");
+    }
+    const int64_t N = h.num_cells, G = N * h.K;
+    const int64_t C = (h.sh_degree + 1) * (h.sh_degree + 1);
+    const int64_t Cv = h.v_sh_degree >= 0 ? (h.v_sh_degree + 1) * (h.v_sh_degree + 1) : 0;
+    Scene probe;  // sizes only: the packed weight count of a neural scene
+    probe.K = h.K;
+    probe.F = h.feat_dim;
+    probe.H = h.hidden;
+    const int64_t P = h.feat_dim > 0 ? neural_weights(probe) : 0;
+    const int64_t sizes_cells[4] = {3 * N, 3 * N, 4 * N, N};
+    std::vector<int64_t> sizes(sizes_cells, sizes_cells + 4);
+    if (h.feat_dim > 0) {
+        sizes.push_back(N * h.feat_dim);
+        sizes.push_back(3 * G);
+        sizes.push_back(P);
+    } else {
+        for (int64_t n : {3 * G, 3 * G, 4 * G, G, 3 * C * G}) sizes.push_back(n);
+    }
+    if (Cv) sizes.push_back(Cv * N);
+    int64_t total = 0;
+    for (int64_t n : sizes) total += n;
+    // the file's length must match its header before anything is allocated for it
+    const bool sized = fseek(f, 0, SEEK_END) == 0 && (int64_t)ftell(f) == (int64_t)sizeof(h) + 4 * total &&
+                       fseek(f, (long)sizeof(h), SEEK_SET) == 0;
+    if (!sized) {
+        fclose(f);
+        return set_error(DGS_ERR_INVALID_ARG, std::string(path) + ": size does not match its header");
+    }
+    std::vector<float> data((size_t)total);
+    const bool body = total == 0 || fread(data.data(), sizeof(float), (size_t)total, f) == (size_t)total;
+    fclose(f);
+    if (!body) return set_error(DGS_ERR_INVALID_ARG, std::string("reading ") + path + " failed");
+    std::vector<const float *> arr;
+    int64_t o = 0;
+    for (int64_t n : sizes) {
+        arr.push_back(data.data() + o);
+        o += n;
+    }
+    dgs_scene_desc d{};
+    d.num_cells = N;
+    d.K = h.K;
+    d.sh_degree = h.sh_degree;
+    d.location = DGS_HOST;
+    d.cell_center = arr[0];
+    d.cell_axes = arr[1];
+    d.cell_quat = arr[2];
+    d.cell_v = arr[3];
+    dgs_neural_desc nd{};
+    size_t k = 4;
+    if (h.feat_dim > 0) {
+        nd.feat_dim = h.feat_dim;
+        nd.hidden = h.hidden;
+        nd.cell_feat = arr[k++];
+        nd.g_offset = arr[k++];
+        nd.mlp = arr[k++];
+        d.neural = &nd;
+    } else {
+        d.g_mean = arr[k++];
+        d.g_scale = arr[k++];
+        d.g_quat = arr[k++];
+        d.g_logit = arr[k++];
+        d.g_sh = arr[k++];
+    }
+    if (Cv) {
+        d.cell_v_sh = arr[k++];
+        d.v_sh_degree = h.v_sh_degree;
+    }
+    return dgs_scene_upload(ctx, &d, scene_id);
+}
+
 extern "C" dgs_status dgs_scene_upload(dgs_ctx *ctx, const dgs_scene_desc *d, uint32_t *scene_id) {
     if (!ctx || !scene_id) return set_error(DGS_ERR_INVALID_ARG, "NULL argument");
     dgs_status s = check_desc(d);

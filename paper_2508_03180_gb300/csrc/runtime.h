@@ -169,6 +169,7 @@ struct ServeState {
     std::deque<PendingReq> pending;
     std::unordered_map<uint64_t, dgs_result> finished;
     std::set<uint64_t> open;                // submitted and not yet consumed by poll
+    std::set<uint64_t> cancelled;           // admitted requests cancelled while their batch ran
     uint64_t next_ticket = 1;
     int64_t reserved = 0;                   // admission estimates of batches in flight
     int64_t budget = 0;

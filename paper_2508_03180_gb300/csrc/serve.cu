@@ -51,7 +51,7 @@ void finish(ServeState &S, InflightBatch &b, dgs_status st) {
     std::lock_guard<std::mutex> lk(S.m);
     for (auto &r : b.reqs) {
         dgs_result res;
-        res.status = st;
+        res.status = S.cancelled.erase(r.ticket) ? DGS_ERR_CANCELLED : st;
         res.batch_size = (int32_t)b.reqs.size();
         res.t_submit_ms = r.t_submit;
         res.t_start_ms = b.t_start;
@@ -588,6 +588,29 @@ extern "C" dgs_status dgs_submit(dgs_ctx *ctx, const dgs_request *req, uint64_t 
     S.open.insert(p.ticket);
     *ticket = p.ticket;
     S.cv_work.notify_one();
+    return DGS_OK;
+}
+
+extern "C" dgs_status dgs_cancel(dgs_ctx *ctx, uint64_t ticket) {
+    if (!ctx) return set_error(DGS_ERR_INVALID_ARG, "NULL ctx");
+    if (!ctx->serve) return set_error(DGS_ERR_INVALID_ARG, "serving is not started");
+    ServeState &S = *ctx->serve;
+    std::lock_guard<std::mutex> lk(S.m);
+    if (!S.open.count(ticket)) return set_error(DGS_ERR_NOT_FOUND, "unknown or consumed ticket");
+    if (S.finished.count(ticket)) return DGS_OK;  // too late: the result keeps its own status
+    for (auto it = S.pending.begin(); it != S.pending.end(); ++it) {
+        if (it->ticket != ticket) continue;
+        dgs_result res;
+        res.status = DGS_ERR_CANCELLED;
+        res.batch_size = 0;
+        res.t_submit_ms = it->t_submit;
+        res.t_start_ms = res.t_done_ms = now_ms();
+        S.pending.erase(it);
+        S.finished[ticket] = res;
+        S.cv_done.notify_all();
+        return DGS_OK;
+    }
+    S.cancelled.insert(ticket);  // admitted: its batch reports it cancelled when it completes
     return DGS_OK;
 }
 

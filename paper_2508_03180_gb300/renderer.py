@@ -110,6 +110,14 @@ class Context:
     def release_scene(self, scene_id: int):
         L.dgs_scene_release(self.ctx, scene_id)
 
+    def save_scene(self, scene_id: int, path) -> None:
+        """Write the scene's current parameters to a scene file."""
+        L.dgs_scene_save(self.ctx, scene_id, path)
+
+    def load_scene(self, path) -> int:
+        """Upload the scene stored in a scene file; returns its id."""
+        return L.dgs_scene_load(self.ctx, path)
+
     # ------------------------------------------------------------ cameras
     def set_camera(self, slot: int, cam):
         L.dgs_camera_set(self.ctx, slot, _camera_struct(cam))
@@ -263,3 +271,6 @@ class Context:
 
     def poll(self, ticket: int, timeout_us: int = -1):
         return L.dgs_poll(self.ctx, ticket, timeout_us)
+
+    def cancel(self, ticket: int):
+        L.dgs_cancel(self.ctx, ticket)

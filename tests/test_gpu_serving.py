@@ -200,3 +200,50 @@ def test_empty_scene_in_a_served_batch():
     for ch in range(3):
         assert torch.all(outs[0].view(3, -1)[ch] == bg[ch])
     c.close()
+
+
+def test_cancel_queued_and_running_requests_leaves_the_others_intact(scenes):
+    """Cancelling requests, newest first, while the queue is long: each one
+    still queued or in a batch on the GPU completes with DGS_ERR_CANCELLED
+    (the newest, cancelled right after its submission behind a long queue,
+    certainly does); one that had already finished keeps status 0 and its
+    image.  Every request not cancelled, including those batched with a
+    cancelled one, returns exactly the image dgs_render gives it alone."""
+    from paper_2508_03180_gb300 import _lib as L
+    c = _ctx()
+    sids = [c.upload_scene(s) for s in scenes]
+    cams = [synth.sphere_cameras(1, 3.0, 1280, 720, seed0=50 + i)[0] for i in range(60)]
+    ref = []
+    for i, cam in enumerate(cams):
+        img, _, _ = c.render(sids[i % 2], [cam])
+        ref.append(img.clone())
+    torch.cuda.synchronize()
+    c.serve_start(max_batch=4)
+    outs = [torch.zeros_like(r) for r in ref]
+    tickets = [c.submit(sids[i % 2], cam, outs[i]) for i, cam in enumerate(cams)]
+    cancel = set(range(1, 60, 3))
+    for i in sorted(cancel, reverse=True):
+        c.cancel(tickets[i])
+    results = [c.poll(t, 10_000_000) for t in tickets]
+    # cancelled after it finished: the result keeps its own status
+    t_late = c.submit(sids[0], cams[0], outs[0])
+    time.sleep(0.5)
+    c.cancel(t_late)
+    late = c.poll(t_late, 10_000_000)
+    with pytest.raises(L.DgsError) as ei:
+        c.cancel(t_late)  # consumed by the poll
+    assert ei.value.code == L.DGS_ERR_NOT_FOUND
+    c.serve_stop()
+    torch.cuda.synchronize()
+    assert late is not None and late.status == 0
+    assert results[max(cancel)].status == L.DGS_ERR_CANCELLED
+    n_cancelled = 0
+    for i, r in enumerate(results):
+        assert r is not None, i
+        if i in cancel and r.status == L.DGS_ERR_CANCELLED:
+            n_cancelled += 1
+            continue
+        assert r.status == 0, (i, r.status)
+        assert torch.equal(outs[i], ref[i]), i
+    print(f"{n_cancelled} of {len(cancel)} cancellations took effect")
+    c.close()
