@@ -470,11 +470,13 @@ dgs_status dgs_render_compare(dgs_ctx *ctx, uint32_t scene_id, int32_t n_views, 
  * ignored otherwise), sigma <= 0 weighing 0; their Gaussians move with the
  * cell (the offsets are in the cell's frame).
  * out_center [N][3], out_quat [N][4] (nullable): the new values, in
- * out_location memory (host outputs synchronise the stream).  Runs on
+ * out_location memory (host outputs synchronise the stream, and so does a
+ * neural DGS_ALIGN_QUAT, whose decode is checked).  Runs on
  * `stream`; renders of the scene on other streams must be ordered against
  * it by the caller (as for dgs_scene_update).
  * Errors: INVALID_ARG (what, location, camera slot unset for a neural
- * DGS_ALIGN_QUAT), NOT_FOUND (scene), OOM. */
+ * DGS_ALIGN_QUAT), NOT_FOUND (scene), OOM, TIMEOUT (a tensor-core
+ * completion wait of the decode gave up). */
 #define DGS_ALIGN_QUAT 1
 #define DGS_ALIGN_CENTER 2
 dgs_status dgs_cell_align(dgs_ctx *ctx, uint32_t scene_id, int32_t what, int32_t cam_slot, float *out_center,

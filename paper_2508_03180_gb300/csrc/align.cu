@@ -135,7 +135,8 @@ extern "C" dgs_status dgs_cell_align(dgs_ctx *ctx, uint32_t scene_id, int32_t wh
     const size_t o_pk = up(sizeof(ViewDesc)),
                  o_dec = o_pk + up(decode ? sizeof(float) * decode_scratch_floats(sc.F, sc.H, sc.K, N, G, false) : 0),
                  o_stg = o_dec + up(decode ? sizeof(float) * kDecF * G : 0),
-                 total = o_stg + (out_location == DGS_HOST ? sizeof(float) * 7 * N : 0);
+                 o_err = o_stg + up(out_location == DGS_HOST ? sizeof(float) * 7 * N : 0),
+                 total = o_err + 256;
     dgs_status s;
     if ((s = ctx->align_tmp.ensure(total))) return s;
     char *base = (char *)ctx->align_tmp.p;
@@ -145,8 +146,9 @@ extern "C" dgs_status dgs_cell_align(dgs_ctx *ctx, uint32_t scene_id, int32_t wh
         const ViewDesc v = make_view(ctx->cams[cam_slot], 0, 0, 0, sc, 0, 0);
         CK(cudaMemcpyAsync(base, &v, sizeof(v), cudaMemcpyHostToDevice, st));  // pageable: staged before return
         dec = (float *)(base + o_dec);
+        CK(cudaMemsetAsync(base + o_err, 0, 4, st));
         launch_decode((const ViewDesc *)base, 1, 0, sd, nullptr, N, dec, (float *)(base + o_pk), nullptr,
-                      BlendParams{}, nullptr, nullptr, st);  // every cell of the one view; no records
+                      BlendParams{}, nullptr, nullptr, (uint32_t *)(base + o_err), st);  // every cell of the one view; no records
     }
     float *oc = out_center, *oq = out_quat;
     if (out_location == DGS_HOST) {
@@ -160,6 +162,12 @@ extern "C" dgs_status dgs_cell_align(dgs_ctx *ctx, uint32_t scene_id, int32_t wh
         if (out_center) CK(cudaMemcpyAsync(out_center, oc, sizeof(float) * 3 * N, cudaMemcpyDeviceToHost, st));
         if (out_quat) CK(cudaMemcpyAsync(out_quat, oq, sizeof(float) * 4 * N, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
+    }
+    if (decode) {  // the decode's tensor-core completion waits (synchronises the stream)
+        uint32_t e = 0;
+        CK(cudaStreamSynchronize(st));
+        CK(cudaMemcpy(&e, base + o_err, 4, cudaMemcpyDeviceToHost));
+        if (e) return set_error(DGS_ERR_TIMEOUT, "the decode's tensor-core completion wait gave up");
     }
     return DGS_OK;
 }

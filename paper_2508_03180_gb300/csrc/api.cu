@@ -720,7 +720,7 @@ std::unique_ptr<Workspace> acquire_ws(dgs_ctx *ctx, cudaStream_t st, dgs_status 
 }
 
 dgs_status observe_chain(dgs_ctx *ctx, Workspace &ws, bool wait) {
-    if (!ws.async_pending) return DGS_OK;
+    if (!ws.async_pending && !ws.check_tc) return DGS_OK;
     if (wait) {
         CK(cudaEventSynchronize(ws.done));
     } else {
@@ -728,8 +728,14 @@ dgs_status observe_chain(dgs_ctx *ctx, Workspace &ws, bool wait) {
         if (q == cudaErrorNotReady) return DGS_OK;
         if (q != cudaSuccess) return cuda_error(q, "a render's launch chain");
     }
-    ws.async_pending = false;
     const uint32_t *h = ws.h_small;
+    if (ws.check_tc && h[kSmallTcErr]) {
+        ctx->pending_status = DGS_ERR_TIMEOUT;
+        ctx->pending_msg = "an earlier call's tensor-core completion wait gave up: its results are not valid";
+    }
+    ws.check_tc = false;
+    if (!ws.async_pending) return DGS_OK;
+    ws.async_pending = false;
     const long long L = h[kSmallTotal];
     ws.L = std::min(L, ws.L_cap);
     ws.n_vis = h[kSmallVisible];
@@ -935,7 +941,8 @@ dgs_status chain_forward(dgs_ctx *ctx, Workspace &ws, const std::vector<ChainVie
             StageTimer t(ctx->prof, DGS_STAGE_DECODE, st);
             launch_decode(dv, V, k, sd, (const uint32_t *)ws.zval.p, ws.n_vis, (float *)ws.dec.p,
                           (float *)ws.wpack.p, (const float *)ws.vview.p, bp, (float4 *)ws.rec.p,
-                          grad_buffers ? (float *)ws.g2d.p : nullptr, st);
+                          grad_buffers ? (float *)ws.g2d.p : nullptr, (uint32_t *)ws.small.p + kSmallTcErr, st);
+            ws.check_tc = true;
         } else {
             StageTimer t(ctx->prof, DGS_STAGE_PROJECT_FWD, st);
             launch_project_fwd(dv, V, k, sd, (const uint32_t *)ws.count.p, (const float *)ws.vview.p, bp,
@@ -953,7 +960,7 @@ dgs_status chain_forward(dgs_ctx *ctx, Workspace &ws, const std::vector<ChainVie
                          (const float4 *)ws.rec.p, bp, img, img2, (float *)ws.Dpix.p, (int *)ws.ndpix.p, K_all, st);
     }
     CK(cudaGetLastError());
-    if (device_sized)  // the chain's sizes and flags, read once it has completed (observe_chain)
+    if (device_sized || ws.check_tc)  // the chain's sizes and flags, read once it has completed (observe_chain)
         CK(cudaMemcpyAsync(ws.h_small, ws.small.p, 64, cudaMemcpyDeviceToHost, st));
     ws.stream = st;
     return DGS_OK;

@@ -25,6 +25,7 @@
 #include <algorithm>
 
 #include "project.cuh"
+#include "tc.cuh"
 
 namespace dgs {
 
@@ -413,6 +414,77 @@ __device__ __forceinline__ void ball_offset(const SceneDev &sc, long long g, flo
     for (int c = 0; c < 3; ++c) Ob[c] = on > 1.0f ? O[c] / on : O[c];
 }
 
+// The global inputs of Gaussian k's epilogue: its centre and Eq. 11 bound,
+// and the cell's v_n in the sample's view (zero for an invalid sample, or
+// without vview).
+__device__ __forceinline__ void decode_inputs(const ViewDesc *__restrict__ views, const float *p, int k, int K,
+                                              const float4 *__restrict__ gc, const float *__restrict__ vview,
+                                              float4 &c4, float &vn) {
+    if (__float_as_int(p[1]) == 0) {
+        c4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        vn = 0.f;
+        return;
+    }
+    const int n = __float_as_int(p[0]);
+    c4 = __ldg(gc + (long long)n * K + k);
+    vn = vview ? __ldg(vview + views[__float_as_int(p[23])].cell_base + n) : 0.f;  // (no records: no v_n)
+}
+
+// The forward's epilogue for Gaussian k of one sample (p: its information
+// row): the activations, the centre and the Eq. 11 bound, the decoded values
+// (kept for the adjoint) and the Gaussian's record for the blend (the
+// projection fused into the decode).  out(D, r) is output r of decoder D for
+// this sample, before its activation; c4 the Gaussian's centre and Eq. 11
+// bound, vn the cell's v_n in this view (decode_inputs).
+template <typename Out>
+__device__ __forceinline__ void decode_gaussian(const ViewDesc *__restrict__ views, const float *p, int k,
+                                                float4 c4, float vn, float *__restrict__ dec, const BlendParams &bp,
+                                                float4 *__restrict__ rec, float *__restrict__ g2d_zero, Out out) {
+    if (__float_as_int(p[1]) == 0) return;
+    const long long rid = (long long)(unsigned)__float_as_int(p[2]) | ((long long)__float_as_int(p[3]) << 32);
+    float o[kDecF];
+    o[0] = c4.x; o[1] = c4.y; o[2] = c4.z;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) o[3 + c] = fminf(sigmoid_fast(out(2, 3 * k + c)), c4.w) * p[7 + c];
+    float qv[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) qv[c] = out(3, 4 * k + c);
+    const float qn2 = qv[0] * qv[0] + qv[1] * qv[1] + qv[2] * qv[2] + qv[3] * qv[3];
+    if (qn2 > 0.f) {
+        const float iq = rsqrtf(qn2);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) o[6 + c] = qv[c] * iq;
+    } else {  // no direction to normalise: the identity rotation
+        o[6] = 1.f; o[7] = 0.f; o[8] = 0.f; o[9] = 0.f;
+    }
+    o[10] = tanh_fast(out(0, k));
+#pragma unroll
+    for (int c = 0; c < 3; ++c) o[11 + c] = sigmoid_fast(out(1, 3 * k + c));
+    float2 *dst = reinterpret_cast<float2 *>(dec + (rid + k) * kDecF);
+#pragma unroll
+    for (int i = 0; i < kDecF / 2; ++i) dst[i] = make_float2(o[2 * i], o[2 * i + 1]);
+    if (rec) {  // the Gaussian's record for the blend (the projection fused into the decode)
+        const ViewDesc &Vw = views[__float_as_int(p[23])];
+        GaussIn gi;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) { gi.mean[i] = o[i]; gi.scale[i] = o[3 + i]; }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) gi.quat[i] = o[6 + i];
+        gi.logit = 0.f;
+        const float knone[16][3] = {};
+        ProjCore c;
+        float4 r0, r1, r2;
+        gauss_record<true>(Vw, gi, knone, 0, o[10], vn, bp, c, r0, r1, r2, o + 11);
+        if (!(o[10] > 0.f)) r0 = make_float4(0.f, 0.f, -1.f, -1.f);  // sigma <= 0: not drawn
+        float4 *rp = rec + (rid + k) * kRecF4;
+        rp[0] = r0; rp[1] = r1; rp[2] = r2;
+        if (g2d_zero) {
+            float4 *z = reinterpret_cast<float4 *>(g2d_zero + (rid + k) * kGradF);
+            z[0] = z[1] = z[2] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+}
+
 template <int HW>
 __global__ void __launch_bounds__(256) k_decode(const ViewDesc *__restrict__ views, SceneDev sc, MlpShape S,
                                                 const float *__restrict__ pk, const float *__restrict__ srec,
@@ -444,56 +516,291 @@ __global__ void __launch_bounds__(256) k_decode(const ViewDesc *__restrict__ vie
         for (int idx = threadIdx.x; idx < S.M * K; idx += blockDim.x) {
             const int s = idx / K, k = idx - s * K;
             const float *p = info + s * DINFO;
-            if (__float_as_int(p[1]) == 0) continue;
-            const long long g = (long long)__float_as_int(p[0]) * K + k;
-            const long long rid = (long long)(unsigned)__float_as_int(p[2]) | ((long long)__float_as_int(p[3]) << 32);
-            const float4 c4 = __ldg(gc + g);  // centre and the Eq. 11 bound
-            float o[kDecF];
-            o[0] = c4.x; o[1] = c4.y; o[2] = c4.z;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) o[3 + c] = fminf(sigmoid_fast(Ot[orow(S, 2, 3 * k + c) + s]), c4.w) * p[7 + c];
-            float qv[4];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) qv[c] = Ot[orow(S, 3, 4 * k + c) + s];
-            const float qn2 = qv[0] * qv[0] + qv[1] * qv[1] + qv[2] * qv[2] + qv[3] * qv[3];
-            if (qn2 > 0.f) {
-                const float iq = rsqrtf(qn2);
-#pragma unroll
-                for (int c = 0; c < 4; ++c) o[6 + c] = qv[c] * iq;
-            } else {  // no direction to normalise: the identity rotation
-                o[6] = 1.f; o[7] = 0.f; o[8] = 0.f; o[9] = 0.f;
-            }
-            o[10] = tanh_fast(Ot[orow(S, 0, k) + s]);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) o[11 + c] = sigmoid_fast(Ot[orow(S, 1, 3 * k + c) + s]);
-            float2 *dst = reinterpret_cast<float2 *>(dec + (rid + k) * kDecF);
-#pragma unroll
-            for (int i = 0; i < kDecF / 2; ++i) dst[i] = make_float2(o[2 * i], o[2 * i + 1]);
-            if (rec) {  // the Gaussian's record for the blend (the projection fused into the decode)
-                const ViewDesc &Vw = views[__float_as_int(p[23])];
-                GaussIn gi;
-#pragma unroll
-                for (int i = 0; i < 3; ++i) { gi.mean[i] = o[i]; gi.scale[i] = o[3 + i]; }
-#pragma unroll
-                for (int i = 0; i < 4; ++i) gi.quat[i] = o[6 + i];
-                gi.logit = 0.f;
-                const float knone[16][3] = {};
-                ProjCore c;
-                float4 r0, r1, r2;
-                gauss_record<true>(Vw, gi, knone, 0, o[10], vview[Vw.cell_base + __float_as_int(p[0])], bp, c, r0,
-                                   r1, r2, o + 11);
-                if (!(o[10] > 0.f)) r0 = make_float4(0.f, 0.f, -1.f, -1.f);  // sigma <= 0: not drawn
-                float4 *rp = rec + (rid + k) * kRecF4;
-                rp[0] = r0; rp[1] = r1; rp[2] = r2;
-                if (g2d_zero) {
-                    float4 *z = reinterpret_cast<float4 *>(g2d_zero + (rid + k) * kGradF);
-                    z[0] = z[1] = z[2] = make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-            }
+            float4 c4;
+            float vn;
+            decode_inputs(views, p, k, K, gc, vview, c4, vn);
+            decode_gaussian(views, p, k, c4, vn, dec, bp, rec, g2d_zero,
+                            [&](int D, int r) { return Ot[orow(S, D, r) + s]; });
         }
         __syncthreads();
     }
     cp_async_wait<0>();
+}
+
+// ---------------------------------------------------------------- tensor cores
+// The same two layers on the fifth-generation tensor cores (tcgen05, TF32
+// products with FP32 accumulation in tensor memory) for the common widths:
+// I = F + 4 <= 40 inputs, H <= 32 hidden units per decoder and output blocks
+// that fit 128 columns when each is rounded up to 16 (K <= 10).  A tile is
+// M = 128 samples, one row of the product per sample:
+//   layer 1  D1[128 x 128] = Z[128 x IP] W1^T            (TMEM columns 0 .. 127)
+//   layer 2  D2[128 x N_D] = H[:, 32D .. 32D+32] W2_D^T  (columns 128 + rb_D, per decoder)
+// with IP = I rounded up to 8 (one product consumes K = 8) and every decoder's
+// hidden units padded to 32.  Each factor is split as x = hi + lo with hi
+// exact in TF32, and a product is the sum lo*hi + hi*lo + hi*hi accumulated
+// in FP32 (the dropped lo*lo term is below 2^-21 relative), which keeps the
+// decoded values at the CUDA-core kernels' FP32 accuracy.  One thread issues
+// the products; they complete through an mbarrier (bounded wait).  Biases and
+// the ReLU are applied as the accumulators leave tensor memory: layer 1's
+// into the hi/lo operand tiles of layer 2, layer 2's into an output tile in
+// shared memory, from which the epilogue (decode_gaussian) runs as in
+// k_decode, one (sample, Gaussian) per thread.
+constexpr int TC_M = 128;
+constexpr int TC_THREADS = 512;
+constexpr int TC_CW = 128 / (TC_THREADS / 128);  // accumulator columns a warp moves out of tensor memory
+constexpr int TC_ITEMS = 3;     // (sample, Gaussian) items a thread decodes per tile: 128 K <= 3 x 512
+constexpr int TC_LDO = TC_M + 1;  // output tile row stride (floats): (column, sample) reads spread over banks
+
+struct TcShape {
+    int F, H, K, I, IP;
+    int nout[4], rb[5];                  // output widths; column bases, blocks rounded up to 16 (rb[4] <= 128)
+    int w1o[4], b1o[4], w2o[4], b2o[4];  // offsets in the packed weights
+    // the weight image (floats; its order is the shared-memory layout's):
+    // W1 hi | W1 lo [128 x IP], W2 hi | W2 lo [128 x 32], b1 [128], b2 [128]
+    int g_w1h, g_w1l, g_w2h, g_w2l, g_b1, g_b2, g_total;
+    // dynamic shared memory (bytes): the image, then the operand/output union, then the sample records
+    int s_u, s_info, s_total;
+};
+
+static TcShape tc_shape(int F, int H, int K) {
+    TcShape T{};
+    T.F = F; T.H = H; T.K = K; T.I = F + 4; T.IP = up_to(T.I, 8);
+    const int outs[4] = {K, 3 * K, 3 * K, 4 * K};
+    int o = 0;
+    T.rb[0] = 0;
+    for (int D = 0; D < 4; ++D) {
+        T.nout[D] = outs[D];
+        T.rb[D + 1] = T.rb[D] + up_to(outs[D], 16);
+        T.w1o[D] = o; T.b1o[D] = o + H * T.I; T.w2o[D] = T.b1o[D] + H; T.b2o[D] = T.w2o[D] + outs[D] * H;
+        o = T.b2o[D] + outs[D];
+    }
+    T.g_w1h = 0;
+    T.g_w1l = T.g_w1h + TC_M * T.IP;
+    T.g_w2h = T.g_w1l + TC_M * T.IP;
+    T.g_w2l = T.g_w2h + TC_M * 32;
+    T.g_b1 = T.g_w2l + TC_M * 32;
+    T.g_b2 = T.g_b1 + TC_M;
+    T.g_total = T.g_b2 + TC_M;
+    T.s_u = 4 * T.g_total;
+    // the union holds Z hi|lo, then H hi|lo, then the output tile
+    const int u = std::max(std::max(2 * 4 * TC_M * T.IP, 2 * 4 * TC_M * TC_M), 4 * TC_M * TC_LDO);
+    T.s_info = T.s_u + u;
+    T.s_total = T.s_info + 4 * TC_M * DINFO;
+    return T;
+}
+
+static bool tc_fits(int F, int H, int K) {
+    if (F + 4 > 40 || H > 32 || H < 1 || F < 1 || K < 1 || TC_M * K > TC_ITEMS * TC_THREADS) return false;
+    const TcShape T = tc_shape(F, H, K);
+    return T.rb[4] <= TC_M && T.s_total <= kSmemMax;
+}
+
+// The weight image: element e of a region holds the operand entry at its
+// core-matrix position (the inverse of tc::cm_off), hi or lo part.
+__global__ void k_mlp_pack_tc(const float *__restrict__ w, TcShape T, float *__restrict__ img) {
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < T.g_total; idx += gridDim.x * blockDim.x) {
+        float v = 0.f;
+        bool lo = false;
+        if (idx < T.g_w2h) {  // W1 [hidden jj][input k], KK = IP
+            lo = idx >= T.g_w1l;
+            const int o = 4 * (idx - (lo ? T.g_w1l : T.g_w1h)), sbo = T.IP * 32;
+            const int rem = o % sbo, jj = 8 * (o / sbo) + (rem % 128) / 16, k = 4 * (rem / 128) + (rem % 16) / 4;
+            const int D = jj / 32, j = jj % 32;
+            if (j < T.H && k < T.I) v = w[T.w1o[D] + j * T.I + k];
+        } else if (idx < T.g_b1) {  // W2 [padded output column cc][hidden j], KK = 32
+            lo = idx >= T.g_w2l;
+            const int o = 4 * (idx - (lo ? T.g_w2l : T.g_w2h));
+            const int rem = o % 1024, cc = 8 * (o / 1024) + (rem % 128) / 16, j = 4 * (rem / 128) + (rem % 16) / 4;
+            int D = 0;
+            while (D < 3 && cc >= T.rb[D + 1]) ++D;
+            const int r = cc - T.rb[D];
+            if (cc < T.rb[4] && r < T.nout[D] && j < T.H) v = w[T.w2o[D] + r * T.H + j];
+        } else if (idx < T.g_b2) {
+            const int jj = idx - T.g_b1, D = jj / 32, j = jj % 32;
+            if (j < T.H) v = w[T.b1o[D] + j];
+        } else {
+            const int cc = idx - T.g_b2;
+            int D = 0;
+            while (D < 3 && cc >= T.rb[D + 1]) ++D;
+            const int r = cc - T.rb[D];
+            if (cc < T.rb[4] && r < T.nout[D]) v = w[T.b2o[D] + r];
+        }
+        if (idx < T.g_b1) {
+            float hi, l;
+            tc::split_tf32(v, hi, l);
+            v = lo ? l : hi;
+        }
+        img[idx] = v;
+    }
+}
+
+// Stage samples [q0, q0 + 128): records (invalid past the end) and Z as the
+// hi and lo operand tiles (zero for invalid samples and padded inputs).
+__device__ __forceinline__ void tc_stage(const TcShape &T, unsigned char *sm, const SceneDev &sc,
+                                         const float *__restrict__ srec, long long nsamp, long long q0) {
+    float *info = reinterpret_cast<float *>(sm + T.s_info);
+    const int nv = (int)min((long long)TC_M, nsamp - q0);
+    {
+        const float4 *s4 = reinterpret_cast<const float4 *>(srec + q0 * DINFO);
+        float4 *d4 = reinterpret_cast<float4 *>(info);
+        for (int i = threadIdx.x; i < TC_M * (DINFO / 4); i += blockDim.x)
+            d4[i] = i < nv * (DINFO / 4) ? __ldg(s4 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+    unsigned char *zh = sm + T.s_u, *zl = zh + 4 * TC_M * T.IP;
+    // one 16-byte chunk (4 inputs) of one sample per item; consecutive threads
+    // take consecutive samples (a warp's stores fill whole 128-byte lines)
+    for (int it = threadIdx.x; it < TC_M * (T.IP / 4); it += blockDim.x) {
+        const int s = it % TC_M, c = it / TC_M;
+        const float *p = info + s * DINFO;
+        const bool valid = __float_as_int(p[1]) != 0;
+        const float *row = sc.feat + (long long)__float_as_int(p[0]) * T.F;
+        float z[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = 4 * c + u;
+            z[u] = !valid || i >= T.I ? 0.f : (i < T.F ? __ldg(row + i) : p[19 + i - T.F]);
+        }
+        float4 h, l;
+        tc::split_tf32(z[0], h.x, l.x);
+        tc::split_tf32(z[1], h.y, l.y);
+        tc::split_tf32(z[2], h.z, l.z);
+        tc::split_tf32(z[3], h.w, l.w);
+        const uint32_t off = tc::cm_off(s, 4 * c, T.IP);
+        *reinterpret_cast<float4 *>(zh + off) = h;
+        *reinterpret_cast<float4 *>(zl + off) = l;
+    }
+}
+
+// Products of one layer: D (+)= A B^T as lo*hi + hi*lo + hi*hi over ksteps
+// steps of 8.  a/b: byte addresses of the hi tiles; the lo tiles follow at
+// a_lo / b_lo bytes; sbo_a, sbo_b: their 8-row group strides.
+__device__ __forceinline__ void tc_layer(uint32_t d, uint32_t a, uint32_t a_lo, uint32_t sbo_a, uint32_t b,
+                                         uint32_t b_lo, uint32_t sbo_b, int ksteps, uint32_t idesc) {
+    const uint32_t as[3] = {a + a_lo, a, a}, bs[3] = {b, b + b_lo, b};
+    bool acc = false;
+#pragma unroll
+    for (int t = 0; t < 3; ++t)
+        for (int k = 0; k < ksteps; ++k) {
+            tc::mma_tf32(d, tc::desc(as[t] + 256 * k, sbo_a), tc::desc(bs[t] + 256 * k, sbo_b), idesc, acc);
+            acc = true;
+        }
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1) k_decode_tc(const ViewDesc *__restrict__ views, SceneDev sc,
+                                                               TcShape T, const float *__restrict__ img,
+                                                               const float *__restrict__ srec,
+                                                               const float4 *__restrict__ gc, long long nsamp,
+                                                               float *__restrict__ dec, const float *__restrict__ vview,
+                                                               BlendParams bp, float4 *__restrict__ rec,
+                                                               float *__restrict__ g2d_zero, uint32_t *err) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tslot;
+    __shared__ int abort_flag;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int K = T.K;
+    // the weight image once per CTA (its layout is the shared-memory layout)
+    {
+        const float4 *s4 = reinterpret_cast<const float4 *>(img);
+        float4 *d4 = reinterpret_cast<float4 *>(sm);
+        for (int i = t; i < T.g_total / 4; i += blockDim.x) d4[i] = __ldg(s4 + i);
+    }
+    if (t == 0) {
+        tc::mbar_init(&mbar, 1);
+        abort_flag = 0;
+    }
+    if (warp == 0) tc::tmem_alloc<256>(&tslot);
+    tc::sync_threads();
+    const uint32_t tm = tslot;
+    const uint32_t base = tc::smem_u32(sm);
+    const uint32_t w1 = base + 4 * T.g_w1h, w1_lo = 4 * (T.g_w1l - T.g_w1h);
+    const uint32_t w2 = base + 4 * T.g_w2h, w2_lo = 4 * (T.g_w2l - T.g_w2h);
+    const uint32_t u = base + T.s_u;
+    const float *b1 = reinterpret_cast<const float *>(sm) + T.g_b1;
+    const float *b2 = reinterpret_cast<const float *>(sm) + T.g_b2;
+    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;  // this warp's TMEM lanes
+    const int s = 32 * (warp & 3) + lane;                         // its sample (TMEM lane)
+    const int cbase = TC_CW * (warp >> 2);                        // its TC_CW of the 128 columns
+    uint32_t phase = 0;
+    for (long long q0 = (long long)blockIdx.x * TC_M; q0 < nsamp; q0 += (long long)gridDim.x * TC_M) {
+        tc_stage(T, sm, sc, srec, nsamp, q0);
+        const float *info = reinterpret_cast<const float *>(sm + T.s_info);
+        tc::fence_async_smem();
+        tc::sync_threads();
+        if (t == 0) {
+            tc_layer(tm, u, 4 * TC_M * T.IP, T.IP * 32, w1, w1_lo, T.IP * 32, T.IP / 8, tc::idesc_tf32(TC_M, TC_M));
+            tc::commit(&mbar);
+        }
+        if (!tc::mbar_wait(&mbar, phase)) abort_flag = 1;
+        phase ^= 1;
+        tc::fence_after();
+        __syncthreads();
+        if (abort_flag) break;
+        // layer 1 leaves tensor memory: + b1, ReLU, split into the H operand tiles (over Z, now read)
+        {
+            unsigned char *hh = sm + T.s_u, *hl = hh + 4 * TC_M * TC_M;
+#pragma unroll 1
+            for (int c0 = cbase; c0 < cbase + TC_CW; c0 += 16) {
+                float v[16];
+                tc::ld16(tm + lane_base + (uint32_t)c0, v);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float4 h, l;
+                    float x[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) x[j] = fmaxf(v[4 * q + j] + b1[c0 + 4 * q + j], 0.f);
+                    tc::split_tf32(x[0], h.x, l.x);
+                    tc::split_tf32(x[1], h.y, l.y);
+                    tc::split_tf32(x[2], h.z, l.z);
+                    tc::split_tf32(x[3], h.w, l.w);
+                    const uint32_t off = tc::cm_off(s, c0 + 4 * q, TC_M);
+                    *reinterpret_cast<float4 *>(hh + off) = h;
+                    *reinterpret_cast<float4 *>(hl + off) = l;
+                }
+            }
+        }
+        tc::fence_async_smem();
+        tc::sync_threads();
+        if (t == 0) {
+            for (int D = 0; D < 4; ++D) {
+                const int n = T.rb[D + 1] - T.rb[D];
+                tc_layer(tm + 128 + (uint32_t)T.rb[D], u + 32 * D * 32, 4 * TC_M * TC_M, TC_M * 32,
+                         w2 + (uint32_t)(T.rb[D] / 8) * 1024, w2_lo, 1024, 4, tc::idesc_tf32(TC_M, n));
+            }
+            tc::commit(&mbar);
+        }
+        if (!tc::mbar_wait(&mbar, phase)) abort_flag = 1;
+        phase ^= 1;
+        tc::fence_after();
+        __syncthreads();
+        if (abort_flag) break;
+        // layer 2 leaves tensor memory: + b2 into the output tile (over H, now read)
+        float *Ot = reinterpret_cast<float *>(sm + T.s_u);
+        for (int c0 = cbase; c0 < cbase + TC_CW; c0 += 16) {
+            if (c0 >= T.rb[4]) break;
+            float v[16];
+            tc::ld16(tm + lane_base + 128u + (uint32_t)c0, v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) Ot[(c0 + j) * TC_LDO + s] = v[j] + b2[c0 + j];
+        }
+        tc::sync_threads();
+#pragma unroll
+        for (int j = 0; j < TC_ITEMS; ++j) {
+            const int idx = t + j * TC_THREADS;
+            if (idx >= TC_M * K) break;
+            const int si = idx / K, k = idx - si * K;
+            float4 c4;
+            float vn;
+            decode_inputs(views, info + si * DINFO, k, K, gc, vview, c4, vn);
+            decode_gaussian(views, info + si * DINFO, k, c4, vn, dec, bp, rec, g2d_zero,
+                            [&](int D, int r) { return Ot[(T.rb[D] + r) * TC_LDO + si]; });
+        }
+        tc::sync_threads();  // the tiles are read before the next stage overwrites them
+    }
+    if (abort_flag && t == 0) atomicOr(err, 1u);
+    tc::sync_threads();
+    if (warp == 0) tc::tmem_free<256>(tm);
 }
 
 // ---------------------------------------------------------------- adjoint
@@ -1009,7 +1316,8 @@ long long decode_scratch_floats(int F, int H, int K, long long nsamp, long long 
     const MlpShape S = mlp_shape(F, H, K, bwd);
     const long long n = std::max(1LL, nsamp);
     const long long tiles = (n + S.M - 1) / S.M;
-    return up_to(S.g_total, 4) + n * DINFO +
+    const int img = tc_fits(F, H, K) ? std::max(S.g_total, tc_shape(F, H, K).g_total) : S.g_total;
+    return up_to(img, 4) + n * DINFO +
            (bwd ? (wgrad_fused(S) ? 0LL : (long long)S.row_all * S.M * tiles) : 4 * std::max(1LL, G));
 }
 
@@ -1022,8 +1330,23 @@ static void decode_prep(const ViewDesc *views, int n_views, int slot, const Scen
 
 void launch_decode(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const uint32_t *samples,
                    long long nsamp, float *dec, float *scratch, const float *vview, const BlendParams &bp,
-                   float4 *rec, float *g2d_zero, cudaStream_t st) {
+                   float4 *rec, float *g2d_zero, uint32_t *err, cudaStream_t st) {
     if (nsamp <= 0 || !sc.feat) return;
+    if (tc_fits(sc.F, sc.H, sc.K)) {
+        const TcShape T = tc_shape(sc.F, sc.H, sc.K);
+        float *img = scratch, *srec = scratch + up_to(T.g_total, 4);
+        float4 *gc = reinterpret_cast<float4 *>(srec + nsamp * DINFO);
+        k_mlp_pack_tc<<<(T.g_total + 255) / 256, 256, 0, st>>>(sc.mlp, T, img);
+        const long long b = std::min((nsamp + 127) / 128, 152LL * 16);
+        k_decode_samples<<<(unsigned)std::max(1LL, b), 128, 0, st>>>(views, n_views, slot, sc, samples, nsamp, srec);
+        const long long bg = std::min((sc.G + 127) / 128, 152LL * 16);
+        k_decode_centres<<<(unsigned)std::max(1LL, bg), 128, 0, st>>>(sc, gc);
+        const long long tiles = (nsamp + TC_M - 1) / TC_M;
+        const int grid = persistent_grid(k_decode_tc, TC_THREADS, (size_t)T.s_total, tiles);
+        k_decode_tc<<<grid, TC_THREADS, (size_t)T.s_total, st>>>(views, sc, T, img, srec, gc, nsamp, dec, vview, bp,
+                                                               rec, g2d_zero, err);
+        return;
+    }
     const MlpShape S = mlp_shape(sc.F, sc.H, sc.K, false);
     float *pk = scratch, *srec = scratch + up_to(S.g_total, 4);
     float4 *gc = reinterpret_cast<float4 *>(srec + nsamp * DINFO);

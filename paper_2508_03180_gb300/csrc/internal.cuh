@@ -179,10 +179,12 @@ void launch_gauss_bin(const ViewDesc *views, int n_views, const SceneDev &sc, co
 // for sample q) of scene `slot` into dec [rec_base + g][kDecF] and, with rec
 // non-NULL, write their records (colour and opacity as decoded, sigma <= 0
 // not drawn; v_n from vview) and zero their g2d rows (g2d_zero non-NULL).
-// Features are rows [N][F].
+// Features are rows [N][F].  At the common widths the products run on the
+// tensor cores; *err (a device word) is set to 1 if one of their completion
+// waits gives up (the results are then not valid).
 void launch_decode(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const uint32_t *samples,
                    long long nsamp, float *dec, float *scratch, const float *vview, const BlendParams &bp,
-                   float4 *rec, float *g2d_zero, cudaStream_t st);
+                   float4 *rec, float *g2d_zero, uint32_t *err, cudaStream_t st);
 // Floats of scratch (16-byte aligned) that one launch_decode (bwd = false)
 // or launch_decode_bwd (bwd = true) call needs.
 long long decode_scratch_floats(int F, int H, int K, long long nsamp, long long G, bool bwd);

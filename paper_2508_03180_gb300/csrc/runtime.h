@@ -28,6 +28,7 @@ constexpr int kSmallVisible = 2;  // (view, cell) pairs that survived culling
 constexpr int kSmallPairs = 3;    // L clamped to the pair capacity (captured chains)
 constexpr int kSmallOverflow = 4; // L exceeded the pair capacity (captured chains)
 constexpr int kSmallWork = 5;     // work counter of the pulling blend (captured chains)
+constexpr int kSmallTcErr = 6;    // a tensor-core product's completion wait gave up (decode)
 
 dgs_status set_error(dgs_status code, const std::string &msg);
 dgs_status cuda_error(cudaError_t e, const char *what);
@@ -107,6 +108,7 @@ struct Workspace {
     // on the device only (pair buffers sized L_cap), and L, n_vis and the
     // chain's flags are read from h_small once it has completed (observe_chain).
     bool async_pending = false;
+    bool check_tc = false;  // the chain ran tensor-core kernels: observe their wait flag once it completes
     long long L_cap = 0;
     dgs_status init();
     std::vector<DevBuf *> all();

@@ -23,7 +23,9 @@ def rctx():
     c.close()
 
 
-@pytest.mark.parametrize("F,H,K", [(32, 32, 6), (16, 24, 10), (20, 36, 7), (64, 64, 32)])
+# (32, 32, 10), (32, 32, 6), (16, 24, 10): the tensor-core products (F + 4 <= 40, H <= 32, K <= 10);
+# (20, 36, 7), (64, 64, 32): the CUDA-core ones
+@pytest.mark.parametrize("F,H,K", [(32, 32, 10), (32, 32, 6), (16, 24, 10), (20, 36, 7), (64, 64, 32)])
 def test_decode_and_render(rctx, F, H, K):
     from paper_2508_03180_gb300 import _lib as L
     sc = synth.neural_scene(n_cells=900, K=K, F=F, H=H, seed=F + K)
