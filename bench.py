@@ -447,17 +447,17 @@ def neural_fwdbwd_bench(rctx, fp32_tflops, steps=5, F=32, H=32, K=10):
         P = sum(H * (F + 4) + H + o * H + o for o in (K, 3 * K, 3 * K, 4 * K))  # packed decoder weights
         grads = dict(g_mlp=torch.empty(P, device="cuda"), g_feat=torch.empty(scene.N, F, device="cuda"),
                      g_offset=torch.empty(scene.G, 3, device="cuda"))
-        stats = {}
 
-        def step():
-            _, state, st = rctx.render(sid, cams, want_state=True, out=img, slots=slots, stats=True)
-            stats["visible"] = int(st.visible_cells)
+        def step():  # asynchronous: the decode's sample count stays on the device
+            _, state, _ = rctx.render(sid, cams, want_state=True, out=img, slots=slots)
             rctx.loss_l1(img, target, dl, loss)
             rctx.backward(state, dl, grads)
             rctx.release_state(state)
 
         for _ in range(3):
             step()
+        _, st0, st = rctx.render(sid, cams, want_state=True, out=img, slots=slots, stats=True)  # the counts, untimed
+        rctx.release_state(st0)
         torch.cuda.synchronize()
         rctx.profile_enable(True)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -469,7 +469,7 @@ def neural_fwdbwd_bench(rctx, fp32_tflops, steps=5, F=32, H=32, K=10):
         prof = rctx.profile_read()
         rctx.profile_enable(False)
         ms = e0.elapsed_time(e1) / steps
-        vis = stats["visible"]
+        vis = int(st.visible_cells)
         fma_fwd = 4 * H * (F + 4) + 11 * K * H
         fma_bwd = 4 * H * (F + 4) + 2 * 11 * K * H + 4 * H * F + 4 * H * (F + 5) + 11 * K * (H + 1)
         out = {"workload": f"neural 100,000 cells x {K} Gaussians, F={F}, H={H}, multi-scale layout, "

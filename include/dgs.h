@@ -248,11 +248,12 @@ typedef struct {
  * completed (when its buffers are reused, or by dgs_render_backward on its
  * state if it has completed by then), the capacity grows to fit, and the next
  * dgs_render or dgs_render_backward on the context returns DGS_ERR_CAPACITY
- * (a radix sort that gave up: DGS_ERR_TIMEOUT) once; render it again.  The
- * call synchronises the stream once after binning, and sizes the pairs
- * exactly, when stats are requested, when the scene has neural cells (the
- * decode needs the visible-cell count on the host), and on the context's first
- * render (to learn its pairs per tile); host output synchronises at the end. */
+ * (a radix sort or a tensor-core wait of the decode that gave up:
+ * DGS_ERR_TIMEOUT) once; render it again.  Neural scenes are asynchronous
+ * too (the decode reads the visible-cell count on the device).  The call
+ * synchronises the stream once after binning, and sizes the pairs exactly,
+ * when stats are requested and on the context's first render (to learn its
+ * pairs per tile); host output synchronises at the end. */
 dgs_status dgs_render(dgs_ctx *ctx, uint32_t scene_id, int32_t n_views, const uint32_t *cam_slots,
                       float *out_rgb, int32_t out_location, dgs_fwd_state **state, dgs_stream stream,
                       dgs_stats *stats);

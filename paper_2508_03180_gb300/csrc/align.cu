@@ -147,7 +147,7 @@ extern "C" dgs_status dgs_cell_align(dgs_ctx *ctx, uint32_t scene_id, int32_t wh
         CK(cudaMemcpyAsync(base, &v, sizeof(v), cudaMemcpyHostToDevice, st));  // pageable: staged before return
         dec = (float *)(base + o_dec);
         CK(cudaMemsetAsync(base + o_err, 0, 4, st));
-        launch_decode((const ViewDesc *)base, 1, 0, sd, nullptr, N, dec, (float *)(base + o_pk), nullptr,
+        launch_decode((const ViewDesc *)base, 1, 0, sd, nullptr, N, nullptr, dec, (float *)(base + o_pk), nullptr,
                       BlendParams{}, nullptr, nullptr, (uint32_t *)(base + o_err), st);  // every cell of the one view; no records
     }
     float *oc = out_center, *oq = out_quat;

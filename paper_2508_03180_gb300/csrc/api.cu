@@ -924,9 +924,12 @@ dgs_status chain_forward(dgs_ctx *ctx, Workspace &ws, const std::vector<ChainVie
     const long long nrec = std::max(1LL, ws.n_records), px1 = std::max(1LL, px);
     bool any_neural = false;
     for (const Scene *sc : slots) any_neural = any_neural || sc->F > 0;
+    // the decode's samples: the visible (view, cell) entries, counted on the
+    // device (a device-sized chain knows only their capacity on the host)
+    const long long n_samp = device_sized ? ws.n_entries : ws.n_vis;
     long long npk = 0;
     for (const Scene *sc : slots)
-        if (sc->F > 0) npk = std::max(npk, decode_scratch_floats(sc->F, sc->H, sc->K, ws.n_vis, sc->G, false));
+        if (sc->F > 0) npk = std::max(npk, decode_scratch_floats(sc->F, sc->H, sc->K, n_samp, sc->G, false));
     if ((any_neural && (s = ws.dec.ensure(sizeof(float) * kDecF * nrec))) ||
         (any_neural && (s = ws.wpack.ensure(sizeof(float) * npk))) ||
         (s = ws.rec.ensure(sizeof(float4) * kRecF4 * nrec)) ||
@@ -939,8 +942,8 @@ dgs_status chain_forward(dgs_ctx *ctx, Workspace &ws, const std::vector<ChainVie
         if (slots[k]->F > 0) {  // neural cells: decode the visible cells' Gaussians for every view first
             // the decode writes the records too (the projection fused into it)
             StageTimer t(ctx->prof, DGS_STAGE_DECODE, st);
-            launch_decode(dv, V, k, sd, (const uint32_t *)ws.zval.p, ws.n_vis, (float *)ws.dec.p,
-                          (float *)ws.wpack.p, (const float *)ws.vview.p, bp, (float4 *)ws.rec.p,
+            launch_decode(dv, V, k, sd, (const uint32_t *)ws.zval.p, n_samp, (const uint32_t *)ws.small.p + kSmallVisible,
+                          (float *)ws.dec.p, (float *)ws.wpack.p, (const float *)ws.vview.p, bp, (float4 *)ws.rec.p,
                           grad_buffers ? (float *)ws.g2d.p : nullptr, (uint32_t *)ws.small.p + kSmallTcErr, st);
             ws.check_tc = true;
         } else {
@@ -986,10 +989,10 @@ static dgs_status render_impl(dgs_ctx *ctx, uint32_t scene_id, int n_views, cons
         ctx->pool.push_back(std::move(ws));
         return s;
     }
-    // No host synchronisation unless stats are asked for, a neural scene needs
-    // its visible-cell count on the host (the decode), or this context has not
-    // rendered yet (no pairs-per-tile estimate to size the pair buffers).
-    const bool device_sized = !stats && ctx->scenes[scene_id]->F == 0 && ctx->pairs_per_tile > 0.0;
+    // No host synchronisation unless stats are asked for or this context has
+    // not rendered yet (no pairs-per-tile estimate to size the pair buffers);
+    // a neural scene's decode reads its visible-cell count on the device.
+    const bool device_sized = !stats && ctx->pairs_per_tile > 0.0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     const bool timing = stats && stats->timing;
     if (timing) {
@@ -1136,8 +1139,10 @@ extern "C" dgs_status dgs_render_backward(dgs_ctx *ctx, dgs_fwd_state *state, co
     if (neural && (o_mlp || o_f || o_off || o_cc || o_ca || o_cq)) {
         if ((s = ws.gdec.ensure(sizeof(float) * kDecF * std::max(1LL, ws.n_records)))) return s;
         // the decode adjoint forms every output; unrequested ones go to scratch after its rows
+        // the samples as the forward counted them on the device (their count may not be on the host yet)
+        const long long n_samp = ws.n_vis >= 0 ? ws.n_vis : ws.n_entries;
         if ((s = ws.gscratch.ensure(sizeof(float) * std::max(1LL, P + NF + GO))) ||
-            (s = ws.wpack.ensure(sizeof(float) * decode_scratch_floats(sc.F, sc.H, sc.K, ws.n_vis, G, true))))
+            (s = ws.wpack.ensure(sizeof(float) * decode_scratch_floats(sc.F, sc.H, sc.K, n_samp, G, true))))
             return s;
         float *gscr = (float *)ws.gscratch.p;
         float *m = o_mlp ? o_mlp : gscr, *f = o_f ? o_f : gscr + P, *off = o_off ? o_off : gscr + P + NF;
@@ -1150,8 +1155,9 @@ extern "C" dgs_status dgs_render_backward(dgs_ctx *ctx, dgs_fwd_state *state, co
         CK(cudaMemsetAsync(m, 0, sizeof(float) * P, st));
         CK(cudaMemsetAsync(f, 0, sizeof(float) * NF, st));
         CK(cudaMemsetAsync(off, 0, sizeof(float) * GO, st));
-        launch_decode_bwd((const ViewDesc *)ws.views.p, ws.V, 0, sc.dev(), (const uint32_t *)ws.zval.p, ws.n_vis,
-                          (const float *)ws.gdec.p, m, f, off, CellGrads{o_cc, o_ca, o_cq}, (float *)ws.wpack.p, st);
+        launch_decode_bwd((const ViewDesc *)ws.views.p, ws.V, 0, sc.dev(), (const uint32_t *)ws.zval.p, n_samp,
+                          (const uint32_t *)ws.small.p + kSmallVisible, (const float *)ws.gdec.p, m, f, off,
+                          CellGrads{o_cc, o_ca, o_cq}, (float *)ws.wpack.p, st);
     } else if (!neural) {
         StageTimer t(ctx->prof, DGS_STAGE_PROJECT_BWD, st);
         launch_project_bwd((const ViewDesc *)ws.views.p, ws.V, 0, sc.dev(), (const uint32_t *)ws.count.p, bp,

@@ -178,7 +178,8 @@ __device__ __forceinline__ SampleInfo get_info(const float *s_info, int s) {
 // and the last four inputs; invalid for entries of another scene slot.
 __global__ void __launch_bounds__(128) k_decode_samples(const ViewDesc *__restrict__ views, int n_views, int slot,
                                                         SceneDev sc, const uint32_t *__restrict__ samples,
-                                                        long long nsamp, float *__restrict__ srec) {
+                                                        long long nsamp, const uint32_t *__restrict__ d_n, float *__restrict__ srec) {
+    if (d_n) nsamp = min(nsamp, (long long)*d_n);  // the count on the device (capacity nsamp)
     const long long N = sc.N;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nsamp;
          q += (long long)gridDim.x * blockDim.x) {
@@ -488,10 +489,11 @@ __device__ __forceinline__ void decode_gaussian(const ViewDesc *__restrict__ vie
 template <int HW>
 __global__ void __launch_bounds__(256) k_decode(const ViewDesc *__restrict__ views, SceneDev sc, MlpShape S,
                                                 const float *__restrict__ pk, const float *__restrict__ srec,
-                                                const float4 *__restrict__ gc, long long nsamp,
+                                                const float4 *__restrict__ gc, long long nsamp, const uint32_t *__restrict__ d_n,
                                                 float *__restrict__ dec, const float *__restrict__ vview,
                                                 BlendParams bp, float4 *__restrict__ rec,
                                                 float *__restrict__ g2d_zero) {
+    if (d_n) nsamp = min(nsamp, (long long)*d_n);  // the count on the device (capacity nsamp)
     extern __shared__ float4 smem4[];
     float *sm = reinterpret_cast<float *>(smem4);
     float *Wb = sm + S.s_w;
@@ -690,10 +692,11 @@ __device__ __forceinline__ void tc_layer(uint32_t d, uint32_t a, uint32_t a_lo, 
 __global__ void __launch_bounds__(TC_THREADS, 1) k_decode_tc(const ViewDesc *__restrict__ views, SceneDev sc,
                                                                TcShape T, const float *__restrict__ img,
                                                                const float *__restrict__ srec,
-                                                               const float4 *__restrict__ gc, long long nsamp,
+                                                               const float4 *__restrict__ gc, long long nsamp, const uint32_t *__restrict__ d_n,
                                                                float *__restrict__ dec, const float *__restrict__ vview,
                                                                BlendParams bp, float4 *__restrict__ rec,
                                                                float *__restrict__ g2d_zero, uint32_t *err) {
+    if (d_n) nsamp = min(nsamp, (long long)*d_n);  // the count on the device (capacity nsamp)
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tslot;
@@ -827,11 +830,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_decode_tc(const ViewDesc *__r
 // terms are compiled out).
 template <int HW, bool FUSE, bool CELL>
 __global__ void __launch_bounds__(256) k_decode_bwd(SceneDev sc, MlpShape S, const float *__restrict__ pk,
-                                                    const float *__restrict__ srec, long long nsamp,
+                                                    const float *__restrict__ srec, long long nsamp, const uint32_t *__restrict__ d_n,
                                                     const float *__restrict__ gdec,
                                                         float *__restrict__ g_feat, float *__restrict__ g_offset,
                                                         float *__restrict__ rows, float *__restrict__ g_mlp,
                                                         CellGrads cg) {
+    if (d_n) nsamp = min(nsamp, (long long)*d_n);  // the count on the device (capacity nsamp)
     extern __shared__ float4 smem4[];
     float *sm = reinterpret_cast<float *>(smem4);
     const int K = S.K, F = S.F, Hp = S.Hp, H4 = 4 * S.Hp, Rp = S.rb[4];
@@ -1206,8 +1210,9 @@ struct WgProblem {
 };
 struct WgProblems { WgProblem p[5]; };
 
-__global__ void __launch_bounds__(WT_T) k_mlp_wgrad(const float *__restrict__ rows, MlpShape S, long long nsamp,
+__global__ void __launch_bounds__(WT_T) k_mlp_wgrad(const float *__restrict__ rows, MlpShape S, long long nsamp, const uint32_t *__restrict__ d_n,
                                                     int chunk, WgProblems probs, float *__restrict__ g_mlp) {
+    if (d_n) nsamp = min(nsamp, (long long)*d_n);  // the count on the device (capacity nsamp)
     __shared__ __align__(16) float sA[2][WT_S][WT_A + 4];
     __shared__ __align__(16) float sB[2][WT_S][WT_B + 4];
     const WgProblem P = probs.p[blockIdx.z];
@@ -1322,15 +1327,16 @@ long long decode_scratch_floats(int F, int H, int K, long long nsamp, long long 
 }
 
 static void decode_prep(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const MlpShape &S,
-                        const uint32_t *samples, long long nsamp, float *pk, float *srec, cudaStream_t st) {
+                        const uint32_t *samples, long long nsamp, const uint32_t *d_n, float *pk, float *srec,
+                        cudaStream_t st) {
     k_mlp_pack<<<(S.g_total + 255) / 256, 256, 0, st>>>(sc.mlp, S, pk);
     const long long b = std::min((nsamp + 127) / 128, 152LL * 16);
-    k_decode_samples<<<(unsigned)std::max(1LL, b), 128, 0, st>>>(views, n_views, slot, sc, samples, nsamp, srec);
+    k_decode_samples<<<(unsigned)std::max(1LL, b), 128, 0, st>>>(views, n_views, slot, sc, samples, nsamp, d_n, srec);
 }
 
 void launch_decode(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const uint32_t *samples,
-                   long long nsamp, float *dec, float *scratch, const float *vview, const BlendParams &bp,
-                   float4 *rec, float *g2d_zero, uint32_t *err, cudaStream_t st) {
+                   long long nsamp, const uint32_t *d_nsamp, float *dec, float *scratch, const float *vview,
+                   const BlendParams &bp, float4 *rec, float *g2d_zero, uint32_t *err, cudaStream_t st) {
     if (nsamp <= 0 || !sc.feat) return;
     if (tc_fits(sc.F, sc.H, sc.K)) {
         const TcShape T = tc_shape(sc.F, sc.H, sc.K);
@@ -1338,47 +1344,50 @@ void launch_decode(const ViewDesc *views, int n_views, int slot, const SceneDev 
         float4 *gc = reinterpret_cast<float4 *>(srec + nsamp * DINFO);
         k_mlp_pack_tc<<<(T.g_total + 255) / 256, 256, 0, st>>>(sc.mlp, T, img);
         const long long b = std::min((nsamp + 127) / 128, 152LL * 16);
-        k_decode_samples<<<(unsigned)std::max(1LL, b), 128, 0, st>>>(views, n_views, slot, sc, samples, nsamp, srec);
+        k_decode_samples<<<(unsigned)std::max(1LL, b), 128, 0, st>>>(views, n_views, slot, sc, samples, nsamp, d_nsamp,
+                                                                     srec);
         const long long bg = std::min((sc.G + 127) / 128, 152LL * 16);
         k_decode_centres<<<(unsigned)std::max(1LL, bg), 128, 0, st>>>(sc, gc);
         const long long tiles = (nsamp + TC_M - 1) / TC_M;
         const int grid = persistent_grid(k_decode_tc, TC_THREADS, (size_t)T.s_total, tiles);
-        k_decode_tc<<<grid, TC_THREADS, (size_t)T.s_total, st>>>(views, sc, T, img, srec, gc, nsamp, dec, vview, bp,
-                                                               rec, g2d_zero, err);
+        k_decode_tc<<<grid, TC_THREADS, (size_t)T.s_total, st>>>(views, sc, T, img, srec, gc, nsamp, d_nsamp, dec,
+                                                               vview, bp, rec, g2d_zero, err);
         return;
     }
     const MlpShape S = mlp_shape(sc.F, sc.H, sc.K, false);
     float *pk = scratch, *srec = scratch + up_to(S.g_total, 4);
     float4 *gc = reinterpret_cast<float4 *>(srec + nsamp * DINFO);
-    decode_prep(views, n_views, slot, sc, S, samples, nsamp, pk, srec, st);
+    decode_prep(views, n_views, slot, sc, S, samples, nsamp, d_nsamp, pk, srec, st);
     const long long bg = std::min((sc.G + 127) / 128, 152LL * 16);
     k_decode_centres<<<(unsigned)std::max(1LL, bg), 128, 0, st>>>(sc, gc);
     const size_t smem = sizeof(float) * (size_t)S.s_total;
     const long long tiles = (nsamp + S.M - 1) / S.M;
     if (S.HW == 4) {
         const int b = persistent_grid(k_decode<4>, 32 * S.W, smem, tiles);
-        k_decode<4><<<b, 32 * S.W, smem, st>>>(views, sc, S, pk, srec, gc, nsamp, dec, vview, bp, rec, g2d_zero);
+        k_decode<4><<<b, 32 * S.W, smem, st>>>(views, sc, S, pk, srec, gc, nsamp, d_nsamp, dec, vview, bp, rec,
+                                               g2d_zero);
     } else {
         const int b = persistent_grid(k_decode<8>, 32 * S.W, smem, tiles);
-        k_decode<8><<<b, 32 * S.W, smem, st>>>(views, sc, S, pk, srec, gc, nsamp, dec, vview, bp, rec, g2d_zero);
+        k_decode<8><<<b, 32 * S.W, smem, st>>>(views, sc, S, pk, srec, gc, nsamp, d_nsamp, dec, vview, bp, rec,
+                                               g2d_zero);
     }
 }
 
 void launch_decode_bwd(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const uint32_t *samples,
-                       long long nsamp, const float *gdec, float *g_mlp, float *g_feat, float *g_offset,
-                       CellGrads cg, float *scratch, cudaStream_t st) {
+                       long long nsamp, const uint32_t *d_nsamp, const float *gdec, float *g_mlp, float *g_feat,
+                       float *g_offset, CellGrads cg, float *scratch, cudaStream_t st) {
     if (nsamp <= 0 || !sc.feat) return;
     const MlpShape S = mlp_shape(sc.F, sc.H, sc.K, true);
     float *pk = scratch, *srec = scratch + up_to(S.g_total, 4), *rows = srec + nsamp * DINFO;
-    decode_prep(views, n_views, slot, sc, S, samples, nsamp, pk, srec, st);
+    decode_prep(views, n_views, slot, sc, S, samples, nsamp, d_nsamp, pk, srec, st);
     const size_t smem = sizeof(float) * (size_t)S.s_total;
     const long long tiles = (nsamp + S.M - 1) / S.M;
     const bool cell = cg.center || cg.axes || cg.quat;
 #define DGS_DBWD(HWV, FUSEV, CELLV, ROWS)                                                                      \
     do {                                                                                                      \
         const int b = persistent_grid(k_decode_bwd<HWV, FUSEV, CELLV>, 32 * S.W, smem, tiles);                \
-        k_decode_bwd<HWV, FUSEV, CELLV><<<b, 32 * S.W, smem, st>>>(sc, S, pk, srec, nsamp, gdec, g_feat,      \
-                                                                   g_offset, ROWS, g_mlp, cg);                \
+        k_decode_bwd<HWV, FUSEV, CELLV><<<b, 32 * S.W, smem, st>>>(sc, S, pk, srec, nsamp, d_nsamp, gdec,     \
+                                                                   g_feat, g_offset, ROWS, g_mlp, cg);        \
     } while (0)
     if (wgrad_fused(S)) {
         if (cell) DGS_DBWD(4, true, true, nullptr); else DGS_DBWD(4, true, false, nullptr);
@@ -1395,7 +1404,7 @@ void launch_decode_bwd(const ViewDesc *views, int n_views, int slot, const Scene
     for (int D = 0; D < 4; ++D) pr.p[1 + D] = WgProblem{S.row_do + S.rb[D], S.nout[D], S.row_h + D * S.Hp, S.H, D};
     const int chunk = 4096;
     const dim3 grid((unsigned)((nsamp + chunk - 1) / chunk), 16, 5);
-    k_mlp_wgrad<<<grid, WT_T, 0, st>>>(rows, S, nsamp, chunk, pr, g_mlp);
+    k_mlp_wgrad<<<grid, WT_T, 0, st>>>(rows, S, nsamp, d_nsamp, chunk, pr, g_mlp);
 }
 
 }  // namespace dgs

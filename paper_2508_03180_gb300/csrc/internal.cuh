@@ -179,12 +179,14 @@ void launch_gauss_bin(const ViewDesc *views, int n_views, const SceneDev &sc, co
 // for sample q) of scene `slot` into dec [rec_base + g][kDecF] and, with rec
 // non-NULL, write their records (colour and opacity as decoded, sigma <= 0
 // not drawn; v_n from vview) and zero their g2d rows (g2d_zero non-NULL).
-// Features are rows [N][F].  At the common widths the products run on the
-// tensor cores; *err (a device word) is set to 1 if one of their completion
-// waits gives up (the results are then not valid).
+// Features are rows [N][F].  d_nsamp (nullable): the sample count on the
+// device, at most nsamp (then the capacity the scratch is sized for).  At the
+// common widths the products run on the tensor cores; *err (a device word) is
+// set to 1 if one of their completion waits gives up (the results are then
+// not valid).
 void launch_decode(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const uint32_t *samples,
-                   long long nsamp, float *dec, float *scratch, const float *vview, const BlendParams &bp,
-                   float4 *rec, float *g2d_zero, uint32_t *err, cudaStream_t st);
+                   long long nsamp, const uint32_t *d_nsamp, float *dec, float *scratch, const float *vview,
+                   const BlendParams &bp, float4 *rec, float *g2d_zero, uint32_t *err, cudaStream_t st);
 // Floats of scratch (16-byte aligned) that one launch_decode (bwd = false)
 // or launch_decode_bwd (bwd = true) call needs.
 long long decode_scratch_floats(int F, int H, int K, long long nsamp, long long G, bool bwd);
@@ -204,8 +206,8 @@ void launch_cell_align(const SceneDev &sc, float *cell, const float *dec, int wh
 // cg: the cell gradients through the decode (centre: the decoder inputs and
 // the Gaussian centres; axes: the centres and scales; rotation: the centres).
 void launch_decode_bwd(const ViewDesc *views, int n_views, int slot, const SceneDev &sc, const uint32_t *samples,
-                       long long nsamp, const float *gdec, float *g_mlp, float *g_feat, float *g_offset,
-                       CellGrads cg, float *scratch, cudaStream_t st);
+                       long long nsamp, const uint32_t *d_nsamp, const float *gdec, float *g_mlp, float *g_feat,
+                       float *g_offset, CellGrads cg, float *scratch, cudaStream_t st);
 // One launch for every scene of the device scene table (dsz->n_scenes
 // entries, Gaussian counts <= G_cap, which sizes the grid).
 void launch_project_fwd_table(const ViewDesc *views, const SceneDev *scenes, long long G_cap, const uint32_t *count,

@@ -1,6 +1,7 @@
 """dgs_render without stats is asynchronous on its stream (no host
-synchronisation: the pair count stays on the device and the pair buffers are
-sized from the context's pairs-per-tile estimate), gives exactly the image,
+synchronisation: the pair count and, for neural cells, the decode's sample
+count stay on the device and the pair buffers are sized from the context's
+pairs-per-tile estimate), gives exactly the image,
 binning and gradients of the synchronising render (stats requested), and a
 render whose pairs exceed the capacity is reported by the next call, after
 which the capacity has grown and the render is exact again."""
@@ -53,6 +54,56 @@ def test_render_without_stats_returns_before_the_gpu_finishes():
             ref = gb[k].double()
             noise = (gb2[k].double() - ref).norm()
             assert (ga[k].double() - ref).norm() <= 4.0 * noise + 1e-6 * ref.norm(), k
+        ctx.release_state(state)
+        ctx.release_state(ref_state)
+    finally:
+        ctx.close()
+
+
+def test_neural_render_without_stats_is_asynchronous_and_exact():
+    """Neural cells: the decode reads the visible-cell count on the device,
+    so the render of a neural scene is asynchronous too, and its decoded
+    values, image, tile lists and gradients equal the synchronising path's."""
+    from oracle import decode as odec
+    F, H, K = 32, 32, 10
+    scene = synth.neural_scene(n_cells=20_000, K=K, F=F, H=H, seed=4, box=1.0)
+    cams = synth.sphere_cameras(8, 3.0, 1920, 1080, seed0=2)
+    ctx = Context()
+    try:
+        sid = ctx.upload_scene(scene)
+        ref, ref_state, st = ctx.render(sid, cams, want_state=True, stats=True)
+        torch.cuda.synchronize()
+        ctx.render(sid, cams)
+        torch.cuda.synchronize()
+        stream = torch.cuda.current_stream()
+        img, state, _ = ctx.render(sid, cams, want_state=True)
+        pending = not stream.query()
+        torch.cuda.synchronize()
+        assert pending, "the neural render returned only after its kernels had finished"
+        assert torch.equal(img, ref)
+        for what, dt in ((L.DGS_BUF_TILE_CELLS, np.uint32), (L.DGS_BUF_PIX_NDONE, np.int32)):
+            assert np.array_equal(ctx.read(state, what, dt), ctx.read(ref_state, what, dt))
+        V = len(cams)
+        vis = np.repeat(ctx.read(ref_state, L.DGS_BUF_CELL_RECT, np.int32, (V, scene.N, 4))[..., 0] >= 0, K, axis=1)
+        assert vis.sum() > 1000
+        dec = ctx.read(state, L.DGS_BUF_DECODED, np.float32, (V, scene.G, 14))
+        dec_ref = ctx.read(ref_state, L.DGS_BUF_DECODED, np.float32, (V, scene.G, 14))
+        assert np.array_equal(dec[vis], dec_ref[vis])  # decoded for the visible cells only
+        P = odec.packed_size(F, H, K)
+        dl = torch.randn(img.numel(), generator=torch.Generator().manual_seed(5)).cuda() * 1e-3
+
+        def grads(s):
+            g = dict(g_mlp=torch.zeros(P, device="cuda"), g_feat=torch.zeros(scene.N, F, device="cuda"),
+                     g_offset=torch.zeros(scene.G, 3, device="cuda"))
+            ctx.backward(s, dl, g)
+            return g
+        ga, gb, gb2 = grads(state), grads(ref_state), grads(ref_state)
+        torch.cuda.synchronize()
+        for k in ga:
+            ref_k = gb[k].double()
+            noise = (gb2[k].double() - ref_k).norm()
+            assert ref_k.abs().max() > 0, k
+            assert (ga[k].double() - ref_k).norm() <= 4.0 * noise + 1e-6 * ref_k.norm(), k
         ctx.release_state(state)
         ctx.release_state(ref_state)
     finally:
