@@ -155,10 +155,12 @@ const char *dgs_last_error(dgs_ctx *ctx);
  * scale, rotation; output widths K, 3K, 3K, 4K): W1 [hidden][feat_dim+4]
  * row-major, b1 [hidden], W2 [out][hidden] row-major, b2 [out].
  * 1 <= feat_dim <= 64, 1 <= hidden <= 64.  Neural scenes render through
- * dgs_render, and dgs_render_backward gives the gradients to the packed
- * decoder weights, the cell features and the offsets (g_mlp, g_feat,
- * g_offset); serving and the comparators take explicit scenes only
- * (INVALID_ARG for a neural one). */
+ * dgs_render and the serving loop, and dgs_render_backward gives the
+ * gradients to the packed decoder weights, the cell features and the
+ * offsets (g_mlp, g_feat, g_offset); the comparators take explicit scenes
+ * only (INVALID_ARG for a neural one).  At feat_dim + 4 <= 40, hidden <= 32
+ * and K <= 10 the decode's products run on the tensor cores (TF32 in three
+ * split products, FP32 accumulation: FP32-level values). */
 typedef struct {
     int32_t feat_dim;
     int32_t hidden;
@@ -531,7 +533,9 @@ typedef struct {
  * synchronisation separates binning from blending.  If the (tile, cell)
  * pairs of a batch exceed the buffers, the kernels stop at the capacity, the
  * worker sees the overflow flag when the batch finishes, grows the buffers,
- * captures again and re-runs the batch before reporting it.
+ * captures again and re-runs the batch before reporting it.  Scenes with
+ * neural cells are served like explicit ones (their decode is part of the
+ * chain; each composition of neural scenes in a batch has its own graph).
  * flags: DGS_SERVE_NO_GRAPHS runs every batch as a plain launch chain that
  * reads the sort length back to the host midway (for comparison). */
 #define DGS_SERVE_NO_GRAPHS 1

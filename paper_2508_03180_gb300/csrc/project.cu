@@ -136,6 +136,7 @@ __global__ void __launch_bounds__(128) k_project_fwd_table(const ViewDesc *__res
     const int n_views = dsz->n_views, n_scenes = dsz->n_scenes;
     for (int s = 0; s < n_scenes; ++s) {
         const SceneDev sc = scenes[s];
+        if (sc.feat) continue;  // neural cells: the decode writes their records
         project_scene(views, n_views, s, sc, count, vview, bp, rec, nullptr);
     }
 }

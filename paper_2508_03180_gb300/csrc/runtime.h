@@ -133,6 +133,7 @@ struct ChainCaps {
     int V = 0, S = 0;
     long long E = 0, R = 0, T = 0, P = 0, L = 0;
     long long G = 0;  // Gaussians of the largest scene (sizes the projection grid)
+    long long W = 0;  // decode scratch floats (neural scenes resident; 0: none)
 };
 
 // One stream's serving chain: a workspace sized for `caps` and one
@@ -145,7 +146,9 @@ struct GraphSlot {
     long long view_tiles = 0, view_px = 0;  // largest view seen
     long long L_need = 0;                   // pairs of the last overflowing batch, with headroom
     uint64_t scene_epoch = 0;
-    std::map<int, cudaGraphExec_t> graphs;
+    // per batch class: the K specialisation, then (slot, scene id) of each
+    // neural scene (its decode launches are part of the graph)
+    std::map<std::vector<uint32_t>, cudaGraphExec_t> graphs;
     void drop();
     ~GraphSlot() { drop(); }
 };

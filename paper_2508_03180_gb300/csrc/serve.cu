@@ -33,9 +33,11 @@ double now_ms() {
 int64_t request_bytes(const Scene &sc, const dgs_camera &c) {
     const int64_t px = (int64_t)c.W * c.H;
     const int64_t tiles = (int64_t)((c.W + 15) / 16) * ((c.H + 15) / 16);
-    // per pixel: image, D, count; per Gaussian: one record; per cell: binning
-    // arrays and sort scratch; per tile: a generous 64 (tile, cell) pairs
-    return px * 20 + sc.G * 48 + sc.N * 40 + tiles * 64 * 24 + (1 << 20);
+    // per pixel: image, D, count; per Gaussian: one record (and its decoded
+    // values for neural cells); per cell: binning arrays and sort scratch (and
+    // the decode's sample record); per tile: a generous 64 (tile, cell) pairs
+    const int64_t neural = sc.F > 0 ? sc.G * 4 * kDecF + sc.N * 96 : 0;
+    return px * 20 + sc.G * 48 + sc.N * 40 + tiles * 64 * 24 + neural + (1 << 20);
 }
 
 // Host function enqueued behind every chain: wakes the worker.
@@ -111,7 +113,8 @@ dgs_status plan_batch(dgs_ctx *ctx, const std::vector<PendingReq> &reqs, BatchPl
 long long slot_bytes(const ChainCaps &c) {
     const long long n = std::max(c.E, c.L);
     return (long long)sizeof(ViewDesc) * c.V + (long long)sizeof(SceneDev) * c.S + 36 * c.E + 4 * c.E / 1024 +
-           8 * n + 1024 * (n / 4096 + 1) + 8 * c.L + 8 * c.T + 48 * c.R + 20 * c.P;
+           8 * n + 1024 * (n / 4096 + 1) + 8 * c.L + 8 * c.T + 48 * c.R + 20 * c.P +
+           (c.W > 0 ? 4 * c.W + 4LL * kDecF * c.R : 0);
 }
 
 long long grown(long long have, long long need) {
@@ -132,6 +135,15 @@ dgs_status fit_slot(dgs_ctx *ctx, ServeState &S, GraphSlot &g, const BatchPlan &
         maxN = std::max<long long>(maxN, kv.second->N);
         maxG = std::max<long long>(maxG, kv.second->G);
     }
+    // the decode's scratch for the resident neural scenes, for E samples
+    auto decode_floats = [&](long long E) {
+        long long w = 0;
+        for (auto &kv : ctx->scenes) {
+            const Scene &sc = *kv.second;
+            if (sc.F > 0) w = std::max(w, decode_scratch_floats(sc.F, sc.H, sc.K, E, sc.G, false));
+        }
+        return w;
+    };
     for (const ViewDesc &v : p.views) {
         g.view_tiles = std::max(g.view_tiles, (long long)v.Tx * v.Ty);
         g.view_px = std::max(g.view_px, (long long)v.W * v.H);
@@ -145,6 +157,7 @@ dgs_status fit_slot(dgs_ctx *ctx, ServeState &S, GraphSlot &g, const BatchPlan &
         c.R = grown(c.R, std::max(p.need.R, B * maxG));
         c.T = grown(c.T, std::max(p.need.T, B * g.view_tiles));
         c.P = grown(c.P, std::max(p.need.P, B * g.view_px));
+        c.W = std::max(c.W, decode_floats(c.E));
         // pairs: sized from the estimate when the tile capacity changes,
         // otherwise grown only by an overflow (g.L_need)
         c.L = grown(c.L, g.L_need);
@@ -155,7 +168,7 @@ dgs_status fit_slot(dgs_ctx *ctx, ServeState &S, GraphSlot &g, const BatchPlan &
     ChainCaps c = target(S.max_batch);
     if (slot_bytes(c) > S.budget / kServeStreams) c = target(0);
     if (g.ws && c.V == g.caps.V && c.S == g.caps.S && c.E == g.caps.E && c.R == g.caps.R && c.T == g.caps.T &&
-        c.P == g.caps.P && c.L == g.caps.L && c.G == g.caps.G)
+        c.P == g.caps.P && c.L == g.caps.L && c.G == g.caps.G && c.W == g.caps.W)
         return DGS_OK;
     g.drop();
     dgs_status s;
@@ -175,7 +188,8 @@ dgs_status fit_slot(dgs_ctx *ctx, ServeState &S, GraphSlot &g, const BatchPlan &
         (s = ws.scan.ensure(4 * scan_scratch_words(c.E))) || (s = ensure_sort_scratch(ws, std::max(c.E, c.L))) ||
         (s = ws.tkey.ensure(4 * c.L)) || (s = ws.tval.ensure(4 * c.L)) || (s = ws.ranges.ensure(8 * c.T)) ||
         (s = ws.rec.ensure(sizeof(float4) * kRecF4 * c.R)) || (s = ws.Dpix.ensure(4 * c.P)) ||
-        (s = ws.ndpix.ensure(4 * c.P)) || (s = ws.rgb.ensure(12 * c.P)) || (s = ws.vview.ensure(4 * c.E)))
+        (s = ws.ndpix.ensure(4 * c.P)) || (s = ws.rgb.ensure(12 * c.P)) || (s = ws.vview.ensure(4 * c.E)) ||
+        (c.W > 0 && ((s = ws.dec.ensure(sizeof(float) * kDecF * c.R)) || (s = ws.wpack.ensure(sizeof(float) * c.W)))))
         return s;
     if (ws.h_views_cap < (size_t)c.V) {
         if (ws.h_views) cudaFreeHost(ws.h_views);
@@ -234,6 +248,15 @@ dgs_status record_chain(dgs_ctx *ctx, Workspace &ws, const ChainCaps &c, const B
     radix_sort_pairs((uint32_t *)ws.tkey.p, (uint32_t *)ws.tval.p, c.L, bits, sc, st, d_L);
     CKR(cudaMemsetAsync(ws.ranges.p, 0, 8 * (size_t)c.T, st));
     launch_tile_ranges((const uint32_t *)ws.tkey.p, c.L, (uint2 *)ws.ranges.p, st, d_L);
+    // neural scenes: the decode writes their records (slot k's samples of the
+    // visible entries, counted on the device); the table projection skips them
+    for (size_t k = 0; k < p.scenes.size(); ++k) {
+        const Scene &scn = *p.scenes[k];
+        if (scn.F == 0) continue;
+        launch_decode(dv, c.V, (int)k, scn.dev(), (const uint32_t *)ws.zval.p, c.E, small + kSmallVisible,
+                      (float *)ws.dec.p, (float *)ws.wpack.p, (const float *)ws.vview.p, bp, (float4 *)ws.rec.p,
+                      nullptr, small + kSmallTcErr, st);
+    }
     launch_project_fwd_table(dv, (const SceneDev *)ws.scenes.p, c.G, (const uint32_t *)ws.count.p,
                              (const float *)ws.vview.p, bp, (float4 *)ws.rec.p, st, dsz);
     launch_blend_fwd(dv, c.V, (int)c.T, (const uint2 *)ws.ranges.p, (const uint32_t *)ws.tval.p,
@@ -268,16 +291,29 @@ dgs_status launch_batch_graph(dgs_ctx *ctx, ServeState &S, InflightBatch &b, int
     dgs_status s;
     if ((s = plan_batch(ctx, b.reqs, p)) || (s = fit_slot(ctx, S, g, p, st))) return s;
     cudaGraphExec_t exec = nullptr;
-    auto it = g.graphs.find(p.K_all);
+    std::vector<uint32_t> key{(uint32_t)p.K_all};
+    for (size_t k = 0; k < p.scenes.size(); ++k)
+        if (p.scenes[k]->F > 0) {
+            key.push_back((uint32_t)k);
+            key.push_back(p.scene_set[k]);
+        }
+    auto it = g.graphs.find(key);
     if (it != g.graphs.end()) {
         exec = it->second;
     } else {
         if ((s = capture_chain(ctx, g, p, st, &exec))) return s;
-        g.graphs[p.K_all] = exec;
+        g.graphs[key] = exec;
         ++S.graphs_captured;
     }
     Workspace &ws = *g.ws;
     memcpy(ws.h_views, p.views.data(), sizeof(ViewDesc) * p.views.size());
+    // the capacity's unused view slots: past every entry, in no scene slot
+    // (the decode's search over the views' first entries never picks them)
+    for (size_t v = p.views.size(); v < (size_t)g.caps.V; ++v) {
+        ws.h_views[v] = p.views.back();
+        ws.h_views[v].cell_base = (long long)1 << 62;
+        ws.h_views[v].scene_slot = -1;
+    }
     for (size_t k = 0; k < p.scenes.size(); ++k) ws.h_scenes[k] = p.scenes[k]->dev();
     ws.h_sizes->n_entries = (uint32_t)p.need.E;
     ws.h_sizes->n_views = p.need.V;
@@ -342,8 +378,9 @@ dgs_status launch_batch(dgs_ctx *ctx, ServeState &S, InflightBatch &b, int si) {
 int check_graph_batch(ServeState &S, int si, dgs_status *err) {
     GraphSlot &g = S.gslot[si];
     const uint32_t *hs = g.ws->h_small;
-    if (hs[kSmallSortErr]) {
-        *err = set_error(DGS_ERR_TIMEOUT, "radix sort look-back wait gave up");
+    if (hs[kSmallSortErr] || hs[kSmallTcErr]) {
+        *err = set_error(DGS_ERR_TIMEOUT, hs[kSmallSortErr] ? "radix sort look-back wait gave up"
+                                                            : "a tensor-core completion wait of the decode gave up");
         return 0;
     }
     const double L = (double)hs[kSmallTotal];
@@ -571,7 +608,6 @@ extern "C" dgs_status dgs_submit(dgs_ctx *ctx, const dgs_request *req, uint64_t 
         std::lock_guard<std::mutex> lk(ctx->mu);
         auto it = ctx->scenes.find(req->scene_id);
         if (it == ctx->scenes.end()) return set_error(DGS_ERR_NOT_FOUND, "unknown scene id");
-        if (it->second->F > 0) return set_error(DGS_ERR_INVALID_ARG, "serving of neural-cell scenes is not built");
         bytes = request_bytes(*it->second, c);
     }
     ServeState &S = *ctx->serve;

@@ -66,6 +66,9 @@ def test_decode_and_render(rctx, F, H, K):
 
 
 def test_paths_not_built_refuse_neural_scenes(rctx):
+    """Explicit-Gaussian gradients of a neural scene and the comparators (which
+    project explicit Gaussians) are refused; serving takes neural scenes
+    (tests/test_gpu_serving.py)."""
     from paper_2508_03180_gb300 import _lib as L
     sc = synth.neural_scene(n_cells=50, K=4, F=8, H=8, seed=1)
     sid = rctx.upload_scene(sc)
@@ -76,13 +79,7 @@ def test_paths_not_built_refuse_neural_scenes(rctx):
             rctx.backward(state, torch.zeros_like(flat), dict(g_mean=torch.zeros(sc.G, 3, device="cuda")))
         with pytest.raises(L.DgsError) as e2:
             rctx.render_compare(sid, [cam], "alpha")
-        rctx.serve_start(max_batch=2)
-        try:
-            with pytest.raises(L.DgsError) as e3:
-                rctx.submit(sid, cam, torch.zeros(3 * 32 * 32, device="cuda"))
-        finally:
-            rctx.serve_stop()
-        assert e1.value.code == e2.value.code == e3.value.code == L.DGS_ERR_INVALID_ARG
+        assert e1.value.code == e2.value.code == L.DGS_ERR_INVALID_ARG
     finally:
         rctx.release_state(state)
         rctx.release_scene(sid)

@@ -67,6 +67,50 @@ def test_same_result_alone_and_in_a_mixed_batch(scenes, graphs):
     c.close()
 
 
+@pytest.mark.parametrize("graphs", [True, False])
+def test_neural_scenes_served_alone_and_mixed(scenes, graphs):
+    """Neural-cell scenes in serving: batches that mix two neural scenes (one
+    on the tensor-core decode, one wider on the CUDA-core decode) with an
+    explicit scene return exactly the image dgs_render gives each view alone;
+    each composition of neural scenes is its own captured graph."""
+    c = _ctx()
+    neural = [synth.neural_scene(n_cells=700, K=10, F=32, H=32, seed=3),
+              synth.neural_scene(n_cells=500, K=6, F=20, H=36, seed=4)]
+    sids = [c.upload_scene(scenes[0])] + [c.upload_scene(n) for n in neural]
+    cams = [synth.sphere_cameras(1, 3.0, W, H, seed0=20 + i)[0] for i, (W, H) in
+            enumerate([(64, 48), (128, 72), (33, 17), (200, 120), (96, 96), (160, 90), (80, 64), (120, 40)])]
+    which = [1, 0, 2, 1, 1, 2, 0, 2]
+    ref = []
+    for cam, w in zip(cams, which):
+        img, _, _ = c.render(sids[w], [cam])
+        ref.append(img.clone())
+    torch.cuda.synchronize()
+    c.serve_start(max_batch=8, graphs=graphs)
+    results, outs = [], []
+    for rnd in range(2):  # the second round replays the captured graphs
+        o = [torch.zeros_like(r) for r in ref]
+        ts = [c.submit(sids[w], cam, o[i]) for i, (cam, w) in enumerate(zip(cams, which))]
+        results += [c.poll(t, -1) for t in ts]
+        outs.append(o)
+    # only neural scenes in a batch
+    o3 = [torch.zeros_like(ref[i]) for i in (0, 2, 3)]
+    ts = [c.submit(sids[which[i]], cams[i], o3[j]) for j, i in enumerate((0, 2, 3))]
+    results += [c.poll(t, -1) for t in ts]
+    stats = c.serve_stats()
+    c.serve_stop()
+    torch.cuda.synchronize()
+    assert all(r.status == 0 for r in results), [r.status for r in results]
+    assert max(r.batch_size for r in results) > 1
+    if graphs:
+        assert stats["graphs_captured"] >= 1
+    for o in outs:
+        for a, r in zip(o, ref):
+            assert torch.equal(a, r)
+    for a, i in zip(o3, (0, 2, 3)):
+        assert torch.equal(a, ref[i])
+    c.close()
+
+
 def test_pair_overflow_grows_buffers_and_reruns():
     # thousands of large cells over a 48x32 view: far more (tile, cell) pairs
     # per tile than the initial estimate that sizes the captured buffers
