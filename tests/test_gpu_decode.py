@@ -65,6 +65,33 @@ def test_decode_and_render(rctx, F, H, K):
         rctx.release_scene(sid)
 
 
+@pytest.mark.parametrize("F,H,K", [(32, 32, 10), (20, 36, 7)])
+def test_neural_scene_out_of_view(rctx, F, H, K):
+    """Nothing in view: the decode's device count is 0 while its capacity is
+    not (the asynchronous chain), or 0 on the host (stats); both renders give
+    the background, and a backward gives zero gradients."""
+    from oracle import decode as odec
+    sc = synth.neural_scene(n_cells=300, K=K, F=F, H=H, seed=2)
+    away = synth.look_at((0.0, -3.0, 0.0), (0.0, -6.0, 0.0), 96, 64)  # looking away from the cells
+    sid = rctx.upload_scene(sc)
+    try:
+        rctx.render(sid, [synth.small_camera(64, 48)])  # the context has rendered: later renders are device-sized
+        a, sa, _ = rctx.render(sid, [away], want_state=True)
+        b, sb, st = rctx.render(sid, [away], want_state=True, stats=True)
+        torch.cuda.synchronize()
+        assert st.visible_cells == 0
+        assert torch.equal(a, b) and float(a.abs().max()) == 0.0
+        P = odec.packed_size(F, H, K)
+        g = dict(g_mlp=torch.full((P,), 7.0, device="cuda"), g_feat=torch.full((sc.N, F), 7.0, device="cuda"))
+        rctx.backward(sa, torch.ones_like(a), g)
+        torch.cuda.synchronize()
+        assert float(g["g_mlp"].abs().max()) == 0.0 and float(g["g_feat"].abs().max()) == 0.0
+        rctx.release_state(sa)
+        rctx.release_state(sb)
+    finally:
+        rctx.release_scene(sid)
+
+
 def test_paths_not_built_refuse_neural_scenes(rctx):
     """Explicit-Gaussian gradients of a neural scene and the comparators (which
     project explicit Gaussians) are refused; serving takes neural scenes
