@@ -548,9 +548,9 @@ __global__ void __launch_bounds__(256) k_decode(const ViewDesc *__restrict__ vie
 // shared memory, from which the epilogue (decode_gaussian) runs as in
 // k_decode, one (sample, Gaussian) per thread.
 constexpr int TC_M = 128;
-constexpr int TC_THREADS = 512;
-constexpr int TC_CW = 128 / (TC_THREADS / 128);  // accumulator columns a warp moves out of tensor memory
-constexpr int TC_ITEMS = 3;     // (sample, Gaussian) items a thread decodes per tile: 128 K <= 3 x 512
+constexpr int TC_THREADS = 768;  // 24 warps: the epilogue's latency is what they hide (72 registers)
+constexpr int TC_CW = 32;        // accumulator columns a warp moves out of tensor memory (warps 0-15)
+constexpr int TC_ITEMS = 2;      // (sample, Gaussian) items a thread decodes per tile: 128 K <= 2 x 768
 constexpr int TC_LDO = TC_M + 1;  // output tile row stride (floats): (column, sample) reads spread over banks
 
 struct TcShape {
@@ -651,17 +651,24 @@ __device__ __forceinline__ void tc_stage(const TcShape &T, unsigned char *sm, co
     __syncthreads();
     unsigned char *zh = sm + T.s_u, *zl = zh + 4 * TC_M * T.IP;
     // one 16-byte chunk (4 inputs) of one sample per item; consecutive threads
-    // take consecutive samples (a warp's stores fill whole 128-byte lines)
-    for (int it = threadIdx.x; it < TC_M * (T.IP / 4); it += blockDim.x) {
-        const int s = it % TC_M, c = it / TC_M;
+    // walk a sample's feature row (16-byte loads where the row allows)
+    const int nc = T.IP / 4;
+    const bool vec = (T.F & 3) == 0;
+    for (int it = threadIdx.x; it < TC_M * nc; it += blockDim.x) {
+        const int s = it / nc, c = it - s * nc;
         const float *p = info + s * DINFO;
         const bool valid = __float_as_int(p[1]) != 0;
         const float *row = sc.feat + (long long)__float_as_int(p[0]) * T.F;
         float z[4];
+        if (valid && vec && 4 * c + 3 < T.F) {
+            const float4 f = __ldg(reinterpret_cast<const float4 *>(row) + c);
+            z[0] = f.x; z[1] = f.y; z[2] = f.z; z[3] = f.w;
+        } else {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int i = 4 * c + u;
-            z[u] = !valid || i >= T.I ? 0.f : (i < T.F ? __ldg(row + i) : p[19 + i - T.F]);
+            for (int u = 0; u < 4; ++u) {
+                const int i = 4 * c + u;
+                z[u] = !valid || i >= T.I ? 0.f : (i < T.F ? __ldg(row + i) : p[19 + i - T.F]);
+            }
         }
         float4 h, l;
         tc::split_tf32(z[0], h.x, l.x);
@@ -724,7 +731,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_decode_tc(const ViewDesc *__r
     const float *b2 = reinterpret_cast<const float *>(sm) + T.g_b2;
     const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;  // this warp's TMEM lanes
     const int s = 32 * (warp & 3) + lane;                         // its sample (TMEM lane)
-    const int cbase = TC_CW * (warp >> 2);                        // its TC_CW of the 128 columns
+    const int cbase = warp < 16 ? TC_CW * (warp >> 2) : 0;       // its TC_CW of the 128 columns
+    const int cend = warp < 16 ? cbase + TC_CW : 0;               // (warps 16.. move none)
     uint32_t phase = 0;
     for (long long q0 = (long long)blockIdx.x * TC_M; q0 < nsamp; q0 += (long long)gridDim.x * TC_M) {
         tc_stage(T, sm, sc, srec, nsamp, q0);
@@ -744,7 +752,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_decode_tc(const ViewDesc *__r
         {
             unsigned char *hh = sm + T.s_u, *hl = hh + 4 * TC_M * TC_M;
 #pragma unroll 1
-            for (int c0 = cbase; c0 < cbase + TC_CW; c0 += 16) {
+            for (int c0 = cbase; c0 < cend; c0 += 16) {
                 float v[16];
                 tc::ld16(tm + lane_base + (uint32_t)c0, v);
 #pragma unroll
@@ -780,7 +788,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_decode_tc(const ViewDesc *__r
         if (abort_flag) break;
         // layer 2 leaves tensor memory: + b2 into the output tile (over H, now read)
         float *Ot = reinterpret_cast<float *>(sm + T.s_u);
-        for (int c0 = cbase; c0 < cbase + TC_CW; c0 += 16) {
+        for (int c0 = cbase; c0 < cend; c0 += 16) {
             if (c0 >= T.rb[4]) break;
             float v[16];
             tc::ld16(tm + lane_base + 128u + (uint32_t)c0, v);
