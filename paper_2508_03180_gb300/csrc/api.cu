@@ -453,7 +453,8 @@ extern "C" dgs_status dgs_scene_save(dgs_ctx *ctx, uint32_t scene_id, const char
     // every array back to its row-major layout (the inverse of fill_scene's transposes)
     struct Part { const float *planes; int64_t rows; int cols; int64_t stride; };
     const float *cell = (const float *)sc.cell.p;
-    std::vector<Part> parts = {{cell, N, 3, N}, {cell + 3 * N, N, 3, N}, {cell + 6 * N, N, 4, N}, {cell + 10 * N, N, 1, N}};
+    std::vector<Part> parts = {
+        {cell, N, 3, N}, {cell + 3 * N, N, 3, N}, {cell + 6 * N, N, 4, N}, {cell + 10 * N, N, 1, N}};
     if (sc.F > 0) {
         parts.push_back({(const float *)sc.feat.p, N * sc.F, 1, N * sc.F});
         parts.push_back({(const float *)sc.goff.p, G, 3, G});
@@ -942,8 +943,8 @@ dgs_status chain_forward(dgs_ctx *ctx, Workspace &ws, const std::vector<ChainVie
         if (slots[k]->F > 0) {  // neural cells: decode the visible cells' Gaussians for every view first
             // the decode writes the records too (the projection fused into it)
             StageTimer t(ctx->prof, DGS_STAGE_DECODE, st);
-            launch_decode(dv, V, k, sd, (const uint32_t *)ws.zval.p, n_samp, (const uint32_t *)ws.small.p + kSmallVisible,
-                          (float *)ws.dec.p, (float *)ws.wpack.p, (const float *)ws.vview.p, bp, (float4 *)ws.rec.p,
+            launch_decode(dv, V, k, sd, (const uint32_t *)ws.zval.p, n_samp,
+                          (const uint32_t *)ws.small.p + kSmallVisible, (float *)ws.dec.p, (float *)ws.wpack.p, (const float *)ws.vview.p, bp, (float4 *)ws.rec.p,
                           grad_buffers ? (float *)ws.g2d.p : nullptr, (uint32_t *)ws.small.p + kSmallTcErr, st);
             ws.check_tc = true;
         } else {

@@ -178,7 +178,8 @@ __device__ __forceinline__ SampleInfo get_info(const float *s_info, int s) {
 // and the last four inputs; invalid for entries of another scene slot.
 __global__ void __launch_bounds__(128) k_decode_samples(const ViewDesc *__restrict__ views, int n_views, int slot,
                                                         SceneDev sc, const uint32_t *__restrict__ samples,
-                                                        long long nsamp, const uint32_t *__restrict__ d_n, float *__restrict__ srec) {
+                                                        long long nsamp,
+                                                        const uint32_t *__restrict__ d_n, float *__restrict__ srec) {
     if (d_n) nsamp = min(nsamp, (long long)*d_n);  // the count on the device (capacity nsamp)
     const long long N = sc.N;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nsamp;
@@ -489,7 +490,8 @@ __device__ __forceinline__ void decode_gaussian(const ViewDesc *__restrict__ vie
 template <int HW>
 __global__ void __launch_bounds__(256) k_decode(const ViewDesc *__restrict__ views, SceneDev sc, MlpShape S,
                                                 const float *__restrict__ pk, const float *__restrict__ srec,
-                                                const float4 *__restrict__ gc, long long nsamp, const uint32_t *__restrict__ d_n,
+                                                const float4 *__restrict__ gc, long long nsamp,
+                                                const uint32_t *__restrict__ d_n,
                                                 float *__restrict__ dec, const float *__restrict__ vview,
                                                 BlendParams bp, float4 *__restrict__ rec,
                                                 float *__restrict__ g2d_zero) {
@@ -699,7 +701,8 @@ __device__ __forceinline__ void tc_layer(uint32_t d, uint32_t a, uint32_t a_lo, 
 __global__ void __launch_bounds__(TC_THREADS, 1) k_decode_tc(const ViewDesc *__restrict__ views, SceneDev sc,
                                                                TcShape T, const float *__restrict__ img,
                                                                const float *__restrict__ srec,
-                                                               const float4 *__restrict__ gc, long long nsamp, const uint32_t *__restrict__ d_n,
+                                                               const float4 *__restrict__ gc, long long nsamp,
+                                                               const uint32_t *__restrict__ d_n,
                                                                float *__restrict__ dec, const float *__restrict__ vview,
                                                                BlendParams bp, float4 *__restrict__ rec,
                                                                float *__restrict__ g2d_zero, uint32_t *err) {
@@ -838,7 +841,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_decode_tc(const ViewDesc *__r
 // terms are compiled out).
 template <int HW, bool FUSE, bool CELL>
 __global__ void __launch_bounds__(256) k_decode_bwd(SceneDev sc, MlpShape S, const float *__restrict__ pk,
-                                                    const float *__restrict__ srec, long long nsamp, const uint32_t *__restrict__ d_n,
+                                                    const float *__restrict__ srec, long long nsamp,
+                                                    const uint32_t *__restrict__ d_n,
                                                     const float *__restrict__ gdec,
                                                         float *__restrict__ g_feat, float *__restrict__ g_offset,
                                                         float *__restrict__ rows, float *__restrict__ g_mlp,
@@ -1218,7 +1222,8 @@ struct WgProblem {
 };
 struct WgProblems { WgProblem p[5]; };
 
-__global__ void __launch_bounds__(WT_T) k_mlp_wgrad(const float *__restrict__ rows, MlpShape S, long long nsamp, const uint32_t *__restrict__ d_n,
+__global__ void __launch_bounds__(WT_T) k_mlp_wgrad(const float *__restrict__ rows, MlpShape S, long long nsamp,
+                                                    const uint32_t *__restrict__ d_n,
                                                     int chunk, WgProblems probs, float *__restrict__ g_mlp) {
     if (d_n) nsamp = min(nsamp, (long long)*d_n);  // the count on the device (capacity nsamp)
     __shared__ __align__(16) float sA[2][WT_S][WT_A + 4];
