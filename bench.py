@@ -429,8 +429,11 @@ def neural_fwdbwd_bench(rctx, fp32_tflops, steps=5, F=32, H=32, K=10):
     random weights) on the multi-scale layout (100,000 cells x 10 Gaussians
     in [-10,10]^3, semi-axes over [0.001, 1]), the headline's 8 views at
     1920x1080, L1 loss, forward + backward to the weights, features and
-    offsets.  The decode and its adjoint are FP32-issue bound; their FLOPs per
-    decoded (view, cell) are counted from the kernels' loops."""
+    offsets.  The decode's products run on the tensor cores at these widths
+    and its adjoint's on the CUDA cores; both are reported against the
+    measured FP32 FMA rate for comparison, their FLOPs per decoded (view,
+    cell) counted from the kernels' loops.  Timed steps render without stats
+    (asynchronously); one untimed render reads the counts."""
     import torch
 
     from paper_2508_03180_gb300 import _lib as L
