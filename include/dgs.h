@@ -617,8 +617,19 @@ dgs_status dgs_debug_check_guards(int64_t *n_checked);
  *                           its trailing guard overwritten (a host-side
  *                           cudaMemset inside the allocation), so a later
  *                           dgs_debug_check_guards reports it.
+ *   DGS_FAULT_TC_WAIT       while count != 0, the tensor-core decode of
+ *                           neural cells launched on the current device
+ *                           issues no products for its first tile and waits
+ *                           about 2^24 clocks for them, so its completion
+ *                           wait runs out with nothing in flight: the kernel
+ *                           frees its tensor memory and returns, the decode
+ *                           results are not valid, and the render's chain
+ *                           reports DGS_ERR_TIMEOUT (returned, once it is
+ *                           seen complete, by the next call on the context,
+ *                           as for a render whose sort gave up).
  * ctx may be NULL except for DGS_FAULT_SERVE_WORKER (serving started). */
-enum { DGS_FAULT_ALLOC = 1, DGS_FAULT_SORT_WAIT = 2, DGS_FAULT_SERVE_WORKER = 3, DGS_FAULT_GUARD = 4 };
+enum { DGS_FAULT_ALLOC = 1, DGS_FAULT_SORT_WAIT = 2, DGS_FAULT_SERVE_WORKER = 3, DGS_FAULT_GUARD = 4,
+       DGS_FAULT_TC_WAIT = 5 };
 dgs_status dgs_debug_inject_fault(dgs_ctx *ctx, int32_t kind, int32_t count);
 
 #ifdef __cplusplus

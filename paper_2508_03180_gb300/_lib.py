@@ -27,6 +27,7 @@ DGS_FAULT_ALLOC = 1
 DGS_FAULT_SORT_WAIT = 2
 DGS_FAULT_SERVE_WORKER = 3
 DGS_FAULT_GUARD = 4
+DGS_FAULT_TC_WAIT = 5
 DGS_HOST = 0
 DGS_DEVICE = 1
 

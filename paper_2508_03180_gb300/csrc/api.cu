@@ -1386,6 +1386,11 @@ extern "C" dgs_status dgs_debug_inject_fault(dgs_ctx *ctx, int32_t kind, int32_t
             CK(set_sort_fault(count != 0));
             return DGS_OK;
         }
+        case DGS_FAULT_TC_WAIT: {
+            if (ctx) CK(cudaSetDevice(ctx->cfg.device));
+            CK(set_tc_fault(count != 0));
+            return DGS_OK;
+        }
         case DGS_FAULT_SERVE_WORKER:
             return serve_inject_fault(ctx, count);
         case DGS_FAULT_GUARD:

@@ -638,6 +638,16 @@ __global__ void k_mlp_pack_tc(const float *__restrict__ w, TcShape T, float *__r
     }
 }
 
+// Fault injection (dgs_debug_inject_fault, DGS_FAULT_TC_WAIT): while set, the
+// tensor-core decode issues no products for its first tile and waits about
+// 2^24 clocks, so its completion wait runs out with nothing in flight.
+__device__ int g_tc_fault = 0;
+
+cudaError_t set_tc_fault(bool on) {
+    const int v = on ? 1 : 0;
+    return cudaMemcpyToSymbol(g_tc_fault, &v, sizeof(int));
+}
+
 // Stage samples [q0, q0 + 128): records (invalid past the end) and Z as the
 // hi and lo operand tiles (zero for invalid samples and padded inputs).
 __device__ __forceinline__ void tc_stage(const TcShape &T, unsigned char *sm, const SceneDev &sc,
@@ -737,16 +747,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_decode_tc(const ViewDesc *__r
     const int cbase = warp < 16 ? TC_CW * (warp >> 2) : 0;       // its TC_CW of the 128 columns
     const int cend = warp < 16 ? cbase + TC_CW : 0;               // (warps 16.. move none)
     uint32_t phase = 0;
+    const bool fault = g_tc_fault != 0;
+    const long long wait_clocks = fault ? (1LL << 24) : (1LL << 31);
     for (long long q0 = (long long)blockIdx.x * TC_M; q0 < nsamp; q0 += (long long)gridDim.x * TC_M) {
         tc_stage(T, sm, sc, srec, nsamp, q0);
         const float *info = reinterpret_cast<const float *>(sm + T.s_info);
         tc::fence_async_smem();
         tc::sync_threads();
-        if (t == 0) {
+        if (t == 0 && !fault) {
             tc_layer(tm, u, 4 * TC_M * T.IP, T.IP * 32, w1, w1_lo, T.IP * 32, T.IP / 8, tc::idesc_tf32(TC_M, TC_M));
             tc::commit(&mbar);
         }
-        if (!tc::mbar_wait(&mbar, phase)) abort_flag = 1;
+        if (!tc::mbar_wait(&mbar, phase, wait_clocks)) abort_flag = 1;
         phase ^= 1;
         tc::fence_after();
         __syncthreads();
@@ -784,7 +796,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_decode_tc(const ViewDesc *__r
             }
             tc::commit(&mbar);
         }
-        if (!tc::mbar_wait(&mbar, phase)) abort_flag = 1;
+        if (!tc::mbar_wait(&mbar, phase, wait_clocks)) abort_flag = 1;
         phase ^= 1;
         tc::fence_after();
         __syncthreads();

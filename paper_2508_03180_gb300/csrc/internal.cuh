@@ -250,6 +250,7 @@ long long resident_ctas(const void *kernel, int threads);
 
 // Test-only: make the radix sort's look-back waits run out (see sort.cu).
 cudaError_t set_sort_fault(bool on);
+cudaError_t set_tc_fault(bool on);  // the tensor-core decode's completion wait runs out (DGS_FAULT_TC_WAIT)
 
 // Asynchronous 16-byte global-to-shared copies (cp.async, cached in L2
 // only): both addresses 16-byte aligned.  A copy is complete for the issuing

@@ -54,8 +54,8 @@ __device__ __forceinline__ void mbar_init(uint64_t *mbar, uint32_t count) {
 }
 
 // Wait for the phase with the given parity; gives up after 2^20 polls or
-// about 2^31 clocks (about a second) and returns false.
-__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity) {
+// `clocks` clocks (by default 2^31, about a second) and returns false.
+__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, long long clocks = 1LL << 31) {
     const uint32_t a = smem_u32(mbar);
     const long long t0 = clock64();
     for (int it = 0; it < (1 << 20); ++it) {
@@ -66,7 +66,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity) {
             : "r"(a), "r"(parity)
             : "memory");
         if (ok) return true;
-        if (clock64() - t0 > (1LL << 31)) break;
+        if (clock64() - t0 > clocks) break;
     }
     return false;
 }

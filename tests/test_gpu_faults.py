@@ -10,7 +10,11 @@ fault-injection calls, include/dgs.h):
   DGS_ERR_WORKER at once (no poll blocks), submit refuses new requests, and
   serving restarts;
 * guard words next to device buffers report an overwrite (made on the host,
-  inside the allocation) and pass again once that buffer is released.
+  inside the allocation) and pass again once that buffer is released;
+* the tensor-core decode's completion wait made to run out (no products
+  issued, a short limit) ends the kernel, the next call on the context
+  returns DGS_ERR_TIMEOUT, and the context then renders the neural scene
+  exactly as before.
 """
 import time
 
@@ -146,3 +150,36 @@ def test_guard_words_report_an_overwrite():
         L.dgs_debug_inject_fault(None, L.DGS_FAULT_GUARD, 0)
         ctx.close()  # releases the overwritten buffer
     assert L.dgs_debug_check_guards() >= 0
+
+
+def test_tensor_core_wait_runs_out_and_the_context_stays_usable():
+    from oracle import decode as odec
+    F, H, K = 32, 32, 10
+    sc = synth.neural_scene(n_cells=600, K=K, F=F, H=H, seed=5)
+    cams = [synth.small_camera(96, 64), synth.sphere_cameras(1, 3.0, 80, 60, seed0=4)[0]]
+    ctx = Context()
+    try:
+        sid = ctx.upload_scene(sc)
+        ref = _render(ctx, sid, cams)
+        g = dict(g_mlp=torch.zeros(odec.packed_size(F, H, K), device="cuda"))
+        L.dgs_debug_inject_fault(ctx.ctx, L.DGS_FAULT_TC_WAIT, 1)
+        try:
+            t0 = time.monotonic()
+            img, state, _ = ctx.render(sid, cams, want_state=True)  # asynchronous: returns before the wait ends
+            torch.cuda.synchronize()
+            elapsed = time.monotonic() - t0
+        finally:
+            L.dgs_debug_inject_fault(ctx.ctx, L.DGS_FAULT_TC_WAIT, 0)
+        assert elapsed < 5.0, elapsed
+        with pytest.raises(L.DgsError) as ei:
+            ctx.backward(state, torch.ones_like(img), g)  # the completed chain's status is seen here
+        assert ei.value.code == L.DGS_ERR_TIMEOUT and "tensor-core" in str(ei.value), str(ei.value)
+        ctx.release_state(state)
+        assert torch.equal(_render(ctx, sid, cams), ref)
+        _, state2, _ = ctx.render(sid, cams, want_state=True)
+        ctx.backward(state2, torch.ones_like(img), g)
+        torch.cuda.synchronize()
+        assert g["g_mlp"].abs().max() > 0
+        ctx.release_state(state2)
+    finally:
+        ctx.close()
