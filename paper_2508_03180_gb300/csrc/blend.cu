@@ -496,18 +496,18 @@ __device__ __forceinline__ float rcp_approx(float x) {
 // Screen-space gradient terms of (pixel, Gaussian) pairs for the two pixels
 // of one lane row at once (one f32x2 operation per pixel pair), with the
 // constant factors left to the caller (applied once per reduced total):
-//   acc[0..1] = sum L (s1, s2) dq'     (dmu = 2 ln 2 acc, see below)
+//   acc[0..1] = sum dq' (dx, dy)       (moments; mean_terms makes them the mean's)
 //   acc[2..4] = sum dq' (dx^2, dx dy, dy^2)  (da, db, dc = -1/2, -1, -1/2 x acc)
 //   acc[5..7] = sum v T alpha e       (drgb)
 //   dop       = sum dalpha G          (dsigma)
 //   dv       -= S alpha / (1 - v alpha)  (the pair's share of dL/dv, per cell)
 // with dq' = G dalpha sigma = -2 dL/dq.  cA = v T_n and vS = v S_n are the
-// pixels' per-cell factors; dx and pdx = L_00 dx the lane's column offsets
-// (shared by its rows).  A pixel with G' = 0 (not reached, or inactive) adds
+// pixels' per-cell factors; dx the lane's column offsets (shared by its
+// rows).  A pixel with G' = 0 (not reached, or inactive) adds
 // exactly 0, and the opacity-clamped branch is a select, so no per-pixel
 // branch remains.
 __device__ __forceinline__ void pair_grad2(float2 acc[8], float2 &dop, float2 &dv, float2 Gv, float4 r0, float4 r1,
-                                           float4 r2, float2 dx, float2 pdx, float py, float2 cA, float2 Sn, float2 vS,
+                                           float4 r2, float2 dx, float py, float2 cA, float2 Sn, float2 vS,
                                            float2 e0, float2 e1, float2 e2, float2 eD, float alpha_max) {
     const float v = r2.w, op = r1.w;
     const float2 raw = __fmul2_rn(make_float2(op, op), Gv);
@@ -532,16 +532,25 @@ __device__ __forceinline__ void pair_grad2(float2 acc[8], float2 &dop, float2 &d
     const float2 dq = __fmul2_rn(dG, make_float2(op, op));
     const float dys = py - r0.y;
     const float2 dy = make_float2(dys, dys);
-    // q = |L^T d|^2 with the record's L scaled by kappa (kappa^2 = log2(e)/2):
-    // dq/dmu = -2 Q d = -(2/kappa^2) L (s1, s2), 2/kappa^2 = 4 ln 2
-    const float2 s1 = __ffma2_rn(make_float2(r1.y, r1.y), dy, pdx);
-    const float s2 = r1.z * dys, zs2 = r1.z * s2;
-    acc[0] = __ffma2_rn(dq, __fmul2_rn(make_float2(r1.x, r1.x), s1), acc[0]);
-    acc[1] = __ffma2_rn(dq, __ffma2_rn(make_float2(r1.y, r1.y), s1, make_float2(zs2, zs2)), acc[1]);
-    const float2 dqx = __fmul2_rn(dq, dx);
+    const float2 dqx = __fmul2_rn(dq, dx), dqy = __fmul2_rn(dq, dy);
+    acc[0] = __fadd2_rn(acc[0], dqx);
+    acc[1] = __fadd2_rn(acc[1], dqy);
     acc[2] = __ffma2_rn(dqx, dx, acc[2]);
     acc[3] = __ffma2_rn(dqx, dy, acc[3]);
-    acc[4] = __ffma2_rn(__fmul2_rn(dq, dy), dy, acc[4]);
+    acc[4] = __ffma2_rn(dqy, dy, acc[4]);
+}
+
+// The mean's terms of a lane, from its moments m = sum dq' (dx, dy): with the
+// record's L scaled by kappa (kappa^2 = log2(e)/2), q = |L^T d|^2 and
+// dq/dmu = -2 Q d = -(2/kappa^2) L (s1, s2), (s1, s2) = L^T d = (p dx + r dy,
+// t dy), 2/kappa^2 = 4 ln 2; summed over pixels, sum dq' L (s1, s2) =
+// (p u, r u + t^2 m_y) with u = p m_x + r m_y (linear in the moments, so each
+// lane converts its partial sums before the warp reduction: no shuffle).
+__device__ __forceinline__ void mean_terms(float4 r1, float &a0, float &a1) {
+    const float u = fmaf(r1.x, a0, r1.y * a1);
+    const float b1 = fmaf(r1.y, u, r1.z * r1.z * a1);
+    a0 = r1.x * u;
+    a1 = b1;
 }
 
 // Constant factor of reduction slot j (see pair_grad2): dL/dq = -dq'/2, so
@@ -787,17 +796,17 @@ __global__ void __launch_bounds__(WT, BWD_MINB) k_blend_bwd(const ViewDesc *__re
             for (int j = 0; j < 8; ++j) acc2[j] = make_float2(0.f, 0.f);
             float2 dop2 = make_float2(0.f, 0.f);
             const float2 gdx = __fadd2_rn(px2, make_float2(-r0.x, -r0.x));
-            const float2 gpdx = __fmul2_rn(make_float2(r1.x, r1.x), gdx);
 #pragma unroll
             for (int rr = 0; rr < NR; ++rr) {
                 float2 e0, e1, e2, eD;
                 efac(rr, e0, e1, e2, eD);
-                pair_grad2(acc2, dop2, dv2, gv[rr], r0, r1, r2, gdx, gpdx, pys[rr], __fmul2_rn(v2, Tn[rr]), S[rr],
+                pair_grad2(acc2, dop2, dv2, gv[rr], r0, r1, r2, gdx, pys[rr], __fmul2_rn(v2, Tn[rr]), S[rr],
                            __fmul2_rn(v2, S[rr]), e0, e1, e2, eD, bp.alpha_max);
             }
             float acc[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) acc[j] = acc2[j].x + acc2[j].y;
+            mean_terms(r1, acc[0], acc[1]);
             const float tot = transposed_warp_sum8(acc, lane);
             const float dop_tot = warp_sum(dop2.x + dop2.y);
             float *gk = gbase + k * kGradF;
