@@ -496,48 +496,60 @@ __device__ __forceinline__ float rcp_approx(float x) {
 // Screen-space gradient terms of (pixel, Gaussian) pairs for the two pixels
 // of one lane row at once (one f32x2 operation per pixel pair), with the
 // constant factors left to the caller (applied once per reduced total):
-//   acc[0..1] = sum dq' (dx, dy)       (moments; mean_terms makes them the mean's)
-//   acc[2..4] = sum dq' (dx^2, dx dy, dy^2)  (da, db, dc = -1/2, -1, -1/2 x acc)
+//   acc[1], acc[4] = sum dq' dy, sum dq' dy^2 per column (column_terms forms
+//   the lane's moments sum dq' (dx, dy), which mean_terms makes the mean's,
+//   and sum dq' (dx^2, dx dy, dy^2): da, db, dc = -1/2, -1, -1/2 x acc)
 //   acc[5..7] = sum v T alpha e       (drgb)
 //   dop       = sum dalpha G          (dsigma)
-//   dv       -= S alpha / (1 - v alpha)  (the pair's share of dL/dv, per cell)
-// with dq' = G dalpha sigma = -2 dL/dq.  cA = v T_n and vS = v S_n are the
-// pixels' per-cell factors; dx the lane's column offsets (shared by its
-// rows).  A pixel with G' = 0 (not reached, or inactive) adds
+//   pv       += alpha / (1 - v alpha)  (per pixel; times -S_n, dL/dv's share)
+// with dq' = G dalpha sigma = -2 dL/dq.  cA = v T_n and nvS = -v S_n are the
+// pixels' per-cell factors (formed once per cell); dx the lane's column
+// offsets (shared by its rows).  A pixel with G' = 0 (not reached, or inactive) adds
 // exactly 0, and the opacity-clamped branch is a select, so no per-pixel
 // branch remains.
-__device__ __forceinline__ void pair_grad2(float2 acc[8], float2 &dop, float2 &dv, float2 Gv, float4 r0, float4 r1,
-                                           float4 r2, float2 dx, float py, float2 cA, float2 Sn, float2 vS,
+__device__ __forceinline__ void pair_grad2(float2 acc[8], float2 &dop, float2 &pv, float2 Gv, float4 r0, float4 r1,
+                                           float4 r2, float2 dx, float py, float2 cA, float2 nvS,
                                            float2 e0, float2 e1, float2 e2, float2 eD, float alpha_max) {
     const float v = r2.w, op = r1.w;
     const float2 raw = __fmul2_rn(make_float2(op, op), Gv);
     const float2 al = make_float2(fminf(raw.x, alpha_max), fminf(raw.y, alpha_max));
     const float2 om = __ffma2_rn(make_float2(-v, -v), al, make_float2(1.0f, 1.0f));
     const float2 rom = make_float2(rcp_approx(om.x), rcp_approx(om.y));
-    const float2 inner = __fadd2_rn(
-        __ffma2_rn(e2, make_float2(r2.z, r2.z),
-                   __ffma2_rn(e1, make_float2(r2.y, r2.y), __fmul2_rn(e0, make_float2(r2.x, r2.x)))),
-        eD);
-    const float2 dal = __ffma2_rn(make_float2(-vS.x, -vS.y), rom, __fmul2_rn(cA, inner));
+    const float2 inner = __ffma2_rn(
+        e0, make_float2(r2.x, r2.x),
+        __ffma2_rn(e1, make_float2(r2.y, r2.y), __ffma2_rn(e2, make_float2(r2.z, r2.z), eD)));
+    const float2 dal = __ffma2_rn(nvS, rom, __fmul2_rn(cA, inner));
     const float2 ca_al = __fmul2_rn(cA, al);
     acc[5] = __ffma2_rn(ca_al, e0, acc[5]);
     acc[6] = __ffma2_rn(ca_al, e1, acc[6]);
     acc[7] = __ffma2_rn(ca_al, e2, acc[7]);
-    const float2 sa = __fmul2_rn(Sn, al);
-    dv = __ffma2_rn(make_float2(-sa.x, -sa.y), rom, dv);
+    pv = __ffma2_rn(al, rom, pv);
     float2 dG = __fmul2_rn(dal, Gv);
     dG.x = raw.x < alpha_max ? dG.x : 0.f;
     dG.y = raw.y < alpha_max ? dG.y : 0.f;
     dop = __fadd2_rn(dop, dG);
-    const float2 dq = __fmul2_rn(dG, make_float2(op, op));
-    const float dys = py - r0.y;
-    const float2 dy = make_float2(dys, dys);
-    const float2 dqx = __fmul2_rn(dq, dx), dqy = __fmul2_rn(dq, dy);
-    acc[0] = __fadd2_rn(acc[0], dqx);
+    // per column of the lane (dx is the same for its rows): sum dq' dy and
+    // sum dq' dy^2; the dx-weighted sums follow from dop (dq' = sigma dG)
+    // and these in column_terms
+    const float dys = py - r0.y, opdy = op * dys;
+    const float2 dqy = __fmul2_rn(dG, make_float2(opdy, opdy));
     acc[1] = __fadd2_rn(acc[1], dqy);
-    acc[2] = __ffma2_rn(dqx, dx, acc[2]);
-    acc[3] = __ffma2_rn(dqx, dy, acc[3]);
-    acc[4] = __ffma2_rn(dqy, dy, acc[4]);
+    acc[4] = __ffma2_rn(dqy, make_float2(dys, dys), acc[4]);
+}
+
+// A lane's totals of slots 0..4 from its per-column sums (components x, y:
+// its two columns, offsets dx from the Gaussian's centre): with D = sigma dop
+// = sum dq' per column and Y = acc[1] = sum dq' dy per column,
+//   sum dq' dx = D.dx, sum dq' dy = sum Y, sum dq' dx^2 = D.dx^2,
+//   sum dq' dx dy = Y.dx, sum dq' dy^2 = sum acc[4].
+__device__ __forceinline__ void column_terms(const float2 acc2[8], float2 dop, float op, float2 dx, float acc[8]) {
+    const float2 D = __fmul2_rn(dop, make_float2(op, op));
+    const float2 t = __fmul2_rn(D, dx);
+    acc[0] = t.x + t.y;
+    acc[1] = acc2[1].x + acc2[1].y;
+    acc[2] = fmaf(t.x, dx.x, t.y * dx.y);
+    acc[3] = fmaf(acc2[1].x, dx.x, acc2[1].y * dx.y);
+    acc[4] = acc2[4].x + acc2[4].y;
 }
 
 // The mean's terms of a lane, from its moments m = sum dq' (dx, dy): with the
@@ -776,7 +788,14 @@ __global__ void __launch_bounds__(WT, BWD_MINB) k_blend_bwd(const ViewDesc *__re
                 dv += Tn[rr].y * X[rr].y;
             }
         }
-        float2 dv2 = make_float2(0.f, 0.f);
+        // per pixel: sum alpha / (1 - v alpha) of the cell's Gaussians; v T_n; -v S_n
+        float2 pv[NR], cA[NR], nvS[NR];
+#pragma unroll
+        for (int rr = 0; rr < NR; ++rr) {
+            pv[rr] = make_float2(0.f, 0.f);
+            cA[rr] = __fmul2_rn(v2, Tn[rr]);
+            nvS[rr] = __fmul2_rn(make_float2(-v, -v), S[rr]);
+        }
         const uint32_t cellid = __ldg(cells + e);
         float *gbase = g2d + (V.rec_base + (long long)cellid * K) * kGradF;
         // pass 2: gradient terms per Gaussian reaching the sub-tile, two
@@ -800,12 +819,13 @@ __global__ void __launch_bounds__(WT, BWD_MINB) k_blend_bwd(const ViewDesc *__re
             for (int rr = 0; rr < NR; ++rr) {
                 float2 e0, e1, e2, eD;
                 efac(rr, e0, e1, e2, eD);
-                pair_grad2(acc2, dop2, dv2, gv[rr], r0, r1, r2, gdx, pys[rr], __fmul2_rn(v2, Tn[rr]), S[rr],
-                           __fmul2_rn(v2, S[rr]), e0, e1, e2, eD, bp.alpha_max);
+                pair_grad2(acc2, dop2, pv[rr], gv[rr], r0, r1, r2, gdx, pys[rr], cA[rr], nvS[rr], e0, e1, e2, eD,
+                           bp.alpha_max);
             }
             float acc[8];
+            column_terms(acc2, dop2, r1.w, gdx, acc);
 #pragma unroll
-            for (int j = 0; j < 8; ++j) acc[j] = acc2[j].x + acc2[j].y;
+            for (int j = 5; j < 8; ++j) acc[j] = acc2[j].x + acc2[j].y;
             mean_terms(r1, acc[0], acc[1]);
             const float tot = transposed_warp_sum8(acc, lane);
             const float dop_tot = warp_sum(dop2.x + dop2.y);
@@ -815,6 +835,9 @@ __global__ void __launch_bounds__(WT, BWD_MINB) k_blend_bwd(const ViewDesc *__re
             if (lane == 1 && dop_tot != 0.f) atomicAdd(gk + 5, dop_tot);
         }
         if (want_v) {  // per (view, cell) entry: v_n may differ between views
+            float2 dv2 = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int rr = 0; rr < NR; ++rr) dv2 = __ffma2_rn(make_float2(-S[rr].x, -S[rr].y), pv[rr], dv2);
             dv = warp_sum(dv + (dv2.x + dv2.y));
             if (lane == 0 && dv != 0.f) atomicAdd(g_cell_v + V.cell_base + cellid, dv);
         }
