@@ -102,6 +102,10 @@ __device__ __forceinline__ int lane_row(int lane, int r) { return (lane >> 3) + 
 // four pixels outweighs the register cost; the kernels are held to 64
 // registers (32 one-warp CTAs per SM; 1% faster than 72 registers and 28).
 constexpr int FWD_PPL = 4;
+// an offset from the Gaussian's centre that no box reaches: s1 or s2 then
+// squares to at least ~1e18 (the record's L entries are far above 1e-9), and
+// exp2 of its negation is +0
+constexpr float kFar = 1e18f;
 constexpr int FWD_SUB = kTile / (2 * FWD_PPL);  // sub-tiles per tile
 constexpr int FWD_MINB = 32;
 
@@ -198,10 +202,21 @@ __device__ __forceinline__ void blend_fwd_unit(int unit, const ViewDesc *__restr
                 hy[rr] = fabsf(dy[rr]) <= r0.w;
             }
             bool h[PPL], any = false;
+            if (VAR) {
 #pragma unroll
-            for (int q = 0; q < PPL; ++q) {
-                h[q] = !done[q] && hx[q & 1] && hy[q >> 1];
-                any = any || h[q];
+                for (int q = 0; q < PPL; ++q) {
+                    h[q] = !done[q] && hx[q & 1] && hy[q >> 1];
+                    any = any || h[q];
+                }
+            } else {
+                // outside the box along a column or a row: an offset far off
+                // the Gaussian, so exp2 gives alpha = +0 exactly (in-box pixels
+                // compute as before; a done pixel's sums are not used)
+                any = (hx[0] || hx[1]) && (hy[0] || hy[NR - 1]);
+#pragma unroll
+                for (int c = 0; c < 2; ++c) dx[c] = hx[c] ? dx[c] : kFar;
+#pragma unroll
+                for (int rr = 0; rr < NR; ++rr) dy[rr] = hy[rr] ? dy[rr] : kFar;
             }
             // warp-uniform skip: lanes without a hit run the body with alpha = 0
             if (!__any_sync(0xffffffffu, any)) continue;
@@ -217,8 +232,13 @@ __device__ __forceinline__ void blend_fwd_unit(int unit, const ViewDesc *__restr
                 float2 al = __fmul2_rn(make_float2(r1.w, r1.w), make_float2(ex2_approx(-qd.x), ex2_approx(-qd.y)));
                 // a pixel the Gaussian does not reach (or, with the alpha skip, an
                 // alpha below 1/255) takes alpha 0: every update below leaves it unchanged
-                al.x = h[2 * rr] && (!VAR || al.x >= amin) ? fminf(al.x, bp.alpha_max) : 0.f;
-                al.y = h[2 * rr + 1] && (!VAR || al.y >= amin) ? fminf(al.y, bp.alpha_max) : 0.f;
+                if (VAR) {
+                    al.x = h[2 * rr] && al.x >= amin ? fminf(al.x, bp.alpha_max) : 0.f;
+                    al.y = h[2 * rr + 1] && al.y >= amin ? fminf(al.y, bp.alpha_max) : 0.f;
+                } else {
+                    al.x = fminf(al.x, bp.alpha_max);
+                    al.y = fminf(al.y, bp.alpha_max);
+                }
                 A0[rr] = __ffma2_rn(al, make_float2(r2.x, r2.x), A0[rr]);
                 A1[rr] = __ffma2_rn(al, make_float2(r2.y, r2.y), A1[rr]);
                 A2[rr] = __ffma2_rn(al, make_float2(r2.z, r2.z), A2[rr]);
@@ -732,10 +752,21 @@ __global__ void __launch_bounds__(WT, BWD_MINB) k_blend_bwd(const ViewDesc *__re
                     hy[rr] = fabsf(dy[rr]) <= r0.w;
                 }
                 bool h[PPL], any = false;
+                if (VAR) {
 #pragma unroll
-                for (int q = 0; q < PPL; ++q) {
-                    h[q] = act[q] && hx[q & 1] && hy[q >> 1];
-                    any = any || h[q];
+                    for (int q = 0; q < PPL; ++q) {
+                        h[q] = act[q] && hx[q & 1] && hy[q >> 1];
+                        any = any || h[q];
+                    }
+                } else {
+                    // outside the box along a column or a row: an offset far off the
+                    // Gaussian (G' = +0 exactly, as in the forward); inactive pixels
+                    // get G' = 0 when it is stored (their X and P are not used)
+                    any = (hx[0] || hx[1]) && (hy[0] || hy[NR - 1]);
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) dx[c] = hx[c] ? dx[c] : kFar;
+#pragma unroll
+                    for (int rr = 0; rr < NR; ++rr) dy[rr] = hy[rr] ? dy[rr] : kFar;
                 }
                 if (!any) {
                     s_G[i][lane] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -753,10 +784,13 @@ __global__ void __launch_bounds__(WT, BWD_MINB) k_blend_bwd(const ViewDesc *__re
                     const float2 qd = __ffma2_rn(s1, s1, make_float2(s22, s22));
                     float2 Gv = make_float2(ex2_approx(-qd.x), ex2_approx(-qd.y));
                     float2 rw = __fmul2_rn(make_float2(r1.w, r1.w), Gv);
-                    // not reached (or alpha skipped as in the forward): G' = 0 leaves X and P as they are
-                    if (!h[2 * rr] || (VAR && rw.x < amin)) Gv.x = rw.x = 0.f;
-                    if (!h[2 * rr + 1] || (VAR && rw.y < amin)) Gv.y = rw.y = 0.f;
-                    gq[rr] = Gv;
+                    if (VAR) {  // not reached (or alpha skipped as in the forward): G' = 0 leaves X and P as they are
+                        if (!h[2 * rr] || rw.x < amin) Gv.x = rw.x = 0.f;
+                        if (!h[2 * rr + 1] || rw.y < amin) Gv.y = rw.y = 0.f;
+                        gq[rr] = Gv;
+                    } else {
+                        gq[rr] = make_float2(act[2 * rr] ? Gv.x : 0.f, act[2 * rr + 1] ? Gv.y : 0.f);
+                    }
                     const float2 al = make_float2(fminf(rw.x, bp.alpha_max), fminf(rw.y, bp.alpha_max));
                     float2 e0, e1, e2, eD;
                     efac(rr, e0, e1, e2, eD);
