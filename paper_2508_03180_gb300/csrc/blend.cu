@@ -86,6 +86,16 @@ __device__ __forceinline__ bool touches_rows(float4 r0, float x0, float y0, floa
     return !(lx - r0.x > r0.z || r0.x - hx > r0.z || ly - r0.y > r0.w || r0.y - hy > r0.w);
 }
 
+// Does record piece r0 pass the AABB test at every pixel centre of the block?
+// Exact: testing its first and last columns and rows suffices (FP32
+// subtraction is monotone, so every offset lies between theirs).
+__device__ __forceinline__ bool covers_rows(float4 r0, float x0, float y0, float rows) {
+    const float lx = x0 + 0.5f, hx = x0 + (float)kTile - 0.5f;
+    const float ly = y0 + 0.5f, hy = y0 + rows - 0.5f;
+    return fabsf(lx - r0.x) <= r0.z && fabsf(hx - r0.x) <= r0.z && fabsf(ly - r0.y) <= r0.w &&
+           fabsf(hy - r0.y) <= r0.w;
+}
+
 // Pixels of a lane in a 16 x (2 PPL) sub-tile: lane l = 8 j + i takes the
 // columns i and i + 8 and the rows j + 4 r (r < PPL / 2); pixel q = 2 r + c.
 // Each q thus spans an 8x4 quadrant of the warp's lanes, which meets fewer
@@ -176,6 +186,9 @@ __device__ __forceinline__ void blend_fwd_unit(int unit, const ViewDesc *__restr
         const float4 *r = s_rec[buf];
         const float v = r[2].w;
         unsigned mask = __ballot_sync(0xffffffffu, lane < K && touches_rows(r[kRecF4 * lane], bx0, by0, (float)ROWS));
+        // Gaussians whose box holds the whole sub-tile: no per-pixel test
+        const unsigned full = VAR ? 0u : __ballot_sync(0xffffffffu, lane < K && covers_rows(r[kRecF4 * lane], bx0, by0,
+                                                                                            (float)ROWS));
         // the lane's two pixels of a row as packed pairs (one f32x2 operation
         // per pair; per component the same IEEE operations as one pixel)
         float2 A0[NR], A1[NR], A2[NR], B[NR], P[NR];
@@ -190,36 +203,36 @@ __device__ __forceinline__ void blend_fwd_unit(int unit, const ViewDesc *__restr
             const int k = __ffs(mask) - 1;
             const float4 r0 = r[3 * k];
             float dx[2], dy[NR];
-            bool hx[2], hy[NR];
 #pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                dx[c] = pxs[c] - r0.x;
-                hx[c] = fabsf(dx[c]) <= r0.z;
-            }
+            for (int c = 0; c < 2; ++c) dx[c] = pxs[c] - r0.x;
 #pragma unroll
-            for (int rr = 0; rr < NR; ++rr) {
-                dy[rr] = pys[rr] - r0.y;
-                hy[rr] = fabsf(dy[rr]) <= r0.w;
-            }
-            bool h[PPL], any = false;
-            if (VAR) {
+            for (int rr = 0; rr < NR; ++rr) dy[rr] = pys[rr] - r0.y;
+            bool h[PPL];
+            if (VAR || !((full >> k) & 1u)) {  // (else every pixel of the sub-tile is in the box)
+                bool hx[2], hy[NR], any = false;
 #pragma unroll
-                for (int q = 0; q < PPL; ++q) {
-                    h[q] = !done[q] && hx[q & 1] && hy[q >> 1];
-                    any = any || h[q];
+                for (int c = 0; c < 2; ++c) hx[c] = fabsf(dx[c]) <= r0.z;
+#pragma unroll
+                for (int rr = 0; rr < NR; ++rr) hy[rr] = fabsf(dy[rr]) <= r0.w;
+                if (VAR) {
+#pragma unroll
+                    for (int q = 0; q < PPL; ++q) {
+                        h[q] = !done[q] && hx[q & 1] && hy[q >> 1];
+                        any = any || h[q];
+                    }
+                } else {
+                    // outside the box along a column or a row: an offset far off
+                    // the Gaussian, so exp2 gives alpha = +0 exactly (in-box pixels
+                    // compute as before; a done pixel's sums are not used)
+                    any = (hx[0] || hx[1]) && (hy[0] || hy[NR - 1]);
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) dx[c] = hx[c] ? dx[c] : kFar;
+#pragma unroll
+                    for (int rr = 0; rr < NR; ++rr) dy[rr] = hy[rr] ? dy[rr] : kFar;
                 }
-            } else {
-                // outside the box along a column or a row: an offset far off
-                // the Gaussian, so exp2 gives alpha = +0 exactly (in-box pixels
-                // compute as before; a done pixel's sums are not used)
-                any = (hx[0] || hx[1]) && (hy[0] || hy[NR - 1]);
-#pragma unroll
-                for (int c = 0; c < 2; ++c) dx[c] = hx[c] ? dx[c] : kFar;
-#pragma unroll
-                for (int rr = 0; rr < NR; ++rr) dy[rr] = hy[rr] ? dy[rr] : kFar;
+                // warp-uniform skip: lanes without a hit run the body with alpha = 0
+                if (!__any_sync(0xffffffffu, any)) continue;
             }
-            // warp-uniform skip: lanes without a hit run the body with alpha = 0
-            if (!__any_sync(0xffffffffu, any)) continue;
             const float4 r1 = r[3 * k + 1];
             const float4 r2 = r[3 * k + 2];
             const float2 pdx = __fmul2_rn(make_float2(r1.x, r1.x), make_float2(dx[0], dx[1]));
