@@ -540,6 +540,7 @@ __device__ __forceinline__ float rcp_approx(float x) {
 // offsets (shared by its rows).  A pixel with G' = 0 (not reached, or inactive) adds
 // exactly 0, and the opacity-clamped branch is a select, so no per-pixel
 // branch remains.
+template <bool WV>
 __device__ __forceinline__ void pair_grad2(float2 acc[8], float2 &dop, float2 &pv, float2 Gv, float4 r0, float4 r1,
                                            float4 r2, float2 dx, float py, float2 cA, float2 nvS,
                                            float2 e0, float2 e1, float2 e2, float2 eD, float alpha_max) {
@@ -556,7 +557,7 @@ __device__ __forceinline__ void pair_grad2(float2 acc[8], float2 &dop, float2 &p
     acc[5] = __ffma2_rn(ca_al, e0, acc[5]);
     acc[6] = __ffma2_rn(ca_al, e1, acc[6]);
     acc[7] = __ffma2_rn(ca_al, e2, acc[7]);
-    pv = __ffma2_rn(al, rom, pv);
+    if (WV) pv = __ffma2_rn(al, rom, pv);
     float2 dG = __fmul2_rn(dal, Gv);
     dG.x = raw.x < alpha_max ? dG.x : 0.f;
     dG.y = raw.y < alpha_max ? dG.y : 0.f;
@@ -617,7 +618,7 @@ constexpr int BWD_PPL = 4;
 constexpr int BWD_SUB = kTile / (2 * BWD_PPL);  // sub-tiles per tile
 constexpr int BWD_MINB = 24;  // resident one-warp CTAs per SM the register budget is set for
 
-template <int KT, int PPL, bool VAR>
+template <int KT, int PPL, bool VAR, bool WV>
 __global__ void __launch_bounds__(WT, BWD_MINB) k_blend_bwd(const ViewDesc *__restrict__ views, int n_views,
                                                   const uint2 *__restrict__ ranges, const uint32_t *__restrict__ cells,
                                                   const float4 *__restrict__ rec, BlendParams bp,
@@ -710,7 +711,7 @@ __global__ void __launch_bounds__(WT, BWD_MINB) k_blend_bwd(const ViewDesc *__re
     const uint2 rg = ranges[tile];
     const uint32_t end = rg.x + min((uint32_t)ndmax, rg.y - rg.x);
     const float4 *vrec = rec + V.rec_base * kRecF4;
-    const bool want_v = g_cell_v != nullptr;
+    constexpr bool want_v = WV;  // dL/dv_n requested (g_cell_v): else its per-pixel sums are not formed
 
     float2 T[NR], S[NR];
 #pragma unroll
@@ -866,8 +867,8 @@ __global__ void __launch_bounds__(WT, BWD_MINB) k_blend_bwd(const ViewDesc *__re
             for (int rr = 0; rr < NR; ++rr) {
                 float2 e0, e1, e2, eD;
                 efac(rr, e0, e1, e2, eD);
-                pair_grad2(acc2, dop2, pv[rr], gv[rr], r0, r1, r2, gdx, pys[rr], cA[rr], nvS[rr], e0, e1, e2, eD,
-                           bp.alpha_max);
+                pair_grad2<WV>(acc2, dop2, pv[rr], gv[rr], r0, r1, r2, gdx, pys[rr], cA[rr], nvS[rr], e0, e1, e2, eD,
+                               bp.alpha_max);
             }
             float acc[8];
             column_terms(acc2, dop2, r1.w, gdx, acc);
@@ -902,8 +903,14 @@ void launch_blend_bwd(const ViewDesc *views, int n_views, int total_tiles, int K
     if (total_tiles == 0) return;
     const unsigned grid = (unsigned)total_tiles * BWD_SUB;
 #define DGS_BWD(KV, VV)                                                                                          \
-    k_blend_bwd<KV, BWD_PPL, VV><<<grid, WT, 0, st>>>(views, n_views, ranges, tile_cells, rec, bp, rgb, D, nd,     \
-                                                      dL_drgb, g2d, g_cell_v)
+    do {                                                                                                        \
+        if (g_cell_v)                                                                                           \
+            k_blend_bwd<KV, BWD_PPL, VV, true><<<grid, WT, 0, st>>>(views, n_views, ranges, tile_cells, rec, bp,  \
+                                                                    rgb, D, nd, dL_drgb, g2d, g_cell_v);        \
+        else                                                                                                    \
+            k_blend_bwd<KV, BWD_PPL, VV, false><<<grid, WT, 0, st>>>(views, n_views, ranges, tile_cells, rec, bp, \
+                                                                     rgb, D, nd, dL_drgb, g2d, nullptr);        \
+    } while (0)
     if (blend_variants(bp)) {
         switch (K_all) {
             case 8: DGS_BWD(8, true); break;
